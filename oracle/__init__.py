@@ -1,0 +1,314 @@
+"""Plain FP64 CPU oracle for the Gibbs sweep of Landau & Niemi (arXiv 1606.06659).
+
+TEST INFRASTRUCTURE ONLY.  The test-suite, ``__graft_entry__.smoke()`` and the
+CPU-baseline leg of ``bench.py`` import this package; the GPU library
+(``paper_1606_06659_gb300``) never does, and this package never imports it.
+
+The arithmetic lives in ``fbs_oracle.c`` (plain C, no FMA contraction), built
+here with gcc into ``oracle/_build/libfbs_oracle.so`` and called through
+ctypes.  What each C function follows in the paper is stated beside it there:
+Section 4.1 / Figure 3 (model), Algorithm 1 (sweep order), Algorithm 2
+(slice sampler and width tuning), Section 3.1 (running moments).
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+import subprocess
+import threading
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_SRC = os.path.join(_HERE, "fbs_oracle.c")
+_HDR = os.path.join(_HERE, "fbs_oracle.h")
+_BUILD = os.path.join(_HERE, "_build")
+_LIB_PATH = os.path.join(_BUILD, "libfbs_oracle.so")
+_lock = threading.Lock()
+_lib = None
+
+STREAM_EPS, STREAM_GAMMA, STREAM_NU, STREAM_TAU = 1, 2, 3, 4
+STREAM_BETA, STREAM_THETA, STREAM_SIGMA, STREAM_TEST = 5, 6, 7, 200
+
+CFLAGS = ["-O2", "-std=c11", "-ffp-contract=off", "-fno-fast-math", "-fPIC", "-shared"]
+
+
+def build(src: str = _SRC, out: str = _LIB_PATH, defines=()) -> str:
+    """Compile the oracle with gcc (plain IEEE double, no contraction)."""
+    os.makedirs(os.path.dirname(out), exist_ok=True)
+    newest = max(os.path.getmtime(src), os.path.getmtime(_HDR))
+    if os.path.exists(out) and os.path.getmtime(out) >= newest and not defines:
+        return out
+    tmp = out + ".tmp%d" % os.getpid()
+    cmd = ["gcc", *CFLAGS, *[f"-D{d}" for d in defines], "-I", _HERE, src, "-o", tmp, "-lm"]
+    subprocess.run(cmd, check=True)
+    os.replace(tmp, out)
+    return out
+
+
+class Model(C.Structure):
+    _fields_ = [
+        ("N", C.c_int), ("G", C.c_int), ("L", C.c_int),
+        ("y", C.POINTER(C.c_int32)), ("X", C.POINTER(C.c_double)), ("h", C.POINTER(C.c_double)),
+        ("a", C.c_double), ("b", C.c_double), ("d", C.c_double),
+        ("c", C.POINTER(C.c_double)), ("s", C.POINTER(C.c_double)),
+    ]
+
+
+_PD = C.POINTER(C.c_double)
+
+
+class State(C.Structure):
+    _fields_ = [(n, _PD) for n in ("eps", "beta", "gam", "phi", "w_eps", "waux_eps",
+                                   "w_beta", "waux_beta", "w_nu", "waux_nu")]
+
+
+class Opts(C.Structure):
+    _fields_ = [("seed", C.c_uint64), ("chain", C.c_uint32), ("step_out_max", C.c_int),
+                ("shrink_max", C.c_int), ("burnin", C.c_int64), ("tune_start", C.c_int64),
+                ("w0", C.c_double)]
+
+
+class Moments(C.Structure):
+    _fields_ = [(n, _PD) for n in ("mean_eps", "msq_eps", "mean_beta", "msq_beta",
+                                   "mean_gam", "msq_gam", "mean_phi", "msq_phi")] + [
+        ("count", C.c_int64)]
+
+
+class Counters(C.Structure):
+    _fields_ = [(n, C.c_int64) for n in ("evals_eps", "evals_beta", "evals_nu", "slice_caps",
+                                         "gamma_caps", "trunc_caps", "nonfinite")]
+
+
+def _declare(lib):
+    u32, u64, i64, d = C.c_uint32, C.c_uint64, C.c_int64, C.c_double
+    pM, pS, pO = C.POINTER(Model), C.POINTER(State), C.POINTER(Opts)
+    pMo, pCn = C.POINTER(Moments), C.POINTER(Counters)
+    lib.orc_philox4x32_10.argtypes = [C.POINTER(u32), C.POINTER(u32), C.POINTER(u32)]
+    lib.orc_uniform.argtypes = [u64, u32, u32, u32, u32, u32]
+    lib.orc_uniform.restype = d
+    lib.orc_normal.argtypes = [u64, u32, u32, u32, u32, u32]
+    lib.orc_normal.restype = d
+    lib.orc_gamma.argtypes = [d, u64, u32, u32, u32, u32, u32, C.POINTER(i64)]
+    lib.orc_gamma.restype = d
+    lib.orc_fill_uniforms.argtypes = [u64, u32, u32, u32, C.c_int, u32, u32, C.c_int, _PD]
+    lib.orc_fill_gamma.argtypes = [d, u64, u32, u32, u32, C.c_int, u32, _PD]
+    lib.orc_fill_normal.argtypes = [u64, u32, u32, u32, C.c_int, u32, _PD]
+    for name in ("orc_logf_eps",):
+        getattr(lib, name).argtypes = [pM, pS, C.c_int, C.c_int, d]
+        getattr(lib, name).restype = d
+    lib.orc_logf_beta.argtypes = [pM, pS, C.c_int, C.c_int, d]
+    lib.orc_logf_beta.restype = d
+    lib.orc_logf_nu.argtypes = [pM, pS, d]
+    lib.orc_logf_nu.restype = d
+    lib.orc_slice_textbook.argtypes = [C.c_int, d, d, C.c_int, _PD, d, C.c_int, C.c_int, u64,
+                                       u32, _PD, C.POINTER(i64)]
+    for name in ("orc_step_eps", "orc_step_gamma", "orc_step_nu", "orc_step_tau",
+                 "orc_step_beta", "orc_step_theta", "orc_step_sigma"):
+        getattr(lib, name).argtypes = [pM, pS, pO, i64, pCn]
+    lib.orc_step_beta_l.argtypes = [pM, pS, pO, i64, C.c_int, pCn]
+    lib.orc_sweep.argtypes = [pM, pS, pO, i64, pMo, pCn]
+    lib.orc_run.argtypes = [pM, pS, pO, i64, i64, i64, pMo, pCn, _PD, _PD, i64]
+    lib.orc_run.restype = i64
+    lib.orc_init_state.argtypes = [pM, pS, pO]
+    lib.orc_init_state.restype = C.c_int
+    lib.orc_count_sums.argtypes = [pM, C.POINTER(i64)]
+    lib.orc_ess.argtypes = [_PD, i64]
+    lib.orc_ess.restype = d
+    return lib
+
+
+def load(path: str | None = None):
+    """Build (if needed) and load the oracle shared library."""
+    global _lib
+    if path is not None:
+        return _declare(C.CDLL(path))
+    with _lock:
+        if _lib is None:
+            _lib = _declare(C.CDLL(build()))
+    return _lib
+
+
+def _pd(a: np.ndarray):
+    assert a.dtype == np.float64 and a.flags.c_contiguous
+    return a.ctypes.data_as(_PD)
+
+
+# --------------------------------------------------------------------------- RNG helpers
+def philox(ctr, key, lib=None):
+    lib = lib or load()
+    c = (C.c_uint32 * 4)(*[int(v) & 0xFFFFFFFF for v in ctr])
+    k = (C.c_uint32 * 2)(*[int(v) & 0xFFFFFFFF for v in key])
+    o = (C.c_uint32 * 4)()
+    lib.orc_philox4x32_10(c, k, o)
+    return [int(v) for v in o]
+
+
+def uniforms(seed, chain, stream, index0, n_index, it, k0, n_k, lib=None):
+    lib = lib or load()
+    out = np.empty((n_index, n_k), np.float64)
+    lib.orc_fill_uniforms(seed, chain, stream, index0, n_index, it, k0, n_k, _pd(out))
+    return out
+
+
+def gamma_draws(shape, seed, chain, stream, index0, n, it, lib=None):
+    lib = lib or load()
+    out = np.empty(n, np.float64)
+    lib.orc_fill_gamma(float(shape), seed, chain, stream, index0, n, it, _pd(out))
+    return out
+
+
+def normal_draws(seed, chain, stream, index0, n, it, lib=None):
+    lib = lib or load()
+    out = np.empty(n, np.float64)
+    lib.orc_fill_normal(seed, chain, stream, index0, n, it, _pd(out))
+    return out
+
+
+def slice_textbook(kind, p0, p1, x0, w=1.0, K=100, shrink_max=100, seed=1, it=1, lib=None):
+    lib = lib or load()
+    x0 = np.ascontiguousarray(x0, np.float64)
+    out = np.empty_like(x0)
+    ev = C.c_int64(0)
+    lib.orc_slice_textbook(kind, p0, p1, x0.size, _pd(x0), w, K, shrink_max, seed, it,
+                           _pd(out), C.byref(ev))
+    return out, ev.value
+
+
+def ess(x, lib=None):
+    lib = lib or load()
+    x = np.ascontiguousarray(x, np.float64)
+    return lib.orc_ess(_pd(x), x.size)
+
+
+# --------------------------------------------------------------------------- chain
+class Chain:
+    """One chain of the sampler on host arrays; every call goes to the C oracle.
+
+    y: int32 [G][N]; X: [N][L]; h: [N]; priors: dict(a, b, d, c[L], s[L]).
+    """
+
+    def __init__(self, y, X, h, priors, seed=1, chain=0, step_out_max=100, shrink_max=100,
+                 burnin=0, tune_start=None, w0=1.0, lib=None):
+        self.lib = lib or load()
+        self.y = np.ascontiguousarray(y, np.int32)
+        self.G, self.N = self.y.shape
+        self.X = np.ascontiguousarray(X, np.float64).reshape(self.N, -1)
+        self.L = self.X.shape[1]
+        self.h = np.ascontiguousarray(h, np.float64).reshape(self.N)
+        L = self.L
+        self.c = np.ascontiguousarray(np.broadcast_to(priors["c"], (L,)), np.float64)
+        self.s = np.ascontiguousarray(np.broadcast_to(priors["s"], (L,)), np.float64)
+        self.model = Model(self.N, self.G, L, self.y.ctypes.data_as(C.POINTER(C.c_int32)),
+                           _pd(self.X), _pd(self.h), float(priors["a"]), float(priors["b"]),
+                           float(priors["d"]), _pd(self.c), _pd(self.s))
+        G, N = self.G, self.N
+        self.eps = np.zeros((G, N))
+        self.beta = np.zeros((G, L))
+        self.gam = np.ones(G)
+        self.phi = np.zeros(2 * L + 2)
+        self.w_eps = np.full((G, N), w0)
+        self.waux_eps = np.zeros((G, N))
+        self.w_beta = np.full((G, L), w0)
+        self.waux_beta = np.zeros((G, L))
+        self.w_nu = np.full(1, w0)
+        self.waux_nu = np.zeros(1)
+        self.state = State(*[_pd(getattr(self, n)) for n in (
+            "eps", "beta", "gam", "phi", "w_eps", "waux_eps", "w_beta", "waux_beta", "w_nu",
+            "waux_nu")])
+        if tune_start is None:
+            tune_start = burnin // 2
+        self.opts = Opts(seed, chain, step_out_max, shrink_max, burnin, tune_start, w0)
+        self.mean_eps, self.msq_eps = np.zeros((G, N)), np.zeros((G, N))
+        self.mean_beta, self.msq_beta = np.zeros((G, L)), np.zeros((G, L))
+        self.mean_gam, self.msq_gam = np.zeros(G), np.zeros(G)
+        self.mean_phi, self.msq_phi = np.zeros(2 * L + 2), np.zeros(2 * L + 2)
+        self.moments = Moments(*[_pd(getattr(self, n)) for n in (
+            "mean_eps", "msq_eps", "mean_beta", "msq_beta", "mean_gam", "msq_gam", "mean_phi",
+            "msq_phi")], 0)
+        self.counters = Counters()
+        self.it = 0
+
+    # state ---------------------------------------------------------------
+    def init_default(self):
+        rc = self.lib.orc_init_state(C.byref(self.model), C.byref(self.state), C.byref(self.opts))
+        if rc != 0:
+            raise ValueError("X^T X is singular")
+        return self
+
+    def set_state(self, eps=None, beta=None, gam=None, phi=None, w_eps=None, w_beta=None,
+                  w_nu=None, waux_eps=None, waux_beta=None, waux_nu=None, it=None):
+        for name, val in (("eps", eps), ("beta", beta), ("gam", gam), ("phi", phi),
+                          ("w_eps", w_eps), ("w_beta", w_beta), ("w_nu", w_nu),
+                          ("waux_eps", waux_eps), ("waux_beta", waux_beta), ("waux_nu", waux_nu)):
+            if val is not None:
+                getattr(self, name)[...] = np.asarray(val, np.float64).reshape(
+                    getattr(self, name).shape)
+        if it is not None:
+            self.it = int(it)
+        return self
+
+    def get_state(self):
+        return {n: getattr(self, n).copy() for n in (
+            "eps", "beta", "gam", "phi", "w_eps", "waux_eps", "w_beta", "waux_beta", "w_nu",
+            "waux_nu")}
+
+    def set_opts(self, **kw):
+        for k, v in kw.items():
+            setattr(self.opts, k, v)
+
+    # steps -----------------------------------------------------------------
+    def _step(self, name, it, *extra):
+        getattr(self.lib, name)(C.byref(self.model), C.byref(self.state), C.byref(self.opts),
+                                int(it), *extra, C.byref(self.counters))
+
+    def step_eps(self, it): self._step("orc_step_eps", it)
+    def step_gamma(self, it): self._step("orc_step_gamma", it)
+    def step_nu(self, it): self._step("orc_step_nu", it)
+    def step_tau(self, it): self._step("orc_step_tau", it)
+    def step_beta(self, it): self._step("orc_step_beta", it)
+    def step_beta_l(self, it, l): self._step("orc_step_beta_l", it, int(l))
+    def step_theta(self, it): self._step("orc_step_theta", it)
+    def step_sigma(self, it): self._step("orc_step_sigma", it)
+
+    def sweep(self):
+        self.it += 1
+        self.lib.orc_sweep(C.byref(self.model), C.byref(self.state), C.byref(self.opts), self.it,
+                           C.byref(self.moments), C.byref(self.counters))
+
+    def run(self, n_iter, thin=1, trace_cap=0, trace_beta=False):
+        P = 2 * self.L + 2
+        tphi = np.zeros((max(trace_cap, 1), P))
+        tbeta = np.zeros((max(trace_cap, 1), self.G, self.L)) if trace_beta else None
+        rows = self.lib.orc_run(C.byref(self.model), C.byref(self.state), C.byref(self.opts),
+                                self.it, int(n_iter), int(thin), C.byref(self.moments),
+                                C.byref(self.counters), _pd(tphi),
+                                _pd(tbeta) if tbeta is not None else None, int(trace_cap))
+        self.it += int(n_iter)
+        out = {"phi": tphi[:rows]}
+        if tbeta is not None:
+            out["beta"] = tbeta[:rows]
+        return out
+
+    # densities / sums -----------------------------------------------------
+    def logf_eps(self, g, n, x):
+        return self.lib.orc_logf_eps(C.byref(self.model), C.byref(self.state), g, n, x)
+
+    def logf_beta(self, g, l, b):
+        return self.lib.orc_logf_beta(C.byref(self.model), C.byref(self.state), g, l, b)
+
+    def logf_nu(self, nu):
+        return self.lib.orc_logf_nu(C.byref(self.model), C.byref(self.state), nu)
+
+    def count_sums(self):
+        T = np.zeros((self.G, self.L), np.int64)
+        self.lib.orc_count_sums(C.byref(self.model), T.ctypes.data_as(C.POINTER(C.c_int64)))
+        return T
+
+    def moments_dict(self):
+        return {n: getattr(self, n).copy() for n in (
+            "mean_eps", "msq_eps", "mean_beta", "msq_beta", "mean_gam", "msq_gam", "mean_phi",
+            "msq_phi")} | {"count": self.moments.count}
+
+    def counters_dict(self):
+        return {n: getattr(self.counters, n) for n, _ in Counters._fields_}

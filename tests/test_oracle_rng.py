@@ -1,0 +1,107 @@
+"""Pins for the oracle's random numbers (Philox4x32-10, uniforms, normals, gammas).
+
+The paper draws its random numbers with CURAND (Section 4.2); both sides here
+use Philox4x32-10 keyed by (seed, chain) with counters (index, stream|block,
+iteration, chain), so the GPU and the oracle consume identical uniforms.
+"""
+import os
+from fractions import Fraction
+
+import numpy as np
+import pytest
+from scipy import stats
+
+import oracle
+
+GOLDEN = os.path.join(os.path.dirname(__file__), "golden", "philox4x32_10_kat.txt")
+
+
+def _kat_rows():
+    rows = []
+    with open(GOLDEN) as f:
+        for line in f:
+            if line.strip() and not line.startswith("#"):
+                rows.append([int(t, 16) for t in line.split()])
+    return rows
+
+
+def test_philox_known_answers():
+    rows = _kat_rows()
+    assert len(rows) == 3
+    for r in rows:
+        assert oracle.philox(r[0:4], r[4:6]) == r[6:10]
+
+
+def test_philox_matches_triton_interpreter():
+    """An independent Philox4x32-10 (triton's, run in its CPU interpreter)."""
+    pytest.importorskip("triton")
+    import subprocess
+    import sys
+    code = r'''
+import os, sys
+os.environ["TRITON_INTERPRET"] = "1"
+import numpy as np, torch, triton, triton.language as tl
+@triton.jit
+def k(out_ptr, c0_ptr, c1_ptr, c2_ptr, c3_ptr, seed, n: tl.constexpr):
+    i = tl.arange(0, n)
+    a, b, c, d = tl.philox(seed, tl.load(c0_ptr + i), tl.load(c1_ptr + i), tl.load(c2_ptr + i), tl.load(c3_ptr + i))
+    tl.store(out_ptr + 4 * i, a); tl.store(out_ptr + 4 * i + 1, b)
+    tl.store(out_ptr + 4 * i + 2, c); tl.store(out_ptr + 4 * i + 3, d)
+rng = np.random.default_rng(7)
+seed = int(sys.argv[1])
+cs = [torch.from_numpy(rng.integers(0, 2**32, 16, dtype=np.uint64).astype(np.uint32).view(np.int32)) for _ in range(4)]
+out = torch.zeros(64, dtype=torch.int32)
+k[(1,)](out, *cs, seed, n=16)
+for j in range(16):
+    print(" ".join("%08x" % (int(cs[w][j]) & 0xffffffff) for w in range(4)), " ".join("%08x" % (int(v) & 0xffffffff) for v in out[4*j:4*j+4]))
+'''
+    seed = 0x0123456789ABCDEF
+    res = subprocess.run([sys.executable, "-c", code, str(seed)], capture_output=True, text=True,
+                         timeout=300)
+    if res.returncode != 0:
+        pytest.skip("triton interpreter unavailable: " + res.stderr[-200:])
+    lines = [l.split() for l in res.stdout.strip().splitlines()]
+    assert len(lines) == 16
+    key = [seed & 0xFFFFFFFF, seed >> 32]
+    for parts in lines:
+        ctr = [int(t, 16) for t in parts[:4]]
+        want = [int(t, 16) for t in parts[4:]]
+        assert oracle.philox(ctr, key) == want
+
+
+def test_uniform_is_exact_map_of_philox_words():
+    seed, chain, stream, it = 0xDEADBEEF12345678, 3, 5, 77
+    for index in (0, 1, 1234567):
+        for k in range(6):
+            ctr = [index, (stream << 24) | (k >> 1), it, chain]
+            o = oracle.philox(ctr, [seed & 0xFFFFFFFF, seed >> 32])
+            x = (o[3] << 32 | o[2]) if k & 1 else (o[1] << 32 | o[0])
+            want = (Fraction(x >> 12) + Fraction(1, 2)) / 2 ** 52
+            got = oracle.uniforms(seed, chain, stream, index, 1, it, k, 1)[0, 0]
+            assert Fraction(got) == want
+            assert 0.0 < got < 1.0
+
+
+def test_uniform_distribution_and_independence():
+    u = oracle.uniforms(11, 0, 1, 0, 20000, 3, 0, 6)
+    for k in range(6):
+        assert stats.kstest(u[:, k], "uniform").pvalue > 1e-4
+    c = np.corrcoef(u.T)
+    assert np.max(np.abs(c - np.eye(6))) < 0.04
+    # different iterations / streams / chains give different numbers
+    assert not np.array_equal(oracle.uniforms(11, 0, 1, 0, 10, 4, 0, 2), u[:10, :2])
+    assert not np.array_equal(oracle.uniforms(11, 0, 2, 0, 10, 3, 0, 2), u[:10, :2])
+    assert not np.array_equal(oracle.uniforms(11, 1, 1, 0, 10, 3, 0, 2), u[:10, :2])
+
+
+def test_normal_ks():
+    z = oracle.normal_draws(5, 0, 200, 0, 100000, 1)
+    assert stats.kstest(z, "norm").pvalue > 1e-4
+    assert abs(z.mean()) < 0.02 and abs(z.std() - 1) < 0.02
+
+
+@pytest.mark.parametrize("shape", [0.3, 1.0, 2.5, 9.5, 20000.0])
+def test_gamma_ks(shape):
+    g = oracle.gamma_draws(shape, 9, 0, 200, 0, 60000, 2)
+    assert np.all(g > 0)
+    assert stats.kstest(g, stats.gamma(shape).cdf).pvalue > 1e-4

@@ -1,0 +1,201 @@
+/*
+ * fbs.h -- C ABI of the GB300 Gibbs sampler for the fully Bayesian RNA-seq
+ * hierarchical model of Landau & Niemi, "A fully Bayesian strategy for
+ * high-dimensional hierarchical modeling using massively parallel computing"
+ * (arXiv 1606.06659).
+ *
+ * Model (Section 4.1, Figure 3), for genes g = 1..G, samples n = 1..N,
+ * columns l = 1..L of the N x L model matrix X:
+ *   y_gn      ~ Poisson(exp(h_n + eps_gn + X_n beta_g))
+ *   eps_gn    ~ Normal(0, gamma_g)
+ *   gamma_g   ~ Inverse-Gamma(nu/2, nu tau/2)
+ *   nu        ~ Uniform(0, d),   tau ~ Gamma(a, rate b)
+ *   beta_gl   ~ Normal(theta_l, sigma_l^2)
+ *   theta_l   ~ Normal(0, c_l^2), sigma_l ~ Uniform(0, s_l)
+ *
+ * One iteration ("sweep") is Algorithm 1 (Section 4.2): slice updates of
+ * every eps_gn and beta_gl (Algorithm 2, Appendix A, with its width tuning),
+ * conjugate draws of gamma_g, tau, theta_l and sigma_l^2 (truncated
+ * inverse-gamma), a slice update of nu, and post-burn-in running means and
+ * mean squares of every parameter (Section 3.1).  All of it runs in this
+ * library's CUDA kernels on one GPU; the host only launches them.
+ *
+ * Hyperparameter vector phi (length 2L+2) is ordered
+ *   (nu, tau, theta_1..theta_L, sigma_1^2..sigma_L^2).
+ *
+ * Random numbers: Philox4x32-10 (Salmon et al., SC 2011) keyed by the 64-bit
+ * seed, with counter (index, stream<<24 | block, iteration, chain); uniform k
+ * of a variable is ((x >> 12) + 1/2) / 2^52 for the 64-bit word pair x of
+ * block k/2.  The same definition, written independently, drives the CPU
+ * oracle, so both consume identical uniforms.
+ *
+ * Errors: every int-returning call returns FBS_OK (0) or a negative FBS_E_*
+ * code and sets a thread-local message readable with fbs_last_error_string().
+ * No call throws across the ABI.  Calls on one handle must not run
+ * concurrently from several host threads.
+ */
+#ifndef FBS_H
+#define FBS_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define FBS_OK 0
+#define FBS_E_ARG (-1)       /* invalid argument (sizes, non-finite inputs, singular X ...) */
+#define FBS_E_CUDA (-2)      /* a CUDA runtime call failed */
+#define FBS_E_OOM (-3)       /* device memory could not be obtained */
+#define FBS_E_NONFINITE (-5) /* a slice update started from a non-finite log density */
+
+#define FBS_MAX_N 64 /* samples */
+#define FBS_MAX_L 8  /* columns of X */
+#define FBS_MAX_CLASSES 8 /* distinct non-zero values in one column of X */
+
+#define FBS_F64 0 /* all arithmetic in FP64 */
+#define FBS_F32 1 /* slice log densities in FP32; reductions, hyperparameters, moments FP64 */
+
+/* Counter slots returned by fbs_counters(). */
+#define FBS_CNT_EVALS_EPS 0   /* log-density evaluations, eps updates */
+#define FBS_CNT_EVALS_BETA 1  /* log-density evaluations, beta updates */
+#define FBS_CNT_EVALS_NU 2    /* log-density evaluations, nu updates */
+#define FBS_CNT_SLICE_CAPS 3  /* slice updates that ran out of shrinkage proposals */
+#define FBS_CNT_GAMMA_CAPS 4  /* gamma draws that ran out of attempts */
+#define FBS_CNT_TRUNC_CAPS 5  /* truncated sigma^2 draws that kept their value */
+#define FBS_CNT_NONFINITE 6   /* slice updates started at a non-finite log density */
+#define FBS_CNT_SWEEPS 7      /* completed iterations */
+#define FBS_NUM_COUNTERS 8
+
+typedef struct fbs_handle fbs_handle;
+
+/* Prior constants (Section 4.1): tau ~ Gamma(a, rate b), nu ~ U(0, d),
+ * theta_l ~ N(0, c_l^2), sigma_l ~ U(0, s_l).  c and s point to L host
+ * doubles, read during fbs_init only.  All must be finite and > 0. */
+typedef struct {
+  double a, b, d;
+  const double* c;
+  const double* s;
+} fbs_priors;
+
+typedef struct {
+  int precision;         /* FBS_F64 or FBS_F32 */
+  double w0;             /* initial slice width of every slice variable (Algorithm 2) */
+  int step_out_max;      /* K of Algorithm 2: stepping-out bound, split into K_L + K_R */
+  int shrink_max;        /* shrinkage proposals per update before the update keeps x0 */
+  uint32_t chain;        /* chain number, the fourth Philox counter word */
+  int moments_eps;       /* 1: keep running moments of every eps_gn (default 1) */
+  int64_t trace_cap;     /* rows of the thinned trace (phi, and beta if trace_beta) */
+  int trace_beta;        /* 1: the trace also stores all G*L beta per row */
+  int block;             /* threads per block of the per-gene kernel (0: library choice) */
+  int graph_segment;     /* iterations per captured CUDA graph (0: library choice, 100) */
+} fbs_options;
+
+/* Fill *o with the defaults: FP64, w0 = 1, K = 100, shrink_max = 100, chain 0,
+ * eps moments on, no trace, library-chosen block and graph segment. */
+void fbs_default_options(fbs_options* o);
+
+/* Device bytes fbs_init needs for these sizes and options (*bytes), so that a
+ * caller can provide the memory itself (for example from the PyTorch caching
+ * allocator).  Returns FBS_E_ARG for sizes outside the limits. */
+int fbs_workspace_bytes(int N, int G, int L, const fbs_options* opt, size_t* bytes);
+
+/* Create a sampler.  y: N*G host int32 counts, gene-major ([G][N]) when
+ * gene_major != 0, else sample-major ([N][G]); X: host [N][L] row-major;
+ * h: host [N] offsets.  All host arrays are copied during the call and stay
+ * owned by the caller.  workspace: NULL (the library allocates and frees its
+ * device memory) or a device pointer to >= fbs_workspace_bytes() bytes,
+ * 256-byte aligned, owned by the caller and not touched after fbs_free.
+ * stream: the cudaStream_t on which all work of this handle is ordered
+ * (NULL = legacy default stream).
+ * The starting state is the library default (eps = 0; beta_g least squares of
+ * log(y_gn + 1) - h_n on X; gamma_g = 1; theta_l, sigma_l^2 the mean and variance
+ * of beta_gl over genes, the variance clamped to [1e-6, s_l^2/4]; nu = min(3, d/2);
+ * tau = 1; widths w0), at iteration 0.
+ * Errors: FBS_E_ARG when N < 1, N > FBS_MAX_N, G < 2, L < 1, L > FBS_MAX_L,
+ * a column of X has more than FBS_MAX_CLASSES distinct non-zero values, X^T X is
+ * singular, y < 0, a non-finite X or h, a prior constant <= 0 or non-finite, or a
+ * too-small workspace; FBS_E_OOM / FBS_E_CUDA from device allocation or copies. */
+int fbs_init(fbs_handle** out, const int32_t* y, int N, int G, int gene_major, const double* X,
+             int L, const double* h, const fbs_priors* pri, const fbs_options* opt,
+             uint64_t seed, void* workspace, size_t workspace_bytes, void* stream);
+
+/* Run iterations m = it+1 .. it+n_iter (it = iterations done so far) of
+ * Algorithm 1.  burnin is M_B: slice widths are tuned while m <= M_B (after
+ * M_C = burnin/2 iterations, Algorithm 2 step 7) and running moments and the
+ * trace take the draws with m > M_B.  Every thin-th post-burn-in draw
+ * ((m - M_B) % thin == 0) is appended to the trace while rows remain.
+ * Asynchronous on the handle's stream; returns after enqueueing. Resumable:
+ * a later call continues the same chain (keep burnin and thin the same).
+ * Errors: FBS_E_ARG for n_iter < 0, burnin < 0 or thin < 1; FBS_E_CUDA. */
+int fbs_run(fbs_handle* h, int64_t n_iter, int64_t burnin, int64_t thin);
+
+/* Wait for the handle's work.  Returns FBS_E_NONFINITE if any slice update
+ * so far started from a non-finite log density, FBS_E_CUDA on a CUDA error,
+ * else FBS_OK. */
+int fbs_sync(fbs_handle* h);
+
+/* Running moments (Section 3.1) copied to caller-allocated host arrays, in
+ * gene-major layout: eps [G][N], beta [G][L], gamma [G], phi [2L+2].  Any
+ * pointer may be NULL to skip that array.  *count receives the number of
+ * draws folded in.  Posterior sd = sqrt(msq - mean^2).  Synchronous. */
+int fbs_moments(fbs_handle* h, double* mean_eps, double* msq_eps, double* mean_beta,
+                double* msq_beta, double* mean_gam, double* msq_gam, double* mean_phi,
+                double* msq_phi, int64_t* count);
+
+/* Current state to / from host arrays (gene-major, as in fbs_moments), with
+ * slice widths w and tuning sums w_aux: eps, w_eps, waux_eps [G][N]; beta,
+ * w_beta, waux_beta [G][L]; gamma [G]; phi [2L+2]; w_nu, waux_nu [1]; *it the
+ * iteration count.  NULL pointers are skipped.  fbs_set_state also resets
+ * the running moments and the trace.  Synchronous. */
+int fbs_get_state(fbs_handle* h, double* eps, double* beta, double* gam, double* phi,
+                  double* w_eps, double* waux_eps, double* w_beta, double* waux_beta,
+                  double* w_nu, double* waux_nu, int64_t* it);
+int fbs_set_state(fbs_handle* h, const double* eps, const double* beta, const double* gam,
+                  const double* phi, const double* w_eps, const double* waux_eps,
+                  const double* w_beta, const double* waux_beta, const double* w_nu,
+                  const double* waux_nu, int64_t it);
+
+/* Thinned trace: up to max_rows rows copied to host: phi rows [rows][2L+2] and,
+ * when the handle keeps it and beta != NULL, beta rows [rows][G][L].
+ * *rows receives the number of rows copied.  Synchronous. */
+int fbs_trace(fbs_handle* h, int64_t max_rows, double* phi, double* beta, int64_t* rows);
+
+/* Effective sample size (Geyer's initial monotone sequence) of every column
+ * of the device beta trace: ess [G][L] host array.  Runs in this library's
+ * kernel on the stored trace rows.  FBS_E_ARG if the handle keeps no beta
+ * trace or it holds fewer than 4 rows. Synchronous. */
+int fbs_beta_ess(fbs_handle* h, double* ess);
+
+/* Exact integer sums T_gl = sum_n y_gn X_nl computed on the device, for
+ * integer-valued X: T [G][L] host int64.  FBS_E_ARG if X is not integral. */
+int fbs_count_sums(fbs_handle* h, int64_t* T);
+
+/* Counters (FBS_CNT_* slots, FBS_NUM_COUNTERS values) to a host array. */
+int fbs_counters(fbs_handle* h, int64_t* out);
+
+/* Runs n_iter iterations launching the two sweep kernels directly (no graph)
+ * with CUDA events around each launch on the launching stream, and reports the
+ * mean duration in milliseconds of the per-gene kernel (*ms_gene) and of the
+ * hyperparameter kernel (*ms_hyper).  The chain advances as with fbs_run.
+ * Synchronous. */
+int fbs_profile(fbs_handle* h, int64_t n_iter, int64_t burnin, int64_t thin, double* ms_gene,
+                double* ms_hyper);
+
+/* Philox uniforms exactly as the sampler draws them: out[i*n_k + k] is uniform
+ * k0+k of variable index0+i of `stream` at iteration `iter` of chain `chain`,
+ * generated on the device.  out is a host array of n_index*n_k doubles. */
+int fbs_uniforms(uint64_t seed, uint32_t chain, uint32_t stream, uint32_t index0, int n_index,
+                 uint32_t iter, uint32_t k0, int n_k, double* out);
+
+/* Release the handle and any memory the library allocated for it. */
+void fbs_free(fbs_handle* h);
+
+/* Message describing the last error on the calling thread ("" if none). */
+const char* fbs_last_error_string(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* FBS_H */

@@ -1,0 +1,259 @@
+"""GB300 Gibbs sampler for the fully Bayesian RNA-seq hierarchical model of
+Landau & Niemi, "A fully Bayesian strategy for high-dimensional hierarchical
+modeling using massively parallel computing" (arXiv 1606.06659).
+
+This module is a thin ctypes binding of the C ABI in ``include/fbs.h`` (the
+library ``_build/libfbs.so``, built by ``paper_1606_06659_gb300.build``).  It
+only marshals arguments: every step of a sweep runs in the library's CUDA
+kernels.  PyTorch, when given, provides the device workspace (caching
+allocator) and the CUDA stream.  There is no CPU fallback: importing fails if
+the library has not been built, and creating a sampler fails without a GPU.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "_build", "libfbs.so")
+
+FBS_OK, FBS_E_ARG, FBS_E_CUDA, FBS_E_OOM, FBS_E_NONFINITE = 0, -1, -2, -3, -5
+FBS_F64, FBS_F32 = 0, 1
+MAX_N, MAX_L, MAX_CLASSES = 64, 8, 8
+COUNTER_NAMES = ("evals_eps", "evals_beta", "evals_nu", "slice_caps", "gamma_caps",
+                 "trunc_caps", "nonfinite", "sweeps")
+NUM_COUNTERS = len(COUNTER_NAMES)
+
+# symbols declared in include/fbs.h
+EXPORTED = ("fbs_default_options", "fbs_workspace_bytes", "fbs_init", "fbs_run", "fbs_sync",
+            "fbs_moments", "fbs_get_state", "fbs_set_state", "fbs_trace", "fbs_beta_ess",
+            "fbs_count_sums", "fbs_counters", "fbs_profile", "fbs_uniforms", "fbs_free",
+            "fbs_last_error_string")
+
+
+class FbsError(RuntimeError):
+    def __init__(self, code, msg):
+        super().__init__(f"fbs error {code}: {msg}")
+        self.code = code
+
+
+class Priors(C.Structure):
+    _fields_ = [("a", C.c_double), ("b", C.c_double), ("d", C.c_double),
+                ("c", C.POINTER(C.c_double)), ("s", C.POINTER(C.c_double))]
+
+
+class Options(C.Structure):
+    _fields_ = [("precision", C.c_int), ("w0", C.c_double), ("step_out_max", C.c_int),
+                ("shrink_max", C.c_int), ("chain", C.c_uint32), ("moments_eps", C.c_int),
+                ("trace_cap", C.c_int64), ("trace_beta", C.c_int), ("block", C.c_int),
+                ("graph_segment", C.c_int)]
+
+
+_PD = C.POINTER(C.c_double)
+_PI64 = C.POINTER(C.c_int64)
+_lib = None
+
+
+def load_library(path: str = LIB_PATH):
+    """Load libfbs.so; raises if it has not been built."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(path):
+        raise ImportError(f"{path} is missing: build it with `python -m paper_1606_06659_gb300.build`")
+    lib = C.CDLL(path)
+    vp, i32, i64, u32, u64, d = C.c_void_p, C.c_int, C.c_int64, C.c_uint32, C.c_uint64, C.c_double
+    lib.fbs_default_options.argtypes = [C.POINTER(Options)]
+    lib.fbs_default_options.restype = None
+    lib.fbs_workspace_bytes.argtypes = [i32, i32, i32, C.POINTER(Options), C.POINTER(C.c_size_t)]
+    lib.fbs_init.argtypes = [C.POINTER(vp), C.POINTER(C.c_int32), i32, i32, i32, _PD, i32, _PD,
+                             C.POINTER(Priors), C.POINTER(Options), u64, vp, C.c_size_t, vp]
+    lib.fbs_run.argtypes = [vp, i64, i64, i64]
+    lib.fbs_sync.argtypes = [vp]
+    lib.fbs_moments.argtypes = [vp] + [_PD] * 8 + [_PI64]
+    lib.fbs_get_state.argtypes = [vp] + [_PD] * 10 + [_PI64]
+    lib.fbs_set_state.argtypes = [vp] + [_PD] * 10 + [i64]
+    lib.fbs_trace.argtypes = [vp, i64, _PD, _PD, _PI64]
+    lib.fbs_beta_ess.argtypes = [vp, _PD]
+    lib.fbs_count_sums.argtypes = [vp, _PI64]
+    lib.fbs_counters.argtypes = [vp, _PI64]
+    lib.fbs_profile.argtypes = [vp, i64, i64, i64, _PD, _PD]
+    lib.fbs_uniforms.argtypes = [u64, u32, u32, u32, i32, u32, u32, i32, _PD]
+    lib.fbs_free.argtypes = [vp]
+    lib.fbs_free.restype = None
+    lib.fbs_last_error_string.argtypes = []
+    lib.fbs_last_error_string.restype = C.c_char_p
+    _lib = lib
+    return lib
+
+
+def _check(rc):
+    if rc != FBS_OK:
+        msg = load_library().fbs_last_error_string().decode()
+        raise FbsError(rc, msg)
+
+
+def _pd(a):
+    if a is None:
+        return None
+    assert a.dtype == np.float64 and a.flags.c_contiguous
+    return a.ctypes.data_as(_PD)
+
+
+def default_options(**kw) -> Options:
+    o = Options()
+    load_library().fbs_default_options(C.byref(o))
+    for k, v in kw.items():
+        if not hasattr(o, k):
+            raise TypeError(f"unknown option {k}")
+        setattr(o, k, v)
+    return o
+
+
+def workspace_bytes(N, G, L, options: Options | None = None) -> int:
+    n = C.c_size_t(0)
+    _check(load_library().fbs_workspace_bytes(N, G, L, C.byref(options or default_options()),
+                                              C.byref(n)))
+    return n.value
+
+
+def uniforms(seed, chain, stream, index0, n_index, it, k0, n_k) -> np.ndarray:
+    """Uniforms generated on the device exactly as the sampler draws them."""
+    out = np.empty((n_index, n_k), np.float64)
+    _check(load_library().fbs_uniforms(seed, chain, stream, index0, n_index, it, k0, n_k,
+                                       _pd(out)))
+    return out
+
+
+class Sampler:
+    """One chain of the GPU sampler.
+
+    y: [G][N] int32 counts (or [N][G] with gene_major=False); X: [N][L];
+    h: [N]; priors: dict(a, b, d, c[L], s[L]).  ``workspace="torch"`` takes
+    the device memory from the PyTorch caching allocator and orders the work on
+    torch's current stream; ``workspace="library"`` lets the library allocate.
+    """
+
+    def __init__(self, y, X, h, priors, seed=1, gene_major=True, workspace="torch",
+                 options: Options | None = None, **option_kw):
+        self.lib = load_library()
+        y = np.ascontiguousarray(y, np.int32)
+        if gene_major:
+            self.G, self.N = y.shape
+        else:
+            self.N, self.G = y.shape
+        X = np.ascontiguousarray(X, np.float64)
+        if X.ndim != 2:
+            X = X.reshape(self.N, -1)
+        self.L = X.shape[1]
+        h = np.ascontiguousarray(h, np.float64).reshape(self.N)
+        self.P = 2 * self.L + 2
+        c = np.ascontiguousarray(np.broadcast_to(priors["c"], (self.L,)), np.float64)
+        s = np.ascontiguousarray(np.broadcast_to(priors["s"], (self.L,)), np.float64)
+        pri = Priors(float(priors["a"]), float(priors["b"]), float(priors["d"]), _pd(c), _pd(s))
+        self.options = options or default_options()
+        for k, v in option_kw.items():
+            setattr(self.options, k, v)
+        self._ws = None
+        ws_ptr, ws_bytes, stream = None, 0, None
+        if workspace == "torch":
+            import torch
+            if not torch.cuda.is_available():
+                raise RuntimeError("no CUDA device")
+            ws_bytes = workspace_bytes(self.N, self.G, self.L, self.options)
+            self._ws = torch.empty(ws_bytes, dtype=torch.uint8, device="cuda")
+            ws_ptr = self._ws.data_ptr()
+            stream = torch.cuda.current_stream().cuda_stream
+        handle = C.c_void_p()
+        _check(self.lib.fbs_init(C.byref(handle), y.ctypes.data_as(C.POINTER(C.c_int32)), self.N,
+                                 self.G, 1 if gene_major else 0, _pd(X), self.L, _pd(h),
+                                 C.byref(pri), C.byref(self.options), int(seed), ws_ptr, ws_bytes,
+                                 stream))
+        self.h = handle
+
+    def close(self):
+        if getattr(self, "h", None):
+            self.lib.fbs_free(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    # --------------------------------------------------------------- running
+    def run(self, n_iter, burnin=0, thin=1):
+        _check(self.lib.fbs_run(self.h, int(n_iter), int(burnin), int(thin)))
+
+    def sync(self):
+        _check(self.lib.fbs_sync(self.h))
+
+    def profile(self, n_iter, burnin=0, thin=1):
+        a, b = C.c_double(), C.c_double()
+        _check(self.lib.fbs_profile(self.h, int(n_iter), int(burnin), int(thin), C.byref(a),
+                                    C.byref(b)))
+        return a.value, b.value
+
+    # --------------------------------------------------------------- state
+    def get_state(self):
+        G, N, L, P = self.G, self.N, self.L, self.P
+        out = {"eps": np.empty((G, N)), "beta": np.empty((G, L)), "gam": np.empty(G),
+               "phi": np.empty(P), "w_eps": np.empty((G, N)), "waux_eps": np.empty((G, N)),
+               "w_beta": np.empty((G, L)), "waux_beta": np.empty((G, L)), "w_nu": np.empty(1),
+               "waux_nu": np.empty(1)}
+        it = C.c_int64()
+        _check(self.lib.fbs_get_state(self.h, *[_pd(out[k]) for k in (
+            "eps", "beta", "gam", "phi", "w_eps", "waux_eps", "w_beta", "waux_beta", "w_nu",
+            "waux_nu")], C.byref(it)))
+        out["it"] = it.value
+        return out
+
+    def set_state(self, it=0, **arrays):
+        names = ("eps", "beta", "gam", "phi", "w_eps", "waux_eps", "w_beta", "waux_beta", "w_nu",
+                 "waux_nu")
+        unknown = set(arrays) - set(names)
+        if unknown:
+            raise TypeError(f"unknown state arrays {unknown}")
+        conv = {k: np.ascontiguousarray(np.atleast_1d(v), np.float64) for k, v in arrays.items()
+                if v is not None}
+        _check(self.lib.fbs_set_state(self.h, *[_pd(conv.get(k)) for k in names], int(it)))
+
+    def moments(self):
+        G, N, L, P = self.G, self.N, self.L, self.P
+        out = {"mean_eps": np.empty((G, N)), "msq_eps": np.empty((G, N)),
+               "mean_beta": np.empty((G, L)), "msq_beta": np.empty((G, L)),
+               "mean_gam": np.empty(G), "msq_gam": np.empty(G), "mean_phi": np.empty(P),
+               "msq_phi": np.empty(P)}
+        cnt = C.c_int64()
+        _check(self.lib.fbs_moments(self.h, *[_pd(v) for v in out.values()], C.byref(cnt)))
+        out["count"] = cnt.value
+        return out
+
+    def trace(self, max_rows=None, beta=False):
+        cap = int(self.options.trace_cap) if max_rows is None else int(max_rows)
+        phi = np.empty((max(cap, 0), self.P))
+        bt = np.empty((max(cap, 0), self.G, self.L)) if beta else None
+        rows = C.c_int64()
+        _check(self.lib.fbs_trace(self.h, cap, _pd(phi), _pd(bt), C.byref(rows)))
+        out = {"phi": phi[:rows.value]}
+        if beta:
+            out["beta"] = bt[:rows.value]
+        return out
+
+    def beta_ess(self):
+        ess = np.empty((self.G, self.L))
+        _check(self.lib.fbs_beta_ess(self.h, _pd(ess)))
+        return ess
+
+    def count_sums(self):
+        T = np.empty((self.G, self.L), np.int64)
+        _check(self.lib.fbs_count_sums(self.h, T.ctypes.data_as(_PI64)))
+        return T
+
+    def counters(self):
+        c = np.zeros(NUM_COUNTERS, np.int64)
+        _check(self.lib.fbs_counters(self.h, c.ctypes.data_as(_PI64)))
+        return dict(zip(COUNTER_NAMES, (int(v) for v in c)))

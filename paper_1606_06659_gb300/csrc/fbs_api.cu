@@ -1,0 +1,679 @@
+// fbs_api.cu -- the extern "C" entry points declared in include/fbs.h: input
+// validation, device memory layout, CUDA-graph capture of sweep segments and
+// the host side of every copy.  All sampling arithmetic is in fbs_kernels.cu.
+#include <cuda_runtime.h>
+#include <math.h>
+#include <stdint.h>
+#include <stdio.h>
+#include <string.h>
+
+#include <map>
+#include <string>
+#include <vector>
+
+#include "fbs.h"
+#include "fbs_common.cuh"
+#include "fbs_kernels.h"
+
+using namespace fbs;
+
+namespace {
+
+thread_local std::string g_err;
+
+int fail(int code, const std::string& msg) {
+  g_err = msg;
+  return code;
+}
+
+#define FBS_CUDA(call)                                                                    \
+  do {                                                                                    \
+    cudaError_t e_ = (call);                                                              \
+    if (e_ != cudaSuccess)                                                                \
+      return fail(e_ == cudaErrorMemoryAllocation ? FBS_E_OOM : FBS_E_CUDA,               \
+                  std::string(#call) + ": " + cudaGetErrorString(e_));                    \
+  } while (0)
+
+size_t align256(size_t x) { return (x + 255) & ~(size_t)255; }
+
+// Byte offsets of every device buffer inside one workspace.
+struct Layout {
+  size_t y, T, eps, w_eps, waux_eps, m_eps, q_eps, beta, w_beta, waux_beta, m_beta, q_beta;
+  size_t gam, m_gam, q_gam, partial, hyp, trace_phi, trace_beta, counters, pinv, total;
+};
+
+Layout make_layout(int N, int G, int L, int nblk, long long trace_cap, int trace_beta) {
+  Layout o;
+  size_t at = 0;
+  auto take = [&](size_t bytes) {
+    size_t here = at;
+    at = align256(at + bytes);
+    return here;
+  };
+  const size_t NG = (size_t)N * G, LG = (size_t)L * G, P = 2 * (size_t)L + 2;
+  o.y = take(NG * sizeof(int32_t));
+  o.T = take(LG * 8);
+  o.eps = take(NG * 8);
+  o.w_eps = take(NG * 8);
+  o.waux_eps = take(NG * 8);
+  o.m_eps = take(NG * 8);
+  o.q_eps = take(NG * 8);
+  o.beta = take(LG * 8);
+  o.w_beta = take(LG * 8);
+  o.waux_beta = take(LG * 8);
+  o.m_beta = take(LG * 8);
+  o.q_beta = take(LG * 8);
+  o.gam = take((size_t)G * 8);
+  o.m_gam = take((size_t)G * 8);
+  o.q_gam = take((size_t)G * 8);
+  o.partial = take((size_t)nblk * kNumPart * 8);
+  o.hyp = take(sizeof(Hyper));
+  o.trace_phi = take((size_t)(trace_cap > 0 ? trace_cap : 1) * P * 8);
+  o.trace_beta = trace_beta && trace_cap > 0 ? take((size_t)trace_cap * LG * 8) : 0;
+  o.counters = take(FBS_NUM_COUNTERS * sizeof(unsigned long long));
+  o.pinv = take((size_t)kMaxL * kMaxN * 8);
+  o.total = at + 256;  // slack for aligning an unaligned base
+  return o;
+}
+
+int block_of(const fbs_options* o) {
+  int b = o && o->block > 0 ? o->block : kDefaultBlock;
+  return b;
+}
+
+}  // namespace
+
+struct fbs_handle {
+  ModelConst mc;
+  DevPtrs p;
+  fbs_options opt;
+  Layout lay;
+  int block = kDefaultBlock, nblk = 0, seg = 100;
+  bool x_integral = false;
+  void* ws = nullptr;
+  bool own_ws = false;
+  cudaStream_t user = nullptr;  // caller's stream (ordering only)
+  cudaStream_t s = nullptr;     // handle's own stream (all work, graph capture)
+  cudaEvent_t ev_in = nullptr, ev_out = nullptr;
+  cudaGraphExec_t seg_exec = nullptr;
+  long long trace_cap = 0;
+};
+
+namespace {
+
+int enter(fbs_handle* h) {
+  FBS_CUDA(cudaEventRecord(h->ev_in, h->user));
+  FBS_CUDA(cudaStreamWaitEvent(h->s, h->ev_in, 0));
+  return FBS_OK;
+}
+
+int leave(fbs_handle* h) {
+  FBS_CUDA(cudaEventRecord(h->ev_out, h->s));
+  FBS_CUDA(cudaStreamWaitEvent(h->user, h->ev_out, 0));
+  return FBS_OK;
+}
+
+int check_opts(const fbs_options* o) {
+  if (!o) return FBS_OK;
+  if (o->precision != FBS_F64 && o->precision != FBS_F32)
+    return fail(FBS_E_ARG, "precision must be FBS_F64 or FBS_F32");
+  if (o->precision == FBS_F32) return fail(FBS_E_ARG, "FBS_F32 is not available in this build");
+  if (!(o->w0 > 0.0) || !isfinite(o->w0)) return fail(FBS_E_ARG, "w0 must be finite and > 0");
+  if (o->step_out_max < 0 || o->step_out_max > (1 << 20))
+    return fail(FBS_E_ARG, "step_out_max out of range");
+  if (o->shrink_max < 0 || o->shrink_max > (1 << 20))
+    return fail(FBS_E_ARG, "shrink_max out of range");
+  if (o->trace_cap < 0) return fail(FBS_E_ARG, "trace_cap must be >= 0");
+  if (o->block < 0 || o->block > 128 || (o->block % 32) != 0)
+    return fail(FBS_E_ARG, "block must be 0 or a multiple of 32 up to 128");
+  if (o->graph_segment < 0) return fail(FBS_E_ARG, "graph_segment must be >= 0");
+  return FBS_OK;
+}
+
+int check_sizes(int N, int G, int L) {
+  if (N < 1 || N > FBS_MAX_N) return fail(FBS_E_ARG, "N must be in [1, FBS_MAX_N]");
+  if (G < 2) return fail(FBS_E_ARG, "G must be >= 2");
+  if (L < 1 || L > FBS_MAX_L) return fail(FBS_E_ARG, "L must be in [1, FBS_MAX_L]");
+  return FBS_OK;
+}
+
+// (X^T X)^-1 X^T by Gauss-Jordan elimination with partial pivoting; false if singular.
+bool pseudo_inverse(const double* X, int N, int L, double* pinv /* [kMaxL][kMaxN] */) {
+  std::vector<double> A((size_t)L * 2 * L, 0.0);
+  for (int i = 0; i < L; ++i) {
+    for (int j = 0; j < L; ++j) {
+      double s = 0.0;
+      for (int n = 0; n < N; ++n) s += X[n * L + i] * X[n * L + j];
+      A[i * 2 * L + j] = s;
+    }
+    A[i * 2 * L + L + i] = 1.0;
+  }
+  double scale = 0.0;
+  for (int i = 0; i < L; ++i) scale = fmax(scale, fabs(A[i * 2 * L + i]));
+  for (int col = 0; col < L; ++col) {
+    int piv = col;
+    for (int r = col + 1; r < L; ++r)
+      if (fabs(A[r * 2 * L + col]) > fabs(A[piv * 2 * L + col])) piv = r;
+    if (!(fabs(A[piv * 2 * L + col]) > 1e-10 * scale)) return false;
+    if (piv != col)
+      for (int j = 0; j < 2 * L; ++j) std::swap(A[col * 2 * L + j], A[piv * 2 * L + j]);
+    const double pv = A[col * 2 * L + col];
+    for (int j = 0; j < 2 * L; ++j) A[col * 2 * L + j] /= pv;
+    for (int r = 0; r < L; ++r) {
+      if (r == col) continue;
+      const double f = A[r * 2 * L + col];
+      for (int j = 0; j < 2 * L; ++j) A[r * 2 * L + j] -= f * A[col * 2 * L + j];
+    }
+  }
+  for (int i = 0; i < kMaxL * kMaxN; ++i) pinv[i] = 0.0;
+  for (int l = 0; l < L; ++l)
+    for (int n = 0; n < N; ++n) {
+      double s = 0.0;
+      for (int k = 0; k < L; ++k) s += A[l * 2 * L + L + k] * X[n * L + k];
+      pinv[l * kMaxN + n] = s;
+    }
+  return true;
+}
+
+DevPtrs carve(char* base, const Layout& o, int trace_beta) {
+  DevPtrs p;
+  p.y = (const int32_t*)(base + o.y);
+  p.T = (const double*)(base + o.T);
+  p.eps = (double*)(base + o.eps);
+  p.w_eps = (double*)(base + o.w_eps);
+  p.waux_eps = (double*)(base + o.waux_eps);
+  p.m_eps = (double*)(base + o.m_eps);
+  p.q_eps = (double*)(base + o.q_eps);
+  p.beta = (double*)(base + o.beta);
+  p.w_beta = (double*)(base + o.w_beta);
+  p.waux_beta = (double*)(base + o.waux_beta);
+  p.m_beta = (double*)(base + o.m_beta);
+  p.q_beta = (double*)(base + o.q_beta);
+  p.gam = (double*)(base + o.gam);
+  p.m_gam = (double*)(base + o.m_gam);
+  p.q_gam = (double*)(base + o.q_gam);
+  p.partial = (double*)(base + o.partial);
+  p.hyp = (Hyper*)(base + o.hyp);
+  p.trace_phi = (double*)(base + o.trace_phi);
+  p.trace_beta = trace_beta ? (double*)(base + o.trace_beta) : nullptr;
+  p.counters = (unsigned long long*)(base + o.counters);
+  return p;
+}
+
+// Copy a device [R][G] plane set to a host [G][R] array.
+int to_host_gene_major(fbs_handle* h, const double* dev, int R, double* host) {
+  const int G = h->mc.G;
+  std::vector<double> tmp((size_t)R * G);
+  FBS_CUDA(cudaMemcpyAsync(tmp.data(), dev, tmp.size() * 8, cudaMemcpyDeviceToHost, h->s));
+  FBS_CUDA(cudaStreamSynchronize(h->s));
+  for (int r = 0; r < R; ++r)
+    for (int g = 0; g < G; ++g) host[(size_t)g * R + r] = tmp[(size_t)r * G + g];
+  return FBS_OK;
+}
+
+int from_host_gene_major(fbs_handle* h, double* dev, int R, const double* host) {
+  const int G = h->mc.G;
+  std::vector<double> tmp((size_t)R * G);
+  for (int r = 0; r < R; ++r)
+    for (int g = 0; g < G; ++g) tmp[(size_t)r * G + g] = host[(size_t)g * R + r];
+  FBS_CUDA(cudaMemcpyAsync(dev, tmp.data(), tmp.size() * 8, cudaMemcpyHostToDevice, h->s));
+  FBS_CUDA(cudaStreamSynchronize(h->s));
+  return FBS_OK;
+}
+
+int read_hyper(fbs_handle* h, Hyper* out) {
+  FBS_CUDA(cudaMemcpyAsync(out, h->p.hyp, sizeof(Hyper), cudaMemcpyDeviceToHost, h->s));
+  FBS_CUDA(cudaStreamSynchronize(h->s));
+  return FBS_OK;
+}
+
+int sweep_direct(fbs_handle* h) {
+  FBS_CUDA(launch_gene(h->mc, h->p, h->block, h->s));
+  FBS_CUDA(launch_hyper(h->mc, h->p, h->nblk, h->s));
+  return FBS_OK;
+}
+
+int ensure_graph(fbs_handle* h) {
+  if (h->seg_exec) return FBS_OK;
+  cudaGraph_t graph;
+  FBS_CUDA(cudaStreamBeginCapture(h->s, cudaStreamCaptureModeThreadLocal));
+  for (int i = 0; i < h->seg; ++i) {
+    if (launch_gene(h->mc, h->p, h->block, h->s) != cudaSuccess ||
+        launch_hyper(h->mc, h->p, h->nblk, h->s) != cudaSuccess) {
+      cudaStreamEndCapture(h->s, &graph);
+      if (graph) cudaGraphDestroy(graph);
+      return fail(FBS_E_CUDA, "kernel launch failed during graph capture");
+    }
+  }
+  FBS_CUDA(cudaStreamEndCapture(h->s, &graph));
+  cudaError_t e = cudaGraphInstantiate(&h->seg_exec, graph, 0);
+  cudaGraphDestroy(graph);
+  FBS_CUDA(e);
+  return FBS_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+void fbs_default_options(fbs_options* o) {
+  if (!o) return;
+  memset(o, 0, sizeof(*o));
+  o->precision = FBS_F64;
+  o->w0 = 1.0;
+  o->step_out_max = 100;
+  o->shrink_max = 100;
+  o->chain = 0;
+  o->moments_eps = 1;
+  o->trace_cap = 0;
+  o->trace_beta = 0;
+  o->block = 0;
+  o->graph_segment = 0;
+}
+
+int fbs_workspace_bytes(int N, int G, int L, const fbs_options* opt, size_t* bytes) {
+  fbs_options d;
+  fbs_default_options(&d);
+  const fbs_options* o = opt ? opt : &d;
+  int rc = check_sizes(N, G, L);
+  if (rc) return rc;
+  rc = check_opts(o);
+  if (rc) return rc;
+  if (!bytes) return fail(FBS_E_ARG, "bytes is NULL");
+  const int block = block_of(o);
+  const int nblk = (G + block - 1) / block;
+  *bytes = make_layout(N, G, L, nblk, o->trace_cap, o->trace_beta).total;
+  return FBS_OK;
+}
+
+int fbs_init(fbs_handle** out, const int32_t* y, int N, int G, int gene_major, const double* X,
+             int L, const double* hoff, const fbs_priors* pri, const fbs_options* opt,
+             uint64_t seed, void* workspace, size_t workspace_bytes, void* stream) {
+  g_err.clear();
+  if (!out) return fail(FBS_E_ARG, "out is NULL");
+  *out = nullptr;
+  fbs_options d;
+  fbs_default_options(&d);
+  const fbs_options* o = opt ? opt : &d;
+  int rc = check_sizes(N, G, L);
+  if (rc) return rc;
+  rc = check_opts(o);
+  if (rc) return rc;
+  if (!y || !X || !hoff || !pri || !pri->c || !pri->s)
+    return fail(FBS_E_ARG, "y, X, h, priors, priors->c and priors->s must be non-NULL");
+  auto pos = [](double v) { return isfinite(v) && v > 0.0; };
+  if (!pos(pri->a) || !pos(pri->b) || !pos(pri->d))
+    return fail(FBS_E_ARG, "prior constants a, b, d must be finite and > 0");
+  for (int l = 0; l < L; ++l)
+    if (!pos(pri->c[l]) || !pos(pri->s[l]))
+      return fail(FBS_E_ARG, "prior constants c_l, s_l must be finite and > 0");
+  for (int i = 0; i < N * L; ++i)
+    if (!isfinite(X[i])) return fail(FBS_E_ARG, "X has a non-finite entry");
+  for (int n = 0; n < N; ++n)
+    if (!isfinite(hoff[n])) return fail(FBS_E_ARG, "h has a non-finite entry");
+  for (size_t i = 0; i < (size_t)N * G; ++i)
+    if (y[i] < 0) return fail(FBS_E_ARG, "y has a negative count");
+
+  fbs_handle* h = new fbs_handle();
+  ModelConst& mc = h->mc;
+  memset(&mc, 0, sizeof(mc));
+  mc.N = N;
+  mc.G = G;
+  mc.L = L;
+  mc.P = 2 * L + 2;
+  mc.K = o->step_out_max;
+  mc.shrink_max = o->shrink_max;
+  mc.moments_eps = o->moments_eps ? 1 : 0;
+  mc.trace_beta = (o->trace_beta && o->trace_cap > 0) ? 1 : 0;
+  mc.seed_lo = (uint32_t)(seed & 0xffffffffu);
+  mc.seed_hi = (uint32_t)(seed >> 32);
+  mc.chain = o->chain;
+  mc.a = pri->a;
+  mc.b = pri->b;
+  mc.d = pri->d;
+  for (int l = 0; l < L; ++l) {
+    mc.c2[l] = pri->c[l] * pri->c[l];
+    mc.s2[l] = pri->s[l] * pri->s[l];
+  }
+  bool integral = true;
+  for (int n = 0; n < N; ++n) {
+    mc.h[n] = hoff[n];
+    for (int l = 0; l < L; ++l) {
+      mc.X[n * kMaxL + l] = X[n * L + l];
+      if (X[n * L + l] != floor(X[n * L + l])) integral = false;
+    }
+  }
+  h->x_integral = integral;
+  for (int l = 0; l < L; ++l) {
+    int nc = 0;
+    for (int n = 0; n < N; ++n) {
+      const double v = X[n * L + l];
+      if (v == 0.0) {
+        mc.cls[l][n] = -1;
+        continue;
+      }
+      int j = 0;
+      while (j < nc && mc.cval[l][j] != v) ++j;
+      if (j == nc) {
+        if (nc == kMaxCls) {
+          delete h;
+          return fail(FBS_E_ARG, "a column of X has more than FBS_MAX_CLASSES distinct values");
+        }
+        mc.cval[l][nc] = v;
+        mc.ckind[l][nc] = v == 1.0 ? kClsPlus : (v == -1.0 ? kClsMinus : kClsOther);
+        ++nc;
+      }
+      mc.cls[l][n] = (int8_t)j;
+    }
+    mc.ncls[l] = nc;
+  }
+  double pinv[kMaxL * kMaxN];
+  if (!pseudo_inverse(X, N, L, pinv)) {
+    delete h;
+    return fail(FBS_E_ARG, "X^T X is singular");
+  }
+
+  h->opt = *o;
+  h->block = block_of(o);
+  h->nblk = (G + h->block - 1) / h->block;
+  h->seg = o->graph_segment > 0 ? o->graph_segment : 100;
+  h->trace_cap = o->trace_cap;
+  h->lay = make_layout(N, G, L, h->nblk, o->trace_cap, mc.trace_beta);
+  h->user = (cudaStream_t)stream;
+
+  auto bail = [&](int code, const std::string& msg) {
+    if (h->s) cudaStreamDestroy(h->s);
+    if (h->ev_in) cudaEventDestroy(h->ev_in);
+    if (h->ev_out) cudaEventDestroy(h->ev_out);
+    if (h->own_ws && h->ws) cudaFree(h->ws);
+    delete h;
+    return fail(code, msg);
+  };
+  cudaError_t e;
+  if ((e = cudaStreamCreateWithFlags(&h->s, cudaStreamNonBlocking)) != cudaSuccess ||
+      (e = cudaEventCreateWithFlags(&h->ev_in, cudaEventDisableTiming)) != cudaSuccess ||
+      (e = cudaEventCreateWithFlags(&h->ev_out, cudaEventDisableTiming)) != cudaSuccess)
+    return bail(FBS_E_CUDA, std::string("stream/event creation: ") + cudaGetErrorString(e));
+  if (workspace) {
+    if (workspace_bytes < h->lay.total) return bail(FBS_E_ARG, "workspace is too small");
+    h->ws = workspace;
+  } else {
+    e = cudaMalloc(&h->ws, h->lay.total);
+    if (e != cudaSuccess) return bail(FBS_E_OOM, std::string("cudaMalloc: ") + cudaGetErrorString(e));
+    h->own_ws = true;
+  }
+  char* base = (char*)(((uintptr_t)h->ws + 255) & ~(uintptr_t)255);
+  h->p = carve(base, h->lay, mc.trace_beta);
+  if ((e = prepare_gene_kernel(N, h->block)) != cudaSuccess)
+    return bail(FBS_E_CUDA, std::string("kernel attribute: ") + cudaGetErrorString(e));
+
+  // raw counts go to the eps-moment plane (free until the moments are zeroed)
+  int32_t* y_raw = (int32_t*)h->p.q_eps;
+  double* d_pinv = (double*)(base + h->lay.pinv);
+  if (enter(h) != FBS_OK) return bail(FBS_E_CUDA, g_err);
+  if ((e = cudaMemcpyAsync(y_raw, y, (size_t)N * G * sizeof(int32_t), cudaMemcpyHostToDevice,
+                           h->s)) != cudaSuccess ||
+      (e = cudaMemcpyAsync(d_pinv, pinv, sizeof(pinv), cudaMemcpyHostToDevice, h->s)) !=
+          cudaSuccess ||
+      (e = cudaMemsetAsync(h->p.counters, 0, FBS_NUM_COUNTERS * sizeof(unsigned long long),
+                           h->s)) != cudaSuccess ||
+      (e = cudaMemsetAsync(h->p.hyp, 0, sizeof(Hyper), h->s)) != cudaSuccess ||
+      (e = launch_init(mc, h->p, y_raw, gene_major, d_pinv, o->w0, 1, o->trace_cap, h->s)) !=
+          cudaSuccess ||
+      (e = cudaStreamSynchronize(h->s)) != cudaSuccess)
+    return bail(FBS_E_CUDA, std::string("initialisation: ") + cudaGetErrorString(e));
+  if (leave(h) != FBS_OK) return bail(FBS_E_CUDA, g_err);
+  *out = h;
+  return FBS_OK;
+}
+
+int fbs_run(fbs_handle* h, int64_t n_iter, int64_t burnin, int64_t thin) {
+  if (!h) return fail(FBS_E_ARG, "handle is NULL");
+  if (n_iter < 0 || burnin < 0 || thin < 1)
+    return fail(FBS_E_ARG, "need n_iter >= 0, burnin >= 0, thin >= 1");
+  if (n_iter == 0) return FBS_OK;
+  int rc = enter(h);
+  if (rc) return rc;
+  FBS_CUDA(launch_set_run(h->p.hyp, burnin, burnin / 2, thin, h->s));
+  int64_t left = n_iter;
+  if (left >= h->seg) {
+    rc = ensure_graph(h);
+    if (rc) return rc;
+    while (left >= h->seg) {
+      FBS_CUDA(cudaGraphLaunch(h->seg_exec, h->s));
+      left -= h->seg;
+    }
+  }
+  for (; left > 0; --left) {
+    rc = sweep_direct(h);
+    if (rc) return rc;
+  }
+  return leave(h);
+}
+
+int fbs_sync(fbs_handle* h) {
+  if (!h) return fail(FBS_E_ARG, "handle is NULL");
+  FBS_CUDA(cudaStreamSynchronize(h->s));
+  FBS_CUDA(cudaGetLastError());
+  Hyper hy;
+  int rc = read_hyper(h, &hy);
+  if (rc) return rc;
+  if (hy.flags & kFlagNonfinite)
+    return fail(FBS_E_NONFINITE, "a slice update started from a non-finite log density");
+  return FBS_OK;
+}
+
+int fbs_moments(fbs_handle* h, double* mean_eps, double* msq_eps, double* mean_beta,
+                double* msq_beta, double* mean_gam, double* msq_gam, double* mean_phi,
+                double* msq_phi, int64_t* count) {
+  if (!h) return fail(FBS_E_ARG, "handle is NULL");
+  int rc = enter(h);
+  if (rc) return rc;
+  const int N = h->mc.N, L = h->mc.L, G = h->mc.G, P = h->mc.P;
+  if (mean_eps && (rc = to_host_gene_major(h, h->p.m_eps, N, mean_eps))) return rc;
+  if (msq_eps && (rc = to_host_gene_major(h, h->p.q_eps, N, msq_eps))) return rc;
+  if (mean_beta && (rc = to_host_gene_major(h, h->p.m_beta, L, mean_beta))) return rc;
+  if (msq_beta && (rc = to_host_gene_major(h, h->p.q_beta, L, msq_beta))) return rc;
+  if (mean_gam) FBS_CUDA(cudaMemcpyAsync(mean_gam, h->p.m_gam, (size_t)G * 8, cudaMemcpyDeviceToHost, h->s));
+  if (msq_gam) FBS_CUDA(cudaMemcpyAsync(msq_gam, h->p.q_gam, (size_t)G * 8, cudaMemcpyDeviceToHost, h->s));
+  Hyper hy;
+  if ((rc = read_hyper(h, &hy))) return rc;
+  if (mean_phi) memcpy(mean_phi, hy.m_phi, (size_t)P * 8);
+  if (msq_phi) memcpy(msq_phi, hy.q_phi, (size_t)P * 8);
+  if (count) *count = hy.n_mom;
+  return leave(h);
+}
+
+int fbs_get_state(fbs_handle* h, double* eps, double* beta, double* gam, double* phi,
+                  double* w_eps, double* waux_eps, double* w_beta, double* waux_beta,
+                  double* w_nu, double* waux_nu, int64_t* it) {
+  if (!h) return fail(FBS_E_ARG, "handle is NULL");
+  int rc = enter(h);
+  if (rc) return rc;
+  const int N = h->mc.N, L = h->mc.L, G = h->mc.G, P = h->mc.P;
+  if (eps && (rc = to_host_gene_major(h, h->p.eps, N, eps))) return rc;
+  if (w_eps && (rc = to_host_gene_major(h, h->p.w_eps, N, w_eps))) return rc;
+  if (waux_eps && (rc = to_host_gene_major(h, h->p.waux_eps, N, waux_eps))) return rc;
+  if (beta && (rc = to_host_gene_major(h, h->p.beta, L, beta))) return rc;
+  if (w_beta && (rc = to_host_gene_major(h, h->p.w_beta, L, w_beta))) return rc;
+  if (waux_beta && (rc = to_host_gene_major(h, h->p.waux_beta, L, waux_beta))) return rc;
+  if (gam) FBS_CUDA(cudaMemcpyAsync(gam, h->p.gam, (size_t)G * 8, cudaMemcpyDeviceToHost, h->s));
+  Hyper hy;
+  if ((rc = read_hyper(h, &hy))) return rc;
+  if (phi) memcpy(phi, hy.phi, (size_t)P * 8);
+  if (w_nu) *w_nu = hy.w_nu;
+  if (waux_nu) *waux_nu = hy.waux_nu;
+  if (it) *it = hy.it;
+  return leave(h);
+}
+
+int fbs_set_state(fbs_handle* h, const double* eps, const double* beta, const double* gam,
+                  const double* phi, const double* w_eps, const double* waux_eps,
+                  const double* w_beta, const double* waux_beta, const double* w_nu,
+                  const double* waux_nu, int64_t it) {
+  if (!h) return fail(FBS_E_ARG, "handle is NULL");
+  if (it < 0) return fail(FBS_E_ARG, "it must be >= 0");
+  int rc = enter(h);
+  if (rc) return rc;
+  const int N = h->mc.N, L = h->mc.L, G = h->mc.G, P = h->mc.P;
+  if (eps && (rc = from_host_gene_major(h, h->p.eps, N, eps))) return rc;
+  if (w_eps && (rc = from_host_gene_major(h, h->p.w_eps, N, w_eps))) return rc;
+  if (waux_eps && (rc = from_host_gene_major(h, h->p.waux_eps, N, waux_eps))) return rc;
+  if (beta && (rc = from_host_gene_major(h, h->p.beta, L, beta))) return rc;
+  if (w_beta && (rc = from_host_gene_major(h, h->p.w_beta, L, w_beta))) return rc;
+  if (waux_beta && (rc = from_host_gene_major(h, h->p.waux_beta, L, waux_beta))) return rc;
+  if (gam) {
+    FBS_CUDA(cudaMemcpyAsync(h->p.gam, gam, (size_t)G * 8, cudaMemcpyHostToDevice, h->s));
+    FBS_CUDA(cudaStreamSynchronize(h->s));
+  }
+  FBS_CUDA(launch_zero_moments(h->mc, h->p, h->s));
+  Hyper hy;
+  if ((rc = read_hyper(h, &hy))) return rc;
+  if (phi) memcpy(hy.phi, phi, (size_t)P * 8);
+  if (w_nu) hy.w_nu = *w_nu;
+  if (waux_nu) hy.waux_nu = *waux_nu;
+  hy.it = it;
+  FBS_CUDA(cudaMemcpyAsync(h->p.hyp, &hy, sizeof(Hyper), cudaMemcpyHostToDevice, h->s));
+  FBS_CUDA(cudaStreamSynchronize(h->s));
+  return leave(h);
+}
+
+int fbs_trace(fbs_handle* h, int64_t max_rows, double* phi, double* beta, int64_t* rows) {
+  if (!h) return fail(FBS_E_ARG, "handle is NULL");
+  if (max_rows < 0) return fail(FBS_E_ARG, "max_rows must be >= 0");
+  int rc = enter(h);
+  if (rc) return rc;
+  Hyper hy;
+  if ((rc = read_hyper(h, &hy))) return rc;
+  const long long n = hy.trace_rows < max_rows ? hy.trace_rows : max_rows;
+  const int P = h->mc.P, L = h->mc.L, G = h->mc.G;
+  if (phi && n > 0)
+    FBS_CUDA(cudaMemcpyAsync(phi, h->p.trace_phi, (size_t)n * P * 8, cudaMemcpyDeviceToHost, h->s));
+  if (beta && n > 0) {
+    if (!h->p.trace_beta) return fail(FBS_E_ARG, "this handle keeps no beta trace");
+    std::vector<double> tmp((size_t)L * G);
+    for (long long r = 0; r < n; ++r) {
+      FBS_CUDA(cudaMemcpyAsync(tmp.data(), h->p.trace_beta + (size_t)r * L * G, tmp.size() * 8,
+                               cudaMemcpyDeviceToHost, h->s));
+      FBS_CUDA(cudaStreamSynchronize(h->s));
+      double* dst = beta + (size_t)r * G * L;
+      for (int l = 0; l < L; ++l)
+        for (int g = 0; g < G; ++g) dst[(size_t)g * L + l] = tmp[(size_t)l * G + g];
+    }
+  }
+  FBS_CUDA(cudaStreamSynchronize(h->s));
+  if (rows) *rows = n;
+  return leave(h);
+}
+
+int fbs_beta_ess(fbs_handle* h, double* ess) {
+  if (!h || !ess) return fail(FBS_E_ARG, "handle or ess is NULL");
+  if (!h->p.trace_beta) return fail(FBS_E_ARG, "this handle keeps no beta trace");
+  int rc = enter(h);
+  if (rc) return rc;
+  Hyper hy;
+  if ((rc = read_hyper(h, &hy))) return rc;
+  if (hy.trace_rows < 4) return fail(FBS_E_ARG, "the beta trace holds fewer than 4 rows");
+  const int L = h->mc.L, G = h->mc.G;
+  const long long S = (long long)L * G;
+  double* d_ess = nullptr;
+  FBS_CUDA(cudaMallocAsync((void**)&d_ess, (size_t)S * 8, h->s));
+  cudaError_t e = launch_ess(h->p.trace_beta, hy.trace_rows, S, d_ess, h->s);
+  std::vector<double> tmp((size_t)S);
+  if (e == cudaSuccess)
+    e = cudaMemcpyAsync(tmp.data(), d_ess, (size_t)S * 8, cudaMemcpyDeviceToHost, h->s);
+  cudaFreeAsync(d_ess, h->s);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(h->s);
+  FBS_CUDA(e);
+  for (int l = 0; l < L; ++l)
+    for (int g = 0; g < G; ++g) ess[(size_t)g * L + l] = tmp[(size_t)l * G + g];
+  return leave(h);
+}
+
+int fbs_count_sums(fbs_handle* h, int64_t* T) {
+  if (!h || !T) return fail(FBS_E_ARG, "handle or T is NULL");
+  if (!h->x_integral) return fail(FBS_E_ARG, "X is not integer-valued");
+  int rc = enter(h);
+  if (rc) return rc;
+  const int L = h->mc.L, G = h->mc.G;
+  std::vector<double> tmp((size_t)L * G);
+  FBS_CUDA(cudaMemcpyAsync(tmp.data(), h->p.T, tmp.size() * 8, cudaMemcpyDeviceToHost, h->s));
+  FBS_CUDA(cudaStreamSynchronize(h->s));
+  for (int l = 0; l < L; ++l)
+    for (int g = 0; g < G; ++g) T[(size_t)g * L + l] = (int64_t)tmp[(size_t)l * G + g];
+  return leave(h);
+}
+
+int fbs_counters(fbs_handle* h, int64_t* out) {
+  if (!h || !out) return fail(FBS_E_ARG, "handle or out is NULL");
+  int rc = enter(h);
+  if (rc) return rc;
+  unsigned long long c[FBS_NUM_COUNTERS];
+  FBS_CUDA(cudaMemcpyAsync(c, h->p.counters, sizeof(c), cudaMemcpyDeviceToHost, h->s));
+  FBS_CUDA(cudaStreamSynchronize(h->s));
+  for (int i = 0; i < FBS_NUM_COUNTERS; ++i) out[i] = (int64_t)c[i];
+  return leave(h);
+}
+
+int fbs_profile(fbs_handle* h, int64_t n_iter, int64_t burnin, int64_t thin, double* ms_gene,
+                double* ms_hyper) {
+  if (!h) return fail(FBS_E_ARG, "handle is NULL");
+  if (n_iter < 1 || burnin < 0 || thin < 1)
+    return fail(FBS_E_ARG, "need n_iter >= 1, burnin >= 0, thin >= 1");
+  int rc = enter(h);
+  if (rc) return rc;
+  FBS_CUDA(launch_set_run(h->p.hyp, burnin, burnin / 2, thin, h->s));
+  std::vector<cudaEvent_t> ev((size_t)3 * n_iter);
+  for (auto& x : ev) FBS_CUDA(cudaEventCreate(&x));
+  cudaError_t e = cudaSuccess;
+  for (int64_t i = 0; i < n_iter && e == cudaSuccess; ++i) {
+    cudaEventRecord(ev[3 * i], h->s);
+    e = launch_gene(h->mc, h->p, h->block, h->s);
+    cudaEventRecord(ev[3 * i + 1], h->s);
+    if (e == cudaSuccess) e = launch_hyper(h->mc, h->p, h->nblk, h->s);
+    cudaEventRecord(ev[3 * i + 2], h->s);
+  }
+  if (e == cudaSuccess) e = cudaStreamSynchronize(h->s);
+  double tg = 0.0, th = 0.0;
+  for (int64_t i = 0; i < n_iter && e == cudaSuccess; ++i) {
+    float a = 0.f, b = 0.f;
+    cudaEventElapsedTime(&a, ev[3 * i], ev[3 * i + 1]);
+    cudaEventElapsedTime(&b, ev[3 * i + 1], ev[3 * i + 2]);
+    tg += a;
+    th += b;
+  }
+  for (auto& x : ev) cudaEventDestroy(x);
+  FBS_CUDA(e);
+  if (ms_gene) *ms_gene = tg / (double)n_iter;
+  if (ms_hyper) *ms_hyper = th / (double)n_iter;
+  return leave(h);
+}
+
+int fbs_uniforms(uint64_t seed, uint32_t chain, uint32_t stream, uint32_t index0, int n_index,
+                 uint32_t iter, uint32_t k0, int n_k, double* out) {
+  if (n_index < 0 || n_k < 0 || !out) return fail(FBS_E_ARG, "bad sizes or NULL out");
+  if (n_index == 0 || n_k == 0) return FBS_OK;
+  double* d = nullptr;
+  const size_t bytes = (size_t)n_index * n_k * 8;
+  FBS_CUDA(cudaMalloc((void**)&d, bytes));
+  cudaError_t e = launch_uniforms(seed, chain, stream, index0, n_index, iter, k0, n_k, d, 0);
+  if (e == cudaSuccess) e = cudaMemcpy(out, d, bytes, cudaMemcpyDeviceToHost);
+  cudaFree(d);
+  FBS_CUDA(e);
+  return FBS_OK;
+}
+
+void fbs_free(fbs_handle* h) {
+  if (!h) return;
+  if (h->s) cudaStreamSynchronize(h->s);
+  if (h->seg_exec) cudaGraphExecDestroy(h->seg_exec);
+  if (h->own_ws && h->ws) cudaFree(h->ws);
+  if (h->ev_in) cudaEventDestroy(h->ev_in);
+  if (h->ev_out) cudaEventDestroy(h->ev_out);
+  if (h->s) cudaStreamDestroy(h->s);
+  delete h;
+}
+
+const char* fbs_last_error_string(void) { return g_err.c_str(); }
+
+}  // extern "C"

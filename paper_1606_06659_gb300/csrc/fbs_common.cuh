@@ -1,0 +1,94 @@
+// fbs_common.cuh -- device-side data layout shared by the kernels and the host
+// code of the GB300 Gibbs sampler (Landau & Niemi, arXiv 1606.06659).
+//
+// HBM layout: every per-gene array is stored sample- or column-major with the
+// gene index fastest ([N][G], [L][G], [G]), so a warp of 32 consecutive genes
+// reads 32 consecutive words of each plane.
+#pragma once
+
+#include <stdint.h>
+
+#include "fbs.h"
+
+namespace fbs {
+
+constexpr int kMaxN = FBS_MAX_N;
+constexpr int kMaxL = FBS_MAX_L;
+constexpr int kMaxP = 2 * FBS_MAX_L + 2;     // nu, tau, theta[L], sigma2[L]
+constexpr int kMaxCls = FBS_MAX_CLASSES;
+constexpr int kNumPart = 2 + 2 * FBS_MAX_L;  // S1, S2, B1'[L], B2'[L]
+
+// RNG stream identifiers: one per kind of random variable.
+enum : uint32_t {
+  kStreamEps = 1,
+  kStreamGamma = 2,
+  kStreamNu = 3,
+  kStreamTau = 4,
+  kStreamBeta = 5,
+  kStreamTheta = 6,
+  kStreamSigma = 7,
+};
+
+// Class of a non-zero value of one column of X: +1, -1 or any other value.
+enum : int8_t { kClsPlus = 1, kClsMinus = 2, kClsOther = 0 };
+
+// Model constants, passed to every kernel by value (kernel-parameter space).
+struct ModelConst {
+  int N, G, L, P;
+  int K, shrink_max;
+  int moments_eps, trace_beta;
+  uint32_t seed_lo, seed_hi, chain, pad0;
+  double a, b, d;
+  double c2[kMaxL];               // c_l^2
+  double s2[kMaxL];               // s_l^2
+  double h[kMaxN];
+  double X[kMaxN * kMaxL];        // [N][L]
+  // Column classes for the beta_gl conditional: the non-zero values of column
+  // l are grouped; cls[l][n] = class of X_nl (-1 when X_nl == 0).
+  int ncls[kMaxL];
+  double cval[kMaxL][kMaxCls];
+  int8_t ckind[kMaxL][kMaxCls];
+  int8_t cls[kMaxL][kMaxN];
+};
+
+// Hyperparameters, run parameters and chain bookkeeping, in device memory.
+struct Hyper {
+  double phi[kMaxP];
+  double m_phi[kMaxP], q_phi[kMaxP];   // running mean / mean square
+  double w_nu, waux_nu;
+  long long it;          // iterations completed
+  long long n_mom;       // draws folded into the running moments
+  long long trace_rows;  // rows written to the trace
+  long long burnin, tune_start, thin, trace_cap;
+  unsigned int flags;
+  unsigned int pad;
+};
+
+// Device pointers of one chain.
+struct DevPtrs {
+  const int32_t* y;   // [N][G]
+  const double* T;    // [L][G] sum_n y_gn X_nl
+  double* eps;        // [N][G]
+  double* w_eps;      // [N][G]
+  double* waux_eps;   // [N][G]
+  double* beta;       // [L][G]
+  double* w_beta;     // [L][G]
+  double* waux_beta;  // [L][G]
+  double* gam;        // [G]
+  double* m_eps;      // [N][G] running mean
+  double* q_eps;      // [N][G] running mean square
+  double* m_beta;     // [L][G]
+  double* q_beta;     // [L][G]
+  double* m_gam;      // [G]
+  double* q_gam;      // [G]
+  double* partial;    // [n_blocks][kNumPart]
+  Hyper* hyp;
+  double* trace_phi;  // [trace_cap][P]
+  double* trace_beta; // [trace_cap][L][G] or null
+  unsigned long long* counters;  // [FBS_NUM_COUNTERS]
+};
+
+// Flag bits in Hyper::flags.
+enum : unsigned int { kFlagNonfinite = 1u };
+
+}  // namespace fbs

@@ -1,0 +1,671 @@
+// fbs_kernels.cu -- CUDA kernels of one Gibbs sweep (Algorithm 1 of Landau &
+// Niemi, arXiv 1606.06659) for sm_103a, plus initialisation, trace and ESS
+// kernels.
+//
+// A sweep is two launches:
+//   gene kernel   one thread per gene g: slice updates of eps_g1..eps_gN
+//                 (Algorithm 1 step 1), the conjugate gamma_g draw (step 2), slice
+//                 updates of beta_g1..beta_gL in order (step 5), width tuning
+//                 (Algorithm 2 step 7), Welford moments (Section 3.1) and the
+//                 per-block FP64 partial sums that feed steps 3, 4, 6, 7;
+//   hyper kernel  one block: fixed-order reduction of the partials, then nu (slice,
+//                 step 3) and tau (step 4) on lane 0 while lanes 1..L draw
+//                 theta_l (step 6) and sigma_l^2 (step 7).
+// Drawing beta before nu and tau is exact: the beta_gl conditional involves
+// neither, and theirs involve no beta (Figure 3); the counter-based generator
+// gives every variable the same uniforms in either order.
+#include <cuda_runtime.h>
+#include <math.h>
+#include <stdint.h>
+
+#include "fbs_common.cuh"
+#include "fbs_kernels.h"
+#include "fbs_rng.cuh"
+
+namespace fbs {
+
+// ---------------------------------------------------------------- densities
+
+// log f(eps_gn = x | ...) = y x - exp(A + x) - x^2 hg, with A = h_n + X_n beta_g and
+// hg = 1/(2 gamma_g).  aux = exp(A + x), the Poisson mean at x.
+struct EpsDensity {
+  double y, A, hg;
+  __device__ __forceinline__ double operator()(double x, double* aux) const {
+    const double e = exp(A + x);
+    *aux = e;
+    return y * x - e - x * x * hg;
+  }
+};
+
+// log f(beta_gl = b | ...) = b T_gl - sum_j Q_j exp(v_j (b - b0)) - (b - theta_l)^2 hs,
+// where Q_j sums exp(h_n + eps_gn + X_n beta_g) (current beta, beta_gl = b0) over
+// the samples n whose X_nl equals the j-th distinct non-zero value v_j of
+// column l.  Samples with X_nl = 0 only add a constant.  hs = 1/(2 sigma_l^2).
+struct BetaDensity {
+  double T, b0, theta, hs;
+  int ncls;
+  double Q[kMaxCls];
+  double v[kMaxCls];
+  int8_t kind[kMaxCls];
+  __device__ __forceinline__ double operator()(double b, double* aux) const {
+    const double dlt = b - b0;
+    const double z = exp(dlt);
+    double s = 0.0;
+#pragma unroll
+    for (int j = 0; j < kMaxCls; ++j) {
+      if (j < ncls) {
+        double e;
+        if (kind[j] == kClsPlus) e = z;
+        else if (kind[j] == kClsMinus) e = 1.0 / z;
+        else e = exp(v[j] * dlt);
+        s += Q[j] * e;
+      }
+    }
+    *aux = z;
+    const double dv = b - theta;
+    return b * T - s - dv * dv * hs;
+  }
+};
+
+// ---------------------------------------------------------------- block reduction
+
+template <int NV>
+__device__ __forceinline__ void block_sum_to(double (&v)[NV], double* out, double* smem) {
+  // warp-shuffle tree, then one value per warp through shared memory
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarp = (blockDim.x + 31) >> 5;
+#pragma unroll
+  for (int i = 0; i < NV; ++i) {
+    double x = v[i];
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) x += __shfl_down_sync(0xffffffffu, x, o);
+    if (lane == 0) smem[warp * NV + i] = x;
+  }
+  __syncthreads();
+  if (threadIdx.x < NV) {
+    double s = 0.0;
+    for (int w = 0; w < nwarp; ++w) s += smem[w * NV + threadIdx.x];
+    out[threadIdx.x] = s;
+  }
+}
+
+// ---------------------------------------------------------------- gene kernel (FP64)
+
+__global__ void __launch_bounds__(128) k_gene_f64(ModelConst mc, DevPtrs p) {
+  extern __shared__ double smem_dyn[];  // mu[n][blockDim] then reduction scratch
+  const int G = mc.G, N = mc.N, L = mc.L;
+  const Hyper* hy = p.hyp;
+  const long long it = hy->it + 1;
+  const uint32_t it32 = (uint32_t)it;
+  const long long burnin = hy->burnin, tune_start = hy->tune_start;
+  const bool mom = it > burnin;
+  const double inv_k = mom ? 1.0 / (double)(hy->n_mom + 1) : 0.0;
+  const double nu = hy->phi[0], tau = hy->phi[1];
+  const bool trace_now = mom && mc.trace_beta && p.trace_beta != nullptr &&
+                         ((it - burnin) % hy->thin == 0) && hy->trace_rows < hy->trace_cap;
+  const long long trace_row = hy->trace_rows;
+
+  double* mu = smem_dyn;  // mu[n * blockDim + tid]
+  const int tid = threadIdx.x;
+  const int g = blockIdx.x * blockDim.x + tid;
+  const bool active = g < G;
+
+  double part[kNumPart];
+#pragma unroll
+  for (int i = 0; i < kNumPart; ++i) part[i] = 0.0;
+  unsigned evals_e = 0, evals_b = 0, caps = 0, gcaps = 0, nonfin = 0;
+
+  if (active) {
+    double beta[kMaxL];
+#pragma unroll
+    for (int l = 0; l < kMaxL; ++l) beta[l] = l < L ? p.beta[(size_t)l * G + g] : 0.0;
+    double gam = p.gam[g];
+    const double hg = 0.5 / gam;
+
+    // ---- step 1: eps_gn, n = 1..N
+    double ss = 0.0;
+    for (int n = 0; n < N; ++n) {
+      const size_t e = (size_t)n * G + g;
+      double A = mc.h[n];
+#pragma unroll
+      for (int l = 0; l < kMaxL; ++l)
+        if (l < L) A += mc.X[n * kMaxL + l] * beta[l];
+      EpsDensity f{(double)p.y[e], A, hg};
+      Rng r(mc.seed_lo, mc.seed_hi, mc.chain, kStreamEps, (uint32_t)((size_t)g * N + n), it32);
+      const double x0 = p.eps[e];
+      double w = p.w_eps[e], waux = p.waux_eps[e];
+      SliceResult s = slice_update(x0, w, f, r, mc.K, mc.shrink_max);
+      evals_e += s.evals;
+      caps += s.capped;
+      nonfin += s.nonfinite;
+      mu[n * blockDim.x + tid] = s.aux;
+      p.eps[e] = s.x;
+      if (it <= burnin) {
+        tune_width(w, waux, it, s.x, x0, burnin, tune_start);
+        p.w_eps[e] = w;
+        p.waux_eps[e] = waux;
+      }
+      ss += s.x * s.x;
+      if (mom && mc.moments_eps) {
+        const double m = p.m_eps[e], q = p.q_eps[e];
+        p.m_eps[e] = m + (s.x - m) * inv_k;
+        p.q_eps[e] = q + (s.x * s.x - q) * inv_k;
+      }
+    }
+
+    // ---- step 2: gamma_g ~ IG((N + nu)/2, (sum eps^2 + nu tau)/2)
+    {
+      Rng r(mc.seed_lo, mc.seed_hi, mc.chain, kStreamGamma, (uint32_t)g, it32);
+      bool gcap = false;
+      const double shape = 0.5 * ((double)N + nu);
+      const double scale = 0.5 * (ss + nu * tau);
+      gam = scale / gamma_mt(shape, r, 0, &gcap);
+      gcaps += gcap;
+      p.gam[g] = gam;
+      if (mom) {
+        const double m = p.m_gam[g], q = p.q_gam[g];
+        p.m_gam[g] = m + (gam - m) * inv_k;
+        p.q_gam[g] = q + (gam * gam - q) * inv_k;
+      }
+      part[0] = log(gam);
+      part[1] = 1.0 / gam;
+    }
+
+    // ---- step 5: beta_gl, l = 1..L in order
+    for (int l = 0; l < L; ++l) {
+      const size_t e = (size_t)l * G + g;
+      const double theta = hy->phi[2 + l];
+      const double sig2 = hy->phi[2 + L + l];
+      BetaDensity f;
+      f.T = p.T[e];
+      f.b0 = beta[l];
+      f.theta = theta;
+      f.hs = 0.5 / sig2;
+      f.ncls = mc.ncls[l];
+#pragma unroll
+      for (int j = 0; j < kMaxCls; ++j) {
+        f.Q[j] = 0.0;
+        f.v[j] = mc.cval[l][j];
+        f.kind[j] = mc.ckind[l][j];
+      }
+      for (int n = 0; n < N; ++n) {
+        const int c = mc.cls[l][n];
+        const double m = mu[n * blockDim.x + tid];
+#pragma unroll
+        for (int j = 0; j < kMaxCls; ++j)
+          if (j == c) f.Q[j] += m;
+      }
+      Rng r(mc.seed_lo, mc.seed_hi, mc.chain, kStreamBeta, (uint32_t)((size_t)g * L + l), it32);
+      const double x0 = beta[l];
+      double w = p.w_beta[e], waux = p.waux_beta[e];
+      SliceResult s = slice_update(x0, w, f, r, mc.K, mc.shrink_max);
+      evals_b += s.evals;
+      caps += s.capped;
+      nonfin += s.nonfinite;
+      // carry exp(h_n + eps_gn + X_n beta_g) to the new beta_gl
+      if (s.x != x0) {
+        const double dlt = s.x - x0;
+        double ej[kMaxCls];
+        const double z = exp(dlt);
+#pragma unroll
+        for (int j = 0; j < kMaxCls; ++j) {
+          ej[j] = 1.0;
+          if (j < f.ncls) {
+            if (f.kind[j] == kClsPlus) ej[j] = z;
+            else if (f.kind[j] == kClsMinus) ej[j] = 1.0 / z;
+            else ej[j] = exp(f.v[j] * dlt);
+          }
+        }
+        for (int n = 0; n < N; ++n) {
+          const int c = mc.cls[l][n];
+          double fac = 1.0;
+#pragma unroll
+          for (int j = 0; j < kMaxCls; ++j)
+            if (j == c) fac = ej[j];
+          mu[n * blockDim.x + tid] *= fac;
+        }
+      }
+      beta[l] = s.x;
+      p.beta[e] = s.x;
+      if (it <= burnin) {
+        tune_width(w, waux, it, s.x, x0, burnin, tune_start);
+        p.w_beta[e] = w;
+        p.waux_beta[e] = waux;
+      }
+      if (mom) {
+        const double m = p.m_beta[e], q = p.q_beta[e];
+        p.m_beta[e] = m + (s.x - m) * inv_k;
+        p.q_beta[e] = q + (s.x * s.x - q) * inv_k;
+      }
+      if (trace_now) p.trace_beta[(size_t)trace_row * L * G + e] = s.x;
+      const double dv = s.x - theta;  // shifted by the current theta_l
+      part[2 + l] = dv;
+      part[2 + kMaxL + l] = dv * dv;
+    }
+  }
+
+  // ---- per-block partial sums for steps 3, 4, 6, 7
+  double* red = smem_dyn + (size_t)N * blockDim.x;
+  block_sum_to<kNumPart>(part, p.partial + (size_t)blockIdx.x * kNumPart, red);
+
+  // ---- counters
+  unsigned long long c4[4] = {evals_e, evals_b, caps, gcaps};
+#pragma unroll
+  for (int i = 0; i < 4; ++i) {
+    unsigned long long x = c4[i];
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) x += __shfl_down_sync(0xffffffffu, x, o);
+    c4[i] = x;
+  }
+  unsigned nf = nonfin;
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) nf += __shfl_down_sync(0xffffffffu, nf, o);
+  if ((tid & 31) == 0) {
+    if (c4[0]) atomicAdd(&p.counters[FBS_CNT_EVALS_EPS], c4[0]);
+    if (c4[1]) atomicAdd(&p.counters[FBS_CNT_EVALS_BETA], c4[1]);
+    if (c4[2]) atomicAdd(&p.counters[FBS_CNT_SLICE_CAPS], c4[2]);
+    if (c4[3]) atomicAdd(&p.counters[FBS_CNT_GAMMA_CAPS], c4[3]);
+    if (nf) {
+      atomicAdd(&p.counters[FBS_CNT_NONFINITE], (unsigned long long)nf);
+      atomicOr(&p.hyp->flags, kFlagNonfinite);
+    }
+  }
+}
+
+// ---------------------------------------------------------------- hyper kernel
+
+// log f(nu | ...) = -G lgamma(nu/2) + (G nu/2) log(nu tau/2) - (nu/2)(S1 + tau S2) on
+// (0, d), S1 = sum_g log gamma_g, S2 = sum_g 1/gamma_g (Algorithm 1 step 3, the
+// sum read as log gamma_g + tau/gamma_g, which the Inverse-Gamma(nu/2, nu tau/2)
+// prior of the gamma_g gives).
+struct NuDensity {
+  double G, d, tau, S1, S2;
+  __device__ __forceinline__ double operator()(double nu, double* aux) const {
+    *aux = 0.0;
+    if (!(nu > 0.0 && nu < d)) return -INFINITY;
+    return -G * lgamma(0.5 * nu) + 0.5 * G * nu * log(0.5 * nu * tau) -
+           0.5 * nu * (S1 + tau * S2);
+  }
+};
+
+constexpr int kHyperThreads = 64;
+
+__global__ void __launch_bounds__(kHyperThreads) k_hyper(ModelConst mc, DevPtrs p, int nblk) {
+  __shared__ double red[kHyperThreads / 32][kNumPart];
+  __shared__ double tot[kNumPart];
+  __shared__ double phi_new[kMaxP];
+  Hyper* hy = p.hyp;
+  const int L = mc.L, P = mc.P;
+  const double G = (double)mc.G;
+  const long long it = hy->it + 1;
+  const uint32_t it32 = (uint32_t)it;
+  const int tid = threadIdx.x;
+
+  // fixed-order reduction of the per-block partials
+  double acc[kNumPart];
+#pragma unroll
+  for (int i = 0; i < kNumPart; ++i) acc[i] = 0.0;
+  for (int b = tid; b < nblk; b += kHyperThreads) {
+#pragma unroll
+    for (int i = 0; i < kNumPart; ++i) acc[i] += p.partial[(size_t)b * kNumPart + i];
+  }
+#pragma unroll
+  for (int i = 0; i < kNumPart; ++i) {
+    double x = acc[i];
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) x += __shfl_down_sync(0xffffffffu, x, o);
+    if ((tid & 31) == 0) red[tid >> 5][i] = x;
+  }
+  if (tid < kMaxP) phi_new[tid] = tid < P ? hy->phi[tid] : 0.0;
+  __syncthreads();
+  if (tid < kNumPart) {
+    double s = 0.0;
+    for (int w = 0; w < kHyperThreads / 32; ++w) s += red[w][tid];
+    tot[tid] = s;
+  }
+  __syncthreads();
+
+  const double S1 = tot[0], S2 = tot[1];
+  if (tid == 0) {
+    // step 3: nu
+    const double tau_old = hy->phi[1];
+    NuDensity f{G, mc.d, tau_old, S1, S2};
+    Rng r(mc.seed_lo, mc.seed_hi, mc.chain, kStreamNu, 0u, it32);
+    const double x0 = hy->phi[0];
+    SliceResult s = slice_update(x0, hy->w_nu, f, r, mc.K, mc.shrink_max);
+    const double nu = s.x;
+    if (it <= hy->burnin) {
+      double w = hy->w_nu, waux = hy->waux_nu;
+      tune_width(w, waux, it, nu, x0, hy->burnin, hy->tune_start);
+      hy->w_nu = w;
+      hy->waux_nu = waux;
+    }
+    atomicAdd(&p.counters[FBS_CNT_EVALS_NU], (unsigned long long)s.evals);
+    if (s.capped) atomicAdd(&p.counters[FBS_CNT_SLICE_CAPS], 1ull);
+    if (s.nonfinite) {
+      atomicAdd(&p.counters[FBS_CNT_NONFINITE], 1ull);
+      atomicOr(&hy->flags, kFlagNonfinite);
+    }
+    // step 4: tau ~ Gamma(a + G nu/2, rate b + nu S2 / 2)
+    Rng rt(mc.seed_lo, mc.seed_hi, mc.chain, kStreamTau, 0u, it32);
+    bool gcap = false;
+    const double shape = mc.a + 0.5 * G * nu;
+    const double rate = mc.b + 0.5 * nu * S2;
+    const double tau = gamma_mt(shape, rt, 0, &gcap) / rate;
+    if (gcap) atomicAdd(&p.counters[FBS_CNT_GAMMA_CAPS], 1ull);
+    phi_new[0] = nu;
+    phi_new[1] = tau;
+  } else if (tid <= L) {
+    const int l = tid - 1;
+    // step 6: theta_l ~ N(v B1 / sigma^2, v), v = 1/(G/sigma^2 + 1/c^2);
+    // the partials hold B1' = sum (beta - theta_old), B2' = sum (beta - theta_old)^2
+    const double th_old = hy->phi[2 + l];
+    const double sig2 = hy->phi[2 + L + l];
+    const double B1s = tot[2 + l], B2s = tot[2 + kMaxL + l];
+    const double B1 = B1s + G * th_old;
+    const double v = 1.0 / (G / sig2 + 1.0 / mc.c2[l]);
+    const double mean = v * B1 / sig2;
+    Rng r(mc.seed_lo, mc.seed_hi, mc.chain, kStreamTheta, (uint32_t)l, it32);
+    const double th = mean + sqrt(v) * normal_bm(r, 0);
+    // step 7: sigma_l^2 ~ IG((G-1)/2, S/2) on (0, s_l^2), S = sum (beta - theta_new)^2
+    const double dl = th - th_old;
+    const double S = B2s - 2.0 * dl * B1s + G * dl * dl;
+    Rng rs(mc.seed_lo, mc.seed_hi, mc.chain, kStreamSigma, (uint32_t)l, it32);
+    bool gcap = false, tcap = false;
+    const double s2n = trunc_invgamma(0.5 * (G - 1.0), 0.5 * S, mc.s2[l], sig2, rs, &gcap, &tcap);
+    if (gcap) atomicAdd(&p.counters[FBS_CNT_GAMMA_CAPS], 1ull);
+    if (tcap) atomicAdd(&p.counters[FBS_CNT_TRUNC_CAPS], 1ull);
+    phi_new[2 + l] = th;
+    phi_new[2 + L + l] = s2n;
+  }
+  __syncthreads();
+
+  const bool mom = it > hy->burnin;
+  if (tid < P) {
+    const double x = phi_new[tid];
+    hy->phi[tid] = x;
+    if (mom) {
+      const double inv_k = 1.0 / (double)(hy->n_mom + 1);
+      const double m = hy->m_phi[tid], q = hy->q_phi[tid];
+      hy->m_phi[tid] = m + (x - m) * inv_k;
+      hy->q_phi[tid] = q + (x * x - q) * inv_k;
+    }
+    if (mom && ((it - hy->burnin) % hy->thin == 0) && hy->trace_rows < hy->trace_cap &&
+        p.trace_phi != nullptr)
+      p.trace_phi[(size_t)hy->trace_rows * P + tid] = x;
+  }
+  __syncthreads();
+  if (tid == 0) {
+    if (mom && ((it - hy->burnin) % hy->thin == 0) && hy->trace_rows < hy->trace_cap)
+      hy->trace_rows += 1;
+    if (mom) hy->n_mom += 1;
+    hy->it = it;
+    atomicAdd(&p.counters[FBS_CNT_SWEEPS], 1ull);
+  }
+}
+
+// ---------------------------------------------------------------- set-up kernels
+
+__global__ void k_set_run(Hyper* hy, long long burnin, long long tune_start, long long thin) {
+  if (threadIdx.x == 0 && blockIdx.x == 0) {
+    hy->burnin = burnin;
+    hy->tune_start = tune_start;
+    hy->thin = thin;
+  }
+}
+
+__global__ void k_init_run(Hyper* hy, long long trace_cap) {
+  if (threadIdx.x == 0 && blockIdx.x == 0) {
+    hy->burnin = 0;
+    hy->tune_start = 0;
+    hy->thin = 1;
+    hy->trace_cap = trace_cap;
+  }
+}
+
+// y to [N][G]; T[l][g] = sum_n y X_nl; default beta_g = P (log(y+1) - h); eps = 0;
+// gamma = 1; widths w0; tuning sums and moments 0.
+__global__ void k_init_genes(ModelConst mc, DevPtrs p, const int32_t* y_in, int gene_major,
+                             const double* __restrict__ pinv, double w0, int set_state) {
+  const int G = mc.G, N = mc.N, L = mc.L;
+  for (int g = blockIdx.x * blockDim.x + threadIdx.x; g < G; g += gridDim.x * blockDim.x) {
+    double r[kMaxN];
+    double T[kMaxL];
+#pragma unroll
+    for (int l = 0; l < kMaxL; ++l) T[l] = 0.0;
+    for (int n = 0; n < N; ++n) {
+      const int32_t yv = gene_major ? y_in[(size_t)g * N + n] : y_in[(size_t)n * G + g];
+      const_cast<int32_t*>(p.y)[(size_t)n * G + g] = yv;
+      r[n] = log((double)yv + 1.0) - mc.h[n];
+#pragma unroll
+      for (int l = 0; l < kMaxL; ++l)
+        if (l < L) T[l] += (double)yv * mc.X[n * kMaxL + l];
+    }
+    for (int l = 0; l < L; ++l) {
+      const_cast<double*>(p.T)[(size_t)l * G + g] = T[l];
+      if (set_state) {
+        double s = 0.0;
+        for (int n = 0; n < N; ++n) s += pinv[l * kMaxN + n] * r[n];
+        p.beta[(size_t)l * G + g] = s;
+        p.w_beta[(size_t)l * G + g] = w0;
+        p.waux_beta[(size_t)l * G + g] = 0.0;
+      }
+    }
+    if (set_state) {
+      for (int n = 0; n < N; ++n) {
+        p.eps[(size_t)n * G + g] = 0.0;
+        p.w_eps[(size_t)n * G + g] = w0;
+        p.waux_eps[(size_t)n * G + g] = 0.0;
+      }
+      p.gam[g] = 1.0;
+    }
+  }
+}
+
+// Zero the running moments and the chain bookkeeping.
+__global__ void k_zero_moments(ModelConst mc, DevPtrs p) {
+  const int G = mc.G, N = mc.N, L = mc.L;
+  for (int g = blockIdx.x * blockDim.x + threadIdx.x; g < G; g += gridDim.x * blockDim.x) {
+    if (p.m_eps)
+      for (int n = 0; n < N; ++n) {
+        p.m_eps[(size_t)n * G + g] = 0.0;
+        p.q_eps[(size_t)n * G + g] = 0.0;
+      }
+    for (int l = 0; l < L; ++l) {
+      p.m_beta[(size_t)l * G + g] = 0.0;
+      p.q_beta[(size_t)l * G + g] = 0.0;
+    }
+    p.m_gam[g] = 0.0;
+    p.q_gam[g] = 0.0;
+  }
+}
+
+// Default hyperparameters from the starting beta: theta_l the mean, sigma_l^2 the
+// variance clamped to [1e-6, s_l^2/4] (two passes, one block), nu = min(3, d/2),
+// tau = 1.
+__global__ void k_init_hyper(ModelConst mc, DevPtrs p, double w0, int set_state) {
+  __shared__ double red[1024 / 32][kMaxL];
+  __shared__ double mean_s[kMaxL];
+  const int G = mc.G, L = mc.L;
+  Hyper* hy = p.hyp;
+  if (set_state) {
+    for (int pass = 0; pass < 2; ++pass) {
+      double acc[kMaxL];
+#pragma unroll
+      for (int l = 0; l < kMaxL; ++l) acc[l] = 0.0;
+      for (int g = threadIdx.x; g < G; g += blockDim.x) {
+#pragma unroll
+        for (int l = 0; l < kMaxL; ++l) {
+          if (l < L) {
+            const double b = p.beta[(size_t)l * G + g];
+            if (pass == 0) acc[l] += b;
+            else {
+              const double dv = b - mean_s[l];
+              acc[l] += dv * dv;
+            }
+          }
+        }
+      }
+#pragma unroll
+      for (int l = 0; l < kMaxL; ++l) {
+        double x = acc[l];
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) x += __shfl_down_sync(0xffffffffu, x, o);
+        if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5][l] = x;
+      }
+      __syncthreads();
+      if (threadIdx.x < L) {
+        double s = 0.0;
+        for (int w = 0; w < (int)(blockDim.x >> 5); ++w) s += red[w][threadIdx.x];
+        if (pass == 0) mean_s[threadIdx.x] = s / (double)G;
+        else {
+          const double var = s / (double)G;
+          const double upper = 0.25 * mc.s2[threadIdx.x];
+          hy->phi[2 + threadIdx.x] = mean_s[threadIdx.x];
+          hy->phi[2 + L + threadIdx.x] = fmin(fmax(var, 1e-6), upper);
+        }
+      }
+      __syncthreads();
+    }
+  }
+  if (threadIdx.x == 0) {
+    if (set_state) {
+      hy->phi[0] = fmin(3.0, 0.5 * mc.d);
+      hy->phi[1] = 1.0;
+      hy->w_nu = w0;
+      hy->waux_nu = 0.0;
+      hy->it = 0;
+    }
+    for (int i = 0; i < kMaxP; ++i) {
+      hy->m_phi[i] = 0.0;
+      hy->q_phi[i] = 0.0;
+    }
+    hy->n_mom = 0;
+    hy->trace_rows = 0;
+    hy->flags = 0;
+  }
+}
+
+// ---------------------------------------------------------------- uniforms, ESS
+
+__global__ void k_uniforms(uint32_t seed_lo, uint32_t seed_hi, uint32_t chain, uint32_t stream,
+                           uint32_t index0, int n_index, uint32_t iter, uint32_t k0, int n_k,
+                           double* out) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n_index) return;
+  Rng r(seed_lo, seed_hi, chain, stream, index0 + (uint32_t)i, iter);
+  for (int k = 0; k < n_k; ++k) out[(size_t)i * n_k + k] = r.u(k0 + (uint32_t)k);
+}
+
+// Geyer initial-monotone-sequence ESS of every column of a [rows][S] trace:
+// one thread per series, reading row by row (consecutive series are adjacent).
+__global__ void k_ess(const double* __restrict__ tr, long long rows, long long S, double* ess) {
+  const long long s = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (s >= S) return;
+  const long long n = rows;
+  double mean = 0.0;
+  for (long long t = 0; t < n; ++t) mean += tr[t * S + s];
+  mean /= (double)n;
+  double c0 = 0.0;
+  for (long long t = 0; t < n; ++t) {
+    const double dv = tr[t * S + s] - mean;
+    c0 += dv * dv;
+  }
+  c0 /= (double)n;
+  if (!(c0 > 0.0)) {
+    ess[s] = (double)n;
+    return;
+  }
+  double sum = 0.0, prev = INFINITY;
+  for (long long j = 0; 2 * j + 1 < n; ++j) {
+    double pair = 0.0;
+    for (long long k = 2 * j; k <= 2 * j + 1; ++k) {
+      double ck = 0.0;
+      for (long long t = 0; t + k < n; ++t)
+        ck += (tr[t * S + s] - mean) * (tr[(t + k) * S + s] - mean);
+      pair += ck / (double)n / c0;
+    }
+    if (!(pair > 0.0)) break;
+    if (pair > prev) pair = prev;
+    sum += pair;
+    prev = pair;
+  }
+  double tau = -1.0 + 2.0 * sum;
+  if (tau < 1.0 / (double)n) tau = 1.0 / (double)n;
+  ess[s] = (double)n / tau;
+}
+
+// ---------------------------------------------------------------- launchers
+
+size_t gene_smem_bytes(int N, int block) {
+  return (size_t)N * block * sizeof(double) + (size_t)(block / 32) * kNumPart * sizeof(double);
+}
+
+cudaError_t launch_gene(const ModelConst& mc, const DevPtrs& p, int block, cudaStream_t s) {
+  const int nblk = (mc.G + block - 1) / block;
+  k_gene_f64<<<nblk, block, gene_smem_bytes(mc.N, block), s>>>(mc, p);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_hyper(const ModelConst& mc, const DevPtrs& p, int nblk, cudaStream_t s) {
+  k_hyper<<<1, kHyperThreads, 0, s>>>(mc, p, nblk);
+  return cudaGetLastError();
+}
+
+cudaError_t prepare_gene_kernel(int N, int block) {
+  const size_t smem = gene_smem_bytes(N, block);
+  if (smem > 48 * 1024)
+    return cudaFuncSetAttribute(k_gene_f64, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                (int)smem);
+  return cudaSuccess;
+}
+
+cudaError_t launch_set_run(Hyper* hy, long long burnin, long long tune_start, long long thin,
+                           cudaStream_t s) {
+  k_set_run<<<1, 32, 0, s>>>(hy, burnin, tune_start, thin);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_init(const ModelConst& mc, const DevPtrs& p, const int32_t* y_in,
+                        int gene_major, const double* pinv, double w0, int set_state,
+                        long long trace_cap, cudaStream_t s) {
+  const int blk = 256;
+  const int grid = (mc.G + blk - 1) / blk;
+  k_init_run<<<1, 32, 0, s>>>(p.hyp, trace_cap);
+  k_init_genes<<<grid, blk, 0, s>>>(mc, p, y_in, gene_major, pinv, w0, set_state);
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return e;
+  k_zero_moments<<<grid, blk, 0, s>>>(mc, p);
+  e = cudaGetLastError();
+  if (e != cudaSuccess) return e;
+  k_init_hyper<<<1, 1024, 0, s>>>(mc, p, w0, set_state);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_zero_moments(const ModelConst& mc, const DevPtrs& p, cudaStream_t s) {
+  const int blk = 256;
+  const int grid = (mc.G + blk - 1) / blk;
+  k_zero_moments<<<grid, blk, 0, s>>>(mc, p);
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return e;
+  k_init_hyper<<<1, 1024, 0, s>>>(mc, p, 0.0, 0);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_uniforms(uint64_t seed, uint32_t chain, uint32_t stream, uint32_t index0,
+                            int n_index, uint32_t iter, uint32_t k0, int n_k, double* out,
+                            cudaStream_t s) {
+  const int blk = 128;
+  k_uniforms<<<(n_index + blk - 1) / blk, blk, 0, s>>>((uint32_t)seed, (uint32_t)(seed >> 32),
+                                                        chain, stream, index0, n_index, iter, k0,
+                                                        n_k, out);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_ess(const double* tr, long long rows, long long S, double* ess,
+                       cudaStream_t s) {
+  const int blk = 128;
+  k_ess<<<(unsigned)((S + blk - 1) / blk), blk, 0, s>>>(tr, rows, S, ess);
+  return cudaGetLastError();
+}
+
+}  // namespace fbs

@@ -1,0 +1,30 @@
+// fbs_kernels.h -- host-side launchers of the sweep, set-up, uniform and ESS
+// kernels (fbs_kernels.cu).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "fbs_common.cuh"
+
+namespace fbs {
+
+constexpr int kDefaultBlock = 128;
+
+size_t gene_smem_bytes(int N, int block);
+cudaError_t prepare_gene_kernel(int N, int block);
+cudaError_t launch_gene(const ModelConst& mc, const DevPtrs& p, int block, cudaStream_t s);
+cudaError_t launch_hyper(const ModelConst& mc, const DevPtrs& p, int nblk, cudaStream_t s);
+cudaError_t launch_set_run(Hyper* hy, long long burnin, long long tune_start, long long thin,
+                           cudaStream_t s);
+cudaError_t launch_init(const ModelConst& mc, const DevPtrs& p, const int32_t* y_in,
+                        int gene_major, const double* pinv, double w0, int set_state,
+                        long long trace_cap, cudaStream_t s);
+cudaError_t launch_zero_moments(const ModelConst& mc, const DevPtrs& p, cudaStream_t s);
+cudaError_t launch_uniforms(uint64_t seed, uint32_t chain, uint32_t stream, uint32_t index0,
+                            int n_index, uint32_t iter, uint32_t k0, int n_k, double* out,
+                            cudaStream_t s);
+cudaError_t launch_ess(const double* tr, long long rows, long long S, double* ess,
+                       cudaStream_t s);
+
+}  // namespace fbs

@@ -1,0 +1,178 @@
+// fbs_rng.cuh -- counter-based random numbers, variate generators and the
+// stepping-out slice sampler, as device functions.
+//
+// Random numbers: Philox4x32-10 (Salmon, Moraes, Dror & Shaw, SC 2011) in
+// place of the CURAND generator the paper used (Section 4.2).  A variable is
+// addressed by (stream, index, iteration, chain) and its k-th uniform comes
+// from counter block k/2, so any thread can draw any variable's numbers in any
+// order and the CPU oracle, which implements the same definition, consumes the
+// identical uniforms.
+#pragma once
+
+#include <stdint.h>
+
+namespace fbs {
+
+constexpr double kTwoPi = 6.283185307179586476925286766559;
+constexpr int kGammaAttempts = 64;
+constexpr int kTruncAttempts = 16;
+constexpr uint32_t kTruncStride = 256;  // uniforms reserved per truncated-draw attempt
+
+// Ten Philox rounds: two 32x32->64 multiplies per round, key bumped by the
+// Weyl constants between rounds.
+__device__ __forceinline__ uint4 philox4x32_10(uint4 c, uint32_t k0, uint32_t k1) {
+#pragma unroll
+  for (int r = 0; r < 10; ++r) {
+    const uint32_t lo0 = 0xD2511F53u * c.x, hi0 = __umulhi(0xD2511F53u, c.x);
+    const uint32_t lo1 = 0xCD9E8D57u * c.z, hi1 = __umulhi(0xCD9E8D57u, c.z);
+    c = make_uint4(hi1 ^ c.y ^ k0, lo1, hi0 ^ c.w ^ k1, lo0);
+    k0 += 0x9E3779B9u;
+    k1 += 0xBB67AE85u;
+  }
+  return c;
+}
+
+// The uniforms of one random variable.  u(k) returns uniform k; consecutive k
+// share a Philox block, which is cached.
+struct Rng {
+  uint32_t key0, key1, index, sblk, iter, chain;
+  uint32_t cached;
+  uint4 w;
+
+  __device__ __forceinline__ Rng(uint32_t seed_lo, uint32_t seed_hi, uint32_t chain_,
+                                 uint32_t stream, uint32_t index_, uint32_t iter_)
+      : key0(seed_lo), key1(seed_hi), index(index_), sblk(stream << 24), iter(iter_),
+        chain(chain_), cached(0xFFFFFFFFu), w(make_uint4(0, 0, 0, 0)) {}
+
+  __device__ __forceinline__ double u(uint32_t k) {
+    const uint32_t blk = k >> 1;
+    if (blk != cached) {
+      w = philox4x32_10(make_uint4(index, sblk | blk, iter, chain), key0, key1);
+      cached = blk;
+    }
+    const unsigned long long x = (k & 1u)
+                                     ? ((unsigned long long)w.w << 32 | w.z)
+                                     : ((unsigned long long)w.y << 32 | w.x);
+    // (floor(x / 2^12) + 1/2) / 2^52: every step is exact in double
+    return __dmul_rn(__dadd_rn(__ull2double_rn(x >> 12), 0.5), 0x1p-52);
+  }
+};
+
+// Box-Muller normal from uniforms k0, k0+1 (cosine branch).
+__device__ __forceinline__ double normal_bm(Rng& r, uint32_t k0) {
+  const double u1 = r.u(k0), u2 = r.u(k0 + 1);
+  return __dmul_rn(sqrt(__dmul_rn(-2.0, log(u1))), cos(__dmul_rn(kTwoPi, u2)));
+}
+
+// Gamma(shape, 1) by Marsaglia & Tsang (2000): attempt j takes uniforms
+// k0+4j, k0+4j+1 (normal) and k0+4j+2 (acceptance); uniform k0+3 is the
+// U^(1/shape) factor for shape < 1.  After 64 failed attempts the shape is
+// returned and *capped is set.
+__device__ __forceinline__ double gamma_mt(double shape, Rng& r, uint32_t k0, bool* capped) {
+  const double alpha = shape < 1.0 ? __dadd_rn(shape, 1.0) : shape;
+  const double dd = __dsub_rn(alpha, 1.0 / 3.0);
+  const double cc = 1.0 / sqrt(__dmul_rn(9.0, dd));
+  double boost = 1.0;
+  if (shape < 1.0) boost = pow(r.u(k0 + 3), 1.0 / shape);
+  for (uint32_t j = 0; j < (uint32_t)kGammaAttempts; ++j) {
+    const double x = normal_bm(r, k0 + 4 * j);
+    double v = __dadd_rn(1.0, __dmul_rn(cc, x));
+    if (v <= 0.0) continue;
+    v = __dmul_rn(__dmul_rn(v, v), v);
+    const double u = r.u(k0 + 4 * j + 2);
+    const double x2 = __dmul_rn(x, x);
+    if (u < __dsub_rn(1.0, __dmul_rn(__dmul_rn(0.0331, x2), x2)))
+      return __dmul_rn(__dmul_rn(dd, v), boost);
+    const double rhs = __dadd_rn(__dmul_rn(0.5, x2),
+                                 __dmul_rn(dd, __dadd_rn(__dsub_rn(1.0, v), log(v))));
+    if (log(u) < rhs) return __dmul_rn(__dmul_rn(dd, v), boost);
+  }
+  *capped = true;
+  return shape;
+}
+
+// Inverse-Gamma(shape, scale) truncated to (0, upper) by rejection; attempt t
+// uses the gamma uniforms starting at 256 t.  After 16 failures `keep` is
+// returned and *capped is set: keeping the current value leaves the target
+// unchanged because the failure probability does not depend on it.
+__device__ __forceinline__ double trunc_invgamma(double shape, double scale, double upper,
+                                                 double keep, Rng& r, bool* gcap, bool* tcap) {
+  for (uint32_t t = 0; t < (uint32_t)kTruncAttempts; ++t) {
+    const double gv = gamma_mt(shape, r, kTruncStride * t, gcap);
+    const double x = scale / gv;
+    if (x < upper) return x;
+  }
+  *tcap = true;
+  return keep;
+}
+
+struct SliceResult {
+  double x;         // new value
+  double aux;       // the density functor's auxiliary value at x
+  unsigned evals;   // log-density evaluations
+  bool capped;      // shrinkage ran out of proposals; x is the start value
+  bool nonfinite;   // log density at the start value was not finite
+};
+
+// One update of the univariate stepping-out slice sampler (Algorithm 2,
+// steps 1-6) from x0 with width w and stepping-out bound K.  Uniform 0 sets
+// the level log u = log f(x0) + log U, uniform 1 places the interval, uniform
+// 2 splits K into K_L + K_R, uniform 3+j is the j-th shrinkage proposal.
+// f(x, &aux) returns log f(x) (up to a constant) and an auxiliary value that is
+// kept for the accepted point.  The interval arithmetic is rounded step by
+// step (no fused multiply-add) so that it matches a plain IEEE evaluation.
+template <class F>
+__device__ __forceinline__ SliceResult slice_update(double x0, double w, const F& f, Rng& r,
+                                                    int K, int shrink_max) {
+  SliceResult res;
+  double aux0;
+  const double f0 = f(x0, &aux0);
+  res.evals = 1;
+  res.nonfinite = !isfinite(f0);
+  const double logu = __dadd_rn(f0, log(r.u(0)));
+  const double v = __dmul_rn(w, r.u(1));
+  double lo = __dsub_rn(x0, v);
+  double hi = __dadd_rn(lo, w);
+  int KL = (int)__dmul_rn((double)(K + 1), r.u(2));
+  if (KL > K) KL = K;
+  const int KR = K - KL;
+  double aux;
+  for (int k = 0; k < KL; ++k) {
+    ++res.evals;
+    if (logu < f(lo, &aux)) lo = __dsub_rn(lo, w); else break;
+  }
+  for (int k = 0; k < KR; ++k) {
+    ++res.evals;
+    if (logu < f(hi, &aux)) hi = __dadd_rn(hi, w); else break;
+  }
+  for (int j = 0; j < shrink_max; ++j) {
+    const double xs = __dadd_rn(lo, __dmul_rn(__dsub_rn(hi, lo), r.u(3u + (uint32_t)j)));
+    ++res.evals;
+    if (logu < f(xs, &aux)) {
+      res.x = xs;
+      res.aux = aux;
+      res.capped = false;
+      return res;
+    }
+    if (xs > x0) hi = xs; else lo = xs;
+  }
+  res.x = x0;
+  res.aux = aux0;
+  res.capped = true;
+  return res;
+}
+
+// Width tuning, Algorithm 2 step 7: while it <= M_B add it*|x_new - x_old| to
+// w_aux; once it > M_C set w = w_aux / (it (it+1) / 2) when that is positive and
+// finite.
+__device__ __forceinline__ void tune_width(double& w, double& waux, long long it, double x_new,
+                                           double x_old, long long burnin, long long tune_start) {
+  if (it > burnin) return;
+  waux = __dadd_rn(waux, __dmul_rn((double)it, fabs(__dsub_rn(x_new, x_old))));
+  if (it > tune_start) {
+    const double wn = __ddiv_rn(waux, __dmul_rn(__dmul_rn(0.5, (double)it), (double)(it + 1)));
+    if (wn > 0.0 && isfinite(wn)) w = wn;
+  }
+}
+
+}  // namespace fbs

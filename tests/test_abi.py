@@ -1,0 +1,82 @@
+"""The C-ABI library loads and exports every entry point include/*.h declares;
+argument validation needs no GPU (it fails before any CUDA call)."""
+import glob
+import os
+import re
+
+import numpy as np
+import pytest
+
+import paper_1606_06659_gb300 as fbs
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def declared_symbols():
+    names = set()
+    for hdr in glob.glob(os.path.join(ROOT, "include", "*.h")):
+        text = open(hdr).read()
+        text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+        names |= set(re.findall(r"\b(fbs_\w+)\s*\(", text))
+    return names
+
+
+def test_library_exports_every_declared_symbol():
+    lib = fbs.load_library()
+    names = declared_symbols()
+    assert len(names) >= 16
+    assert names <= set(fbs.EXPORTED) | names
+    for n in sorted(names):
+        assert getattr(lib, n) is not None, n
+    assert set(fbs.EXPORTED) == names
+
+
+def test_default_options():
+    o = fbs.default_options()
+    assert (o.precision, o.w0, o.step_out_max, o.shrink_max, o.moments_eps) == (0, 1.0, 100, 100, 1)
+
+
+def _args(**over):
+    N, G, L = 4, 10, 2
+    a = dict(y=np.ones((G, N), np.int32),
+             X=np.stack([np.ones(N), [1.0, 1.0, -1.0, -1.0]], 1), h=np.zeros(N),
+             priors={"a": 1.0, "b": 1.0, "d": 10.0, "c": np.full(L, 10.0), "s": np.full(L, 10.0)})
+    a.update(over)
+    return a
+
+
+@pytest.mark.parametrize("case", ["N0", "G1", "L9", "singular", "negative_y", "nan_h",
+                                  "bad_prior", "too_many_classes", "bad_precision"])
+def test_invalid_arguments_rejected_before_any_cuda_call(case):
+    kw = {}
+    a = _args()
+    if case == "N0":
+        a["y"] = np.ones((10, 0), np.int32); a["X"] = np.ones((0, 2)); a["h"] = np.zeros(0)
+    elif case == "G1":
+        a["y"] = np.ones((1, 4), np.int32)
+    elif case == "L9":
+        a["X"] = np.ones((4, 9)); a["priors"]["c"] = np.full(9, 1.0); a["priors"]["s"] = np.full(9, 1.0)
+    elif case == "singular":
+        a["X"] = np.ones((4, 2))
+    elif case == "negative_y":
+        a["y"] = a["y"].copy(); a["y"][3, 2] = -1
+    elif case == "nan_h":
+        a["h"] = np.array([0.0, np.nan, 0.0, 0.0])
+    elif case == "bad_prior":
+        a["priors"]["d"] = 0.0
+    elif case == "too_many_classes":
+        N = 12
+        a["y"] = np.ones((10, N), np.int32)
+        a["X"] = np.stack([np.ones(N), np.arange(N, dtype=float) / 7.0], 1)
+        a["h"] = np.zeros(N)
+    elif case == "bad_precision":
+        kw["precision"] = 7
+    with pytest.raises(fbs.FbsError) as e:
+        fbs.Sampler(a["y"], a["X"], a["h"], a["priors"], workspace="library", **kw)
+    assert e.value.code == fbs.FBS_E_ARG
+
+
+def test_workspace_bytes_grows_with_trace():
+    base = fbs.workspace_bytes(16, 40000, 5)
+    o = fbs.default_options(trace_cap=10, trace_beta=1)
+    assert fbs.workspace_bytes(16, 40000, 5, o) >= base + 10 * 40000 * 5 * 8

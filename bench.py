@@ -1,0 +1,367 @@
+#!/usr/bin/env python
+"""Benchmark of the GB300 Gibbs sampler on the paper-scale workload.
+
+Workload: the RNA-seq model of Landau & Niemi (arXiv 1606.06659) on synthetic
+Poisson-lognormal counts with N=16 samples (4 varieties x 4 libraries, the
+paper's 16 x 5 design), G=40000 genes, L=5, theta=(4,0,0,0,0),
+sigma=(2,.5,.3,.2,.2), tau=0.1, nu=3; priors c=s=10, a=b=1, d=10; run length
+20000 iterations with 10000 burn-in and thin 10.
+
+Metric: Gibbs iterations per second (value, device-timed) and min ESS per
+second over all G*L beta.  A "step" is `--sweeps-per-step` consecutive Gibbs
+sweeps (one fbs_run call replaying the captured CUDA graph); L2 is flushed
+(a 256 MiB write) before every timed step.
+
+Lines printed by rank 0 (one JSON object):
+  --impl ours       the CUDA library through its C ABI
+  --impl reference  the CPU oracle on this host's cores, on gene samples of the
+                    same workload, scaled to the full G (there is no runnable
+                    reference implementation of the paper)
+With torchrun (N>1 ranks) every rank runs an independent chain on its own GPU
+(chains are replicas; nothing is exchanged) and value = all ranks' sweeps /
+the slowest rank's time.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+METRIC = "Gibbs iters/sec and min ESS/sec over beta at N=16,G=40000 vs plain FP64 form"
+CFG = 1
+L2_FLUSH_BYTES = 256 << 20
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", choices=("ours", "reference"), default="ours")
+    ap.add_argument("--precision", choices=("f64",), default="f64")
+    ap.add_argument("--sweeps-per-step", type=int, default=100)
+    ap.add_argument("--no-ess", action="store_true", help="skip the 20000-iteration ESS job")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--cpu-seconds", type=float, default=12.0)
+    ap.add_argument("--tune-sweeps", type=int, default=2000,
+                    help="burn-in sweeps that tune the slice widths before the timed steps")
+    return ap.parse_args()
+
+
+# --------------------------------------------------------------------------- helpers
+# FP64 floating-point operations per slice log-density evaluation of k_gene_f64
+# (DFMA counted as 2, DADD and DMUL as 1), measured with ncu on the paper-scale
+# workload: (2*59.0 + 18.2 + 9.5) thread instructions per elapsed cycle x 2.265e6
+# cycles per launch / 6.15e6 device-counted evaluations per launch.  It covers
+# everything the kernel does per evaluation on average (density, Philox-to-double,
+# interval arithmetic, the per-draw log and the moments).  Re-measure when the
+# kernel changes.
+FP64_FLOP_PER_EVAL = 53.7
+FP64_TRAFFIC_BYTES = 39.1e6   # dram read+write per launch, same ncu capture
+# FP64 peak from unit counts and clock: 152 SMs x 2 DFMA/clk x 2 flop x 2.07 GHz
+FP64_PEAK_TFLOPS = 152 * 2 * 2 * 2.07e9 / 1e12
+
+
+def bytes_per_gene(N, L):
+    """Algorithmic HBM bytes of one gene in one post-burn-in FP64 sweep of the
+    per-gene kernel: reads y (4N), eps, w_eps (8N each), beta, w_beta, T (8L each),
+    gamma (8); read+write of the eps/beta/gamma running mean and mean square
+    (32 per parameter); writes eps (8N), beta (8L), gamma (8)."""
+    return 60 * N + 64 * L + 48
+
+
+class ClockSampler:
+    """nvidia-smi clock / throttle-reason samples taken every 200 ms."""
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index):
+        self.gpu, self.proc, self.lines = gpu_index, None, []
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.gpu), f"--query-gpu={self.FIELDS}",
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.thread = threading.Thread(target=self._read, daemon=True)
+            self.thread.start()
+        except (FileNotFoundError, OSError):
+            self.proc = None
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        self.thread.join(timeout=2)
+        sm, smax, reasons = [], [], set()
+        names = ("hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap")
+        for ln in self.lines:
+            parts = [p.strip() for p in ln.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                smax.append(float(parts[2]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, parts[5:9]):
+                if v.lower() == "active":
+                    reasons.add(nm)
+        return {"sm_mhz": statistics.median(sm) if sm else None,
+                "sm_max_mhz": max(smax) if smax else None, "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+def measured_peaks():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    try:
+        with open(path) as f:
+            p = json.load(f)
+        return float(p["hbm_gbs"]), "measured"
+    except (OSError, KeyError, ValueError):
+        return 6800.0, "fallback"
+
+
+def cpu_baseline(data, seconds, G_full):
+    """The CPU oracle as it stands, single-threaded, on a gene sample of the same
+    workload; iterations/s scaled to the full G (one sweep costs O(G))."""
+    import oracle
+    G_s = 2000
+    sub = {k: data[k] for k in ("X", "h", "priors")}
+    sub["y"] = data["y"][:G_s]
+    ch = oracle.Chain(sub["y"], sub["X"], sub["h"], sub["priors"], seed=7, burnin=10000,
+                      tune_start=5000).init_default()
+    n, t0 = 0, time.perf_counter()
+    while True:
+        ch.sweep()
+        n += 1
+        el = time.perf_counter() - t0
+        if el >= seconds:
+            break
+    per_sweep_full = el / n * (G_full / G_s)
+    return {"value": 1.0 / per_sweep_full, "unit": "iters/s", "cores": 1, "kind": "oracle",
+            "sample": f"{n} oracle sweeps over the first {G_s} of {G_full} genes (burn-in, "
+                      f"{el:.1f} s), time scaled by G/{G_s}"}
+
+
+# --------------------------------------------------------------------------- reference arm
+def run_reference(args, rank):
+    if rank != 0:
+        return
+    from paper_1606_06659_gb300 import synthetic
+    data = synthetic.make_config(CFG)
+    G = data["spec"]["G"]
+    import oracle
+    G_s = 1000
+    ch = oracle.Chain(data["y"][:G_s], data["X"], data["h"], data["priors"], seed=7,
+                      burnin=10000, tune_start=5000).init_default()
+    for _ in range(args.warmup):
+        ch.sweep()
+    times = []
+    for _ in range(args.steps):
+        t0 = time.perf_counter()
+        ch.sweep()
+        times.append(time.perf_counter() - t0)
+    per_sweep_full = statistics.mean(times) * G / G_s
+    value = 1.0 / per_sweep_full
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": "iters/s",
+            "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": per_sweep_full * 1e3, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": "RNA-seq Gibbs sweep N=16 G=40000 L=5 (paper design)",
+                       "N": 16, "G": G, "L": 5, "step": "one oracle sweep over a gene sample"},
+            "cpu_baseline": {"value": value, "unit": "iters/s", "cores": 1, "kind": "oracle",
+                             "sample": f"each step one sweep over the first {G_s} of {G} "
+                                       f"genes, time scaled by G/{G_s}"},
+            "e2e": {"value": value, "unit": "iters/s", "h2d_bytes_per_step": 0,
+                    "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+# --------------------------------------------------------------------------- our arm
+def main():
+    args = parse()
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if args.impl == "reference":
+        run_reference(args, rank)
+        return
+
+    import torch
+    import torch.distributed as dist
+
+    import paper_1606_06659_gb300 as fbs
+    from paper_1606_06659_gb300 import synthetic
+
+    if not os.path.exists(fbs.LIB_PATH):
+        from paper_1606_06659_gb300 import build as fbs_build
+        fbs_build.build()
+    assert torch.cuda.is_available(), "bench.py needs a GPU"
+    torch.cuda.set_device(local)
+    if world > 1:
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+
+    data = synthetic.make_config(CFG)
+    spec = data["spec"]
+    N, G, L = spec["N"], spec["G"], spec["L"]
+    S = args.sweeps_per_step
+    seed = 20160621
+    stream = torch.cuda.current_stream()
+
+    def barrier():
+        if world > 1:
+            dist.barrier()
+        torch.cuda.synchronize()
+
+    # ---- the configured job through the public API with host buffers (e2e),
+    #      which also yields the beta trace for the ESS metric
+    y_pinned = torch.from_numpy(np.ascontiguousarray(data["y"])).pin_memory()
+    y_host = y_pinned.numpy()
+    iters, burnin, thin = spec["iters"], spec["burnin"], spec["thin"]
+    trace_rows = (iters - burnin) // thin
+    ess = None
+    job = None
+    if not args.no_ess:
+        barrier()
+        t0 = time.perf_counter()
+        smp = fbs.Sampler(y_host, data["X"], data["h"], data["priors"], seed=seed, chain=rank,
+                          trace_cap=trace_rows, trace_beta=1)
+        ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        ev0.record(stream)
+        phi_reads = 0
+        for _ in range(iters // S):
+            smp.run(S, burnin=burnin, thin=thin)
+            smp.phi()
+            phi_reads += 1
+        ev1.record(stream)
+        mom = smp.moments()
+        torch.cuda.synchronize()
+        wall = time.perf_counter() - t0
+        job_device_s = ev0.elapsed_time(ev1) / 1e3
+        e = smp.beta_ess()
+        ess = {"min": float(e.min()), "p01": float(np.percentile(e, 1)),
+               "median": float(np.median(e)), "rows": trace_rows}
+        h2d = y_host.nbytes + data["X"].nbytes + data["h"].nbytes
+        d2h = phi_reads * 8 * (2 * L + 2) + sum(np.asarray(v).nbytes for k, v in mom.items()
+                                                 if k != "count")
+        job = {"wall_s": wall, "device_s": job_device_s, "steps": phi_reads,
+               "h2d": h2d, "d2h": d2h}
+        smp.close()
+        del smp
+        torch.cuda.empty_cache()
+
+    # ---- device-timed throughput: W warm-up + K timed steps of S sweeps
+    smp = fbs.Sampler(data["y"], data["X"], data["h"], data["priors"], seed=seed + 1, chain=rank)
+    tb = args.tune_sweeps // 2
+    smp.run(args.tune_sweeps, burnin=tb, thin=thin)   # tune the slice widths (burn-in)
+    flush = torch.empty(L2_FLUSH_BYTES, dtype=torch.uint8, device="cuda")
+    for i in range(args.warmup):
+        flush.fill_(i & 0xFF)
+        smp.run(S, burnin=tb, thin=thin)
+    barrier()
+    clocks = ClockSampler(local)
+    clocks.start()
+    evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+           for _ in range(args.steps)]
+    c0 = smp.counters()
+    for i, (a, b) in enumerate(evs):
+        flush.fill_((i + 7) & 0xFF)
+        a.record(stream)
+        smp.run(S, burnin=tb, thin=thin)
+        b.record(stream)
+    torch.cuda.synchronize()
+    c1 = smp.counters()
+    clk = clocks.stop()
+    step_ms = [a.elapsed_time(b) for a, b in evs]
+    total_s = sum(step_ms) / 1e3
+    if world > 1:
+        t = torch.tensor([total_s], device="cuda", dtype=torch.float64)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        total_s = float(t.item())
+        barrier()
+    sweeps_all = args.steps * S * world
+    value = sweeps_all / total_s
+
+    # ---- roofline of the dominant (per-gene) kernel: direct launches with
+    #      CUDA events on its launching stream
+    ms_gene, ms_hyper = smp.profile(S, burnin=tb, thin=thin)
+    peak, peak_kind = measured_peaks()
+    bpg = bytes_per_gene(N, L)
+    achieved = bpg * G / (ms_gene / 1e3) / 1e9
+    evals = {k: (c1[k] - c0[k]) / (args.steps * S) for k in ("evals_eps", "evals_beta",
+                                                               "evals_nu")}
+    ev_launch = evals["evals_eps"] + evals["evals_beta"]
+    tflops = ev_launch * FP64_FLOP_PER_EVAL / (ms_gene / 1e3) / 1e12
+    roofline = {"bound": "alu", "achieved": tflops, "peak": FP64_PEAK_TFLOPS,
+                "unit": "TFLOP/s (FP64)", "frac": tflops / FP64_PEAK_TFLOPS,
+                "traffic": FP64_TRAFFIC_BYTES,
+                "kernel": "k_gene_f64", "kernel_ms": ms_gene, "hyper_kernel_ms": ms_hyper,
+                "flop_per_eval": FP64_FLOP_PER_EVAL, "evals_per_launch": ev_launch,
+                "peak_source": "152 SMs x 2 DFMA/clk x 2 flop x 2.07 GHz",
+                "hbm": {"achieved": achieved, "peak": peak, "unit": "GB/s",
+                        "frac": achieved / peak, "bytes_per_gene": bpg, "genes_per_launch": G,
+                        "peak_source": peak_kind}}
+    smp.close()
+
+    if rank != 0:
+        if world > 1:
+            dist.destroy_process_group()
+        return
+    line = {
+        "metric": METRIC, "value": value, "unit": "iters/s", "n_gpus": world,
+        "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": statistics.mean(step_ms), "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": args.precision, "data": "synthetic",
+        "config": {"workload": "RNA-seq Gibbs sweep N=16 G=40000 L=5 (paper design), "
+                               "one chain per GPU",
+                   "N": N, "G": G, "L": L, "sweeps_per_step": S,
+                   "l2": "256 MiB write before every timed step; state (~40 MB) stays "
+                         "L2-resident within a step",
+                   "job": f"{iters} iterations, burn-in {burnin}, thin {thin}",
+                   "parallelism": f"{world} independent chain(s)"},
+        "gpu_launches": args.steps * (2 * S + 1),
+        "clocks": clk,
+        "roofline": roofline,
+        "evals_per_sweep": evals,
+    }
+    if job is not None:
+        line["e2e"] = {"value": iters * world / job["wall_s"], "unit": "iters/s",
+                       "h2d_bytes_per_step": job["h2d"] / job["steps"],
+                       "d2h_bytes_per_step": job["d2h"] / job["steps"],
+                       "what": "the whole configured job through fbs_init/fbs_run/fbs_moments "
+                               "with pinned host counts: init upload, 20000 sweeps, phi read "
+                               "back after every step, moments read back at the end"}
+        line["min_ess_per_sec"] = ess["min"] / job["wall_s"]
+        line["ess"] = ess | {"job_wall_s": job["wall_s"], "job_device_s": job["device_s"],
+                             "job_iters_per_s_device": iters / job["device_s"]}
+    if not args.no_cpu_baseline:
+        line["cpu_baseline"] = cpu_baseline(data, args.cpu_seconds, G)
+    print(json.dumps(line), flush=True)
+    if world > 1:
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

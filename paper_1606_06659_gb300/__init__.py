@@ -211,6 +211,13 @@ class Sampler:
         out["it"] = it.value
         return out
 
+    def phi(self):
+        """Current hyperparameters (nu, tau, theta[L], sigma^2[L])."""
+        out = np.empty(self.P)
+        _check(self.lib.fbs_get_state(self.h, None, None, None, _pd(out), None, None, None, None,
+                                      None, None, None))
+        return out
+
     def set_state(self, it=0, **arrays):
         names = ("eps", "beta", "gam", "phi", "w_eps", "waux_eps", "w_beta", "waux_beta", "w_nu",
                  "waux_nu")

@@ -189,6 +189,66 @@ int fbs_profile(fbs_handle* h, int64_t n_iter, int64_t burnin, int64_t thin, dou
 int fbs_uniforms(uint64_t seed, uint32_t chain, uint32_t stream, uint32_t index0, int n_index,
                  uint32_t iter, uint32_t k0, int n_k, double* out);
 
+/* ---- One sweep without any allocation ------------------------------------
+ *
+ * The paper has no counterpart to this entry point; it exists for callers
+ * that cannot allocate device memory at the time they want to sweep: code that
+ * runs while the host program forbids cudaMalloc (inside a region where the
+ * allocator must not be called, or where all device memory has been handed to
+ * another pool beforehand), or that already holds the chain's arrays in memory
+ * it owns.  fbs_init needs device memory (its own or a caller workspace) and
+ * creates a stream and events; fbs_sweep_noalloc needs neither.
+ *
+ * It runs iteration `it` of Algorithm 1 (the same kernels as fbs_run) on the
+ * caller's device arrays, in the handle's device layout (genes fastest):
+ *   y [N][G] int32, T [L][G] with T_lg = sum_n y_gn X_nl (inputs);
+ *   eps, w_eps, waux_eps [N][G]; beta, w_beta, waux_beta [L][G]; gamma [G];
+ *   hyp [2L+4] = (nu, tau, theta_1..L, sigma^2_1..L, w_nu, waux_nu)  (in/out);
+ *   running moments m_* / q_* (mean / mean square): eps [N][G] (both may be
+ *   NULL to skip), beta [L][G], gamma [G], phi [2L+2] -- updated, with n_mom
+ *   draws already folded in, when it > burnin and otherwise untouched.
+ * X, h and the priors are host arrays read during the call.  Slice widths are
+ * tuned while it <= burnin (M_C = burnin/2).  No trace is written.
+ *
+ * Scratch: the per-block partial sums, the hyperparameter block and the
+ * counters live in one file-scope static __device__ array of about 290 KiB
+ * (FBS_NOALLOC_MAX_GENES / 128 blocks), which every GPU that loads the library
+ * holds until the process exits.  G above FBS_NOALLOC_MAX_GENES returns
+ * FBS_E_ARG.  The first call on a device looks up the array's device address
+ * (cudaGetSymbolAddress) with that device current; make that first call before
+ * any stream capture.  All calls share the array and every call rewrites what
+ * it reads from it, so calls whose work overlaps on the GPU (different streams
+ * at the same time) race; calls on one stream are ordered.  The call is
+ * asynchronous on `stream` (NULL = legacy default stream): the outputs are
+ * ready when the stream reaches them.  It calls no cudaMalloc, cudaFree or
+ * other allocating routine.  Errors: FBS_E_ARG (sizes, NULL pointers, moment
+ * arrays missing after burn-in, priors, X with too many distinct values),
+ * FBS_E_CUDA. */
+#define FBS_NOALLOC_MAX_GENES (2048 * 128)
+
+typedef struct {
+  int N, G, L;
+  const double* X;      /* host [N][L] */
+  const double* h;      /* host [N] */
+  fbs_priors priors;    /* host */
+  uint64_t seed;
+  uint32_t chain;
+  int step_out_max, shrink_max;
+  int64_t it;           /* iteration to run, >= 1 */
+  int64_t burnin;       /* M_B */
+  int64_t n_mom;        /* draws already in the moments */
+  const int32_t* y;
+  const double* T;
+  double *eps, *w_eps, *waux_eps;
+  double *beta, *w_beta, *waux_beta;
+  double* gam;
+  double* hyp;
+  double *m_eps, *q_eps, *m_beta, *q_beta, *m_gam, *q_gam, *m_phi, *q_phi;
+  void* stream;
+} fbs_sweep_args;
+
+int fbs_sweep_noalloc(const fbs_sweep_args* a);
+
 /* Release the handle and any memory the library allocated for it. */
 void fbs_free(fbs_handle* h);
 

@@ -30,7 +30,8 @@ NUM_COUNTERS = len(COUNTER_NAMES)
 EXPORTED = ("fbs_default_options", "fbs_workspace_bytes", "fbs_init", "fbs_run", "fbs_sync",
             "fbs_moments", "fbs_get_state", "fbs_set_state", "fbs_trace", "fbs_beta_ess",
             "fbs_count_sums", "fbs_counters", "fbs_profile", "fbs_uniforms", "fbs_free",
-            "fbs_last_error_string")
+            "fbs_last_error_string", "fbs_sweep_noalloc")
+NOALLOC_MAX_GENES = 2048 * 128
 
 
 class FbsError(RuntimeError):
@@ -54,6 +55,18 @@ class Options(C.Structure):
 _PD = C.POINTER(C.c_double)
 _PI64 = C.POINTER(C.c_int64)
 _lib = None
+
+
+class SweepArgs(C.Structure):
+    """fbs_sweep_args: one sweep on caller-owned device arrays (fbs_sweep_noalloc)."""
+    _fields_ = [("N", C.c_int), ("G", C.c_int), ("L", C.c_int), ("X", _PD), ("h", _PD),
+                ("priors", Priors), ("seed", C.c_uint64), ("chain", C.c_uint32),
+                ("step_out_max", C.c_int), ("shrink_max", C.c_int), ("it", C.c_int64),
+                ("burnin", C.c_int64), ("n_mom", C.c_int64), ("y", C.c_void_p),
+                ("T", C.c_void_p)] + [(n, C.c_void_p) for n in (
+                    "eps", "w_eps", "waux_eps", "beta", "w_beta", "waux_beta", "gam", "hyp",
+                    "m_eps", "q_eps", "m_beta", "q_beta", "m_gam", "q_gam", "m_phi", "q_phi",
+                    "stream")]
 
 
 def load_library(path: str = LIB_PATH):
@@ -81,6 +94,7 @@ def load_library(path: str = LIB_PATH):
     lib.fbs_counters.argtypes = [vp, _PI64]
     lib.fbs_profile.argtypes = [vp, i64, i64, i64, _PD, _PD]
     lib.fbs_uniforms.argtypes = [u64, u32, u32, u32, i32, u32, u32, i32, _PD]
+    lib.fbs_sweep_noalloc.argtypes = [C.POINTER(SweepArgs)]
     lib.fbs_free.argtypes = [vp]
     lib.fbs_free.restype = None
     lib.fbs_last_error_string.argtypes = []
@@ -125,6 +139,34 @@ def uniforms(seed, chain, stream, index0, n_index, it, k0, n_k) -> np.ndarray:
     _check(load_library().fbs_uniforms(seed, chain, stream, index0, n_index, it, k0, n_k,
                                        _pd(out)))
     return out
+
+
+def sweep_noalloc(X, h, priors, *, seed, it, burnin, n_mom=0, chain=0, step_out_max=100,
+                  shrink_max=100, stream=None, **dev):
+    """One sweep on caller-owned device arrays with no allocation (fbs_sweep_noalloc).
+
+    ``dev`` maps y, T, eps, w_eps, waux_eps, beta, w_beta, waux_beta, gam, hyp and the
+    optional moment arrays (m_eps, q_eps, m_beta, q_beta, m_gam, q_gam, m_phi, q_phi)
+    to device addresses (ints) in the device layout described in include/fbs.h.
+    """
+    X = np.ascontiguousarray(X, np.float64)
+    N, L = X.shape
+    h = np.ascontiguousarray(h, np.float64).reshape(N)
+    c = np.ascontiguousarray(np.broadcast_to(priors["c"], (L,)), np.float64)
+    s = np.ascontiguousarray(np.broadcast_to(priors["s"], (L,)), np.float64)
+    a = SweepArgs()
+    a.N, a.G, a.L = N, int(dev.pop("G")), L
+    a.X, a.h = _pd(X), _pd(h)
+    a.priors = Priors(float(priors["a"]), float(priors["b"]), float(priors["d"]), _pd(c), _pd(s))
+    a.seed, a.chain = int(seed), int(chain)
+    a.step_out_max, a.shrink_max = int(step_out_max), int(shrink_max)
+    a.it, a.burnin, a.n_mom = int(it), int(burnin), int(n_mom)
+    for name, ptr in dev.items():
+        if name not in dict(SweepArgs._fields_):
+            raise TypeError(f"unknown device array {name}")
+        setattr(a, name, ptr)
+    a.stream = stream
+    _check(load_library().fbs_sweep_noalloc(C.byref(a)))
 
 
 class Sampler:

@@ -83,6 +83,8 @@ int block_of(const fbs_options* o) {
 
 }  // namespace
 
+void fbs::set_last_error(const std::string& msg) { g_err = msg; }
+
 struct fbs_handle {
   ModelConst mc;
   DevPtrs p;

@@ -5,6 +5,8 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include <string>
+
 #include "fbs_common.cuh"
 
 namespace fbs {
@@ -24,6 +26,9 @@ cudaError_t launch_zero_moments(const ModelConst& mc, const DevPtrs& p, cudaStre
 cudaError_t launch_uniforms(uint64_t seed, uint32_t chain, uint32_t stream, uint32_t index0,
                             int n_index, uint32_t iter, uint32_t k0, int n_k, double* out,
                             cudaStream_t s);
+// Sets the message fbs_last_error_string() returns on the calling thread.
+void set_last_error(const std::string& msg);
+
 cudaError_t launch_ess(const double* tr, long long rows, long long S, double* ess,
                        cudaStream_t s);
 

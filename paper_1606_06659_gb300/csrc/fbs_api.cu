@@ -76,6 +76,43 @@ Layout make_layout(int N, int G, int L, int nblk, long long trace_cap, int trace
   return o;
 }
 
+// FP32 form: per-gene state in FP32, four FP32 moment planes per parameter.
+struct LayoutF32 {
+  size_t y, T, eps, w_eps, waux_eps, mom_eps, beta, w_beta, waux_beta, mom_beta, gam, mom_gam;
+  size_t partial, hyp, trace_phi, trace_beta, counters, pinv, total;
+};
+
+LayoutF32 make_layout_f32(int N, int G, int L, int nblk, long long trace_cap, int trace_beta) {
+  LayoutF32 o;
+  size_t at = 0;
+  auto take = [&](size_t bytes) {
+    size_t here = at;
+    at = align256(at + bytes);
+    return here;
+  };
+  const size_t NG = (size_t)N * G, LG = (size_t)L * G, P = 2 * (size_t)L + 2;
+  o.y = take(NG * sizeof(int32_t));
+  o.T = take(LG * 8);
+  o.eps = take(NG * 4);
+  o.w_eps = take(NG * 4);
+  o.waux_eps = take(NG * 4);
+  o.mom_eps = take(4 * NG * 4);
+  o.beta = take(LG * 4);
+  o.w_beta = take(LG * 4);
+  o.waux_beta = take(LG * 4);
+  o.mom_beta = take(4 * LG * 4);
+  o.gam = take((size_t)G * 4);
+  o.mom_gam = take(4 * (size_t)G * 4);
+  o.partial = take((size_t)nblk * kNumPart * 8);
+  o.hyp = take(sizeof(Hyper));
+  o.trace_phi = take((size_t)(trace_cap > 0 ? trace_cap : 1) * P * 8);
+  o.trace_beta = trace_beta && trace_cap > 0 ? take((size_t)trace_cap * LG * 8) : 0;
+  o.counters = take(FBS_NUM_COUNTERS * sizeof(unsigned long long));
+  o.pinv = take((size_t)kMaxL * kMaxN * 8);
+  o.total = at + 256;
+  return o;
+}
+
 int block_of(const fbs_options* o) {
   int b = o && o->block > 0 ? o->block : kDefaultBlock;
   return b;
@@ -87,9 +124,12 @@ void fbs::set_last_error(const std::string& msg) { g_err = msg; }
 
 struct fbs_handle {
   ModelConst mc;
-  DevPtrs p;
+  DevPtrs p;        // FP64 state; in the FP32 form only the shared fields are set
+  DevPtrsF32 pf;    // FP32 state (FP32 form only)
+  int prec = FBS_F64;
   fbs_options opt;
   Layout lay;
+  LayoutF32 lay32;
   int block = kDefaultBlock, nblk = 0, seg = 100;
   bool x_integral = false;
   void* ws = nullptr;
@@ -119,7 +159,6 @@ int check_opts(const fbs_options* o) {
   if (!o) return FBS_OK;
   if (o->precision != FBS_F64 && o->precision != FBS_F32)
     return fail(FBS_E_ARG, "precision must be FBS_F64 or FBS_F32");
-  if (o->precision == FBS_F32) return fail(FBS_E_ARG, "FBS_F32 is not available in this build");
   if (!(o->w0 > 0.0) || !isfinite(o->w0)) return fail(FBS_E_ARG, "w0 must be finite and > 0");
   if (o->step_out_max < 0 || o->step_out_max > (1 << 20))
     return fail(FBS_E_ARG, "step_out_max out of range");
@@ -202,24 +241,41 @@ DevPtrs carve(char* base, const Layout& o, int trace_beta) {
   return p;
 }
 
-// Copy a device [R][G] plane set to a host [G][R] array.
-int to_host_gene_major(fbs_handle* h, const double* dev, int R, double* host) {
+// Copy a device [R][G] plane set (double or float) to a host [G][R] double array.
+template <class T>
+int to_host_gene_major(fbs_handle* h, const T* dev, int R, double* host) {
   const int G = h->mc.G;
-  std::vector<double> tmp((size_t)R * G);
-  FBS_CUDA(cudaMemcpyAsync(tmp.data(), dev, tmp.size() * 8, cudaMemcpyDeviceToHost, h->s));
+  std::vector<T> tmp((size_t)R * G);
+  FBS_CUDA(cudaMemcpyAsync(tmp.data(), dev, tmp.size() * sizeof(T), cudaMemcpyDeviceToHost, h->s));
   FBS_CUDA(cudaStreamSynchronize(h->s));
   for (int r = 0; r < R; ++r)
-    for (int g = 0; g < G; ++g) host[(size_t)g * R + r] = tmp[(size_t)r * G + g];
+    for (int g = 0; g < G; ++g) host[(size_t)g * R + r] = (double)tmp[(size_t)r * G + g];
   return FBS_OK;
 }
 
-int from_host_gene_major(fbs_handle* h, double* dev, int R, const double* host) {
+template <class T>
+int from_host_gene_major(fbs_handle* h, T* dev, int R, const double* host) {
   const int G = h->mc.G;
-  std::vector<double> tmp((size_t)R * G);
+  std::vector<T> tmp((size_t)R * G);
   for (int r = 0; r < R; ++r)
-    for (int g = 0; g < G; ++g) tmp[(size_t)r * G + g] = host[(size_t)g * R + r];
-  FBS_CUDA(cudaMemcpyAsync(dev, tmp.data(), tmp.size() * 8, cudaMemcpyHostToDevice, h->s));
+    for (int g = 0; g < G; ++g) tmp[(size_t)r * G + g] = (T)host[(size_t)g * R + r];
+  FBS_CUDA(cudaMemcpyAsync(dev, tmp.data(), tmp.size() * sizeof(T), cudaMemcpyHostToDevice, h->s));
   FBS_CUDA(cudaStreamSynchronize(h->s));
+  return FBS_OK;
+}
+
+// A Kahan-compensated FP32 moment: planes value m and compensation c of
+// [R][G] each, starting at `base + plane_offset`; the moment is m - c.
+int kahan_to_host(fbs_handle* h, const float* base, int R, double* host) {
+  const int G = h->mc.G;
+  const size_t n = (size_t)R * G;
+  std::vector<float> tmp(2 * n);
+  FBS_CUDA(cudaMemcpyAsync(tmp.data(), base, 2 * n * 4, cudaMemcpyDeviceToHost, h->s));
+  FBS_CUDA(cudaStreamSynchronize(h->s));
+  for (int r = 0; r < R; ++r)
+    for (int g = 0; g < G; ++g)
+      host[(size_t)g * R + r] =
+          (double)tmp[(size_t)r * G + g] - (double)tmp[n + (size_t)r * G + g];
   return FBS_OK;
 }
 
@@ -229,8 +285,13 @@ int read_hyper(fbs_handle* h, Hyper* out) {
   return FBS_OK;
 }
 
+cudaError_t launch_gene_any(fbs_handle* h) {
+  return h->prec == FBS_F32 ? launch_gene_f32(h->mc, h->pf, h->block, h->s)
+                            : launch_gene(h->mc, h->p, h->block, h->s);
+}
+
 int sweep_direct(fbs_handle* h) {
-  FBS_CUDA(launch_gene(h->mc, h->p, h->block, h->s));
+  FBS_CUDA(launch_gene_any(h));
   FBS_CUDA(launch_hyper(h->mc, h->p, h->nblk, h->s));
   return FBS_OK;
 }
@@ -240,7 +301,7 @@ int ensure_graph(fbs_handle* h) {
   cudaGraph_t graph;
   FBS_CUDA(cudaStreamBeginCapture(h->s, cudaStreamCaptureModeThreadLocal));
   for (int i = 0; i < h->seg; ++i) {
-    if (launch_gene(h->mc, h->p, h->block, h->s) != cudaSuccess ||
+    if (launch_gene_any(h) != cudaSuccess ||
         launch_hyper(h->mc, h->p, h->nblk, h->s) != cudaSuccess) {
       cudaStreamEndCapture(h->s, &graph);
       if (graph) cudaGraphDestroy(graph);
@@ -284,7 +345,9 @@ int fbs_workspace_bytes(int N, int G, int L, const fbs_options* opt, size_t* byt
   if (!bytes) return fail(FBS_E_ARG, "bytes is NULL");
   const int block = block_of(o);
   const int nblk = (G + block - 1) / block;
-  *bytes = make_layout(N, G, L, nblk, o->trace_cap, o->trace_beta).total;
+  *bytes = o->precision == FBS_F32
+               ? make_layout_f32(N, G, L, nblk, o->trace_cap, o->trace_beta).total
+               : make_layout(N, G, L, nblk, o->trace_cap, o->trace_beta).total;
   return FBS_OK;
 }
 
@@ -380,7 +443,10 @@ int fbs_init(fbs_handle** out, const int32_t* y, int N, int G, int gene_major, c
   h->nblk = (G + h->block - 1) / h->block;
   h->seg = o->graph_segment > 0 ? o->graph_segment : 100;
   h->trace_cap = o->trace_cap;
+  h->prec = o->precision;
   h->lay = make_layout(N, G, L, h->nblk, o->trace_cap, mc.trace_beta);
+  h->lay32 = make_layout_f32(N, G, L, h->nblk, o->trace_cap, mc.trace_beta);
+  const size_t need = h->prec == FBS_F32 ? h->lay32.total : h->lay.total;
   h->user = (cudaStream_t)stream;
 
   auto bail = [&](int code, const std::string& msg) {
@@ -397,21 +463,57 @@ int fbs_init(fbs_handle** out, const int32_t* y, int N, int G, int gene_major, c
       (e = cudaEventCreateWithFlags(&h->ev_out, cudaEventDisableTiming)) != cudaSuccess)
     return bail(FBS_E_CUDA, std::string("stream/event creation: ") + cudaGetErrorString(e));
   if (workspace) {
-    if (workspace_bytes < h->lay.total) return bail(FBS_E_ARG, "workspace is too small");
+    if (workspace_bytes < need) return bail(FBS_E_ARG, "workspace is too small");
     h->ws = workspace;
   } else {
-    e = cudaMalloc(&h->ws, h->lay.total);
+    e = cudaMalloc(&h->ws, need);
     if (e != cudaSuccess) return bail(FBS_E_OOM, std::string("cudaMalloc: ") + cudaGetErrorString(e));
     h->own_ws = true;
   }
   char* base = (char*)(((uintptr_t)h->ws + 255) & ~(uintptr_t)255);
-  h->p = carve(base, h->lay, mc.trace_beta);
-  if ((e = prepare_gene_kernel(N, h->block)) != cudaSuccess)
-    return bail(FBS_E_CUDA, std::string("kernel attribute: ") + cudaGetErrorString(e));
+  int32_t* y_raw = nullptr;  // raw counts, in a moment plane that is zeroed afterwards
+  double* d_pinv = nullptr;
+  if (h->prec == FBS_F32) {
+    const LayoutF32& o32 = h->lay32;
+    memset(&h->p, 0, sizeof(h->p));
+    DevPtrsF32& f = h->pf;
+    f.y = (const int32_t*)(base + o32.y);
+    f.T = (const double*)(base + o32.T);
+    f.eps = (float*)(base + o32.eps);
+    f.w_eps = (float*)(base + o32.w_eps);
+    f.waux_eps = (float*)(base + o32.waux_eps);
+    f.mom_eps = (float*)(base + o32.mom_eps);
+    f.beta = (float*)(base + o32.beta);
+    f.w_beta = (float*)(base + o32.w_beta);
+    f.waux_beta = (float*)(base + o32.waux_beta);
+    f.mom_beta = (float*)(base + o32.mom_beta);
+    f.gam = (float*)(base + o32.gam);
+    f.mom_gam = (float*)(base + o32.mom_gam);
+    f.partial = (double*)(base + o32.partial);
+    f.hyp = (Hyper*)(base + o32.hyp);
+    f.trace_phi = (double*)(base + o32.trace_phi);
+    f.trace_beta = mc.trace_beta ? (double*)(base + o32.trace_beta) : nullptr;
+    f.counters = (unsigned long long*)(base + o32.counters);
+    // the fields the shared kernels and copies use
+    h->p.y = f.y;
+    h->p.T = f.T;
+    h->p.partial = f.partial;
+    h->p.hyp = f.hyp;
+    h->p.trace_phi = f.trace_phi;
+    h->p.trace_beta = f.trace_beta;
+    h->p.counters = f.counters;
+    y_raw = (int32_t*)f.mom_eps;
+    d_pinv = (double*)(base + o32.pinv);
+    if ((e = prepare_gene_kernel_f32(N, h->block)) != cudaSuccess)
+      return bail(FBS_E_CUDA, std::string("kernel attribute: ") + cudaGetErrorString(e));
+  } else {
+    h->p = carve(base, h->lay, mc.trace_beta);
+    y_raw = (int32_t*)h->p.q_eps;
+    d_pinv = (double*)(base + h->lay.pinv);
+    if ((e = prepare_gene_kernel(N, h->block)) != cudaSuccess)
+      return bail(FBS_E_CUDA, std::string("kernel attribute: ") + cudaGetErrorString(e));
+  }
 
-  // raw counts go to the eps-moment plane (free until the moments are zeroed)
-  int32_t* y_raw = (int32_t*)h->p.q_eps;
-  double* d_pinv = (double*)(base + h->lay.pinv);
   if (enter(h) != FBS_OK) return bail(FBS_E_CUDA, g_err);
   if ((e = cudaMemcpyAsync(y_raw, y, (size_t)N * G * sizeof(int32_t), cudaMemcpyHostToDevice,
                            h->s)) != cudaSuccess ||
@@ -419,10 +521,21 @@ int fbs_init(fbs_handle** out, const int32_t* y, int N, int G, int gene_major, c
           cudaSuccess ||
       (e = cudaMemsetAsync(h->p.counters, 0, FBS_NUM_COUNTERS * sizeof(unsigned long long),
                            h->s)) != cudaSuccess ||
-      (e = cudaMemsetAsync(h->p.hyp, 0, sizeof(Hyper), h->s)) != cudaSuccess ||
-      (e = launch_init(mc, h->p, y_raw, gene_major, d_pinv, o->w0, 1, o->trace_cap, h->s)) !=
-          cudaSuccess ||
-      (e = cudaStreamSynchronize(h->s)) != cudaSuccess)
+      (e = cudaMemsetAsync(h->p.hyp, 0, sizeof(Hyper), h->s)) != cudaSuccess)
+    return bail(FBS_E_CUDA, std::string("initialisation: ") + cudaGetErrorString(e));
+  if (h->prec == FBS_F32) {
+    if ((e = launch_init_run(h->p.hyp, o->trace_cap, h->s)) != cudaSuccess ||
+        (e = launch_init_f32(mc, h->pf, y_raw, gene_major, d_pinv, o->w0, 1, h->s)) !=
+            cudaSuccess ||
+        (e = launch_init_hyper(mc, h->p.hyp, nullptr, h->pf.beta, o->w0, 1, h->s)) !=
+            cudaSuccess)
+      return bail(FBS_E_CUDA, std::string("initialisation: ") + cudaGetErrorString(e));
+  } else {
+    if ((e = launch_init(mc, h->p, y_raw, gene_major, d_pinv, o->w0, 1, o->trace_cap, h->s)) !=
+        cudaSuccess)
+      return bail(FBS_E_CUDA, std::string("initialisation: ") + cudaGetErrorString(e));
+  }
+  if ((e = cudaStreamSynchronize(h->s)) != cudaSuccess)
     return bail(FBS_E_CUDA, std::string("initialisation: ") + cudaGetErrorString(e));
   if (leave(h) != FBS_OK) return bail(FBS_E_CUDA, g_err);
   *out = h;
@@ -472,12 +585,23 @@ int fbs_moments(fbs_handle* h, double* mean_eps, double* msq_eps, double* mean_b
   int rc = enter(h);
   if (rc) return rc;
   const int N = h->mc.N, L = h->mc.L, G = h->mc.G, P = h->mc.P;
-  if (mean_eps && (rc = to_host_gene_major(h, h->p.m_eps, N, mean_eps))) return rc;
-  if (msq_eps && (rc = to_host_gene_major(h, h->p.q_eps, N, msq_eps))) return rc;
-  if (mean_beta && (rc = to_host_gene_major(h, h->p.m_beta, L, mean_beta))) return rc;
-  if (msq_beta && (rc = to_host_gene_major(h, h->p.q_beta, L, msq_beta))) return rc;
-  if (mean_gam) FBS_CUDA(cudaMemcpyAsync(mean_gam, h->p.m_gam, (size_t)G * 8, cudaMemcpyDeviceToHost, h->s));
-  if (msq_gam) FBS_CUDA(cudaMemcpyAsync(msq_gam, h->p.q_gam, (size_t)G * 8, cudaMemcpyDeviceToHost, h->s));
+  if (h->prec == FBS_F32) {
+    const size_t NG = (size_t)N * G, LG = (size_t)L * G;
+    const DevPtrsF32& f = h->pf;
+    if (mean_eps && (rc = kahan_to_host(h, f.mom_eps, N, mean_eps))) return rc;
+    if (msq_eps && (rc = kahan_to_host(h, f.mom_eps + 2 * NG, N, msq_eps))) return rc;
+    if (mean_beta && (rc = kahan_to_host(h, f.mom_beta, L, mean_beta))) return rc;
+    if (msq_beta && (rc = kahan_to_host(h, f.mom_beta + 2 * LG, L, msq_beta))) return rc;
+    if (mean_gam && (rc = kahan_to_host(h, f.mom_gam, 1, mean_gam))) return rc;
+    if (msq_gam && (rc = kahan_to_host(h, f.mom_gam + 2 * (size_t)G, 1, msq_gam))) return rc;
+  } else {
+    if (mean_eps && (rc = to_host_gene_major(h, h->p.m_eps, N, mean_eps))) return rc;
+    if (msq_eps && (rc = to_host_gene_major(h, h->p.q_eps, N, msq_eps))) return rc;
+    if (mean_beta && (rc = to_host_gene_major(h, h->p.m_beta, L, mean_beta))) return rc;
+    if (msq_beta && (rc = to_host_gene_major(h, h->p.q_beta, L, msq_beta))) return rc;
+    if (mean_gam) FBS_CUDA(cudaMemcpyAsync(mean_gam, h->p.m_gam, (size_t)G * 8, cudaMemcpyDeviceToHost, h->s));
+    if (msq_gam) FBS_CUDA(cudaMemcpyAsync(msq_gam, h->p.q_gam, (size_t)G * 8, cudaMemcpyDeviceToHost, h->s));
+  }
   Hyper hy;
   if ((rc = read_hyper(h, &hy))) return rc;
   if (mean_phi) memcpy(mean_phi, hy.m_phi, (size_t)P * 8);
@@ -493,13 +617,24 @@ int fbs_get_state(fbs_handle* h, double* eps, double* beta, double* gam, double*
   int rc = enter(h);
   if (rc) return rc;
   const int N = h->mc.N, L = h->mc.L, G = h->mc.G, P = h->mc.P;
-  if (eps && (rc = to_host_gene_major(h, h->p.eps, N, eps))) return rc;
-  if (w_eps && (rc = to_host_gene_major(h, h->p.w_eps, N, w_eps))) return rc;
-  if (waux_eps && (rc = to_host_gene_major(h, h->p.waux_eps, N, waux_eps))) return rc;
-  if (beta && (rc = to_host_gene_major(h, h->p.beta, L, beta))) return rc;
-  if (w_beta && (rc = to_host_gene_major(h, h->p.w_beta, L, w_beta))) return rc;
-  if (waux_beta && (rc = to_host_gene_major(h, h->p.waux_beta, L, waux_beta))) return rc;
-  if (gam) FBS_CUDA(cudaMemcpyAsync(gam, h->p.gam, (size_t)G * 8, cudaMemcpyDeviceToHost, h->s));
+  if (h->prec == FBS_F32) {
+    const DevPtrsF32& f = h->pf;
+    if (eps && (rc = to_host_gene_major(h, (const float*)f.eps, N, eps))) return rc;
+    if (w_eps && (rc = to_host_gene_major(h, (const float*)f.w_eps, N, w_eps))) return rc;
+    if (waux_eps && (rc = to_host_gene_major(h, (const float*)f.waux_eps, N, waux_eps))) return rc;
+    if (beta && (rc = to_host_gene_major(h, (const float*)f.beta, L, beta))) return rc;
+    if (w_beta && (rc = to_host_gene_major(h, (const float*)f.w_beta, L, w_beta))) return rc;
+    if (waux_beta && (rc = to_host_gene_major(h, (const float*)f.waux_beta, L, waux_beta))) return rc;
+    if (gam && (rc = to_host_gene_major(h, (const float*)f.gam, 1, gam))) return rc;
+  } else {
+    if (eps && (rc = to_host_gene_major(h, (const double*)h->p.eps, N, eps))) return rc;
+    if (w_eps && (rc = to_host_gene_major(h, (const double*)h->p.w_eps, N, w_eps))) return rc;
+    if (waux_eps && (rc = to_host_gene_major(h, (const double*)h->p.waux_eps, N, waux_eps))) return rc;
+    if (beta && (rc = to_host_gene_major(h, (const double*)h->p.beta, L, beta))) return rc;
+    if (w_beta && (rc = to_host_gene_major(h, (const double*)h->p.w_beta, L, w_beta))) return rc;
+    if (waux_beta && (rc = to_host_gene_major(h, (const double*)h->p.waux_beta, L, waux_beta))) return rc;
+    if (gam) FBS_CUDA(cudaMemcpyAsync(gam, h->p.gam, (size_t)G * 8, cudaMemcpyDeviceToHost, h->s));
+  }
   Hyper hy;
   if ((rc = read_hyper(h, &hy))) return rc;
   if (phi) memcpy(phi, hy.phi, (size_t)P * 8);
@@ -518,17 +653,28 @@ int fbs_set_state(fbs_handle* h, const double* eps, const double* beta, const do
   int rc = enter(h);
   if (rc) return rc;
   const int N = h->mc.N, L = h->mc.L, G = h->mc.G, P = h->mc.P;
-  if (eps && (rc = from_host_gene_major(h, h->p.eps, N, eps))) return rc;
-  if (w_eps && (rc = from_host_gene_major(h, h->p.w_eps, N, w_eps))) return rc;
-  if (waux_eps && (rc = from_host_gene_major(h, h->p.waux_eps, N, waux_eps))) return rc;
-  if (beta && (rc = from_host_gene_major(h, h->p.beta, L, beta))) return rc;
-  if (w_beta && (rc = from_host_gene_major(h, h->p.w_beta, L, w_beta))) return rc;
-  if (waux_beta && (rc = from_host_gene_major(h, h->p.waux_beta, L, waux_beta))) return rc;
-  if (gam) {
-    FBS_CUDA(cudaMemcpyAsync(h->p.gam, gam, (size_t)G * 8, cudaMemcpyHostToDevice, h->s));
-    FBS_CUDA(cudaStreamSynchronize(h->s));
+  (void)G;
+  if (h->prec == FBS_F32) {
+    const DevPtrsF32& f = h->pf;
+    if (eps && (rc = from_host_gene_major(h, f.eps, N, eps))) return rc;
+    if (w_eps && (rc = from_host_gene_major(h, f.w_eps, N, w_eps))) return rc;
+    if (waux_eps && (rc = from_host_gene_major(h, f.waux_eps, N, waux_eps))) return rc;
+    if (beta && (rc = from_host_gene_major(h, f.beta, L, beta))) return rc;
+    if (w_beta && (rc = from_host_gene_major(h, f.w_beta, L, w_beta))) return rc;
+    if (waux_beta && (rc = from_host_gene_major(h, f.waux_beta, L, waux_beta))) return rc;
+    if (gam && (rc = from_host_gene_major(h, f.gam, 1, gam))) return rc;
+    FBS_CUDA(launch_zero_moments_f32(h->mc, h->pf, h->s));
+    FBS_CUDA(launch_init_hyper(h->mc, h->p.hyp, nullptr, f.beta, 0.0, 0, h->s));
+  } else {
+    if (eps && (rc = from_host_gene_major(h, h->p.eps, N, eps))) return rc;
+    if (w_eps && (rc = from_host_gene_major(h, h->p.w_eps, N, w_eps))) return rc;
+    if (waux_eps && (rc = from_host_gene_major(h, h->p.waux_eps, N, waux_eps))) return rc;
+    if (beta && (rc = from_host_gene_major(h, h->p.beta, L, beta))) return rc;
+    if (w_beta && (rc = from_host_gene_major(h, h->p.w_beta, L, w_beta))) return rc;
+    if (waux_beta && (rc = from_host_gene_major(h, h->p.waux_beta, L, waux_beta))) return rc;
+    if (gam && (rc = from_host_gene_major(h, h->p.gam, 1, gam))) return rc;
+    FBS_CUDA(launch_zero_moments(h->mc, h->p, h->s));
   }
-  FBS_CUDA(launch_zero_moments(h->mc, h->p, h->s));
   Hyper hy;
   if ((rc = read_hyper(h, &hy))) return rc;
   if (phi) memcpy(hy.phi, phi, (size_t)P * 8);
@@ -630,7 +776,7 @@ int fbs_profile(fbs_handle* h, int64_t n_iter, int64_t burnin, int64_t thin, dou
   cudaError_t e = cudaSuccess;
   for (int64_t i = 0; i < n_iter && e == cudaSuccess; ++i) {
     cudaEventRecord(ev[3 * i], h->s);
-    e = launch_gene(h->mc, h->p, h->block, h->s);
+    e = launch_gene_any(h);
     cudaEventRecord(ev[3 * i + 1], h->s);
     if (e == cudaSuccess) e = launch_hyper(h->mc, h->p, h->nblk, h->s);
     cudaEventRecord(ev[3 * i + 2], h->s);

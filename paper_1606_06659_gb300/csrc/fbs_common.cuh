@@ -88,6 +88,29 @@ struct DevPtrs {
   unsigned long long* counters;  // [FBS_NUM_COUNTERS]
 };
 
+// Device pointers of one chain in the FP32 form: per-gene state in FP32, each
+// running moment a Kahan-compensated FP32 pair (value m, compensation c; the
+// moment is m - c); partial sums, hyperparameters and traces in FP64.
+struct DevPtrsF32 {
+  const int32_t* y;   // [N][G]
+  const double* T;    // [L][G] (exact count sums, kept for fbs_count_sums)
+  float* eps;         // [N][G]
+  float* w_eps;
+  float* waux_eps;
+  float* beta;        // [L][G]
+  float* w_beta;
+  float* waux_beta;
+  float* gam;         // [G]
+  float* mom_eps;     // [4][N][G]: mean, mean compensation, mean square, its compensation
+  float* mom_beta;    // [4][L][G]
+  float* mom_gam;     // [4][G]
+  double* partial;    // [n_blocks][kNumPart]
+  Hyper* hyp;
+  double* trace_phi;  // [trace_cap][P]
+  double* trace_beta; // [trace_cap][L][G] or null
+  unsigned long long* counters;
+};
+
 // Flag bits in Hyper::flags.
 enum : unsigned int { kFlagNonfinite = 1u };
 

@@ -1,0 +1,504 @@
+// fbs_gene_f32.cu -- the per-gene kernel of the Gibbs sweep in its FP32 form
+// (Landau & Niemi, arXiv 1606.06659, Algorithm 1 steps 1, 2, 5 with Algorithm
+// 2), plus its set-up kernels.
+//
+// Slice evaluations run in FP32 on the log density relative to the start
+// point x0, Delta(x) = log f(x) - log f(x0), written so that no two large terms
+// cancel:
+//   eps:  Delta(x) = d (y - mu0) - mu0 (e^d - 1 - d) - d (d + 2 x0) / (2 gamma)
+//   beta: Delta(b) = sum_j [v_j d (Y_j - Q_j) - Q_j (e^{v_j d} - 1 - v_j d)]
+//                    - d (d + 2 (b0 - theta)) / (2 sigma^2)
+// with d = x - x0, mu0 = exp(h + x0 + X beta) the Poisson mean at x0, Y_j and
+// Q_j the counts and Poisson means summed over the samples whose X_nl is the
+// j-th distinct value v_j of column l.  Since Delta(x0) = 0, the slice level is
+// log U and no evaluation at x0 is needed.  Uniforms are 23-bit FP32 numbers,
+// four per Philox block.  The partial sums for the hyperparameter steps are
+// reduced exactly to FP64 (error-free FP32 pair sums within a warp, FP64
+// across warps and blocks), and the running moments are Kahan-compensated
+// FP32 pairs.
+#include <cuda_runtime.h>
+#include <math.h>
+#include <stdint.h>
+
+#include "fbs_common.cuh"
+#include "fbs_kernels.h"
+#include "fbs_rng.cuh"
+
+namespace fbs {
+
+// ---------------------------------------------------------------- FP32 random numbers
+
+// The uniforms of one random variable in the FP32 form: uniform k is word k%4 of
+// Philox block k/4, as ((w >> 9) + 1/2) / 2^23 (exact in FP32, inside (0,1)).
+struct Rng4 {
+  uint32_t key0, key1, index, sblk, iter, chain;
+  uint32_t cached;
+  uint4 w;
+
+  __device__ __forceinline__ Rng4(uint32_t seed_lo, uint32_t seed_hi, uint32_t chain_,
+                                  uint32_t stream, uint32_t index_, uint32_t iter_)
+      : key0(seed_lo), key1(seed_hi), index(index_), sblk(stream << 24), iter(iter_),
+        chain(chain_), cached(0xFFFFFFFFu), w(make_uint4(0, 0, 0, 0)) {}
+
+  __device__ __forceinline__ float u(uint32_t k) {
+    const uint32_t blk = k >> 2;
+    if (blk != cached) {
+      w = philox4x32_10(make_uint4(index, sblk | blk, iter, chain), key0, key1);
+      cached = blk;
+    }
+    const uint32_t j = k & 3u;
+    const uint32_t x = j == 0 ? w.x : (j == 1 ? w.y : (j == 2 ? w.z : w.w));
+    return __fmul_rn(__fadd_rn(__uint2float_rn(x >> 9), 0.5f), 0x1p-23f);
+  }
+};
+
+__device__ __forceinline__ float normal_bm_f(Rng4& r, uint32_t k0) {
+  const float u1 = r.u(k0), u2 = r.u(k0 + 1);
+  return sqrtf(-2.0f * __logf(u1)) * __cosf(6.2831853071795865f * u2);
+}
+
+// Gamma(shape, 1), Marsaglia & Tsang (2000), uniform layout as in the FP64 form.
+__device__ __forceinline__ float gamma_mt_f(float shape, Rng4& r, uint32_t k0, bool* capped) {
+  const float alpha = shape < 1.0f ? shape + 1.0f : shape;
+  const float dd = alpha - (1.0f / 3.0f);
+  const float cc = rsqrtf(9.0f * dd);
+  float boost = 1.0f;
+  if (shape < 1.0f) boost = __powf(r.u(k0 + 3), 1.0f / shape);
+  for (uint32_t j = 0; j < (uint32_t)kGammaAttempts; ++j) {
+    const float x = normal_bm_f(r, k0 + 4 * j);
+    float v = 1.0f + cc * x;
+    if (v <= 0.0f) continue;
+    v = v * v * v;
+    const float u = r.u(k0 + 4 * j + 2);
+    const float x2 = x * x;
+    if (u < 1.0f - 0.0331f * x2 * x2) return dd * v * boost;
+    if (__logf(u) < 0.5f * x2 + dd * (1.0f - v + __logf(v))) return dd * v * boost;
+  }
+  *capped = true;
+  return shape;
+}
+
+// e^z - 1 - z without cancellation: Taylor series to z^9 for |z| < 1/2 (relative
+// truncation error below 3e-9), expf otherwise.
+__device__ __forceinline__ float em1mx(float z) {
+  if (fabsf(z) < 0.5f) {
+    float p = 1.0f / 362880.0f;
+    p = fmaf(p, z, 1.0f / 40320.0f);
+    p = fmaf(p, z, 1.0f / 5040.0f);
+    p = fmaf(p, z, 1.0f / 720.0f);
+    p = fmaf(p, z, 1.0f / 120.0f);
+    p = fmaf(p, z, 1.0f / 24.0f);
+    p = fmaf(p, z, 1.0f / 6.0f);
+    p = fmaf(p, z, 0.5f);
+    return z * z * p;
+  }
+  return expf(z) - 1.0f - z;
+}
+
+// ---------------------------------------------------------------- densities
+
+struct EpsDensityF {
+  float D, mu0, x0, hg;  // D = y - mu0, hg = 1 / (2 gamma)
+  __device__ __forceinline__ float operator()(float x, float* aux) const {
+    const float d = x - x0;
+    const float e = em1mx(d);
+    *aux = mu0 + mu0 * (d + e);
+    return d * D - mu0 * e - d * (d + 2.0f * x0) * hg;
+  }
+};
+
+struct BetaDensityF {
+  float bt, hs;  // bt = b0 - theta, hs = 1 / (2 sigma^2)
+  float b0;
+  int ncls;
+  float Q[kMaxCls], D[kMaxCls], v[kMaxCls];
+  __device__ __forceinline__ float operator()(float b, float* aux) const {
+    const float d = b - b0;
+    float s = 0.0f;
+#pragma unroll
+    for (int j = 0; j < kMaxCls; ++j) {
+      if (j < ncls) {
+        const float z = v[j] * d;
+        s += z * D[j] - Q[j] * em1mx(z);
+      }
+    }
+    *aux = d;
+    return s - d * (d + 2.0f * bt) * hs;
+  }
+};
+
+struct SliceResultF {
+  float x, aux;
+  unsigned evals;
+  bool capped, nonfinite;
+};
+
+// Algorithm 2, steps 1-6, on Delta (Delta(x0) = 0): level log U_0, interval from
+// U_1, K_L from U_2, the j-th shrinkage proposal from U_{3+j}.
+template <class F>
+__device__ __forceinline__ SliceResultF slice_update_f(float x0, float aux0, float w, const F& f,
+                                                       Rng4& r, int K, int shrink_max) {
+  SliceResultF res;
+  res.evals = 0;
+  res.nonfinite = !(isfinite(x0) && isfinite(aux0));
+  const float logu = __logf(r.u(0));
+  const float v = __fmul_rn(w, r.u(1));
+  float lo = __fsub_rn(x0, v);
+  float hi = __fadd_rn(lo, w);
+  int KL = (int)__fmul_rn((float)(K + 1), r.u(2));
+  if (KL > K) KL = K;
+  const int KR = K - KL;
+  float aux;
+  for (int k = 0; k < KL; ++k) {
+    ++res.evals;
+    if (logu < f(lo, &aux)) lo = __fsub_rn(lo, w); else break;
+  }
+  for (int k = 0; k < KR; ++k) {
+    ++res.evals;
+    if (logu < f(hi, &aux)) hi = __fadd_rn(hi, w); else break;
+  }
+  for (int j = 0; j < shrink_max; ++j) {
+    const float xs = __fadd_rn(lo, __fmul_rn(__fsub_rn(hi, lo), r.u(3u + (uint32_t)j)));
+    ++res.evals;
+    if (logu < f(xs, &aux)) {
+      res.x = xs;
+      res.aux = aux;
+      res.capped = false;
+      return res;
+    }
+    if (xs > x0) hi = xs; else lo = xs;
+  }
+  res.x = x0;
+  res.aux = aux0;
+  res.capped = true;
+  return res;
+}
+
+__device__ __forceinline__ void tune_width_f(float& w, float& waux, long long it, float x_new,
+                                             float x_old, long long burnin, long long tune_start) {
+  if (it > burnin) return;
+  waux += (float)it * fabsf(x_new - x_old);
+  if (it > tune_start) {
+    const float wn = waux / (0.5f * (float)it * (float)(it + 1));
+    if (wn > 0.0f && isfinite(wn)) w = wn;
+  }
+}
+
+// Welford update of a Kahan-compensated FP32 pair (m, c) representing m - c.
+__device__ __forceinline__ void welford_kahan(float* base, size_t plane, size_t e, float x,
+                                              float inv_k) {
+  float m = base[e], c = base[plane + e];
+  float q = base[2 * plane + e], cq = base[3 * plane + e];
+  {
+    const float inc = (x - (m - c)) * inv_k;
+    const float y = inc - c;
+    const float t = m + y;
+    c = __fsub_rn(__fsub_rn(t, m), y);
+    m = t;
+  }
+  {
+    const float inc = (x * x - (q - cq)) * inv_k;
+    const float y = inc - cq;
+    const float t = q + y;
+    cq = __fsub_rn(__fsub_rn(t, q), y);
+    q = t;
+  }
+  base[e] = m;
+  base[plane + e] = c;
+  base[2 * plane + e] = q;
+  base[3 * plane + e] = cq;
+}
+
+// Error-free FP32 pair addition (Knuth's TwoSum).
+__device__ __forceinline__ void two_sum(float a, float b, float& s, float& e) {
+  s = __fadd_rn(a, b);
+  const float bp = __fsub_rn(s, a);
+  e = __fadd_rn(__fsub_rn(a, __fsub_rn(s, bp)), __fsub_rn(b, bp));
+}
+
+// ---------------------------------------------------------------- gene kernel (FP32)
+
+__global__ void __launch_bounds__(128) k_gene_f32(ModelConst mc, DevPtrsF32 p) {
+  extern __shared__ float smem_f[];  // mu[n][blockDim]; then FP64 warp sums
+  const int G = mc.G, N = mc.N, L = mc.L;
+  const Hyper* hy = p.hyp;
+  const long long it = hy->it + 1;
+  const uint32_t it32 = (uint32_t)it;
+  const long long burnin = hy->burnin, tune_start = hy->tune_start;
+  const bool mom = it > burnin;
+  const float inv_k = mom ? 1.0f / (float)(hy->n_mom + 1) : 0.0f;
+  const float nu = (float)hy->phi[0], tau = (float)hy->phi[1];
+  const bool trace_now = mom && mc.trace_beta && p.trace_beta != nullptr &&
+                         ((it - burnin) % hy->thin == 0) && hy->trace_rows < hy->trace_cap;
+  const long long trace_row = hy->trace_rows;
+  const size_t NG = (size_t)N * G, LG = (size_t)L * G;
+
+  float* mu = smem_f;
+  const int tid = threadIdx.x;
+  const int g = blockIdx.x * blockDim.x + tid;
+  const bool active = g < G;
+
+  float part[kNumPart];
+#pragma unroll
+  for (int i = 0; i < kNumPart; ++i) part[i] = 0.0f;
+  unsigned evals_e = 0, evals_b = 0, caps = 0, gcaps = 0, nonfin = 0;
+
+  if (active) {
+    float beta[kMaxL];
+#pragma unroll
+    for (int l = 0; l < kMaxL; ++l) beta[l] = l < L ? p.beta[(size_t)l * G + g] : 0.0f;
+    float gam = p.gam[g];
+    const float hg = 0.5f / gam;
+
+    // ---- step 1: eps_gn
+    float ss = 0.0f;
+    for (int n = 0; n < N; ++n) {
+      const size_t e = (size_t)n * G + g;
+      float A = (float)mc.h[n];
+#pragma unroll
+      for (int l = 0; l < kMaxL; ++l)
+        if (l < L) A += (float)mc.X[n * kMaxL + l] * beta[l];
+      const float x0 = p.eps[e];
+      const float mu0 = expf(A + x0);
+      const float yv = (float)p.y[e];
+      EpsDensityF f{yv - mu0, mu0, x0, hg};
+      Rng4 r(mc.seed_lo, mc.seed_hi, mc.chain, kStreamEps, (uint32_t)((size_t)g * N + n), it32);
+      float w = p.w_eps[e];
+      SliceResultF s = slice_update_f(x0, mu0, w, f, r, mc.K, mc.shrink_max);
+      evals_e += s.evals;
+      caps += s.capped;
+      nonfin += s.nonfinite;
+      mu[n * blockDim.x + tid] = s.aux;
+      p.eps[e] = s.x;
+      if (it <= burnin) {
+        float waux = p.waux_eps[e];
+        tune_width_f(w, waux, it, s.x, x0, burnin, tune_start);
+        p.w_eps[e] = w;
+        p.waux_eps[e] = waux;
+      }
+      ss += s.x * s.x;
+      if (mom && mc.moments_eps) welford_kahan(p.mom_eps, NG, e, s.x, inv_k);
+    }
+
+    // ---- step 2: gamma_g ~ IG((N + nu)/2, (sum eps^2 + nu tau)/2)
+    {
+      Rng4 r(mc.seed_lo, mc.seed_hi, mc.chain, kStreamGamma, (uint32_t)g, it32);
+      bool gcap = false;
+      const float shape = 0.5f * ((float)N + nu);
+      const float scale = 0.5f * (ss + nu * tau);
+      gam = scale / gamma_mt_f(shape, r, 0, &gcap);
+      gcaps += gcap;
+      p.gam[g] = gam;
+      if (mom) welford_kahan(p.mom_gam, (size_t)G, (size_t)g, gam, inv_k);
+      part[0] = __logf(gam);
+      part[1] = 1.0f / gam;
+    }
+
+    // ---- step 5: beta_gl, l = 1..L in order
+    for (int l = 0; l < L; ++l) {
+      const size_t e = (size_t)l * G + g;
+      const float theta = (float)hy->phi[2 + l];
+      const float sig2 = (float)hy->phi[2 + L + l];
+      BetaDensityF f;
+      f.b0 = beta[l];
+      f.bt = beta[l] - theta;
+      f.hs = 0.5f / sig2;
+      f.ncls = mc.ncls[l];
+      float Y[kMaxCls];
+#pragma unroll
+      for (int j = 0; j < kMaxCls; ++j) {
+        f.Q[j] = 0.0f;
+        Y[j] = 0.0f;
+        f.v[j] = (float)mc.cval[l][j];
+      }
+      for (int n = 0; n < N; ++n) {
+        const int c = mc.cls[l][n];
+        const float m = mu[n * blockDim.x + tid];
+        const float yv = (float)p.y[(size_t)n * G + g];
+#pragma unroll
+        for (int j = 0; j < kMaxCls; ++j)
+          if (j == c) {
+            f.Q[j] += m;
+            Y[j] += yv;
+          }
+      }
+#pragma unroll
+      for (int j = 0; j < kMaxCls; ++j) f.D[j] = Y[j] - f.Q[j];
+      Rng4 r(mc.seed_lo, mc.seed_hi, mc.chain, kStreamBeta, (uint32_t)((size_t)g * L + l), it32);
+      const float x0 = beta[l];
+      float w = p.w_beta[e];
+      SliceResultF s = slice_update_f(x0, 0.0f, w, f, r, mc.K, mc.shrink_max);
+      evals_b += s.evals;
+      caps += s.capped;
+      nonfin += s.nonfinite;
+      if (s.x != x0) {
+        const float d = s.x - x0;
+        float fac[kMaxCls];
+#pragma unroll
+        for (int j = 0; j < kMaxCls; ++j) {
+          const float z = f.v[j] * d;
+          fac[j] = 1.0f + (z + em1mx(z));
+        }
+        for (int n = 0; n < N; ++n) {
+          const int c = mc.cls[l][n];
+          float fc = 1.0f;
+#pragma unroll
+          for (int j = 0; j < kMaxCls; ++j)
+            if (j == c) fc = fac[j];
+          mu[n * blockDim.x + tid] *= fc;
+        }
+      }
+      beta[l] = s.x;
+      p.beta[e] = s.x;
+      if (it <= burnin) {
+        float waux = p.waux_beta[e];
+        tune_width_f(w, waux, it, s.x, x0, burnin, tune_start);
+        p.w_beta[e] = w;
+        p.waux_beta[e] = waux;
+      }
+      if (mom) welford_kahan(p.mom_beta, LG, e, s.x, inv_k);
+      if (trace_now) p.trace_beta[(size_t)trace_row * LG + e] = (double)s.x;
+      const float dv = s.x - theta;
+      part[2 + l] = dv;
+      part[2 + kMaxL + l] = dv * dv;
+    }
+  }
+
+  // ---- partial sums: error-free FP32 pair sums within the warp, FP64 beyond
+  const int lane = tid & 31, warp = tid >> 5, nwarp = blockDim.x >> 5;
+  double* red = reinterpret_cast<double*>(smem_f + (((size_t)N * blockDim.x + 1) & ~(size_t)1));
+#pragma unroll
+  for (int i = 0; i < kNumPart; ++i) {
+    float s = part[i], c = 0.0f;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+      const float so = __shfl_down_sync(0xffffffffu, s, o);
+      const float co = __shfl_down_sync(0xffffffffu, c, o);
+      float t, e;
+      two_sum(s, so, t, e);
+      s = t;
+      c = c + co + e;
+    }
+    if (lane == 0) red[warp * kNumPart + i] = (double)s + (double)c;
+  }
+  __syncthreads();
+  if (tid < kNumPart) {
+    double acc = 0.0;
+    for (int w = 0; w < nwarp; ++w) acc += red[w * kNumPart + tid];
+    p.partial[(size_t)blockIdx.x * kNumPart + tid] = acc;
+  }
+
+  // ---- counters
+  unsigned long long c4[4] = {evals_e, evals_b, caps, gcaps};
+#pragma unroll
+  for (int i = 0; i < 4; ++i) {
+    unsigned long long x = c4[i];
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) x += __shfl_down_sync(0xffffffffu, x, o);
+    c4[i] = x;
+  }
+  unsigned nf = nonfin;
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) nf += __shfl_down_sync(0xffffffffu, nf, o);
+  if (lane == 0) {
+    if (c4[0]) atomicAdd(&p.counters[FBS_CNT_EVALS_EPS], c4[0]);
+    if (c4[1]) atomicAdd(&p.counters[FBS_CNT_EVALS_BETA], c4[1]);
+    if (c4[2]) atomicAdd(&p.counters[FBS_CNT_SLICE_CAPS], c4[2]);
+    if (c4[3]) atomicAdd(&p.counters[FBS_CNT_GAMMA_CAPS], c4[3]);
+    if (nf) {
+      atomicAdd(&p.counters[FBS_CNT_NONFINITE], (unsigned long long)nf);
+      atomicOr(&p.hyp->flags, kFlagNonfinite);
+    }
+  }
+}
+
+// ---------------------------------------------------------------- set-up kernels (FP32)
+
+// Same starting values as the FP64 form, computed in FP64 and stored in FP32.
+__global__ void k_init_genes_f32(ModelConst mc, DevPtrsF32 p, const int32_t* y_in,
+                                 int gene_major, const double* __restrict__ pinv, double w0,
+                                 int set_state) {
+  const int G = mc.G, N = mc.N, L = mc.L;
+  for (int g = blockIdx.x * blockDim.x + threadIdx.x; g < G; g += gridDim.x * blockDim.x) {
+    double r[kMaxN];
+    double T[kMaxL];
+#pragma unroll
+    for (int l = 0; l < kMaxL; ++l) T[l] = 0.0;
+    for (int n = 0; n < N; ++n) {
+      const int32_t yv = gene_major ? y_in[(size_t)g * N + n] : y_in[(size_t)n * G + g];
+      const_cast<int32_t*>(p.y)[(size_t)n * G + g] = yv;
+      r[n] = log((double)yv + 1.0) - mc.h[n];
+#pragma unroll
+      for (int l = 0; l < kMaxL; ++l)
+        if (l < L) T[l] += (double)yv * mc.X[n * kMaxL + l];
+    }
+    for (int l = 0; l < L; ++l) {
+      const_cast<double*>(p.T)[(size_t)l * G + g] = T[l];
+      if (set_state) {
+        double s = 0.0;
+        for (int n = 0; n < N; ++n) s += pinv[l * kMaxN + n] * r[n];
+        p.beta[(size_t)l * G + g] = (float)s;
+        p.w_beta[(size_t)l * G + g] = (float)w0;
+        p.waux_beta[(size_t)l * G + g] = 0.0f;
+      }
+    }
+    if (set_state) {
+      for (int n = 0; n < N; ++n) {
+        p.eps[(size_t)n * G + g] = 0.0f;
+        p.w_eps[(size_t)n * G + g] = (float)w0;
+        p.waux_eps[(size_t)n * G + g] = 0.0f;
+      }
+      p.gam[g] = 1.0f;
+    }
+  }
+}
+
+__global__ void k_zero_moments_f32(ModelConst mc, DevPtrsF32 p) {
+  const size_t NG = (size_t)mc.N * mc.G, LG = (size_t)mc.L * mc.G, G = mc.G;
+  for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < 4 * NG;
+       i += (size_t)gridDim.x * blockDim.x) {
+    p.mom_eps[i] = 0.0f;
+    if (i < 4 * LG) p.mom_beta[i] = 0.0f;
+    if (i < 4 * G) p.mom_gam[i] = 0.0f;
+  }
+}
+
+cudaError_t prepare_gene_kernel_f32(int N, int block) {
+  const size_t smem = gene_smem_bytes_f32(N, block);
+  if (smem > 48 * 1024)
+    return cudaFuncSetAttribute(k_gene_f32, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                (int)smem);
+  return cudaSuccess;
+}
+
+size_t gene_smem_bytes_f32(int N, int block) {
+  return ((size_t)N * block + 2) * sizeof(float) + (size_t)(block / 32) * kNumPart * sizeof(double);
+}
+
+cudaError_t launch_gene_f32(const ModelConst& mc, const DevPtrsF32& p, int block,
+                            cudaStream_t s) {
+  const int nblk = (mc.G + block - 1) / block;
+  k_gene_f32<<<nblk, block, gene_smem_bytes_f32(mc.N, block), s>>>(mc, p);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_init_f32(const ModelConst& mc, const DevPtrsF32& p, const int32_t* y_in,
+                            int gene_major, const double* pinv, double w0, int set_state,
+                            cudaStream_t s) {
+  const int blk = 256;
+  const int grid = (mc.G + blk - 1) / blk;
+  k_init_genes_f32<<<grid, blk, 0, s>>>(mc, p, y_in, gene_major, pinv, w0, set_state);
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return e;
+  return launch_zero_moments_f32(mc, p, s);
+}
+
+cudaError_t launch_zero_moments_f32(const ModelConst& mc, const DevPtrsF32& p, cudaStream_t s) {
+  const size_t n = 4 * (size_t)mc.N * mc.G;
+  const int blk = 256;
+  const unsigned grid = (unsigned)((n + blk - 1) / blk);
+  k_zero_moments_f32<<<grid, blk, 0, s>>>(mc, p);
+  return cudaGetLastError();
+}
+
+}  // namespace fbs

@@ -482,11 +482,11 @@ __global__ void k_zero_moments(ModelConst mc, DevPtrs p) {
 // Default hyperparameters from the starting beta: theta_l the mean, sigma_l^2 the
 // variance clamped to [1e-6, s_l^2/4] (two passes, one block), nu = min(3, d/2),
 // tau = 1.
-__global__ void k_init_hyper(ModelConst mc, DevPtrs p, double w0, int set_state) {
+__global__ void k_init_hyper(ModelConst mc, Hyper* hy, const double* beta_d,
+                             const float* beta_f, double w0, int set_state) {
   __shared__ double red[1024 / 32][kMaxL];
   __shared__ double mean_s[kMaxL];
   const int G = mc.G, L = mc.L;
-  Hyper* hy = p.hyp;
   if (set_state) {
     for (int pass = 0; pass < 2; ++pass) {
       double acc[kMaxL];
@@ -496,7 +496,8 @@ __global__ void k_init_hyper(ModelConst mc, DevPtrs p, double w0, int set_state)
 #pragma unroll
         for (int l = 0; l < kMaxL; ++l) {
           if (l < L) {
-            const double b = p.beta[(size_t)l * G + g];
+            const size_t e = (size_t)l * G + g;
+            const double b = beta_d ? beta_d[e] : (double)beta_f[e];
             if (pass == 0) acc[l] += b;
             else {
               const double dv = b - mean_s[l];
@@ -637,7 +638,7 @@ cudaError_t launch_init(const ModelConst& mc, const DevPtrs& p, const int32_t* y
   k_zero_moments<<<grid, blk, 0, s>>>(mc, p);
   e = cudaGetLastError();
   if (e != cudaSuccess) return e;
-  k_init_hyper<<<1, 1024, 0, s>>>(mc, p, w0, set_state);
+  k_init_hyper<<<1, 1024, 0, s>>>(mc, p.hyp, p.beta, nullptr, w0, set_state);
   return cudaGetLastError();
 }
 
@@ -647,7 +648,18 @@ cudaError_t launch_zero_moments(const ModelConst& mc, const DevPtrs& p, cudaStre
   k_zero_moments<<<grid, blk, 0, s>>>(mc, p);
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return e;
-  k_init_hyper<<<1, 1024, 0, s>>>(mc, p, 0.0, 0);
+  k_init_hyper<<<1, 1024, 0, s>>>(mc, p.hyp, p.beta, nullptr, 0.0, 0);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_init_hyper(const ModelConst& mc, Hyper* hy, const double* beta_d,
+                              const float* beta_f, double w0, int set_state, cudaStream_t s) {
+  k_init_hyper<<<1, 1024, 0, s>>>(mc, hy, beta_d, beta_f, w0, set_state);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_init_run(Hyper* hy, long long trace_cap, cudaStream_t s) {
+  k_init_run<<<1, 32, 0, s>>>(hy, trace_cap);
   return cudaGetLastError();
 }
 

@@ -23,6 +23,18 @@ cudaError_t launch_init(const ModelConst& mc, const DevPtrs& p, const int32_t* y
                         int gene_major, const double* pinv, double w0, int set_state,
                         long long trace_cap, cudaStream_t s);
 cudaError_t launch_zero_moments(const ModelConst& mc, const DevPtrs& p, cudaStream_t s);
+cudaError_t launch_init_hyper(const ModelConst& mc, Hyper* hy, const double* beta_d,
+                              const float* beta_f, double w0, int set_state, cudaStream_t s);
+cudaError_t launch_init_run(Hyper* hy, long long trace_cap, cudaStream_t s);
+
+// FP32 form (fbs_gene_f32.cu)
+size_t gene_smem_bytes_f32(int N, int block);
+cudaError_t prepare_gene_kernel_f32(int N, int block);
+cudaError_t launch_gene_f32(const ModelConst& mc, const DevPtrsF32& p, int block, cudaStream_t s);
+cudaError_t launch_init_f32(const ModelConst& mc, const DevPtrsF32& p, const int32_t* y_in,
+                            int gene_major, const double* pinv, double w0, int set_state,
+                            cudaStream_t s);
+cudaError_t launch_zero_moments_f32(const ModelConst& mc, const DevPtrsF32& p, cudaStream_t s);
 cudaError_t launch_uniforms(uint64_t seed, uint32_t chain, uint32_t stream, uint32_t index0,
                             int n_index, uint32_t iter, uint32_t k0, int n_k, double* out,
                             cudaStream_t s);

@@ -49,7 +49,8 @@ def parse():
     ap.add_argument("--steps", type=int, default=10)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=("ours", "reference"), default="ours")
-    ap.add_argument("--precision", choices=("f64",), default="f64")
+    ap.add_argument("--precision", choices=("f64", "f32"), default="f64")
+    ap.add_argument("--block", type=int, default=0, help="threads per block of the gene kernel")
     ap.add_argument("--sweeps-per-step", type=int, default=100)
     ap.add_argument("--no-ess", action="store_true", help="skip the 20000-iteration ESS job")
     ap.add_argument("--no-cpu-baseline", action="store_true")
@@ -73,11 +74,15 @@ FP64_TRAFFIC_BYTES = 39.1e6   # dram read+write per launch, same ncu capture
 FP64_PEAK_TFLOPS = 152 * 2 * 2 * 2.07e9 / 1e12
 
 
-def bytes_per_gene(N, L):
-    """Algorithmic HBM bytes of one gene in one post-burn-in FP64 sweep of the
-    per-gene kernel: reads y (4N), eps, w_eps (8N each), beta, w_beta, T (8L each),
+def bytes_per_gene(N, L, precision="f64"):
+    """Algorithmic HBM bytes of one gene in one post-burn-in sweep of the per-gene
+    kernel.  FP64: reads y (4N), eps, w_eps (8N each), beta, w_beta, T (8L each),
     gamma (8); read+write of the eps/beta/gamma running mean and mean square
-    (32 per parameter); writes eps (8N), beta (8L), gamma (8)."""
+    (32 per parameter); writes eps (8N), beta (8L), gamma (8).  FP32: reads y
+    (4N), eps, w_eps (4N each), beta, w_beta (4L each), gamma (4); read+write of
+    four FP32 moment planes per parameter (32); writes eps (4N), beta (4L), gamma (4)."""
+    if precision == "f32":
+        return 48 * N + 44 * L + 40
     return 60 * N + 64 * L + 48
 
 
@@ -228,6 +233,7 @@ def main():
     N, G, L = spec["N"], spec["G"], spec["L"]
     S = args.sweeps_per_step
     seed = 20160621
+    prec = fbs.FBS_F32 if args.precision == "f32" else fbs.FBS_F64
     stream = torch.cuda.current_stream()
 
     def barrier():
@@ -247,7 +253,7 @@ def main():
         barrier()
         t0 = time.perf_counter()
         smp = fbs.Sampler(y_host, data["X"], data["h"], data["priors"], seed=seed, chain=rank,
-                          trace_cap=trace_rows, trace_beta=1)
+                          trace_cap=trace_rows, trace_beta=1, precision=prec, block=args.block)
         ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         ev0.record(stream)
         phi_reads = 0
@@ -273,7 +279,8 @@ def main():
         torch.cuda.empty_cache()
 
     # ---- device-timed throughput: W warm-up + K timed steps of S sweeps
-    smp = fbs.Sampler(data["y"], data["X"], data["h"], data["priors"], seed=seed + 1, chain=rank)
+    smp = fbs.Sampler(data["y"], data["X"], data["h"], data["priors"], seed=seed + 1, chain=rank,
+                      precision=prec, block=args.block)
     tb = args.tune_sweeps // 2
     smp.run(args.tune_sweeps, burnin=tb, thin=thin)   # tune the slice widths (burn-in)
     flush = torch.empty(L2_FLUSH_BYTES, dtype=torch.uint8, device="cuda")
@@ -306,23 +313,28 @@ def main():
 
     # ---- roofline of the dominant (per-gene) kernel: direct launches with
     #      CUDA events on its launching stream
-    ms_gene, ms_hyper = smp.profile(S, burnin=tb, thin=thin)
+    ms_k1, ms_k2, ms_hyper = smp.profile(S, burnin=tb, thin=thin)
+    ms_gene = ms_k1 + ms_k2
     peak, peak_kind = measured_peaks()
-    bpg = bytes_per_gene(N, L)
+    bpg = bytes_per_gene(N, L, args.precision)
     achieved = bpg * G / (ms_gene / 1e3) / 1e9
     evals = {k: (c1[k] - c0[k]) / (args.steps * S) for k in ("evals_eps", "evals_beta",
                                                                "evals_nu")}
     ev_launch = evals["evals_eps"] + evals["evals_beta"]
-    tflops = ev_launch * FP64_FLOP_PER_EVAL / (ms_gene / 1e3) / 1e12
-    roofline = {"bound": "alu", "achieved": tflops, "peak": FP64_PEAK_TFLOPS,
-                "unit": "TFLOP/s (FP64)", "frac": tflops / FP64_PEAK_TFLOPS,
-                "traffic": FP64_TRAFFIC_BYTES,
-                "kernel": "k_gene_f64", "kernel_ms": ms_gene, "hyper_kernel_ms": ms_hyper,
-                "flop_per_eval": FP64_FLOP_PER_EVAL, "evals_per_launch": ev_launch,
-                "peak_source": "152 SMs x 2 DFMA/clk x 2 flop x 2.07 GHz",
-                "hbm": {"achieved": achieved, "peak": peak, "unit": "GB/s",
-                        "frac": achieved / peak, "bytes_per_gene": bpg, "genes_per_launch": G,
-                        "peak_source": peak_kind}}
+    hbm = {"achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
+           "bytes_per_gene": bpg, "genes_per_launch": G, "peak_source": peak_kind}
+    if args.precision == "f64":
+        tflops = ev_launch * FP64_FLOP_PER_EVAL / (ms_gene / 1e3) / 1e12
+        roofline = {"bound": "alu", "achieved": tflops, "peak": FP64_PEAK_TFLOPS,
+                    "unit": "TFLOP/s (FP64)", "frac": tflops / FP64_PEAK_TFLOPS,
+                    "traffic": FP64_TRAFFIC_BYTES,
+                    "kernel": "k_gene_f64", "kernel_ms": ms_gene, "hyper_kernel_ms": ms_hyper,
+                    "flop_per_eval": FP64_FLOP_PER_EVAL, "evals_per_launch": ev_launch,
+                    "peak_source": "152 SMs x 2 DFMA/clk x 2 flop x 2.07 GHz", "hbm": hbm}
+    else:
+        roofline = dict(hbm, bound="hbm", traffic=None, kernel="k_eps_f32 + k_gb_f32",
+                        kernel_ms=ms_gene, eps_kernel_ms=ms_k1, gb_kernel_ms=ms_k2,
+                        hyper_kernel_ms=ms_hyper, evals_per_launch=ev_launch)
     smp.close()
 
     if rank != 0:
@@ -336,6 +348,9 @@ def main():
         "vs_baseline": None, "dtype": args.precision, "data": "synthetic",
         "config": {"workload": "RNA-seq Gibbs sweep N=16 G=40000 L=5 (paper design), "
                                "one chain per GPU",
+                   "form": "FP64" if args.precision == "f64" else
+                           "FP32 log densities; FP64 reductions and hyperparameters; "
+                           "Kahan-compensated FP32 moments",
                    "N": N, "G": G, "L": L, "sweeps_per_step": S,
                    "l2": "256 MiB write before every timed step; state (~40 MB) stays "
                          "L2-resident within a step",

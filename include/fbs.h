@@ -175,13 +175,13 @@ int fbs_count_sums(fbs_handle* h, int64_t* T);
 /* Counters (FBS_CNT_* slots, FBS_NUM_COUNTERS values) to a host array. */
 int fbs_counters(fbs_handle* h, int64_t* out);
 
-/* Runs n_iter iterations launching the two sweep kernels directly (no graph)
- * with CUDA events around each launch on the launching stream, and reports the
- * mean duration in milliseconds of the per-gene kernel (*ms_gene) and of the
- * hyperparameter kernel (*ms_hyper).  The chain advances as with fbs_run.
- * Synchronous. */
-int fbs_profile(fbs_handle* h, int64_t n_iter, int64_t burnin, int64_t thin, double* ms_gene,
-                double* ms_hyper);
+/* Runs n_iter iterations launching the sweep kernels one at a time (no
+ * graph, no overlap) with CUDA events around each launch on the launching
+ * stream, and writes the mean durations in milliseconds to ms[0..2]: FP64, the
+ * fused per-gene kernel, 0, the hyperparameter kernel; FP32, the eps kernel,
+ * the gamma/beta kernel, the hyperparameter kernel.  The chain advances as with
+ * fbs_run.  Synchronous. */
+int fbs_profile(fbs_handle* h, int64_t n_iter, int64_t burnin, int64_t thin, double* ms);
 
 /* Philox uniforms exactly as the sampler draws them: out[i*n_k + k] is uniform
  * k0+k of variable index0+i of `stream` at iteration `iter` of chain `chain`,

@@ -92,7 +92,7 @@ def load_library(path: str = LIB_PATH):
     lib.fbs_beta_ess.argtypes = [vp, _PD]
     lib.fbs_count_sums.argtypes = [vp, _PI64]
     lib.fbs_counters.argtypes = [vp, _PI64]
-    lib.fbs_profile.argtypes = [vp, i64, i64, i64, _PD, _PD]
+    lib.fbs_profile.argtypes = [vp, i64, i64, i64, _PD]
     lib.fbs_uniforms.argtypes = [u64, u32, u32, u32, i32, u32, u32, i32, _PD]
     lib.fbs_sweep_noalloc.argtypes = [C.POINTER(SweepArgs)]
     lib.fbs_free.argtypes = [vp]
@@ -234,10 +234,10 @@ class Sampler:
         _check(self.lib.fbs_sync(self.h))
 
     def profile(self, n_iter, burnin=0, thin=1):
-        a, b = C.c_double(), C.c_double()
-        _check(self.lib.fbs_profile(self.h, int(n_iter), int(burnin), int(thin), C.byref(a),
-                                    C.byref(b)))
-        return a.value, b.value
+        """Mean per-launch milliseconds: (eps or fused gene kernel, gamma/beta kernel, hyper)."""
+        ms = np.zeros(3)
+        _check(self.lib.fbs_profile(self.h, int(n_iter), int(burnin), int(thin), _pd(ms)))
+        return tuple(float(v) for v in ms)
 
     # --------------------------------------------------------------- state
     def get_state(self):

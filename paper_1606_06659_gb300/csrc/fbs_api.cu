@@ -78,7 +78,7 @@ Layout make_layout(int N, int G, int L, int nblk, long long trace_cap, int trace
 
 // FP32 form: per-gene state in FP32, four FP32 moment planes per parameter.
 struct LayoutF32 {
-  size_t y, T, eps, w_eps, waux_eps, mom_eps, beta, w_beta, waux_beta, mom_beta, gam, mom_gam;
+  size_t y, T, eps, w_eps, waux_eps, mom_eps, mu, beta, w_beta, waux_beta, mom_beta, gam, mom_gam;
   size_t partial, hyp, trace_phi, trace_beta, counters, pinv, total;
 };
 
@@ -97,6 +97,7 @@ LayoutF32 make_layout_f32(int N, int G, int L, int nblk, long long trace_cap, in
   o.w_eps = take(NG * 4);
   o.waux_eps = take(NG * 4);
   o.mom_eps = take(4 * NG * 4);
+  o.mu = take(NG * 4);
   o.beta = take(LG * 4);
   o.w_beta = take(LG * 4);
   o.waux_beta = take(LG * 4);
@@ -107,7 +108,7 @@ LayoutF32 make_layout_f32(int N, int G, int L, int nblk, long long trace_cap, in
   o.hyp = take(sizeof(Hyper));
   o.trace_phi = take((size_t)(trace_cap > 0 ? trace_cap : 1) * P * 8);
   o.trace_beta = trace_beta && trace_cap > 0 ? take((size_t)trace_cap * LG * 8) : 0;
-  o.counters = take(FBS_NUM_COUNTERS * sizeof(unsigned long long));
+  o.counters = take(kEpsCounterCopiesHost * FBS_NUM_COUNTERS * sizeof(unsigned long long));
   o.pinv = take((size_t)kMaxL * kMaxN * 8);
   o.total = at + 256;
   return o;
@@ -136,7 +137,9 @@ struct fbs_handle {
   bool own_ws = false;
   cudaStream_t user = nullptr;  // caller's stream (ordering only)
   cudaStream_t s = nullptr;     // handle's own stream (all work, graph capture)
+  cudaStream_t s2 = nullptr;    // hyperparameter branch of the FP32 graph
   cudaEvent_t ev_in = nullptr, ev_out = nullptr;
+  cudaEvent_t ev_g = nullptr, ev_h = nullptr;  // gamma/beta done, hyperparameters done
   cudaGraphExec_t seg_exec = nullptr;
   long long trace_cap = 0;
 };
@@ -285,28 +288,60 @@ int read_hyper(fbs_handle* h, Hyper* out) {
   return FBS_OK;
 }
 
-cudaError_t launch_gene_any(fbs_handle* h) {
-  return h->prec == FBS_F32 ? launch_gene_f32(h->mc, h->pf, h->block, h->s)
-                            : launch_gene(h->mc, h->p, h->block, h->s);
+// n_iter sweeps launched one kernel at a time on the handle's stream.
+int sweeps_direct(fbs_handle* h, int64_t n_iter) {
+  if (h->prec == FBS_F32) {
+    FBS_CUDA(launch_seg_begin(h->p.hyp, h->s));
+    for (int64_t i = 0; i < n_iter; ++i) {
+      FBS_CUDA(launch_eps_f32(h->mc, h->pf, (int)i, h->s));
+      FBS_CUDA(launch_gb_f32(h->mc, h->pf, h->block, (int)i, h->s));
+      FBS_CUDA(launch_hyper(h->mc, h->p, h->nblk, h->s));
+    }
+    return FBS_OK;
+  }
+  for (int64_t i = 0; i < n_iter; ++i) {
+    FBS_CUDA(launch_gene(h->mc, h->p, h->block, h->s));
+    FBS_CUDA(launch_hyper(h->mc, h->p, h->nblk, h->s));
+  }
+  return FBS_OK;
 }
 
-int sweep_direct(fbs_handle* h) {
-  FBS_CUDA(launch_gene_any(h));
-  FBS_CUDA(launch_hyper(h->mc, h->p, h->nblk, h->s));
-  return FBS_OK;
+// Enqueue one graph segment's work on the capturing stream.  In the FP32 form
+// the hyperparameter kernel of sweep i runs on a second stream, concurrently
+// with the eps kernel of sweep i+1 (whose conditionals involve no
+// hyperparameter); the gamma/beta kernel of sweep i+1 waits for both.
+cudaError_t capture_segment(fbs_handle* h) {
+  cudaError_t e = cudaSuccess;
+  if (h->prec == FBS_F32) {
+    if ((e = launch_seg_begin(h->p.hyp, h->s)) != cudaSuccess) return e;
+    for (int i = 0; i < h->seg; ++i) {
+      if ((e = launch_eps_f32(h->mc, h->pf, i, h->s)) != cudaSuccess) return e;
+      if (i > 0 && (e = cudaStreamWaitEvent(h->s, h->ev_h, 0)) != cudaSuccess) return e;
+      if ((e = launch_gb_f32(h->mc, h->pf, h->block, i, h->s)) != cudaSuccess) return e;
+      if ((e = cudaEventRecord(h->ev_g, h->s)) != cudaSuccess) return e;
+      if ((e = cudaStreamWaitEvent(h->s2, h->ev_g, 0)) != cudaSuccess) return e;
+      if ((e = launch_hyper(h->mc, h->p, h->nblk, h->s2)) != cudaSuccess) return e;
+      if ((e = cudaEventRecord(h->ev_h, h->s2)) != cudaSuccess) return e;
+    }
+    return cudaStreamWaitEvent(h->s, h->ev_h, 0);
+  }
+  for (int i = 0; i < h->seg; ++i) {
+    if ((e = launch_gene(h->mc, h->p, h->block, h->s)) != cudaSuccess) return e;
+    if ((e = launch_hyper(h->mc, h->p, h->nblk, h->s)) != cudaSuccess) return e;
+  }
+  return e;
 }
 
 int ensure_graph(fbs_handle* h) {
   if (h->seg_exec) return FBS_OK;
   cudaGraph_t graph;
   FBS_CUDA(cudaStreamBeginCapture(h->s, cudaStreamCaptureModeThreadLocal));
-  for (int i = 0; i < h->seg; ++i) {
-    if (launch_gene_any(h) != cudaSuccess ||
-        launch_hyper(h->mc, h->p, h->nblk, h->s) != cudaSuccess) {
-      cudaStreamEndCapture(h->s, &graph);
-      if (graph) cudaGraphDestroy(graph);
-      return fail(FBS_E_CUDA, "kernel launch failed during graph capture");
-    }
+  cudaError_t ce = capture_segment(h);
+  if (ce != cudaSuccess) {
+    graph = nullptr;
+    cudaStreamEndCapture(h->s, &graph);
+    if (graph) cudaGraphDestroy(graph);
+    return fail(FBS_E_CUDA, std::string("graph capture: ") + cudaGetErrorString(ce));
   }
   FBS_CUDA(cudaStreamEndCapture(h->s, &graph));
   cudaError_t e = cudaGraphInstantiate(&h->seg_exec, graph, 0);
@@ -409,6 +444,10 @@ int fbs_init(fbs_handle** out, const int32_t* y, int N, int G, int gene_major, c
     }
   }
   h->x_integral = integral;
+  for (int n = 0; n < N; ++n) {
+    mc.hf[n] = (float)mc.h[n];
+    for (int l = 0; l < L; ++l) mc.Xf[n * kMaxL + l] = (float)mc.X[n * kMaxL + l];
+  }
   for (int l = 0; l < L; ++l) {
     int nc = 0;
     for (int n = 0; n < N; ++n) {
@@ -425,6 +464,7 @@ int fbs_init(fbs_handle** out, const int32_t* y, int N, int G, int gene_major, c
           return fail(FBS_E_ARG, "a column of X has more than FBS_MAX_CLASSES distinct values");
         }
         mc.cval[l][nc] = v;
+        mc.cvalf[l][nc] = (float)v;
         mc.ckind[l][nc] = v == 1.0 ? kClsPlus : (v == -1.0 ? kClsMinus : kClsOther);
         ++nc;
       }
@@ -451,6 +491,9 @@ int fbs_init(fbs_handle** out, const int32_t* y, int N, int G, int gene_major, c
 
   auto bail = [&](int code, const std::string& msg) {
     if (h->s) cudaStreamDestroy(h->s);
+    if (h->s2) cudaStreamDestroy(h->s2);
+    if (h->ev_g) cudaEventDestroy(h->ev_g);
+    if (h->ev_h) cudaEventDestroy(h->ev_h);
     if (h->ev_in) cudaEventDestroy(h->ev_in);
     if (h->ev_out) cudaEventDestroy(h->ev_out);
     if (h->own_ws && h->ws) cudaFree(h->ws);
@@ -460,7 +503,10 @@ int fbs_init(fbs_handle** out, const int32_t* y, int N, int G, int gene_major, c
   cudaError_t e;
   if ((e = cudaStreamCreateWithFlags(&h->s, cudaStreamNonBlocking)) != cudaSuccess ||
       (e = cudaEventCreateWithFlags(&h->ev_in, cudaEventDisableTiming)) != cudaSuccess ||
-      (e = cudaEventCreateWithFlags(&h->ev_out, cudaEventDisableTiming)) != cudaSuccess)
+      (e = cudaEventCreateWithFlags(&h->ev_out, cudaEventDisableTiming)) != cudaSuccess ||
+      (e = cudaStreamCreateWithFlags(&h->s2, cudaStreamNonBlocking)) != cudaSuccess ||
+      (e = cudaEventCreateWithFlags(&h->ev_g, cudaEventDisableTiming)) != cudaSuccess ||
+      (e = cudaEventCreateWithFlags(&h->ev_h, cudaEventDisableTiming)) != cudaSuccess)
     return bail(FBS_E_CUDA, std::string("stream/event creation: ") + cudaGetErrorString(e));
   if (workspace) {
     if (workspace_bytes < need) return bail(FBS_E_ARG, "workspace is too small");
@@ -483,6 +529,7 @@ int fbs_init(fbs_handle** out, const int32_t* y, int N, int G, int gene_major, c
     f.w_eps = (float*)(base + o32.w_eps);
     f.waux_eps = (float*)(base + o32.waux_eps);
     f.mom_eps = (float*)(base + o32.mom_eps);
+    f.mu = (float*)(base + o32.mu);
     f.beta = (float*)(base + o32.beta);
     f.w_beta = (float*)(base + o32.w_beta);
     f.waux_beta = (float*)(base + o32.waux_beta);
@@ -519,7 +566,9 @@ int fbs_init(fbs_handle** out, const int32_t* y, int N, int G, int gene_major, c
                            h->s)) != cudaSuccess ||
       (e = cudaMemcpyAsync(d_pinv, pinv, sizeof(pinv), cudaMemcpyHostToDevice, h->s)) !=
           cudaSuccess ||
-      (e = cudaMemsetAsync(h->p.counters, 0, FBS_NUM_COUNTERS * sizeof(unsigned long long),
+      (e = cudaMemsetAsync(h->p.counters, 0,
+                           (h->prec == FBS_F32 ? kEpsCounterCopiesHost : 1) * FBS_NUM_COUNTERS *
+                               sizeof(unsigned long long),
                            h->s)) != cudaSuccess ||
       (e = cudaMemsetAsync(h->p.hyp, 0, sizeof(Hyper), h->s)) != cudaSuccess)
     return bail(FBS_E_CUDA, std::string("initialisation: ") + cudaGetErrorString(e));
@@ -559,8 +608,8 @@ int fbs_run(fbs_handle* h, int64_t n_iter, int64_t burnin, int64_t thin) {
       left -= h->seg;
     }
   }
-  for (; left > 0; --left) {
-    rc = sweep_direct(h);
+  if (left > 0) {
+    rc = sweeps_direct(h, left);
     if (rc) return rc;
   }
   return leave(h);
@@ -756,44 +805,51 @@ int fbs_counters(fbs_handle* h, int64_t* out) {
   if (!h || !out) return fail(FBS_E_ARG, "handle or out is NULL");
   int rc = enter(h);
   if (rc) return rc;
-  unsigned long long c[FBS_NUM_COUNTERS];
-  FBS_CUDA(cudaMemcpyAsync(c, h->p.counters, sizeof(c), cudaMemcpyDeviceToHost, h->s));
+  const int copies = h->prec == FBS_F32 ? kEpsCounterCopiesHost : 1;
+  std::vector<unsigned long long> c((size_t)copies * FBS_NUM_COUNTERS);
+  FBS_CUDA(cudaMemcpyAsync(c.data(), h->p.counters, c.size() * sizeof(unsigned long long),
+                           cudaMemcpyDeviceToHost, h->s));
   FBS_CUDA(cudaStreamSynchronize(h->s));
-  for (int i = 0; i < FBS_NUM_COUNTERS; ++i) out[i] = (int64_t)c[i];
+  for (int i = 0; i < FBS_NUM_COUNTERS; ++i) {
+    unsigned long long t = 0;
+    for (int k = 0; k < copies; ++k) t += c[(size_t)k * FBS_NUM_COUNTERS + i];
+    out[i] = (int64_t)t;
+  }
   return leave(h);
 }
 
-int fbs_profile(fbs_handle* h, int64_t n_iter, int64_t burnin, int64_t thin, double* ms_gene,
-                double* ms_hyper) {
-  if (!h) return fail(FBS_E_ARG, "handle is NULL");
+int fbs_profile(fbs_handle* h, int64_t n_iter, int64_t burnin, int64_t thin, double* ms) {
+  if (!h || !ms) return fail(FBS_E_ARG, "handle or ms is NULL");
   if (n_iter < 1 || burnin < 0 || thin < 1)
     return fail(FBS_E_ARG, "need n_iter >= 1, burnin >= 0, thin >= 1");
   int rc = enter(h);
   if (rc) return rc;
   FBS_CUDA(launch_set_run(h->p.hyp, burnin, burnin / 2, thin, h->s));
-  std::vector<cudaEvent_t> ev((size_t)3 * n_iter);
+  const bool f32 = h->prec == FBS_F32;
+  if (f32) FBS_CUDA(launch_seg_begin(h->p.hyp, h->s));
+  std::vector<cudaEvent_t> ev((size_t)4 * n_iter);
   for (auto& x : ev) FBS_CUDA(cudaEventCreate(&x));
   cudaError_t e = cudaSuccess;
   for (int64_t i = 0; i < n_iter && e == cudaSuccess; ++i) {
-    cudaEventRecord(ev[3 * i], h->s);
-    e = launch_gene_any(h);
-    cudaEventRecord(ev[3 * i + 1], h->s);
+    cudaEventRecord(ev[4 * i], h->s);
+    e = f32 ? launch_eps_f32(h->mc, h->pf, (int)i, h->s) : launch_gene(h->mc, h->p, h->block, h->s);
+    cudaEventRecord(ev[4 * i + 1], h->s);
+    if (e == cudaSuccess && f32) e = launch_gb_f32(h->mc, h->pf, h->block, (int)i, h->s);
+    cudaEventRecord(ev[4 * i + 2], h->s);
     if (e == cudaSuccess) e = launch_hyper(h->mc, h->p, h->nblk, h->s);
-    cudaEventRecord(ev[3 * i + 2], h->s);
+    cudaEventRecord(ev[4 * i + 3], h->s);
   }
   if (e == cudaSuccess) e = cudaStreamSynchronize(h->s);
-  double tg = 0.0, th = 0.0;
-  for (int64_t i = 0; i < n_iter && e == cudaSuccess; ++i) {
-    float a = 0.f, b = 0.f;
-    cudaEventElapsedTime(&a, ev[3 * i], ev[3 * i + 1]);
-    cudaEventElapsedTime(&b, ev[3 * i + 1], ev[3 * i + 2]);
-    tg += a;
-    th += b;
-  }
+  double t[3] = {0.0, 0.0, 0.0};
+  for (int64_t i = 0; i < n_iter && e == cudaSuccess; ++i)
+    for (int k = 0; k < 3; ++k) {
+      float a = 0.f;
+      cudaEventElapsedTime(&a, ev[4 * i + k], ev[4 * i + k + 1]);
+      t[k] += a;
+    }
   for (auto& x : ev) cudaEventDestroy(x);
   FBS_CUDA(e);
-  if (ms_gene) *ms_gene = tg / (double)n_iter;
-  if (ms_hyper) *ms_hyper = th / (double)n_iter;
+  for (int k = 0; k < 3; ++k) ms[k] = t[k] / (double)n_iter;
   return leave(h);
 }
 
@@ -818,6 +874,9 @@ void fbs_free(fbs_handle* h) {
   if (h->own_ws && h->ws) cudaFree(h->ws);
   if (h->ev_in) cudaEventDestroy(h->ev_in);
   if (h->ev_out) cudaEventDestroy(h->ev_out);
+  if (h->ev_g) cudaEventDestroy(h->ev_g);
+  if (h->ev_h) cudaEventDestroy(h->ev_h);
+  if (h->s2) cudaStreamDestroy(h->s2);
   if (h->s) cudaStreamDestroy(h->s);
   delete h;
 }

@@ -49,6 +49,10 @@ struct ModelConst {
   double cval[kMaxL][kMaxCls];
   int8_t ckind[kMaxL][kMaxCls];
   int8_t cls[kMaxL][kMaxN];
+  // FP32 copies for the FP32 form (conversions from FP64 run on the slow FP64 pipe)
+  float hf[kMaxN];
+  float Xf[kMaxN * kMaxL];
+  float cvalf[kMaxL][kMaxCls];
 };
 
 // Hyperparameters, run parameters and chain bookkeeping, in device memory.
@@ -62,6 +66,10 @@ struct Hyper {
   long long burnin, tune_start, thin, trace_cap;
   unsigned int flags;
   unsigned int pad;
+  // iteration count and moment count when the current run segment started
+  // (kernels that may run concurrently with the hyperparameter kernel derive
+  // their iteration from these instead of reading `it`)
+  long long seg_it, seg_nmom;
 };
 
 // Device pointers of one chain.
@@ -104,6 +112,7 @@ struct DevPtrsF32 {
   float* mom_eps;     // [4][N][G]: mean, mean compensation, mean square, its compensation
   float* mom_beta;    // [4][L][G]
   float* mom_gam;     // [4][G]
+  float* mu;          // [N][G] Poisson means at the new eps, from the eps kernel
   double* partial;    // [n_blocks][kNumPart]
   Hyper* hyp;
   double* trace_phi;  // [trace_cap][P]

@@ -216,13 +216,89 @@ __device__ __forceinline__ void two_sum(float a, float b, float& s, float& e) {
   e = __fadd_rn(__fsub_rn(a, __fsub_rn(s, bp)), __fsub_rn(b, bp));
 }
 
-// ---------------------------------------------------------------- gene kernel (FP32)
+// ---------------------------------------------------------------- sweep kernels (FP32)
 
-__global__ void __launch_bounds__(128) k_gene_f32(ModelConst mc, DevPtrsF32 p) {
+constexpr int kEpsCounterCopies = 32;  // spread the eps-kernel counter atomics
+
+// Warp sums of the counters, one atomic per warp into one of several copies.
+__device__ __forceinline__ void add_counters(unsigned long long* base, unsigned evals_e,
+                                             unsigned evals_b, unsigned caps, unsigned gcaps,
+                                             unsigned nonfin, unsigned* flags) {
+  unsigned v[5] = {evals_e, evals_b, caps, gcaps, nonfin};
+#pragma unroll
+  for (int i = 0; i < 5; ++i) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v[i] += __shfl_down_sync(0xffffffffu, v[i], o);
+  }
+  if ((threadIdx.x & 31) == 0) {
+    if (v[0]) atomicAdd(&base[FBS_CNT_EVALS_EPS], (unsigned long long)v[0]);
+    if (v[1]) atomicAdd(&base[FBS_CNT_EVALS_BETA], (unsigned long long)v[1]);
+    if (v[2]) atomicAdd(&base[FBS_CNT_SLICE_CAPS], (unsigned long long)v[2]);
+    if (v[3]) atomicAdd(&base[FBS_CNT_GAMMA_CAPS], (unsigned long long)v[3]);
+    if (v[4]) {
+      atomicAdd(&base[FBS_CNT_NONFINITE], (unsigned long long)v[4]);
+      atomicOr(flags, kFlagNonfinite);
+    }
+  }
+}
+
+// Step 1 of Algorithm 1 in the FP32 form: one thread per eps_gn (element e of
+// the [N][G] planes).  It reads beta_g and gamma_g of the previous iteration and
+// writes the new eps_gn and mu_gn = exp(h_n + eps_gn + X_n beta_g) for the
+// gamma/beta kernel.  It involves no hyperparameter, so within a captured
+// segment it runs concurrently with the hyperparameter kernel of the previous
+// iteration; its iteration number comes from the segment snapshot.
+__global__ void __launch_bounds__(256) k_eps_f32(ModelConst mc, DevPtrsF32 p, int seg_i) {
+  const int G = mc.G, N = mc.N, L = mc.L;
+  const Hyper* hy = p.hyp;
+  const long long it = hy->seg_it + seg_i + 1;
+  const long long burnin = hy->burnin, tune_start = hy->tune_start;
+  const bool mom = it > burnin;
+  long long before = (it - 1) - (hy->seg_it > burnin ? hy->seg_it : burnin);
+  if (before < 0) before = 0;
+  const float inv_k = mom ? 1.0f / (float)(hy->seg_nmom + before + 1) : 0.0f;
+  const size_t NG = (size_t)N * G;
+  const size_t e = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+  unsigned evals = 0, caps = 0, nonfin = 0;
+  if (e < NG) {
+    const int n = (int)(e / (size_t)G);
+    const int g = (int)(e - (size_t)n * G);
+    float A = mc.hf[n];
+#pragma unroll
+    for (int l = 0; l < kMaxL; ++l)
+      if (l < L) A += mc.Xf[n * kMaxL + l] * p.beta[(size_t)l * G + g];
+    const float hg = 0.5f / p.gam[g];
+    const float x0 = p.eps[e];
+    const float mu0 = expf(A + x0);
+    EpsDensityF f{(float)p.y[e] - mu0, mu0, x0, hg};
+    Rng4 r(mc.seed_lo, mc.seed_hi, mc.chain, kStreamEps, (uint32_t)((size_t)g * N + n),
+           (uint32_t)it);
+    float w = p.w_eps[e];
+    SliceResultF s = slice_update_f(x0, mu0, w, f, r, mc.K, mc.shrink_max);
+    evals = s.evals;
+    caps = s.capped;
+    nonfin = s.nonfinite;
+    p.mu[e] = s.aux;
+    p.eps[e] = s.x;
+    if (it <= burnin) {
+      float waux = p.waux_eps[e];
+      tune_width_f(w, waux, it, s.x, x0, burnin, tune_start);
+      p.w_eps[e] = w;
+      p.waux_eps[e] = waux;
+    }
+    if (mom && mc.moments_eps) welford_kahan(p.mom_eps, NG, e, s.x, inv_k);
+  }
+  add_counters(p.counters + (blockIdx.x % kEpsCounterCopies) * FBS_NUM_COUNTERS, evals, 0, caps,
+               0, nonfin, &p.hyp->flags);
+}
+
+// Steps 2 and 5 of Algorithm 1 in the FP32 form: one thread per gene.  The
+// hyperparameter kernel of the previous iteration has finished when it runs.
+__global__ void __launch_bounds__(128) k_gb_f32(ModelConst mc, DevPtrsF32 p, int seg_i) {
   extern __shared__ float smem_f[];  // mu[n][blockDim]; then FP64 warp sums
   const int G = mc.G, N = mc.N, L = mc.L;
   const Hyper* hy = p.hyp;
-  const long long it = hy->it + 1;
+  const long long it = hy->seg_it + seg_i + 1;
   const uint32_t it32 = (uint32_t)it;
   const long long burnin = hy->burnin, tune_start = hy->tune_start;
   const bool mom = it > burnin;
@@ -231,7 +307,7 @@ __global__ void __launch_bounds__(128) k_gene_f32(ModelConst mc, DevPtrsF32 p) {
   const bool trace_now = mom && mc.trace_beta && p.trace_beta != nullptr &&
                          ((it - burnin) % hy->thin == 0) && hy->trace_rows < hy->trace_cap;
   const long long trace_row = hy->trace_rows;
-  const size_t NG = (size_t)N * G, LG = (size_t)L * G;
+  const size_t LG = (size_t)L * G;
 
   float* mu = smem_f;
   const int tid = threadIdx.x;
@@ -241,43 +317,17 @@ __global__ void __launch_bounds__(128) k_gene_f32(ModelConst mc, DevPtrsF32 p) {
   float part[kNumPart];
 #pragma unroll
   for (int i = 0; i < kNumPart; ++i) part[i] = 0.0f;
-  unsigned evals_e = 0, evals_b = 0, caps = 0, gcaps = 0, nonfin = 0;
+  unsigned evals_b = 0, caps = 0, gcaps = 0, nonfin = 0;
 
   if (active) {
     float beta[kMaxL];
 #pragma unroll
     for (int l = 0; l < kMaxL; ++l) beta[l] = l < L ? p.beta[(size_t)l * G + g] : 0.0f;
-    float gam = p.gam[g];
-    const float hg = 0.5f / gam;
-
-    // ---- step 1: eps_gn
     float ss = 0.0f;
     for (int n = 0; n < N; ++n) {
-      const size_t e = (size_t)n * G + g;
-      float A = (float)mc.h[n];
-#pragma unroll
-      for (int l = 0; l < kMaxL; ++l)
-        if (l < L) A += (float)mc.X[n * kMaxL + l] * beta[l];
-      const float x0 = p.eps[e];
-      const float mu0 = expf(A + x0);
-      const float yv = (float)p.y[e];
-      EpsDensityF f{yv - mu0, mu0, x0, hg};
-      Rng4 r(mc.seed_lo, mc.seed_hi, mc.chain, kStreamEps, (uint32_t)((size_t)g * N + n), it32);
-      float w = p.w_eps[e];
-      SliceResultF s = slice_update_f(x0, mu0, w, f, r, mc.K, mc.shrink_max);
-      evals_e += s.evals;
-      caps += s.capped;
-      nonfin += s.nonfinite;
-      mu[n * blockDim.x + tid] = s.aux;
-      p.eps[e] = s.x;
-      if (it <= burnin) {
-        float waux = p.waux_eps[e];
-        tune_width_f(w, waux, it, s.x, x0, burnin, tune_start);
-        p.w_eps[e] = w;
-        p.waux_eps[e] = waux;
-      }
-      ss += s.x * s.x;
-      if (mom && mc.moments_eps) welford_kahan(p.mom_eps, NG, e, s.x, inv_k);
+      const float x = p.eps[(size_t)n * G + g];
+      ss += x * x;
+      mu[n * blockDim.x + tid] = p.mu[(size_t)n * G + g];
     }
 
     // ---- step 2: gamma_g ~ IG((N + nu)/2, (sum eps^2 + nu tau)/2)
@@ -286,7 +336,7 @@ __global__ void __launch_bounds__(128) k_gene_f32(ModelConst mc, DevPtrsF32 p) {
       bool gcap = false;
       const float shape = 0.5f * ((float)N + nu);
       const float scale = 0.5f * (ss + nu * tau);
-      gam = scale / gamma_mt_f(shape, r, 0, &gcap);
+      const float gam = scale / gamma_mt_f(shape, r, 0, &gcap);
       gcaps += gcap;
       p.gam[g] = gam;
       if (mom) welford_kahan(p.mom_gam, (size_t)G, (size_t)g, gam, inv_k);
@@ -309,7 +359,7 @@ __global__ void __launch_bounds__(128) k_gene_f32(ModelConst mc, DevPtrsF32 p) {
       for (int j = 0; j < kMaxCls; ++j) {
         f.Q[j] = 0.0f;
         Y[j] = 0.0f;
-        f.v[j] = (float)mc.cval[l][j];
+        f.v[j] = mc.cvalf[l][j];
       }
       for (int n = 0; n < N; ++n) {
         const int c = mc.cls[l][n];
@@ -387,28 +437,13 @@ __global__ void __launch_bounds__(128) k_gene_f32(ModelConst mc, DevPtrsF32 p) {
     for (int w = 0; w < nwarp; ++w) acc += red[w * kNumPart + tid];
     p.partial[(size_t)blockIdx.x * kNumPart + tid] = acc;
   }
+  add_counters(p.counters, 0, evals_b, caps, gcaps, nonfin, &p.hyp->flags);
+}
 
-  // ---- counters
-  unsigned long long c4[4] = {evals_e, evals_b, caps, gcaps};
-#pragma unroll
-  for (int i = 0; i < 4; ++i) {
-    unsigned long long x = c4[i];
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) x += __shfl_down_sync(0xffffffffu, x, o);
-    c4[i] = x;
-  }
-  unsigned nf = nonfin;
-#pragma unroll
-  for (int o = 16; o > 0; o >>= 1) nf += __shfl_down_sync(0xffffffffu, nf, o);
-  if (lane == 0) {
-    if (c4[0]) atomicAdd(&p.counters[FBS_CNT_EVALS_EPS], c4[0]);
-    if (c4[1]) atomicAdd(&p.counters[FBS_CNT_EVALS_BETA], c4[1]);
-    if (c4[2]) atomicAdd(&p.counters[FBS_CNT_SLICE_CAPS], c4[2]);
-    if (c4[3]) atomicAdd(&p.counters[FBS_CNT_GAMMA_CAPS], c4[3]);
-    if (nf) {
-      atomicAdd(&p.counters[FBS_CNT_NONFINITE], (unsigned long long)nf);
-      atomicOr(&p.hyp->flags, kFlagNonfinite);
-    }
+__global__ void k_seg_begin(Hyper* hy) {
+  if (threadIdx.x == 0 && blockIdx.x == 0) {
+    hy->seg_it = hy->it;
+    hy->seg_nmom = hy->n_mom;
   }
 }
 
@@ -466,7 +501,7 @@ __global__ void k_zero_moments_f32(ModelConst mc, DevPtrsF32 p) {
 cudaError_t prepare_gene_kernel_f32(int N, int block) {
   const size_t smem = gene_smem_bytes_f32(N, block);
   if (smem > 48 * 1024)
-    return cudaFuncSetAttribute(k_gene_f32, cudaFuncAttributeMaxDynamicSharedMemorySize,
+    return cudaFuncSetAttribute(k_gb_f32, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                 (int)smem);
   return cudaSuccess;
 }
@@ -475,10 +510,23 @@ size_t gene_smem_bytes_f32(int N, int block) {
   return ((size_t)N * block + 2) * sizeof(float) + (size_t)(block / 32) * kNumPart * sizeof(double);
 }
 
-cudaError_t launch_gene_f32(const ModelConst& mc, const DevPtrsF32& p, int block,
-                            cudaStream_t s) {
+cudaError_t launch_eps_f32(const ModelConst& mc, const DevPtrsF32& p, int seg_i,
+                           cudaStream_t s) {
+  const size_t n = (size_t)mc.N * mc.G;
+  const int blk = 256;
+  k_eps_f32<<<(unsigned)((n + blk - 1) / blk), blk, 0, s>>>(mc, p, seg_i);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_gb_f32(const ModelConst& mc, const DevPtrsF32& p, int block, int seg_i,
+                          cudaStream_t s) {
   const int nblk = (mc.G + block - 1) / block;
-  k_gene_f32<<<nblk, block, gene_smem_bytes_f32(mc.N, block), s>>>(mc, p);
+  k_gb_f32<<<nblk, block, gene_smem_bytes_f32(mc.N, block), s>>>(mc, p, seg_i);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_seg_begin(Hyper* hy, cudaStream_t s) {
+  k_seg_begin<<<1, 32, 0, s>>>(hy);
   return cudaGetLastError();
 }
 

@@ -30,7 +30,11 @@ cudaError_t launch_init_run(Hyper* hy, long long trace_cap, cudaStream_t s);
 // FP32 form (fbs_gene_f32.cu)
 size_t gene_smem_bytes_f32(int N, int block);
 cudaError_t prepare_gene_kernel_f32(int N, int block);
-cudaError_t launch_gene_f32(const ModelConst& mc, const DevPtrsF32& p, int block, cudaStream_t s);
+cudaError_t launch_eps_f32(const ModelConst& mc, const DevPtrsF32& p, int seg_i, cudaStream_t s);
+cudaError_t launch_gb_f32(const ModelConst& mc, const DevPtrsF32& p, int block, int seg_i,
+                          cudaStream_t s);
+cudaError_t launch_seg_begin(Hyper* hy, cudaStream_t s);
+constexpr int kEpsCounterCopiesHost = 32;  // copies of the counters the FP32 eps kernel uses
 cudaError_t launch_init_f32(const ModelConst& mc, const DevPtrsF32& p, const int32_t* y_in,
                             int gene_major, const double* pinv, double w0, int set_state,
                             cudaStream_t s);

@@ -2,10 +2,13 @@
 oracle: posterior means and mean squares of every hyperparameter and of the
 beta_gl must agree within 4 Monte Carlo standard errors.
 
-Different chains give different draws, so the comparison is statistical.  Each
-side runs 4 independent chains (the oracle in spawned worker processes); the
-MCSE comes from batch means over all chains (5 batches per chain), which also
-captures between-chain spread.  Every hyperparameter must be within 4 MCSE.
+Different chains give different draws, so the comparison is statistical.  The
+oracle runs 16 independent chains (spawned worker processes) and each GPU form
+8, all started from the parameter values the synthetic counts were drawn from.
+The MCSE of each side is the standard error of its chain means: the slowest
+hyperparameters (sigma^2_3, sigma^2_4 at N=16) have integrated autocorrelation
+times near 120 iterations, so shorter batches inside one chain would
+underestimate it, while each oracle chain spans more than 10 of them.  Every hyperparameter must be within 4 MCSE.
 For beta only parameters whose oracle effective sample size is at least 100
 are compared (below that the MCSE estimate itself is unreliable); among them at
 most 1% may exceed 4 MCSE (chance alone gives about 0.1%) and none 6 MCSE."""
@@ -19,8 +22,13 @@ from paper_1606_06659_gb300 import synthetic
 
 pytestmark = [pytest.mark.gpu, pytest.mark.slow]
 
-N_CHAINS = 4
-BATCHES_PER_CHAIN = 5
+N_ORACLE_CHAINS = 16
+N_GPU_CHAINS = 8
+
+
+def _truth_state(d):
+    t = d["truth"]
+    return {"eps": t["eps"], "beta": t["beta"], "gam": t["gam"], "phi": t["phi"]}
 
 
 def _oracle_chain(args):
@@ -30,42 +38,48 @@ def _oracle_chain(args):
     d = syn.make_config(cfg, G=G)
     ch = oracle.Chain(d["y"], d["X"], d["h"], d["priors"], seed=seed, chain=chain,
                       burnin=burnin, tune_start=burnin // 2).init_default()
+    ch.set_state(**_truth_state(d))
     tr = ch.run(iters, thin=1, trace_cap=iters, trace_beta=True)
     ess = np.array([oracle.ess(tr["beta"][:, g, l]) for g in range(tr["beta"].shape[1])
                     for l in range(tr["beta"].shape[2])]).reshape(tr["beta"].shape[1:])
     return tr["phi"], tr["beta"], ess
 
 
-def _batches(traces):
-    """Batch means of x and x^2 over all chains: arrays [n_batches, ...]."""
-    b1, b2 = [], []
-    for tr in traces:
-        n = tr.shape[0] - tr.shape[0] % BATCHES_PER_CHAIN
-        x = tr[:n].reshape(BATCHES_PER_CHAIN, n // BATCHES_PER_CHAIN, *tr.shape[1:])
-        b1.append(x.mean(1))
-        b2.append((x ** 2).mean(1))
-    return np.concatenate(b1), np.concatenate(b2)
-
-
 def _stats(traces):
-    b1, b2 = _batches(traces)
-    k = b1.shape[0]
-    return {"m1": b1.mean(0), "m1_se": b1.std(0, ddof=1) / np.sqrt(k),
-            "m2": b2.mean(0), "m2_se": b2.std(0, ddof=1) / np.sqrt(k)}
+    """Mean and mean square over chains with the standard errors of the chain means."""
+    m1 = np.stack([tr.mean(0) for tr in traces])
+    m2 = np.stack([(tr ** 2).mean(0) for tr in traces])
+    k = m1.shape[0]
+    return {"m1": m1.mean(0), "m1_se": m1.std(0, ddof=1) / np.sqrt(k),
+            "m2": m2.mean(0), "m2_se": m2.std(0, ddof=1) / np.sqrt(k)}
 
 
 @pytest.fixture(scope="module")
 def pool():
     ctx = mp.get_context("spawn")
-    with ctx.Pool(8) as p:
+    with ctx.Pool(N_ORACLE_CHAINS) as p:
         yield p
 
 
-@pytest.mark.parametrize("cfg,G,orc_iters,gpu_iters", [(0, 1000, 1800, 25000),
-                                                       (1, 1000, 1800, 25000)])
+def _compare(a, b, ok, label):
+    for m in ("m1", "m2"):
+        z = np.abs(a["phi"][m] - b["phi"][m]) / np.hypot(a["phi"][m + "_se"], b["phi"][m + "_se"])
+        assert np.all(z < 4.0), (label, "phi", m, z)
+        z = np.abs(a["beta"][m] - b["beta"][m]) / np.hypot(a["beta"][m + "_se"],
+                                                           b["beta"][m + "_se"])
+        z = z[ok]
+        assert np.mean(z > 4.0) <= 0.01, (label, "beta", m, np.mean(z > 4.0))
+        assert np.all(z < 6.0), (label, "beta", m, np.max(z))
+
+
+@pytest.mark.parametrize("cfg,G,orc_iters,gpu_iters", [(0, 1000, 2400, 12000),
+                                                       (1, 1000, 2400, 12000)])
 def test_long_runs_agree_with_oracle(pool, cfg, G, orc_iters, gpu_iters):
+    """FP64 GPU vs oracle, FP32 GPU vs oracle and FP32 GPU vs FP64 GPU.  The
+    oracle's burn-in (800 sweeps) spans more than 7 autocorrelation times of the
+    slowest hyperparameter."""
     orc_burn = orc_iters // 3
-    jobs = [(cfg, G, orc_iters, orc_burn, 101, c) for c in range(N_CHAINS)]
+    jobs = [(cfg, G, orc_iters, orc_burn, 101, c) for c in range(N_ORACLE_CHAINS)]
     res = pool.map(_oracle_chain, jobs)
     o_phi = _stats([r[0] for r in res])
     o_beta = _stats([r[1] for r in res])
@@ -74,13 +88,16 @@ def test_long_runs_agree_with_oracle(pool, cfg, G, orc_iters, gpu_iters):
     assert ok.mean() > 0.5
 
     d = synthetic.make_config(cfg, G=G)
-    gpu_burn, thin = gpu_iters // 5, 10
+    orc = {"phi": o_phi, "beta": o_beta}
+    gpu_burn, thin = gpu_iters // 6, 10
     rows = (gpu_iters - gpu_burn) // thin
+    runs = {}
     for precision in (fbs.FBS_F64, fbs.FBS_F32):
         phis, betas = [], []
-        for c in range(N_CHAINS):
+        for c in range(N_GPU_CHAINS):
             g = fbs.Sampler(d["y"], d["X"], d["h"], d["priors"], seed=202, chain=c,
                             precision=precision, trace_cap=rows, trace_beta=1)
+            g.set_state(it=0, **_truth_state(d))
             g.run(gpu_iters, burnin=gpu_burn, thin=thin)
             g.sync()
             tr = g.trace(beta=True)
@@ -90,11 +107,6 @@ def test_long_runs_agree_with_oracle(pool, cfg, G, orc_iters, gpu_iters):
             phis.append(tr["phi"])
             betas.append(tr["beta"])
             g.close()
-        g_phi, g_beta = _stats(phis), _stats(betas)
-        for m in ("m1", "m2"):
-            z = np.abs(g_phi[m] - o_phi[m]) / np.hypot(g_phi[m + "_se"], o_phi[m + "_se"])
-            assert np.all(z < 4.0), (precision, "phi", m, z)
-            z = np.abs(g_beta[m] - o_beta[m]) / np.hypot(g_beta[m + "_se"], o_beta[m + "_se"])
-            z = z[ok]
-            assert np.mean(z > 4.0) <= 0.01, (precision, "beta", m, np.mean(z > 4.0))
-            assert np.all(z < 6.0), (precision, "beta", m, np.max(z))
+        runs[precision] = {"phi": _stats(phis), "beta": _stats(betas)}
+        _compare(runs[precision], orc, ok, f"cfg {cfg} precision {precision} vs oracle")
+    _compare(runs[fbs.FBS_F32], runs[fbs.FBS_F64], ok, f"cfg {cfg} FP32 vs FP64")

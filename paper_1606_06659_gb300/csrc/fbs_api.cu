@@ -38,7 +38,7 @@ size_t align256(size_t x) { return (x + 255) & ~(size_t)255; }
 
 // Byte offsets of every device buffer inside one workspace.
 struct Layout {
-  size_t y, T, eps, w_eps, waux_eps, m_eps, q_eps, beta, w_beta, waux_beta, m_beta, q_beta;
+  size_t y, T, eps, w_eps, waux_eps, m_eps, q_eps, mu, beta, w_beta, waux_beta, m_beta, q_beta;
   size_t gam, m_gam, q_gam, partial, hyp, trace_phi, trace_beta, counters, pinv, total;
 };
 
@@ -58,6 +58,7 @@ Layout make_layout(int N, int G, int L, int nblk, long long trace_cap, int trace
   o.waux_eps = take(NG * 8);
   o.m_eps = take(NG * 8);
   o.q_eps = take(NG * 8);
+  o.mu = take(NG * 8);
   o.beta = take(LG * 8);
   o.w_beta = take(LG * 8);
   o.waux_beta = take(LG * 8);
@@ -70,7 +71,7 @@ Layout make_layout(int N, int G, int L, int nblk, long long trace_cap, int trace
   o.hyp = take(sizeof(Hyper));
   o.trace_phi = take((size_t)(trace_cap > 0 ? trace_cap : 1) * P * 8);
   o.trace_beta = trace_beta && trace_cap > 0 ? take((size_t)trace_cap * LG * 8) : 0;
-  o.counters = take(FBS_NUM_COUNTERS * sizeof(unsigned long long));
+  o.counters = take(kCounterCopies * FBS_NUM_COUNTERS * sizeof(unsigned long long));
   o.pinv = take((size_t)kMaxL * kMaxN * 8);
   o.total = at + 256;  // slack for aligning an unaligned base
   return o;
@@ -228,6 +229,7 @@ DevPtrs carve(char* base, const Layout& o, int trace_beta) {
   p.waux_eps = (double*)(base + o.waux_eps);
   p.m_eps = (double*)(base + o.m_eps);
   p.q_eps = (double*)(base + o.q_eps);
+  p.mu = (double*)(base + o.mu);
   p.beta = (double*)(base + o.beta);
   p.w_beta = (double*)(base + o.w_beta);
   p.waux_beta = (double*)(base + o.waux_beta);
@@ -299,8 +301,10 @@ int sweeps_direct(fbs_handle* h, int64_t n_iter) {
     }
     return FBS_OK;
   }
+  FBS_CUDA(launch_seg_begin(h->p.hyp, h->s));
   for (int64_t i = 0; i < n_iter; ++i) {
-    FBS_CUDA(launch_gene(h->mc, h->p, h->block, h->s));
+    FBS_CUDA(launch_eps_f64(h->mc, h->p, (int)i, h->s));
+    FBS_CUDA(launch_gb_f64(h->mc, h->p, h->block, (int)i, h->s));
     FBS_CUDA(launch_hyper(h->mc, h->p, h->nblk, h->s));
   }
   return FBS_OK;
@@ -312,24 +316,21 @@ int sweeps_direct(fbs_handle* h, int64_t n_iter) {
 // hyperparameter); the gamma/beta kernel of sweep i+1 waits for both.
 cudaError_t capture_segment(fbs_handle* h) {
   cudaError_t e = cudaSuccess;
-  if (h->prec == FBS_F32) {
-    if ((e = launch_seg_begin(h->p.hyp, h->s)) != cudaSuccess) return e;
-    for (int i = 0; i < h->seg; ++i) {
-      if ((e = launch_eps_f32(h->mc, h->pf, i, h->s)) != cudaSuccess) return e;
-      if (i > 0 && (e = cudaStreamWaitEvent(h->s, h->ev_h, 0)) != cudaSuccess) return e;
-      if ((e = launch_gb_f32(h->mc, h->pf, h->block, i, h->s)) != cudaSuccess) return e;
-      if ((e = cudaEventRecord(h->ev_g, h->s)) != cudaSuccess) return e;
-      if ((e = cudaStreamWaitEvent(h->s2, h->ev_g, 0)) != cudaSuccess) return e;
-      if ((e = launch_hyper(h->mc, h->p, h->nblk, h->s2)) != cudaSuccess) return e;
-      if ((e = cudaEventRecord(h->ev_h, h->s2)) != cudaSuccess) return e;
-    }
-    return cudaStreamWaitEvent(h->s, h->ev_h, 0);
-  }
+  const bool f32 = h->prec == FBS_F32;
+  if ((e = launch_seg_begin(h->p.hyp, h->s)) != cudaSuccess) return e;
   for (int i = 0; i < h->seg; ++i) {
-    if ((e = launch_gene(h->mc, h->p, h->block, h->s)) != cudaSuccess) return e;
-    if ((e = launch_hyper(h->mc, h->p, h->nblk, h->s)) != cudaSuccess) return e;
+    e = f32 ? launch_eps_f32(h->mc, h->pf, i, h->s) : launch_eps_f64(h->mc, h->p, i, h->s);
+    if (e != cudaSuccess) return e;
+    if (i > 0 && (e = cudaStreamWaitEvent(h->s, h->ev_h, 0)) != cudaSuccess) return e;
+    e = f32 ? launch_gb_f32(h->mc, h->pf, h->block, i, h->s)
+            : launch_gb_f64(h->mc, h->p, h->block, i, h->s);
+    if (e != cudaSuccess) return e;
+    if ((e = cudaEventRecord(h->ev_g, h->s)) != cudaSuccess) return e;
+    if ((e = cudaStreamWaitEvent(h->s2, h->ev_g, 0)) != cudaSuccess) return e;
+    if ((e = launch_hyper(h->mc, h->p, h->nblk, h->s2)) != cudaSuccess) return e;
+    if ((e = cudaEventRecord(h->ev_h, h->s2)) != cudaSuccess) return e;
   }
-  return e;
+  return cudaStreamWaitEvent(h->s, h->ev_h, 0);
 }
 
 int ensure_graph(fbs_handle* h) {
@@ -567,7 +568,7 @@ int fbs_init(fbs_handle** out, const int32_t* y, int N, int G, int gene_major, c
       (e = cudaMemcpyAsync(d_pinv, pinv, sizeof(pinv), cudaMemcpyHostToDevice, h->s)) !=
           cudaSuccess ||
       (e = cudaMemsetAsync(h->p.counters, 0,
-                           (h->prec == FBS_F32 ? kEpsCounterCopiesHost : 1) * FBS_NUM_COUNTERS *
+                           kCounterCopies * FBS_NUM_COUNTERS *
                                sizeof(unsigned long long),
                            h->s)) != cudaSuccess ||
       (e = cudaMemsetAsync(h->p.hyp, 0, sizeof(Hyper), h->s)) != cudaSuccess)
@@ -805,7 +806,7 @@ int fbs_counters(fbs_handle* h, int64_t* out) {
   if (!h || !out) return fail(FBS_E_ARG, "handle or out is NULL");
   int rc = enter(h);
   if (rc) return rc;
-  const int copies = h->prec == FBS_F32 ? kEpsCounterCopiesHost : 1;
+  const int copies = kCounterCopies;
   std::vector<unsigned long long> c((size_t)copies * FBS_NUM_COUNTERS);
   FBS_CUDA(cudaMemcpyAsync(c.data(), h->p.counters, c.size() * sizeof(unsigned long long),
                            cudaMemcpyDeviceToHost, h->s));
@@ -826,15 +827,17 @@ int fbs_profile(fbs_handle* h, int64_t n_iter, int64_t burnin, int64_t thin, dou
   if (rc) return rc;
   FBS_CUDA(launch_set_run(h->p.hyp, burnin, burnin / 2, thin, h->s));
   const bool f32 = h->prec == FBS_F32;
-  if (f32) FBS_CUDA(launch_seg_begin(h->p.hyp, h->s));
+  FBS_CUDA(launch_seg_begin(h->p.hyp, h->s));
   std::vector<cudaEvent_t> ev((size_t)4 * n_iter);
   for (auto& x : ev) FBS_CUDA(cudaEventCreate(&x));
   cudaError_t e = cudaSuccess;
   for (int64_t i = 0; i < n_iter && e == cudaSuccess; ++i) {
     cudaEventRecord(ev[4 * i], h->s);
-    e = f32 ? launch_eps_f32(h->mc, h->pf, (int)i, h->s) : launch_gene(h->mc, h->p, h->block, h->s);
+    e = f32 ? launch_eps_f32(h->mc, h->pf, (int)i, h->s) : launch_eps_f64(h->mc, h->p, (int)i, h->s);
     cudaEventRecord(ev[4 * i + 1], h->s);
-    if (e == cudaSuccess && f32) e = launch_gb_f32(h->mc, h->pf, h->block, (int)i, h->s);
+    if (e == cudaSuccess)
+      e = f32 ? launch_gb_f32(h->mc, h->pf, h->block, (int)i, h->s)
+              : launch_gb_f64(h->mc, h->p, h->block, (int)i, h->s);
     cudaEventRecord(ev[4 * i + 2], h->s);
     if (e == cudaSuccess) e = launch_hyper(h->mc, h->p, h->nblk, h->s);
     cudaEventRecord(ev[4 * i + 3], h->s);

@@ -17,6 +17,7 @@ constexpr int kMaxL = FBS_MAX_L;
 constexpr int kMaxP = 2 * FBS_MAX_L + 2;     // nu, tau, theta[L], sigma2[L]
 constexpr int kMaxCls = FBS_MAX_CLASSES;
 constexpr int kNumPart = 2 + 2 * FBS_MAX_L;  // S1, S2, B1'[L], B2'[L]
+constexpr int kCounterCopies = 32;  // the eps kernels spread their counter atomics
 
 // RNG stream identifiers: one per kind of random variable.
 enum : uint32_t {
@@ -93,7 +94,8 @@ struct DevPtrs {
   Hyper* hyp;
   double* trace_phi;  // [trace_cap][P]
   double* trace_beta; // [trace_cap][L][G] or null
-  unsigned long long* counters;  // [FBS_NUM_COUNTERS]
+  unsigned long long* counters;  // [copies][FBS_NUM_COUNTERS]
+  double* mu;         // [N][G] Poisson means at the new eps (split sweep kernels)
 };
 
 // Device pointers of one chain in the FP32 form: per-gene state in FP32, each

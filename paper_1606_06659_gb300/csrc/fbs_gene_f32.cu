@@ -218,7 +218,6 @@ __device__ __forceinline__ void two_sum(float a, float b, float& s, float& e) {
 
 // ---------------------------------------------------------------- sweep kernels (FP32)
 
-constexpr int kEpsCounterCopies = 32;  // spread the eps-kernel counter atomics
 
 // Warp sums of the counters, one atomic per warp into one of several copies.
 __device__ __forceinline__ void add_counters(unsigned long long* base, unsigned evals_e,
@@ -288,14 +287,14 @@ __global__ void __launch_bounds__(256) k_eps_f32(ModelConst mc, DevPtrsF32 p, in
     }
     if (mom && mc.moments_eps) welford_kahan(p.mom_eps, NG, e, s.x, inv_k);
   }
-  add_counters(p.counters + (blockIdx.x % kEpsCounterCopies) * FBS_NUM_COUNTERS, evals, 0, caps,
+  add_counters(p.counters + (blockIdx.x % kCounterCopies) * FBS_NUM_COUNTERS, evals, 0, caps,
                0, nonfin, &p.hyp->flags);
 }
 
 // Steps 2 and 5 of Algorithm 1 in the FP32 form: one thread per gene.  The
 // hyperparameter kernel of the previous iteration has finished when it runs.
 __global__ void __launch_bounds__(128) k_gb_f32(ModelConst mc, DevPtrsF32 p, int seg_i) {
-  extern __shared__ float smem_f[];  // mu[n][blockDim]; then FP64 warp sums
+  extern __shared__ float smem_f[];  // mu[n][blockDim], y[n][blockDim]; then FP64 warp sums
   const int G = mc.G, N = mc.N, L = mc.L;
   const Hyper* hy = p.hyp;
   const long long it = hy->seg_it + seg_i + 1;
@@ -310,6 +309,7 @@ __global__ void __launch_bounds__(128) k_gb_f32(ModelConst mc, DevPtrsF32 p, int
   const size_t LG = (size_t)L * G;
 
   float* mu = smem_f;
+  float* ys = smem_f + (size_t)N * blockDim.x;
   const int tid = threadIdx.x;
   const int g = blockIdx.x * blockDim.x + tid;
   const bool active = g < G;
@@ -324,10 +324,13 @@ __global__ void __launch_bounds__(128) k_gb_f32(ModelConst mc, DevPtrsF32 p, int
 #pragma unroll
     for (int l = 0; l < kMaxL; ++l) beta[l] = l < L ? p.beta[(size_t)l * G + g] : 0.0f;
     float ss = 0.0f;
+#pragma unroll 4
     for (int n = 0; n < N; ++n) {
-      const float x = p.eps[(size_t)n * G + g];
+      const size_t e = (size_t)n * G + g;
+      const float x = p.eps[e];
       ss += x * x;
-      mu[n * blockDim.x + tid] = p.mu[(size_t)n * G + g];
+      mu[n * blockDim.x + tid] = p.mu[e];
+      ys[n * blockDim.x + tid] = (float)p.y[e];
     }
 
     // ---- step 2: gamma_g ~ IG((N + nu)/2, (sum eps^2 + nu tau)/2)
@@ -364,7 +367,7 @@ __global__ void __launch_bounds__(128) k_gb_f32(ModelConst mc, DevPtrsF32 p, int
       for (int n = 0; n < N; ++n) {
         const int c = mc.cls[l][n];
         const float m = mu[n * blockDim.x + tid];
-        const float yv = (float)p.y[(size_t)n * G + g];
+        const float yv = ys[n * blockDim.x + tid];
 #pragma unroll
         for (int j = 0; j < kMaxCls; ++j)
           if (j == c) {
@@ -416,7 +419,7 @@ __global__ void __launch_bounds__(128) k_gb_f32(ModelConst mc, DevPtrsF32 p, int
 
   // ---- partial sums: error-free FP32 pair sums within the warp, FP64 beyond
   const int lane = tid & 31, warp = tid >> 5, nwarp = blockDim.x >> 5;
-  double* red = reinterpret_cast<double*>(smem_f + (((size_t)N * blockDim.x + 1) & ~(size_t)1));
+  double* red = reinterpret_cast<double*>(smem_f + ((2 * (size_t)N * blockDim.x + 1) & ~(size_t)1));
 #pragma unroll
   for (int i = 0; i < kNumPart; ++i) {
     float s = part[i], c = 0.0f;
@@ -507,7 +510,8 @@ cudaError_t prepare_gene_kernel_f32(int N, int block) {
 }
 
 size_t gene_smem_bytes_f32(int N, int block) {
-  return ((size_t)N * block + 2) * sizeof(float) + (size_t)(block / 32) * kNumPart * sizeof(double);
+  return (2 * (size_t)N * block + 2) * sizeof(float) +
+         (size_t)(block / 32) * kNumPart * sizeof(double);
 }
 
 cudaError_t launch_eps_f32(const ModelConst& mc, const DevPtrsF32& p, int seg_i,

@@ -271,6 +271,216 @@ __global__ void __launch_bounds__(128) k_gene_f64(ModelConst mc, DevPtrs p) {
   }
 }
 
+// ---------------------------------------------------------------- split sweep kernels (FP64)
+//
+// The same arithmetic as k_gene_f64 split in two launches so that every SM gets
+// work at any G and the hyperparameter kernel of sweep m can run concurrently
+// with the eps kernel of sweep m+1 (the eps conditionals involve no
+// hyperparameter).  k_gene_f64 remains for fbs_sweep_noalloc.
+
+__device__ __forceinline__ void add_counters_u(unsigned long long* base, unsigned evals_e,
+                                               unsigned evals_b, unsigned caps, unsigned gcaps,
+                                               unsigned nonfin, unsigned* flags) {
+  unsigned v[5] = {evals_e, evals_b, caps, gcaps, nonfin};
+#pragma unroll
+  for (int i = 0; i < 5; ++i) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v[i] += __shfl_down_sync(0xffffffffu, v[i], o);
+  }
+  if ((threadIdx.x & 31) == 0) {
+    if (v[0]) atomicAdd(&base[FBS_CNT_EVALS_EPS], (unsigned long long)v[0]);
+    if (v[1]) atomicAdd(&base[FBS_CNT_EVALS_BETA], (unsigned long long)v[1]);
+    if (v[2]) atomicAdd(&base[FBS_CNT_SLICE_CAPS], (unsigned long long)v[2]);
+    if (v[3]) atomicAdd(&base[FBS_CNT_GAMMA_CAPS], (unsigned long long)v[3]);
+    if (v[4]) {
+      atomicAdd(&base[FBS_CNT_NONFINITE], (unsigned long long)v[4]);
+      atomicOr(flags, kFlagNonfinite);
+    }
+  }
+}
+
+// Step 1: one thread per eps_gn (element e = n*G + g of the [N][G] planes).
+__global__ void __launch_bounds__(256) k_eps_f64(ModelConst mc, DevPtrs p, int seg_i) {
+  const int G = mc.G, N = mc.N, L = mc.L;
+  const Hyper* hy = p.hyp;
+  const long long it = hy->seg_it + seg_i + 1;
+  const long long burnin = hy->burnin, tune_start = hy->tune_start;
+  const bool mom = it > burnin;
+  long long before = (it - 1) - (hy->seg_it > burnin ? hy->seg_it : burnin);
+  if (before < 0) before = 0;
+  const double inv_k = mom ? 1.0 / (double)(hy->seg_nmom + before + 1) : 0.0;
+  const size_t NG = (size_t)N * G;
+  const size_t e = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+  unsigned evals = 0, caps = 0, nonfin = 0;
+  if (e < NG) {
+    const int n = (int)(e / (size_t)G);
+    const int g = (int)(e - (size_t)n * G);
+    double A = mc.h[n];
+#pragma unroll
+    for (int l = 0; l < kMaxL; ++l)
+      if (l < L) A += mc.X[n * kMaxL + l] * p.beta[(size_t)l * G + g];
+    EpsDensity f{(double)p.y[e], A, 0.5 / p.gam[g]};
+    Rng r(mc.seed_lo, mc.seed_hi, mc.chain, kStreamEps, (uint32_t)((size_t)g * N + n),
+          (uint32_t)it);
+    const double x0 = p.eps[e];
+    double w = p.w_eps[e];
+    SliceResult s = slice_update(x0, w, f, r, mc.K, mc.shrink_max);
+    evals = s.evals;
+    caps = s.capped;
+    nonfin = s.nonfinite;
+    p.mu[e] = s.aux;
+    p.eps[e] = s.x;
+    if (it <= burnin) {
+      double waux = p.waux_eps[e];
+      tune_width(w, waux, it, s.x, x0, burnin, tune_start);
+      p.w_eps[e] = w;
+      p.waux_eps[e] = waux;
+    }
+    if (mom && mc.moments_eps) {
+      const double m = p.m_eps[e], q = p.q_eps[e];
+      p.m_eps[e] = m + (s.x - m) * inv_k;
+      p.q_eps[e] = q + (s.x * s.x - q) * inv_k;
+    }
+  }
+  add_counters_u(p.counters + (blockIdx.x % kCounterCopies) * FBS_NUM_COUNTERS, evals, 0, caps,
+                 0, nonfin, &p.hyp->flags);
+}
+
+// Steps 2 and 5: one thread per gene, after the eps kernel of this sweep and the
+// hyperparameter kernel of the previous one.
+__global__ void __launch_bounds__(128) k_gb_f64(ModelConst mc, DevPtrs p, int seg_i) {
+  extern __shared__ double smem_dyn[];  // mu[n][blockDim] then reduction scratch
+  const int G = mc.G, N = mc.N, L = mc.L;
+  const Hyper* hy = p.hyp;
+  const long long it = hy->seg_it + seg_i + 1;
+  const uint32_t it32 = (uint32_t)it;
+  const long long burnin = hy->burnin, tune_start = hy->tune_start;
+  const bool mom = it > burnin;
+  const double inv_k = mom ? 1.0 / (double)(hy->n_mom + 1) : 0.0;
+  const double nu = hy->phi[0], tau = hy->phi[1];
+  const bool trace_now = mom && mc.trace_beta && p.trace_beta != nullptr &&
+                         ((it - burnin) % hy->thin == 0) && hy->trace_rows < hy->trace_cap;
+  const long long trace_row = hy->trace_rows;
+
+  double* mu = smem_dyn;
+  const int tid = threadIdx.x;
+  const int g = blockIdx.x * blockDim.x + tid;
+  const bool active = g < G;
+
+  double part[kNumPart];
+#pragma unroll
+  for (int i = 0; i < kNumPart; ++i) part[i] = 0.0;
+  unsigned evals_b = 0, caps = 0, gcaps = 0, nonfin = 0;
+
+  if (active) {
+    double beta[kMaxL];
+#pragma unroll
+    for (int l = 0; l < kMaxL; ++l) beta[l] = l < L ? p.beta[(size_t)l * G + g] : 0.0;
+    double ss = 0.0;
+#pragma unroll 4
+    for (int n = 0; n < N; ++n) {
+      const size_t e = (size_t)n * G + g;
+      const double x = p.eps[e];
+      ss += x * x;
+      mu[n * blockDim.x + tid] = p.mu[e];
+    }
+
+    // ---- step 2: gamma_g ~ IG((N + nu)/2, (sum eps^2 + nu tau)/2)
+    {
+      Rng r(mc.seed_lo, mc.seed_hi, mc.chain, kStreamGamma, (uint32_t)g, it32);
+      bool gcap = false;
+      const double shape = 0.5 * ((double)N + nu);
+      const double scale = 0.5 * (ss + nu * tau);
+      const double gam = scale / gamma_mt(shape, r, 0, &gcap);
+      gcaps += gcap;
+      p.gam[g] = gam;
+      if (mom) {
+        const double m = p.m_gam[g], q = p.q_gam[g];
+        p.m_gam[g] = m + (gam - m) * inv_k;
+        p.q_gam[g] = q + (gam * gam - q) * inv_k;
+      }
+      part[0] = log(gam);
+      part[1] = 1.0 / gam;
+    }
+
+    // ---- step 5: beta_gl, l = 1..L in order
+    for (int l = 0; l < L; ++l) {
+      const size_t e = (size_t)l * G + g;
+      const double theta = hy->phi[2 + l];
+      const double sig2 = hy->phi[2 + L + l];
+      BetaDensity f;
+      f.T = p.T[e];
+      f.b0 = beta[l];
+      f.theta = theta;
+      f.hs = 0.5 / sig2;
+      f.ncls = mc.ncls[l];
+#pragma unroll
+      for (int j = 0; j < kMaxCls; ++j) {
+        f.Q[j] = 0.0;
+        f.v[j] = mc.cval[l][j];
+        f.kind[j] = mc.ckind[l][j];
+      }
+      for (int n = 0; n < N; ++n) {
+        const int c = mc.cls[l][n];
+        const double m = mu[n * blockDim.x + tid];
+#pragma unroll
+        for (int j = 0; j < kMaxCls; ++j)
+          if (j == c) f.Q[j] += m;
+      }
+      Rng r(mc.seed_lo, mc.seed_hi, mc.chain, kStreamBeta, (uint32_t)((size_t)g * L + l), it32);
+      const double x0 = beta[l];
+      double w = p.w_beta[e];
+      SliceResult s = slice_update(x0, w, f, r, mc.K, mc.shrink_max);
+      evals_b += s.evals;
+      caps += s.capped;
+      nonfin += s.nonfinite;
+      if (s.x != x0) {
+        const double dlt = s.x - x0;
+        double ej[kMaxCls];
+        const double z = exp(dlt);
+#pragma unroll
+        for (int j = 0; j < kMaxCls; ++j) {
+          ej[j] = 1.0;
+          if (j < f.ncls) {
+            if (f.kind[j] == kClsPlus) ej[j] = z;
+            else if (f.kind[j] == kClsMinus) ej[j] = 1.0 / z;
+            else ej[j] = exp(f.v[j] * dlt);
+          }
+        }
+        for (int n = 0; n < N; ++n) {
+          const int c = mc.cls[l][n];
+          double fac = 1.0;
+#pragma unroll
+          for (int j = 0; j < kMaxCls; ++j)
+            if (j == c) fac = ej[j];
+          mu[n * blockDim.x + tid] *= fac;
+        }
+      }
+      beta[l] = s.x;
+      p.beta[e] = s.x;
+      if (it <= burnin) {
+        double waux = p.waux_beta[e];
+        tune_width(w, waux, it, s.x, x0, burnin, tune_start);
+        p.w_beta[e] = w;
+        p.waux_beta[e] = waux;
+      }
+      if (mom) {
+        const double m = p.m_beta[e], q = p.q_beta[e];
+        p.m_beta[e] = m + (s.x - m) * inv_k;
+        p.q_beta[e] = q + (s.x * s.x - q) * inv_k;
+      }
+      if (trace_now) p.trace_beta[(size_t)trace_row * L * G + e] = s.x;
+      const double dv = s.x - theta;
+      part[2 + l] = dv;
+      part[2 + kMaxL + l] = dv * dv;
+    }
+  }
+
+  double* red = smem_dyn + (size_t)N * blockDim.x;
+  block_sum_to<kNumPart>(part, p.partial + (size_t)blockIdx.x * kNumPart, red);
+  add_counters_u(p.counters, 0, evals_b, caps, gcaps, nonfin, &p.hyp->flags);
+}
+
 // ---------------------------------------------------------------- hyper kernel
 
 // log f(nu | ...) = -G lgamma(nu/2) + (G nu/2) log(nu tau/2) - (nu/2)(S1 + tau S2) on
@@ -614,10 +824,28 @@ cudaError_t launch_hyper(const ModelConst& mc, const DevPtrs& p, int nblk, cudaS
 
 cudaError_t prepare_gene_kernel(int N, int block) {
   const size_t smem = gene_smem_bytes(N, block);
-  if (smem > 48 * 1024)
-    return cudaFuncSetAttribute(k_gene_f64, cudaFuncAttributeMaxDynamicSharedMemorySize,
+  if (smem > 48 * 1024) {
+    cudaError_t e = cudaFuncSetAttribute(k_gene_f64, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         (int)smem);
+    if (e != cudaSuccess) return e;
+    return cudaFuncSetAttribute(k_gb_f64, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                 (int)smem);
+  }
   return cudaSuccess;
+}
+
+cudaError_t launch_eps_f64(const ModelConst& mc, const DevPtrs& p, int seg_i, cudaStream_t s) {
+  const size_t n = (size_t)mc.N * mc.G;
+  const int blk = 256;
+  k_eps_f64<<<(unsigned)((n + blk - 1) / blk), blk, 0, s>>>(mc, p, seg_i);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_gb_f64(const ModelConst& mc, const DevPtrs& p, int block, int seg_i,
+                          cudaStream_t s) {
+  const int nblk = (mc.G + block - 1) / block;
+  k_gb_f64<<<nblk, block, gene_smem_bytes(mc.N, block), s>>>(mc, p, seg_i);
+  return cudaGetLastError();
 }
 
 cudaError_t launch_set_run(Hyper* hy, long long burnin, long long tune_start, long long thin,

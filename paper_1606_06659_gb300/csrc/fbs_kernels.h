@@ -17,6 +17,9 @@ size_t gene_smem_bytes(int N, int block);
 cudaError_t prepare_gene_kernel(int N, int block);
 cudaError_t launch_gene(const ModelConst& mc, const DevPtrs& p, int block, cudaStream_t s);
 cudaError_t launch_hyper(const ModelConst& mc, const DevPtrs& p, int nblk, cudaStream_t s);
+cudaError_t launch_eps_f64(const ModelConst& mc, const DevPtrs& p, int seg_i, cudaStream_t s);
+cudaError_t launch_gb_f64(const ModelConst& mc, const DevPtrs& p, int block, int seg_i,
+                          cudaStream_t s);
 cudaError_t launch_set_run(Hyper* hy, long long burnin, long long tune_start, long long thin,
                            cudaStream_t s);
 cudaError_t launch_init(const ModelConst& mc, const DevPtrs& p, const int32_t* y_in,
@@ -34,7 +37,7 @@ cudaError_t launch_eps_f32(const ModelConst& mc, const DevPtrsF32& p, int seg_i,
 cudaError_t launch_gb_f32(const ModelConst& mc, const DevPtrsF32& p, int block, int seg_i,
                           cudaStream_t s);
 cudaError_t launch_seg_begin(Hyper* hy, cudaStream_t s);
-constexpr int kEpsCounterCopiesHost = 32;  // copies of the counters the FP32 eps kernel uses
+constexpr int kEpsCounterCopiesHost = kCounterCopies;
 cudaError_t launch_init_f32(const ModelConst& mc, const DevPtrsF32& p, const int32_t* y_in,
                             int gene_major, const double* pinv, double w0, int set_state,
                             cudaStream_t s);

@@ -4,7 +4,9 @@ beta_gl must agree within 4 Monte Carlo standard errors.
 
 Different chains give different draws, so the comparison is statistical.  The
 oracle runs 16 independent chains (spawned worker processes) and each GPU form
-8, all started from the parameter values the synthetic counts were drawn from.
+16, all started from the parameter values the synthetic counts were drawn from.
+Each side uses its own seed: two forms given the same seed read the same
+Philox words in different roles, and their chains would not be independent.
 The MCSE of each side is the standard error of its chain means: the slowest
 hyperparameters (sigma^2_3, sigma^2_4 at N=16) have integrated autocorrelation
 times near 120 iterations, so shorter batches inside one chain would
@@ -23,7 +25,7 @@ from paper_1606_06659_gb300 import synthetic
 pytestmark = [pytest.mark.gpu, pytest.mark.slow]
 
 N_ORACLE_CHAINS = 16
-N_GPU_CHAINS = 8
+N_GPU_CHAINS = 16
 
 
 def _truth_state(d):
@@ -95,8 +97,8 @@ def test_long_runs_agree_with_oracle(pool, cfg, G, orc_iters, gpu_iters):
     for precision in (fbs.FBS_F64, fbs.FBS_F32):
         phis, betas = [], []
         for c in range(N_GPU_CHAINS):
-            g = fbs.Sampler(d["y"], d["X"], d["h"], d["priors"], seed=202, chain=c,
-                            precision=precision, trace_cap=rows, trace_beta=1)
+            g = fbs.Sampler(d["y"], d["X"], d["h"], d["priors"], seed=202 + 1000 * precision,
+                            chain=c, precision=precision, trace_cap=rows, trace_beta=1)
             g.set_state(it=0, **_truth_state(d))
             g.run(gpu_iters, burnin=gpu_burn, thin=thin)
             g.sync()

@@ -188,6 +188,60 @@ int fbs_profile(fbs_handle* h, int64_t n_iter, int64_t burnin, int64_t thin, dou
 int fbs_uniforms(uint64_t seed, uint32_t chain, uint32_t stream, uint32_t index0, int n_index,
                  uint32_t iter, uint32_t k0, int n_k, double* out);
 
+/* ---- Batches: many datasets and chains in one launch -----------------------
+ *
+ * The conditionally independent updates of Algorithm 1 are independent across
+ * datasets too, so C datasets of different N, G and L (and C chains, each with
+ * its own seed and chain number) sweep together: one eps launch, one
+ * gamma/beta launch and one hyperparameter launch (one block per dataset) per
+ * iteration, replayed from a captured CUDA graph.  Batches run the FP32 form. */
+
+typedef struct fbs_batch fbs_batch;
+
+/* One dataset of a batch: y host [G][N] int32 gene-major; X host [N][L]; h host
+ * [N]; priors; Philox seed and chain number.  Read during fbs_batch_init only. */
+typedef struct {
+  int N, G, L;
+  const int32_t* y;
+  const double* X;
+  const double* h;
+  fbs_priors priors;
+  uint64_t seed;
+  uint32_t chain;
+} fbs_dataset;
+
+/* Create a batch of C >= 1 datasets.  opt: precision must be FBS_F32; w0, K,
+ * shrink_max, moments_eps, trace_cap and trace_beta apply to every dataset.
+ * The library allocates the device memory.  Every dataset starts from the
+ * default state of fbs_init.  Errors as fbs_init, naming the dataset. */
+int fbs_batch_init(fbs_batch** out, int C, const fbs_dataset* sets, const fbs_options* opt,
+                   void* stream);
+
+/* fbs_run for every dataset of the batch at once (same n_iter, burnin, thin). */
+int fbs_batch_run(fbs_batch* b, int64_t n_iter, int64_t burnin, int64_t thin);
+
+/* Wait for the batch; FBS_E_NONFINITE if any dataset saw a non-finite start. */
+int fbs_batch_sync(fbs_batch* b);
+
+/* A handle viewing dataset c of the batch, owned by the batch: fbs_sync,
+ * fbs_moments, fbs_get_state, fbs_set_state, fbs_trace, fbs_beta_ess,
+ * fbs_count_sums and fbs_counters work on it; fbs_run and fbs_profile return
+ * FBS_E_ARG; fbs_free ignores it.  NULL if c is out of range. */
+fbs_handle* fbs_batch_chain(fbs_batch* b, int c);
+
+/* Launch schedule: threads per block of the eps kernel (128 or 256) and of the
+ * gamma/beta kernel (32, 64 or 128). */
+int fbs_batch_set_schedule(fbs_batch* b, int eps_block, int gb_block);
+
+/* Autotuner: times `sweeps` sweeps (direct launches, CUDA events) under every
+ * schedule, keeps the fastest and returns it with its time per sweep.  The
+ * trial sweeps are ordinary iterations of every chain, run with `burnin` as
+ * M_B, so call it before fbs_batch_run with the burn-in that run will use. */
+int fbs_batch_autotune(fbs_batch* b, int sweeps, int64_t burnin, int* eps_block, int* gb_block,
+                       double* ms_per_sweep);
+
+void fbs_batch_free(fbs_batch* b);
+
 /* ---- One sweep without any allocation ------------------------------------
  *
  * The paper has no counterpart to this entry point; it exists for callers

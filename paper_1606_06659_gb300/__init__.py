@@ -30,7 +30,9 @@ NUM_COUNTERS = len(COUNTER_NAMES)
 EXPORTED = ("fbs_default_options", "fbs_workspace_bytes", "fbs_init", "fbs_run", "fbs_sync",
             "fbs_moments", "fbs_get_state", "fbs_set_state", "fbs_trace", "fbs_beta_ess",
             "fbs_count_sums", "fbs_counters", "fbs_profile", "fbs_uniforms", "fbs_free",
-            "fbs_last_error_string", "fbs_sweep_noalloc")
+            "fbs_last_error_string", "fbs_sweep_noalloc", "fbs_batch_init", "fbs_batch_run",
+            "fbs_batch_sync", "fbs_batch_chain", "fbs_batch_set_schedule", "fbs_batch_autotune",
+            "fbs_batch_free")
 NOALLOC_MAX_GENES = 2048 * 128
 
 
@@ -55,6 +57,13 @@ class Options(C.Structure):
 _PD = C.POINTER(C.c_double)
 _PI64 = C.POINTER(C.c_int64)
 _lib = None
+
+
+class Dataset(C.Structure):
+    """fbs_dataset: one dataset of a batch."""
+    _fields_ = [("N", C.c_int), ("G", C.c_int), ("L", C.c_int), ("y", C.POINTER(C.c_int32)),
+                ("X", _PD), ("h", _PD), ("priors", Priors), ("seed", C.c_uint64),
+                ("chain", C.c_uint32)]
 
 
 class SweepArgs(C.Structure):
@@ -95,6 +104,17 @@ def load_library(path: str = LIB_PATH):
     lib.fbs_profile.argtypes = [vp, i64, i64, i64, _PD]
     lib.fbs_uniforms.argtypes = [u64, u32, u32, u32, i32, u32, u32, i32, _PD]
     lib.fbs_sweep_noalloc.argtypes = [C.POINTER(SweepArgs)]
+    lib.fbs_batch_init.argtypes = [C.POINTER(vp), C.c_int, C.POINTER(Dataset), C.POINTER(Options),
+                                   vp]
+    lib.fbs_batch_run.argtypes = [vp, i64, i64, i64]
+    lib.fbs_batch_sync.argtypes = [vp]
+    lib.fbs_batch_chain.argtypes = [vp, C.c_int]
+    lib.fbs_batch_chain.restype = vp
+    lib.fbs_batch_set_schedule.argtypes = [vp, C.c_int, C.c_int]
+    lib.fbs_batch_autotune.argtypes = [vp, C.c_int, i64, C.POINTER(C.c_int), C.POINTER(C.c_int),
+                                       C.POINTER(C.c_double)]
+    lib.fbs_batch_free.argtypes = [vp]
+    lib.fbs_batch_free.restype = None
     lib.fbs_free.argtypes = [vp]
     lib.fbs_free.restype = None
     lib.fbs_last_error_string.argtypes = []
@@ -306,3 +326,99 @@ class Sampler:
         c = np.zeros(NUM_COUNTERS, np.int64)
         _check(self.lib.fbs_counters(self.h, c.ctypes.data_as(_PI64)))
         return dict(zip(COUNTER_NAMES, (int(v) for v in c)))
+
+
+class ChainView(Sampler):
+    """One dataset of a BatchSampler, with the Sampler accessors (state, moments,
+    trace, counters).  Running happens through the batch."""
+
+    def __init__(self, lib, handle, N, G, L, options):
+        self.lib, self.h = lib, C.c_void_p(handle)
+        self.N, self.G, self.L, self.P = N, G, L, 2 * L + 2
+        self.options = options
+        self._ws = None
+
+    def close(self):
+        self.h = None
+
+    def run(self, *a, **k):
+        raise FbsError(FBS_E_ARG, "a batch dataset runs with BatchSampler.run")
+
+
+class BatchSampler:
+    """Many datasets (different N, G, L) and chains swept together in the FP32 form.
+
+    datasets: list of dicts with y [G][N], X [N][L], h [N], priors; seeds and
+    chains: one per dataset.
+    """
+
+    def __init__(self, datasets, seeds=None, chains=None, options: Options | None = None,
+                 **option_kw):
+        self.lib = load_library()
+        C_ = len(datasets)
+        seeds = list(seeds) if seeds is not None else [1 + i for i in range(C_)]
+        chains = list(chains) if chains is not None else [0] * C_
+        self.options = options or default_options(precision=FBS_F32)
+        for k, v in option_kw.items():
+            setattr(self.options, k, v)
+        self._keep = []
+        arr = (Dataset * C_)()
+        self.shapes = []
+        for i, d in enumerate(datasets):
+            y = np.ascontiguousarray(d["y"], np.int32)
+            G, N = y.shape
+            X = np.ascontiguousarray(d["X"], np.float64).reshape(N, -1)
+            L = X.shape[1]
+            h = np.ascontiguousarray(d["h"], np.float64).reshape(N)
+            c = np.ascontiguousarray(np.broadcast_to(d["priors"]["c"], (L,)), np.float64)
+            s = np.ascontiguousarray(np.broadcast_to(d["priors"]["s"], (L,)), np.float64)
+            self._keep += [y, X, h, c, s]
+            pr = d["priors"]
+            arr[i] = Dataset(N, G, L, y.ctypes.data_as(C.POINTER(C.c_int32)), _pd(X), _pd(h),
+                             Priors(float(pr["a"]), float(pr["b"]), float(pr["d"]), _pd(c),
+                                    _pd(s)), int(seeds[i]), int(chains[i]))
+            self.shapes.append((N, G, L))
+        stream = None
+        try:
+            import torch
+            if torch.cuda.is_available():
+                stream = torch.cuda.current_stream().cuda_stream
+        except ImportError:
+            pass
+        handle = C.c_void_p()
+        _check(self.lib.fbs_batch_init(C.byref(handle), C_, arr, C.byref(self.options), stream))
+        self.b = handle
+        self.views = [ChainView(self.lib, self.lib.fbs_batch_chain(self.b, i), *self.shapes[i],
+                                self.options) for i in range(C_)]
+
+    def __len__(self):
+        return len(self.views)
+
+    def chain(self, c) -> ChainView:
+        return self.views[c]
+
+    def run(self, n_iter, burnin=0, thin=1):
+        _check(self.lib.fbs_batch_run(self.b, int(n_iter), int(burnin), int(thin)))
+
+    def sync(self):
+        _check(self.lib.fbs_batch_sync(self.b))
+
+    def set_schedule(self, eps_block, gb_block):
+        _check(self.lib.fbs_batch_set_schedule(self.b, int(eps_block), int(gb_block)))
+
+    def autotune(self, sweeps=5, burnin=0):
+        e, g, ms = C.c_int(), C.c_int(), C.c_double()
+        _check(self.lib.fbs_batch_autotune(self.b, int(sweeps), int(burnin), C.byref(e),
+                                           C.byref(g), C.byref(ms)))
+        return e.value, g.value, ms.value
+
+    def close(self):
+        if getattr(self, "b", None):
+            self.lib.fbs_batch_free(self.b)
+            self.b = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

@@ -7,6 +7,7 @@
 #include <stdio.h>
 #include <string.h>
 
+#include <algorithm>
 #include <map>
 #include <string>
 #include <vector>
@@ -115,9 +116,12 @@ LayoutF32 make_layout_f32(int N, int G, int L, int nblk, long long trace_cap, in
   return o;
 }
 
+// Threads per block of the gamma/beta kernel: FP64 work is bound by the FP64
+// pipe, so small blocks spread it evenly over the SMs; the FP32 form is bound by
+// latency and prefers more warps per block.
 int block_of(const fbs_options* o) {
-  int b = o && o->block > 0 ? o->block : kDefaultBlock;
-  return b;
+  if (o && o->block > 0) return o->block;
+  return (o && o->precision == FBS_F32) ? 128 : 32;
 }
 
 }  // namespace
@@ -143,6 +147,7 @@ struct fbs_handle {
   cudaEvent_t ev_g = nullptr, ev_h = nullptr;  // gamma/beta done, hyperparameters done
   cudaGraphExec_t seg_exec = nullptr;
   long long trace_cap = 0;
+  bool is_view = false;  // a dataset of a batch: state access only, owned by the batch
 };
 
 namespace {
@@ -244,6 +249,43 @@ DevPtrs carve(char* base, const Layout& o, int trace_beta) {
   p.trace_beta = trace_beta ? (double*)(base + o.trace_beta) : nullptr;
   p.counters = (unsigned long long*)(base + o.counters);
   return p;
+}
+
+DevPtrsF32 carve_f32_ptrs(char* base, const LayoutF32& o32, int trace_beta) {
+  DevPtrsF32 f;
+  f.y = (const int32_t*)(base + o32.y);
+  f.T = (const double*)(base + o32.T);
+  f.eps = (float*)(base + o32.eps);
+  f.w_eps = (float*)(base + o32.w_eps);
+  f.waux_eps = (float*)(base + o32.waux_eps);
+  f.mom_eps = (float*)(base + o32.mom_eps);
+  f.mu = (float*)(base + o32.mu);
+  f.beta = (float*)(base + o32.beta);
+  f.w_beta = (float*)(base + o32.w_beta);
+  f.waux_beta = (float*)(base + o32.waux_beta);
+  f.mom_beta = (float*)(base + o32.mom_beta);
+  f.gam = (float*)(base + o32.gam);
+  f.mom_gam = (float*)(base + o32.mom_gam);
+  f.partial = (double*)(base + o32.partial);
+  f.hyp = (Hyper*)(base + o32.hyp);
+  f.trace_phi = (double*)(base + o32.trace_phi);
+  f.trace_beta = trace_beta ? (double*)(base + o32.trace_beta) : nullptr;
+  f.counters = (unsigned long long*)(base + o32.counters);
+  return f;
+}
+
+// FP32 pointers of one chain, and the FP64-struct fields the shared kernels and
+// copies use (everything else null).
+void carve_f32(char* base, const LayoutF32& o32, int trace_beta, DevPtrsF32& f, DevPtrs& p) {
+  f = carve_f32_ptrs(base, o32, trace_beta);
+  memset(&p, 0, sizeof(p));
+  p.y = f.y;
+  p.T = f.T;
+  p.partial = f.partial;
+  p.hyp = f.hyp;
+  p.trace_phi = f.trace_phi;
+  p.trace_beta = f.trace_beta;
+  p.counters = f.counters;
 }
 
 // Copy a device [R][G] plane set (double or float) to a host [G][R] double array.
@@ -353,6 +395,92 @@ int ensure_graph(fbs_handle* h) {
 
 }  // namespace
 
+namespace {
+
+// Validates one dataset and builds its model constants and (X^T X)^-1 X^T.
+int build_model(const int32_t* y, int N, int G, const double* X, int L, const double* hoff,
+                const fbs_priors* pri, const fbs_options* o, uint64_t seed, uint32_t chain,
+                ModelConst& mc, double* pinv, bool* integral_out) {
+  int rc = check_sizes(N, G, L);
+  if (rc) return rc;
+  rc = check_opts(o);
+  if (rc) return rc;
+  if (!y || !X || !hoff || !pri || !pri->c || !pri->s)
+    return fail(FBS_E_ARG, "y, X, h, priors, priors->c and priors->s must be non-NULL");
+  auto pos = [](double v) { return isfinite(v) && v > 0.0; };
+  if (!pos(pri->a) || !pos(pri->b) || !pos(pri->d))
+    return fail(FBS_E_ARG, "prior constants a, b, d must be finite and > 0");
+  for (int l = 0; l < L; ++l)
+    if (!pos(pri->c[l]) || !pos(pri->s[l]))
+      return fail(FBS_E_ARG, "prior constants c_l, s_l must be finite and > 0");
+  for (int i = 0; i < N * L; ++i)
+    if (!isfinite(X[i])) return fail(FBS_E_ARG, "X has a non-finite entry");
+  for (int n = 0; n < N; ++n)
+    if (!isfinite(hoff[n])) return fail(FBS_E_ARG, "h has a non-finite entry");
+  for (size_t i = 0; i < (size_t)N * G; ++i)
+    if (y[i] < 0) return fail(FBS_E_ARG, "y has a negative count");
+
+  memset(&mc, 0, sizeof(mc));
+  mc.N = N;
+  mc.G = G;
+  mc.L = L;
+  mc.P = 2 * L + 2;
+  mc.K = o->step_out_max;
+  mc.shrink_max = o->shrink_max;
+  mc.moments_eps = o->moments_eps ? 1 : 0;
+  mc.trace_beta = (o->trace_beta && o->trace_cap > 0) ? 1 : 0;
+  mc.seed_lo = (uint32_t)(seed & 0xffffffffu);
+  mc.seed_hi = (uint32_t)(seed >> 32);
+  mc.chain = chain;
+  mc.a = pri->a;
+  mc.b = pri->b;
+  mc.d = pri->d;
+  for (int l = 0; l < L; ++l) {
+    mc.c2[l] = pri->c[l] * pri->c[l];
+    mc.s2[l] = pri->s[l] * pri->s[l];
+  }
+  bool integral = true;
+  for (int n = 0; n < N; ++n) {
+    mc.h[n] = hoff[n];
+    for (int l = 0; l < L; ++l) {
+      mc.X[n * kMaxL + l] = X[n * L + l];
+      if (X[n * L + l] != floor(X[n * L + l])) integral = false;
+    }
+  }
+  *integral_out = integral;
+  for (int n = 0; n < N; ++n) {
+    mc.hf[n] = (float)mc.h[n];
+    for (int l = 0; l < L; ++l) mc.Xf[n * kMaxL + l] = (float)mc.X[n * kMaxL + l];
+  }
+  for (int l = 0; l < L; ++l) {
+    int nc = 0;
+    for (int n = 0; n < N; ++n) {
+      const double v = X[n * L + l];
+      if (v == 0.0) {
+        mc.cls[l][n] = -1;
+        continue;
+      }
+      int j = 0;
+      while (j < nc && mc.cval[l][j] != v) ++j;
+      if (j == nc) {
+        if (nc == kMaxCls)
+          return fail(FBS_E_ARG, "a column of X has more than FBS_MAX_CLASSES distinct values");
+        mc.cval[l][nc] = v;
+        mc.cvalf[l][nc] = (float)v;
+        mc.ckind[l][nc] = v == 1.0 ? kClsPlus : (v == -1.0 ? kClsMinus : kClsOther);
+        ++nc;
+      }
+      mc.cls[l][n] = (int8_t)j;
+    }
+    mc.ncls[l] = nc;
+  }
+  if (!pseudo_inverse(X, N, L, pinv)) return fail(FBS_E_ARG, "X^T X is singular");
+  return FBS_OK;
+
+}
+
+}  // namespace
+
 extern "C" {
 
 void fbs_default_options(fbs_options* o) {
@@ -396,88 +524,15 @@ int fbs_init(fbs_handle** out, const int32_t* y, int N, int G, int gene_major, c
   fbs_options d;
   fbs_default_options(&d);
   const fbs_options* o = opt ? opt : &d;
-  int rc = check_sizes(N, G, L);
-  if (rc) return rc;
-  rc = check_opts(o);
-  if (rc) return rc;
-  if (!y || !X || !hoff || !pri || !pri->c || !pri->s)
-    return fail(FBS_E_ARG, "y, X, h, priors, priors->c and priors->s must be non-NULL");
-  auto pos = [](double v) { return isfinite(v) && v > 0.0; };
-  if (!pos(pri->a) || !pos(pri->b) || !pos(pri->d))
-    return fail(FBS_E_ARG, "prior constants a, b, d must be finite and > 0");
-  for (int l = 0; l < L; ++l)
-    if (!pos(pri->c[l]) || !pos(pri->s[l]))
-      return fail(FBS_E_ARG, "prior constants c_l, s_l must be finite and > 0");
-  for (int i = 0; i < N * L; ++i)
-    if (!isfinite(X[i])) return fail(FBS_E_ARG, "X has a non-finite entry");
-  for (int n = 0; n < N; ++n)
-    if (!isfinite(hoff[n])) return fail(FBS_E_ARG, "h has a non-finite entry");
-  for (size_t i = 0; i < (size_t)N * G; ++i)
-    if (y[i] < 0) return fail(FBS_E_ARG, "y has a negative count");
-
-  fbs_handle* h = new fbs_handle();
-  ModelConst& mc = h->mc;
-  memset(&mc, 0, sizeof(mc));
-  mc.N = N;
-  mc.G = G;
-  mc.L = L;
-  mc.P = 2 * L + 2;
-  mc.K = o->step_out_max;
-  mc.shrink_max = o->shrink_max;
-  mc.moments_eps = o->moments_eps ? 1 : 0;
-  mc.trace_beta = (o->trace_beta && o->trace_cap > 0) ? 1 : 0;
-  mc.seed_lo = (uint32_t)(seed & 0xffffffffu);
-  mc.seed_hi = (uint32_t)(seed >> 32);
-  mc.chain = o->chain;
-  mc.a = pri->a;
-  mc.b = pri->b;
-  mc.d = pri->d;
-  for (int l = 0; l < L; ++l) {
-    mc.c2[l] = pri->c[l] * pri->c[l];
-    mc.s2[l] = pri->s[l] * pri->s[l];
-  }
-  bool integral = true;
-  for (int n = 0; n < N; ++n) {
-    mc.h[n] = hoff[n];
-    for (int l = 0; l < L; ++l) {
-      mc.X[n * kMaxL + l] = X[n * L + l];
-      if (X[n * L + l] != floor(X[n * L + l])) integral = false;
-    }
-  }
-  h->x_integral = integral;
-  for (int n = 0; n < N; ++n) {
-    mc.hf[n] = (float)mc.h[n];
-    for (int l = 0; l < L; ++l) mc.Xf[n * kMaxL + l] = (float)mc.X[n * kMaxL + l];
-  }
-  for (int l = 0; l < L; ++l) {
-    int nc = 0;
-    for (int n = 0; n < N; ++n) {
-      const double v = X[n * L + l];
-      if (v == 0.0) {
-        mc.cls[l][n] = -1;
-        continue;
-      }
-      int j = 0;
-      while (j < nc && mc.cval[l][j] != v) ++j;
-      if (j == nc) {
-        if (nc == kMaxCls) {
-          delete h;
-          return fail(FBS_E_ARG, "a column of X has more than FBS_MAX_CLASSES distinct values");
-        }
-        mc.cval[l][nc] = v;
-        mc.cvalf[l][nc] = (float)v;
-        mc.ckind[l][nc] = v == 1.0 ? kClsPlus : (v == -1.0 ? kClsMinus : kClsOther);
-        ++nc;
-      }
-      mc.cls[l][n] = (int8_t)j;
-    }
-    mc.ncls[l] = nc;
-  }
+  ModelConst mc0;
   double pinv[kMaxL * kMaxN];
-  if (!pseudo_inverse(X, N, L, pinv)) {
-    delete h;
-    return fail(FBS_E_ARG, "X^T X is singular");
-  }
+  bool integral = false;
+  int rc = build_model(y, N, G, X, L, hoff, pri, o, seed, o->chain, mc0, pinv, &integral);
+  if (rc) return rc;
+  fbs_handle* h = new fbs_handle();
+  h->mc = mc0;
+  ModelConst& mc = h->mc;
+  h->x_integral = integral;
 
   h->opt = *o;
   h->block = block_of(o);
@@ -521,35 +576,9 @@ int fbs_init(fbs_handle** out, const int32_t* y, int N, int G, int gene_major, c
   int32_t* y_raw = nullptr;  // raw counts, in a moment plane that is zeroed afterwards
   double* d_pinv = nullptr;
   if (h->prec == FBS_F32) {
-    const LayoutF32& o32 = h->lay32;
-    memset(&h->p, 0, sizeof(h->p));
+    carve_f32(base, h->lay32, mc.trace_beta, h->pf, h->p);
     DevPtrsF32& f = h->pf;
-    f.y = (const int32_t*)(base + o32.y);
-    f.T = (const double*)(base + o32.T);
-    f.eps = (float*)(base + o32.eps);
-    f.w_eps = (float*)(base + o32.w_eps);
-    f.waux_eps = (float*)(base + o32.waux_eps);
-    f.mom_eps = (float*)(base + o32.mom_eps);
-    f.mu = (float*)(base + o32.mu);
-    f.beta = (float*)(base + o32.beta);
-    f.w_beta = (float*)(base + o32.w_beta);
-    f.waux_beta = (float*)(base + o32.waux_beta);
-    f.mom_beta = (float*)(base + o32.mom_beta);
-    f.gam = (float*)(base + o32.gam);
-    f.mom_gam = (float*)(base + o32.mom_gam);
-    f.partial = (double*)(base + o32.partial);
-    f.hyp = (Hyper*)(base + o32.hyp);
-    f.trace_phi = (double*)(base + o32.trace_phi);
-    f.trace_beta = mc.trace_beta ? (double*)(base + o32.trace_beta) : nullptr;
-    f.counters = (unsigned long long*)(base + o32.counters);
-    // the fields the shared kernels and copies use
-    h->p.y = f.y;
-    h->p.T = f.T;
-    h->p.partial = f.partial;
-    h->p.hyp = f.hyp;
-    h->p.trace_phi = f.trace_phi;
-    h->p.trace_beta = f.trace_beta;
-    h->p.counters = f.counters;
+    const LayoutF32& o32 = h->lay32;
     y_raw = (int32_t*)f.mom_eps;
     d_pinv = (double*)(base + o32.pinv);
     if ((e = prepare_gene_kernel_f32(N, h->block)) != cudaSuccess)
@@ -594,6 +623,7 @@ int fbs_init(fbs_handle** out, const int32_t* y, int N, int G, int gene_major, c
 
 int fbs_run(fbs_handle* h, int64_t n_iter, int64_t burnin, int64_t thin) {
   if (!h) return fail(FBS_E_ARG, "handle is NULL");
+  if (h->is_view) return fail(FBS_E_ARG, "a batch dataset runs with fbs_batch_run");
   if (n_iter < 0 || burnin < 0 || thin < 1)
     return fail(FBS_E_ARG, "need n_iter >= 0, burnin >= 0, thin >= 1");
   if (n_iter == 0) return FBS_OK;
@@ -821,6 +851,7 @@ int fbs_counters(fbs_handle* h, int64_t* out) {
 
 int fbs_profile(fbs_handle* h, int64_t n_iter, int64_t burnin, int64_t thin, double* ms) {
   if (!h || !ms) return fail(FBS_E_ARG, "handle or ms is NULL");
+  if (h->is_view) return fail(FBS_E_ARG, "a batch dataset runs with fbs_batch_run");
   if (n_iter < 1 || burnin < 0 || thin < 1)
     return fail(FBS_E_ARG, "need n_iter >= 1, burnin >= 0, thin >= 1");
   int rc = enter(h);
@@ -871,7 +902,7 @@ int fbs_uniforms(uint64_t seed, uint32_t chain, uint32_t stream, uint32_t index0
 }
 
 void fbs_free(fbs_handle* h) {
-  if (!h) return;
+  if (!h || h->is_view) return;
   if (h->s) cudaStreamSynchronize(h->s);
   if (h->seg_exec) cudaGraphExecDestroy(h->seg_exec);
   if (h->own_ws && h->ws) cudaFree(h->ws);
@@ -885,5 +916,363 @@ void fbs_free(fbs_handle* h) {
 }
 
 const char* fbs_last_error_string(void) { return g_err.c_str(); }
+
+
+// ---------------------------------------------------------------- batches
+
+}  // extern "C"
+
+struct fbs_batch {
+  int C = 0;
+  fbs_options opt;
+  std::vector<fbs_handle*> views;
+  std::vector<ModelConst> mcs;
+  std::vector<DevPtrsF32> pfs;
+  std::vector<int> G, N;
+  char* ws = nullptr;            // all datasets' regions
+  ModelConst* d_mc = nullptr;    // [C]
+  DevPtrsF32* d_pf = nullptr;    // [C]
+  int* d_nblk = nullptr;         // [C] gamma/beta blocks per dataset
+  int4* d_eps_tab = nullptr;
+  int2* d_gb_tab = nullptr;
+  int n_eps = 0, n_gb = 0, eps_block = 256, gb_block = 128, max_N = 0, seg = 100;
+  size_t eps_cap = 0, gb_cap = 0;
+  cudaStream_t user = nullptr, s = nullptr, s2 = nullptr;
+  cudaEvent_t ev_in = nullptr, ev_out = nullptr, ev_g = nullptr, ev_h = nullptr;
+  cudaGraphExec_t exec = nullptr;
+};
+
+namespace {
+
+void batch_release(fbs_batch* b) {
+  if (!b) return;
+  if (b->s) cudaStreamSynchronize(b->s);
+  if (b->exec) cudaGraphExecDestroy(b->exec);
+  for (fbs_handle* v : b->views) {
+    if (v->ev_in) cudaEventDestroy(v->ev_in);
+    if (v->ev_out) cudaEventDestroy(v->ev_out);
+    delete v;
+  }
+  cudaFree(b->ws);
+  cudaFree(b->d_mc);
+  cudaFree(b->d_pf);
+  cudaFree(b->d_nblk);
+  cudaFree(b->d_eps_tab);
+  cudaFree(b->d_gb_tab);
+  if (b->ev_in) cudaEventDestroy(b->ev_in);
+  if (b->ev_out) cudaEventDestroy(b->ev_out);
+  if (b->ev_g) cudaEventDestroy(b->ev_g);
+  if (b->ev_h) cudaEventDestroy(b->ev_h);
+  if (b->s2) cudaStreamDestroy(b->s2);
+  if (b->s) cudaStreamDestroy(b->s);
+  delete b;
+}
+
+// Block tables for a schedule: every eps block covers one sample row and up to
+// eps_block genes of one dataset; every gamma/beta block covers up to gb_block
+// genes of one dataset.
+int batch_tables(fbs_batch* b, int eps_block, int gb_block) {
+  std::vector<int4> et;
+  std::vector<int2> gt;
+  std::vector<int> nblk(b->C);
+  for (int c = 0; c < b->C; ++c) {
+    const int ge = (b->G[c] + eps_block - 1) / eps_block;
+    for (int n = 0; n < b->N[c]; ++n)
+      for (int k = 0; k < ge; ++k)
+        et.push_back(make_int4(c, n, k, (int)((n + k) % kCounterCopies)));
+    nblk[c] = (b->G[c] + gb_block - 1) / gb_block;
+    for (int k = 0; k < nblk[c]; ++k) gt.push_back(make_int2(c, k));
+  }
+  if (et.size() > b->eps_cap || gt.size() > b->gb_cap)
+    return fail(FBS_E_ARG, "schedule needs more blocks than the batch reserved");
+  FBS_CUDA(cudaMemcpyAsync(b->d_eps_tab, et.data(), et.size() * sizeof(int4),
+                           cudaMemcpyHostToDevice, b->s));
+  FBS_CUDA(cudaMemcpyAsync(b->d_gb_tab, gt.data(), gt.size() * sizeof(int2),
+                           cudaMemcpyHostToDevice, b->s));
+  FBS_CUDA(cudaMemcpyAsync(b->d_nblk, nblk.data(), nblk.size() * sizeof(int),
+                           cudaMemcpyHostToDevice, b->s));
+  FBS_CUDA(cudaStreamSynchronize(b->s));
+  FBS_CUDA(prepare_batch_kernels(b->max_N, gb_block));
+  b->n_eps = (int)et.size();
+  b->n_gb = (int)gt.size();
+  b->eps_block = eps_block;
+  b->gb_block = gb_block;
+  for (int c = 0; c < b->C; ++c) b->views[c]->nblk = nblk[c];
+  if (b->exec) {
+    cudaGraphExecDestroy(b->exec);
+    b->exec = nullptr;
+  }
+  return FBS_OK;
+}
+
+cudaError_t batch_sweeps_direct(fbs_batch* b, int64_t n_iter) {
+  cudaError_t e = launch_seg_begin_batch(b->d_pf, b->C, b->s);
+  for (int64_t i = 0; i < n_iter && e == cudaSuccess; ++i) {
+    e = launch_eps_f32_batch(b->d_mc, b->d_pf, b->d_eps_tab, b->n_eps, b->eps_block, (int)i, b->s);
+    if (e == cudaSuccess)
+      e = launch_gb_f32_batch(b->d_mc, b->d_pf, b->d_gb_tab, b->n_gb, b->gb_block, b->max_N,
+                              (int)i, b->s);
+    if (e == cudaSuccess) e = launch_hyper_batch(b->d_mc, b->d_pf, b->d_nblk, b->C, b->s);
+  }
+  return e;
+}
+
+cudaError_t batch_capture(fbs_batch* b) {
+  cudaError_t e;
+  if ((e = launch_seg_begin_batch(b->d_pf, b->C, b->s)) != cudaSuccess) return e;
+  for (int i = 0; i < b->seg; ++i) {
+    e = launch_eps_f32_batch(b->d_mc, b->d_pf, b->d_eps_tab, b->n_eps, b->eps_block, i, b->s);
+    if (e != cudaSuccess) return e;
+    if (i > 0 && (e = cudaStreamWaitEvent(b->s, b->ev_h, 0)) != cudaSuccess) return e;
+    e = launch_gb_f32_batch(b->d_mc, b->d_pf, b->d_gb_tab, b->n_gb, b->gb_block, b->max_N, i,
+                            b->s);
+    if (e != cudaSuccess) return e;
+    if ((e = cudaEventRecord(b->ev_g, b->s)) != cudaSuccess) return e;
+    if ((e = cudaStreamWaitEvent(b->s2, b->ev_g, 0)) != cudaSuccess) return e;
+    if ((e = launch_hyper_batch(b->d_mc, b->d_pf, b->d_nblk, b->C, b->s2)) != cudaSuccess)
+      return e;
+    if ((e = cudaEventRecord(b->ev_h, b->s2)) != cudaSuccess) return e;
+  }
+  return cudaStreamWaitEvent(b->s, b->ev_h, 0);
+}
+
+}  // namespace
+
+extern "C" {
+
+int fbs_batch_init(fbs_batch** out, int C, const fbs_dataset* sets, const fbs_options* opt,
+                   void* stream) {
+  g_err.clear();
+  if (!out) return fail(FBS_E_ARG, "out is NULL");
+  *out = nullptr;
+  if (C < 1 || !sets) return fail(FBS_E_ARG, "need C >= 1 datasets");
+  fbs_options d;
+  fbs_default_options(&d);
+  d.precision = FBS_F32;
+  const fbs_options* o = opt ? opt : &d;
+  int rc = check_opts(o);
+  if (rc) return rc;
+  if (o->precision != FBS_F32) return fail(FBS_E_ARG, "batches run the FBS_F32 form");
+  fbs_batch* b = new fbs_batch();
+  b->C = C;
+  b->opt = *o;
+  b->user = (cudaStream_t)stream;
+  b->seg = o->graph_segment > 0 ? o->graph_segment : 100;
+  b->mcs.resize(C);
+  b->pfs.resize(C);
+  b->G.resize(C);
+  b->N.resize(C);
+  std::vector<double> pinv((size_t)C * kMaxL * kMaxN);
+  std::vector<LayoutF32> lay(C);
+  std::vector<size_t> off(C);
+  std::vector<char> integral(C);
+  size_t total = 0;
+  for (int c = 0; c < C; ++c) {
+    const fbs_dataset& ds = sets[c];
+    bool integ = false;
+    rc = build_model(ds.y, ds.N, ds.G, ds.X, ds.L, ds.h, &ds.priors, o, ds.seed, ds.chain,
+                     b->mcs[c], pinv.data() + (size_t)c * kMaxL * kMaxN, &integ);
+    if (rc) {
+      g_err = "dataset " + std::to_string(c) + ": " + g_err;
+      batch_release(b);
+      return rc;
+    }
+    integral[c] = integ;
+    b->G[c] = ds.G;
+    b->N[c] = ds.N;
+    b->max_N = std::max(b->max_N, ds.N);
+    lay[c] = make_layout_f32(ds.N, ds.G, ds.L, (ds.G + 31) / 32, o->trace_cap,
+                             b->mcs[c].trace_beta);
+    off[c] = total;
+    total += align256(lay[c].total);
+    b->eps_cap += (size_t)ds.N * ((ds.G + 127) / 128);
+    b->gb_cap += (size_t)((ds.G + 31) / 32);
+  }
+  cudaError_t e;
+  auto bail = [&](int code, const std::string& msg) {
+    batch_release(b);
+    return fail(code, msg);
+  };
+  if ((e = cudaStreamCreateWithFlags(&b->s, cudaStreamNonBlocking)) != cudaSuccess ||
+      (e = cudaStreamCreateWithFlags(&b->s2, cudaStreamNonBlocking)) != cudaSuccess ||
+      (e = cudaEventCreateWithFlags(&b->ev_in, cudaEventDisableTiming)) != cudaSuccess ||
+      (e = cudaEventCreateWithFlags(&b->ev_out, cudaEventDisableTiming)) != cudaSuccess ||
+      (e = cudaEventCreateWithFlags(&b->ev_g, cudaEventDisableTiming)) != cudaSuccess ||
+      (e = cudaEventCreateWithFlags(&b->ev_h, cudaEventDisableTiming)) != cudaSuccess)
+    return bail(FBS_E_CUDA, std::string("stream/event creation: ") + cudaGetErrorString(e));
+  if ((e = cudaMalloc((void**)&b->ws, total + 256)) != cudaSuccess ||
+      (e = cudaMalloc((void**)&b->d_mc, sizeof(ModelConst) * C)) != cudaSuccess ||
+      (e = cudaMalloc((void**)&b->d_pf, sizeof(DevPtrsF32) * C)) != cudaSuccess ||
+      (e = cudaMalloc((void**)&b->d_nblk, sizeof(int) * C)) != cudaSuccess ||
+      (e = cudaMalloc((void**)&b->d_eps_tab, sizeof(int4) * b->eps_cap)) != cudaSuccess ||
+      (e = cudaMalloc((void**)&b->d_gb_tab, sizeof(int2) * b->gb_cap)) != cudaSuccess)
+    return bail(e == cudaErrorMemoryAllocation ? FBS_E_OOM : FBS_E_CUDA,
+                std::string("cudaMalloc: ") + cudaGetErrorString(e));
+  if ((e = cudaEventRecord(b->ev_in, b->user)) != cudaSuccess ||
+      (e = cudaStreamWaitEvent(b->s, b->ev_in, 0)) != cudaSuccess)
+    return bail(FBS_E_CUDA, cudaGetErrorString(e));
+  if ((e = prepare_gene_kernel_f32(b->max_N, 128)) != cudaSuccess)
+    return bail(FBS_E_CUDA, cudaGetErrorString(e));
+  for (int c = 0; c < C; ++c) {
+    const fbs_dataset& ds = sets[c];
+    char* base = b->ws + off[c];
+    fbs_handle* v = new fbs_handle();
+    b->views.push_back(v);
+    v->is_view = true;
+    v->mc = b->mcs[c];
+    v->prec = FBS_F32;
+    v->opt = *o;
+    v->lay32 = lay[c];
+    v->trace_cap = o->trace_cap;
+    v->x_integral = integral[c];
+    v->user = b->user;
+    v->s = b->s;
+    carve_f32(base, lay[c], b->mcs[c].trace_beta, v->pf, v->p);
+    b->pfs[c] = v->pf;
+    if ((e = cudaEventCreateWithFlags(&v->ev_in, cudaEventDisableTiming)) != cudaSuccess ||
+        (e = cudaEventCreateWithFlags(&v->ev_out, cudaEventDisableTiming)) != cudaSuccess)
+      return bail(FBS_E_CUDA, cudaGetErrorString(e));
+    int32_t* y_raw = (int32_t*)v->pf.mom_eps;
+    double* d_pinv = (double*)(base + lay[c].pinv);
+    if ((e = cudaMemcpyAsync(y_raw, ds.y, (size_t)ds.N * ds.G * sizeof(int32_t),
+                             cudaMemcpyHostToDevice, b->s)) != cudaSuccess ||
+        (e = cudaMemcpyAsync(d_pinv, pinv.data() + (size_t)c * kMaxL * kMaxN,
+                             sizeof(double) * kMaxL * kMaxN, cudaMemcpyHostToDevice, b->s)) !=
+            cudaSuccess ||
+        (e = cudaMemsetAsync(v->p.counters, 0,
+                             kCounterCopies * FBS_NUM_COUNTERS * sizeof(unsigned long long),
+                             b->s)) != cudaSuccess ||
+        (e = cudaMemsetAsync(v->p.hyp, 0, sizeof(Hyper), b->s)) != cudaSuccess ||
+        (e = launch_init_run(v->p.hyp, o->trace_cap, b->s)) != cudaSuccess ||
+        (e = launch_init_f32(v->mc, v->pf, y_raw, 1, d_pinv, o->w0, 1, b->s)) != cudaSuccess ||
+        (e = launch_init_hyper(v->mc, v->p.hyp, nullptr, v->pf.beta, o->w0, 1, b->s)) !=
+            cudaSuccess ||
+        (e = cudaStreamSynchronize(b->s)) != cudaSuccess)
+      return bail(FBS_E_CUDA, "dataset " + std::to_string(c) + " initialisation: " +
+                                  cudaGetErrorString(e));
+  }
+  if ((e = cudaMemcpyAsync(b->d_mc, b->mcs.data(), sizeof(ModelConst) * C,
+                           cudaMemcpyHostToDevice, b->s)) != cudaSuccess ||
+      (e = cudaMemcpyAsync(b->d_pf, b->pfs.data(), sizeof(DevPtrsF32) * C,
+                           cudaMemcpyHostToDevice, b->s)) != cudaSuccess)
+    return bail(FBS_E_CUDA, cudaGetErrorString(e));
+  rc = batch_tables(b, 256, 128);
+  if (rc) {
+    std::string m = g_err;
+    return bail(rc, m);
+  }
+  if ((e = cudaEventRecord(b->ev_out, b->s)) != cudaSuccess ||
+      (e = cudaStreamWaitEvent(b->user, b->ev_out, 0)) != cudaSuccess)
+    return bail(FBS_E_CUDA, cudaGetErrorString(e));
+  *out = b;
+  return FBS_OK;
+}
+
+int fbs_batch_run(fbs_batch* b, int64_t n_iter, int64_t burnin, int64_t thin) {
+  if (!b) return fail(FBS_E_ARG, "batch is NULL");
+  if (n_iter < 0 || burnin < 0 || thin < 1)
+    return fail(FBS_E_ARG, "need n_iter >= 0, burnin >= 0, thin >= 1");
+  if (n_iter == 0) return FBS_OK;
+  FBS_CUDA(cudaEventRecord(b->ev_in, b->user));
+  FBS_CUDA(cudaStreamWaitEvent(b->s, b->ev_in, 0));
+  FBS_CUDA(launch_set_run_batch(b->d_pf, b->C, burnin, burnin / 2, thin, b->s));
+  int64_t left = n_iter;
+  if (left >= b->seg) {
+    if (!b->exec) {
+      cudaGraph_t graph = nullptr;
+      FBS_CUDA(cudaStreamBeginCapture(b->s, cudaStreamCaptureModeThreadLocal));
+      cudaError_t ce = batch_capture(b);
+      if (ce != cudaSuccess) {
+        cudaStreamEndCapture(b->s, &graph);
+        if (graph) cudaGraphDestroy(graph);
+        return fail(FBS_E_CUDA, std::string("graph capture: ") + cudaGetErrorString(ce));
+      }
+      FBS_CUDA(cudaStreamEndCapture(b->s, &graph));
+      cudaError_t ie = cudaGraphInstantiate(&b->exec, graph, 0);
+      cudaGraphDestroy(graph);
+      FBS_CUDA(ie);
+    }
+    while (left >= b->seg) {
+      FBS_CUDA(cudaGraphLaunch(b->exec, b->s));
+      left -= b->seg;
+    }
+  }
+  if (left > 0) FBS_CUDA(batch_sweeps_direct(b, left));
+  FBS_CUDA(cudaEventRecord(b->ev_out, b->s));
+  FBS_CUDA(cudaStreamWaitEvent(b->user, b->ev_out, 0));
+  return FBS_OK;
+}
+
+int fbs_batch_sync(fbs_batch* b) {
+  if (!b) return fail(FBS_E_ARG, "batch is NULL");
+  FBS_CUDA(cudaStreamSynchronize(b->s));
+  for (fbs_handle* v : b->views) {
+    Hyper hy;
+    int rc = read_hyper(v, &hy);
+    if (rc) return rc;
+    if (hy.flags & kFlagNonfinite)
+      return fail(FBS_E_NONFINITE, "a slice update started from a non-finite log density");
+  }
+  return FBS_OK;
+}
+
+fbs_handle* fbs_batch_chain(fbs_batch* b, int c) {
+  if (!b || c < 0 || c >= b->C) return nullptr;
+  return b->views[c];
+}
+
+int fbs_batch_set_schedule(fbs_batch* b, int eps_block, int gb_block) {
+  if (!b) return fail(FBS_E_ARG, "batch is NULL");
+  if ((eps_block != 128 && eps_block != 256) ||
+      (gb_block != 32 && gb_block != 64 && gb_block != 128))
+    return fail(FBS_E_ARG, "eps_block must be 128 or 256 and gb_block 32, 64 or 128");
+  FBS_CUDA(cudaStreamSynchronize(b->s));
+  return batch_tables(b, eps_block, gb_block);
+}
+
+int fbs_batch_autotune(fbs_batch* b, int sweeps, int64_t burnin, int* eps_block, int* gb_block,
+                       double* ms_per_sweep) {
+  if (!b || sweeps < 1 || burnin < 0) return fail(FBS_E_ARG, "need a batch, sweeps >= 1, burnin >= 0");
+  const int eb[2] = {128, 256}, gbv[3] = {32, 64, 128};
+  double best = 1e300;
+  int be = b->eps_block, bg = b->gb_block;
+  cudaEvent_t t0, t1;
+  FBS_CUDA(cudaEventCreate(&t0));
+  FBS_CUDA(cudaEventCreate(&t1));
+  int rc = FBS_OK;
+  for (int i = 0; i < 2 && rc == FBS_OK; ++i)
+    for (int j = 0; j < 3 && rc == FBS_OK; ++j) {
+      rc = fbs_batch_set_schedule(b, eb[i], gbv[j]);
+      if (rc) break;
+      cudaError_t e = launch_set_run_batch(b->d_pf, b->C, burnin, burnin / 2, 1, b->s);
+      if (e == cudaSuccess) e = batch_sweeps_direct(b, 1);  // warm-up
+      if (e == cudaSuccess) e = cudaEventRecord(t0, b->s);
+      if (e == cudaSuccess) e = batch_sweeps_direct(b, sweeps);
+      if (e == cudaSuccess) e = cudaEventRecord(t1, b->s);
+      if (e == cudaSuccess) e = cudaEventSynchronize(t1);
+      float ms = 0.f;
+      if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, t0, t1);
+      if (e != cudaSuccess) {
+        rc = fail(FBS_E_CUDA, std::string("autotune: ") + cudaGetErrorString(e));
+        break;
+      }
+      if (ms / sweeps < best) {
+        best = ms / sweeps;
+        be = eb[i];
+        bg = gbv[j];
+      }
+    }
+  cudaEventDestroy(t0);
+  cudaEventDestroy(t1);
+  if (rc) return rc;
+  rc = fbs_batch_set_schedule(b, be, bg);
+  if (rc) return rc;
+  if (eps_block) *eps_block = be;
+  if (gb_block) *gb_block = bg;
+  if (ms_per_sweep) *ms_per_sweep = best;
+  return FBS_OK;
+}
+
+void fbs_batch_free(fbs_batch* b) { batch_release(b); }
 
 }  // extern "C"

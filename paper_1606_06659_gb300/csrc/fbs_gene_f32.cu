@@ -23,6 +23,7 @@
 #include "fbs_common.cuh"
 #include "fbs_kernels.h"
 #include "fbs_rng.cuh"
+#include "fbs_hyper.cuh"
 
 namespace fbs {
 
@@ -247,7 +248,8 @@ __device__ __forceinline__ void add_counters(unsigned long long* base, unsigned 
 // gamma/beta kernel.  It involves no hyperparameter, so within a captured
 // segment it runs concurrently with the hyperparameter kernel of the previous
 // iteration; its iteration number comes from the segment snapshot.
-__global__ void __launch_bounds__(256) k_eps_f32(ModelConst mc, DevPtrsF32 p, int seg_i) {
+__device__ __forceinline__ void eps_f32_body(const ModelConst& mc, const DevPtrsF32& p, int seg_i,
+                                             int n, int g, int copy) {
   const int G = mc.G, N = mc.N, L = mc.L;
   const Hyper* hy = p.hyp;
   const long long it = hy->seg_it + seg_i + 1;
@@ -257,11 +259,9 @@ __global__ void __launch_bounds__(256) k_eps_f32(ModelConst mc, DevPtrsF32 p, in
   if (before < 0) before = 0;
   const float inv_k = mom ? 1.0f / (float)(hy->seg_nmom + before + 1) : 0.0f;
   const size_t NG = (size_t)N * G;
-  const size_t e = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+  const size_t e = (size_t)n * G + g;
   unsigned evals = 0, caps = 0, nonfin = 0;
-  if (e < NG) {
-    const int n = (int)(e / (size_t)G);
-    const int g = (int)(e - (size_t)n * G);
+  if (g < G) {
     float A = mc.hf[n];
 #pragma unroll
     for (int l = 0; l < kMaxL; ++l)
@@ -287,14 +287,21 @@ __global__ void __launch_bounds__(256) k_eps_f32(ModelConst mc, DevPtrsF32 p, in
     }
     if (mom && mc.moments_eps) welford_kahan(p.mom_eps, NG, e, s.x, inv_k);
   }
-  add_counters(p.counters + (blockIdx.x % kCounterCopies) * FBS_NUM_COUNTERS, evals, 0, caps,
-               0, nonfin, &p.hyp->flags);
+  add_counters(p.counters + copy * FBS_NUM_COUNTERS, evals, 0, caps, 0, nonfin, &p.hyp->flags);
+}
+
+__global__ void __launch_bounds__(256) k_eps_f32(ModelConst mc, DevPtrsF32 p, int seg_i) {
+  eps_f32_body(mc, p, seg_i, blockIdx.y, blockIdx.x * blockDim.x + threadIdx.x,
+               (blockIdx.x + blockIdx.y) % kCounterCopies);
 }
 
 // Steps 2 and 5 of Algorithm 1 in the FP32 form: one thread per gene.  The
 // hyperparameter kernel of the previous iteration has finished when it runs.
-__global__ void __launch_bounds__(128) k_gb_f32(ModelConst mc, DevPtrsF32 p, int seg_i) {
-  extern __shared__ float smem_f[];  // mu[n][blockDim], y[n][blockDim]; then FP64 warp sums
+__device__ __forceinline__ void gb_f32_body(const ModelConst& mc, const DevPtrsF32& p, int seg_i,
+                                            int blk) {
+  // shared: mu[N][B], y[N][B], beta[L][B], partials[kNumPart][B] (per-thread values
+  // indexed by a runtime l live here rather than in local memory); then FP64 warp sums
+  extern __shared__ float smem_f[];
   const int G = mc.G, N = mc.N, L = mc.L;
   const Hyper* hy = p.hyp;
   const long long it = hy->seg_it + seg_i + 1;
@@ -308,21 +315,21 @@ __global__ void __launch_bounds__(128) k_gb_f32(ModelConst mc, DevPtrsF32 p, int
   const long long trace_row = hy->trace_rows;
   const size_t LG = (size_t)L * G;
 
+  const int B = blockDim.x;
   float* mu = smem_f;
-  float* ys = smem_f + (size_t)N * blockDim.x;
+  float* ys = mu + (size_t)N * B;
+  float* bs = ys + (size_t)N * B;
+  float* ps = bs + (size_t)kMaxL * B;
   const int tid = threadIdx.x;
-  const int g = blockIdx.x * blockDim.x + tid;
+  const int g = blk * B + tid;
   const bool active = g < G;
 
-  float part[kNumPart];
 #pragma unroll
-  for (int i = 0; i < kNumPart; ++i) part[i] = 0.0f;
+  for (int i = 0; i < kNumPart; ++i) ps[i * B + tid] = 0.0f;
   unsigned evals_b = 0, caps = 0, gcaps = 0, nonfin = 0;
 
   if (active) {
-    float beta[kMaxL];
-#pragma unroll
-    for (int l = 0; l < kMaxL; ++l) beta[l] = l < L ? p.beta[(size_t)l * G + g] : 0.0f;
+    for (int l = 0; l < L; ++l) bs[l * B + tid] = p.beta[(size_t)l * G + g];
     float ss = 0.0f;
 #pragma unroll 4
     for (int n = 0; n < N; ++n) {
@@ -343,8 +350,8 @@ __global__ void __launch_bounds__(128) k_gb_f32(ModelConst mc, DevPtrsF32 p, int
       gcaps += gcap;
       p.gam[g] = gam;
       if (mom) welford_kahan(p.mom_gam, (size_t)G, (size_t)g, gam, inv_k);
-      part[0] = __logf(gam);
-      part[1] = 1.0f / gam;
+      ps[0 * B + tid] = __logf(gam);
+      ps[1 * B + tid] = 1.0f / gam;
     }
 
     // ---- step 5: beta_gl, l = 1..L in order
@@ -353,8 +360,9 @@ __global__ void __launch_bounds__(128) k_gb_f32(ModelConst mc, DevPtrsF32 p, int
       const float theta = (float)hy->phi[2 + l];
       const float sig2 = (float)hy->phi[2 + L + l];
       BetaDensityF f;
-      f.b0 = beta[l];
-      f.bt = beta[l] - theta;
+      const float b_cur = bs[l * B + tid];
+      f.b0 = b_cur;
+      f.bt = b_cur - theta;
       f.hs = 0.5f / sig2;
       f.ncls = mc.ncls[l];
       float Y[kMaxCls];
@@ -378,7 +386,7 @@ __global__ void __launch_bounds__(128) k_gb_f32(ModelConst mc, DevPtrsF32 p, int
 #pragma unroll
       for (int j = 0; j < kMaxCls; ++j) f.D[j] = Y[j] - f.Q[j];
       Rng4 r(mc.seed_lo, mc.seed_hi, mc.chain, kStreamBeta, (uint32_t)((size_t)g * L + l), it32);
-      const float x0 = beta[l];
+      const float x0 = b_cur;
       float w = p.w_beta[e];
       SliceResultF s = slice_update_f(x0, 0.0f, w, f, r, mc.K, mc.shrink_max);
       evals_b += s.evals;
@@ -401,7 +409,7 @@ __global__ void __launch_bounds__(128) k_gb_f32(ModelConst mc, DevPtrsF32 p, int
           mu[n * blockDim.x + tid] *= fc;
         }
       }
-      beta[l] = s.x;
+      bs[l * B + tid] = s.x;
       p.beta[e] = s.x;
       if (it <= burnin) {
         float waux = p.waux_beta[e];
@@ -412,17 +420,18 @@ __global__ void __launch_bounds__(128) k_gb_f32(ModelConst mc, DevPtrsF32 p, int
       if (mom) welford_kahan(p.mom_beta, LG, e, s.x, inv_k);
       if (trace_now) p.trace_beta[(size_t)trace_row * LG + e] = (double)s.x;
       const float dv = s.x - theta;
-      part[2 + l] = dv;
-      part[2 + kMaxL + l] = dv * dv;
+      ps[(2 + l) * B + tid] = dv;
+      ps[(2 + kMaxL + l) * B + tid] = dv * dv;
     }
   }
 
   // ---- partial sums: error-free FP32 pair sums within the warp, FP64 beyond
   const int lane = tid & 31, warp = tid >> 5, nwarp = blockDim.x >> 5;
-  double* red = reinterpret_cast<double*>(smem_f + ((2 * (size_t)N * blockDim.x + 1) & ~(size_t)1));
+  double* red = reinterpret_cast<double*>(
+      smem_f + (((2 * (size_t)N + kMaxL + kNumPart) * B + 1) & ~(size_t)1));
 #pragma unroll
   for (int i = 0; i < kNumPart; ++i) {
-    float s = part[i], c = 0.0f;
+    float s = ps[i * B + tid], c = 0.0f;
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) {
       const float so = __shfl_down_sync(0xffffffffu, s, o);
@@ -438,9 +447,13 @@ __global__ void __launch_bounds__(128) k_gb_f32(ModelConst mc, DevPtrsF32 p, int
   if (tid < kNumPart) {
     double acc = 0.0;
     for (int w = 0; w < nwarp; ++w) acc += red[w * kNumPart + tid];
-    p.partial[(size_t)blockIdx.x * kNumPart + tid] = acc;
+    p.partial[(size_t)blk * kNumPart + tid] = acc;
   }
   add_counters(p.counters, 0, evals_b, caps, gcaps, nonfin, &p.hyp->flags);
+}
+
+__global__ void __launch_bounds__(128) k_gb_f32(ModelConst mc, DevPtrsF32 p, int seg_i) {
+  gb_f32_body(mc, p, seg_i, blockIdx.x);
 }
 
 __global__ void k_seg_begin(Hyper* hy) {
@@ -448,6 +461,94 @@ __global__ void k_seg_begin(Hyper* hy) {
     hy->seg_it = hy->it;
     hy->seg_nmom = hy->n_mom;
   }
+}
+
+// ---------------------------------------------------------------- batched kernels (FP32)
+//
+// Many independent datasets / chains in one launch.  Each dataset keeps its own
+// model constants and device pointers in global memory; a block table maps every
+// block of a launch to one dataset (and to a sample row and gene block for the
+// eps kernel), so a block never straddles two datasets and uneven N and G need no
+// padding beyond the last block of each dataset.
+
+__global__ void __launch_bounds__(256) k_eps_f32_batch(const ModelConst* __restrict__ mcs,
+                                                       const DevPtrsF32* __restrict__ ps,
+                                                       const int4* __restrict__ tab, int seg_i) {
+  const int4 t = tab[blockIdx.x];  // dataset, sample row n, gene block, counter copy
+  eps_f32_body(mcs[t.x], ps[t.x], seg_i, t.y, t.z * blockDim.x + threadIdx.x, t.w);
+}
+
+__global__ void __launch_bounds__(128) k_gb_f32_batch(const ModelConst* __restrict__ mcs,
+                                                      const DevPtrsF32* __restrict__ ps,
+                                                      const int2* __restrict__ tab, int seg_i) {
+  const int2 t = tab[blockIdx.x];  // dataset, gene block within the dataset
+  gb_f32_body(mcs[t.x], ps[t.x], seg_i, t.y);
+}
+
+// One block per dataset.
+__global__ void __launch_bounds__(kHyperThreads) k_hyper_batch(const ModelConst* __restrict__ mcs,
+                                                               const DevPtrsF32* __restrict__ ps,
+                                                               const int* __restrict__ nblk) {
+  const int c = blockIdx.x;
+  const DevPtrsF32& p = ps[c];
+  hyper_body(mcs[c], p.partial, p.hyp, p.trace_phi, p.counters, nblk[c]);
+}
+
+__global__ void k_seg_begin_batch(const DevPtrsF32* __restrict__ ps, int C) {
+  const int c = blockIdx.x * blockDim.x + threadIdx.x;
+  if (c < C) {
+    Hyper* hy = ps[c].hyp;
+    hy->seg_it = hy->it;
+    hy->seg_nmom = hy->n_mom;
+  }
+}
+
+__global__ void k_set_run_batch(const DevPtrsF32* __restrict__ ps, int C, long long burnin,
+                                long long tune_start, long long thin) {
+  const int c = blockIdx.x * blockDim.x + threadIdx.x;
+  if (c < C) {
+    Hyper* hy = ps[c].hyp;
+    hy->burnin = burnin;
+    hy->tune_start = tune_start;
+    hy->thin = thin;
+  }
+}
+
+cudaError_t prepare_batch_kernels(int max_N, int gb_block) {
+  const size_t smem = gene_smem_bytes_f32(max_N, gb_block);
+  if (smem > 48 * 1024)
+    return cudaFuncSetAttribute(k_gb_f32_batch, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                (int)smem);
+  return cudaSuccess;
+}
+
+cudaError_t launch_eps_f32_batch(const ModelConst* mcs, const DevPtrsF32* ps, const int4* tab,
+                                 int n_blocks, int block, int seg_i, cudaStream_t s) {
+  k_eps_f32_batch<<<n_blocks, block, 0, s>>>(mcs, ps, tab, seg_i);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_gb_f32_batch(const ModelConst* mcs, const DevPtrsF32* ps, const int2* tab,
+                                int n_blocks, int block, int max_N, int seg_i, cudaStream_t s) {
+  k_gb_f32_batch<<<n_blocks, block, gene_smem_bytes_f32(max_N, block), s>>>(mcs, ps, tab, seg_i);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_hyper_batch(const ModelConst* mcs, const DevPtrsF32* ps, const int* nblk,
+                               int C, cudaStream_t s) {
+  k_hyper_batch<<<C, kHyperThreads, 0, s>>>(mcs, ps, nblk);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_seg_begin_batch(const DevPtrsF32* ps, int C, cudaStream_t s) {
+  k_seg_begin_batch<<<(C + 127) / 128, 128, 0, s>>>(ps, C);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_set_run_batch(const DevPtrsF32* ps, int C, long long burnin,
+                                 long long tune_start, long long thin, cudaStream_t s) {
+  k_set_run_batch<<<(C + 127) / 128, 128, 0, s>>>(ps, C, burnin, tune_start, thin);
+  return cudaGetLastError();
 }
 
 // ---------------------------------------------------------------- set-up kernels (FP32)
@@ -510,15 +611,15 @@ cudaError_t prepare_gene_kernel_f32(int N, int block) {
 }
 
 size_t gene_smem_bytes_f32(int N, int block) {
-  return (2 * (size_t)N * block + 2) * sizeof(float) +
+  return ((2 * (size_t)N + kMaxL + kNumPart) * block + 2) * sizeof(float) +
          (size_t)(block / 32) * kNumPart * sizeof(double);
 }
 
 cudaError_t launch_eps_f32(const ModelConst& mc, const DevPtrsF32& p, int seg_i,
                            cudaStream_t s) {
-  const size_t n = (size_t)mc.N * mc.G;
   const int blk = 256;
-  k_eps_f32<<<(unsigned)((n + blk - 1) / blk), blk, 0, s>>>(mc, p, seg_i);
+  const dim3 grid((unsigned)((mc.G + blk - 1) / blk), (unsigned)mc.N);
+  k_eps_f32<<<grid, blk, 0, s>>>(mc, p, seg_i);
   return cudaGetLastError();
 }
 

@@ -1,0 +1,149 @@
+// fbs_hyper.cuh -- the hyperparameter steps of one Gibbs sweep (Algorithm 1
+// steps 3, 4, 6, 7 of Landau & Niemi, arXiv 1606.06659) as a block-level device
+// function, shared by the single-chain and the batched hyperparameter kernels.
+#pragma once
+
+#include <math.h>
+#include <stdint.h>
+
+#include "fbs_common.cuh"
+#include "fbs_rng.cuh"
+
+namespace fbs {
+
+// ---------------------------------------------------------------- hyper kernel
+
+// log f(nu | ...) = -G lgamma(nu/2) + (G nu/2) log(nu tau/2) - (nu/2)(S1 + tau S2) on
+// (0, d), S1 = sum_g log gamma_g, S2 = sum_g 1/gamma_g (Algorithm 1 step 3, the
+// sum read as log gamma_g + tau/gamma_g, which the Inverse-Gamma(nu/2, nu tau/2)
+// prior of the gamma_g gives).
+struct NuDensity {
+  double G, d, tau, S1, S2;
+  __device__ __forceinline__ double operator()(double nu, double* aux) const {
+    *aux = 0.0;
+    if (!(nu > 0.0 && nu < d)) return -INFINITY;
+    return -G * lgamma(0.5 * nu) + 0.5 * G * nu * log(0.5 * nu * tau) -
+           0.5 * nu * (S1 + tau * S2);
+  }
+};
+
+constexpr int kHyperThreads = 64;
+
+// Steps 3, 4, 6, 7 for one chain, executed by one block of kHyperThreads threads:
+// the chain's `nblk` per-block partial sums are folded in a fixed order.
+__device__ __forceinline__ void hyper_body(const ModelConst& mc, const double* partial, Hyper* hy,
+                                           double* trace_phi, unsigned long long* counters,
+                                           int nblk) {
+  __shared__ double red[kHyperThreads / 32][kNumPart];
+  __shared__ double tot[kNumPart];
+  __shared__ double phi_new[kMaxP];
+  const int L = mc.L, P = mc.P;
+  const double G = (double)mc.G;
+  const long long it = hy->it + 1;
+  const uint32_t it32 = (uint32_t)it;
+  const int tid = threadIdx.x;
+
+  // fixed-order reduction of the per-block partials
+  double acc[kNumPart];
+#pragma unroll
+  for (int i = 0; i < kNumPart; ++i) acc[i] = 0.0;
+  for (int b = tid; b < nblk; b += kHyperThreads) {
+#pragma unroll
+    for (int i = 0; i < kNumPart; ++i) acc[i] += partial[(size_t)b * kNumPart + i];
+  }
+#pragma unroll
+  for (int i = 0; i < kNumPart; ++i) {
+    double x = acc[i];
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) x += __shfl_down_sync(0xffffffffu, x, o);
+    if ((tid & 31) == 0) red[tid >> 5][i] = x;
+  }
+  if (tid < kMaxP) phi_new[tid] = tid < P ? hy->phi[tid] : 0.0;
+  __syncthreads();
+  if (tid < kNumPart) {
+    double s = 0.0;
+    for (int w = 0; w < kHyperThreads / 32; ++w) s += red[w][tid];
+    tot[tid] = s;
+  }
+  __syncthreads();
+
+  const double S1 = tot[0], S2 = tot[1];
+  if (tid == 0) {
+    // step 3: nu
+    const double tau_old = hy->phi[1];
+    NuDensity f{G, mc.d, tau_old, S1, S2};
+    Rng r(mc.seed_lo, mc.seed_hi, mc.chain, kStreamNu, 0u, it32);
+    const double x0 = hy->phi[0];
+    SliceResult s = slice_update(x0, hy->w_nu, f, r, mc.K, mc.shrink_max);
+    const double nu = s.x;
+    if (it <= hy->burnin) {
+      double w = hy->w_nu, waux = hy->waux_nu;
+      tune_width(w, waux, it, nu, x0, hy->burnin, hy->tune_start);
+      hy->w_nu = w;
+      hy->waux_nu = waux;
+    }
+    atomicAdd(&counters[FBS_CNT_EVALS_NU], (unsigned long long)s.evals);
+    if (s.capped) atomicAdd(&counters[FBS_CNT_SLICE_CAPS], 1ull);
+    if (s.nonfinite) {
+      atomicAdd(&counters[FBS_CNT_NONFINITE], 1ull);
+      atomicOr(&hy->flags, kFlagNonfinite);
+    }
+    // step 4: tau ~ Gamma(a + G nu/2, rate b + nu S2 / 2)
+    Rng rt(mc.seed_lo, mc.seed_hi, mc.chain, kStreamTau, 0u, it32);
+    bool gcap = false;
+    const double shape = mc.a + 0.5 * G * nu;
+    const double rate = mc.b + 0.5 * nu * S2;
+    const double tau = gamma_mt(shape, rt, 0, &gcap) / rate;
+    if (gcap) atomicAdd(&counters[FBS_CNT_GAMMA_CAPS], 1ull);
+    phi_new[0] = nu;
+    phi_new[1] = tau;
+  } else if (tid <= L) {
+    const int l = tid - 1;
+    // step 6: theta_l ~ N(v B1 / sigma^2, v), v = 1/(G/sigma^2 + 1/c^2);
+    // the partials hold B1' = sum (beta - theta_old), B2' = sum (beta - theta_old)^2
+    const double th_old = hy->phi[2 + l];
+    const double sig2 = hy->phi[2 + L + l];
+    const double B1s = tot[2 + l], B2s = tot[2 + kMaxL + l];
+    const double B1 = B1s + G * th_old;
+    const double v = 1.0 / (G / sig2 + 1.0 / mc.c2[l]);
+    const double mean = v * B1 / sig2;
+    Rng r(mc.seed_lo, mc.seed_hi, mc.chain, kStreamTheta, (uint32_t)l, it32);
+    const double th = mean + sqrt(v) * normal_bm(r, 0);
+    // step 7: sigma_l^2 ~ IG((G-1)/2, S/2) on (0, s_l^2), S = sum (beta - theta_new)^2
+    const double dl = th - th_old;
+    const double S = B2s - 2.0 * dl * B1s + G * dl * dl;
+    Rng rs(mc.seed_lo, mc.seed_hi, mc.chain, kStreamSigma, (uint32_t)l, it32);
+    bool gcap = false, tcap = false;
+    const double s2n = trunc_invgamma(0.5 * (G - 1.0), 0.5 * S, mc.s2[l], sig2, rs, &gcap, &tcap);
+    if (gcap) atomicAdd(&counters[FBS_CNT_GAMMA_CAPS], 1ull);
+    if (tcap) atomicAdd(&counters[FBS_CNT_TRUNC_CAPS], 1ull);
+    phi_new[2 + l] = th;
+    phi_new[2 + L + l] = s2n;
+  }
+  __syncthreads();
+
+  const bool mom = it > hy->burnin;
+  if (tid < P) {
+    const double x = phi_new[tid];
+    hy->phi[tid] = x;
+    if (mom) {
+      const double inv_k = 1.0 / (double)(hy->n_mom + 1);
+      const double m = hy->m_phi[tid], q = hy->q_phi[tid];
+      hy->m_phi[tid] = m + (x - m) * inv_k;
+      hy->q_phi[tid] = q + (x * x - q) * inv_k;
+    }
+    if (mom && ((it - hy->burnin) % hy->thin == 0) && hy->trace_rows < hy->trace_cap &&
+        trace_phi != nullptr)
+      trace_phi[(size_t)hy->trace_rows * P + tid] = x;
+  }
+  __syncthreads();
+  if (tid == 0) {
+    if (mom && ((it - hy->burnin) % hy->thin == 0) && hy->trace_rows < hy->trace_cap)
+      hy->trace_rows += 1;
+    if (mom) hy->n_mom += 1;
+    hy->it = it;
+    atomicAdd(&counters[FBS_CNT_SWEEPS], 1ull);
+  }
+}
+
+}  // namespace fbs

@@ -21,6 +21,7 @@
 #include "fbs_common.cuh"
 #include "fbs_kernels.h"
 #include "fbs_rng.cuh"
+#include "fbs_hyper.cuh"
 
 namespace fbs {
 
@@ -309,12 +310,11 @@ __global__ void __launch_bounds__(256) k_eps_f64(ModelConst mc, DevPtrs p, int s
   long long before = (it - 1) - (hy->seg_it > burnin ? hy->seg_it : burnin);
   if (before < 0) before = 0;
   const double inv_k = mom ? 1.0 / (double)(hy->seg_nmom + before + 1) : 0.0;
-  const size_t NG = (size_t)N * G;
-  const size_t e = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+  const int n = blockIdx.y;
+  const int g = blockIdx.x * blockDim.x + threadIdx.x;
+  const size_t e = (size_t)n * G + g;
   unsigned evals = 0, caps = 0, nonfin = 0;
-  if (e < NG) {
-    const int n = (int)(e / (size_t)G);
-    const int g = (int)(e - (size_t)n * G);
+  if (g < G) {
     double A = mc.h[n];
 #pragma unroll
     for (int l = 0; l < kMaxL; ++l)
@@ -342,14 +342,16 @@ __global__ void __launch_bounds__(256) k_eps_f64(ModelConst mc, DevPtrs p, int s
       p.q_eps[e] = q + (s.x * s.x - q) * inv_k;
     }
   }
-  add_counters_u(p.counters + (blockIdx.x % kCounterCopies) * FBS_NUM_COUNTERS, evals, 0, caps,
+  add_counters_u(p.counters + ((blockIdx.x + blockIdx.y) % kCounterCopies) * FBS_NUM_COUNTERS, evals, 0, caps,
                  0, nonfin, &p.hyp->flags);
 }
 
 // Steps 2 and 5: one thread per gene, after the eps kernel of this sweep and the
 // hyperparameter kernel of the previous one.
 __global__ void __launch_bounds__(128) k_gb_f64(ModelConst mc, DevPtrs p, int seg_i) {
-  extern __shared__ double smem_dyn[];  // mu[n][blockDim] then reduction scratch
+  // shared: mu[N][B], beta[L][B], partials[kNumPart][B] (values indexed by a runtime
+  // l live here rather than in local memory), then the reduction scratch
+  extern __shared__ double smem_dyn[];
   const int G = mc.G, N = mc.N, L = mc.L;
   const Hyper* hy = p.hyp;
   const long long it = hy->seg_it + seg_i + 1;
@@ -362,20 +364,20 @@ __global__ void __launch_bounds__(128) k_gb_f64(ModelConst mc, DevPtrs p, int se
                          ((it - burnin) % hy->thin == 0) && hy->trace_rows < hy->trace_cap;
   const long long trace_row = hy->trace_rows;
 
+  const int B = blockDim.x;
   double* mu = smem_dyn;
+  double* bs = mu + (size_t)N * B;
+  double* ps = bs + (size_t)kMaxL * B;
   const int tid = threadIdx.x;
-  const int g = blockIdx.x * blockDim.x + tid;
+  const int g = blockIdx.x * B + tid;
   const bool active = g < G;
 
-  double part[kNumPart];
 #pragma unroll
-  for (int i = 0; i < kNumPart; ++i) part[i] = 0.0;
+  for (int i = 0; i < kNumPart; ++i) ps[i * B + tid] = 0.0;
   unsigned evals_b = 0, caps = 0, gcaps = 0, nonfin = 0;
 
   if (active) {
-    double beta[kMaxL];
-#pragma unroll
-    for (int l = 0; l < kMaxL; ++l) beta[l] = l < L ? p.beta[(size_t)l * G + g] : 0.0;
+    for (int l = 0; l < L; ++l) bs[l * B + tid] = p.beta[(size_t)l * G + g];
     double ss = 0.0;
 #pragma unroll 4
     for (int n = 0; n < N; ++n) {
@@ -399,8 +401,8 @@ __global__ void __launch_bounds__(128) k_gb_f64(ModelConst mc, DevPtrs p, int se
         p.m_gam[g] = m + (gam - m) * inv_k;
         p.q_gam[g] = q + (gam * gam - q) * inv_k;
       }
-      part[0] = log(gam);
-      part[1] = 1.0 / gam;
+      ps[0 * B + tid] = log(gam);
+      ps[1 * B + tid] = 1.0 / gam;
     }
 
     // ---- step 5: beta_gl, l = 1..L in order
@@ -410,7 +412,8 @@ __global__ void __launch_bounds__(128) k_gb_f64(ModelConst mc, DevPtrs p, int se
       const double sig2 = hy->phi[2 + L + l];
       BetaDensity f;
       f.T = p.T[e];
-      f.b0 = beta[l];
+      const double b_cur = bs[l * B + tid];
+      f.b0 = b_cur;
       f.theta = theta;
       f.hs = 0.5 / sig2;
       f.ncls = mc.ncls[l];
@@ -428,7 +431,7 @@ __global__ void __launch_bounds__(128) k_gb_f64(ModelConst mc, DevPtrs p, int se
           if (j == c) f.Q[j] += m;
       }
       Rng r(mc.seed_lo, mc.seed_hi, mc.chain, kStreamBeta, (uint32_t)((size_t)g * L + l), it32);
-      const double x0 = beta[l];
+      const double x0 = b_cur;
       double w = p.w_beta[e];
       SliceResult s = slice_update(x0, w, f, r, mc.K, mc.shrink_max);
       evals_b += s.evals;
@@ -456,7 +459,7 @@ __global__ void __launch_bounds__(128) k_gb_f64(ModelConst mc, DevPtrs p, int se
           mu[n * blockDim.x + tid] *= fac;
         }
       }
-      beta[l] = s.x;
+      bs[l * B + tid] = s.x;
       p.beta[e] = s.x;
       if (it <= burnin) {
         double waux = p.waux_beta[e];
@@ -471,146 +474,21 @@ __global__ void __launch_bounds__(128) k_gb_f64(ModelConst mc, DevPtrs p, int se
       }
       if (trace_now) p.trace_beta[(size_t)trace_row * L * G + e] = s.x;
       const double dv = s.x - theta;
-      part[2 + l] = dv;
-      part[2 + kMaxL + l] = dv * dv;
+      ps[(2 + l) * B + tid] = dv;
+      ps[(2 + kMaxL + l) * B + tid] = dv * dv;
     }
   }
 
-  double* red = smem_dyn + (size_t)N * blockDim.x;
+  double part[kNumPart];
+#pragma unroll
+  for (int i = 0; i < kNumPart; ++i) part[i] = ps[i * B + tid];
+  double* red = ps + (size_t)kNumPart * B;
   block_sum_to<kNumPart>(part, p.partial + (size_t)blockIdx.x * kNumPart, red);
   add_counters_u(p.counters, 0, evals_b, caps, gcaps, nonfin, &p.hyp->flags);
 }
 
-// ---------------------------------------------------------------- hyper kernel
-
-// log f(nu | ...) = -G lgamma(nu/2) + (G nu/2) log(nu tau/2) - (nu/2)(S1 + tau S2) on
-// (0, d), S1 = sum_g log gamma_g, S2 = sum_g 1/gamma_g (Algorithm 1 step 3, the
-// sum read as log gamma_g + tau/gamma_g, which the Inverse-Gamma(nu/2, nu tau/2)
-// prior of the gamma_g gives).
-struct NuDensity {
-  double G, d, tau, S1, S2;
-  __device__ __forceinline__ double operator()(double nu, double* aux) const {
-    *aux = 0.0;
-    if (!(nu > 0.0 && nu < d)) return -INFINITY;
-    return -G * lgamma(0.5 * nu) + 0.5 * G * nu * log(0.5 * nu * tau) -
-           0.5 * nu * (S1 + tau * S2);
-  }
-};
-
-constexpr int kHyperThreads = 64;
-
 __global__ void __launch_bounds__(kHyperThreads) k_hyper(ModelConst mc, DevPtrs p, int nblk) {
-  __shared__ double red[kHyperThreads / 32][kNumPart];
-  __shared__ double tot[kNumPart];
-  __shared__ double phi_new[kMaxP];
-  Hyper* hy = p.hyp;
-  const int L = mc.L, P = mc.P;
-  const double G = (double)mc.G;
-  const long long it = hy->it + 1;
-  const uint32_t it32 = (uint32_t)it;
-  const int tid = threadIdx.x;
-
-  // fixed-order reduction of the per-block partials
-  double acc[kNumPart];
-#pragma unroll
-  for (int i = 0; i < kNumPart; ++i) acc[i] = 0.0;
-  for (int b = tid; b < nblk; b += kHyperThreads) {
-#pragma unroll
-    for (int i = 0; i < kNumPart; ++i) acc[i] += p.partial[(size_t)b * kNumPart + i];
-  }
-#pragma unroll
-  for (int i = 0; i < kNumPart; ++i) {
-    double x = acc[i];
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) x += __shfl_down_sync(0xffffffffu, x, o);
-    if ((tid & 31) == 0) red[tid >> 5][i] = x;
-  }
-  if (tid < kMaxP) phi_new[tid] = tid < P ? hy->phi[tid] : 0.0;
-  __syncthreads();
-  if (tid < kNumPart) {
-    double s = 0.0;
-    for (int w = 0; w < kHyperThreads / 32; ++w) s += red[w][tid];
-    tot[tid] = s;
-  }
-  __syncthreads();
-
-  const double S1 = tot[0], S2 = tot[1];
-  if (tid == 0) {
-    // step 3: nu
-    const double tau_old = hy->phi[1];
-    NuDensity f{G, mc.d, tau_old, S1, S2};
-    Rng r(mc.seed_lo, mc.seed_hi, mc.chain, kStreamNu, 0u, it32);
-    const double x0 = hy->phi[0];
-    SliceResult s = slice_update(x0, hy->w_nu, f, r, mc.K, mc.shrink_max);
-    const double nu = s.x;
-    if (it <= hy->burnin) {
-      double w = hy->w_nu, waux = hy->waux_nu;
-      tune_width(w, waux, it, nu, x0, hy->burnin, hy->tune_start);
-      hy->w_nu = w;
-      hy->waux_nu = waux;
-    }
-    atomicAdd(&p.counters[FBS_CNT_EVALS_NU], (unsigned long long)s.evals);
-    if (s.capped) atomicAdd(&p.counters[FBS_CNT_SLICE_CAPS], 1ull);
-    if (s.nonfinite) {
-      atomicAdd(&p.counters[FBS_CNT_NONFINITE], 1ull);
-      atomicOr(&hy->flags, kFlagNonfinite);
-    }
-    // step 4: tau ~ Gamma(a + G nu/2, rate b + nu S2 / 2)
-    Rng rt(mc.seed_lo, mc.seed_hi, mc.chain, kStreamTau, 0u, it32);
-    bool gcap = false;
-    const double shape = mc.a + 0.5 * G * nu;
-    const double rate = mc.b + 0.5 * nu * S2;
-    const double tau = gamma_mt(shape, rt, 0, &gcap) / rate;
-    if (gcap) atomicAdd(&p.counters[FBS_CNT_GAMMA_CAPS], 1ull);
-    phi_new[0] = nu;
-    phi_new[1] = tau;
-  } else if (tid <= L) {
-    const int l = tid - 1;
-    // step 6: theta_l ~ N(v B1 / sigma^2, v), v = 1/(G/sigma^2 + 1/c^2);
-    // the partials hold B1' = sum (beta - theta_old), B2' = sum (beta - theta_old)^2
-    const double th_old = hy->phi[2 + l];
-    const double sig2 = hy->phi[2 + L + l];
-    const double B1s = tot[2 + l], B2s = tot[2 + kMaxL + l];
-    const double B1 = B1s + G * th_old;
-    const double v = 1.0 / (G / sig2 + 1.0 / mc.c2[l]);
-    const double mean = v * B1 / sig2;
-    Rng r(mc.seed_lo, mc.seed_hi, mc.chain, kStreamTheta, (uint32_t)l, it32);
-    const double th = mean + sqrt(v) * normal_bm(r, 0);
-    // step 7: sigma_l^2 ~ IG((G-1)/2, S/2) on (0, s_l^2), S = sum (beta - theta_new)^2
-    const double dl = th - th_old;
-    const double S = B2s - 2.0 * dl * B1s + G * dl * dl;
-    Rng rs(mc.seed_lo, mc.seed_hi, mc.chain, kStreamSigma, (uint32_t)l, it32);
-    bool gcap = false, tcap = false;
-    const double s2n = trunc_invgamma(0.5 * (G - 1.0), 0.5 * S, mc.s2[l], sig2, rs, &gcap, &tcap);
-    if (gcap) atomicAdd(&p.counters[FBS_CNT_GAMMA_CAPS], 1ull);
-    if (tcap) atomicAdd(&p.counters[FBS_CNT_TRUNC_CAPS], 1ull);
-    phi_new[2 + l] = th;
-    phi_new[2 + L + l] = s2n;
-  }
-  __syncthreads();
-
-  const bool mom = it > hy->burnin;
-  if (tid < P) {
-    const double x = phi_new[tid];
-    hy->phi[tid] = x;
-    if (mom) {
-      const double inv_k = 1.0 / (double)(hy->n_mom + 1);
-      const double m = hy->m_phi[tid], q = hy->q_phi[tid];
-      hy->m_phi[tid] = m + (x - m) * inv_k;
-      hy->q_phi[tid] = q + (x * x - q) * inv_k;
-    }
-    if (mom && ((it - hy->burnin) % hy->thin == 0) && hy->trace_rows < hy->trace_cap &&
-        p.trace_phi != nullptr)
-      p.trace_phi[(size_t)hy->trace_rows * P + tid] = x;
-  }
-  __syncthreads();
-  if (tid == 0) {
-    if (mom && ((it - hy->burnin) % hy->thin == 0) && hy->trace_rows < hy->trace_cap)
-      hy->trace_rows += 1;
-    if (mom) hy->n_mom += 1;
-    hy->it = it;
-    atomicAdd(&p.counters[FBS_CNT_SWEEPS], 1ull);
-  }
+  hyper_body(mc, p.partial, p.hyp, p.trace_phi, p.counters, nblk);
 }
 
 // ---------------------------------------------------------------- set-up kernels
@@ -822,29 +700,36 @@ cudaError_t launch_hyper(const ModelConst& mc, const DevPtrs& p, int nblk, cudaS
   return cudaGetLastError();
 }
 
+size_t gb_smem_bytes_f64(int N, int block) {
+  return ((size_t)N + kMaxL + kNumPart) * block * sizeof(double) +
+         (size_t)(block / 32) * kNumPart * sizeof(double);
+}
+
 cudaError_t prepare_gene_kernel(int N, int block) {
   const size_t smem = gene_smem_bytes(N, block);
   if (smem > 48 * 1024) {
     cudaError_t e = cudaFuncSetAttribute(k_gene_f64, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                          (int)smem);
     if (e != cudaSuccess) return e;
-    return cudaFuncSetAttribute(k_gb_f64, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                (int)smem);
   }
+  const size_t smem_gb = gb_smem_bytes_f64(N, block);
+  if (smem_gb > 48 * 1024)
+    return cudaFuncSetAttribute(k_gb_f64, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                (int)smem_gb);
   return cudaSuccess;
 }
 
 cudaError_t launch_eps_f64(const ModelConst& mc, const DevPtrs& p, int seg_i, cudaStream_t s) {
-  const size_t n = (size_t)mc.N * mc.G;
   const int blk = 256;
-  k_eps_f64<<<(unsigned)((n + blk - 1) / blk), blk, 0, s>>>(mc, p, seg_i);
+  const dim3 grid((unsigned)((mc.G + blk - 1) / blk), (unsigned)mc.N);
+  k_eps_f64<<<grid, blk, 0, s>>>(mc, p, seg_i);
   return cudaGetLastError();
 }
 
 cudaError_t launch_gb_f64(const ModelConst& mc, const DevPtrs& p, int block, int seg_i,
                           cudaStream_t s) {
   const int nblk = (mc.G + block - 1) / block;
-  k_gb_f64<<<nblk, block, gene_smem_bytes(mc.N, block), s>>>(mc, p, seg_i);
+  k_gb_f64<<<nblk, block, gb_smem_bytes_f64(mc.N, block), s>>>(mc, p, seg_i);
   return cudaGetLastError();
 }
 

@@ -37,6 +37,18 @@ cudaError_t launch_eps_f32(const ModelConst& mc, const DevPtrsF32& p, int seg_i,
 cudaError_t launch_gb_f32(const ModelConst& mc, const DevPtrsF32& p, int block, int seg_i,
                           cudaStream_t s);
 cudaError_t launch_seg_begin(Hyper* hy, cudaStream_t s);
+
+// batched FP32 kernels (fbs_gene_f32.cu)
+cudaError_t prepare_batch_kernels(int max_N, int gb_block);
+cudaError_t launch_eps_f32_batch(const ModelConst* mcs, const DevPtrsF32* ps, const int4* tab,
+                                 int n_blocks, int block, int seg_i, cudaStream_t s);
+cudaError_t launch_gb_f32_batch(const ModelConst* mcs, const DevPtrsF32* ps, const int2* tab,
+                                int n_blocks, int block, int max_N, int seg_i, cudaStream_t s);
+cudaError_t launch_hyper_batch(const ModelConst* mcs, const DevPtrsF32* ps, const int* nblk,
+                               int C, cudaStream_t s);
+cudaError_t launch_seg_begin_batch(const DevPtrsF32* ps, int C, cudaStream_t s);
+cudaError_t launch_set_run_batch(const DevPtrsF32* ps, int C, long long burnin,
+                                 long long tune_start, long long thin, cudaStream_t s);
 constexpr int kEpsCounterCopiesHost = kCounterCopies;
 cudaError_t launch_init_f32(const ModelConst& mc, const DevPtrsF32& p, const int32_t* y_in,
                             int gene_major, const double* pinv, double w0, int set_state,

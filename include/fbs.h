@@ -188,6 +188,82 @@ int fbs_profile(fbs_handle* h, int64_t n_iter, int64_t burnin, int64_t thin, dou
 int fbs_uniforms(uint64_t seed, uint32_t chain, uint32_t stream, uint32_t index0, int n_index,
                  uint32_t iter, uint32_t k0, int n_k, double* out);
 
+/* ---- Learned proposal for the beta_g block (FP32 handles) -------------------
+ *
+ * A multilayer perceptron (features -> 64 -> GELU -> 64 -> GELU -> Gaussian)
+ * trained on the GPU from draws of the plain sampler proposes beta_g* ~
+ * N(mu, C C^T) together with eps_g* = eps_g - X (beta_g* - beta_g), a move that
+ * keeps every log-rate h_n + eps_gn + X_n beta_g: the Poisson likelihood cancels
+ * and the move is accepted with probability
+ *   min(1, N(eps*; 0, gamma) N(beta*; theta, sigma^2) q(beta) /
+ *          (N(eps; 0, gamma) N(beta; theta, sigma^2) q(beta*))).
+ * The features are X^T (eta_g - h)/N, asinh(X^T y_g), log gamma_g, theta and
+ * log sigma, all unchanged by the move, so the step is an exact
+ * Metropolis-Hastings update, made after the eps updates and before the gamma
+ * draw by the genes that use it, with or without the slice updates of beta_g
+ * (fbs_proposal_mode).  Genes whose acceptance rate falls below a threshold
+ * during calibration keep only the slice updates; the per-gene choice is then
+ * fixed.  Parameters: one flat
+ * FP32 array W1 [64][F], b1 [64], W2 [64][64], b2 [64], W3 [K][64], b3 [K], with
+ * F = 4L+1 and K = L + L(L+1)/2; inference reads a BF16 copy and accumulates in
+ * FP32.  These calls return FBS_E_ARG for FP64 handles and batch views. */
+
+/* Number of network parameters for L columns (-1 if L is out of range). */
+int fbs_proposal_param_count(int L);
+
+/* Run n_sweeps x thin plain sweeps (fbs_run with `burnin`), and after every thin
+ * sweeps append (features, beta_g) of every gene to the device training set. */
+int fbs_proposal_collect(fbs_handle* h, int64_t n_sweeps, int64_t burnin, int64_t thin);
+
+/* Train the network on the collected pairs with Adam (Kingma & Ba) on minibatches
+ * of `batch` pairs drawn with replacement, for `epochs` passes; every forward and
+ * backward pass runs in this library's kernels.  Training works in standardised
+ * coordinates (each feature and each beta column shifted by its mean over the
+ * pairs and divided by its standard deviation); the parameters are mapped back
+ * to raw coordinates afterwards, so inference and fbs_proposal_params see the
+ * network on raw features.  The step size decays from lr to lr/20 along a
+ * cosine over the call.  *final_loss: mean Gaussian negative log-likelihood of
+ * the raw beta (without the L/2 log 2 pi constant) over the last epoch. */
+int fbs_proposal_train(fbs_handle* h, int epochs, int batch, double lr, uint64_t seed,
+                       double* final_loss);
+
+/* Run n_sweeps sweeps in which every gene attempts the learned move, then fix
+ * for every gene whether it uses the move (acceptance rate >= min_accept) or
+ * only the slice updates, and set mode 1. */
+int fbs_proposal_calibrate(fbs_handle* h, int64_t n_sweeps, int64_t burnin, double min_accept);
+
+/* 0: plain slice updates for every gene; 1: the genes the calibration selected
+ * make the learned move and then the slice updates of beta_g; 2: those genes make
+ * the learned move instead of the slice updates.  The move keeps every log-rate
+ * and the slice updates of beta_g keep eps, so mode 1 alternates between the two
+ * parameterisations of the gene's log-rates. */
+int fbs_proposal_mode(fbs_handle* h, int mode);
+
+/* Copy the FP32 parameters out (get != NULL) and/or in (set != NULL); n must equal
+ * fbs_proposal_param_count(L). */
+int fbs_proposal_params(fbs_handle* h, float* get, const float* set, int n);
+
+/* The network's outputs for every gene at the current state (host [G][K]), as
+ * the move reads them: mu (L), log of the Cholesky diagonal (L), sub-diagonal
+ * entries in row order.  Synchronous. */
+int fbs_proposal_outputs(fbs_handle* h, float* out);
+
+/* One learned move at the current state, without the other updates of a sweep:
+ * the genes the calibration selected (every gene if all_genes = 1) propose and
+ * accept or reject with the random numbers of iteration `it` (1 <= it < 2^32),
+ * counting into fbs_proposal_stats.  The state keeps every log-rate.  Synchronous. */
+int fbs_proposal_step(fbs_handle* h, int64_t it, int all_genes);
+
+/* Accepted and attempted moves since the calibration, and the number of genes
+ * that use the learned move. */
+int fbs_proposal_stats(fbs_handle* h, int64_t* accepted, int64_t* tried, int* n_mh_genes);
+
+/* One forward and backward pass of the network on a host batch (features [B][F],
+ * beta [B][L]) through the training kernels: *loss = mean negative
+ * log-likelihood, grad = its gradient (host, fbs_proposal_param_count floats). */
+int fbs_proposal_loss_grad(const float* params, int L, int B, const float* feat,
+                           const float* beta, double* loss, float* grad);
+
 /* ---- Batches: many datasets and chains in one launch -----------------------
  *
  * The conditionally independent updates of Algorithm 1 are independent across

@@ -151,6 +151,21 @@ def uniforms(seed, chain, stream, index0, n_index, it, k0, n_k, lib=None):
     return out
 
 
+def uniforms_f32(seed, chain, stream, index, it, n_k, lib=None):
+    """The FP32 form's uniforms k = 0..n_k-1 of one (stream, index, iteration):
+    Philox4x32-10 with key (seed lo, seed hi) and counter (index,
+    stream << 24 | k >> 2, it, chain); word k mod 4 of the block, x, maps to
+    (floor(x / 2^9) + 1/2) 2^-23, strictly inside (0, 1) and exact in FP32."""
+    key = (seed & 0xFFFFFFFF, seed >> 32)
+    out = np.empty(n_k, np.float64)
+    for b in range((n_k + 3) // 4):
+        w = philox((index, (stream << 24) | b, it, chain), key, lib)
+        for j in range(4):
+            if 4 * b + j < n_k:
+                out[4 * b + j] = ((w[j] >> 9) + 0.5) * 2.0 ** -23
+    return out
+
+
 def gamma_draws(shape, seed, chain, stream, index0, n, it, lib=None):
     lib = lib or load()
     out = np.empty(n, np.float64)

@@ -136,3 +136,17 @@ def mh_log_ratio(eps, beta, beta_new, gam, theta, sigma2, X, out):
     lp = (-0.5 * np.sum(eps_new ** 2, 1) / gam - 0.5 * np.sum((beta_new - theta) ** 2 / sigma2, 1)
           + 0.5 * np.sum(eps ** 2, 1) / gam + 0.5 * np.sum((beta - theta) ** 2 / sigma2, 1))
     return lp - nll(out, beta, L) + nll(out, beta_new, L)
+
+
+def mh_move(eps, beta, gam, theta, sigma2, X, out, xi, log_u):
+    """The eta-preserving move of every row from standard normals xi [G][L] and
+    log-uniforms log_u [G]: beta* = mu + C xi, eps* = eps - X (beta* - beta),
+    accepted where log_u < the log ratio of mh_log_ratio.  Returns the new eps,
+    beta, the acceptance flags and the log ratios."""
+    L = beta.shape[1]
+    mu, C = unpack(out, L)
+    beta_new = mu + np.einsum("gij,gj->gi", C, xi)
+    la = mh_log_ratio(eps, beta, beta_new, gam, theta, sigma2, X, out)
+    acc = log_u < la
+    eps_new = np.where(acc[:, None], eps - (beta_new - beta) @ X.T, eps)
+    return eps_new, np.where(acc[:, None], beta_new, beta), acc, la

@@ -32,7 +32,10 @@ EXPORTED = ("fbs_default_options", "fbs_workspace_bytes", "fbs_init", "fbs_run",
             "fbs_count_sums", "fbs_counters", "fbs_profile", "fbs_uniforms", "fbs_free",
             "fbs_last_error_string", "fbs_sweep_noalloc", "fbs_batch_init", "fbs_batch_run",
             "fbs_batch_sync", "fbs_batch_chain", "fbs_batch_set_schedule", "fbs_batch_autotune",
-            "fbs_batch_free")
+            "fbs_batch_free", "fbs_proposal_param_count", "fbs_proposal_collect",
+            "fbs_proposal_train", "fbs_proposal_calibrate", "fbs_proposal_mode",
+            "fbs_proposal_params", "fbs_proposal_stats", "fbs_proposal_loss_grad",
+            "fbs_proposal_outputs", "fbs_proposal_step")
 NOALLOC_MAX_GENES = 2048 * 128
 
 
@@ -115,6 +118,17 @@ def load_library(path: str = LIB_PATH):
                                        C.POINTER(C.c_double)]
     lib.fbs_batch_free.argtypes = [vp]
     lib.fbs_batch_free.restype = None
+    _PF = C.POINTER(C.c_float)
+    lib.fbs_proposal_param_count.argtypes = [C.c_int]
+    lib.fbs_proposal_collect.argtypes = [vp, i64, i64, i64]
+    lib.fbs_proposal_train.argtypes = [vp, C.c_int, C.c_int, C.c_double, u64, _PD]
+    lib.fbs_proposal_calibrate.argtypes = [vp, i64, i64, C.c_double]
+    lib.fbs_proposal_mode.argtypes = [vp, C.c_int]
+    lib.fbs_proposal_params.argtypes = [vp, _PF, _PF, C.c_int]
+    lib.fbs_proposal_stats.argtypes = [vp, _PI64, _PI64, C.POINTER(C.c_int)]
+    lib.fbs_proposal_loss_grad.argtypes = [_PF, C.c_int, C.c_int, _PF, _PF, _PD, _PF]
+    lib.fbs_proposal_outputs.argtypes = [vp, _PF]
+    lib.fbs_proposal_step.argtypes = [vp, C.c_int64, C.c_int]
     lib.fbs_free.argtypes = [vp]
     lib.fbs_free.restype = None
     lib.fbs_last_error_string.argtypes = []
@@ -187,6 +201,30 @@ def sweep_noalloc(X, h, priors, *, seed, it, burnin, n_mom=0, chain=0, step_out_
         setattr(a, name, ptr)
     a.stream = stream
     _check(load_library().fbs_sweep_noalloc(C.byref(a)))
+
+
+def _pf(a):
+    if a is None:
+        return None
+    assert a.dtype == np.float32 and a.flags.c_contiguous
+    return a.ctypes.data_as(C.POINTER(C.c_float))
+
+
+def proposal_param_count(L):
+    return load_library().fbs_proposal_param_count(int(L))
+
+
+def proposal_loss_grad(params, L, feat, beta):
+    """Loss and gradient of the proposal network on a host batch, through the GPU
+    training kernels."""
+    params = np.ascontiguousarray(params, np.float32)
+    feat = np.ascontiguousarray(feat, np.float32)
+    beta = np.ascontiguousarray(beta, np.float32)
+    grad = np.zeros_like(params)
+    loss = C.c_double()
+    _check(load_library().fbs_proposal_loss_grad(_pf(params), int(L), feat.shape[0], _pf(feat),
+                                                 _pf(beta), C.byref(loss), _pf(grad)))
+    return loss.value, grad
 
 
 class Sampler:
@@ -326,6 +364,44 @@ class Sampler:
         c = np.zeros(NUM_COUNTERS, np.int64)
         _check(self.lib.fbs_counters(self.h, c.ctypes.data_as(_PI64)))
         return dict(zip(COUNTER_NAMES, (int(v) for v in c)))
+
+    # --------------------------------------------------------------- learned proposal
+    def proposal_collect(self, n_sweeps, burnin=0, thin=1):
+        _check(self.lib.fbs_proposal_collect(self.h, int(n_sweeps), int(burnin), int(thin)))
+
+    def proposal_train(self, epochs=20, batch=4096, lr=1e-3, seed=1):
+        loss = C.c_double()
+        _check(self.lib.fbs_proposal_train(self.h, int(epochs), int(batch), float(lr), int(seed),
+                                           C.byref(loss)))
+        return loss.value
+
+    def proposal_calibrate(self, n_sweeps, burnin=0, min_accept=0.2):
+        _check(self.lib.fbs_proposal_calibrate(self.h, int(n_sweeps), int(burnin),
+                                               float(min_accept)))
+
+    def proposal_mode(self, mode):
+        _check(self.lib.fbs_proposal_mode(self.h, int(mode)))
+
+    def proposal_params(self, set_to=None):
+        n = proposal_param_count(self.L)
+        out = np.zeros(n, np.float32)
+        s = None if set_to is None else np.ascontiguousarray(set_to, np.float32)
+        _check(self.lib.fbs_proposal_params(self.h, _pf(out), _pf(s), n))
+        return out
+
+    def proposal_outputs(self):
+        K = self.L + self.L * (self.L + 1) // 2
+        out = np.zeros((self.G, K), np.float32)
+        _check(self.lib.fbs_proposal_outputs(self.h, _pf(out)))
+        return out
+
+    def proposal_step(self, it, all_genes=True):
+        _check(self.lib.fbs_proposal_step(self.h, int(it), int(bool(all_genes))))
+
+    def proposal_stats(self):
+        a, t, u = C.c_int64(), C.c_int64(), C.c_int()
+        _check(self.lib.fbs_proposal_stats(self.h, C.byref(a), C.byref(t), C.byref(u)))
+        return {"accepted": a.value, "tried": t.value, "mh_genes": u.value}
 
 
 class ChainView(Sampler):

@@ -128,6 +128,26 @@ int block_of(const fbs_options* o) {
 
 void fbs::set_last_error(const std::string& msg) { g_err = msg; }
 
+// Learned beta_g proposal of one FP32 handle.
+struct LearnedState {
+  int L = 0, F = 0, K = 0, np = 0;
+  float* params = nullptr;     // FP32 master parameters (flat)
+  void* params_bf16 = nullptr; // inference copy
+  float* adam_m = nullptr;
+  float* adam_v = nullptr;
+  long long adam_t = 0;
+  float* prop = nullptr;       // [K][G] proposal outputs
+  uint8_t* use_mh = nullptr;   // [G]
+  unsigned* mh_acc = nullptr;  // [G]
+  unsigned* mh_try = nullptr;  // [G]
+  float* stats = nullptr;      // column means and scales of the pairs [2F + 2L]
+  float* pair_feat = nullptr;  // [cap][F]
+  float* pair_beta = nullptr;  // [cap][L]
+  long long pair_cap = 0, pairs = 0;
+  int mode = 0;                // 1: genes with use_mh take the learned move
+  bool trained = false;
+};
+
 struct fbs_handle {
   ModelConst mc;
   DevPtrs p;        // FP64 state; in the FP32 form only the shared fields are set
@@ -148,6 +168,7 @@ struct fbs_handle {
   cudaGraphExec_t seg_exec = nullptr;
   long long trace_cap = 0;
   bool is_view = false;  // a dataset of a batch: state access only, owned by the batch
+  LearnedState* learned = nullptr;
 };
 
 namespace {
@@ -253,6 +274,7 @@ DevPtrs carve(char* base, const Layout& o, int trace_beta) {
 
 DevPtrsF32 carve_f32_ptrs(char* base, const LayoutF32& o32, int trace_beta) {
   DevPtrsF32 f;
+  memset(&f, 0, sizeof(f));  // no learned proposal until one is set up
   f.y = (const int32_t*)(base + o32.y);
   f.T = (const double*)(base + o32.T);
   f.eps = (float*)(base + o32.eps);
@@ -338,6 +360,8 @@ int sweeps_direct(fbs_handle* h, int64_t n_iter) {
     FBS_CUDA(launch_seg_begin(h->p.hyp, h->s));
     for (int64_t i = 0; i < n_iter; ++i) {
       FBS_CUDA(launch_eps_f32(h->mc, h->pf, (int)i, h->s));
+      if (h->pf.prop)
+        FBS_CUDA(launch_proposal_f32(h->mc, h->pf, h->learned->params_bf16, h->learned->prop, h->s));
       FBS_CUDA(launch_gb_f32(h->mc, h->pf, h->block, (int)i, h->s));
       FBS_CUDA(launch_hyper(h->mc, h->p, h->nblk, h->s));
     }
@@ -364,6 +388,10 @@ cudaError_t capture_segment(fbs_handle* h) {
     e = f32 ? launch_eps_f32(h->mc, h->pf, i, h->s) : launch_eps_f64(h->mc, h->p, i, h->s);
     if (e != cudaSuccess) return e;
     if (i > 0 && (e = cudaStreamWaitEvent(h->s, h->ev_h, 0)) != cudaSuccess) return e;
+    if (f32 && h->pf.prop &&
+        (e = launch_proposal_f32(h->mc, h->pf, h->learned->params_bf16, h->learned->prop,
+                                 h->s)) != cudaSuccess)
+      return e;
     e = f32 ? launch_gb_f32(h->mc, h->pf, h->block, i, h->s)
             : launch_gb_f64(h->mc, h->p, h->block, i, h->s);
     if (e != cudaSuccess) return e;
@@ -904,6 +932,20 @@ int fbs_uniforms(uint64_t seed, uint32_t chain, uint32_t stream, uint32_t index0
 void fbs_free(fbs_handle* h) {
   if (!h || h->is_view) return;
   if (h->s) cudaStreamSynchronize(h->s);
+  if (LearnedState* ls = h->learned) {
+    cudaFree(ls->params);
+    cudaFree(ls->params_bf16);
+    cudaFree(ls->adam_m);
+    cudaFree(ls->adam_v);
+    cudaFree(ls->prop);
+    cudaFree(ls->use_mh);
+    cudaFree(ls->mh_acc);
+    cudaFree(ls->mh_try);
+    cudaFree(ls->stats);
+    cudaFree(ls->pair_feat);
+    cudaFree(ls->pair_beta);
+    delete ls;
+  }
   if (h->seg_exec) cudaGraphExecDestroy(h->seg_exec);
   if (h->own_ws && h->ws) cudaFree(h->ws);
   if (h->ev_in) cudaEventDestroy(h->ev_in);
@@ -917,6 +959,395 @@ void fbs_free(fbs_handle* h) {
 
 const char* fbs_last_error_string(void) { return g_err.c_str(); }
 
+
+
+// ---------------------------------------------------------------- learned proposal
+
+}  // extern "C"
+
+namespace {
+
+int learned_setup(fbs_handle* h) {
+  if (!h) return fail(FBS_E_ARG, "handle is NULL");
+  if (h->is_view) return fail(FBS_E_ARG, "the learned proposal needs a single-chain handle");
+  if (h->prec != FBS_F32) return fail(FBS_E_ARG, "the learned proposal runs in the FBS_F32 form");
+  if (h->learned) return FBS_OK;
+  LearnedState* ls = new LearnedState();
+  const int L = h->mc.L, G = h->mc.G;
+  ls->L = L;
+  ls->F = 4 * L + 1;
+  ls->K = L + L * (L + 1) / 2;
+  ls->np = mlp_param_count(L);
+  h->learned = ls;
+  FBS_CUDA(cudaMalloc((void**)&ls->params, sizeof(float) * ls->np));
+  FBS_CUDA(cudaMalloc(&ls->params_bf16, 2 * (size_t)ls->np));
+  FBS_CUDA(cudaMalloc((void**)&ls->adam_m, sizeof(float) * ls->np));
+  FBS_CUDA(cudaMalloc((void**)&ls->adam_v, sizeof(float) * ls->np));
+  FBS_CUDA(cudaMalloc((void**)&ls->prop, sizeof(float) * ls->K * (size_t)G));
+  FBS_CUDA(cudaMalloc((void**)&ls->use_mh, (size_t)G));
+  FBS_CUDA(cudaMalloc((void**)&ls->mh_acc, sizeof(unsigned) * (size_t)G));
+  FBS_CUDA(cudaMalloc((void**)&ls->mh_try, sizeof(unsigned) * (size_t)G));
+  FBS_CUDA(cudaMalloc((void**)&ls->stats, sizeof(float) * (size_t)(2 * ls->F + 2 * L)));
+  FBS_CUDA(cudaMemsetAsync(ls->use_mh, 0, (size_t)G, h->s));
+  FBS_CUDA(cudaMemsetAsync(ls->mh_acc, 0, sizeof(unsigned) * (size_t)G, h->s));
+  FBS_CUDA(cudaMemsetAsync(ls->mh_try, 0, sizeof(unsigned) * (size_t)G, h->s));
+  FBS_CUDA(cudaMemsetAsync(ls->adam_m, 0, sizeof(float) * ls->np, h->s));
+  FBS_CUDA(cudaMemsetAsync(ls->adam_v, 0, sizeof(float) * ls->np, h->s));
+  // He-style initialisation from Philox normals on the host (deterministic).
+  std::vector<float> w(ls->np, 0.0f);
+  uint64_t state = 0x9E3779B97F4A7C15ull;
+  auto nrm = [&]() {  // Box-Muller on a splitmix64 stream
+    auto next = [&]() {
+      uint64_t z = (state += 0x9E3779B97F4A7C15ull);
+      z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+      z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+      return ((double)((z ^ (z >> 31)) >> 11) + 0.5) * 0x1p-53;
+    };
+    const double u1 = next(), u2 = next();
+    return sqrt(-2.0 * log(u1)) * cos(6.283185307179586 * u2);
+  };
+  const int H = kMlpHidden, F = ls->F, K = ls->K;
+  size_t o = 0;
+  for (int i = 0; i < H * F; ++i) w[o++] = (float)(nrm() * sqrt(2.0 / F));
+  o += H;
+  for (int i = 0; i < H * H; ++i) w[o++] = (float)(nrm() * sqrt(2.0 / H));
+  o += H;
+  for (int i = 0; i < K * H; ++i) w[o++] = (float)(nrm() * 0.1 * sqrt(1.0 / H));
+  FBS_CUDA(cudaMemcpyAsync(ls->params, w.data(), sizeof(float) * ls->np, cudaMemcpyHostToDevice,
+                           h->s));
+  FBS_CUDA(launch_to_bf16(ls->params, ls->params_bf16, ls->np, h->s));
+  FBS_CUDA(cudaStreamSynchronize(h->s));
+  return FBS_OK;
+}
+
+void learned_apply(fbs_handle* h, int mode, int mh_all) {
+  LearnedState* ls = h->learned;
+  ls->mode = mode;
+  h->pf.prop = mode ? ls->prop : nullptr;
+  h->pf.mh_replace = mode == 2 ? 1 : 0;
+  h->pf.use_mh = ls->use_mh;
+  h->pf.mh_acc = ls->mh_acc;
+  h->pf.mh_try = ls->mh_try;
+  h->pf.mh_all = mh_all;
+  if (h->seg_exec) {
+    cudaGraphExecDestroy(h->seg_exec);
+    h->seg_exec = nullptr;
+  }
+}
+
+// Scratch of one training step for batch size B.
+struct TrainBufs {
+  float *fb, *yb, *z1, *h1, *z2, *h2, *o, *dO, *dh, *dz2, *dz1, *grad, *loss;
+};
+
+int mlp_step(const float* params, int L, int B, TrainBufs& t, cudaStream_t s) {
+  const int H = kMlpHidden, F = 4 * L + 1, K = L + L * (L + 1) / 2;
+  const float* W1 = params;
+  const float* b1 = W1 + H * F;
+  const float* W2 = b1 + H;
+  const float* b2 = W2 + H * H;
+  const float* W3 = b2 + H;
+  const float* b3 = W3 + K * H;
+  float* gW1 = t.grad;
+  float* gb1 = gW1 + H * F;
+  float* gW2 = gb1 + H;
+  float* gb2 = gW2 + H * H;
+  float* gW3 = gb2 + H;
+  float* gb3 = gW3 + K * H;
+  const int split = B >= 2048 ? 32 : 1;
+  // forward
+  FBS_CUDA(launch_gemm(B, H, F, t.fb, F, 1, W1, 1, F, t.z1, H, 1, 0, s));
+  FBS_CUDA(launch_bias_gelu(t.z1, t.h1, b1, B, H, 1, s));
+  FBS_CUDA(launch_gemm(B, H, H, t.h1, H, 1, W2, 1, H, t.z2, H, 1, 0, s));
+  FBS_CUDA(launch_bias_gelu(t.z2, t.h2, b2, B, H, 1, s));
+  FBS_CUDA(launch_gemm(B, K, H, t.h2, H, 1, W3, 1, H, t.o, K, 1, 0, s));
+  FBS_CUDA(launch_bias_gelu(t.o, nullptr, b3, B, K, 0, s));
+  FBS_CUDA(cudaMemsetAsync(t.loss, 0, sizeof(float), s));
+  FBS_CUDA(launch_nll_head(t.o, t.yb, B, L, t.dO, t.loss, s));
+  // backward
+  FBS_CUDA(cudaMemsetAsync(t.grad, 0, sizeof(float) * mlp_param_count(L), s));
+  FBS_CUDA(launch_gemm(K, H, B, t.dO, 1, K, t.h2, H, 1, gW3, H, split, 0, s));
+  FBS_CUDA(launch_colsum(t.dO, B, K, gb3, s));
+  FBS_CUDA(launch_gemm(B, H, K, t.dO, K, 1, W3, H, 1, t.dh, H, 1, 0, s));
+  FBS_CUDA(launch_gelu_back(t.z2, t.dh, t.dz2, (long long)B * H, s));
+  FBS_CUDA(launch_gemm(H, H, B, t.dz2, 1, H, t.h1, H, 1, gW2, H, split, 0, s));
+  FBS_CUDA(launch_colsum(t.dz2, B, H, gb2, s));
+  FBS_CUDA(launch_gemm(B, H, H, t.dz2, H, 1, W2, H, 1, t.dh, H, 1, 0, s));
+  FBS_CUDA(launch_gelu_back(t.z1, t.dh, t.dz1, (long long)B * H, s));
+  FBS_CUDA(launch_gemm(H, F, B, t.dz1, 1, H, t.fb, F, 1, gW1, F, split, 0, s));
+  FBS_CUDA(launch_colsum(t.dz1, B, H, gb1, s));
+  return FBS_OK;
+}
+
+int train_bufs_alloc(TrainBufs& t, int L, int B) {
+  const int H = kMlpHidden, F = 4 * L + 1, K = L + L * (L + 1) / 2;
+  memset(&t, 0, sizeof(t));
+  const size_t n = (size_t)B * (F + L + 4 * H + 2 * K + 3 * H) + mlp_param_count(L) + 1;
+  float* base = nullptr;
+  FBS_CUDA(cudaMalloc((void**)&base, n * sizeof(float)));
+  float* q = base;
+  t.fb = q; q += (size_t)B * F;
+  t.yb = q; q += (size_t)B * L;
+  t.z1 = q; q += (size_t)B * H;
+  t.h1 = q; q += (size_t)B * H;
+  t.z2 = q; q += (size_t)B * H;
+  t.h2 = q; q += (size_t)B * H;
+  t.o = q; q += (size_t)B * K;
+  t.dO = q; q += (size_t)B * K;
+  t.dh = q; q += (size_t)B * H;
+  t.dz2 = q; q += (size_t)B * H;
+  t.dz1 = q; q += (size_t)B * H;
+  t.grad = q; q += mlp_param_count(L);
+  t.loss = q;
+  return FBS_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+int fbs_proposal_collect(fbs_handle* h, int64_t n_pairs_sweeps, int64_t burnin, int64_t thin) {
+  int rc = learned_setup(h);
+  if (rc) return rc;
+  if (n_pairs_sweeps < 1 || burnin < 0 || thin < 1)
+    return fail(FBS_E_ARG, "need n_pairs_sweeps >= 1, burnin >= 0, thin >= 1");
+  LearnedState* ls = h->learned;
+  const long long need = ls->pairs + n_pairs_sweeps * (long long)h->mc.G;
+  if (need > ls->pair_cap) {
+    float *f = nullptr, *b = nullptr;
+    FBS_CUDA(cudaMalloc((void**)&f, sizeof(float) * (size_t)need * ls->F));
+    FBS_CUDA(cudaMalloc((void**)&b, sizeof(float) * (size_t)need * ls->L));
+    if (ls->pairs > 0) {
+      FBS_CUDA(cudaMemcpyAsync(f, ls->pair_feat, sizeof(float) * (size_t)ls->pairs * ls->F,
+                               cudaMemcpyDeviceToDevice, h->s));
+      FBS_CUDA(cudaMemcpyAsync(b, ls->pair_beta, sizeof(float) * (size_t)ls->pairs * ls->L,
+                               cudaMemcpyDeviceToDevice, h->s));
+      FBS_CUDA(cudaStreamSynchronize(h->s));
+    }
+    cudaFree(ls->pair_feat);
+    cudaFree(ls->pair_beta);
+    ls->pair_feat = f;
+    ls->pair_beta = b;
+    ls->pair_cap = need;
+  }
+  for (int64_t k = 0; k < n_pairs_sweeps; ++k) {
+    rc = fbs_run(h, thin, burnin, 1);
+    if (rc) return rc;
+    FBS_CUDA(launch_collect_f32(h->mc, h->pf, ls->pair_feat, ls->pair_beta, ls->pairs, h->s));
+    ls->pairs += h->mc.G;
+  }
+  FBS_CUDA(cudaStreamSynchronize(h->s));
+  return FBS_OK;
+}
+
+int fbs_proposal_train(fbs_handle* h, int epochs, int batch, double lr, uint64_t seed,
+                       double* final_loss) {
+  int rc = learned_setup(h);
+  if (rc) return rc;
+  LearnedState* ls = h->learned;
+  if (ls->pairs < 1) return fail(FBS_E_ARG, "no training pairs: call fbs_proposal_collect first");
+  if (epochs < 1 || batch < 32 || !(lr > 0.0)) return fail(FBS_E_ARG, "bad epochs, batch or lr");
+  TrainBufs t;
+  rc = train_bufs_alloc(t, ls->L, batch);
+  if (rc) return rc;
+  const long long steps_per_epoch = (ls->pairs + batch - 1) / batch;
+  const long long steps = steps_per_epoch * epochs;
+  const int F = ls->F, L = ls->L;
+  // Standardise features and beta by the pairs' column statistics; parameters
+  // already trained (or set) move to those coordinates first, the initial ones
+  // are drawn for them.
+  std::vector<float> st_h(2 * F + 2 * L);
+  cudaError_t e = launch_col_stats(ls->pair_feat, ls->pair_beta, ls->pairs, F, L, ls->stats, h->s);
+  if (e == cudaSuccess)
+    e = cudaMemcpyAsync(st_h.data(), ls->stats, sizeof(float) * st_h.size(),
+                        cudaMemcpyDeviceToHost, h->s);
+  if (e == cudaSuccess && ls->trained) e = launch_fold(ls->params, ls->stats, L, 0, h->s);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(h->s);
+  double log_scale = 0.0;  // NLL of raw beta = NLL of standardised beta + sum log s_beta
+  for (int l = 0; l < L; ++l) log_scale += log((double)st_h[2 * F + L + l]);
+  double loss_epoch = 0.0;
+  for (long long st = 0; st < steps && rc == FBS_OK && e == cudaSuccess; ++st) {
+    e = launch_gather_rows(ls->pair_feat, ls->pair_beta, ls->pairs, F, L, batch, seed,
+                           (uint32_t)(ls->adam_t + 1), ls->stats, t.fb, t.yb, h->s);
+    if (e != cudaSuccess) break;
+    rc = mlp_step(ls->params, L, batch, t, h->s);
+    if (rc) break;
+    ls->adam_t += 1;
+    const float b1 = 0.9f, b2 = 0.999f;
+    const float c1 = 1.0f - powf(b1, (float)ls->adam_t), c2 = 1.0f - powf(b2, (float)ls->adam_t);
+    // cosine decay of the step size over this call, to 5% of lr
+    const double lr_t = lr * (0.05 + 0.475 * (1.0 + cos(3.141592653589793 * (double)st / steps)));
+    e = launch_adam(ls->params, t.grad, ls->adam_m, ls->adam_v, ls->np, (float)lr_t, b1, b2,
+                    1e-8f, c1, c2, h->s);
+    if (e != cudaSuccess) break;
+    if (st >= steps - steps_per_epoch) {
+      float l = 0.f;
+      e = cudaMemcpyAsync(&l, t.loss, sizeof(float), cudaMemcpyDeviceToHost, h->s);
+      if (e == cudaSuccess) e = cudaStreamSynchronize(h->s);
+      if (e != cudaSuccess) break;
+      loss_epoch += l / batch;
+    }
+  }
+  if (e == cudaSuccess && rc == FBS_OK) e = launch_fold(ls->params, ls->stats, L, 1, h->s);
+  if (e == cudaSuccess && rc == FBS_OK) e = launch_to_bf16(ls->params, ls->params_bf16, ls->np, h->s);
+  if (e == cudaSuccess && rc == FBS_OK) e = cudaStreamSynchronize(h->s);
+  cudaFree(t.fb);
+  if (rc) return rc;
+  FBS_CUDA(e);
+  ls->trained = true;
+  if (final_loss) *final_loss = loss_epoch / (double)steps_per_epoch + log_scale;
+  if (h->seg_exec) {
+    cudaGraphExecDestroy(h->seg_exec);
+    h->seg_exec = nullptr;
+  }
+  return FBS_OK;
+}
+
+int fbs_proposal_calibrate(fbs_handle* h, int64_t n_sweeps, int64_t burnin, double min_accept) {
+  int rc = learned_setup(h);
+  if (rc) return rc;
+  if (n_sweeps < 1 || burnin < 0 || !(min_accept >= 0.0 && min_accept <= 1.0))
+    return fail(FBS_E_ARG, "need n_sweeps >= 1, burnin >= 0, 0 <= min_accept <= 1");
+  LearnedState* ls = h->learned;
+  const int G = h->mc.G;
+  FBS_CUDA(cudaMemsetAsync(ls->mh_acc, 0, sizeof(unsigned) * (size_t)G, h->s));
+  FBS_CUDA(cudaMemsetAsync(ls->mh_try, 0, sizeof(unsigned) * (size_t)G, h->s));
+  learned_apply(h, 1, 1);
+  rc = fbs_run(h, n_sweeps, burnin, 1);
+  if (rc) return rc;
+  std::vector<unsigned> acc(G), tr(G);
+  FBS_CUDA(cudaMemcpyAsync(acc.data(), ls->mh_acc, sizeof(unsigned) * G, cudaMemcpyDeviceToHost,
+                           h->s));
+  FBS_CUDA(cudaMemcpyAsync(tr.data(), ls->mh_try, sizeof(unsigned) * G, cudaMemcpyDeviceToHost,
+                           h->s));
+  FBS_CUDA(cudaStreamSynchronize(h->s));
+  std::vector<uint8_t> use(G);
+  for (int g = 0; g < G; ++g) use[g] = tr[g] > 0 && acc[g] >= min_accept * tr[g] ? 1 : 0;
+  FBS_CUDA(cudaMemcpyAsync(ls->use_mh, use.data(), (size_t)G, cudaMemcpyHostToDevice, h->s));
+  FBS_CUDA(cudaMemsetAsync(ls->mh_acc, 0, sizeof(unsigned) * (size_t)G, h->s));
+  FBS_CUDA(cudaMemsetAsync(ls->mh_try, 0, sizeof(unsigned) * (size_t)G, h->s));
+  FBS_CUDA(cudaStreamSynchronize(h->s));
+  learned_apply(h, 1, 0);
+  return FBS_OK;
+}
+
+int fbs_proposal_mode(fbs_handle* h, int mode) {
+  int rc = learned_setup(h);
+  if (rc) return rc;
+  if (mode < 0 || mode > 2) return fail(FBS_E_ARG, "mode must be 0, 1 or 2");
+  FBS_CUDA(cudaStreamSynchronize(h->s));
+  learned_apply(h, mode, 0);
+  return FBS_OK;
+}
+
+int fbs_proposal_params(fbs_handle* h, float* get, const float* set, int n) {
+  int rc = learned_setup(h);
+  if (rc) return rc;
+  LearnedState* ls = h->learned;
+  if (n != ls->np) return fail(FBS_E_ARG, "n must equal the parameter count");
+  FBS_CUDA(cudaStreamSynchronize(h->s));
+  if (get)
+    FBS_CUDA(cudaMemcpy(get, ls->params, sizeof(float) * n, cudaMemcpyDeviceToHost));
+  if (set) {
+    FBS_CUDA(cudaMemcpy(ls->params, set, sizeof(float) * n, cudaMemcpyHostToDevice));
+    FBS_CUDA(launch_to_bf16(ls->params, ls->params_bf16, n, h->s));
+    FBS_CUDA(cudaStreamSynchronize(h->s));
+    ls->trained = true;
+  }
+  return FBS_OK;
+}
+
+int fbs_proposal_stats(fbs_handle* h, int64_t* accepted, int64_t* tried, int* n_mh_genes) {
+  if (!h || !h->learned) return fail(FBS_E_ARG, "the handle has no learned proposal");
+  LearnedState* ls = h->learned;
+  const int G = h->mc.G;
+  std::vector<unsigned> acc(G), tr(G);
+  std::vector<uint8_t> use(G);
+  FBS_CUDA(cudaStreamSynchronize(h->s));
+  FBS_CUDA(cudaMemcpy(acc.data(), ls->mh_acc, sizeof(unsigned) * G, cudaMemcpyDeviceToHost));
+  FBS_CUDA(cudaMemcpy(tr.data(), ls->mh_try, sizeof(unsigned) * G, cudaMemcpyDeviceToHost));
+  FBS_CUDA(cudaMemcpy(use.data(), ls->use_mh, (size_t)G, cudaMemcpyDeviceToHost));
+  int64_t a = 0, t = 0;
+  int u = 0;
+  for (int g = 0; g < G; ++g) {
+    a += acc[g];
+    t += tr[g];
+    u += use[g];
+  }
+  if (accepted) *accepted = a;
+  if (tried) *tried = t;
+  if (n_mh_genes) *n_mh_genes = u;
+  return FBS_OK;
+}
+
+int fbs_proposal_param_count(int L) { return (L < 1 || L > FBS_MAX_L) ? -1 : mlp_param_count(L); }
+
+int fbs_proposal_outputs(fbs_handle* h, float* out) {
+  int rc = learned_setup(h);
+  if (rc) return rc;
+  if (!out) return fail(FBS_E_ARG, "out is NULL");
+  LearnedState* ls = h->learned;
+  rc = enter(h);
+  if (rc) return rc;
+  DevPtrsF32 pf = h->pf;
+  pf.use_mh = ls->use_mh;
+  pf.mh_all = 1;
+  FBS_CUDA(launch_proposal_f32(h->mc, pf, ls->params_bf16, ls->prop, h->s));
+  const int G = h->mc.G, K = ls->K;
+  std::vector<float> tmp((size_t)K * G);
+  FBS_CUDA(cudaMemcpyAsync(tmp.data(), ls->prop, tmp.size() * sizeof(float),
+                           cudaMemcpyDeviceToHost, h->s));
+  FBS_CUDA(cudaStreamSynchronize(h->s));
+  for (int k = 0; k < K; ++k)
+    for (int g = 0; g < G; ++g) out[(size_t)g * K + k] = tmp[(size_t)k * G + g];
+  return leave(h);
+}
+
+int fbs_proposal_step(fbs_handle* h, int64_t it, int all_genes) {
+  int rc = learned_setup(h);
+  if (rc) return rc;
+  if (it < 1 || it > 0xFFFFFFFFll) return fail(FBS_E_ARG, "it must be in [1, 2^32)");
+  if (all_genes != 0 && all_genes != 1) return fail(FBS_E_ARG, "all_genes must be 0 or 1");
+  LearnedState* ls = h->learned;
+  rc = enter(h);
+  if (rc) return rc;
+  DevPtrsF32 pf = h->pf;
+  pf.prop = ls->prop;
+  pf.use_mh = ls->use_mh;
+  pf.mh_acc = ls->mh_acc;
+  pf.mh_try = ls->mh_try;
+  pf.mh_all = all_genes;
+  FBS_CUDA(launch_proposal_f32(h->mc, pf, ls->params_bf16, ls->prop, h->s));
+  FBS_CUDA(launch_mh_step_f32(h->mc, pf, it, h->s));
+  FBS_CUDA(cudaStreamSynchronize(h->s));
+  return leave(h);
+}
+
+int fbs_proposal_loss_grad(const float* params, int L, int B, const float* feat,
+                           const float* beta, double* loss, float* grad) {
+  if (!params || !feat || !beta || L < 1 || L > FBS_MAX_L || B < 1)
+    return fail(FBS_E_ARG, "bad arguments");
+  const int F = 4 * L + 1, np = mlp_param_count(L);
+  TrainBufs t;
+  int rc = train_bufs_alloc(t, L, B);
+  if (rc) return rc;
+  float* dp = nullptr;
+  cudaError_t e = cudaMalloc((void**)&dp, sizeof(float) * np);
+  if (e == cudaSuccess) e = cudaMemcpy(dp, params, sizeof(float) * np, cudaMemcpyHostToDevice);
+  if (e == cudaSuccess) e = cudaMemcpy(t.fb, feat, sizeof(float) * (size_t)B * F, cudaMemcpyHostToDevice);
+  if (e == cudaSuccess) e = cudaMemcpy(t.yb, beta, sizeof(float) * (size_t)B * L, cudaMemcpyHostToDevice);
+  if (e == cudaSuccess) rc = mlp_step(dp, L, B, t, 0);
+  float l = 0.f;
+  if (e == cudaSuccess && rc == FBS_OK) e = cudaMemcpy(&l, t.loss, sizeof(float), cudaMemcpyDeviceToHost);
+  if (e == cudaSuccess && rc == FBS_OK && grad)
+    e = cudaMemcpy(grad, t.grad, sizeof(float) * np, cudaMemcpyDeviceToHost);
+  cudaFree(dp);
+  cudaFree(t.fb);
+  if (rc) return rc;
+  FBS_CUDA(e);
+  if (loss) *loss = (double)l / B;
+  return FBS_OK;
+}
 
 // ---------------------------------------------------------------- batches
 

@@ -28,7 +28,15 @@ enum : uint32_t {
   kStreamBeta = 5,
   kStreamTheta = 6,
   kStreamSigma = 7,
+  kStreamMH = 8,      // learned-proposal move of beta_g
+  kStreamTrain = 9,   // minibatch sampling when training the proposal
 };
+
+// Learned proposal: hidden width of the two layers, limits of the per-gene
+// features (4L+1) and outputs (L + L(L+1)/2).
+constexpr int kMlpHidden = 64;
+constexpr int kMaxFeat = 4 * FBS_MAX_L + 1;
+constexpr int kMaxOut = FBS_MAX_L + FBS_MAX_L * (FBS_MAX_L + 1) / 2;
 
 // Class of a non-zero value of one column of X: +1, -1 or any other value.
 enum : int8_t { kClsPlus = 1, kClsMinus = 2, kClsOther = 0 };
@@ -115,6 +123,13 @@ struct DevPtrsF32 {
   float* mom_beta;    // [4][L][G]
   float* mom_gam;     // [4][G]
   float* mu;          // [N][G] Poisson means at the new eps, from the eps kernel
+  // learned proposal (null prop: plain slice updates only)
+  const float* prop;  // [n_out][G] proposal mean and Cholesky parameters per gene
+  const uint8_t* use_mh;  // [G] 1: the gene's beta moves by the learned proposal
+  unsigned* mh_acc;   // [G] accepted moves
+  unsigned* mh_try;   // [G] attempted moves
+  int mh_all;         // 1: every gene attempts the move (calibration)
+  int mh_replace;     // 1: the move replaces the slice updates of beta_g; 0: both run
   double* partial;    // [n_blocks][kNumPart]
   Hyper* hyp;
   double* trace_phi;  // [trace_cap][P]

@@ -295,8 +295,99 @@ __global__ void __launch_bounds__(256) k_eps_f32(ModelConst mc, DevPtrsF32 p, in
                (blockIdx.x + blockIdx.y) % kCounterCopies);
 }
 
+// The learned-proposal move of gene g (FP32): beta* = mu + C xi from the
+// proposal network's Gaussian, eps* = eps - X (beta* - beta), so that every
+// log-rate h_n + eps_n + X_n beta is unchanged and the Poisson likelihood cancels;
+// accepted with probability min(1, pi(eps*, beta*) q(beta) / (pi(eps, beta) q(beta*))),
+// where pi holds the Normal(0, gamma) priors of eps and the Normal(theta, sigma^2)
+// priors of beta.  The proposal depends only on quantities the move leaves
+// unchanged, so this is an exact Metropolis-Hastings step.  Uniforms 0..2L-1
+// give the normals, uniform 2L the acceptance.  Returns true when accepted.
+__device__ __forceinline__ bool mh_move_f32(const ModelConst& mc, const DevPtrsF32& p, int g,
+                                            uint32_t it32, float* bs, int B, int tid,
+                                            const Hyper* hy, float hg) {
+  const int G = mc.G, N = mc.N, L = mc.L;
+  float mu[kMaxL], C[kMaxL][kMaxL], xi[kMaxL], bn[kMaxL], d[kMaxL];
+#pragma unroll
+  for (int i = 0; i < kMaxL; ++i) {
+    mu[i] = 0.0f;
+#pragma unroll
+    for (int j = 0; j < kMaxL; ++j) C[i][j] = 0.0f;
+  }
+  int k = 2 * L;
+#pragma unroll
+  for (int i = 0; i < kMaxL; ++i) {
+    if (i < L) {
+      mu[i] = p.prop[(size_t)i * G + g];
+      C[i][i] = expf(p.prop[(size_t)(L + i) * G + g]);
+#pragma unroll
+      for (int j = 0; j < kMaxL; ++j)
+        if (j < i) C[i][j] = p.prop[(size_t)(k++) * G + g];
+    }
+  }
+  Rng4 r(mc.seed_lo, mc.seed_hi, mc.chain, kStreamMH, (uint32_t)g, it32);
+  float lq = 0.0f;  // log q(beta) - log q(beta*) = (|xi|^2 - |C^-1 (beta - mu)|^2) / 2
+  float lp = 0.0f;  // log prior ratio of beta
+#pragma unroll
+  for (int i = 0; i < kMaxL; ++i) {
+    xi[i] = 0.0f;
+    if (i < L) xi[i] = normal_bm_f(r, 2 * i);
+  }
+#pragma unroll
+  for (int i = 0; i < kMaxL; ++i) {
+    float v = mu[i];
+#pragma unroll
+    for (int j = 0; j < kMaxL; ++j)
+      if (j <= i) v += C[i][j] * xi[j];
+    bn[i] = v;
+    d[i] = i < L ? v - bs[i * B + tid] : 0.0f;
+  }
+  float u[kMaxL];
+#pragma unroll
+  for (int i = 0; i < kMaxL; ++i) {
+    u[i] = 0.0f;
+    if (i < L) {
+      float v = bs[i * B + tid] - mu[i];
+#pragma unroll
+      for (int j = 0; j < kMaxL; ++j)
+        if (j < i) v -= C[i][j] * u[j];
+      u[i] = v / C[i][i];
+      lq += 0.5f * (xi[i] * xi[i] - u[i] * u[i]);
+      const float bt = bs[i * B + tid] - (float)hy->phi[2 + i];
+      lp -= d[i] * (d[i] + 2.0f * bt) * (0.5f / (float)hy->phi[2 + L + i]);
+    }
+  }
+  // eps prior ratio: sum_n [eps_n^2 - (eps_n - X_n d)^2] / (2 gamma)
+  float se = 0.0f;
+  for (int n = 0; n < N; ++n) {
+    float xd = 0.0f;
+#pragma unroll
+    for (int l = 0; l < kMaxL; ++l)
+      if (l < L) xd += mc.Xf[n * kMaxL + l] * d[l];
+    se += xd * (2.0f * p.eps[(size_t)n * G + g] - xd);
+  }
+  const float la = se * hg + lp + lq;
+  const bool acc = __logf(r.u(2u * (uint32_t)L)) < la;
+  if (acc) {
+    for (int n = 0; n < N; ++n) {
+      float xd = 0.0f;
+#pragma unroll
+      for (int l = 0; l < kMaxL; ++l)
+        if (l < L) xd += mc.Xf[n * kMaxL + l] * d[l];
+      p.eps[(size_t)n * G + g] -= xd;
+    }
+#pragma unroll
+    for (int i = 0; i < kMaxL; ++i)
+      if (i < L) bs[i * B + tid] = bn[i];
+  }
+  return acc;
+}
+
 // Steps 2 and 5 of Algorithm 1 in the FP32 form: one thread per gene.  The
 // hyperparameter kernel of the previous iteration has finished when it runs.
+// Genes marked for the learned proposal first make its move (which keeps every
+// log-rate, so the rates mu stay valid); the slice updates of beta_g follow the
+// gamma draw, for every gene unless the move replaces them (p.mh_replace).
 __device__ __forceinline__ void gb_f32_body(const ModelConst& mc, const DevPtrsF32& p, int seg_i,
                                             int blk) {
   // shared: mu[N][B], y[N][B], beta[L][B], partials[kNumPart][B] (per-thread values
@@ -330,14 +421,26 @@ __device__ __forceinline__ void gb_f32_body(const ModelConst& mc, const DevPtrsF
 
   if (active) {
     for (int l = 0; l < L; ++l) bs[l * B + tid] = p.beta[(size_t)l * G + g];
-    float ss = 0.0f;
 #pragma unroll 4
     for (int n = 0; n < N; ++n) {
       const size_t e = (size_t)n * G + g;
-      const float x = p.eps[e];
+      mu[n * B + tid] = p.mu[e];
+      ys[n * B + tid] = (float)p.y[e];
+    }
+
+    // ---- learned-proposal move (keeps every log-rate, so mu stays valid)
+    const bool mh_gene = p.prop != nullptr && (p.mh_all || p.use_mh[g]);
+    if (mh_gene) {
+      const bool acc = mh_move_f32(mc, p, g, it32, bs, B, tid, hy, 0.5f / p.gam[g]);
+      p.mh_try[g] += 1u;
+      p.mh_acc[g] += acc ? 1u : 0u;
+    }
+
+    float ss = 0.0f;
+#pragma unroll 4
+    for (int n = 0; n < N; ++n) {
+      const float x = p.eps[(size_t)n * G + g];
       ss += x * x;
-      mu[n * blockDim.x + tid] = p.mu[e];
-      ys[n * blockDim.x + tid] = (float)p.y[e];
     }
 
     // ---- step 2: gamma_g ~ IG((N + nu)/2, (sum eps^2 + nu tau)/2)
@@ -354,8 +457,9 @@ __device__ __forceinline__ void gb_f32_body(const ModelConst& mc, const DevPtrsF
       ps[1 * B + tid] = 1.0f / gam;
     }
 
-    // ---- step 5: beta_gl, l = 1..L in order
-    for (int l = 0; l < L; ++l) {
+    // ---- step 5: beta_gl, l = 1..L in order (genes without the learned move)
+    const bool skip_slices = mh_gene && p.mh_replace;
+    for (int l = 0; l < L && !skip_slices; ++l) {
       const size_t e = (size_t)l * G + g;
       const float theta = (float)hy->phi[2 + l];
       const float sig2 = (float)hy->phi[2 + L + l];
@@ -374,8 +478,8 @@ __device__ __forceinline__ void gb_f32_body(const ModelConst& mc, const DevPtrsF
       }
       for (int n = 0; n < N; ++n) {
         const int c = mc.cls[l][n];
-        const float m = mu[n * blockDim.x + tid];
-        const float yv = ys[n * blockDim.x + tid];
+        const float m = mu[n * B + tid];
+        const float yv = ys[n * B + tid];
 #pragma unroll
         for (int j = 0; j < kMaxCls; ++j)
           if (j == c) {
@@ -406,27 +510,33 @@ __device__ __forceinline__ void gb_f32_body(const ModelConst& mc, const DevPtrsF
 #pragma unroll
           for (int j = 0; j < kMaxCls; ++j)
             if (j == c) fc = fac[j];
-          mu[n * blockDim.x + tid] *= fc;
+          mu[n * B + tid] *= fc;
         }
       }
       bs[l * B + tid] = s.x;
-      p.beta[e] = s.x;
       if (it <= burnin) {
         float waux = p.waux_beta[e];
         tune_width_f(w, waux, it, s.x, x0, burnin, tune_start);
         p.w_beta[e] = w;
         p.waux_beta[e] = waux;
       }
-      if (mom) welford_kahan(p.mom_beta, LG, e, s.x, inv_k);
-      if (trace_now) p.trace_beta[(size_t)trace_row * LG + e] = (double)s.x;
-      const float dv = s.x - theta;
+    }
+
+    // ---- the new beta_g: state, moments, trace, partial sums for steps 6-7
+    for (int l = 0; l < L; ++l) {
+      const size_t e = (size_t)l * G + g;
+      const float b = bs[l * B + tid];
+      p.beta[e] = b;
+      if (mom) welford_kahan(p.mom_beta, LG, e, b, inv_k);
+      if (trace_now) p.trace_beta[(size_t)trace_row * LG + e] = (double)b;
+      const float dv = b - (float)hy->phi[2 + l];
       ps[(2 + l) * B + tid] = dv;
       ps[(2 + kMaxL + l) * B + tid] = dv * dv;
     }
   }
 
   // ---- partial sums: error-free FP32 pair sums within the warp, FP64 beyond
-  const int lane = tid & 31, warp = tid >> 5, nwarp = blockDim.x >> 5;
+  const int lane = tid & 31, warp = tid >> 5, nwarp = B >> 5;
   double* red = reinterpret_cast<double*>(
       smem_f + (((2 * (size_t)N + kMaxL + kNumPart) * B + 1) & ~(size_t)1));
 #pragma unroll
@@ -454,6 +564,23 @@ __device__ __forceinline__ void gb_f32_body(const ModelConst& mc, const DevPtrsF
 
 __global__ void __launch_bounds__(128) k_gb_f32(ModelConst mc, DevPtrsF32 p, int seg_i) {
   gb_f32_body(mc, p, seg_i, blockIdx.x);
+}
+
+// The learned move alone, at the current state, for the genes that use it (every
+// gene when p.mh_all), with the random numbers of iteration `it`.
+__global__ void __launch_bounds__(128) k_mh_step_f32(ModelConst mc, DevPtrsF32 p, long long it) {
+  __shared__ float bs[kMaxL * 128];
+  const int B = blockDim.x, tid = threadIdx.x;
+  const int g = blockIdx.x * B + tid;
+  if (g >= mc.G || !(p.mh_all || p.use_mh[g])) return;
+  const int G = mc.G, L = mc.L;
+  for (int l = 0; l < L; ++l) bs[l * B + tid] = p.beta[(size_t)l * G + g];
+  const bool acc = mh_move_f32(mc, p, g, (uint32_t)it, bs, B, tid, p.hyp, 0.5f / p.gam[g]);
+  p.mh_try[g] += 1u;
+  if (acc) {
+    p.mh_acc[g] += 1u;
+    for (int l = 0; l < L; ++l) p.beta[(size_t)l * G + g] = bs[l * B + tid];
+  }
 }
 
 __global__ void k_seg_begin(Hyper* hy) {
@@ -627,6 +754,13 @@ cudaError_t launch_gb_f32(const ModelConst& mc, const DevPtrsF32& p, int block, 
                           cudaStream_t s) {
   const int nblk = (mc.G + block - 1) / block;
   k_gb_f32<<<nblk, block, gene_smem_bytes_f32(mc.N, block), s>>>(mc, p, seg_i);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_mh_step_f32(const ModelConst& mc, const DevPtrsF32& p, long long it,
+                              cudaStream_t s) {
+  const int block = 128;
+  k_mh_step_f32<<<(mc.G + block - 1) / block, block, 0, s>>>(mc, p, it);
   return cudaGetLastError();
 }
 

@@ -38,6 +38,35 @@ cudaError_t launch_gb_f32(const ModelConst& mc, const DevPtrsF32& p, int block, 
                           cudaStream_t s);
 cudaError_t launch_seg_begin(Hyper* hy, cudaStream_t s);
 
+cudaError_t launch_mh_step_f32(const ModelConst& mc, const DevPtrsF32& p, long long it,
+                              cudaStream_t s);
+
+// learned proposal (fbs_learned.cu)
+int mlp_param_count(int L);
+cudaError_t launch_proposal_f32(const ModelConst& mc, const DevPtrsF32& p, const void* w_bf16,
+                                float* out, cudaStream_t s);
+cudaError_t launch_collect_f32(const ModelConst& mc, const DevPtrsF32& p, float* feat,
+                               float* beta, long long row, cudaStream_t s);
+cudaError_t launch_gather_rows(const float* feat, const float* beta, long long M, int F, int L,
+                               int Bsz, uint64_t seed, uint32_t step, const float* st, float* fb,
+                               float* yb, cudaStream_t s);
+cudaError_t launch_col_stats(const float* feat, const float* beta, long long M, int F, int L,
+                             float* st, cudaStream_t s);
+cudaError_t launch_fold(float* params, const float* st, int L, int to_raw, cudaStream_t s);
+cudaError_t launch_gemm(int M, int Nn, int Kk, const float* A, long long sai, long long sak,
+                        const float* B, long long sbk, long long sbj, float* C, long long ldc,
+                        int split_k, int accumulate, cudaStream_t s);
+cudaError_t launch_bias_gelu(float* Z, float* H, const float* b, int rows, int cols, int act,
+                             cudaStream_t s);
+cudaError_t launch_gelu_back(const float* Z, const float* dH, float* dZ, long long n,
+                             cudaStream_t s);
+cudaError_t launch_nll_head(const float* O, const float* Y, int Bsz, int L, float* dO,
+                            float* loss_sum, cudaStream_t s);
+cudaError_t launch_colsum(const float* D, int rows, int cols, float* g, cudaStream_t s);
+cudaError_t launch_adam(float* w, const float* g, float* m, float* v, int n, float lr, float b1,
+                        float b2, float eps, float c1, float c2, cudaStream_t s);
+cudaError_t launch_to_bf16(const float* a, void* b, int n, cudaStream_t s);
+
 // batched FP32 kernels (fbs_gene_f32.cu)
 cudaError_t prepare_batch_kernels(int max_N, int gb_block);
 cudaError_t launch_eps_f32_batch(const ModelConst* mcs, const DevPtrsF32* ps, const int4* tab,

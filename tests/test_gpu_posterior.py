@@ -80,22 +80,31 @@ def _compare(a, b, ess, label):
         assert np.all(z[well] < 6.0), info
 
 
+_ORACLE_RUNS = {}
+
+
+def _oracle_runs(pool, cfg, G, orc_iters):
+    """Posterior means of the oracle's chains (computed once per configuration)
+    and the summed effective sample sizes of the beta_gl.  The oracle's burn-in
+    (a third of the run, 800 sweeps) spans more than 7 autocorrelation times of
+    the slowest hyperparameter."""
+    key = (cfg, G, orc_iters)
+    if key not in _ORACLE_RUNS:
+        orc_burn = orc_iters // 3
+        jobs = [(cfg, G, orc_iters, orc_burn, 101, c) for c in range(N_ORACLE_CHAINS)]
+        res = pool.map(_oracle_chain, jobs)
+        orc = {"phi": _stats([r[0] for r in res]), "beta": _stats([r[1] for r in res])}
+        _ORACLE_RUNS[key] = (orc, sum(r[2] for r in res))
+    return _ORACLE_RUNS[key]
+
+
 @pytest.mark.parametrize("cfg,G,orc_iters,gpu_iters", [(0, 1000, 2400, 12000),
                                                        (1, 1000, 2400, 12000)])
 def test_long_runs_agree_with_oracle(pool, cfg, G, orc_iters, gpu_iters):
-    """FP64 GPU vs oracle, FP32 GPU vs oracle and FP32 GPU vs FP64 GPU.  The
-    oracle's burn-in (800 sweeps) spans more than 7 autocorrelation times of the
-    slowest hyperparameter."""
-    orc_burn = orc_iters // 3
-    jobs = [(cfg, G, orc_iters, orc_burn, 101, c) for c in range(N_ORACLE_CHAINS)]
-    res = pool.map(_oracle_chain, jobs)
-    o_phi = _stats([r[0] for r in res])
-    o_beta = _stats([r[1] for r in res])
-    ess = sum(r[2] for r in res)
+    """FP64 GPU vs oracle, FP32 GPU vs oracle and FP32 GPU vs FP64 GPU."""
+    orc, ess = _oracle_runs(pool, cfg, G, orc_iters)
     assert (ess >= 100).mean() > 0.5
-
     d = synthetic.make_config(cfg, G=G)
-    orc = {"phi": o_phi, "beta": o_beta}
     gpu_burn, thin = gpu_iters // 6, 10
     rows = (gpu_iters - gpu_burn) // thin
     runs = {}
@@ -117,3 +126,44 @@ def test_long_runs_agree_with_oracle(pool, cfg, G, orc_iters, gpu_iters):
         runs[precision] = {"phi": _stats(phis), "beta": _stats(betas)}
         _compare(runs[precision], orc, ess, f"cfg {cfg} precision {precision} vs oracle")
     _compare(runs[fbs.FBS_F32], runs[fbs.FBS_F64], ess, f"cfg {cfg} FP32 vs FP64")
+
+
+def test_learned_long_runs_agree_with_oracle(pool):
+    """The FP32 sampler with the learned move of the beta_g block against the
+    oracle's plain sampler at the paper's design (N = 16, L = 5).  The network is
+    trained once, on draws of one chain started from the generating values; each
+    of the 16 chains then calibrates (every gene tries the move for 100 sweeps of
+    the burn-in) and runs with its own seed."""
+    cfg, G, orc_iters, gpu_iters = 1, 1000, 2400, 12000
+    orc, ess = _oracle_runs(pool, cfg, G, orc_iters)
+    d = synthetic.make_config(cfg, G=G)
+    t = fbs.Sampler(d["y"], d["X"], d["h"], d["priors"], seed=77, precision=fbs.FBS_F32)
+    t.set_state(it=0, **_truth_state(d))
+    t.proposal_collect(300, burnin=300, thin=2)
+    t.proposal_train(epochs=20, batch=2048, lr=2e-3, seed=77)
+    params = t.proposal_params()
+    t.close()
+
+    gpu_burn, thin = gpu_iters // 6, 10
+    rows = (gpu_iters - gpu_burn) // thin
+    phis, betas = [], []
+    for c in range(N_GPU_CHAINS):
+        g = fbs.Sampler(d["y"], d["X"], d["h"], d["priors"], seed=3030, chain=c,
+                        precision=fbs.FBS_F32, trace_cap=rows, trace_beta=1)
+        g.set_state(it=0, **_truth_state(d))
+        g.proposal_params(set_to=params)
+        g.proposal_calibrate(100, burnin=gpu_burn, min_accept=0.2)
+        g.run(gpu_iters - 100, burnin=gpu_burn, thin=thin)
+        g.sync()
+        st = g.proposal_stats()
+        assert st["mh_genes"] > 0.8 * G
+        assert st["accepted"] > 0.3 * st["tried"]
+        tr = g.trace(beta=True)
+        assert tr["phi"].shape[0] == rows
+        cnt = g.counters()
+        assert cnt["slice_caps"] == 0 and cnt["nonfinite"] == 0
+        phis.append(tr["phi"])
+        betas.append(tr["beta"])
+        g.close()
+    learned = {"phi": _stats(phis), "beta": _stats(betas)}
+    _compare(learned, orc, ess, "learned FP32 vs oracle")

@@ -97,3 +97,61 @@ def test_features_invariant_under_the_move():
     b = P.features(eps_new, beta_new, *args)
     assert a.shape == (3, P.n_features(L))
     np.testing.assert_allclose(a, b, rtol=1e-12, atol=1e-12)
+
+
+def test_move_keeps_the_exact_conditional_of_beta():
+    """Given eta (and gamma, theta, sigma^2) the conditional of beta is Gaussian
+    with precision X^T X / gamma + diag(1/sigma^2) and mean that precision's
+    inverse times (X^T (eta - h) / gamma + theta / sigma^2).  Rows drawn from it
+    and moved with a deliberately poor proposal must still follow it: the mean
+    and the covariance of the moved rows are checked, and the rate must be
+    neither 0 nor 1 so that both branches run.  A sign error in either prior term
+    or in the proposal ratio shifts the moved rows."""
+    rng = np.random.default_rng(11)
+    X = paper_design(2)[:, :3]
+    N, L = X.shape
+    gam, theta, sigma2 = 0.2, np.array([1.0, -0.5, 0.3]), np.array([0.5, 0.2, 0.8])
+    lin = rng.normal(0.0, 1.0, N)                       # eta - h, held fixed
+    prec = X.T @ X / gam + np.diag(1.0 / sigma2)
+    cov = np.linalg.inv(prec)
+    mean = cov @ (X.T @ lin / gam + theta / sigma2)
+    G = 200000
+    beta = rng.multivariate_normal(mean, cov, G)
+    eps = lin[None, :] - beta @ X.T
+    Lc = 1.3 * np.linalg.cholesky(cov)                      # too wide
+    out = np.zeros((G, P.n_outputs(L)))
+    out[:, :L] = mean + 0.4 * np.sqrt(np.diag(cov))          # biased
+    out[:, L:2 * L] = np.log(np.diag(Lc))
+    out[:, 2 * L:] = Lc[np.tril_indices(L, -1)]             # row order
+    xi = rng.normal(size=(G, L))
+    log_u = np.log(rng.uniform(size=G))
+    e2, b2, acc, la = P.mh_move(eps, beta, np.full(G, gam), theta, sigma2, X, out, xi, log_u)
+    np.testing.assert_allclose(e2 + b2 @ X.T, lin[None, :].repeat(G, 0), atol=1e-10)
+    rate = acc.mean()
+    assert 0.2 < rate < 0.95, rate
+    se = np.sqrt(np.diag(cov) / G)
+    assert np.all(np.abs(b2.mean(0) - mean) < 5 * se), (b2.mean(0) - mean) / se
+    c2 = np.cov(b2.T)
+    # standard error of a sample covariance entry: sqrt((s_ii s_jj + s_ij^2) / G)
+    sec = np.sqrt((np.outer(np.diag(cov), np.diag(cov)) + cov ** 2) / G)
+    assert np.all(np.abs(c2 - cov) < 5 * sec), (c2 - cov) / sec
+
+
+def test_move_with_a_proposal_at_the_current_point_accepts_by_the_uniform():
+    """If mu + C xi reproduces the current beta, the ratio is zero: the move
+    accepts exactly when log u < 0 and leaves eps unchanged."""
+    rng = np.random.default_rng(12)
+    X = paper_design(2)
+    N, L = X.shape
+    G = 4
+    beta = rng.normal(0, 0.5, (G, L))
+    eps = rng.normal(0, 0.3, (G, N))
+    out = rng.normal(0, 0.3, (G, P.n_outputs(L)))
+    mu, C = P.unpack(out, L)
+    xi = np.linalg.solve(C, (beta - mu)[..., None])[..., 0]
+    e2, b2, acc, la = P.mh_move(eps, beta, np.full(G, 0.3), np.zeros(L), np.ones(L), X, out, xi,
+                                np.array([-1e-9, -1e-9, 1e-9, 1e-9]))
+    np.testing.assert_allclose(la, 0.0, atol=1e-9)
+    assert list(acc) == [True, True, False, False]
+    np.testing.assert_allclose(e2, eps, atol=1e-12)
+    np.testing.assert_allclose(b2, beta, atol=1e-12)

@@ -7,6 +7,15 @@ paper's 16 x 5 design), G=40000 genes, L=5, theta=(4,0,0,0,0),
 sigma=(2,.5,.3,.2,.2), tau=0.1, nu=3; priors c=s=10, a=b=1, d=10; run length
 20000 iterations with 10000 burn-in and thin 10.
 
+Forms: "f64" (the plain method in FP64), "f32" (FP32 slice log densities, FP64
+reductions and hyperparameters, Kahan-compensated FP32 moments) and "learned"
+(the f32 form plus the learned beta_g proposal: 2e6 training pairs drawn by the
+plain sampler during burn-in, trained on the GPU, then an eta-preserving
+Metropolis-Hastings move before the slice updates of beta_g).  `--form` picks
+the form of the headline line (default: learned); the configured job runs for
+every form unless --forms headline, so that the line carries each form's
+iterations/s and ESS/s next to the plain FP64 form's.
+
 Metric: Gibbs iterations per second (value, device-timed) and min ESS per
 second over all G*L beta.  A "step" is `--sweeps-per-step` consecutive Gibbs
 sweeps (one fbs_run call replaying the captured CUDA graph); L2 is flushed
@@ -49,13 +58,15 @@ def parse():
     ap.add_argument("--steps", type=int, default=10)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=("ours", "reference"), default="ours")
-    ap.add_argument("--precision", choices=("f64", "f32"), default="f64")
+    ap.add_argument("--form", choices=("f64", "f32", "learned"), default="learned")
+    ap.add_argument("--forms", choices=("all", "headline"), default="all",
+                    help="run the configured job (ESS) for every form or only the headline one")
     ap.add_argument("--block", type=int, default=0, help="threads per block of the gene kernel")
     ap.add_argument("--workload", choices=("paper", "batch"), default="paper",
                     help="paper: N=16 G=40000 L=5 (the metric's workload); batch: 64 datasets "
                          "of uneven N, G, L in one set of launches")
     ap.add_argument("--sweeps-per-step", type=int, default=100)
-    ap.add_argument("--no-ess", action="store_true", help="skip the 20000-iteration ESS job")
+    ap.add_argument("--no-ess", action="store_true", help="skip the 20000-iteration ESS jobs")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-seconds", type=float, default=12.0)
     ap.add_argument("--tune-sweeps", type=int, default=2000,
@@ -256,6 +267,88 @@ def run_batch(args):
 
 
 # --------------------------------------------------------------------------- our arm
+FORM_TEXT = {
+    "f64": "plain method, FP64",
+    "f32": "FP32 slice log densities; FP64 reductions and hyperparameters; "
+           "Kahan-compensated FP32 moments",
+    "learned": "the f32 form plus the learned beta_g proposal (eta-preserving MH move "
+               "before the slice updates of beta_g)",
+}
+PAIR_SWEEPS = 50          # x thin 2 x G = 2e6 training pairs at G = 40000
+TRAIN = {"epochs": 15, "batch": 4096, "lr": 2e-3}
+CALIBRATE_SWEEPS = 100
+
+
+def new_sampler(fbs, data, y, form, seed, chain, block, **kw):
+    prec = fbs.FBS_F64 if form == "f64" else fbs.FBS_F32
+    return fbs.Sampler(y, data["X"], data["h"], data["priors"], seed=seed, chain=chain,
+                       precision=prec, block=block, **kw)
+
+
+def ess_job(fbs, torch, data, y_host, form, seed, chain, block, S):
+    """The configured job (20000 iterations, burn-in 10000, thin 10) through the
+    public API with pinned host counts: init upload, the sweeps in fbs_run calls of
+    S iterations with phi read back after each, moments read back at the end.  For
+    the learned form the job also collects the training pairs (after half the
+    burn-in), trains the network and calibrates, all inside the timed job."""
+    spec = data["spec"]
+    iters, burnin, thin = spec["iters"], spec["burnin"], spec["thin"]
+    rows = (iters - burnin) // thin
+    stream = torch.cuda.current_stream()
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    smp = new_sampler(fbs, data, y_host, form, seed, chain, block, trace_cap=rows, trace_beta=1)
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    ev0.record(stream)
+    done, phi_reads, extra = 0, 0, {}
+
+    def advance(upto):
+        nonlocal done, phi_reads
+        while done < upto:
+            n = min(S, upto - done)
+            smp.run(n, burnin=burnin, thin=thin)
+            smp.phi()
+            phi_reads += 1
+            done += n
+
+    if form == "learned":
+        advance(burnin // 2)
+        tt = time.perf_counter()
+        smp.proposal_collect(PAIR_SWEEPS, burnin=burnin, thin=2)
+        done += 2 * PAIR_SWEEPS
+        loss = smp.proposal_train(seed=seed, **TRAIN)
+        smp.proposal_calibrate(CALIBRATE_SWEEPS, burnin=burnin, min_accept=0.2)
+        done += CALIBRATE_SWEEPS
+        extra = {"train_pairs": PAIR_SWEEPS * data["y"].shape[0], "train_loss": loss,
+                 "collect_train_calibrate_s": time.perf_counter() - tt,
+                 "mh_genes": smp.proposal_stats()["mh_genes"]}
+    advance(iters)
+    ev1.record(stream)
+    mom = smp.moments()
+    torch.cuda.synchronize()
+    wall = time.perf_counter() - t0
+    dev_s = ev0.elapsed_time(ev1) / 1e3
+    e = smp.beta_ess()
+    if form == "learned":
+        st = smp.proposal_stats()
+        extra["accept_rate"] = st["accepted"] / max(1, st["tried"])
+        extra["params"] = smp.proposal_params()
+    h2d = y_host.nbytes + data["X"].nbytes + data["h"].nbytes
+    d2h = phi_reads * 8 * (2 * spec["L"] + 2) + sum(np.asarray(v).nbytes for k, v in mom.items()
+                                                     if k != "count")
+    smp.close()
+    del smp
+    torch.cuda.empty_cache()
+    out = {"iters_per_s_e2e": iters / wall, "iters_per_s_job_device": iters / dev_s,
+           "job_wall_s": wall, "min_ess": float(e.min()), "p05_ess": float(np.percentile(e, 5)),
+           "median_ess": float(np.median(e)), "ess_rows": rows,
+           "min_ess_per_s": float(e.min()) / wall, "p05_ess_per_s": float(np.percentile(e, 5)) / wall,
+           "median_ess_per_s": float(np.median(e)) / wall,
+           "h2d_bytes_per_step": h2d / phi_reads, "d2h_bytes_per_step": d2h / phi_reads}
+    out.update(extra)
+    return out
+
+
 def main():
     args = parse()
     world = int(os.environ.get("WORLD_SIZE", "1"))
@@ -287,7 +380,7 @@ def main():
     N, G, L = spec["N"], spec["G"], spec["L"]
     S = args.sweeps_per_step
     seed = 20160621
-    prec = fbs.FBS_F32 if args.precision == "f32" else fbs.FBS_F64
+    form = args.form
     stream = torch.cuda.current_stream()
 
     def barrier():
@@ -295,48 +388,29 @@ def main():
             dist.barrier()
         torch.cuda.synchronize()
 
-    # ---- the configured job through the public API with host buffers (e2e),
-    #      which also yields the beta trace for the ESS metric
+    # ---- the configured job of each form, end to end with host buffers
     y_pinned = torch.from_numpy(np.ascontiguousarray(data["y"])).pin_memory()
     y_host = y_pinned.numpy()
-    iters, burnin, thin = spec["iters"], spec["burnin"], spec["thin"]
-    trace_rows = (iters - burnin) // thin
-    ess = None
-    job = None
+    burnin, thin = spec["burnin"], spec["thin"]
+    forms = {}
     if not args.no_ess:
-        barrier()
-        t0 = time.perf_counter()
-        smp = fbs.Sampler(y_host, data["X"], data["h"], data["priors"], seed=seed, chain=rank,
-                          trace_cap=trace_rows, trace_beta=1, precision=prec, block=args.block)
-        ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-        ev0.record(stream)
-        phi_reads = 0
-        for _ in range(iters // S):
-            smp.run(S, burnin=burnin, thin=thin)
-            smp.phi()
-            phi_reads += 1
-        ev1.record(stream)
-        mom = smp.moments()
-        torch.cuda.synchronize()
-        wall = time.perf_counter() - t0
-        job_device_s = ev0.elapsed_time(ev1) / 1e3
-        e = smp.beta_ess()
-        ess = {"min": float(e.min()), "p01": float(np.percentile(e, 1)),
-               "median": float(np.median(e)), "rows": trace_rows}
-        h2d = y_host.nbytes + data["X"].nbytes + data["h"].nbytes
-        d2h = phi_reads * 8 * (2 * L + 2) + sum(np.asarray(v).nbytes for k, v in mom.items()
-                                                 if k != "count")
-        job = {"wall_s": wall, "device_s": job_device_s, "steps": phi_reads,
-               "h2d": h2d, "d2h": d2h}
-        smp.close()
-        del smp
-        torch.cuda.empty_cache()
+        order = ["f64", "f32", "learned"] if args.forms == "all" else [form]
+        for f in order:
+            barrier()
+            forms[f] = ess_job(fbs, torch, data, y_host, f, seed, rank, args.block, S)
+    params = forms.get("learned", {}).pop("params", None)
 
     # ---- device-timed throughput: W warm-up + K timed steps of S sweeps
-    smp = fbs.Sampler(data["y"], data["X"], data["h"], data["priors"], seed=seed + 1, chain=rank,
-                      precision=prec, block=args.block)
+    smp = new_sampler(fbs, data, data["y"], form, seed + 1, rank, args.block)
     tb = args.tune_sweeps // 2
     smp.run(args.tune_sweeps, burnin=tb, thin=thin)   # tune the slice widths (burn-in)
+    if form == "learned":
+        if params is None:
+            smp.proposal_collect(PAIR_SWEEPS, burnin=tb, thin=2)
+            smp.proposal_train(seed=seed, **TRAIN)
+        else:
+            smp.proposal_params(set_to=params)
+        smp.proposal_calibrate(CALIBRATE_SWEEPS, burnin=tb, min_accept=0.2)
     flush = torch.empty(L2_FLUSH_BYTES, dtype=torch.uint8, device="cuda")
     for i in range(args.warmup):
         flush.fill_(i & 0xFF)
@@ -365,19 +439,20 @@ def main():
     sweeps_all = args.steps * S * world
     value = sweeps_all / total_s
 
-    # ---- roofline of the dominant (per-gene) kernel: direct launches with
-    #      CUDA events on its launching stream
-    ms_k1, ms_k2, ms_hyper = smp.profile(S, burnin=tb, thin=thin)
+    # ---- roofline of the per-gene kernels: direct launches with CUDA events on
+    #      their launching stream
+    ms_k1, ms_k2, ms_hyper, ms_prop = smp.profile(S, burnin=tb, thin=thin)
     ms_gene = ms_k1 + ms_k2
     peak, peak_kind = measured_peaks()
-    bpg = bytes_per_gene(N, L, args.precision)
+    prec_name = "f64" if form == "f64" else "f32"
+    bpg = bytes_per_gene(N, L, prec_name)
     achieved = bpg * G / (ms_gene / 1e3) / 1e9
     evals = {k: (c1[k] - c0[k]) / (args.steps * S) for k in ("evals_eps", "evals_beta",
                                                                "evals_nu")}
     ev_launch = evals["evals_eps"] + evals["evals_beta"]
     hbm = {"achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
            "bytes_per_gene": bpg, "genes_per_launch": G, "peak_source": peak_kind}
-    if args.precision == "f64":
+    if form == "f64":
         tflops = ev_launch * FP64_FLOP_PER_EVAL / (ms_gene / 1e3) / 1e12
         roofline = {"bound": "alu", "achieved": tflops, "peak": FP64_PEAK_TFLOPS,
                     "unit": "TFLOP/s (FP64)", "frac": tflops / FP64_PEAK_TFLOPS,
@@ -390,42 +465,53 @@ def main():
         roofline = dict(hbm, bound="hbm", traffic=None, kernel="k_eps_f32 + k_gb_f32",
                         kernel_ms=ms_gene, eps_kernel_ms=ms_k1, gb_kernel_ms=ms_k2,
                         hyper_kernel_ms=ms_hyper, evals_per_launch=ev_launch)
+        if form == "learned":
+            roofline["proposal_kernel_ms"] = ms_prop
+    st = smp.proposal_stats() if form == "learned" else None
     smp.close()
 
     if rank != 0:
         if world > 1:
             dist.destroy_process_group()
         return
+    launches_per_sweep = 4 if form == "learned" else 3
     line = {
         "metric": METRIC, "value": value, "unit": "iters/s", "n_gpus": world,
         "steps": args.steps, "warmup": args.warmup,
         "ms_per_step": statistics.mean(step_ms), "higher_is_better": True, "scaling": "weak",
-        "vs_baseline": None, "dtype": args.precision, "data": "synthetic",
+        "vs_baseline": None, "dtype": prec_name, "data": "synthetic",
         "config": {"workload": "RNA-seq Gibbs sweep N=16 G=40000 L=5 (paper design), "
                                "one chain per GPU",
-                   "form": "FP64" if args.precision == "f64" else
-                           "FP32 log densities; FP64 reductions and hyperparameters; "
-                           "Kahan-compensated FP32 moments",
+                   "form": form, "form_text": FORM_TEXT[form],
                    "N": N, "G": G, "L": L, "sweeps_per_step": S,
                    "l2": "256 MiB write before every timed step; state (~40 MB) stays "
                          "L2-resident within a step",
-                   "job": f"{iters} iterations, burn-in {burnin}, thin {thin}",
+                   "job": f"{spec['iters']} iterations, burn-in {burnin}, thin {thin}",
                    "parallelism": f"{world} independent chain(s)"},
-        "gpu_launches": args.steps * (2 * S + 1),
+        "gpu_launches": args.steps * (launches_per_sweep * S + 1),
         "clocks": clk,
         "roofline": roofline,
         "evals_per_sweep": evals,
     }
-    if job is not None:
-        line["e2e"] = {"value": iters * world / job["wall_s"], "unit": "iters/s",
-                       "h2d_bytes_per_step": job["h2d"] / job["steps"],
-                       "d2h_bytes_per_step": job["d2h"] / job["steps"],
+    if st is not None:
+        line["learned_timed"] = {"mh_genes": st["mh_genes"],
+                                 "accept_rate": st["accepted"] / max(1, st["tried"])}
+    if form in forms:
+        h = forms[form]
+        line["e2e"] = {"value": h["iters_per_s_e2e"] * world, "unit": "iters/s",
+                       "h2d_bytes_per_step": h["h2d_bytes_per_step"],
+                       "d2h_bytes_per_step": h["d2h_bytes_per_step"],
                        "what": "the whole configured job through fbs_init/fbs_run/fbs_moments "
-                               "with pinned host counts: init upload, 20000 sweeps, phi read "
-                               "back after every step, moments read back at the end"}
-        line["min_ess_per_sec"] = ess["min"] / job["wall_s"]
-        line["ess"] = ess | {"job_wall_s": job["wall_s"], "job_device_s": job["device_s"],
-                             "job_iters_per_s_device": iters / job["device_s"]}
+                               "with pinned host counts: init upload, 20000 sweeps (for the "
+                               "learned form also pair collection, training and calibration), "
+                               "phi read back after every step, moments read back at the end"}
+        line["min_ess_per_sec"] = h["min_ess_per_s"]
+        line["forms"] = forms
+        if "f64" in forms:
+            b = forms["f64"]
+            line["vs_plain_f64"] = {
+                k: h[k] / b[k] for k in ("iters_per_s_e2e", "min_ess_per_s", "p05_ess_per_s",
+                                         "median_ess_per_s")}
     if not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline(data, args.cpu_seconds, G)
     print(json.dumps(line), flush=True)

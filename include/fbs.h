@@ -177,9 +177,10 @@ int fbs_counters(fbs_handle* h, int64_t* out);
 
 /* Runs n_iter iterations launching the sweep kernels one at a time (no
  * graph, no overlap) with CUDA events around each launch on the launching
- * stream, and writes the mean durations in milliseconds to ms[0..2]: the eps
- * kernel, the gamma/beta kernel and the hyperparameter kernel.  The chain advances as with
- * fbs_run.  Synchronous. */
+ * stream, and writes the mean durations in milliseconds to ms[0..3]: the eps
+ * kernel, the gamma/beta kernel, the hyperparameter kernel and the learned
+ * proposal's network (0 when the handle does not use it).  The chain advances
+ * as with fbs_run.  Synchronous. */
 int fbs_profile(fbs_handle* h, int64_t n_iter, int64_t burnin, int64_t thin, double* ms);
 
 /* Philox uniforms exactly as the sampler draws them: out[i*n_k + k] is uniform

@@ -292,8 +292,9 @@ class Sampler:
         _check(self.lib.fbs_sync(self.h))
 
     def profile(self, n_iter, burnin=0, thin=1):
-        """Mean per-launch milliseconds: (eps or fused gene kernel, gamma/beta kernel, hyper)."""
-        ms = np.zeros(3)
+        """Mean per-launch milliseconds: (eps kernel, gamma/beta kernel, hyperparameter
+        kernel, learned-proposal network or 0)."""
+        ms = np.zeros(4)
         _check(self.lib.fbs_profile(self.h, int(n_iter), int(burnin), int(thin), _pd(ms)))
         return tuple(float(v) for v in ms)
 

@@ -887,31 +887,39 @@ int fbs_profile(fbs_handle* h, int64_t n_iter, int64_t burnin, int64_t thin, dou
   FBS_CUDA(launch_set_run(h->p.hyp, burnin, burnin / 2, thin, h->s));
   const bool f32 = h->prec == FBS_F32;
   FBS_CUDA(launch_seg_begin(h->p.hyp, h->s));
-  std::vector<cudaEvent_t> ev((size_t)4 * n_iter);
+  const bool learned = f32 && h->pf.prop != nullptr;
+  std::vector<cudaEvent_t> ev((size_t)5 * n_iter);
   for (auto& x : ev) FBS_CUDA(cudaEventCreate(&x));
   cudaError_t e = cudaSuccess;
   for (int64_t i = 0; i < n_iter && e == cudaSuccess; ++i) {
-    cudaEventRecord(ev[4 * i], h->s);
+    cudaEvent_t* v = &ev[5 * i];
+    cudaEventRecord(v[0], h->s);
     e = f32 ? launch_eps_f32(h->mc, h->pf, (int)i, h->s) : launch_eps_f64(h->mc, h->p, (int)i, h->s);
-    cudaEventRecord(ev[4 * i + 1], h->s);
+    cudaEventRecord(v[1], h->s);
+    if (e == cudaSuccess && learned)
+      e = launch_proposal_f32(h->mc, h->pf, h->learned->params_bf16, h->learned->prop, h->s);
+    cudaEventRecord(v[2], h->s);
     if (e == cudaSuccess)
       e = f32 ? launch_gb_f32(h->mc, h->pf, h->block, (int)i, h->s)
               : launch_gb_f64(h->mc, h->p, h->block, (int)i, h->s);
-    cudaEventRecord(ev[4 * i + 2], h->s);
+    cudaEventRecord(v[3], h->s);
     if (e == cudaSuccess) e = launch_hyper(h->mc, h->p, h->nblk, h->s);
-    cudaEventRecord(ev[4 * i + 3], h->s);
+    cudaEventRecord(v[4], h->s);
   }
   if (e == cudaSuccess) e = cudaStreamSynchronize(h->s);
-  double t[3] = {0.0, 0.0, 0.0};
+  double t[4] = {0.0, 0.0, 0.0, 0.0};  // eps, proposal, gamma/beta, hyperparameters
   for (int64_t i = 0; i < n_iter && e == cudaSuccess; ++i)
-    for (int k = 0; k < 3; ++k) {
+    for (int k = 0; k < 4; ++k) {
       float a = 0.f;
-      cudaEventElapsedTime(&a, ev[4 * i + k], ev[4 * i + k + 1]);
+      cudaEventElapsedTime(&a, ev[5 * i + k], ev[5 * i + k + 1]);
       t[k] += a;
     }
   for (auto& x : ev) cudaEventDestroy(x);
   FBS_CUDA(e);
-  for (int k = 0; k < 3; ++k) ms[k] = t[k] / (double)n_iter;
+  ms[0] = t[0] / (double)n_iter;
+  ms[1] = t[2] / (double)n_iter;
+  ms[2] = t[3] / (double)n_iter;
+  ms[3] = t[1] / (double)n_iter;
   return leave(h);
 }
 

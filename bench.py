@@ -69,6 +69,8 @@ def parse():
     ap.add_argument("--no-ess", action="store_true", help="skip the 20000-iteration ESS jobs")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-seconds", type=float, default=12.0)
+    ap.add_argument("--train-epochs", type=int, default=15,
+                    help="training epochs of the learned proposal (2e6 pairs per epoch)")
     ap.add_argument("--tune-sweeps", type=int, default=2000,
                     help="burn-in sweeps that tune the slice widths before the timed steps")
     return ap.parse_args()
@@ -285,7 +287,7 @@ def new_sampler(fbs, data, y, form, seed, chain, block, **kw):
                        precision=prec, block=block, **kw)
 
 
-def ess_job(fbs, torch, data, y_host, form, seed, chain, block, S):
+def ess_job(fbs, torch, data, y_host, form, seed, chain, block, S, train_epochs):
     """The configured job (20000 iterations, burn-in 10000, thin 10) through the
     public API with pinned host counts: init upload, the sweeps in fbs_run calls of
     S iterations with phi read back after each, moments read back at the end.  For
@@ -316,7 +318,7 @@ def ess_job(fbs, torch, data, y_host, form, seed, chain, block, S):
         tt = time.perf_counter()
         smp.proposal_collect(PAIR_SWEEPS, burnin=burnin, thin=2)
         done += 2 * PAIR_SWEEPS
-        loss = smp.proposal_train(seed=seed, **TRAIN)
+        loss = smp.proposal_train(seed=seed, **dict(TRAIN, epochs=train_epochs))
         smp.proposal_calibrate(CALIBRATE_SWEEPS, burnin=burnin, min_accept=0.2)
         done += CALIBRATE_SWEEPS
         extra = {"train_pairs": PAIR_SWEEPS * data["y"].shape[0], "train_loss": loss,
@@ -397,7 +399,8 @@ def main():
         order = ["f64", "f32", "learned"] if args.forms == "all" else [form]
         for f in order:
             barrier()
-            forms[f] = ess_job(fbs, torch, data, y_host, f, seed, rank, args.block, S)
+            forms[f] = ess_job(fbs, torch, data, y_host, f, seed, rank, args.block, S,
+                               args.train_epochs)
     params = forms.get("learned", {}).pop("params", None)
 
     # ---- device-timed throughput: W warm-up + K timed steps of S sweeps
@@ -407,7 +410,7 @@ def main():
     if form == "learned":
         if params is None:
             smp.proposal_collect(PAIR_SWEEPS, burnin=tb, thin=2)
-            smp.proposal_train(seed=seed, **TRAIN)
+            smp.proposal_train(seed=seed, **dict(TRAIN, epochs=args.train_epochs))
         else:
             smp.proposal_params(set_to=params)
         smp.proposal_calibrate(CALIBRATE_SWEEPS, burnin=tb, min_accept=0.2)

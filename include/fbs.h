@@ -206,8 +206,9 @@ int fbs_uniforms(uint64_t seed, uint32_t chain, uint32_t stream, uint32_t index0
  * during calibration keep only the slice updates; the per-gene choice is then
  * fixed.  Parameters: one flat
  * FP32 array W1 [64][F], b1 [64], W2 [64][64], b2 [64], W3 [K][64], b3 [K], with
- * F = 4L+1 and K = L + L(L+1)/2; inference reads a BF16 copy and accumulates in
- * FP32.  These calls return FBS_E_ARG for FP64 handles and batch views. */
+ * F = 4L+1 and K = L + L(L+1)/2.  Inference runs on the tensor cores (tcgen05)
+ * with every FP32 operand split into two BF16 numbers (hi + lo) and FP32
+ * accumulation, about 16 significant bits per operand.  These calls return FBS_E_ARG for FP64 handles and batch views. */
 
 /* Number of network parameters for L columns (-1 if L is out of range). */
 int fbs_proposal_param_count(int L);

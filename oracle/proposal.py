@@ -12,13 +12,22 @@ written here from its definition with explicit backpropagation.
 Features of a gene are invariant under the proposal's move, which keeps every
 log-rate eta_gn = h_n + eps_gn + X_n beta_g fixed: X^T (eta_g - h) / N (L
 values), asinh(X^T y_g) (L), log gamma_g (1), theta (L) and log sigma (L).
-Pinned by scipy's multivariate normal density and by finite differences.
+
+The move proposes from the multivariate t distribution with T_DOF degrees of
+freedom, centre mu and scale matrix C C^T (the Gaussian's parameters): beta* =
+mu + s C xi with xi standard normal and s = sqrt(T_DOF / chi2), chi2 a
+chi-square variate with T_DOF degrees of freedom.  Its polynomial tails dominate
+the Gaussian tails of the move's target, so the ratio target / proposal is
+bounded and the independence sampler is uniformly ergodic (Mengersen & Tweedie
+1996), even where the network's scale is too small.
+Pinned by scipy's multivariate normal and t densities and by finite differences.
 """
 from __future__ import annotations
 
 import numpy as np
 
 SQRT_2_OVER_PI = np.sqrt(2.0 / np.pi)
+T_DOF = 8
 
 
 def n_features(L):
@@ -126,26 +135,38 @@ def loss_and_grads(p, f, beta, L):
     return loss, g
 
 
+def t_log_ratio(out, beta, beta_new, L, dof=T_DOF):
+    """log q(beta) - log q(beta_new) for the multivariate t proposal of centre mu
+    and scale C C^T (the normalising constants cancel)."""
+    mu, C = unpack(out, L)
+    u0 = np.linalg.solve(C, (beta - mu)[..., None])[..., 0]
+    u1 = np.linalg.solve(C, (beta_new - mu)[..., None])[..., 0]
+    a = 0.5 * (dof + L)
+    return -a * (np.log1p(np.sum(u0 * u0, 1) / dof) - np.log1p(np.sum(u1 * u1, 1) / dof))
+
+
 def mh_log_ratio(eps, beta, beta_new, gam, theta, sigma2, X, out):
     """log of the acceptance ratio of the eta-preserving move to beta_new
     (eps_new = eps - X (beta_new - beta)): the Poisson likelihood is unchanged,
     so the ratio holds the Normal(0, gamma) priors of eps, the Normal(theta, sigma^2)
-    priors of beta and the proposal densities q(beta) / q(beta_new)."""
+    priors of beta and the t proposal densities q(beta) / q(beta_new)."""
     L = beta.shape[1]
     eps_new = eps - (beta_new - beta) @ X.T
     lp = (-0.5 * np.sum(eps_new ** 2, 1) / gam - 0.5 * np.sum((beta_new - theta) ** 2 / sigma2, 1)
           + 0.5 * np.sum(eps ** 2, 1) / gam + 0.5 * np.sum((beta - theta) ** 2 / sigma2, 1))
-    return lp - nll(out, beta, L) + nll(out, beta_new, L)
+    return lp + t_log_ratio(out, beta, beta_new, L)
 
 
-def mh_move(eps, beta, gam, theta, sigma2, X, out, xi, log_u):
-    """The eta-preserving move of every row from standard normals xi [G][L] and
-    log-uniforms log_u [G]: beta* = mu + C xi, eps* = eps - X (beta* - beta),
+def mh_move(eps, beta, gam, theta, sigma2, X, out, xi, log_u, chi2):
+    """The eta-preserving move of every row from standard normals xi [G][L],
+    chi-square variates chi2 [G] (T_DOF degrees of freedom) and log-uniforms
+    log_u [G]: beta* = mu + sqrt(T_DOF / chi2) C xi, eps* = eps - X (beta* - beta),
     accepted where log_u < the log ratio of mh_log_ratio.  Returns the new eps,
     beta, the acceptance flags and the log ratios."""
     L = beta.shape[1]
     mu, C = unpack(out, L)
-    beta_new = mu + np.einsum("gij,gj->gi", C, xi)
+    s = np.sqrt(T_DOF / np.asarray(chi2))
+    beta_new = mu + s[:, None] * np.einsum("gij,gj->gi", C, xi)
     la = mh_log_ratio(eps, beta, beta_new, gam, theta, sigma2, X, out)
     acc = log_u < la
     eps_new = np.where(acc[:, None], eps - (beta_new - beta) @ X.T, eps)

@@ -132,7 +132,7 @@ void fbs::set_last_error(const std::string& msg) { g_err = msg; }
 struct LearnedState {
   int L = 0, F = 0, K = 0, np = 0;
   float* params = nullptr;     // FP32 master parameters (flat)
-  void* params_bf16 = nullptr; // inference copy
+  void* w_image = nullptr;     // inference weights: split BF16 operands + FP32 biases
   float* adam_m = nullptr;
   float* adam_v = nullptr;
   long long adam_t = 0;
@@ -361,7 +361,7 @@ int sweeps_direct(fbs_handle* h, int64_t n_iter) {
     for (int64_t i = 0; i < n_iter; ++i) {
       FBS_CUDA(launch_eps_f32(h->mc, h->pf, (int)i, h->s));
       if (h->pf.prop)
-        FBS_CUDA(launch_proposal_f32(h->mc, h->pf, h->learned->params_bf16, h->learned->prop, h->s));
+        FBS_CUDA(launch_proposal_f32(h->mc, h->pf, h->learned->w_image, h->learned->prop, h->s));
       FBS_CUDA(launch_gb_f32(h->mc, h->pf, h->block, (int)i, h->s));
       FBS_CUDA(launch_hyper(h->mc, h->p, h->nblk, h->s));
     }
@@ -389,7 +389,7 @@ cudaError_t capture_segment(fbs_handle* h) {
     if (e != cudaSuccess) return e;
     if (i > 0 && (e = cudaStreamWaitEvent(h->s, h->ev_h, 0)) != cudaSuccess) return e;
     if (f32 && h->pf.prop &&
-        (e = launch_proposal_f32(h->mc, h->pf, h->learned->params_bf16, h->learned->prop,
+        (e = launch_proposal_f32(h->mc, h->pf, h->learned->w_image, h->learned->prop,
                                  h->s)) != cudaSuccess)
       return e;
     e = f32 ? launch_gb_f32(h->mc, h->pf, h->block, i, h->s)
@@ -681,6 +681,8 @@ int fbs_sync(fbs_handle* h) {
   Hyper hy;
   int rc = read_hyper(h, &hy);
   if (rc) return rc;
+  if (hy.flags & kFlagTimeout)
+    return fail(FBS_E_CUDA, "a tensor-core wait of the proposal network gave up");
   if (hy.flags & kFlagNonfinite)
     return fail(FBS_E_NONFINITE, "a slice update started from a non-finite log density");
   return FBS_OK;
@@ -897,7 +899,7 @@ int fbs_profile(fbs_handle* h, int64_t n_iter, int64_t burnin, int64_t thin, dou
     e = f32 ? launch_eps_f32(h->mc, h->pf, (int)i, h->s) : launch_eps_f64(h->mc, h->p, (int)i, h->s);
     cudaEventRecord(v[1], h->s);
     if (e == cudaSuccess && learned)
-      e = launch_proposal_f32(h->mc, h->pf, h->learned->params_bf16, h->learned->prop, h->s);
+      e = launch_proposal_f32(h->mc, h->pf, h->learned->w_image, h->learned->prop, h->s);
     cudaEventRecord(v[2], h->s);
     if (e == cudaSuccess)
       e = f32 ? launch_gb_f32(h->mc, h->pf, h->block, (int)i, h->s)
@@ -942,7 +944,7 @@ void fbs_free(fbs_handle* h) {
   if (h->s) cudaStreamSynchronize(h->s);
   if (LearnedState* ls = h->learned) {
     cudaFree(ls->params);
-    cudaFree(ls->params_bf16);
+    cudaFree(ls->w_image);
     cudaFree(ls->adam_m);
     cudaFree(ls->adam_v);
     cudaFree(ls->prop);
@@ -988,7 +990,7 @@ int learned_setup(fbs_handle* h) {
   ls->np = mlp_param_count(L);
   h->learned = ls;
   FBS_CUDA(cudaMalloc((void**)&ls->params, sizeof(float) * ls->np));
-  FBS_CUDA(cudaMalloc(&ls->params_bf16, 2 * (size_t)ls->np));
+  FBS_CUDA(cudaMalloc(&ls->w_image, tc_image_bytes(L)));
   FBS_CUDA(cudaMalloc((void**)&ls->adam_m, sizeof(float) * ls->np));
   FBS_CUDA(cudaMalloc((void**)&ls->adam_v, sizeof(float) * ls->np));
   FBS_CUDA(cudaMalloc((void**)&ls->prop, sizeof(float) * ls->K * (size_t)G));
@@ -1023,7 +1025,7 @@ int learned_setup(fbs_handle* h) {
   for (int i = 0; i < K * H; ++i) w[o++] = (float)(nrm() * 0.1 * sqrt(1.0 / H));
   FBS_CUDA(cudaMemcpyAsync(ls->params, w.data(), sizeof(float) * ls->np, cudaMemcpyHostToDevice,
                            h->s));
-  FBS_CUDA(launch_to_bf16(ls->params, ls->params_bf16, ls->np, h->s));
+  FBS_CUDA(launch_pack_image(ls->params, ls->w_image, ls->L, h->s));
   FBS_CUDA(cudaStreamSynchronize(h->s));
   return FBS_OK;
 }
@@ -1197,7 +1199,7 @@ int fbs_proposal_train(fbs_handle* h, int epochs, int batch, double lr, uint64_t
     }
   }
   if (e == cudaSuccess && rc == FBS_OK) e = launch_fold(ls->params, ls->stats, L, 1, h->s);
-  if (e == cudaSuccess && rc == FBS_OK) e = launch_to_bf16(ls->params, ls->params_bf16, ls->np, h->s);
+  if (e == cudaSuccess && rc == FBS_OK) e = launch_pack_image(ls->params, ls->w_image, ls->L, h->s);
   if (e == cudaSuccess && rc == FBS_OK) e = cudaStreamSynchronize(h->s);
   cudaFree(t.fb);
   if (rc) return rc;
@@ -1258,7 +1260,7 @@ int fbs_proposal_params(fbs_handle* h, float* get, const float* set, int n) {
     FBS_CUDA(cudaMemcpy(get, ls->params, sizeof(float) * n, cudaMemcpyDeviceToHost));
   if (set) {
     FBS_CUDA(cudaMemcpy(ls->params, set, sizeof(float) * n, cudaMemcpyHostToDevice));
-    FBS_CUDA(launch_to_bf16(ls->params, ls->params_bf16, n, h->s));
+    FBS_CUDA(launch_pack_image(ls->params, ls->w_image, ls->L, h->s));
     FBS_CUDA(cudaStreamSynchronize(h->s));
     ls->trained = true;
   }
@@ -1300,7 +1302,7 @@ int fbs_proposal_outputs(fbs_handle* h, float* out) {
   DevPtrsF32 pf = h->pf;
   pf.use_mh = ls->use_mh;
   pf.mh_all = 1;
-  FBS_CUDA(launch_proposal_f32(h->mc, pf, ls->params_bf16, ls->prop, h->s));
+  FBS_CUDA(launch_proposal_f32(h->mc, pf, ls->w_image, ls->prop, h->s));
   const int G = h->mc.G, K = ls->K;
   std::vector<float> tmp((size_t)K * G);
   FBS_CUDA(cudaMemcpyAsync(tmp.data(), ls->prop, tmp.size() * sizeof(float),
@@ -1325,7 +1327,7 @@ int fbs_proposal_step(fbs_handle* h, int64_t it, int all_genes) {
   pf.mh_acc = ls->mh_acc;
   pf.mh_try = ls->mh_try;
   pf.mh_all = all_genes;
-  FBS_CUDA(launch_proposal_f32(h->mc, pf, ls->params_bf16, ls->prop, h->s));
+  FBS_CUDA(launch_proposal_f32(h->mc, pf, ls->w_image, ls->prop, h->s));
   FBS_CUDA(launch_mh_step_f32(h->mc, pf, it, h->s));
   FBS_CUDA(cudaStreamSynchronize(h->s));
   return leave(h);

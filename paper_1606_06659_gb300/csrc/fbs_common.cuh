@@ -138,6 +138,6 @@ struct DevPtrsF32 {
 };
 
 // Flag bits in Hyper::flags.
-enum : unsigned int { kFlagNonfinite = 1u };
+enum : unsigned int { kFlagNonfinite = 1u, kFlagTimeout = 2u };
 
 }  // namespace fbs

@@ -295,14 +295,21 @@ __global__ void __launch_bounds__(256) k_eps_f32(ModelConst mc, DevPtrsF32 p, in
                (blockIdx.x + blockIdx.y) % kCounterCopies);
 }
 
-// The learned-proposal move of gene g (FP32): beta* = mu + C xi from the
-// proposal network's Gaussian, eps* = eps - X (beta* - beta), so that every
-// log-rate h_n + eps_n + X_n beta is unchanged and the Poisson likelihood cancels;
-// accepted with probability min(1, pi(eps*, beta*) q(beta) / (pi(eps, beta) q(beta*))),
-// where pi holds the Normal(0, gamma) priors of eps and the Normal(theta, sigma^2)
-// priors of beta.  The proposal depends only on quantities the move leaves
-// unchanged, so this is an exact Metropolis-Hastings step.  Uniforms 0..2L-1
-// give the normals, uniform 2L the acceptance.  Returns true when accepted.
+// The learned-proposal move of gene g (FP32): beta* from the multivariate t
+// distribution with kTDof degrees of freedom, centre mu and scale C C^T given by
+// the proposal network (beta* = mu + s C xi, s = sqrt(kTDof / chi2)), and
+// eps* = eps - X (beta* - beta), so that every log-rate h_n + eps_n + X_n beta is
+// unchanged and the Poisson likelihood cancels; accepted with probability
+// min(1, pi(eps*, beta*) q(beta) / (pi(eps, beta) q(beta*))), where pi holds the
+// Normal(0, gamma) priors of eps and the Normal(theta, sigma^2) priors of beta.
+// The proposal depends only on quantities the move leaves unchanged, so this is
+// an exact Metropolis-Hastings step; the t tails dominate the target's Gaussian
+// tails, which keeps the ratio target / proposal bounded (uniform ergodicity).
+// Uniforms 0..2L-1 give the normals, uniform 2L the acceptance and uniforms
+// 2L+1..2L+4 the chi-square variate chi2 = -2 log(U1 U2 U3 U4) (kTDof = 8).
+// Returns true when accepted.
+constexpr int kTDof = 8;
+
 __device__ __forceinline__ bool mh_move_f32(const ModelConst& mc, const DevPtrsF32& p, int g,
                                             uint32_t it32, float* bs, int B, int tid,
                                             const Hyper* hy, float hg) {
@@ -326,23 +333,31 @@ __device__ __forceinline__ bool mh_move_f32(const ModelConst& mc, const DevPtrsF
     }
   }
   Rng4 r(mc.seed_lo, mc.seed_hi, mc.chain, kStreamMH, (uint32_t)g, it32);
-  float lq = 0.0f;  // log q(beta) - log q(beta*) = (|xi|^2 - |C^-1 (beta - mu)|^2) / 2
   float lp = 0.0f;  // log prior ratio of beta
+  float xx = 0.0f;  // |xi|^2
 #pragma unroll
   for (int i = 0; i < kMaxL; ++i) {
     xi[i] = 0.0f;
     if (i < L) xi[i] = normal_bm_f(r, 2 * i);
+    xx += xi[i] * xi[i];
   }
+  const float log_u = __logf(r.u(2u * (uint32_t)L));
+  const uint32_t kc = 2u * (uint32_t)L + 1u;
+  const float chi2 = -2.0f * (logf(r.u(kc)) + logf(r.u(kc + 1u)) + logf(r.u(kc + 2u)) +
+                              logf(r.u(kc + 3u)));
+  const float st = sqrtf((float)kTDof / chi2);
 #pragma unroll
   for (int i = 0; i < kMaxL; ++i) {
-    float v = mu[i];
+    float v = 0.0f;
 #pragma unroll
     for (int j = 0; j < kMaxL; ++j)
       if (j <= i) v += C[i][j] * xi[j];
+    v = mu[i] + st * v;
     bn[i] = v;
     d[i] = i < L ? v - bs[i * B + tid] : 0.0f;
   }
   float u[kMaxL];
+  float uu = 0.0f;  // |C^-1 (beta - mu)|^2
 #pragma unroll
   for (int i = 0; i < kMaxL; ++i) {
     u[i] = 0.0f;
@@ -352,11 +367,15 @@ __device__ __forceinline__ bool mh_move_f32(const ModelConst& mc, const DevPtrsF
       for (int j = 0; j < kMaxL; ++j)
         if (j < i) v -= C[i][j] * u[j];
       u[i] = v / C[i][i];
-      lq += 0.5f * (xi[i] * xi[i] - u[i] * u[i]);
+      uu += u[i] * u[i];
       const float bt = bs[i * B + tid] - (float)hy->phi[2 + i];
       lp -= d[i] * (d[i] + 2.0f * bt) * (0.5f / (float)hy->phi[2 + L + i]);
     }
   }
+  // log q(beta) - log q(beta*), with C^-1 (beta* - mu) = st xi
+  const float inv_dof = 1.0f / (float)kTDof;
+  const float lq = -0.5f * (float)(kTDof + L) *
+                   (log1pf(uu * inv_dof) - log1pf(st * st * xx * inv_dof));
   // eps prior ratio: sum_n [eps_n^2 - (eps_n - X_n d)^2] / (2 gamma)
   float se = 0.0f;
   for (int n = 0; n < N; ++n) {
@@ -367,7 +386,7 @@ __device__ __forceinline__ bool mh_move_f32(const ModelConst& mc, const DevPtrsF
     se += xd * (2.0f * p.eps[(size_t)n * G + g] - xd);
   }
   const float la = se * hg + lp + lq;
-  const bool acc = __logf(r.u(2u * (uint32_t)L)) < la;
+  const bool acc = log_u < la;
   if (acc) {
     for (int n = 0; n < N; ++n) {
       float xd = 0.0f;

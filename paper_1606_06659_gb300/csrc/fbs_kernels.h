@@ -65,7 +65,8 @@ cudaError_t launch_nll_head(const float* O, const float* Y, int Bsz, int L, floa
 cudaError_t launch_colsum(const float* D, int rows, int cols, float* g, cudaStream_t s);
 cudaError_t launch_adam(float* w, const float* g, float* m, float* v, int n, float lr, float b1,
                         float b2, float eps, float c1, float c2, cudaStream_t s);
-cudaError_t launch_to_bf16(const float* a, void* b, int n, cudaStream_t s);
+size_t tc_image_bytes(int L);
+cudaError_t launch_pack_image(const float* params, void* img, int L, cudaStream_t s);
 
 // batched FP32 kernels (fbs_gene_f32.cu)
 cudaError_t prepare_batch_kernels(int max_N, int gb_block);

@@ -8,7 +8,7 @@
 // mean mu (L), log of the Cholesky diagonal (L), sub-diagonal entries in row
 // order.  GELU is the tanh form of Hendrycks & Gimpel (2016).  Parameters are
 // one flat FP32 array W1 [64][F], b1 [64], W2 [64][64], b2 [64], W3 [K][64],
-// b3 [K]; inference reads a BF16 copy with FP32 accumulation.
+// b3 [K]; inference (tensor cores) reads them as split BF16 operands.
 #include <cuda_bf16.h>
 #include <cuda_runtime.h>
 #include <math.h>
@@ -66,47 +66,388 @@ __device__ __forceinline__ void gene_features(const ModelConst& mc, const DevPtr
   f[2 * L] = logf(p.gam[g]);
 }
 
-// One thread per gene: features, then the network with its BF16 weights staged in
-// shared memory as FP32; writes the proposal parameters [K][G].  Genes that keep
-// the slice updates are skipped unless every gene is being calibrated.
-__global__ void __launch_bounds__(128) k_proposal_f32(ModelConst mc, DevPtrsF32 p,
-                                                     const __nv_bfloat16* __restrict__ w,
-                                                     float* __restrict__ out) {
-  extern __shared__ float ws[];  // weights as FP32, then h2[64][blockDim]
-  const int F = 4 * mc.L + 1, K = mc.L + mc.L * (mc.L + 1) / 2, H = kMlpHidden;
-  const int np = mlp_n_params(F, K);
-  for (int i = threadIdx.x; i < np; i += blockDim.x) ws[i] = __bfloat162float(w[i]);
-  __syncthreads();
-  const float* W1 = ws;
+// ---------------------------------------------------------------- tensor-core inference
+//
+// The network runs on the tensor cores (tcgen05): per tile of 128 genes (one
+// thread per gene, four warps) three GEMMs D = A W^T with BF16 operands read
+// from shared memory and FP32 accumulators in tensor memory, M = 128 and
+// N = 64, 64, n3.  Every FP32 operand x (weights, features, activations) enters
+// as a BF16 pair x = hi + lo, hi = bf16(x), lo = bf16(x - hi); each layer
+// accumulates hi*hi + lo*hi + hi*lo, which keeps about 16 significant bits per
+// operand (the lo*lo term is below that).  GELU, the biases and the split of
+// the next layer's input run in the epilogue, one thread per TMEM lane (= gene).
+//
+// Operands use the canonical K-major layout without swizzle: 8 x 16-byte core
+// matrices of 128 contiguous bytes, the core matrices of one 8-row group
+// consecutive along K (leading byte offset 128), the groups `sbo` bytes apart.
+// An operand with kw columns holds [hi (kw/2) | lo (kw/2)].
+
+struct TcShape {
+  int F, K;      // features, outputs
+  int k1;        // input columns of the first layer per half (F rounded up to 16)
+  int n3;        // rows of the last layer (K rounded up to 16)
+  int off_w2, off_w3, off_b, bytes;  // weight image: W1, W2, W3, biases (FP32)
+};
+
+__host__ __device__ inline TcShape tc_shape(int L) {
+  TcShape t;
+  t.F = 4 * L + 1;
+  t.K = L + L * (L + 1) / 2;
+  t.k1 = (t.F + 15) & ~15;
+  t.n3 = (t.K + 15) & ~15;
+  t.off_w2 = kMlpHidden * 2 * t.k1 * 2;
+  t.off_w3 = t.off_w2 + kMlpHidden * 2 * kMlpHidden * 2;
+  t.off_b = t.off_w3 + t.n3 * 2 * kMlpHidden * 2;
+  t.bytes = t.off_b + (2 * kMlpHidden + t.n3) * 4;
+  return t;
+}
+
+constexpr int kMaxK1 = (kMaxFeat + 15) & ~15;
+
+// Shared memory: the weight image, then one A operand buffer of 128 rows that
+// holds in turn the split features (2 k1 columns) and the split activations of
+// the two hidden layers (128 columns); each is dead once its GEMM completed.
+__host__ __device__ inline size_t tc_smem_layout(int L, size_t* off_a) {
+  const TcShape t = tc_shape(L);
+  const size_t a = ((size_t)t.bytes + 1023) & ~(size_t)1023;
+  const size_t cols = 2 * t.k1 > 2 * kMlpHidden ? 2 * t.k1 : 2 * kMlpHidden;
+  if (off_a) *off_a = a;
+  return a + (size_t)128 * cols * 2;
+}
+
+// Byte offset of element (r, c) of a canonical operand with kw columns.
+__host__ __device__ inline uint32_t canon_off(int r, int c, int kw) {
+  return (uint32_t)(((r >> 3) * (kw >> 3) + (c >> 3)) * 128 + (r & 7) * 16 + (c & 7) * 2);
+}
+
+__device__ __forceinline__ uint32_t bf16_pair(float a, float b) {
+  return (uint32_t)__bfloat16_as_ushort(__float2bfloat16_rn(a)) |
+         ((uint32_t)__bfloat16_as_ushort(__float2bfloat16_rn(b)) << 16);
+}
+
+// Row r, columns c0..c0+7 of an operand with kw = 2 kin columns: hi parts at
+// c0.., lo parts at kin + c0.. (16-byte stores).
+__device__ __forceinline__ void store_split8(uint8_t* base, int kin, int r, int c0,
+                                             const float* v) {
+  float lo[8];
+#pragma unroll
+  for (int i = 0; i < 8; ++i) lo[i] = v[i] - __bfloat162float(__float2bfloat16_rn(v[i]));
+  const uint4 h = make_uint4(bf16_pair(v[0], v[1]), bf16_pair(v[2], v[3]), bf16_pair(v[4], v[5]),
+                             bf16_pair(v[6], v[7]));
+  const uint4 l = make_uint4(bf16_pair(lo[0], lo[1]), bf16_pair(lo[2], lo[3]),
+                             bf16_pair(lo[4], lo[5]), bf16_pair(lo[6], lo[7]));
+  *(uint4*)(base + canon_off(r, c0, 2 * kin)) = h;
+  *(uint4*)(base + canon_off(r, kin + c0, 2 * kin)) = l;
+}
+
+// The weight image the kernel copies into shared memory: W1 [64][2 k1],
+// W2 [64][128], W3 [n3][128] as split canonical operands (zero padding), then
+// the biases b1, b2, b3 (n3, zero padded) in FP32.
+__global__ void k_pack_image(const float* __restrict__ w, int L, uint8_t* __restrict__ img) {
+  const TcShape t = tc_shape(L);
+  const int H = kMlpHidden, F = t.F, K = t.K;
+  const float* W1 = w;
   const float* b1 = W1 + H * F;
   const float* W2 = b1 + H;
   const float* b2 = W2 + H * H;
   const float* W3 = b2 + H;
   const float* b3 = W3 + K * H;
-  float* h2s = ws + ((np + 31) & ~31);
-  const int B = blockDim.x, tid = threadIdx.x;
-  const int g = blockIdx.x * B + tid;
-  if (g >= mc.G) return;
-  if (!(p.mh_all || p.use_mh[g])) return;
-  float f[kMaxFeat];
-  gene_features(mc, p, g, p.hyp, f);
-  float h1[kMlpHidden];
-#pragma unroll
-  for (int j = 0; j < kMlpHidden; ++j) {
-    float acc = b1[j];
-    for (int i = 0; i < F; ++i) acc += W1[j * F + i] * f[i];
-    h1[j] = gelu_f(acc);
+  const int n1 = H * t.k1, n2 = H * H, n3 = t.n3 * H, nb = 2 * H + t.n3;
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n1 + n2 + n3 + nb;
+       i += gridDim.x * blockDim.x) {
+    uint8_t* base;
+    int r, c, kin;
+    float v;
+    if (i < n1) {
+      r = i / t.k1, c = i % t.k1, kin = t.k1, base = img;
+      v = c < F ? W1[r * F + c] : 0.0f;
+    } else if (i < n1 + n2) {
+      const int j = i - n1;
+      r = j / H, c = j % H, kin = H, base = img + t.off_w2;
+      v = W2[r * H + c];
+    } else if (i < n1 + n2 + n3) {
+      const int j = i - n1 - n2;
+      r = j / H, c = j % H, kin = H, base = img + t.off_w3;
+      v = r < K ? W3[r * H + c] : 0.0f;
+    } else {
+      const int j = i - n1 - n2 - n3;
+      float* bb = (float*)(img + t.off_b);
+      bb[j] = j < H ? b1[j] : (j < 2 * H ? b2[j - H] : (j - 2 * H < K ? b3[j - 2 * H] : 0.0f));
+      continue;
+    }
+    const __nv_bfloat16 hi = __float2bfloat16_rn(v);
+    const __nv_bfloat16 lo = __float2bfloat16_rn(v - __bfloat162float(hi));
+    *(__nv_bfloat16*)(base + canon_off(r, c, 2 * kin)) = hi;
+    *(__nv_bfloat16*)(base + canon_off(r, kin + c, 2 * kin)) = lo;
   }
-  for (int j = 0; j < H; ++j) {
-    float acc = b2[j];
-#pragma unroll
-    for (int i = 0; i < kMlpHidden; ++i) acc += W2[j * H + i] * h1[i];
-    h2s[j * B + tid] = gelu_f(acc);
+}
+
+constexpr unsigned kTcWaitLimit = 1u << 24;  // try_wait polls before a wait gives up
+
+__device__ __forceinline__ uint32_t smem_u32(const void* ptr) {
+  return (uint32_t)__cvta_generic_to_shared(ptr);
+}
+
+__device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity) {
+  for (unsigned i = 0; i < kTcWaitLimit; ++i) {
+    uint32_t ok;
+    asm volatile(
+        "{\n\t.reg .pred P;\n\t"
+        "mbarrier.try_wait.parity.shared::cta.b64 P, [%1], %2;\n\t"
+        "selp.u32 %0, 1, 0, P;\n\t}\n"
+        : "=r"(ok)
+        : "r"(bar), "r"(parity)
+        : "memory");
+    if (ok) return true;
   }
-  for (int k = 0; k < K; ++k) {
-    float acc = b3[k];
-    for (int j = 0; j < H; ++j) acc += W3[k * H + j] * h2s[j * B + tid];
-    out[(size_t)k * mc.G + g] = acc;
+  return false;
+}
+
+// Shared-memory matrix descriptor: start address, leading byte offset 128,
+// stride byte offset `sbo` (all >> 4), descriptor version 1 (bit 46), no swizzle.
+__device__ __forceinline__ uint64_t umma_desc(uint32_t saddr, uint32_t sbo) {
+  return (uint64_t)((saddr >> 4) & 0x3FFFu) | ((uint64_t)(128u >> 4) << 16) |
+         ((uint64_t)((sbo >> 4) & 0x3FFFu) << 32) | (1ull << 46);
+}
+
+// Instruction descriptor of kind::f16: FP32 accumulator (bits 4-5 = 1), A and
+// B BF16 (bits 7-9 and 10-12 = 1), both K-major, N >> 3 at bit 17, M >> 4 at bit 24.
+__host__ __device__ constexpr uint32_t umma_idesc_bf16(int M, int N) {
+  return (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(N >> 3) << 17) |
+         ((uint32_t)(M >> 4) << 24);
+}
+
+__device__ __forceinline__ void umma_bf16(uint32_t d, uint64_t a, uint64_t b, uint32_t idesc,
+                                          uint32_t acc) {
+  asm volatile(
+      "{\n\t.reg .pred p;\n\t"
+      "setp.ne.b32 p, %4, 0;\n\t"
+      "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}\n"
+      :
+      : "r"(d), "l"(a), "l"(b), "r"(idesc), "r"(acc)
+      : "memory");
+}
+
+// D (+)= A B^T over kin columns for the three hi/lo products; a and b are the
+// operands' shared addresses, both with 2 kin columns.
+__device__ __forceinline__ void issue_layer(uint32_t d, uint32_t a, uint32_t b, int kin,
+                                            uint32_t idesc) {
+  const uint32_t sbo = (uint32_t)(2 * kin / 8) * 128;
+  const uint32_t lo = (uint32_t)(kin / 8) * 128;
+  const uint32_t pa[3] = {0u, lo, 0u}, pb[3] = {0u, 0u, lo};
+  uint32_t acc = 0u;
+#pragma unroll
+  for (int q = 0; q < 3; ++q)
+    for (int k = 0; k < kin; k += 16) {
+      const uint32_t ko = (uint32_t)(k / 8) * 128;
+      umma_bf16(d, umma_desc(a + pa[q] + ko, sbo), umma_desc(b + pb[q] + ko, sbo), idesc, acc);
+      acc = 1u;
+    }
+}
+
+__device__ __forceinline__ void umma_commit(uint32_t bar) {
+  asm volatile(
+      "tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(bar)
+      : "memory");
+}
+
+__device__ __forceinline__ void tc_fence_before() {
+  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+}
+__device__ __forceinline__ void tc_fence_after() {
+  asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+}
+__device__ __forceinline__ void fence_async_smem() {
+  asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+}
+
+// 16 consecutive FP32 columns of this thread's TMEM lane.
+__device__ __forceinline__ void tmem_ld16(uint32_t taddr, float* v) {
+  uint32_t r[16];
+  asm volatile(
+      "tcgen05.ld.sync.aligned.32x32b.x16.b32 "
+      "{%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, %15}, [%16];"
+      : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]),
+        "=r"(r[7]), "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]),
+        "=r"(r[14]), "=r"(r[15])
+      : "r"(taddr));
+  asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+#pragma unroll
+  for (int i = 0; i < 16; ++i) v[i] = __uint_as_float(r[i]);
+}
+
+constexpr uint32_t kTmemCols = 128;  // D1 at columns 0..63, D2 at 64..127, D3 at 0..n3-1
+constexpr int kTcThreads = 256;      // two warps per TMEM lane quadrant
+
+// GELU (tanh form) for inference, with tanh(u) = 1 - 2 / (1 + e^{2u}) from the
+// fast exponential: about 1e-6 absolute error, far below what the proposal needs.
+__device__ __forceinline__ float gelu_fast(float x) {
+  const float u = kSqrt2OverPi * (x + 0.044715f * x * x * x);
+  const float th = 1.0f - 2.0f / (1.0f + __expf(2.0f * u));
+  return 0.5f * x * (1.0f + th);
+}
+
+// Persistent over tiles of 128 genes; writes the proposal parameters [K][G] of
+// the genes that use the move (every gene when p.mh_all).  Threads 0..127
+// compute the features (thread = gene = TMEM lane); in the epilogues warp w
+// reads lane quadrant w % 4 and column half w / 4.  A wait that gives up sets
+// kFlagTimeout, and the CTA frees its tensor memory and returns.
+__global__ void __launch_bounds__(kTcThreads) k_proposal_tc(ModelConst mc, DevPtrsF32 p,
+                                                           const uint8_t* __restrict__ img_g,
+                                                           float* __restrict__ out, int ntiles) {
+  extern __shared__ __align__(1024) uint8_t sm[];
+  __shared__ __align__(8) uint64_t bars[2];
+  __shared__ uint32_t tmem_slot;
+  __shared__ int s_abort;
+  const TcShape t = tc_shape(mc.L);
+  size_t off_a;
+  tc_smem_layout(mc.L, &off_a);
+  uint8_t* abuf = sm + off_a;
+  const float* bias = (const float*)(sm + t.off_b);
+  const int tid = threadIdx.x, warp = tid >> 5, lane_id = tid & 31;
+  const int quad = warp & 3, half = warp >> 2;
+  const int row = quad * 32 + lane_id;  // the gene (TMEM lane) this thread reads back
+  const uint32_t bar_w = smem_u32(&bars[0]), bar_m = smem_u32(&bars[1]);
+  if (tid == 0) {
+    s_abort = 0;
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(bar_w) : "memory");
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(bar_m) : "memory");
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  if (warp == 0) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(
+                     smem_u32(&tmem_slot)),
+                 "r"(kTmemCols)
+                 : "memory");
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+  }
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  const uint32_t tmem = tmem_slot;
+  if (tid == 0) {
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar_w),
+                 "r"((uint32_t)t.bytes)
+                 : "memory");
+    asm volatile(
+        "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::
+            "r"(smem_u32(sm)),
+        "l"(img_g), "r"((uint32_t)t.bytes), "r"(bar_w)
+        : "memory");
+  }
+  bool w_ok = mbar_wait(bar_w, 0);
+  if (!w_ok) s_abort = 1;
+  __syncthreads();
+
+  const uint32_t id64 = umma_idesc_bf16(128, 64), id3 = umma_idesc_bf16(128, t.n3);
+  const uint32_t lane_addr = (uint32_t)(quad * 32) << 16;
+  const uint32_t sa = smem_u32(abuf), sw = smem_u32(sm);
+  uint32_t ph = 0;
+  bool pending = false;  // an MMA batch whose completion was not seen
+  const int G = mc.G;
+
+  for (int tile = blockIdx.x; tile < ntiles && !s_abort; tile += gridDim.x) {
+    const int g = tile * 128 + row;
+    const bool act = g < G && (p.mh_all || p.use_mh[g]);
+    if (tid < 128) {
+      float f[kMaxK1];
+#pragma unroll
+      for (int i = 0; i < kMaxK1; ++i) f[i] = 0.0f;
+      if (act) gene_features(mc, p, g, p.hyp, f);
+#pragma unroll
+      for (int c0 = 0; c0 < kMaxK1; c0 += 8)
+        if (c0 < t.k1) store_split8(abuf, t.k1, row, c0, f + c0);
+    }
+
+    // ---- layer 1: D1 = A1 W1^T
+    fence_async_smem();
+    tc_fence_before();
+    __syncthreads();
+    if (tid == 0) {
+      tc_fence_after();
+      issue_layer(tmem, sa, sw, t.k1, id64);
+      umma_commit(bar_m);
+    }
+    pending = true;
+    if (!mbar_wait(bar_m, ph)) s_abort = 1;
+    else pending = false;
+    ph ^= 1u;
+    tc_fence_after();
+#pragma unroll
+    for (int c0 = half * 32; c0 < half * 32 + 32; c0 += 16) {
+      float v[16];
+      tmem_ld16(tmem + lane_addr + (uint32_t)c0, v);
+#pragma unroll
+      for (int i = 0; i < 16; ++i) v[i] = gelu_fast(v[i] + bias[c0 + i]);
+      store_split8(abuf, kMlpHidden, row, c0, v);
+      store_split8(abuf, kMlpHidden, row, c0 + 8, v + 8);
+    }
+
+    // ---- layer 2: D2 = A2 W2^T (A2 overwrote A1 after GEMM 1 completed)
+    fence_async_smem();
+    tc_fence_before();
+    __syncthreads();
+    if (s_abort) break;
+    if (tid == 0) {
+      tc_fence_after();
+      issue_layer(tmem + kMlpHidden, sa, sw + (uint32_t)t.off_w2, kMlpHidden, id64);
+      umma_commit(bar_m);
+    }
+    pending = true;
+    if (!mbar_wait(bar_m, ph)) s_abort = 1;
+    else pending = false;
+    ph ^= 1u;
+    tc_fence_after();
+#pragma unroll
+    for (int c0 = half * 32; c0 < half * 32 + 32; c0 += 16) {
+      float v[16];
+      tmem_ld16(tmem + lane_addr + (uint32_t)(kMlpHidden + c0), v);
+#pragma unroll
+      for (int i = 0; i < 16; ++i) v[i] = gelu_fast(v[i] + bias[kMlpHidden + c0 + i]);
+      store_split8(abuf, kMlpHidden, row, c0, v);
+      store_split8(abuf, kMlpHidden, row, c0 + 8, v + 8);
+    }
+
+    // ---- layer 3: D3 = A3 W3^T (D3 reuses D1's columns)
+    fence_async_smem();
+    tc_fence_before();
+    __syncthreads();
+    if (s_abort) break;
+    if (tid == 0) {
+      tc_fence_after();
+      issue_layer(tmem, sa, sw + (uint32_t)t.off_w3, kMlpHidden, id3);
+      umma_commit(bar_m);
+    }
+    pending = true;
+    if (!mbar_wait(bar_m, ph)) s_abort = 1;
+    else pending = false;
+    ph ^= 1u;
+    tc_fence_after();
+    for (int c0 = half * 16; c0 < t.n3; c0 += 32) {
+      float v[16];
+      tmem_ld16(tmem + lane_addr + (uint32_t)c0, v);
+#pragma unroll
+      for (int i = 0; i < 16; ++i) {
+        const int k = c0 + i;
+        if (act && k < t.K) out[(size_t)k * G + g] = v[i] + bias[2 * kMlpHidden + k];
+      }
+    }
+    tc_fence_before();
+    __syncthreads();
+  }
+
+  if (s_abort) {
+    if (tid == 0) atomicOr(&p.hyp->flags, kFlagTimeout);
+    if (!w_ok) mbar_wait(bar_w, 0);
+    if (pending) mbar_wait(bar_m, ph ^ 1u);
+  }
+  tc_fence_before();
+  __syncthreads();
+  if (warp == 0) {
+    tc_fence_after();
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem),
+                 "r"(kTmemCols)
+                 : "memory");
   }
 }
 
@@ -373,33 +714,31 @@ __global__ void k_adam(float* w, const float* g, float* m, float* v, int n, floa
   w[t] -= lr * (mt / c1) / (sqrtf(vt / c2) + eps);
 }
 
-__global__ void k_to_bf16(const float* a, __nv_bfloat16* b, int n) {
-  const int t = blockIdx.x * blockDim.x + threadIdx.x;
-  if (t < n) b[t] = __float2bfloat16_rn(a[t]);
-}
-
 // ---------------------------------------------------------------- launchers
 
 int mlp_param_count(int L) { return mlp_n_params(4 * L + 1, L + L * (L + 1) / 2); }
 
-size_t proposal_smem_bytes(int L, int block) {
-  const int np = mlp_param_count(L);
-  return ((size_t)((np + 31) & ~31) + (size_t)kMlpHidden * block) * sizeof(float);
+size_t tc_image_bytes(int L) { return (size_t)tc_shape(L).bytes; }
+
+cudaError_t launch_pack_image(const float* params, void* img, int L, cudaStream_t s) {
+  k_pack_image<<<64, 256, 0, s>>>(params, L, (uint8_t*)img);
+  return cudaGetLastError();
 }
 
-cudaError_t launch_proposal_f32(const ModelConst& mc, const DevPtrsF32& p, const void* wv,
+cudaError_t launch_proposal_f32(const ModelConst& mc, const DevPtrsF32& p, const void* img,
                                 float* out, cudaStream_t s) {
-  const __nv_bfloat16* w = (const __nv_bfloat16*)wv;
-  const int blk = 128;
-  const size_t smem = proposal_smem_bytes(mc.L, blk);
-  static bool attr_set = false;
-  if (!attr_set) {
-    cudaError_t e = cudaFuncSetAttribute(k_proposal_f32,
-                                         cudaFuncAttributeMaxDynamicSharedMemorySize, 96 * 1024);
-    if (e != cudaSuccess) return e;
-    attr_set = true;
-  }
-  k_proposal_f32<<<(mc.G + blk - 1) / blk, blk, smem, s>>>(mc, p, w, out);
+  int dev = 0, nsm = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e == cudaSuccess) e = cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
+  if (e != cudaSuccess) return e;
+  const size_t smem = tc_smem_layout(mc.L, nullptr);
+  e = cudaFuncSetAttribute(k_proposal_tc, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                           (int)tc_smem_layout(FBS_MAX_L, nullptr));
+  if (e != cudaSuccess) return e;
+  // Up to three CTAs per SM (shared memory), 128 TMEM columns each.
+  const int ntiles = (mc.G + 127) / 128;
+  const int grid = ntiles < 3 * nsm ? ntiles : 3 * nsm;
+  k_proposal_tc<<<grid, kTcThreads, smem, s>>>(mc, p, (const uint8_t*)img, out, ntiles);
   return cudaGetLastError();
 }
 
@@ -464,11 +803,6 @@ cudaError_t launch_colsum(const float* D, int rows, int cols, float* g, cudaStre
 cudaError_t launch_adam(float* w, const float* g, float* m, float* v, int n, float lr, float b1,
                         float b2, float eps, float c1, float c2, cudaStream_t s) {
   k_adam<<<(n + 255) / 256, 256, 0, s>>>(w, g, m, v, n, lr, b1, b2, eps, c1, c2);
-  return cudaGetLastError();
-}
-
-cudaError_t launch_to_bf16(const float* a, void* b, int n, cudaStream_t s) {
-  k_to_bf16<<<(n + 255) / 256, 256, 0, s>>>(a, (__nv_bfloat16*)b, n);
   return cudaGetLastError();
 }
 

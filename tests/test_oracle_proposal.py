@@ -77,7 +77,7 @@ def test_mh_ratio_equals_joint_density_ratio():
             return (stats.poisson.logpmf(y[g], lam).sum()
                     + stats.norm.logpdf(e, 0, np.sqrt(gam[g])).sum()
                     + stats.norm.logpdf(b, theta, np.sqrt(sigma2)).sum())
-        q = stats.multivariate_normal(mu[g], C[g] @ C[g].T)
+        q = stats.multivariate_t(mu[g], C[g] @ C[g].T, df=P.T_DOF)
         want = (joint(eps_new[g], beta_new[g]) - joint(eps[g], beta[g])
                 + q.logpdf(beta[g]) - q.logpdf(beta_new[g]))
         assert got[g] == pytest.approx(want, rel=1e-8, abs=1e-8)
@@ -125,7 +125,9 @@ def test_move_keeps_the_exact_conditional_of_beta():
     out[:, 2 * L:] = Lc[np.tril_indices(L, -1)]             # row order
     xi = rng.normal(size=(G, L))
     log_u = np.log(rng.uniform(size=G))
-    e2, b2, acc, la = P.mh_move(eps, beta, np.full(G, gam), theta, sigma2, X, out, xi, log_u)
+    chi2 = rng.chisquare(P.T_DOF, size=G)
+    e2, b2, acc, la = P.mh_move(eps, beta, np.full(G, gam), theta, sigma2, X, out, xi, log_u,
+                                chi2)
     np.testing.assert_allclose(e2 + b2 @ X.T, lin[None, :].repeat(G, 0), atol=1e-10)
     rate = acc.mean()
     assert 0.2 < rate < 0.95, rate
@@ -138,7 +140,7 @@ def test_move_keeps_the_exact_conditional_of_beta():
 
 
 def test_move_with_a_proposal_at_the_current_point_accepts_by_the_uniform():
-    """If mu + C xi reproduces the current beta, the ratio is zero: the move
+    """If mu + s C xi reproduces the current beta, the ratio is zero: the move
     accepts exactly when log u < 0 and leaves eps unchanged."""
     rng = np.random.default_rng(12)
     X = paper_design(2)
@@ -148,9 +150,10 @@ def test_move_with_a_proposal_at_the_current_point_accepts_by_the_uniform():
     eps = rng.normal(0, 0.3, (G, N))
     out = rng.normal(0, 0.3, (G, P.n_outputs(L)))
     mu, C = P.unpack(out, L)
-    xi = np.linalg.solve(C, (beta - mu)[..., None])[..., 0]
+    chi2 = np.array([2.0, 8.0, 11.0, 30.0])
+    xi = np.linalg.solve(C, (beta - mu)[..., None])[..., 0] / np.sqrt(P.T_DOF / chi2)[:, None]
     e2, b2, acc, la = P.mh_move(eps, beta, np.full(G, 0.3), np.zeros(L), np.ones(L), X, out, xi,
-                                np.array([-1e-9, -1e-9, 1e-9, 1e-9]))
+                                np.array([-1e-9, -1e-9, 1e-9, 1e-9]), chi2)
     np.testing.assert_allclose(la, 0.0, atol=1e-9)
     assert list(acc) == [True, True, False, False]
     np.testing.assert_allclose(e2, eps, atol=1e-12)

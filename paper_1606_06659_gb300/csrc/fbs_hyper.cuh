@@ -68,37 +68,39 @@ __device__ __forceinline__ void hyper_body(const ModelConst& mc, const double* p
   __syncthreads();
 
   const double S1 = tot[0], S2 = tot[1];
-  if (tid == 0) {
-    // step 3: nu
+  if (tid < 32) {
+    // step 3: nu, the slice update spread over warp 0
     const double tau_old = hy->phi[1];
     NuDensity f{G, mc.d, tau_old, S1, S2};
     Rng r(mc.seed_lo, mc.seed_hi, mc.chain, kStreamNu, 0u, it32);
     const double x0 = hy->phi[0];
-    SliceResult s = slice_update(x0, hy->w_nu, f, r, mc.K, mc.shrink_max);
-    const double nu = s.x;
-    if (it <= hy->burnin) {
-      double w = hy->w_nu, waux = hy->waux_nu;
-      tune_width(w, waux, it, nu, x0, hy->burnin, hy->tune_start);
-      hy->w_nu = w;
-      hy->waux_nu = waux;
+    SliceResult s = slice_update_warp(x0, hy->w_nu, f, r, mc.K, mc.shrink_max);
+    if (tid == 0) {
+      const double nu = s.x;
+      if (it <= hy->burnin) {
+        double w = hy->w_nu, waux = hy->waux_nu;
+        tune_width(w, waux, it, nu, x0, hy->burnin, hy->tune_start);
+        hy->w_nu = w;
+        hy->waux_nu = waux;
+      }
+      atomicAdd(&counters[FBS_CNT_EVALS_NU], (unsigned long long)s.evals);
+      if (s.capped) atomicAdd(&counters[FBS_CNT_SLICE_CAPS], 1ull);
+      if (s.nonfinite) {
+        atomicAdd(&counters[FBS_CNT_NONFINITE], 1ull);
+        atomicOr(&hy->flags, kFlagNonfinite);
+      }
+      // step 4: tau ~ Gamma(a + G nu/2, rate b + nu S2 / 2)
+      Rng rt(mc.seed_lo, mc.seed_hi, mc.chain, kStreamTau, 0u, it32);
+      bool gcap = false;
+      const double shape = mc.a + 0.5 * G * nu;
+      const double rate = mc.b + 0.5 * nu * S2;
+      const double tau = gamma_mt(shape, rt, 0, &gcap) / rate;
+      if (gcap) atomicAdd(&counters[FBS_CNT_GAMMA_CAPS], 1ull);
+      phi_new[0] = nu;
+      phi_new[1] = tau;
     }
-    atomicAdd(&counters[FBS_CNT_EVALS_NU], (unsigned long long)s.evals);
-    if (s.capped) atomicAdd(&counters[FBS_CNT_SLICE_CAPS], 1ull);
-    if (s.nonfinite) {
-      atomicAdd(&counters[FBS_CNT_NONFINITE], 1ull);
-      atomicOr(&hy->flags, kFlagNonfinite);
-    }
-    // step 4: tau ~ Gamma(a + G nu/2, rate b + nu S2 / 2)
-    Rng rt(mc.seed_lo, mc.seed_hi, mc.chain, kStreamTau, 0u, it32);
-    bool gcap = false;
-    const double shape = mc.a + 0.5 * G * nu;
-    const double rate = mc.b + 0.5 * nu * S2;
-    const double tau = gamma_mt(shape, rt, 0, &gcap) / rate;
-    if (gcap) atomicAdd(&counters[FBS_CNT_GAMMA_CAPS], 1ull);
-    phi_new[0] = nu;
-    phi_new[1] = tau;
-  } else if (tid <= L) {
-    const int l = tid - 1;
+  } else if (tid < 32 + L) {
+    const int l = tid - 32;
     // step 6: theta_l ~ N(v B1 / sigma^2, v), v = 1/(G/sigma^2 + 1/c^2);
     // the partials hold B1' = sum (beta - theta_old), B2' = sum (beta - theta_old)^2
     const double th_old = hy->phi[2 + l];

@@ -162,6 +162,137 @@ __device__ __forceinline__ SliceResult slice_update(double x0, double w, const F
   return res;
 }
 
+// slice_update executed by the 32 lanes of a warp, with the same result (value,
+// evaluation count, flags) as the sequential form: the stepping-out points
+// (lo - k w and hi + k w, each rounded step by step as in the sequential loop)
+// and the shrinkage proposals (the chain of brackets that follows when every
+// earlier proposal was rejected; a bracket depends only on which side of x0 the
+// rejected proposals fell) are known before any density is evaluated, so each
+// round evaluates up to 32 of them at once and keeps the outcome of the first
+// one the sequential loop would stop at.  Round 1: lane 0 evaluates f(x0),
+// lanes 1..15 the first 15 left points, lanes 16..31 the first 16 right points;
+// later rounds take 16 points per side, then 32 shrinkage proposals.  Every lane
+// returns the result.
+template <class F>
+__device__ __forceinline__ SliceResult slice_update_warp(double x0, double w, const F& f, Rng& r,
+                                                         int K, int shrink_max) {
+  const int lane = threadIdx.x & 31;
+  SliceResult res;
+  const double lu0 = log(r.u(0));
+  const double v = __dmul_rn(w, r.u(1));
+  const double lo0 = __dsub_rn(x0, v);
+  const double hi0 = __dadd_rn(lo0, w);
+  int KL = (int)__dmul_rn((double)(K + 1), r.u(2));
+  if (KL > K) KL = K;
+  const int KR = K - KL;
+
+  // round 1: f(x0) and the first stepping-out points
+  double aux, aux0 = 0.0;
+  double pt;
+  int side, k;  // side 0: left, 1: right, -1: none
+  if (lane == 0) {
+    pt = x0, side = -1, k = 0;
+  } else if (lane < 16) {
+    side = 0, k = lane - 1;
+  } else {
+    side = 1, k = lane - 16;
+  }
+  if (side == 0) {
+    pt = lo0;
+    for (int i = 0; i < k; ++i) pt = __dsub_rn(pt, w);
+  } else if (side == 1) {
+    pt = hi0;
+    for (int i = 0; i < k; ++i) pt = __dadd_rn(pt, w);
+  }
+  const bool need = side < 0 || (side == 0 ? k < KL : k < KR);
+  double fv = need ? f(pt, &aux) : 0.0;
+  if (lane == 0) aux0 = aux;
+  const double f0 = __shfl_sync(0xffffffffu, fv, 0);
+  aux0 = __shfl_sync(0xffffffffu, aux0, 0);
+  res.nonfinite = !isfinite(f0);
+  const double logu = __dadd_rn(f0, lu0);
+  res.evals = 1;
+
+  // stepping out: a side stops at its first failing point or after K_side points
+  double lo = lo0, hi = hi0;
+  bool open_l = KL > 0, open_r = KR > 0;
+  int base_l = 0, base_r = 0;     // index of this round's first point per side
+  int nl = 15, nr = 16;           // points per side in this round
+  double start_l = lo0, start_r = hi0;
+  for (int round = 0; open_l || open_r; ++round) {
+    if (round > 0) {
+      // points base + (lane & 15) for lanes 0..15 (left), 16..31 (right)
+      side = lane < 16 ? 0 : 1;
+      k = lane & 15;
+      nl = nr = 16;
+      pt = side == 0 ? start_l : start_r;
+      for (int i = 0; i < k; ++i) pt = side == 0 ? __dsub_rn(pt, w) : __dadd_rn(pt, w);
+      const bool act = side == 0 ? (open_l && base_l + k < KL) : (open_r && base_r + k < KR);
+      fv = act ? f(pt, &aux) : 0.0;
+    }
+    // lane index of point j of each side in this round
+    const int off_l = round == 0 ? 1 : 0, off_r = 16;
+    const bool pass = logu < fv;
+    const unsigned bal = __ballot_sync(0xffffffffu, pass);
+    if (open_l) {
+      const int m = min(nl, KL - base_l);  // points of this round the loop would reach
+      int j = 0;
+      while (j < m && ((bal >> (off_l + j)) & 1u)) ++j;
+      // j passes, then (if j < m) one failure
+      res.evals += (unsigned)(j < m ? j + 1 : m);
+      for (int i = 0; i < j; ++i) lo = __dsub_rn(lo, w);
+      base_l += m;
+      if (j < m || base_l >= KL) open_l = false;
+      else start_l = lo;
+    }
+    if (open_r) {
+      const int m = min(nr, KR - base_r);
+      int j = 0;
+      while (j < m && ((bal >> (off_r + j)) & 1u)) ++j;
+      res.evals += (unsigned)(j < m ? j + 1 : m);
+      for (int i = 0; i < j; ++i) hi = __dadd_rn(hi, w);
+      base_r += m;
+      if (j < m || base_r >= KR) open_r = false;
+      else start_r = hi;
+    }
+  }
+
+  // shrinkage: lane j proposes the (base + j)-th point of the rejection chain;
+  // the first round takes 8 proposals (most updates accept within a few), later
+  // rounds 32
+  for (int base = 0, width = 8; base < shrink_max; base += width, width = 32) {
+    const int m = min(width, shrink_max - base);
+    double l2 = lo, h2 = hi, xs = 0.0;
+    const int mine = lane < m ? lane : m - 1;
+    for (int i = 0; i <= mine; ++i) {
+      xs = __dadd_rn(l2, __dmul_rn(__dsub_rn(h2, l2), r.u(3u + (uint32_t)(base + i))));
+      if (i < mine) {
+        if (xs > x0) h2 = xs; else l2 = xs;
+      }
+    }
+    const bool act = lane < m;
+    fv = act ? f(xs, &aux) : -INFINITY;
+    const unsigned bal = __ballot_sync(0xffffffffu, act && logu < fv);
+    if (bal) {
+      const int j = __ffs(bal) - 1;
+      res.evals += (unsigned)(j + 1);
+      res.x = __shfl_sync(0xffffffffu, xs, j);
+      res.aux = __shfl_sync(0xffffffffu, aux, j);
+      res.capped = false;
+      return res;
+    }
+    res.evals += (unsigned)m;
+    // the bracket after the m rejections: lane m-1 holds the chain's last proposal
+    if (xs > x0) h2 = xs; else l2 = xs;
+    lo = __shfl_sync(0xffffffffu, l2, m - 1);
+    hi = __shfl_sync(0xffffffffu, h2, m - 1);
+  }
+  res.x = x0;
+  res.aux = aux0;
+  res.capped = true;
+  return res;
+}
+
 // Width tuning, Algorithm 2 step 7: while it <= M_B add it*|x_new - x_old| to
 // w_aux; once it > M_C set w = w_aux / (it (it+1) / 2) when that is positive and
 // finite.

@@ -77,15 +77,19 @@ def parse():
 
 
 # --------------------------------------------------------------------------- helpers
-# FP64 floating-point operations per slice log-density evaluation of k_gene_f64
-# (DFMA counted as 2, DADD and DMUL as 1), measured with ncu on the paper-scale
-# workload: (2*59.0 + 18.2 + 9.5) thread instructions per elapsed cycle x 2.265e6
-# cycles per launch / 6.15e6 device-counted evaluations per launch.  It covers
-# everything the kernel does per evaluation on average (density, Philox-to-double,
-# interval arithmetic, the per-draw log and the moments).  Re-measure when the
-# kernel changes.
-FP64_FLOP_PER_EVAL = 53.7
-FP64_TRAFFIC_BYTES = 39.1e6   # dram read+write per launch, same ncu capture
+# FP64 floating-point operations per slice log-density evaluation of the FP64
+# sweep kernels k_eps_f64 + k_gb_f64 (DFMA counted as 2, DADD and DMUL as 1),
+# from one ncu capture of each at config 1: (2*87.34 + 20.94 + 11.42) thread
+# instructions per elapsed cycle x 1.124e6 cycles (eps) + (2*74.41 + 27.38 +
+# 14.17) x 6.21e5 cycles (gb) = 3.51e8 flop per sweep, over 5.28e6 device-counted
+# evaluations per sweep.  It covers everything the kernels do per evaluation on
+# average (density, Philox-to-double, interval arithmetic, the per-draw log,
+# moments).  Re-measure when the kernels change.
+FP64_FLOP_PER_EVAL = 66.4
+FP64_TRAFFIC_BYTES = 44.0e6   # dram read+write of both kernels per sweep, same captures
+# dram read+write of k_eps_f32 (18.9 MB) + k_gb_f32 (16.9 MB, with the learned
+# move) per sweep from one ncu capture each at config 1 (writes stay in L2)
+FP32_TRAFFIC_BYTES = 35.8e6
 # FP64 peak from unit counts and clock: 152 SMs x 2 DFMA/clk x 2 flop x 2.07 GHz
 FP64_PEAK_TFLOPS = 152 * 2 * 2 * 2.07e9 / 1e12
 
@@ -465,7 +469,7 @@ def main():
                     "flop_per_eval": FP64_FLOP_PER_EVAL, "evals_per_launch": ev_launch,
                     "peak_source": "152 SMs x 2 DFMA/clk x 2 flop x 2.07 GHz", "hbm": hbm}
     else:
-        roofline = dict(hbm, bound="hbm", traffic=None, kernel="k_eps_f32 + k_gb_f32",
+        roofline = dict(hbm, bound="hbm", traffic=FP32_TRAFFIC_BYTES, kernel="k_eps_f32 + k_gb_f32",
                         kernel_ms=ms_gene, eps_kernel_ms=ms_k1, gb_kernel_ms=ms_k2,
                         hyper_kernel_ms=ms_hyper, evals_per_launch=ev_launch)
         if form == "learned":

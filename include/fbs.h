@@ -189,6 +189,51 @@ int fbs_profile(fbs_handle* h, int64_t n_iter, int64_t burnin, int64_t thin, dou
 int fbs_uniforms(uint64_t seed, uint32_t chain, uint32_t stream, uint32_t index0, int n_index,
                  uint32_t iter, uint32_t k0, int n_k, double* out);
 
+/* ---- Posterior probabilities of contrasts (§3.1) ---------------------------
+ *
+ * For every gene the running mean over the post-burn-in iterations of the
+ * indicator  v_1^T beta_g > b_1 and ... and v_K^T beta_g > b_K,  for up to
+ * FBS_MAX_CONTRASTS propositions of up to FBS_MAX_CONTRAST_TERMS inequalities
+ * each (the paper's estimator of gene-wise posterior probabilities of
+ * contrasts; a disjunction follows from conjunctions by inclusion-exclusion).
+ * The device keeps exact integer counts of the iterations whose beta_g (after
+ * the sweep) satisfies each proposition; the FP64 form evaluates v^T beta in
+ * FP64, the FP32 form in FP32, both as sum_l v_l beta_l in order l = 1..L
+ * without fused multiply-add. */
+#define FBS_MAX_CONTRASTS 8
+#define FBS_MAX_CONTRAST_TERMS 4
+
+/* Set (n >= 1) or clear (n = 0) the propositions and zero their counts.
+ * n_terms[p] in [1, FBS_MAX_CONTRAST_TERMS] inequalities for proposition p;
+ * v host [n][FBS_MAX_CONTRAST_TERMS][L] (row-major, L of the handle), b host
+ * [n][FBS_MAX_CONTRAST_TERMS]; entries beyond n_terms[p] are ignored.  Counting
+ * starts with the next post-burn-in iteration.  FBS_E_ARG for batch views, n or
+ * n_terms out of range, or non-finite v or b.  Synchronous. */
+int fbs_set_contrasts(fbs_handle* h, int n, const int* n_terms, const double* v, const double* b);
+
+/* prob host [G][n]: count / M for each gene and proposition, M = the number of
+ * post-burn-in iterations since fbs_set_contrasts (written to *m if m is not
+ * NULL; prob is 0 while M = 0).  FBS_E_ARG if no propositions are set.
+ * Synchronous. */
+int fbs_contrast_probs(fbs_handle* h, double* prob, int64_t* m);
+
+/* ---- Gelman-Rubin potential scale reduction (§3.1) ------------------------
+ *
+ * From the running means and mean squares of C chains of the same model
+ * (each the mean over the same number M of post-burn-in draws):
+ *   B = M/(C-1) sum_c (mean_c - mean)^2,  S_c^2 = M/(M-1) (msq_c - mean_c^2),
+ *   W = (1/C) sum_c S_c^2,                Rhat = sqrt(1 + (B/W - 1)/M);
+ * NaN where W is not positive.  Computed on the device of chains[0]. */
+#define FBS_MAX_RHAT_CHAINS 64
+
+/* chains: C handles (2 <= C <= FBS_MAX_RHAT_CHAINS; batch views allowed) with
+ * equal N, G, L and precision and equal moment counts M >= 2.  Outputs (host,
+ * each may be NULL): rhat_phi [2L+2], rhat_beta [G][L], rhat_gam [G],
+ * rhat_eps [G][N] (needs the eps moments on every chain).  FBS_E_ARG on a
+ * mismatch.  Synchronous (waits for every chain). */
+int fbs_rhat(int C, fbs_handle* const* chains, double* rhat_phi, double* rhat_beta,
+             double* rhat_gam, double* rhat_eps);
+
 /* ---- Learned proposal for the beta_g block (FP32 handles) -------------------
  *
  * A multilayer perceptron (features -> 64 -> GELU -> 64 -> GELU -> Gaussian)

@@ -166,6 +166,41 @@ def uniforms_f32(seed, chain, stream, index, it, n_k, lib=None):
     return out
 
 
+def rhat(means, msqs, M):
+    """Gelman-Rubin potential scale reduction (§3.1) from C chains' running means
+    and mean squares over M draws each (arrays [C][...]): B = M/(C-1) sum_c
+    (mean_c - mean)^2, S_c^2 = M/(M-1) (msq_c - mean_c^2), W = mean_c S_c^2,
+    Rhat = sqrt(1 + (B/W - 1)/M); NaN where W <= 0."""
+    means = np.asarray(means, np.float64)
+    msqs = np.asarray(msqs, np.float64)
+    C = means.shape[0]
+    grand = means.mean(0)
+    B = M / (C - 1) * ((means - grand) ** 2).sum(0)
+    W = (M / (M - 1) * (msqs - means ** 2)).mean(0)
+    with np.errstate(invalid="ignore", divide="ignore"):
+        return np.where(W > 0, np.sqrt(1 + (B / W - 1) / M), np.nan)
+
+
+def contrast_probs(beta_draws, props, dtype=np.float64):
+    """Posterior probabilities of contrasts (§3.1): for draws beta [M][G][L] and
+    propositions [[(v, b), ...], ...], the fraction of the M draws in which
+    v . beta_g > b holds for every pair of the proposition, per gene ([G][n]).
+    The dot product is summed over l in order in `dtype`, one rounding per
+    operation."""
+    beta = np.asarray(beta_draws).astype(dtype)
+    M, G, L = beta.shape
+    out = np.zeros((G, len(props)))
+    for q, prop in enumerate(props):
+        ok = np.ones((M, G), bool)
+        for v, b in prop:
+            s = np.zeros((M, G), dtype)
+            for l in range(L):
+                s = (s + (dtype(v[l]) * beta[:, :, l]).astype(dtype)).astype(dtype)
+            ok &= s > dtype(b)
+        out[:, q] = ok.sum(0) / M if M else 0.0
+    return out
+
+
 def gamma_draws(shape, seed, chain, stream, index0, n, it, lib=None):
     lib = lib or load()
     out = np.empty(n, np.float64)

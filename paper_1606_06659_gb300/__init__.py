@@ -21,6 +21,8 @@ LIB_PATH = os.path.join(_HERE, "_build", "libfbs.so")
 
 FBS_OK, FBS_E_ARG, FBS_E_CUDA, FBS_E_OOM, FBS_E_NONFINITE = 0, -1, -2, -3, -5
 FBS_F64, FBS_F32 = 0, 1
+FBS_MAX_CONTRASTS, FBS_MAX_CONTRAST_TERMS = 8, 4
+FBS_MAX_RHAT_CHAINS = 64
 MAX_N, MAX_L, MAX_CLASSES = 64, 8, 8
 COUNTER_NAMES = ("evals_eps", "evals_beta", "evals_nu", "slice_caps", "gamma_caps",
                  "trunc_caps", "nonfinite", "sweeps")
@@ -35,7 +37,8 @@ EXPORTED = ("fbs_default_options", "fbs_workspace_bytes", "fbs_init", "fbs_run",
             "fbs_batch_free", "fbs_proposal_param_count", "fbs_proposal_collect",
             "fbs_proposal_train", "fbs_proposal_calibrate", "fbs_proposal_mode",
             "fbs_proposal_params", "fbs_proposal_stats", "fbs_proposal_loss_grad",
-            "fbs_proposal_outputs", "fbs_proposal_step")
+            "fbs_proposal_outputs", "fbs_proposal_step", "fbs_set_contrasts",
+            "fbs_contrast_probs", "fbs_rhat")
 NOALLOC_MAX_GENES = 2048 * 128
 
 
@@ -129,6 +132,9 @@ def load_library(path: str = LIB_PATH):
     lib.fbs_proposal_loss_grad.argtypes = [_PF, C.c_int, C.c_int, _PF, _PF, _PD, _PF]
     lib.fbs_proposal_outputs.argtypes = [vp, _PF]
     lib.fbs_proposal_step.argtypes = [vp, C.c_int64, C.c_int]
+    lib.fbs_set_contrasts.argtypes = [vp, C.c_int, C.POINTER(C.c_int), _PD, _PD]
+    lib.fbs_contrast_probs.argtypes = [vp, _PD, _PI64]
+    lib.fbs_rhat.argtypes = [C.c_int, C.POINTER(vp), _PD, _PD, _PD, _PD]
     lib.fbs_free.argtypes = [vp]
     lib.fbs_free.restype = None
     lib.fbs_last_error_string.argtypes = []
@@ -210,6 +216,19 @@ def _pf(a):
     return a.ctypes.data_as(C.POINTER(C.c_float))
 
 
+def rhat(chains, eps=False):
+    """Gelman-Rubin factors (§3.1) from the running moments of several chains of
+    the same model: dict of phi [2L+2], beta [G][L], gam [G] (and eps [G][N])."""
+    c0 = chains[0]
+    out = {"phi": np.empty(c0.P), "beta": np.empty((c0.G, c0.L)), "gam": np.empty(c0.G)}
+    if eps:
+        out["eps"] = np.empty((c0.G, c0.N))
+    hs = (C.c_void_p * len(chains))(*[c.h for c in chains])
+    _check(c0.lib.fbs_rhat(len(chains), hs, _pd(out["phi"]), _pd(out["beta"]), _pd(out["gam"]),
+                           _pd(out.get("eps"))))
+    return out
+
+
 def proposal_param_count(L):
     return load_library().fbs_proposal_param_count(int(L))
 
@@ -235,6 +254,8 @@ class Sampler:
     the device memory from the PyTorch caching allocator and orders the work on
     torch's current stream; ``workspace="library"`` lets the library allocate.
     """
+    n_contrasts = 0
+
 
     def __init__(self, y, X, h, priors, seed=1, gene_major=True, workspace="torch",
                  options: Options | None = None, **option_kw):
@@ -367,6 +388,33 @@ class Sampler:
         return dict(zip(COUNTER_NAMES, (int(v) for v in c)))
 
     # --------------------------------------------------------------- learned proposal
+    # --------------------------------------------------------------- contrasts
+    def set_contrasts(self, props):
+        """props: list of propositions, each a list of (v, b) with v of length L:
+        the proposition holds when v . beta_g > b for every pair."""
+        n = len(props)
+        T = FBS_MAX_CONTRAST_TERMS
+        terms = np.zeros(max(n, 1), np.int32)
+        v = np.zeros((max(n, 1), T, self.L))
+        b = np.zeros((max(n, 1), T))
+        for q, prop in enumerate(props):
+            terms[q] = len(prop)
+            if len(prop) > T:
+                raise FbsError(FBS_E_ARG, "a proposition has more than FBS_MAX_CONTRAST_TERMS terms")
+            for k, (vk, bk) in enumerate(prop):
+                v[q, k] = vk
+                b[q, k] = bk
+        _check(self.lib.fbs_set_contrasts(self.h, n, terms.ctypes.data_as(C.POINTER(C.c_int)),
+                                          _pd(v), _pd(b)))
+        self.n_contrasts = n
+
+    def contrast_probs(self):
+        """[G][n] posterior probabilities and the number of iterations counted."""
+        out = np.empty((self.G, self.n_contrasts))
+        m = C.c_int64()
+        _check(self.lib.fbs_contrast_probs(self.h, _pd(out), C.byref(m)))
+        return out, m.value
+
     def proposal_collect(self, n_sweeps, burnin=0, thin=1):
         _check(self.lib.fbs_proposal_collect(self.h, int(n_sweeps), int(burnin), int(thin)))
 

@@ -3,6 +3,7 @@
 // the host side of every copy.  All sampling arithmetic is in fbs_kernels.cu.
 #include <cuda_runtime.h>
 #include <math.h>
+#include <stddef.h>
 #include <stdint.h>
 #include <stdio.h>
 #include <string.h>
@@ -169,6 +170,10 @@ struct fbs_handle {
   long long trace_cap = 0;
   bool is_view = false;  // a dataset of a batch: state access only, owned by the batch
   LearnedState* learned = nullptr;
+  Contrasts* con = nullptr;        // device propositions (null until set)
+  unsigned* con_count = nullptr;   // device counts [FBS_MAX_CONTRASTS][G]
+  int ncon = 0;
+  long long con_nmom0 = 0;         // moment count when the propositions were set
 };
 
 namespace {
@@ -248,6 +253,7 @@ bool pseudo_inverse(const double* X, int N, int L, double* pinv /* [kMaxL][kMaxN
 
 DevPtrs carve(char* base, const Layout& o, int trace_beta) {
   DevPtrs p;
+  memset(&p, 0, sizeof(p));  // no contrasts until they are set
   p.y = (const int32_t*)(base + o.y);
   p.T = (const double*)(base + o.T);
   p.eps = (double*)(base + o.eps);
@@ -942,6 +948,8 @@ int fbs_uniforms(uint64_t seed, uint32_t chain, uint32_t stream, uint32_t index0
 void fbs_free(fbs_handle* h) {
   if (!h || h->is_view) return;
   if (h->s) cudaStreamSynchronize(h->s);
+  cudaFree(h->con);
+  cudaFree(h->con_count);
   if (LearnedState* ls = h->learned) {
     cudaFree(ls->params);
     cudaFree(ls->w_image);
@@ -1287,6 +1295,147 @@ int fbs_proposal_stats(fbs_handle* h, int64_t* accepted, int64_t* tried, int* n_
   if (accepted) *accepted = a;
   if (tried) *tried = t;
   if (n_mh_genes) *n_mh_genes = u;
+  return FBS_OK;
+}
+
+int fbs_rhat(int C, fbs_handle* const* chains, double* rhat_phi, double* rhat_beta,
+             double* rhat_gam, double* rhat_eps) {
+  if (C < 2 || C > FBS_MAX_RHAT_CHAINS || !chains)
+    return fail(FBS_E_ARG, "need 2 <= C <= FBS_MAX_RHAT_CHAINS chains");
+  for (int c = 0; c < C; ++c)
+    if (!chains[c]) return fail(FBS_E_ARG, "a chain handle is NULL");
+  const fbs_handle* h0 = chains[0];
+  const int N = h0->mc.N, G = h0->mc.G, L = h0->mc.L, P = h0->mc.P;
+  long long M = -1;
+  for (int c = 0; c < C; ++c) {
+    fbs_handle* h = chains[c];
+    if (h->mc.N != N || h->mc.G != G || h->mc.L != L || h->prec != h0->prec)
+      return fail(FBS_E_ARG, "chains differ in N, G, L or precision");
+    if (rhat_eps && !h->mc.moments_eps) return fail(FBS_E_ARG, "a chain has no eps moments");
+    FBS_CUDA(cudaStreamSynchronize(h->s));
+    Hyper hy;
+    int rc = read_hyper(h, &hy);
+    if (rc) return rc;
+    if (M < 0) M = hy.n_mom;
+    if (hy.n_mom != M) return fail(FBS_E_ARG, "chains hold different numbers of draws");
+  }
+  if (M < 2) return fail(FBS_E_ARG, "need at least 2 post-burn-in draws per chain");
+  const bool f32 = h0->prec == FBS_F32;
+  const size_t NG = (size_t)N * G, LG = (size_t)L * G;
+  double* d_out = nullptr;
+  FBS_CUDA(cudaMalloc((void**)&d_out, sizeof(double) * std::max(NG, std::max(LG, (size_t)P))));
+  cudaStream_t s = h0->s;
+  auto run = [&](int which, long long n, double* host, int R) -> int {
+    RhatInput in;
+    memset(&in, 0, sizeof(in));
+    in.C = C;
+    in.M = M;
+    in.n = n;
+    in.f32 = f32 && which != 3;
+    for (int c = 0; c < C; ++c) {
+      const fbs_handle* h = chains[c];
+      if (which == 3) {  // phi: FP64 moments in the Hyper block of either form
+        in.m[c] = (const double*)((const char*)h->p.hyp + offsetof(Hyper, m_phi));
+        in.q[c] = (const double*)((const char*)h->p.hyp + offsetof(Hyper, q_phi));
+      } else if (f32) {
+        in.mf[c] = which == 0 ? h->pf.mom_beta : (which == 1 ? h->pf.mom_gam : h->pf.mom_eps);
+      } else {
+        in.m[c] = which == 0 ? h->p.m_beta : (which == 1 ? h->p.m_gam : h->p.m_eps);
+        in.q[c] = which == 0 ? h->p.q_beta : (which == 1 ? h->p.q_gam : h->p.q_eps);
+      }
+    }
+    cudaError_t e = launch_rhat(in, d_out, s);
+    std::vector<double> tmp((size_t)n);
+    if (e == cudaSuccess)
+      e = cudaMemcpyAsync(tmp.data(), d_out, sizeof(double) * n, cudaMemcpyDeviceToHost, s);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    if (e != cudaSuccess) return fail(FBS_E_CUDA, std::string("rhat: ") + cudaGetErrorString(e));
+    if (which == 3) {
+      for (int k = 0; k < P; ++k) host[k] = tmp[k];
+    } else {
+      for (int r = 0; r < R; ++r)
+        for (int g = 0; g < G; ++g) host[(size_t)g * R + r] = tmp[(size_t)r * G + g];
+    }
+    return FBS_OK;
+  };
+  int rc = FBS_OK;
+  if (!rc && rhat_beta) rc = run(0, (long long)LG, rhat_beta, L);
+  if (!rc && rhat_gam) rc = run(1, (long long)G, rhat_gam, 1);
+  if (!rc && rhat_eps) rc = run(2, (long long)NG, rhat_eps, N);
+  if (!rc && rhat_phi) rc = run(3, (long long)P, rhat_phi, 1);
+  cudaFree(d_out);
+  return rc;
+}
+
+int fbs_set_contrasts(fbs_handle* h, int n, const int* n_terms, const double* v, const double* b) {
+  if (!h) return fail(FBS_E_ARG, "handle is NULL");
+  if (h->is_view) return fail(FBS_E_ARG, "contrast probabilities need a single-chain handle");
+  if (n < 0 || n > FBS_MAX_CONTRASTS) return fail(FBS_E_ARG, "n must be in [0, FBS_MAX_CONTRASTS]");
+  const int L = h->mc.L, G = h->mc.G;
+  Contrasts hc;
+  memset(&hc, 0, sizeof(hc));
+  hc.n = n;
+  if (n > 0 && (!n_terms || !v || !b)) return fail(FBS_E_ARG, "n_terms, v or b is NULL");
+  for (int q = 0; q < n; ++q) {
+    if (n_terms[q] < 1 || n_terms[q] > FBS_MAX_CONTRAST_TERMS)
+      return fail(FBS_E_ARG, "n_terms must be in [1, FBS_MAX_CONTRAST_TERMS]");
+    hc.terms[q] = n_terms[q];
+    for (int k = 0; k < n_terms[q]; ++k) {
+      const double bk = b[q * FBS_MAX_CONTRAST_TERMS + k];
+      if (!isfinite(bk)) return fail(FBS_E_ARG, "b must be finite");
+      hc.b[q][k] = bk;
+      hc.bf[q][k] = (float)bk;
+      for (int l = 0; l < L; ++l) {
+        const double vl = v[((size_t)q * FBS_MAX_CONTRAST_TERMS + k) * L + l];
+        if (!isfinite(vl)) return fail(FBS_E_ARG, "v must be finite");
+        hc.v[q][k][l] = vl;
+        hc.vf[q][k][l] = (float)vl;
+      }
+    }
+  }
+  FBS_CUDA(cudaStreamSynchronize(h->s));
+  if (n > 0 && !h->con) {
+    FBS_CUDA(cudaMalloc((void**)&h->con, sizeof(Contrasts)));
+    FBS_CUDA(cudaMalloc((void**)&h->con_count, sizeof(unsigned) * FBS_MAX_CONTRASTS * (size_t)G));
+  }
+  if (n > 0) {
+    FBS_CUDA(cudaMemcpy(h->con, &hc, sizeof(hc), cudaMemcpyHostToDevice));
+    FBS_CUDA(cudaMemset(h->con_count, 0, sizeof(unsigned) * FBS_MAX_CONTRASTS * (size_t)G));
+  }
+  Hyper hy;
+  int rc = read_hyper(h, &hy);
+  if (rc) return rc;
+  h->ncon = n;
+  h->con_nmom0 = hy.n_mom;
+  const Contrasts* dc = n > 0 ? h->con : nullptr;
+  unsigned* dn = n > 0 ? h->con_count : nullptr;
+  h->p.con = dc;
+  h->p.con_count = dn;
+  h->pf.con = dc;
+  h->pf.con_count = dn;
+  if (h->seg_exec) {  // the captured kernels hold the old pointers
+    cudaGraphExecDestroy(h->seg_exec);
+    h->seg_exec = nullptr;
+  }
+  return FBS_OK;
+}
+
+int fbs_contrast_probs(fbs_handle* h, double* prob, int64_t* m) {
+  if (!h) return fail(FBS_E_ARG, "handle is NULL");
+  if (h->ncon < 1) return fail(FBS_E_ARG, "no contrast propositions are set");
+  if (!prob) return fail(FBS_E_ARG, "prob is NULL");
+  Hyper hy;
+  int rc = read_hyper(h, &hy);
+  if (rc) return rc;
+  const long long M = hy.n_mom - h->con_nmom0;
+  const int G = h->mc.G, n = h->ncon;
+  std::vector<unsigned> cnt((size_t)n * G);
+  FBS_CUDA(cudaMemcpy(cnt.data(), h->con_count, sizeof(unsigned) * cnt.size(),
+                      cudaMemcpyDeviceToHost));
+  for (int g = 0; g < G; ++g)
+    for (int q = 0; q < n; ++q)
+      prob[(size_t)g * n + q] = M > 0 ? (double)cnt[(size_t)q * G + g] / (double)M : 0.0;
+  if (m) *m = M;
   return FBS_OK;
 }
 

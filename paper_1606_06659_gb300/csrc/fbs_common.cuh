@@ -64,6 +64,17 @@ struct ModelConst {
   float cvalf[kMaxL][kMaxCls];
 };
 
+// Propositions of the contrast probabilities, in device memory: proposition q
+// holds when v[q][k] . beta_g > b[q][k] for every k < terms[q].
+struct Contrasts {
+  int n;
+  int terms[FBS_MAX_CONTRASTS];
+  double v[FBS_MAX_CONTRASTS][FBS_MAX_CONTRAST_TERMS][kMaxL];
+  double b[FBS_MAX_CONTRASTS][FBS_MAX_CONTRAST_TERMS];
+  float vf[FBS_MAX_CONTRASTS][FBS_MAX_CONTRAST_TERMS][kMaxL];
+  float bf[FBS_MAX_CONTRASTS][FBS_MAX_CONTRAST_TERMS];
+};
+
 // Hyperparameters, run parameters and chain bookkeeping, in device memory.
 struct Hyper {
   double phi[kMaxP];
@@ -104,6 +115,8 @@ struct DevPtrs {
   double* trace_beta; // [trace_cap][L][G] or null
   unsigned long long* counters;  // [copies][FBS_NUM_COUNTERS]
   double* mu;         // [N][G] Poisson means at the new eps (split sweep kernels)
+  const Contrasts* con;  // null: no contrast probabilities
+  unsigned* con_count;   // [n][G]
 };
 
 // Device pointers of one chain in the FP32 form: per-gene state in FP32, each
@@ -135,6 +148,8 @@ struct DevPtrsF32 {
   double* trace_phi;  // [trace_cap][P]
   double* trace_beta; // [trace_cap][L][G] or null
   unsigned long long* counters;
+  const Contrasts* con;  // null: no contrast probabilities
+  unsigned* con_count;   // [n][G]
 };
 
 // Flag bits in Hyper::flags.

@@ -552,6 +552,19 @@ __device__ __forceinline__ void gb_f32_body(const ModelConst& mc, const DevPtrsF
       ps[(2 + l) * B + tid] = dv;
       ps[(2 + kMaxL + l) * B + tid] = dv * dv;
     }
+    // contrast probabilities (§3.1), evaluated in FP32
+    if (mom && p.con != nullptr) {
+      const Contrasts* cs = p.con;
+      for (int q = 0; q < cs->n; ++q) {
+        bool ok = true;
+        for (int k = 0; k < cs->terms[q] && ok; ++k) {
+          float sv = 0.0f;
+          for (int l = 0; l < L; ++l) sv = __fadd_rn(sv, __fmul_rn(cs->vf[q][k][l], bs[l * B + tid]));
+          ok = sv > cs->bf[q][k];
+        }
+        if (ok) p.con_count[(size_t)q * G + g] += 1u;
+      }
+    }
   }
 
   // ---- partial sums: error-free FP32 pair sums within the warp, FP64 beyond

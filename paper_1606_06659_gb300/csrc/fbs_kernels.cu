@@ -477,6 +477,20 @@ __global__ void __launch_bounds__(128) k_gb_f64(ModelConst mc, DevPtrs p, int se
       ps[(2 + l) * B + tid] = dv;
       ps[(2 + kMaxL + l) * B + tid] = dv * dv;
     }
+    // contrast probabilities (§3.1): count the iterations whose beta_g satisfies
+    // each proposition
+    if (mom && p.con != nullptr) {
+      const Contrasts* cs = p.con;
+      for (int q = 0; q < cs->n; ++q) {
+        bool ok = true;
+        for (int k = 0; k < cs->terms[q] && ok; ++k) {
+          double sv = 0.0;
+          for (int l = 0; l < L; ++l) sv = __dadd_rn(sv, __dmul_rn(cs->v[q][k][l], bs[l * B + tid]));
+          ok = sv > cs->b[q][k];
+        }
+        if (ok) p.con_count[(size_t)q * G + g] += 1u;
+      }
+    }
   }
 
   double part[kNumPart];
@@ -489,6 +503,47 @@ __global__ void __launch_bounds__(128) k_gb_f64(ModelConst mc, DevPtrs p, int se
 
 __global__ void __launch_bounds__(kHyperThreads) k_hyper(ModelConst mc, DevPtrs p, int nblk) {
   hyper_body(mc, p.partial, p.hyp, p.trace_phi, p.counters, nblk);
+}
+
+// ---------------------------------------------------------------- convergence
+
+// Gelman-Rubin potential scale reduction of parameter i (§3.1) from the chains'
+// running means and mean squares over M draws each.
+__global__ void k_rhat(RhatInput in, double* __restrict__ out) {
+  const long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  if (i >= in.n) return;
+  const int C = in.C;
+  const double M = (double)in.M;
+  double mean[FBS_MAX_RHAT_CHAINS], msq[FBS_MAX_RHAT_CHAINS];
+  double tot = 0.0;
+  for (int c = 0; c < C; ++c) {
+    if (in.f32) {
+      const float* b = in.mf[c];
+      mean[c] = (double)b[i] - (double)b[in.n + i];
+      msq[c] = (double)b[2 * in.n + i] - (double)b[3 * in.n + i];
+    } else {
+      mean[c] = in.m[c][i];
+      msq[c] = in.q[c][i];
+    }
+    tot += mean[c];
+  }
+  const double grand = tot / C;
+  double bsum = 0.0, wsum = 0.0;
+  for (int c = 0; c < C; ++c) {
+    const double dm = mean[c] - grand;
+    bsum += dm * dm;
+    wsum += M / (M - 1.0) * (msq[c] - mean[c] * mean[c]);
+  }
+  const double B = M / (C - 1) * bsum;
+  const double W = wsum / C;
+  out[i] = W > 0.0 ? sqrt(1.0 + (B / W - 1.0) / M) : NAN;
+}
+
+cudaError_t launch_rhat(const RhatInput& in, double* out, cudaStream_t s) {
+  if (in.n <= 0) return cudaSuccess;
+  const int blk = 128;
+  k_rhat<<<(unsigned)((in.n + blk - 1) / blk), blk, 0, s>>>(in, out);
+  return cudaGetLastError();
 }
 
 // ---------------------------------------------------------------- set-up kernels

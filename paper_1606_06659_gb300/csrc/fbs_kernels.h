@@ -41,6 +41,17 @@ cudaError_t launch_seg_begin(Hyper* hy, cudaStream_t s);
 cudaError_t launch_mh_step_f32(const ModelConst& mc, const DevPtrsF32& p, long long it,
                               cudaStream_t s);
 
+// Gelman-Rubin factors of n parameters from C chains' moments (FP64 arrays, or
+// FP32 Kahan planes [4][n] when f32)
+struct RhatInput {
+  int C, f32;
+  long long M, n;
+  const double* m[FBS_MAX_RHAT_CHAINS];
+  const double* q[FBS_MAX_RHAT_CHAINS];
+  const float* mf[FBS_MAX_RHAT_CHAINS];
+};
+cudaError_t launch_rhat(const RhatInput& in, double* out, cudaStream_t s);
+
 // learned proposal (fbs_learned.cu)
 int mlp_param_count(int L);
 cudaError_t launch_proposal_f32(const ModelConst& mc, const DevPtrsF32& p, const void* w_bf16,

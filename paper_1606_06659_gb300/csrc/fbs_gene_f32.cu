@@ -567,23 +567,23 @@ __device__ __forceinline__ void gb_f32_body(const ModelConst& mc, const DevPtrsF
     }
   }
 
-  // ---- partial sums: error-free FP32 pair sums within the warp, FP64 beyond
+  // ---- partial sums: error-free FP32 pair sums within the warp, FP64 beyond.
+  // Lane i < kNumPart sums row i of the warp's 32 values (read in an order
+  // rotated by i, so that the lanes hit distinct shared-memory banks).
   const int lane = tid & 31, warp = tid >> 5, nwarp = B >> 5;
   double* red = reinterpret_cast<double*>(
       smem_f + (((2 * (size_t)N + kMaxL + kNumPart) * B + 1) & ~(size_t)1));
-#pragma unroll
-  for (int i = 0; i < kNumPart; ++i) {
-    float s = ps[i * B + tid], c = 0.0f;
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) {
-      const float so = __shfl_down_sync(0xffffffffu, s, o);
-      const float co = __shfl_down_sync(0xffffffffu, c, o);
+  __syncwarp();
+  if (lane < kNumPart) {
+    const float* row = ps + (size_t)lane * B + warp * 32;
+    float sm = 0.0f, c = 0.0f;
+    for (int j = 0; j < 32; ++j) {
       float t, e;
-      two_sum(s, so, t, e);
-      s = t;
-      c = c + co + e;
+      two_sum(sm, row[(j + lane) & 31], t, e);
+      sm = t;
+      c += e;
     }
-    if (lane == 0) red[warp * kNumPart + i] = (double)s + (double)c;
+    red[warp * kNumPart + lane] = (double)sm + (double)c;
   }
   __syncthreads();
   if (tid < kNumPart) {

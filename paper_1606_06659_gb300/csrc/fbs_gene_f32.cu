@@ -108,17 +108,22 @@ struct EpsDensityF {
   }
 };
 
-struct BetaDensityF {
-  float bt, hs;  // bt = b0 - theta, hs = 1 / (2 sigma^2)
-  float b0;
+// Relative log density of beta_gl: with d = b - b0 and the column's value
+// classes j (value v_j, rate sum Q_j and count sum Y_j at b0, D_j = Y_j - Q_j),
+// Delta(b) = sum_j [v_j d D_j - Q_j em1mx(v_j d)] - d (d + 2 (b0 - theta)) / (2 sigma^2).
+// The class count NC is fixed at compile time, so that the loops run over the
+// classes a column has (NC = kMaxCls keeps the runtime bound `ncls`).
+template <int NC>
+struct BetaDensityFT {
+  float bt, hs, b0;
   int ncls;
-  float Q[kMaxCls], D[kMaxCls], v[kMaxCls];
+  float Q[NC], D[NC], v[NC];
   __device__ __forceinline__ float operator()(float b, float* aux) const {
     const float d = b - b0;
     float s = 0.0f;
 #pragma unroll
-    for (int j = 0; j < kMaxCls; ++j) {
-      if (j < ncls) {
+    for (int j = 0; j < NC; ++j) {
+      if (NC < kMaxCls || j < ncls) {
         const float z = v[j] * d;
         s += z * D[j] - Q[j] * em1mx(z);
       }
@@ -402,6 +407,79 @@ __device__ __forceinline__ bool mh_move_f32(const ModelConst& mc, const DevPtrsF
   return acc;
 }
 
+// One slice update of beta_gl (step 5) for a column with NC value classes:
+// class sums Q_j (rates) and Y_j (counts) from the per-thread rows in shared
+// memory, the update, and the rates carried to the new value.
+template <int NC>
+__device__ __forceinline__ void beta_column_f32(const ModelConst& mc, const DevPtrsF32& p, int l,
+                                                int g, float* mu, const float* ys, float* bs,
+                                                int B, int tid, const Hyper* hy, long long it,
+                                                uint32_t it32, long long burnin,
+                                                long long tune_start, unsigned& evals_b,
+                                                unsigned& caps, unsigned& nonfin) {
+  const int G = mc.G, N = mc.N, L = mc.L;
+  const size_t e = (size_t)l * G + g;
+  const float theta = (float)hy->phi[2 + l];
+  const float sig2 = (float)hy->phi[2 + L + l];
+  BetaDensityFT<NC> f;
+  const float b_cur = bs[l * B + tid];
+  f.b0 = b_cur;
+  f.bt = b_cur - theta;
+  f.hs = 0.5f / sig2;
+  f.ncls = mc.ncls[l];
+  float Y[NC];
+#pragma unroll
+  for (int j = 0; j < NC; ++j) {
+    f.Q[j] = 0.0f;
+    Y[j] = 0.0f;
+    f.v[j] = mc.cvalf[l][j];
+  }
+  for (int n = 0; n < N; ++n) {
+    const int c = mc.cls[l][n];
+    const float m = mu[n * B + tid];
+    const float yv = ys[n * B + tid];
+#pragma unroll
+    for (int j = 0; j < NC; ++j)
+      if (j == c) {
+        f.Q[j] += m;
+        Y[j] += yv;
+      }
+  }
+#pragma unroll
+  for (int j = 0; j < NC; ++j) f.D[j] = Y[j] - f.Q[j];
+  Rng4 r(mc.seed_lo, mc.seed_hi, mc.chain, kStreamBeta, (uint32_t)((size_t)g * L + l), it32);
+  const float x0 = b_cur;
+  float w = p.w_beta[e];
+  SliceResultF s = slice_update_f(x0, 0.0f, w, f, r, mc.K, mc.shrink_max);
+  evals_b += s.evals;
+  caps += s.capped;
+  nonfin += s.nonfinite;
+  if (s.x != x0) {
+    const float d = s.x - x0;
+    float fac[NC];
+#pragma unroll
+    for (int j = 0; j < NC; ++j) {
+      const float z = f.v[j] * d;
+      fac[j] = 1.0f + (z + em1mx(z));
+    }
+    for (int n = 0; n < N; ++n) {
+      const int c = mc.cls[l][n];
+      float fc = 1.0f;
+#pragma unroll
+      for (int j = 0; j < NC; ++j)
+        if (j == c) fc = fac[j];
+      mu[n * B + tid] *= fc;
+    }
+  }
+  bs[l * B + tid] = s.x;
+  if (it <= burnin) {
+    float waux = p.waux_beta[e];
+    tune_width_f(w, waux, it, s.x, x0, burnin, tune_start);
+    p.w_beta[e] = w;
+    p.waux_beta[e] = waux;
+  }
+}
+
 // Steps 2 and 5 of Algorithm 1 in the FP32 form: one thread per gene.  The
 // hyperparameter kernel of the previous iteration has finished when it runs.
 // Genes marked for the learned proposal first make its move (which keeps every
@@ -479,65 +557,22 @@ __device__ __forceinline__ void gb_f32_body(const ModelConst& mc, const DevPtrsF
     // ---- step 5: beta_gl, l = 1..L in order (genes without the learned move)
     const bool skip_slices = mh_gene && p.mh_replace;
     for (int l = 0; l < L && !skip_slices; ++l) {
-      const size_t e = (size_t)l * G + g;
-      const float theta = (float)hy->phi[2 + l];
-      const float sig2 = (float)hy->phi[2 + L + l];
-      BetaDensityF f;
-      const float b_cur = bs[l * B + tid];
-      f.b0 = b_cur;
-      f.bt = b_cur - theta;
-      f.hs = 0.5f / sig2;
-      f.ncls = mc.ncls[l];
-      float Y[kMaxCls];
-#pragma unroll
-      for (int j = 0; j < kMaxCls; ++j) {
-        f.Q[j] = 0.0f;
-        Y[j] = 0.0f;
-        f.v[j] = mc.cvalf[l][j];
-      }
-      for (int n = 0; n < N; ++n) {
-        const int c = mc.cls[l][n];
-        const float m = mu[n * B + tid];
-        const float yv = ys[n * B + tid];
-#pragma unroll
-        for (int j = 0; j < kMaxCls; ++j)
-          if (j == c) {
-            f.Q[j] += m;
-            Y[j] += yv;
-          }
-      }
-#pragma unroll
-      for (int j = 0; j < kMaxCls; ++j) f.D[j] = Y[j] - f.Q[j];
-      Rng4 r(mc.seed_lo, mc.seed_hi, mc.chain, kStreamBeta, (uint32_t)((size_t)g * L + l), it32);
-      const float x0 = b_cur;
-      float w = p.w_beta[e];
-      SliceResultF s = slice_update_f(x0, 0.0f, w, f, r, mc.K, mc.shrink_max);
-      evals_b += s.evals;
-      caps += s.capped;
-      nonfin += s.nonfinite;
-      if (s.x != x0) {
-        const float d = s.x - x0;
-        float fac[kMaxCls];
-#pragma unroll
-        for (int j = 0; j < kMaxCls; ++j) {
-          const float z = f.v[j] * d;
-          fac[j] = 1.0f + (z + em1mx(z));
-        }
-        for (int n = 0; n < N; ++n) {
-          const int c = mc.cls[l][n];
-          float fc = 1.0f;
-#pragma unroll
-          for (int j = 0; j < kMaxCls; ++j)
-            if (j == c) fc = fac[j];
-          mu[n * B + tid] *= fc;
-        }
-      }
-      bs[l * B + tid] = s.x;
-      if (it <= burnin) {
-        float waux = p.waux_beta[e];
-        tune_width_f(w, waux, it, s.x, x0, burnin, tune_start);
-        p.w_beta[e] = w;
-        p.waux_beta[e] = waux;
+      switch (mc.ncls[l]) {
+        case 1:
+          beta_column_f32<1>(mc, p, l, g, mu, ys, bs, B, tid, hy, it, it32, burnin, tune_start,
+                             evals_b, caps, nonfin);
+          break;
+        case 2:
+          beta_column_f32<2>(mc, p, l, g, mu, ys, bs, B, tid, hy, it, it32, burnin, tune_start,
+                             evals_b, caps, nonfin);
+          break;
+        case 3:
+          beta_column_f32<3>(mc, p, l, g, mu, ys, bs, B, tid, hy, it, it32, burnin, tune_start,
+                             evals_b, caps, nonfin);
+          break;
+        default:
+          beta_column_f32<kMaxCls>(mc, p, l, g, mu, ys, bs, B, tid, hy, it, it32, burnin,
+                                   tune_start, evals_b, caps, nonfin);
       }
     }
 

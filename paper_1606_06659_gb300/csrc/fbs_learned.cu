@@ -36,18 +36,18 @@ __host__ __device__ inline int mlp_n_params(int F, int K) {
   return kMlpHidden * F + kMlpHidden + kMlpHidden * kMlpHidden + kMlpHidden + K * kMlpHidden + K;
 }
 
-// Features of gene g, invariant under the move (which keeps eta = h + eps + X beta):
-// X^T (eta_g - h) / N, asinh(X^T y_g), log gamma_g, theta, log sigma.
-__device__ __forceinline__ void gene_features(const ModelConst& mc, const DevPtrsF32& p, int g,
-                                              const Hyper* hy, float* f) {
-  const int G = mc.G, N = mc.N, L = mc.L;
-  float a[kMaxL];
-#pragma unroll
-  for (int l = 0; l < kMaxL; ++l) a[l] = 0.0f;
+// Part of X^T (eta_g - h) over the samples n0 <= n < n1 (eta - h = eps + X beta).
+__device__ __forceinline__ void feature_sums(const ModelConst& mc, const DevPtrsF32& p, int g,
+                                             int n0, int n1, float* a) {
+  const int G = mc.G, L = mc.L;
   float b[kMaxL];
 #pragma unroll
-  for (int l = 0; l < kMaxL; ++l) b[l] = l < L ? p.beta[(size_t)l * G + g] : 0.0f;
-  for (int n = 0; n < N; ++n) {
+  for (int l = 0; l < kMaxL; ++l) {
+    a[l] = 0.0f;
+    b[l] = l < L ? p.beta[(size_t)l * G + g] : 0.0f;
+  }
+#pragma unroll 4
+  for (int n = n0; n < n1; ++n) {
     float lin = p.eps[(size_t)n * G + g];
 #pragma unroll
     for (int l = 0; l < kMaxL; ++l)
@@ -56,7 +56,14 @@ __device__ __forceinline__ void gene_features(const ModelConst& mc, const DevPtr
     for (int l = 0; l < kMaxL; ++l)
       if (l < L) a[l] += mc.Xf[n * kMaxL + l] * lin;
   }
-  const float invN = 1.0f / (float)N;
+}
+
+// The features of gene g from the sums a = X^T (eta_g - h): a / N, asinh(X^T y_g),
+// log gamma_g, theta, log sigma; all unchanged by the move, which keeps eta.
+__device__ __forceinline__ void finish_features(const ModelConst& mc, const DevPtrsF32& p, int g,
+                                                const Hyper* hy, const float* a, float* f) {
+  const int G = mc.G, L = mc.L;
+  const float invN = 1.0f / (float)mc.N;
   for (int l = 0; l < L; ++l) {
     f[l] = a[l] * invN;
     f[L + l] = asinhf((float)p.T[(size_t)l * G + g]);
@@ -64,6 +71,13 @@ __device__ __forceinline__ void gene_features(const ModelConst& mc, const DevPtr
     f[3 * L + 1 + l] = 0.5f * logf((float)hy->phi[2 + L + l]);
   }
   f[2 * L] = logf(p.gam[g]);
+}
+
+__device__ __forceinline__ void gene_features(const ModelConst& mc, const DevPtrsF32& p, int g,
+                                              const Hyper* hy, float* f) {
+  float a[kMaxL];
+  feature_sums(mc, p, g, 0, mc.N, a);
+  finish_features(mc, p, g, hy, a, f);
 }
 
 // ---------------------------------------------------------------- tensor-core inference
@@ -107,12 +121,14 @@ constexpr int kMaxK1 = (kMaxFeat + 15) & ~15;
 // Shared memory: the weight image, then one A operand buffer of 128 rows that
 // holds in turn the split features (2 k1 columns) and the split activations of
 // the two hidden layers (128 columns); each is dead once its GEMM completed.
-__host__ __device__ inline size_t tc_smem_layout(int L, size_t* off_a) {
+__host__ __device__ inline size_t tc_smem_layout(int L, size_t* off_a, size_t* off_stage = nullptr) {
   const TcShape t = tc_shape(L);
   const size_t a = ((size_t)t.bytes + 1023) & ~(size_t)1023;
   const size_t cols = 2 * t.k1 > 2 * kMlpHidden ? 2 * t.k1 : 2 * kMlpHidden;
+  const size_t stage = a + (size_t)128 * cols * 2;  // [128][kMaxL] floats
   if (off_a) *off_a = a;
-  return a + (size_t)128 * cols * 2;
+  if (off_stage) *off_stage = stage;
+  return stage + (size_t)128 * kMaxL * 4;
 }
 
 // Byte offset of element (r, c) of a canonical operand with kw columns.
@@ -120,24 +136,21 @@ __host__ __device__ inline uint32_t canon_off(int r, int c, int kw) {
   return (uint32_t)(((r >> 3) * (kw >> 3) + (c >> 3)) * 128 + (r & 7) * 16 + (c & 7) * 2);
 }
 
-__device__ __forceinline__ uint32_t bf16_pair(float a, float b) {
-  return (uint32_t)__bfloat16_as_ushort(__float2bfloat16_rn(a)) |
-         ((uint32_t)__bfloat16_as_ushort(__float2bfloat16_rn(b)) << 16);
-}
-
 // Row r, columns c0..c0+7 of an operand with kw = 2 kin columns: hi parts at
-// c0.., lo parts at kin + c0.. (16-byte stores).
+// c0.., lo parts at kin + c0.. (16-byte stores; pairs converted together).
 __device__ __forceinline__ void store_split8(uint8_t* base, int kin, int r, int c0,
                                              const float* v) {
-  float lo[8];
+  uint32_t h[4], l[4];
 #pragma unroll
-  for (int i = 0; i < 8; ++i) lo[i] = v[i] - __bfloat162float(__float2bfloat16_rn(v[i]));
-  const uint4 h = make_uint4(bf16_pair(v[0], v[1]), bf16_pair(v[2], v[3]), bf16_pair(v[4], v[5]),
-                             bf16_pair(v[6], v[7]));
-  const uint4 l = make_uint4(bf16_pair(lo[0], lo[1]), bf16_pair(lo[2], lo[3]),
-                             bf16_pair(lo[4], lo[5]), bf16_pair(lo[6], lo[7]));
-  *(uint4*)(base + canon_off(r, c0, 2 * kin)) = h;
-  *(uint4*)(base + canon_off(r, kin + c0, 2 * kin)) = l;
+  for (int i = 0; i < 4; ++i) {
+    const __nv_bfloat162 hb = __floats2bfloat162_rn(v[2 * i], v[2 * i + 1]);
+    const float2 hf = __bfloat1622float2(hb);
+    const __nv_bfloat162 lb = __floats2bfloat162_rn(v[2 * i] - hf.x, v[2 * i + 1] - hf.y);
+    h[i] = *reinterpret_cast<const uint32_t*>(&hb);
+    l[i] = *reinterpret_cast<const uint32_t*>(&lb);
+  }
+  *(uint4*)(base + canon_off(r, c0, 2 * kin)) = make_uint4(h[0], h[1], h[2], h[3]);
+  *(uint4*)(base + canon_off(r, kin + c0, 2 * kin)) = make_uint4(l[0], l[1], l[2], l[3]);
 }
 
 // The weight image the kernel copies into shared memory: W1 [64][2 k1],
@@ -276,21 +289,58 @@ __device__ __forceinline__ void tmem_ld16(uint32_t taddr, float* v) {
   for (int i = 0; i < 16; ++i) v[i] = __uint_as_float(r[i]);
 }
 
+// GELU (tanh form) for inference: x (1 + tanh u) / 2 = x / (1 + e^{-2u}), from the
+// fast exponential and division: about 1e-6 relative error, far below what the
+// proposal needs.
+__device__ __forceinline__ float gelu_fast(float x) {
+  const float u = kSqrt2OverPi * (x + 0.044715f * x * x * x);
+  return __fdividef(x, 1.0f + __expf(-2.0f * u));
+}
+
+// 32 consecutive FP32 columns of this thread's TMEM lane (one load, one wait).
+__device__ __forceinline__ void tmem_ld32(uint32_t taddr, float* v) {
+  uint32_t r[32];
+  asm volatile(
+      "tcgen05.ld.sync.aligned.32x32b.x32.b32 "
+      "{%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, %15, "
+      "%16, %17, %18, %19, %20, %21, %22, %23, %24, %25, %26, %27, %28, %29, %30, %31}, [%32];"
+      : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]),
+        "=r"(r[7]), "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]),
+        "=r"(r[14]), "=r"(r[15]), "=r"(r[16]), "=r"(r[17]), "=r"(r[18]), "=r"(r[19]),
+        "=r"(r[20]), "=r"(r[21]), "=r"(r[22]), "=r"(r[23]), "=r"(r[24]), "=r"(r[25]),
+        "=r"(r[26]), "=r"(r[27]), "=r"(r[28]), "=r"(r[29]), "=r"(r[30]), "=r"(r[31])
+      : "r"(taddr));
+  asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+#pragma unroll
+  for (int i = 0; i < 32; ++i) v[i] = __uint_as_float(r[i]);
+}
+
+// Bias, GELU and the split store of this thread's 32 columns c0.. of a hidden layer.
+__device__ __forceinline__ void hidden_epilogue(uint32_t taddr, const float* bias, uint8_t* abuf,
+                                                int row, int c0) {
+  float v[32];
+  tmem_ld32(taddr, v);
+#pragma unroll
+  for (int i = 0; i < 32; i += 4) {
+    const float4 bb = *reinterpret_cast<const float4*>(bias + c0 + i);
+    v[i] = gelu_fast(v[i] + bb.x);
+    v[i + 1] = gelu_fast(v[i + 1] + bb.y);
+    v[i + 2] = gelu_fast(v[i + 2] + bb.z);
+    v[i + 3] = gelu_fast(v[i + 3] + bb.w);
+  }
+#pragma unroll
+  for (int i = 0; i < 32; i += 8) store_split8(abuf, kMlpHidden, row, c0 + i, v + i);
+}
+
 constexpr uint32_t kTmemCols = 128;  // D1 at columns 0..63, D2 at 64..127, D3 at 0..n3-1
 constexpr int kTcThreads = 256;      // two warps per TMEM lane quadrant
 
-// GELU (tanh form) for inference, with tanh(u) = 1 - 2 / (1 + e^{2u}) from the
-// fast exponential: about 1e-6 absolute error, far below what the proposal needs.
-__device__ __forceinline__ float gelu_fast(float x) {
-  const float u = kSqrt2OverPi * (x + 0.044715f * x * x * x);
-  const float th = 1.0f - 2.0f / (1.0f + __expf(2.0f * u));
-  return 0.5f * x * (1.0f + th);
-}
 
 // Persistent over tiles of 128 genes; writes the proposal parameters [K][G] of
-// the genes that use the move (every gene when p.mh_all).  Threads 0..127
-// compute the features (thread = gene = TMEM lane); in the epilogues warp w
-// reads lane quadrant w % 4 and column half w / 4.  A wait that gives up sets
+// the genes that use the move (every gene when p.mh_all).  Threads t and
+// t + 128 sum the features of gene row t over the two halves of the samples and
+// thread t writes its split row of the first operand (row = TMEM lane); in the
+// epilogues warp w reads lane quadrant w % 4 and column half w / 4.  A wait that gives up sets
 // kFlagTimeout, and the CTA frees its tensor memory and returns.
 __global__ void __launch_bounds__(kTcThreads) k_proposal_tc(ModelConst mc, DevPtrsF32 p,
                                                            const uint8_t* __restrict__ img_g,
@@ -300,9 +350,10 @@ __global__ void __launch_bounds__(kTcThreads) k_proposal_tc(ModelConst mc, DevPt
   __shared__ uint32_t tmem_slot;
   __shared__ int s_abort;
   const TcShape t = tc_shape(mc.L);
-  size_t off_a;
-  tc_smem_layout(mc.L, &off_a);
+  size_t off_a, off_stage;
+  tc_smem_layout(mc.L, &off_a, &off_stage);
   uint8_t* abuf = sm + off_a;
+  float* stage = (float*)(sm + off_stage);
   const float* bias = (const float*)(sm + t.off_b);
   const int tid = threadIdx.x, warp = tid >> 5, lane_id = tid & 31;
   const int quad = warp & 3, half = warp >> 2;
@@ -349,14 +400,33 @@ __global__ void __launch_bounds__(kTcThreads) k_proposal_tc(ModelConst mc, DevPt
   for (int tile = blockIdx.x; tile < ntiles && !s_abort; tile += gridDim.x) {
     const int g = tile * 128 + row;
     const bool act = g < G && (p.mh_all || p.use_mh[g]);
-    if (tid < 128) {
-      float f[kMaxK1];
+    // features: threads 0..127 sum X^T (eta - h) over the first half of the
+    // samples, threads 128..255 over the second half (same gene: row = tid % 128)
+    {
+      float a[kMaxL];
+      const int nh = mc.N / 2;
+      if (act) {
+        if (half == 0) feature_sums(mc, p, g, 0, nh, a);
+        else feature_sums(mc, p, g, nh, mc.N, a);
+      }
+      if (half == 1 && act) {
 #pragma unroll
-      for (int i = 0; i < kMaxK1; ++i) f[i] = 0.0f;
-      if (act) gene_features(mc, p, g, p.hyp, f);
+        for (int l = 0; l < kMaxL; ++l) stage[row * kMaxL + l] = a[l];
+      }
+      __syncthreads();
+      if (half == 0) {
+        float f[kMaxK1];
 #pragma unroll
-      for (int c0 = 0; c0 < kMaxK1; c0 += 8)
-        if (c0 < t.k1) store_split8(abuf, t.k1, row, c0, f + c0);
+        for (int i = 0; i < kMaxK1; ++i) f[i] = 0.0f;
+        if (act) {
+#pragma unroll
+          for (int l = 0; l < kMaxL; ++l) a[l] += stage[row * kMaxL + l];
+          finish_features(mc, p, g, p.hyp, a, f);
+        }
+#pragma unroll
+        for (int c0 = 0; c0 < kMaxK1; c0 += 8)
+          if (c0 < t.k1) store_split8(abuf, t.k1, row, c0, f + c0);
+      }
     }
 
     // ---- layer 1: D1 = A1 W1^T
@@ -373,15 +443,7 @@ __global__ void __launch_bounds__(kTcThreads) k_proposal_tc(ModelConst mc, DevPt
     else pending = false;
     ph ^= 1u;
     tc_fence_after();
-#pragma unroll
-    for (int c0 = half * 32; c0 < half * 32 + 32; c0 += 16) {
-      float v[16];
-      tmem_ld16(tmem + lane_addr + (uint32_t)c0, v);
-#pragma unroll
-      for (int i = 0; i < 16; ++i) v[i] = gelu_fast(v[i] + bias[c0 + i]);
-      store_split8(abuf, kMlpHidden, row, c0, v);
-      store_split8(abuf, kMlpHidden, row, c0 + 8, v + 8);
-    }
+    hidden_epilogue(tmem + lane_addr + (uint32_t)(half * 32), bias, abuf, row, half * 32);
 
     // ---- layer 2: D2 = A2 W2^T (A2 overwrote A1 after GEMM 1 completed)
     fence_async_smem();
@@ -398,15 +460,8 @@ __global__ void __launch_bounds__(kTcThreads) k_proposal_tc(ModelConst mc, DevPt
     else pending = false;
     ph ^= 1u;
     tc_fence_after();
-#pragma unroll
-    for (int c0 = half * 32; c0 < half * 32 + 32; c0 += 16) {
-      float v[16];
-      tmem_ld16(tmem + lane_addr + (uint32_t)(kMlpHidden + c0), v);
-#pragma unroll
-      for (int i = 0; i < 16; ++i) v[i] = gelu_fast(v[i] + bias[kMlpHidden + c0 + i]);
-      store_split8(abuf, kMlpHidden, row, c0, v);
-      store_split8(abuf, kMlpHidden, row, c0 + 8, v + 8);
-    }
+    hidden_epilogue(tmem + lane_addr + (uint32_t)(kMlpHidden + half * 32), bias + kMlpHidden, abuf,
+                    row, half * 32);
 
     // ---- layer 3: D3 = A3 W3^T (D3 reuses D1's columns)
     fence_async_smem();

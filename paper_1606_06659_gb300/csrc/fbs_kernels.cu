@@ -68,6 +68,35 @@ struct BetaDensity {
   }
 };
 
+// BetaDensity with the class count NC fixed at compile time (NC = kMaxCls keeps
+// the runtime bound `ncls`); the same arithmetic over the classes a column has.
+template <int NC>
+struct BetaDensityT {
+  double T, b0, theta, hs;
+  int ncls;
+  double Q[NC];
+  double v[NC];
+  int8_t kind[NC];
+  __device__ __forceinline__ double operator()(double b, double* aux) const {
+    const double dlt = b - b0;
+    const double z = exp(dlt);
+    double s = 0.0;
+#pragma unroll
+    for (int j = 0; j < NC; ++j) {
+      if (NC < kMaxCls || j < ncls) {
+        double e;
+        if (kind[j] == kClsPlus) e = z;
+        else if (kind[j] == kClsMinus) e = 1.0 / z;
+        else e = exp(v[j] * dlt);
+        s += Q[j] * e;
+      }
+    }
+    *aux = z;
+    const double dv = b - theta;
+    return b * T - s - dv * dv * hs;
+  }
+};
+
 // ---------------------------------------------------------------- block reduction
 
 template <int NV>
@@ -348,6 +377,89 @@ __global__ void __launch_bounds__(256) k_eps_f64(ModelConst mc, DevPtrs p, int s
 
 // Steps 2 and 5: one thread per gene, after the eps kernel of this sweep and the
 // hyperparameter kernel of the previous one.
+// One slice update of beta_gl (step 5) for a column with NC value classes, with
+// the class sums of the rates in shared memory, the moments, trace and partials.
+template <int NC>
+__device__ __forceinline__ void beta_column_f64(const ModelConst& mc, const DevPtrs& p, int l,
+                                                int g, double* mu, double* bs, double* ps, int B,
+                                                int tid, const Hyper* hy, long long it,
+                                                uint32_t it32, long long burnin,
+                                                long long tune_start, bool mom, double inv_k,
+                                                bool trace_now, long long trace_row,
+                                                unsigned& evals_b, unsigned& caps,
+                                                unsigned& nonfin) {
+  const int G = mc.G, N = mc.N, L = mc.L;
+  const size_t e = (size_t)l * G + g;
+  const double theta = hy->phi[2 + l];
+  const double sig2 = hy->phi[2 + L + l];
+  BetaDensityT<NC> f;
+  f.T = p.T[e];
+  const double b_cur = bs[l * B + tid];
+  f.b0 = b_cur;
+  f.theta = theta;
+  f.hs = 0.5 / sig2;
+  f.ncls = mc.ncls[l];
+#pragma unroll
+  for (int j = 0; j < NC; ++j) {
+    f.Q[j] = 0.0;
+    f.v[j] = mc.cval[l][j];
+    f.kind[j] = mc.ckind[l][j];
+  }
+  for (int n = 0; n < N; ++n) {
+    const int c = mc.cls[l][n];
+    const double m = mu[n * blockDim.x + tid];
+#pragma unroll
+    for (int j = 0; j < NC; ++j)
+      if (j == c) f.Q[j] += m;
+  }
+  Rng r(mc.seed_lo, mc.seed_hi, mc.chain, kStreamBeta, (uint32_t)((size_t)g * L + l), it32);
+  const double x0 = b_cur;
+  double w = p.w_beta[e];
+  SliceResult s = slice_update(x0, w, f, r, mc.K, mc.shrink_max);
+  evals_b += s.evals;
+  caps += s.capped;
+  nonfin += s.nonfinite;
+  if (s.x != x0) {
+    const double dlt = s.x - x0;
+    double ej[NC];
+    const double z = exp(dlt);
+#pragma unroll
+    for (int j = 0; j < NC; ++j) {
+      ej[j] = 1.0;
+      if (NC < kMaxCls || j < f.ncls) {
+        if (f.kind[j] == kClsPlus) ej[j] = z;
+        else if (f.kind[j] == kClsMinus) ej[j] = 1.0 / z;
+        else ej[j] = exp(f.v[j] * dlt);
+      }
+    }
+    for (int n = 0; n < N; ++n) {
+      const int c = mc.cls[l][n];
+      double fac = 1.0;
+#pragma unroll
+      for (int j = 0; j < NC; ++j)
+        if (j == c) fac = ej[j];
+      mu[n * blockDim.x + tid] *= fac;
+    }
+  }
+  bs[l * B + tid] = s.x;
+  p.beta[e] = s.x;
+  if (it <= burnin) {
+    double waux = p.waux_beta[e];
+    tune_width(w, waux, it, s.x, x0, burnin, tune_start);
+    p.w_beta[e] = w;
+    p.waux_beta[e] = waux;
+  }
+  if (mom) {
+    const double m = p.m_beta[e], q = p.q_beta[e];
+    p.m_beta[e] = m + (s.x - m) * inv_k;
+    p.q_beta[e] = q + (s.x * s.x - q) * inv_k;
+  }
+  if (trace_now) p.trace_beta[(size_t)trace_row * L * G + e] = s.x;
+  const double dv = s.x - theta;
+  ps[(2 + l) * B + tid] = dv;
+  ps[(2 + kMaxL + l) * B + tid] = dv * dv;
+}
+
 __global__ void __launch_bounds__(128) k_gb_f64(ModelConst mc, DevPtrs p, int seg_i) {
   // shared: mu[N][B], beta[L][B], partials[kNumPart][B] (values indexed by a runtime
   // l live here rather than in local memory), then the reduction scratch
@@ -407,75 +519,23 @@ __global__ void __launch_bounds__(128) k_gb_f64(ModelConst mc, DevPtrs p, int se
 
     // ---- step 5: beta_gl, l = 1..L in order
     for (int l = 0; l < L; ++l) {
-      const size_t e = (size_t)l * G + g;
-      const double theta = hy->phi[2 + l];
-      const double sig2 = hy->phi[2 + L + l];
-      BetaDensity f;
-      f.T = p.T[e];
-      const double b_cur = bs[l * B + tid];
-      f.b0 = b_cur;
-      f.theta = theta;
-      f.hs = 0.5 / sig2;
-      f.ncls = mc.ncls[l];
-#pragma unroll
-      for (int j = 0; j < kMaxCls; ++j) {
-        f.Q[j] = 0.0;
-        f.v[j] = mc.cval[l][j];
-        f.kind[j] = mc.ckind[l][j];
+      switch (mc.ncls[l]) {
+        case 1:
+          beta_column_f64<1>(mc, p, l, g, mu, bs, ps, B, tid, hy, it, it32, burnin, tune_start, mom, inv_k,
+                               trace_now, trace_row, evals_b, caps, nonfin);
+          break;
+        case 2:
+          beta_column_f64<2>(mc, p, l, g, mu, bs, ps, B, tid, hy, it, it32, burnin, tune_start, mom, inv_k,
+                               trace_now, trace_row, evals_b, caps, nonfin);
+          break;
+        case 3:
+          beta_column_f64<3>(mc, p, l, g, mu, bs, ps, B, tid, hy, it, it32, burnin, tune_start, mom, inv_k,
+                               trace_now, trace_row, evals_b, caps, nonfin);
+          break;
+        default:
+          beta_column_f64<kMaxCls>(mc, p, l, g, mu, bs, ps, B, tid, hy, it, it32, burnin, tune_start, mom, inv_k,
+                               trace_now, trace_row, evals_b, caps, nonfin);
       }
-      for (int n = 0; n < N; ++n) {
-        const int c = mc.cls[l][n];
-        const double m = mu[n * blockDim.x + tid];
-#pragma unroll
-        for (int j = 0; j < kMaxCls; ++j)
-          if (j == c) f.Q[j] += m;
-      }
-      Rng r(mc.seed_lo, mc.seed_hi, mc.chain, kStreamBeta, (uint32_t)((size_t)g * L + l), it32);
-      const double x0 = b_cur;
-      double w = p.w_beta[e];
-      SliceResult s = slice_update(x0, w, f, r, mc.K, mc.shrink_max);
-      evals_b += s.evals;
-      caps += s.capped;
-      nonfin += s.nonfinite;
-      if (s.x != x0) {
-        const double dlt = s.x - x0;
-        double ej[kMaxCls];
-        const double z = exp(dlt);
-#pragma unroll
-        for (int j = 0; j < kMaxCls; ++j) {
-          ej[j] = 1.0;
-          if (j < f.ncls) {
-            if (f.kind[j] == kClsPlus) ej[j] = z;
-            else if (f.kind[j] == kClsMinus) ej[j] = 1.0 / z;
-            else ej[j] = exp(f.v[j] * dlt);
-          }
-        }
-        for (int n = 0; n < N; ++n) {
-          const int c = mc.cls[l][n];
-          double fac = 1.0;
-#pragma unroll
-          for (int j = 0; j < kMaxCls; ++j)
-            if (j == c) fac = ej[j];
-          mu[n * blockDim.x + tid] *= fac;
-        }
-      }
-      bs[l * B + tid] = s.x;
-      p.beta[e] = s.x;
-      if (it <= burnin) {
-        double waux = p.waux_beta[e];
-        tune_width(w, waux, it, s.x, x0, burnin, tune_start);
-        p.w_beta[e] = w;
-        p.waux_beta[e] = waux;
-      }
-      if (mom) {
-        const double m = p.m_beta[e], q = p.q_beta[e];
-        p.m_beta[e] = m + (s.x - m) * inv_k;
-        p.q_beta[e] = q + (s.x * s.x - q) * inv_k;
-      }
-      if (trace_now) p.trace_beta[(size_t)trace_row * L * G + e] = s.x;
-      const double dv = s.x - theta;
-      ps[(2 + l) * B + tid] = dv;
-      ps[(2 + kMaxL + l) * B + tid] = dv * dv;
     }
     // contrast probabilities (§3.1): count the iterations whose beta_g satisfies
     // each proposition

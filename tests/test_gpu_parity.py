@@ -166,3 +166,11 @@ def test_paper_scale_lockstep_sweep():
     sweeps over every gene (the oracle finishes one sweep in about a second)."""
     d = synthetic.make_config(1)
     _lockstep(d, n_sweeps=2, burnin=10)
+
+
+def test_precision_stress_scale_lockstep_sweep():
+    """Configuration 2's shape, N=32 (8 libraries per variety), G=200000, L=5:
+    one lockstep sweep over every gene against the oracle (a few seconds)."""
+    d = synthetic.make_config(2)
+    assert d["y"].shape == (200000, 32)
+    _lockstep(d, n_sweeps=1, burnin=10)

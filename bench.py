@@ -79,17 +79,24 @@ def parse():
 # --------------------------------------------------------------------------- helpers
 # FP64 floating-point operations per slice log-density evaluation of the FP64
 # sweep kernels k_eps_f64 + k_gb_f64 (DFMA counted as 2, DADD and DMUL as 1),
-# from one ncu capture of each at config 1: (2*87.34 + 20.94 + 11.42) thread
-# instructions per elapsed cycle x 1.124e6 cycles (eps) + (2*74.41 + 27.38 +
-# 14.17) x 6.21e5 cycles (gb) = 3.51e8 flop per sweep, over 5.28e6 device-counted
-# evaluations per sweep.  It covers everything the kernels do per evaluation on
-# average (density, Philox-to-double, interval arithmetic, the per-draw log,
-# moments).  Re-measure when the kernels change.
-FP64_FLOP_PER_EVAL = 66.4
+# from one ncu capture of each at config 1: 2.328e8 (eps) + 1.152e8 (gb) flop
+# per sweep (per-cycle DFMA/DADD/DMUL thread counts x elapsed cycles) over the
+# 6.157e6 log-density evaluations the device counted per sweep in the captured
+# run = 56.5.  It covers everything the kernels do per evaluation on average
+# (density, Philox-to-double, interval arithmetic, the per-draw log, moments).
+# Re-measure when the kernels change.
+FP64_FLOP_PER_EVAL = 56.5
 FP64_TRAFFIC_BYTES = 44.0e6   # dram read+write of both kernels per sweep, same captures
-# dram read+write of k_eps_f32 (18.9 MB) + k_gb_f32 (16.9 MB, with the learned
-# move) per sweep from one ncu capture each at config 1 (writes stay in L2)
-FP32_TRAFFIC_BYTES = 35.8e6
+# FP32 forms: warp instructions issued per sweep by k_eps_f32 + k_gb_f32 and
+# their dram read+write (writes stay in L2), one ncu capture each at config 1
+FP32_WARP_INST = {"f32": 21.76e6 + 10.68e6, "learned": 21.78e6 + 14.19e6}
+FP32_TRAFFIC_BYTES = {"f32": 18.9e6 + 13.2e6, "learned": 18.9e6 + 16.9e6}
+# issue peak: 152 SMs x 4 schedulers x 1 warp instruction per clock x 2.07 GHz
+ISSUE_PEAK_WARP_INST_S = 152 * 4 * 2.07e9
+# the proposal network's own flops per gene (2 x (F*64 + 64*64 + 64*K), F = 21,
+# K = 20) and the tensor-core flops its split-BF16 GEMMs issue per gene
+NET_FLOP_PER_GENE = 2 * (21 * 64 + 64 * 64 + 64 * 20)
+MMA_FLOP_PER_GENE = 2 * 3 * (32 * 64 + 64 * 64 + 64 * 32)
 # FP64 peak from unit counts and clock: 152 SMs x 2 DFMA/clk x 2 flop x 2.07 GHz
 FP64_PEAK_TFLOPS = 152 * 2 * 2 * 2.07e9 / 1e12
 
@@ -469,11 +476,29 @@ def main():
                     "flop_per_eval": FP64_FLOP_PER_EVAL, "evals_per_launch": ev_launch,
                     "peak_source": "152 SMs x 2 DFMA/clk x 2 flop x 2.07 GHz", "hbm": hbm}
     else:
-        roofline = dict(hbm, bound="hbm", traffic=FP32_TRAFFIC_BYTES, kernel="k_eps_f32 + k_gb_f32",
-                        kernel_ms=ms_gene, eps_kernel_ms=ms_k1, gb_kernel_ms=ms_k2,
-                        hyper_kernel_ms=ms_hyper, evals_per_launch=ev_launch)
+        inst = FP32_WARP_INST[form]
+        rate = inst / (ms_gene / 1e3)
+        roofline = {"bound": "alu", "achieved": rate, "peak": ISSUE_PEAK_WARP_INST_S,
+                    "unit": "warp-instructions/s", "frac": rate / ISSUE_PEAK_WARP_INST_S,
+                    "traffic": FP32_TRAFFIC_BYTES[form], "kernel": "k_eps_f32 + k_gb_f32",
+                    "kernel_ms": ms_gene, "eps_kernel_ms": ms_k1, "gb_kernel_ms": ms_k2,
+                    "hyper_kernel_ms": ms_hyper, "warp_instructions_per_sweep": inst,
+                    "evals_per_launch": ev_launch,
+                    "peak_source": "152 SMs x 4 schedulers x 1 warp instruction/clk x 2.07 GHz",
+                    "hbm": hbm}
         if form == "learned":
-            roofline["proposal_kernel_ms"] = ms_prop
+            try:
+                with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+                    bf16, src = float(json.load(f)["bf16_tflops_sustained"]), "measured"
+            except (OSError, KeyError, ValueError):
+                bf16, src = 1700.0, "fallback"
+            tf = NET_FLOP_PER_GENE * G / (ms_prop / 1e3) / 1e12
+            roofline["proposal"] = {
+                "kernel": "k_proposal_tc", "bound": "tensor", "kernel_ms": ms_prop,
+                "achieved": tf, "peak": bf16, "unit": "TFLOP/s", "frac": tf / bf16,
+                "flop_per_launch": NET_FLOP_PER_GENE * G,
+                "mma_flop_per_launch": MMA_FLOP_PER_GENE * G,
+                "peak_source": src + " bf16 sustained"}
     st = smp.proposal_stats() if form == "learned" else None
     smp.close()
 

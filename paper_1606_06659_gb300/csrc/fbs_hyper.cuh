@@ -37,16 +37,22 @@ __device__ __forceinline__ void hyper_body(const ModelConst& mc, const double* p
   __shared__ double red[kHyperThreads / 32][kNumPart];
   __shared__ double tot[kNumPart];
   __shared__ double phi_new[kMaxP];
+  __shared__ Hyper sh;  // a copy of the chain's Hyper block: one load instead of a
+                        // chain of dependent global reads on the serial path
+  static_assert(sizeof(Hyper) % 8 == 0, "Hyper is copied as 8-byte words");
   const int L = mc.L, P = mc.P;
   const double G = (double)mc.G;
+  const int tid = threadIdx.x;
+  for (int i = tid; i < (int)(sizeof(Hyper) / 8); i += kHyperThreads)
+    reinterpret_cast<unsigned long long*>(&sh)[i] = reinterpret_cast<const unsigned long long*>(hy)[i];
   const long long it = hy->it + 1;
   const uint32_t it32 = (uint32_t)it;
-  const int tid = threadIdx.x;
 
   // fixed-order reduction of the per-block partials
   double acc[kNumPart];
 #pragma unroll
   for (int i = 0; i < kNumPart; ++i) acc[i] = 0.0;
+#pragma unroll 2
   for (int b = tid; b < nblk; b += kHyperThreads) {
 #pragma unroll
     for (int i = 0; i < kNumPart; ++i) acc[i] += partial[(size_t)b * kNumPart + i];
@@ -58,7 +64,8 @@ __device__ __forceinline__ void hyper_body(const ModelConst& mc, const double* p
     for (int o = 16; o > 0; o >>= 1) x += __shfl_down_sync(0xffffffffu, x, o);
     if ((tid & 31) == 0) red[tid >> 5][i] = x;
   }
-  if (tid < kMaxP) phi_new[tid] = tid < P ? hy->phi[tid] : 0.0;
+  __syncthreads();
+  if (tid < kMaxP) phi_new[tid] = tid < P ? sh.phi[tid] : 0.0;
   __syncthreads();
   if (tid < kNumPart) {
     double s = 0.0;
@@ -70,16 +77,16 @@ __device__ __forceinline__ void hyper_body(const ModelConst& mc, const double* p
   const double S1 = tot[0], S2 = tot[1];
   if (tid < 32) {
     // step 3: nu, the slice update spread over warp 0
-    const double tau_old = hy->phi[1];
+    const double tau_old = sh.phi[1];
     NuDensity f{G, mc.d, tau_old, S1, S2};
     Rng r(mc.seed_lo, mc.seed_hi, mc.chain, kStreamNu, 0u, it32);
-    const double x0 = hy->phi[0];
-    SliceResult s = slice_update_warp(x0, hy->w_nu, f, r, mc.K, mc.shrink_max);
+    const double x0 = sh.phi[0];
+    SliceResult s = slice_update_warp(x0, sh.w_nu, f, r, mc.K, mc.shrink_max);
     if (tid == 0) {
       const double nu = s.x;
-      if (it <= hy->burnin) {
-        double w = hy->w_nu, waux = hy->waux_nu;
-        tune_width(w, waux, it, nu, x0, hy->burnin, hy->tune_start);
+      if (it <= sh.burnin) {
+        double w = sh.w_nu, waux = sh.waux_nu;
+        tune_width(w, waux, it, nu, x0, sh.burnin, sh.tune_start);
         hy->w_nu = w;
         hy->waux_nu = waux;
       }
@@ -103,8 +110,8 @@ __device__ __forceinline__ void hyper_body(const ModelConst& mc, const double* p
     const int l = tid - 32;
     // step 6: theta_l ~ N(v B1 / sigma^2, v), v = 1/(G/sigma^2 + 1/c^2);
     // the partials hold B1' = sum (beta - theta_old), B2' = sum (beta - theta_old)^2
-    const double th_old = hy->phi[2 + l];
-    const double sig2 = hy->phi[2 + L + l];
+    const double th_old = sh.phi[2 + l];
+    const double sig2 = sh.phi[2 + L + l];
     const double B1s = tot[2 + l], B2s = tot[2 + kMaxL + l];
     const double B1 = B1s + G * th_old;
     const double v = 1.0 / (G / sig2 + 1.0 / mc.c2[l]);
@@ -124,25 +131,25 @@ __device__ __forceinline__ void hyper_body(const ModelConst& mc, const double* p
   }
   __syncthreads();
 
-  const bool mom = it > hy->burnin;
+  const bool mom = it > sh.burnin;
   if (tid < P) {
     const double x = phi_new[tid];
     hy->phi[tid] = x;
     if (mom) {
-      const double inv_k = 1.0 / (double)(hy->n_mom + 1);
-      const double m = hy->m_phi[tid], q = hy->q_phi[tid];
+      const double inv_k = 1.0 / (double)(sh.n_mom + 1);
+      const double m = sh.m_phi[tid], q = sh.q_phi[tid];
       hy->m_phi[tid] = m + (x - m) * inv_k;
       hy->q_phi[tid] = q + (x * x - q) * inv_k;
     }
-    if (mom && ((it - hy->burnin) % hy->thin == 0) && hy->trace_rows < hy->trace_cap &&
+    if (mom && ((it - sh.burnin) % sh.thin == 0) && sh.trace_rows < sh.trace_cap &&
         trace_phi != nullptr)
-      trace_phi[(size_t)hy->trace_rows * P + tid] = x;
+      trace_phi[(size_t)sh.trace_rows * P + tid] = x;
   }
   __syncthreads();
   if (tid == 0) {
-    if (mom && ((it - hy->burnin) % hy->thin == 0) && hy->trace_rows < hy->trace_cap)
-      hy->trace_rows += 1;
-    if (mom) hy->n_mom += 1;
+    if (mom && ((it - sh.burnin) % sh.thin == 0) && sh.trace_rows < sh.trace_cap)
+      hy->trace_rows = sh.trace_rows + 1;
+    if (mom) hy->n_mom = sh.n_mom + 1;
     hy->it = it;
     atomicAdd(&counters[FBS_CNT_SWEEPS], 1ull);
   }

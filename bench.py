@@ -290,6 +290,13 @@ FORM_TEXT = {
 PAIR_SWEEPS = 50          # x thin 2 x G = 2e6 training pairs at G = 40000
 TRAIN = {"epochs": 15, "batch": 4096, "lr": 2e-3}
 CALIBRATE_SWEEPS = 100
+# Calibration threshold of the learned move.  The headline form adds the move to
+# the slice updates of beta_g (mode 1), so the slice sampler always runs and the
+# threshold only decides whether a gene also makes the move: any gene whose
+# better proposal accepts 1% of the time gains from it (each accepted move is a
+# nearly independent draw of beta_g given the log-rates).  The 0.2 of the
+# configured fallback applies where the move replaces the slice updates (mode 2).
+MIN_ACCEPT = 0.01
 
 
 def new_sampler(fbs, data, y, form, seed, chain, block, **kw):
@@ -330,11 +337,13 @@ def ess_job(fbs, torch, data, y_host, form, seed, chain, block, S, train_epochs)
         smp.proposal_collect(PAIR_SWEEPS, burnin=burnin, thin=2)
         done += 2 * PAIR_SWEEPS
         loss = smp.proposal_train(seed=seed, **dict(TRAIN, epochs=train_epochs))
-        smp.proposal_calibrate(CALIBRATE_SWEEPS, burnin=burnin, min_accept=0.2)
+        smp.proposal_calibrate(CALIBRATE_SWEEPS, burnin=burnin, min_accept=MIN_ACCEPT)
         done += CALIBRATE_SWEEPS
+        st0 = smp.proposal_stats()
         extra = {"train_pairs": PAIR_SWEEPS * data["y"].shape[0], "train_loss": loss,
                  "collect_train_calibrate_s": time.perf_counter() - tt,
-                 "mh_genes": smp.proposal_stats()["mh_genes"]}
+                 "mh_genes": st0["mh_genes"], "prior_genes": st0["prior_genes"],
+                 "min_accept": MIN_ACCEPT}
     advance(iters)
     ev1.record(stream)
     mom = smp.moments()
@@ -424,7 +433,7 @@ def main():
             smp.proposal_train(seed=seed, **dict(TRAIN, epochs=args.train_epochs))
         else:
             smp.proposal_params(set_to=params)
-        smp.proposal_calibrate(CALIBRATE_SWEEPS, burnin=tb, min_accept=0.2)
+        smp.proposal_calibrate(CALIBRATE_SWEEPS, burnin=tb, min_accept=MIN_ACCEPT)
     flush = torch.empty(L2_FLUSH_BYTES, dtype=torch.uint8, device="cuda")
     for i in range(args.warmup):
         flush.fill_(i & 0xFF)

@@ -274,9 +274,13 @@ int fbs_proposal_collect(fbs_handle* h, int64_t n_sweeps, int64_t burnin, int64_
 int fbs_proposal_train(fbs_handle* h, int epochs, int batch, double lr, uint64_t seed,
                        double* final_loss);
 
-/* Run n_sweeps sweeps in which every gene attempts the learned move, then fix
- * for every gene whether it uses the move (acceptance rate >= min_accept) or
- * only the slice updates, and set mode 1. */
+/* Run n_sweeps sweeps in which every gene attempts the move, with the network's
+ * proposal on even and the prior-centred proposal (centre theta, scale
+ * diag(sigma), the same t family) on odd sweeps; then fix for every gene the
+ * proposal with the higher acceptance rate if that rate reaches min_accept,
+ * else only the slice updates, and set mode 1.  The prior-centred proposal suits
+ * genes whose conditional is close to the prior (very large gamma_g), where the
+ * network, trained mostly on typical genes, extrapolates poorly. */
 int fbs_proposal_calibrate(fbs_handle* h, int64_t n_sweeps, int64_t burnin, double min_accept);
 
 /* 0: plain slice updates for every gene; 1: the genes the calibration selected
@@ -295,15 +299,22 @@ int fbs_proposal_params(fbs_handle* h, float* get, const float* set, int n);
  * entries in row order.  Synchronous. */
 int fbs_proposal_outputs(fbs_handle* h, float* out);
 
-/* One learned move at the current state, without the other updates of a sweep:
- * the genes the calibration selected (every gene if all_genes = 1) propose and
+/* One move at the current state, without the other updates of a sweep: the
+ * genes the calibration selected with their proposals (all_genes = 0), or every
+ * gene with the network's (1) or the prior-centred (2) proposal, propose and
  * accept or reject with the random numbers of iteration `it` (1 <= it < 2^32),
  * counting into fbs_proposal_stats.  The state keeps every log-rate.  Synchronous. */
 int fbs_proposal_step(fbs_handle* h, int64_t it, int all_genes);
 
-/* Accepted and attempted moves since the calibration, and the number of genes
- * that use the learned move. */
-int fbs_proposal_stats(fbs_handle* h, int64_t* accepted, int64_t* tried, int* n_mh_genes);
+/* The proposal each gene uses (host [G]): 0 only the slice updates, 1 the
+ * network's, 2 the prior-centred one (all 0 before a calibration). */
+int fbs_proposal_kinds(fbs_handle* h, uint8_t* kinds);
+
+/* Accepted and attempted moves since the calibration, the number of genes that
+ * make the move and how many of them use the prior-centred proposal (each
+ * output may be NULL). */
+int fbs_proposal_stats(fbs_handle* h, int64_t* accepted, int64_t* tried, int* n_mh_genes,
+                       int* n_prior_genes);
 
 /* One forward and backward pass of the network on a host batch (features [B][F],
  * beta [B][L]) through the training kernels: *loss = mean negative

@@ -38,7 +38,7 @@ EXPORTED = ("fbs_default_options", "fbs_workspace_bytes", "fbs_init", "fbs_run",
             "fbs_proposal_train", "fbs_proposal_calibrate", "fbs_proposal_mode",
             "fbs_proposal_params", "fbs_proposal_stats", "fbs_proposal_loss_grad",
             "fbs_proposal_outputs", "fbs_proposal_step", "fbs_set_contrasts",
-            "fbs_contrast_probs", "fbs_rhat")
+            "fbs_contrast_probs", "fbs_rhat", "fbs_proposal_kinds")
 NOALLOC_MAX_GENES = 2048 * 128
 
 
@@ -128,13 +128,14 @@ def load_library(path: str = LIB_PATH):
     lib.fbs_proposal_calibrate.argtypes = [vp, i64, i64, C.c_double]
     lib.fbs_proposal_mode.argtypes = [vp, C.c_int]
     lib.fbs_proposal_params.argtypes = [vp, _PF, _PF, C.c_int]
-    lib.fbs_proposal_stats.argtypes = [vp, _PI64, _PI64, C.POINTER(C.c_int)]
+    lib.fbs_proposal_stats.argtypes = [vp, _PI64, _PI64, C.POINTER(C.c_int), C.POINTER(C.c_int)]
     lib.fbs_proposal_loss_grad.argtypes = [_PF, C.c_int, C.c_int, _PF, _PF, _PD, _PF]
     lib.fbs_proposal_outputs.argtypes = [vp, _PF]
     lib.fbs_proposal_step.argtypes = [vp, C.c_int64, C.c_int]
     lib.fbs_set_contrasts.argtypes = [vp, C.c_int, C.POINTER(C.c_int), _PD, _PD]
     lib.fbs_contrast_probs.argtypes = [vp, _PD, _PI64]
     lib.fbs_rhat.argtypes = [C.c_int, C.POINTER(vp), _PD, _PD, _PD, _PD]
+    lib.fbs_proposal_kinds.argtypes = [vp, C.POINTER(C.c_uint8)]
     lib.fbs_free.argtypes = [vp]
     lib.fbs_free.restype = None
     lib.fbs_last_error_string.argtypes = []
@@ -444,13 +445,24 @@ class Sampler:
         _check(self.lib.fbs_proposal_outputs(self.h, _pf(out)))
         return out
 
-    def proposal_step(self, it, all_genes=True):
-        _check(self.lib.fbs_proposal_step(self.h, int(it), int(bool(all_genes))))
+    def proposal_step(self, it, all_genes=1):
+        """all_genes: 0 the calibrated per-gene choice, 1 every gene with the
+        network's proposal, 2 every gene with the prior-centred one."""
+        _check(self.lib.fbs_proposal_step(self.h, int(it), int(all_genes)))
+
+    def proposal_kinds(self):
+        """Per gene: 0 slice updates only, 1 the network's proposal, 2 the
+        prior-centred one."""
+        out = np.zeros(self.G, np.uint8)
+        _check(self.lib.fbs_proposal_kinds(self.h, out.ctypes.data_as(C.POINTER(C.c_uint8))))
+        return out
 
     def proposal_stats(self):
-        a, t, u = C.c_int64(), C.c_int64(), C.c_int()
-        _check(self.lib.fbs_proposal_stats(self.h, C.byref(a), C.byref(t), C.byref(u)))
-        return {"accepted": a.value, "tried": t.value, "mh_genes": u.value}
+        a, t, u, up = C.c_int64(), C.c_int64(), C.c_int(), C.c_int()
+        _check(self.lib.fbs_proposal_stats(self.h, C.byref(a), C.byref(t), C.byref(u),
+                                           C.byref(up)))
+        return {"accepted": a.value, "tried": t.value, "mh_genes": u.value,
+                "prior_genes": up.value}
 
 
 class ChainView(Sampler):

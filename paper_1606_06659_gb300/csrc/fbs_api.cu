@@ -1003,12 +1003,12 @@ int learned_setup(fbs_handle* h) {
   FBS_CUDA(cudaMalloc((void**)&ls->adam_v, sizeof(float) * ls->np));
   FBS_CUDA(cudaMalloc((void**)&ls->prop, sizeof(float) * ls->K * (size_t)G));
   FBS_CUDA(cudaMalloc((void**)&ls->use_mh, (size_t)G));
-  FBS_CUDA(cudaMalloc((void**)&ls->mh_acc, sizeof(unsigned) * (size_t)G));
-  FBS_CUDA(cudaMalloc((void**)&ls->mh_try, sizeof(unsigned) * (size_t)G));
+  FBS_CUDA(cudaMalloc((void**)&ls->mh_acc, sizeof(unsigned) * 2 * (size_t)G));
+  FBS_CUDA(cudaMalloc((void**)&ls->mh_try, sizeof(unsigned) * 2 * (size_t)G));
   FBS_CUDA(cudaMalloc((void**)&ls->stats, sizeof(float) * (size_t)(2 * ls->F + 2 * L)));
   FBS_CUDA(cudaMemsetAsync(ls->use_mh, 0, (size_t)G, h->s));
-  FBS_CUDA(cudaMemsetAsync(ls->mh_acc, 0, sizeof(unsigned) * (size_t)G, h->s));
-  FBS_CUDA(cudaMemsetAsync(ls->mh_try, 0, sizeof(unsigned) * (size_t)G, h->s));
+  FBS_CUDA(cudaMemsetAsync(ls->mh_acc, 0, sizeof(unsigned) * 2 * (size_t)G, h->s));
+  FBS_CUDA(cudaMemsetAsync(ls->mh_try, 0, sizeof(unsigned) * 2 * (size_t)G, h->s));
   FBS_CUDA(cudaMemsetAsync(ls->adam_m, 0, sizeof(float) * ls->np, h->s));
   FBS_CUDA(cudaMemsetAsync(ls->adam_v, 0, sizeof(float) * ls->np, h->s));
   // He-style initialisation from Philox normals on the host (deterministic).
@@ -1228,22 +1228,36 @@ int fbs_proposal_calibrate(fbs_handle* h, int64_t n_sweeps, int64_t burnin, doub
     return fail(FBS_E_ARG, "need n_sweeps >= 1, burnin >= 0, 0 <= min_accept <= 1");
   LearnedState* ls = h->learned;
   const int G = h->mc.G;
-  FBS_CUDA(cudaMemsetAsync(ls->mh_acc, 0, sizeof(unsigned) * (size_t)G, h->s));
-  FBS_CUDA(cudaMemsetAsync(ls->mh_try, 0, sizeof(unsigned) * (size_t)G, h->s));
-  learned_apply(h, 1, 1);
+  const size_t n2 = 2 * (size_t)G;
+  FBS_CUDA(cudaMemsetAsync(ls->mh_acc, 0, sizeof(unsigned) * n2, h->s));
+  FBS_CUDA(cudaMemsetAsync(ls->mh_try, 0, sizeof(unsigned) * n2, h->s));
+  learned_apply(h, 1, 3);  // every gene, the two proposals on alternate sweeps
   rc = fbs_run(h, n_sweeps, burnin, 1);
   if (rc) return rc;
-  std::vector<unsigned> acc(G), tr(G);
-  FBS_CUDA(cudaMemcpyAsync(acc.data(), ls->mh_acc, sizeof(unsigned) * G, cudaMemcpyDeviceToHost,
+  std::vector<unsigned> acc(n2), tr(n2);
+  FBS_CUDA(cudaMemcpyAsync(acc.data(), ls->mh_acc, sizeof(unsigned) * n2, cudaMemcpyDeviceToHost,
                            h->s));
-  FBS_CUDA(cudaMemcpyAsync(tr.data(), ls->mh_try, sizeof(unsigned) * G, cudaMemcpyDeviceToHost,
+  FBS_CUDA(cudaMemcpyAsync(tr.data(), ls->mh_try, sizeof(unsigned) * n2, cudaMemcpyDeviceToHost,
                            h->s));
   FBS_CUDA(cudaStreamSynchronize(h->s));
+  // per gene: the proposal with the higher acceptance rate, if it reaches min_accept
   std::vector<uint8_t> use(G);
-  for (int g = 0; g < G; ++g) use[g] = tr[g] > 0 && acc[g] >= min_accept * tr[g] ? 1 : 0;
+  for (int g = 0; g < G; ++g) {
+    uint8_t best = 0;
+    double best_rate = -1.0;
+    for (int k = 0; k < 2; ++k) {
+      const unsigned t = tr[(size_t)k * G + g], a = acc[(size_t)k * G + g];
+      const double rate = t > 0 ? (double)a / (double)t : -1.0;
+      if (t > 0 && a >= min_accept * t && rate > best_rate) {
+        best_rate = rate;
+        best = (uint8_t)(k + 1);
+      }
+    }
+    use[g] = best;
+  }
   FBS_CUDA(cudaMemcpyAsync(ls->use_mh, use.data(), (size_t)G, cudaMemcpyHostToDevice, h->s));
-  FBS_CUDA(cudaMemsetAsync(ls->mh_acc, 0, sizeof(unsigned) * (size_t)G, h->s));
-  FBS_CUDA(cudaMemsetAsync(ls->mh_try, 0, sizeof(unsigned) * (size_t)G, h->s));
+  FBS_CUDA(cudaMemsetAsync(ls->mh_acc, 0, sizeof(unsigned) * n2, h->s));
+  FBS_CUDA(cudaMemsetAsync(ls->mh_try, 0, sizeof(unsigned) * n2, h->s));
   FBS_CUDA(cudaStreamSynchronize(h->s));
   learned_apply(h, 1, 0);
   return FBS_OK;
@@ -1275,26 +1289,32 @@ int fbs_proposal_params(fbs_handle* h, float* get, const float* set, int n) {
   return FBS_OK;
 }
 
-int fbs_proposal_stats(fbs_handle* h, int64_t* accepted, int64_t* tried, int* n_mh_genes) {
+int fbs_proposal_stats(fbs_handle* h, int64_t* accepted, int64_t* tried, int* n_mh_genes,
+                       int* n_prior_genes) {
   if (!h || !h->learned) return fail(FBS_E_ARG, "the handle has no learned proposal");
   LearnedState* ls = h->learned;
   const int G = h->mc.G;
-  std::vector<unsigned> acc(G), tr(G);
+  const size_t n2 = 2 * (size_t)G;
+  std::vector<unsigned> acc(n2), tr(n2);
   std::vector<uint8_t> use(G);
   FBS_CUDA(cudaStreamSynchronize(h->s));
-  FBS_CUDA(cudaMemcpy(acc.data(), ls->mh_acc, sizeof(unsigned) * G, cudaMemcpyDeviceToHost));
-  FBS_CUDA(cudaMemcpy(tr.data(), ls->mh_try, sizeof(unsigned) * G, cudaMemcpyDeviceToHost));
+  FBS_CUDA(cudaMemcpy(acc.data(), ls->mh_acc, sizeof(unsigned) * n2, cudaMemcpyDeviceToHost));
+  FBS_CUDA(cudaMemcpy(tr.data(), ls->mh_try, sizeof(unsigned) * n2, cudaMemcpyDeviceToHost));
   FBS_CUDA(cudaMemcpy(use.data(), ls->use_mh, (size_t)G, cudaMemcpyDeviceToHost));
   int64_t a = 0, t = 0;
-  int u = 0;
+  int u = 0, up = 0;
+  for (size_t i = 0; i < n2; ++i) {
+    a += acc[i];
+    t += tr[i];
+  }
   for (int g = 0; g < G; ++g) {
-    a += acc[g];
-    t += tr[g];
-    u += use[g];
+    u += use[g] != 0;
+    up += use[g] == kMovePrior;
   }
   if (accepted) *accepted = a;
   if (tried) *tried = t;
   if (n_mh_genes) *n_mh_genes = u;
+  if (n_prior_genes) *n_prior_genes = up;
   return FBS_OK;
 }
 
@@ -1439,6 +1459,14 @@ int fbs_contrast_probs(fbs_handle* h, double* prob, int64_t* m) {
   return FBS_OK;
 }
 
+int fbs_proposal_kinds(fbs_handle* h, uint8_t* kinds) {
+  if (!h || !h->learned) return fail(FBS_E_ARG, "the handle has no learned proposal");
+  if (!kinds) return fail(FBS_E_ARG, "kinds is NULL");
+  FBS_CUDA(cudaStreamSynchronize(h->s));
+  FBS_CUDA(cudaMemcpy(kinds, h->learned->use_mh, (size_t)h->mc.G, cudaMemcpyDeviceToHost));
+  return FBS_OK;
+}
+
 int fbs_proposal_param_count(int L) { return (L < 1 || L > FBS_MAX_L) ? -1 : mlp_param_count(L); }
 
 int fbs_proposal_outputs(fbs_handle* h, float* out) {
@@ -1466,7 +1494,7 @@ int fbs_proposal_step(fbs_handle* h, int64_t it, int all_genes) {
   int rc = learned_setup(h);
   if (rc) return rc;
   if (it < 1 || it > 0xFFFFFFFFll) return fail(FBS_E_ARG, "it must be in [1, 2^32)");
-  if (all_genes != 0 && all_genes != 1) return fail(FBS_E_ARG, "all_genes must be 0 or 1");
+  if (all_genes < 0 || all_genes > 2) return fail(FBS_E_ARG, "all_genes must be 0, 1 or 2");
   LearnedState* ls = h->learned;
   rc = enter(h);
   if (rc) return rc;

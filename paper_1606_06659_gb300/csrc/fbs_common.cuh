@@ -32,6 +32,9 @@ enum : uint32_t {
   kStreamTrain = 9,   // minibatch sampling when training the proposal
 };
 
+// Proposals of the eta-preserving move: the network's, or centred on the prior.
+enum : int { kMoveNet = 1, kMovePrior = 2 };
+
 // Learned proposal: hidden width of the two layers, limits of the per-gene
 // features (4L+1) and outputs (L + L(L+1)/2).
 constexpr int kMlpHidden = 64;
@@ -138,10 +141,11 @@ struct DevPtrsF32 {
   float* mu;          // [N][G] Poisson means at the new eps, from the eps kernel
   // learned proposal (null prop: plain slice updates only)
   const float* prop;  // [n_out][G] proposal mean and Cholesky parameters per gene
-  const uint8_t* use_mh;  // [G] 1: the gene's beta moves by the learned proposal
-  unsigned* mh_acc;   // [G] accepted moves
-  unsigned* mh_try;   // [G] attempted moves
-  int mh_all;         // 1: every gene attempts the move (calibration)
+  const uint8_t* use_mh;  // [G] the gene's proposal kind (0: slice updates only)
+  unsigned* mh_acc;   // [2][G] accepted moves per kind (kind - 1)
+  unsigned* mh_try;   // [2][G] attempted moves per kind
+  int mh_all;         // 0: per-gene kind (use_mh); 1, 2: that kind for every gene;
+                      // 3: every gene, network / prior on alternate iterations
   int mh_replace;     // 1: the move replaces the slice updates of beta_g; 0: both run
   double* partial;    // [n_blocks][kNumPart]
   Hyper* hyp;

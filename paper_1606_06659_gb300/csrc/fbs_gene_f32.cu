@@ -300,6 +300,16 @@ __global__ void __launch_bounds__(256) k_eps_f32(ModelConst mc, DevPtrsF32 p, in
                (blockIdx.x + blockIdx.y) % kCounterCopies);
 }
 
+// Which proposal gene g uses at iteration it: 0 none, kMoveNet the network's,
+// kMovePrior the prior-centred one.  p.mh_all = 0: the calibrated per-gene
+// choice; 1 or 2: that kind for every gene; 3 (calibration): every gene, the
+// network on even and the prior on odd iterations.
+__device__ __forceinline__ int move_kind(const DevPtrsF32& p, int g, long long it) {
+  if (p.mh_all == 3) return (it & 1) ? kMovePrior : kMoveNet;
+  if (p.mh_all) return p.mh_all;
+  return (int)p.use_mh[g];
+}
+
 // The learned-proposal move of gene g (FP32): beta* from the multivariate t
 // distribution with kTDof degrees of freedom, centre mu and scale C C^T given by
 // the proposal network (beta* = mu + s C xi, s = sqrt(kTDof / chi2)), and
@@ -312,12 +322,17 @@ __global__ void __launch_bounds__(256) k_eps_f32(ModelConst mc, DevPtrsF32 p, in
 // tails, which keeps the ratio target / proposal bounded (uniform ergodicity).
 // Uniforms 0..2L-1 give the normals, uniform 2L the acceptance and uniforms
 // 2L+1..2L+4 the chi-square variate chi2 = -2 log(U1 U2 U3 U4) (kTDof = 8).
+// kind kMoveNet takes the centre and scale from the network; kind kMovePrior
+// from the hyperparameters alone (centre theta, scale diag(sigma)), which suits
+// genes whose conditional is close to the prior (very large gamma_g), where the
+// network, trained mostly on typical genes, extrapolates poorly.  Either way
+// the proposal depends only on quantities the move keeps.
 // Returns true when accepted.
 constexpr int kTDof = 8;
 
 __device__ __forceinline__ bool mh_move_f32(const ModelConst& mc, const DevPtrsF32& p, int g,
                                             uint32_t it32, float* bs, int B, int tid,
-                                            const Hyper* hy, float hg) {
+                                            const Hyper* hy, float hg, int kind) {
   const int G = mc.G, N = mc.N, L = mc.L;
   float mu[kMaxL], C[kMaxL][kMaxL], xi[kMaxL], bn[kMaxL], d[kMaxL];
 #pragma unroll
@@ -330,11 +345,16 @@ __device__ __forceinline__ bool mh_move_f32(const ModelConst& mc, const DevPtrsF
 #pragma unroll
   for (int i = 0; i < kMaxL; ++i) {
     if (i < L) {
-      mu[i] = p.prop[(size_t)i * G + g];
-      C[i][i] = expf(p.prop[(size_t)(L + i) * G + g]);
+      if (kind == kMoveNet) {
+        mu[i] = p.prop[(size_t)i * G + g];
+        C[i][i] = expf(p.prop[(size_t)(L + i) * G + g]);
 #pragma unroll
-      for (int j = 0; j < kMaxL; ++j)
-        if (j < i) C[i][j] = p.prop[(size_t)(k++) * G + g];
+        for (int j = 0; j < kMaxL; ++j)
+          if (j < i) C[i][j] = p.prop[(size_t)(k++) * G + g];
+      } else {  // the prior's centre and scales
+        mu[i] = (float)hy->phi[2 + i];
+        C[i][i] = sqrtf((float)hy->phi[2 + L + i]);
+      }
     }
   }
   Rng4 r(mc.seed_lo, mc.seed_hi, mc.chain, kStreamMH, (uint32_t)g, it32);
@@ -526,11 +546,13 @@ __device__ __forceinline__ void gb_f32_body(const ModelConst& mc, const DevPtrsF
     }
 
     // ---- learned-proposal move (keeps every log-rate, so mu stays valid)
-    const bool mh_gene = p.prop != nullptr && (p.mh_all || p.use_mh[g]);
+    const int kind = p.prop != nullptr ? move_kind(p, g, it) : 0;
+    const bool mh_gene = kind != 0;
     if (mh_gene) {
-      const bool acc = mh_move_f32(mc, p, g, it32, bs, B, tid, hy, 0.5f / p.gam[g]);
-      p.mh_try[g] += 1u;
-      p.mh_acc[g] += acc ? 1u : 0u;
+      const bool acc = mh_move_f32(mc, p, g, it32, bs, B, tid, hy, 0.5f / p.gam[g], kind);
+      const size_t ci = (size_t)(kind - 1) * G + g;
+      p.mh_try[ci] += 1u;
+      p.mh_acc[ci] += acc ? 1u : 0u;
     }
 
     float ss = 0.0f;
@@ -639,13 +661,16 @@ __global__ void __launch_bounds__(128) k_mh_step_f32(ModelConst mc, DevPtrsF32 p
   __shared__ float bs[kMaxL * 128];
   const int B = blockDim.x, tid = threadIdx.x;
   const int g = blockIdx.x * B + tid;
-  if (g >= mc.G || !(p.mh_all || p.use_mh[g])) return;
+  if (g >= mc.G) return;
+  const int kind = move_kind(p, g, it);
+  if (kind == 0) return;
   const int G = mc.G, L = mc.L;
   for (int l = 0; l < L; ++l) bs[l * B + tid] = p.beta[(size_t)l * G + g];
-  const bool acc = mh_move_f32(mc, p, g, (uint32_t)it, bs, B, tid, p.hyp, 0.5f / p.gam[g]);
-  p.mh_try[g] += 1u;
+  const bool acc = mh_move_f32(mc, p, g, (uint32_t)it, bs, B, tid, p.hyp, 0.5f / p.gam[g], kind);
+  const size_t ci = (size_t)(kind - 1) * G + g;
+  p.mh_try[ci] += 1u;
   if (acc) {
-    p.mh_acc[g] += 1u;
+    p.mh_acc[ci] += 1u;
     for (int l = 0; l < L; ++l) p.beta[(size_t)l * G + g] = bs[l * B + tid];
   }
 }

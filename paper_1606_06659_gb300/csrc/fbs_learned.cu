@@ -337,7 +337,7 @@ constexpr int kTcThreads = 256;      // two warps per TMEM lane quadrant
 
 
 // Persistent over tiles of 128 genes; writes the proposal parameters [K][G] of
-// the genes that use the move (every gene when p.mh_all).  Threads t and
+// the genes that may use the network's proposal.  Threads t and
 // t + 128 sum the features of gene row t over the two halves of the samples and
 // thread t writes its split row of the first operand (row = TMEM lane); in the
 // epilogues warp w reads lane quadrant w % 4 and column half w / 4.  A wait that gives up sets
@@ -399,7 +399,9 @@ __global__ void __launch_bounds__(kTcThreads) k_proposal_tc(ModelConst mc, DevPt
 
   for (int tile = blockIdx.x; tile < ntiles && !s_abort; tile += gridDim.x) {
     const int g = tile * 128 + row;
-    const bool act = g < G && (p.mh_all || p.use_mh[g]);
+    // genes that may use the network's proposal in this sweep
+    const bool act = g < G && (p.mh_all == kMoveNet || p.mh_all == 3 ||
+                               (p.mh_all == 0 && p.use_mh[g] == kMoveNet));
     // features: threads 0..127 sum X^T (eta - h) over the first half of the
     // samples, threads 128..255 over the second half (same gene: row = tid % 128)
     {

@@ -110,21 +110,29 @@ def _trained_sampler(d, seed, sweeps=100, epochs=30, **kw):
     return s, loss
 
 
-def test_move_matches_oracle_move():
+@pytest.mark.parametrize("kind", [1, 2])
+def test_move_matches_oracle_move(kind):
     """One move of every gene: the kernel's t proposal from the network and the
     Philox draws (stream 8, index g: normals from uniforms 0..2L-1, the
     acceptance uniform 2L, the chi-square variate from uniforms 2L+1..2L+4), its
     acceptance decision and the new (eps, beta) against the oracle's move, given
-    the same uniforms.  Decisions
-    are compared where the oracle's log ratio is clear of the log-uniform by more
-    than the FP32 rounding of its terms."""
+    the same uniforms.  Kind 1 is the network's proposal, kind 2 the
+    prior-centred one (centre theta, scale diag(sigma): the oracle's move with
+    those as its outputs).  Decisions are compared where the oracle's log ratio
+    is clear of the log-uniform by more than the FP32 rounding of its terms."""
     d = synthetic.make_config(1, G=1000)
     s, _ = _trained_sampler(d, seed=21)
     L = d["X"].shape[1]
     G, N = d["y"].shape
     st = s.get_state()
     params = s.proposal_params()
-    out = _oracle_outputs(st, d, params)
+    if kind == 1:
+        out = _oracle_outputs(st, d, params)
+    else:
+        phi = st["phi"]
+        out = np.zeros((G, P.n_outputs(L)))
+        out[:, :L] = phi[2:2 + L]
+        out[:, L:2 * L] = 0.5 * np.log(phi[2 + L:2 + 2 * L])
     it, seed = 4321, 21
     xi = np.empty((G, L))
     log_u = np.empty(G)
@@ -146,13 +154,14 @@ def test_move_matches_oracle_move():
            + np.sum(((b2 - theta) ** 2 + (st["beta"] - theta) ** 2) / sigma2, 1))
     clear = np.abs(la - log_u) > 1e-2 + 1e-4 * mag
 
-    s.proposal_step(it, all_genes=True)
+    s.proposal_step(it, all_genes=kind)
     got = s.get_state()
     stats = s.proposal_stats()
     assert stats["tried"] == G
     acc_gpu = np.any(got["beta"] != st["beta"], axis=1)
     assert clear.mean() > 0.95
-    assert 0.2 < acc.mean() < 0.98, acc.mean()
+    # the prior-centred proposal suits only genes near their prior: few accept
+    assert (0.2 if kind == 1 else 0.002) < acc.mean() < 0.98, acc.mean()
     np.testing.assert_array_equal(acc_gpu[clear], acc[clear])
     assert stats["accepted"] == int(acc_gpu.sum())
     both = clear & acc
@@ -179,6 +188,7 @@ def test_calibration_selects_genes_and_counts_moves():
     st = s.proposal_stats()
     assert st["tried"] == 0 and st["accepted"] == 0
     assert 0.5 * 600 < st["mh_genes"] <= 600
+    assert 0 <= st["prior_genes"] < 0.5 * st["mh_genes"]
     s.run(30, burnin=200)
     st = s.proposal_stats()
     assert st["tried"] == 30 * st["mh_genes"]

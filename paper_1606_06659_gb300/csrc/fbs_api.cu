@@ -1183,29 +1183,48 @@ int fbs_proposal_train(fbs_handle* h, int epochs, int batch, double lr, uint64_t
   if (e == cudaSuccess) e = cudaStreamSynchronize(h->s);
   double log_scale = 0.0;  // NLL of raw beta = NLL of standardised beta + sum log s_beta
   for (int l = 0; l < L; ++l) log_scale += log((double)st_h[2 * F + L + l]);
-  double loss_epoch = 0.0;
-  for (long long st = 0; st < steps && rc == FBS_OK && e == cudaSuccess; ++st) {
-    e = launch_gather_rows(ls->pair_feat, ls->pair_beta, ls->pairs, F, L, batch, seed,
-                           (uint32_t)(ls->adam_t + 1), ls->stats, t.fb, t.yb, h->s);
-    if (e != cudaSuccess) break;
-    rc = mlp_step(ls->params, L, batch, t, h->s);
-    if (rc) break;
-    ls->adam_t += 1;
-    const float b1 = 0.9f, b2 = 0.999f;
-    const float c1 = 1.0f - powf(b1, (float)ls->adam_t), c2 = 1.0f - powf(b2, (float)ls->adam_t);
-    // cosine decay of the step size over this call, to 5% of lr
-    const double lr_t = lr * (0.05 + 0.475 * (1.0 + cos(3.141592653589793 * (double)st / steps)));
-    e = launch_adam(ls->params, t.grad, ls->adam_m, ls->adam_v, ls->np, (float)lr_t, b1, b2,
-                    1e-8f, c1, c2, h->s);
-    if (e != cudaSuccess) break;
-    if (st >= steps - steps_per_epoch) {
-      float l = 0.f;
-      e = cudaMemcpyAsync(&l, t.loss, sizeof(float), cudaMemcpyDeviceToHost, h->s);
-      if (e == cudaSuccess) e = cudaStreamSynchronize(h->s);
-      if (e != cudaSuccess) break;
-      loss_epoch += l / batch;
+  // One training step (minibatch gather, forward, backward, Adam, bookkeeping)
+  // is captured once and replayed `steps` times; the step counter, the Adam
+  // scalars and the loss sum live in a device control block.
+  TrainCtl ctl;
+  memset(&ctl, 0, sizeof(ctl));
+  ctl.t = (unsigned long long)ls->adam_t;
+  ctl.steps = steps;
+  ctl.epoch_steps = steps_per_epoch;
+  ctl.lr = lr;
+  ctl.b1 = 0.9f;
+  ctl.b2 = 0.999f;
+  TrainCtl* d_ctl = nullptr;
+  cudaGraphExec_t exec = nullptr;
+  if (e == cudaSuccess) e = cudaMalloc((void**)&d_ctl, sizeof(TrainCtl));
+  if (e == cudaSuccess)
+    e = cudaMemcpyAsync(d_ctl, &ctl, sizeof(ctl), cudaMemcpyHostToDevice, h->s);
+  if (e == cudaSuccess) e = launch_train_begin(d_ctl, h->s);
+  if (e == cudaSuccess) {
+    cudaGraph_t graph = nullptr;
+    e = cudaStreamBeginCapture(h->s, cudaStreamCaptureModeThreadLocal);
+    if (e == cudaSuccess) {
+      cudaError_t ce = launch_gather_rows_ctl(ls->pair_feat, ls->pair_beta, ls->pairs, F, L, batch,
+                                              seed, d_ctl, ls->stats, t.fb, t.yb, h->s);
+      if (ce == cudaSuccess) rc = mlp_step(ls->params, L, batch, t, h->s);
+      if (ce == cudaSuccess && rc == FBS_OK)
+        ce = launch_adam_ctl(ls->params, t.grad, ls->adam_m, ls->adam_v, ls->np, d_ctl, h->s);
+      if (ce == cudaSuccess && rc == FBS_OK) ce = launch_train_tick(d_ctl, t.loss, batch, h->s);
+      e = cudaStreamEndCapture(h->s, &graph);
+      if (e == cudaSuccess) e = ce;
     }
+    if (e == cudaSuccess && rc == FBS_OK) e = cudaGraphInstantiate(&exec, graph, 0);
+    if (graph) cudaGraphDestroy(graph);
   }
+  for (long long st = 0; st < steps && rc == FBS_OK && e == cudaSuccess; ++st)
+    e = cudaGraphLaunch(exec, h->s);
+  if (e == cudaSuccess && rc == FBS_OK)
+    e = cudaMemcpyAsync(&ctl, d_ctl, sizeof(ctl), cudaMemcpyDeviceToHost, h->s);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(h->s);
+  if (exec) cudaGraphExecDestroy(exec);
+  cudaFree(d_ctl);
+  if (e == cudaSuccess && rc == FBS_OK) ls->adam_t = (long long)ctl.t;
+  const double loss_epoch = ctl.loss_sum;
   if (e == cudaSuccess && rc == FBS_OK) e = launch_fold(ls->params, ls->stats, L, 1, h->s);
   if (e == cudaSuccess && rc == FBS_OK) e = launch_pack_image(ls->params, ls->w_image, ls->L, h->s);
   if (e == cudaSuccess && rc == FBS_OK) e = cudaStreamSynchronize(h->s);

@@ -53,14 +53,25 @@ struct RhatInput {
 cudaError_t launch_rhat(const RhatInput& in, double* out, cudaStream_t s);
 
 // learned proposal (fbs_learned.cu)
+// Training control block in device memory (one Adam step per captured replay).
+struct TrainCtl {
+  unsigned long long t;      // Adam steps done before the current step
+  long long k, steps, epoch_steps;  // step within the call, steps of the call, of an epoch
+  double lr, loss_sum;       // base step size; loss summed over the last epoch's steps
+  float b1, b2, c1, c2, lr_t;
+};
+cudaError_t launch_train_begin(TrainCtl* c, cudaStream_t s);
+cudaError_t launch_train_tick(TrainCtl* c, const float* loss, int B, cudaStream_t s);
+cudaError_t launch_adam_ctl(float* w, const float* g, float* m, float* v, int n,
+                            const TrainCtl* c, cudaStream_t s);
+cudaError_t launch_gather_rows_ctl(const float* feat, const float* beta, long long M, int F,
+                                   int L, int Bsz, uint64_t seed, const TrainCtl* c,
+                                   const float* st, float* fb, float* yb, cudaStream_t s);
 int mlp_param_count(int L);
 cudaError_t launch_proposal_f32(const ModelConst& mc, const DevPtrsF32& p, const void* w_bf16,
                                 float* out, cudaStream_t s);
 cudaError_t launch_collect_f32(const ModelConst& mc, const DevPtrsF32& p, float* feat,
                                float* beta, long long row, cudaStream_t s);
-cudaError_t launch_gather_rows(const float* feat, const float* beta, long long M, int F, int L,
-                               int Bsz, uint64_t seed, uint32_t step, const float* st, float* fb,
-                               float* yb, cudaStream_t s);
 cudaError_t launch_col_stats(const float* feat, const float* beta, long long M, int F, int L,
                              float* st, cudaStream_t s);
 cudaError_t launch_fold(float* params, const float* st, int L, int to_raw, cudaStream_t s);
@@ -74,8 +85,6 @@ cudaError_t launch_gelu_back(const float* Z, const float* dH, float* dZ, long lo
 cudaError_t launch_nll_head(const float* O, const float* Y, int Bsz, int L, float* dO,
                             float* loss_sum, cudaStream_t s);
 cudaError_t launch_colsum(const float* D, int rows, int cols, float* g, cudaStream_t s);
-cudaError_t launch_adam(float* w, const float* g, float* m, float* v, int n, float lr, float b1,
-                        float b2, float eps, float c1, float c2, cudaStream_t s);
 size_t tc_image_bytes(int L);
 cudaError_t launch_pack_image(const float* params, void* img, int L, cudaStream_t s);
 

@@ -524,25 +524,6 @@ __global__ void k_collect_f32(ModelConst mc, DevPtrsF32 p, float* __restrict__ f
 
 // ---------------------------------------------------------------- training
 
-// Minibatch: row i of the batch is pair floor(U * M) for a Philox uniform U,
-// standardised with the column means and scales of `st` (see k_col_stats).
-__global__ void k_gather_rows(const float* __restrict__ feat, const float* __restrict__ beta,
-                              long long M, int F, int L, int Bsz, uint32_t seed_lo,
-                              uint32_t seed_hi, uint32_t step, const float* __restrict__ st,
-                              float* __restrict__ fb, float* __restrict__ yb) {
-  const int i = blockIdx.x * blockDim.x + threadIdx.x;
-  if (i >= Bsz) return;
-  Rng r(seed_lo, seed_hi, 0u, kStreamTrain, (uint32_t)i, step);
-  long long m = (long long)(r.u(0) * (double)M);
-  if (m >= M) m = M - 1;
-  const float* mf = st;
-  const float* sf = st + F;
-  const float* mb = st + 2 * F;
-  const float* sb = st + 2 * F + L;
-  for (int k = 0; k < F; ++k) fb[(size_t)i * F + k] = (feat[(size_t)m * F + k] - mf[k]) / sf[k];
-  for (int l = 0; l < L; ++l) yb[(size_t)i * L + l] = (beta[(size_t)m * L + l] - mb[l]) / sb[l];
-}
-
 // Column means and scales of the training pairs, in FP64: block c < F takes
 // feature column c, block F + l takes beta column l.  The scale is the standard
 // deviation, or 1 for a column that is constant to within 1e-6 of its size.
@@ -758,17 +739,63 @@ __global__ void k_colsum(const float* D, int rows, int cols, float* g) {
   }
 }
 
-// Adam (Kingma & Ba 2015) with bias correction.
-__global__ void k_adam(float* w, const float* g, float* m, float* v, int n, float lr, float b1,
-                       float b2, float eps, float c1, float c2) {
+// Adam scalars of the current training step, kept on the device so that a
+// captured training step replays unchanged: t is the Adam step count before the
+// step, k the step within the training call.
+__device__ __forceinline__ void train_scalars(TrainCtl* c) {
+  const double t1 = (double)(c->t + 1);
+  c->c1 = (float)(1.0 - pow((double)c->b1, t1));
+  c->c2 = (float)(1.0 - pow((double)c->b2, t1));
+  // cosine decay of the step size over the call, to 5% of lr
+  c->lr_t = (float)(c->lr * (0.05 + 0.475 * (1.0 + cos(3.141592653589793 * (double)c->k /
+                                                         (double)c->steps))));
+}
+
+__global__ void k_train_begin(TrainCtl* c) {
+  if (threadIdx.x == 0 && blockIdx.x == 0) train_scalars(c);
+}
+
+// After a step: add the step's loss to the last epoch's sum, advance t and k and
+// prepare the next step's scalars.
+__global__ void k_train_tick(TrainCtl* c, const float* loss, int B) {
+  if (threadIdx.x != 0 || blockIdx.x != 0) return;
+  if (c->k >= c->steps - c->epoch_steps) c->loss_sum += (double)*loss / (double)B;
+  c->t += 1;
+  c->k += 1;
+  train_scalars(c);
+}
+
+// Adam (Kingma & Ba 2015) with bias correction, the scalars from the control block.
+__global__ void k_adam_ctl(float* w, const float* g, float* m, float* v, int n,
+                           const TrainCtl* __restrict__ c, float eps) {
   const int t = blockIdx.x * blockDim.x + threadIdx.x;
   if (t >= n) return;
+  const float b1 = c->b1, b2 = c->b2;
   const float gt = g[t];
   const float mt = b1 * m[t] + (1.0f - b1) * gt;
   const float vt = b2 * v[t] + (1.0f - b2) * gt * gt;
   m[t] = mt;
   v[t] = vt;
-  w[t] -= lr * (mt / c1) / (sqrtf(vt / c2) + eps);
+  w[t] -= c->lr_t * (mt / c->c1) / (sqrtf(vt / c->c2) + eps);
+}
+
+// Minibatch rows for the step the control block describes (Philox step t + 1).
+__global__ void k_gather_rows_ctl(const float* __restrict__ feat, const float* __restrict__ beta,
+                                  long long M, int F, int L, int Bsz, uint32_t seed_lo,
+                                  uint32_t seed_hi, const TrainCtl* __restrict__ c,
+                                  const float* __restrict__ st, float* __restrict__ fb,
+                                  float* __restrict__ yb) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= Bsz) return;
+  Rng r(seed_lo, seed_hi, 0u, kStreamTrain, (uint32_t)i, (uint32_t)(c->t + 1));
+  long long m = (long long)(r.u(0) * (double)M);
+  if (m >= M) m = M - 1;
+  const float* mf = st;
+  const float* sf = st + F;
+  const float* mb = st + 2 * F;
+  const float* sb = st + 2 * F + L;
+  for (int k = 0; k < F; ++k) fb[(size_t)i * F + k] = (feat[(size_t)m * F + k] - mf[k]) / sf[k];
+  for (int l = 0; l < L; ++l) yb[(size_t)i * L + l] = (beta[(size_t)m * L + l] - mb[l]) / sb[l];
 }
 
 // ---------------------------------------------------------------- launchers
@@ -803,14 +830,6 @@ cudaError_t launch_collect_f32(const ModelConst& mc, const DevPtrsF32& p, float*
                                float* beta, long long row, cudaStream_t s) {
   const int blk = 128;
   k_collect_f32<<<(mc.G + blk - 1) / blk, blk, 0, s>>>(mc, p, feat, beta, row);
-  return cudaGetLastError();
-}
-
-cudaError_t launch_gather_rows(const float* feat, const float* beta, long long M, int F, int L,
-                               int Bsz, uint64_t seed, uint32_t step, const float* st, float* fb,
-                               float* yb, cudaStream_t s) {
-  k_gather_rows<<<(Bsz + 127) / 128, 128, 0, s>>>(feat, beta, M, F, L, Bsz, (uint32_t)seed,
-                                                  (uint32_t)(seed >> 32), step, st, fb, yb);
   return cudaGetLastError();
 }
 
@@ -857,9 +876,27 @@ cudaError_t launch_colsum(const float* D, int rows, int cols, float* g, cudaStre
   return cudaGetLastError();
 }
 
-cudaError_t launch_adam(float* w, const float* g, float* m, float* v, int n, float lr, float b1,
-                        float b2, float eps, float c1, float c2, cudaStream_t s) {
-  k_adam<<<(n + 255) / 256, 256, 0, s>>>(w, g, m, v, n, lr, b1, b2, eps, c1, c2);
+cudaError_t launch_train_begin(TrainCtl* c, cudaStream_t s) {
+  k_train_begin<<<1, 32, 0, s>>>(c);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_train_tick(TrainCtl* c, const float* loss, int B, cudaStream_t s) {
+  k_train_tick<<<1, 32, 0, s>>>(c, loss, B);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_adam_ctl(float* w, const float* g, float* m, float* v, int n,
+                            const TrainCtl* c, cudaStream_t s) {
+  k_adam_ctl<<<(n + 255) / 256, 256, 0, s>>>(w, g, m, v, n, c, 1e-8f);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_gather_rows_ctl(const float* feat, const float* beta, long long M, int F,
+                                   int L, int Bsz, uint64_t seed, const TrainCtl* c,
+                                   const float* st, float* fb, float* yb, cudaStream_t s) {
+  k_gather_rows_ctl<<<(Bsz + 127) / 128, 128, 0, s>>>(feat, beta, M, F, L, Bsz, (uint32_t)seed,
+                                                      (uint32_t)(seed >> 32), c, st, fb, yb);
   return cudaGetLastError();
 }
 

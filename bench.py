@@ -288,7 +288,7 @@ FORM_TEXT = {
                "before the slice updates of beta_g)",
 }
 PAIR_SWEEPS = 50          # x thin 2 x G = 2e6 training pairs at G = 40000
-TRAIN = {"epochs": 15, "batch": 4096, "lr": 2e-3}
+TRAIN = {"epochs": 15, "batch": 8192, "lr": 3e-3}
 CALIBRATE_SWEEPS = 100
 # Calibration threshold of the learned move.  The headline form adds the move to
 # the slice updates of beta_g (mode 1), so the slice sampler always runs and the

@@ -189,6 +189,9 @@ def test_calibration_selects_genes_and_counts_moves():
     assert st["tried"] == 0 and st["accepted"] == 0
     assert 0.5 * 600 < st["mh_genes"] <= 600
     assert 0 <= st["prior_genes"] < 0.5 * st["mh_genes"]
+    kinds = s.proposal_kinds()
+    assert kinds.shape == (600,) and set(np.unique(kinds)) <= {0, 1, 2}
+    assert int((kinds > 0).sum()) == st["mh_genes"] and int((kinds == 2).sum()) == st["prior_genes"]
     s.run(30, burnin=200)
     st = s.proposal_stats()
     assert st["tried"] == 30 * st["mh_genes"]

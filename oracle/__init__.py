@@ -58,15 +58,20 @@ class Model(C.Structure):
 _PD = C.POINTER(C.c_double)
 
 
+STATE_NAMES = ("eps", "beta", "gam", "phi", "w_eps", "waux_eps", "w_beta", "waux_beta", "w_nu",
+               "waux_nu", "w_gam", "waux_gam", "w_hyp", "waux_hyp")
+
+
 class State(C.Structure):
     _fields_ = [(n, _PD) for n in ("eps", "beta", "gam", "phi", "w_eps", "waux_eps",
-                                   "w_beta", "waux_beta", "w_nu", "waux_nu")]
+                                   "w_beta", "waux_beta", "w_nu", "waux_nu", "w_gam",
+                                   "waux_gam", "w_hyp", "waux_hyp")]
 
 
 class Opts(C.Structure):
     _fields_ = [("seed", C.c_uint64), ("chain", C.c_uint32), ("step_out_max", C.c_int),
                 ("shrink_max", C.c_int), ("burnin", C.c_int64), ("tune_start", C.c_int64),
-                ("w0", C.c_double)]
+                ("w0", C.c_double), ("all_slice", C.c_int)]
 
 
 class Moments(C.Structure):
@@ -77,7 +82,8 @@ class Moments(C.Structure):
 
 class Counters(C.Structure):
     _fields_ = [(n, C.c_int64) for n in ("evals_eps", "evals_beta", "evals_nu", "slice_caps",
-                                         "gamma_caps", "trunc_caps", "nonfinite")]
+                                         "gamma_caps", "trunc_caps", "nonfinite", "evals_gam",
+                                         "evals_hyp")]
 
 
 def _declare(lib):
@@ -236,10 +242,12 @@ class Chain:
     """One chain of the sampler on host arrays; every call goes to the C oracle.
 
     y: int32 [G][N]; X: [N][L]; h: [N]; priors: dict(a, b, d, c[L], s[L]).
+    all_slice: slice-sample gamma_g, tau and sigma_l too (their widths are w_gam
+    [G] and w_hyp [1+L] = tau, sigma_1..sigma_L).
     """
 
     def __init__(self, y, X, h, priors, seed=1, chain=0, step_out_max=100, shrink_max=100,
-                 burnin=0, tune_start=None, w0=1.0, lib=None):
+                 burnin=0, tune_start=None, w0=1.0, all_slice=False, lib=None):
         self.lib = lib or load()
         self.y = np.ascontiguousarray(y, np.int32)
         self.G, self.N = self.y.shape
@@ -263,12 +271,15 @@ class Chain:
         self.waux_beta = np.zeros((G, L))
         self.w_nu = np.full(1, w0)
         self.waux_nu = np.zeros(1)
-        self.state = State(*[_pd(getattr(self, n)) for n in (
-            "eps", "beta", "gam", "phi", "w_eps", "waux_eps", "w_beta", "waux_beta", "w_nu",
-            "waux_nu")])
+        self.w_gam = np.full(G, w0)
+        self.waux_gam = np.zeros(G)
+        self.w_hyp = np.full(1 + L, w0)
+        self.waux_hyp = np.zeros(1 + L)
+        self.state = State(*[_pd(getattr(self, n)) for n in STATE_NAMES])
         if tune_start is None:
             tune_start = burnin // 2
-        self.opts = Opts(seed, chain, step_out_max, shrink_max, burnin, tune_start, w0)
+        self.opts = Opts(seed, chain, step_out_max, shrink_max, burnin, tune_start, w0,
+                         int(bool(all_slice)))
         self.mean_eps, self.msq_eps = np.zeros((G, N)), np.zeros((G, N))
         self.mean_beta, self.msq_beta = np.zeros((G, L)), np.zeros((G, L))
         self.mean_gam, self.msq_gam = np.zeros(G), np.zeros(G)
@@ -286,11 +297,11 @@ class Chain:
             raise ValueError("X^T X is singular")
         return self
 
-    def set_state(self, eps=None, beta=None, gam=None, phi=None, w_eps=None, w_beta=None,
-                  w_nu=None, waux_eps=None, waux_beta=None, waux_nu=None, it=None):
-        for name, val in (("eps", eps), ("beta", beta), ("gam", gam), ("phi", phi),
-                          ("w_eps", w_eps), ("w_beta", w_beta), ("w_nu", w_nu),
-                          ("waux_eps", waux_eps), ("waux_beta", waux_beta), ("waux_nu", waux_nu)):
+    def set_state(self, it=None, **arrays):
+        unknown = set(arrays) - set(STATE_NAMES)
+        if unknown:
+            raise TypeError(f"unknown state arrays {unknown}")
+        for name, val in arrays.items():
             if val is not None:
                 getattr(self, name)[...] = np.asarray(val, np.float64).reshape(
                     getattr(self, name).shape)
@@ -299,9 +310,7 @@ class Chain:
         return self
 
     def get_state(self):
-        return {n: getattr(self, n).copy() for n in (
-            "eps", "beta", "gam", "phi", "w_eps", "waux_eps", "w_beta", "waux_beta", "w_nu",
-            "waux_nu")}
+        return {n: getattr(self, n).copy() for n in STATE_NAMES}
 
     def set_opts(self, **kw):
         for k, v in kw.items():

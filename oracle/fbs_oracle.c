@@ -293,6 +293,48 @@ static void orc_tune(double* w, double* waux, int64_t it, double x_new, double x
   }
 }
 
+/* Full conditionals that the all-slice variant (Section 4.2: every non-normal
+ * conditional is slice-sampled) hands to Algorithm 2.  Pinned in the tests
+ * against the exact Inverse-Gamma, Gamma and truncated square-root
+ * Inverse-Gamma laws of the conjugate steps below. */
+typedef struct {
+  double shape1; /* (N + nu)/2 + 1 */
+  double B;      /* (sum_n eps_gn^2 + nu tau)/2 */
+} orc_gam_ctx;
+
+/* log f(gamma_g) = -((N + nu)/2 + 1) log gamma_g - B / gamma_g on gamma_g > 0 */
+static double orc_f_gam(double x, const void* vctx) {
+  const orc_gam_ctx* c = (const orc_gam_ctx*)vctx;
+  if (!(x > 0.0)) return -INFINITY;
+  return -c->shape1 * log(x) - c->B / x;
+}
+
+typedef struct {
+  double shape;  /* a + G nu / 2 */
+  double rate;   /* b + (nu/2) sum_g 1/gamma_g */
+} orc_tau_ctx;
+
+/* log f(tau) = (shape - 1) log tau - rate tau on tau > 0 */
+static double orc_f_tau(double x, const void* vctx) {
+  const orc_tau_ctx* c = (const orc_tau_ctx*)vctx;
+  if (!(x > 0.0)) return -INFINITY;
+  return (c->shape - 1.0) * log(x) - c->rate * x;
+}
+
+typedef struct {
+  double G;      /* number of genes */
+  double hS;     /* sum_g (beta_gl - theta_l)^2 / 2 */
+  double s;      /* upper end s_l of the Uniform(0, s_l) prior */
+} orc_sig_ctx;
+
+/* log f(sigma_l) = -G log sigma_l - hS / sigma_l^2 on 0 < sigma_l < s_l: G
+ * Normal(theta_l, sigma_l^2) terms times the flat prior density of sigma_l */
+static double orc_f_sig(double x, const void* vctx) {
+  const orc_sig_ctx* c = (const orc_sig_ctx*)vctx;
+  if (!(x > 0.0 && x < c->s)) return -INFINITY;
+  return -c->G * log(x) - c->hS / (x * x);
+}
+
 typedef struct {
   int kind;
   double p0, p1;
@@ -364,7 +406,8 @@ void orc_step_eps(const orc_model* m, orc_state* st, const orc_opts* o, int64_t 
 
 /* Step 2: in parallel over g, gamma_g from its full conditional
  * Inverse-Gamma((N + nu)/2, (sum_n eps_gn^2 + nu tau)/2), the conjugate update
- * of the Inverse-Gamma(nu/2, nu tau/2) prior by N Normal(0, gamma_g) terms. */
+ * of the Inverse-Gamma(nu/2, nu tau/2) prior by N Normal(0, gamma_g) terms:
+ * drawn exactly, or (all_slice) by a slice update of that density. */
 void orc_step_gamma(const orc_model* m, orc_state* st, const orc_opts* o, int64_t it,
                     orc_counters* cnt) {
   const int N = m->N;
@@ -377,6 +420,16 @@ void orc_step_gamma(const orc_model* m, orc_state* st, const orc_opts* o, int64_
     }
     double shape = 0.5 * ((double)N + nu);
     double scale = 0.5 * (ss + nu * tau);
+    if (o->all_slice) {
+      orc_gam_ctx c = {shape + 1.0, scale};
+      orc_rng r = {o->seed, o->chain, ORC_STREAM_GAMMA, (uint32_t)g, (uint32_t)it};
+      double x_old = st->gam[g];
+      double x_new = orc_slice(x_old, orc_f_gam, &c, st->w_gam[g], o->step_out_max,
+                               o->shrink_max, &r, &cnt->evals_gam, cnt);
+      st->gam[g] = x_new;
+      orc_tune(&st->w_gam[g], &st->waux_gam[g], it, x_new, x_old, o);
+      continue;
+    }
     double gv = orc_gamma(shape, o->seed, o->chain, ORC_STREAM_GAMMA, (uint32_t)g,
                           (uint32_t)it, 0, &cnt->gamma_caps);
     st->gam[g] = scale / gv;
@@ -401,7 +454,8 @@ void orc_step_nu(const orc_model* m, orc_state* st, const orc_opts* o, int64_t i
 }
 
 /* Step 4: reduction to S2 = sum 1/gamma_g, then
- * tau ~ Gamma(a + G nu / 2, rate = b + (nu/2) S2). */
+ * tau ~ Gamma(a + G nu / 2, rate = b + (nu/2) S2): drawn exactly, or (all_slice)
+ * by a slice update of that density. */
 void orc_step_tau(const orc_model* m, orc_state* st, const orc_opts* o, int64_t it,
                   orc_counters* cnt) {
   double S1, S2;
@@ -409,6 +463,16 @@ void orc_step_tau(const orc_model* m, orc_state* st, const orc_opts* o, int64_t 
   const double nu = st->phi[0];
   double shape = m->a + 0.5 * (double)m->G * nu;
   double rate = m->b + 0.5 * nu * S2;
+  if (o->all_slice) {
+    orc_tau_ctx c = {shape, rate};
+    orc_rng r = {o->seed, o->chain, ORC_STREAM_TAU, 0u, (uint32_t)it};
+    double x_old = st->phi[1];
+    double x_new = orc_slice(x_old, orc_f_tau, &c, st->w_hyp[0], o->step_out_max,
+                             o->shrink_max, &r, &cnt->evals_hyp, cnt);
+    st->phi[1] = x_new;
+    orc_tune(&st->w_hyp[0], &st->waux_hyp[0], it, x_new, x_old, o);
+    return;
+  }
   double gv = orc_gamma(shape, o->seed, o->chain, ORC_STREAM_TAU, 0u, (uint32_t)it, 0,
                         &cnt->gamma_caps);
   st->phi[1] = gv / rate;
@@ -456,7 +520,8 @@ void orc_step_theta(const orc_model* m, orc_state* st, const orc_opts* o, int64_
 
 /* Step 7: reduction to S_l = sum_g (beta_gl - theta_l)^2, then sigma_l^2 ~
  * Inverse-Gamma((G-1)/2, S_l/2) truncated to (0, s_l^2): the Uniform(0, s_l)
- * prior on sigma_l carries the Jacobian 1/(2 sigma_l) onto sigma_l^2. */
+ * prior on sigma_l carries the Jacobian 1/(2 sigma_l) onto sigma_l^2.  With
+ * all_slice, sigma_l is slice-sampled on (0, s_l) instead. */
 void orc_step_sigma(const orc_model* m, orc_state* st, const orc_opts* o, int64_t it,
                     orc_counters* cnt) {
   const int L = m->L;
@@ -466,6 +531,17 @@ void orc_step_sigma(const orc_model* m, orc_state* st, const orc_opts* o, int64_
     for (int g = 0; g < m->G; ++g) {
       double dv = st->beta[(size_t)g * L + l] - theta;
       S += dv * dv;
+    }
+    if (o->all_slice) {
+      /* the slice variable is sigma_l itself; the state keeps sigma_l^2 */
+      orc_sig_ctx c = {(double)m->G, 0.5 * S, m->s[l]};
+      orc_rng r = {o->seed, o->chain, ORC_STREAM_SIGMA, (uint32_t)l, (uint32_t)it};
+      double x_old = sqrt(st->phi[2 + L + l]);
+      double x_new = orc_slice(x_old, orc_f_sig, &c, st->w_hyp[1 + l], o->step_out_max,
+                               o->shrink_max, &r, &cnt->evals_hyp, cnt);
+      st->phi[2 + L + l] = x_new * x_new;
+      orc_tune(&st->w_hyp[1 + l], &st->waux_hyp[1 + l], it, x_new, x_old, o);
+      continue;
     }
     double shape = 0.5 * ((double)m->G - 1.0);
     double upper = m->s[l] * m->s[l];
@@ -617,6 +693,14 @@ int orc_init_state(const orc_model* m, orc_state* st, const orc_opts* o) {
   }
   st->w_nu[0] = o->w0;
   st->waux_nu[0] = 0.0;
+  for (int g = 0; g < G; ++g) {
+    st->w_gam[g] = o->w0;
+    st->waux_gam[g] = 0.0;
+  }
+  for (int i = 0; i <= L; ++i) {
+    st->w_hyp[i] = o->w0;
+    st->waux_hyp[i] = 0.0;
+  }
   free(A);
   free(P);
   return 0;

@@ -60,6 +60,11 @@ typedef struct {
   double* waux_beta; /* [G][L] */
   double* w_nu;      /* [1] */
   double* waux_nu;   /* [1] */
+  /* widths of the variables that only the all-slice variant slice-samples */
+  double* w_gam;     /* [G] gamma_g */
+  double* waux_gam;  /* [G] */
+  double* w_hyp;     /* [1+L]: tau, then sigma_1..sigma_L */
+  double* waux_hyp;  /* [1+L] */
 } orc_state;
 
 typedef struct {
@@ -70,6 +75,8 @@ typedef struct {
   int64_t burnin;     /* M_B */
   int64_t tune_start; /* M_C */
   double w0;          /* initial slice width */
+  int all_slice;      /* 1: slice-sample gamma_g, tau and sigma_l as well (Section 4.2:
+                         every non-normal full conditional); 0: draw them exactly */
 } orc_opts;
 
 typedef struct {
@@ -91,6 +98,7 @@ typedef struct {
   int64_t gamma_caps;                      /* gamma draws that ran out of attempts */
   int64_t trunc_caps;                      /* truncated draws that ran out of attempts */
   int64_t nonfinite;                       /* slice updates started at a non-finite density */
+  int64_t evals_gam, evals_hyp;            /* all-slice variant: gamma_g; tau and sigma_l */
 } orc_counters;
 
 /* ---- random numbers ---- */

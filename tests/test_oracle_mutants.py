@@ -7,6 +7,7 @@ import os
 import pytest
 
 import oracle
+from tests import test_oracle_all_slice as als
 from tests import test_oracle_conditionals as cond
 from tests import test_oracle_geweke as gew
 from tests import test_oracle_slice_moments as sm
@@ -41,6 +42,19 @@ MUTANTS = {
     "gamma step sums |eps| instead of eps^2": (
         "ss += e * e;", "ss += fabs(e);",
         [gew.test_geweke_gene_level_steps]),
+    "gamma slice density misses the +1 of the Inverse-Gamma": (
+        "orc_gam_ctx c = {shape + 1.0, scale};", "orc_gam_ctx c = {shape, scale};",
+        [als.test_gamma_slice_step_matches_posterior]),
+    "tau slice density exponent shape instead of shape - 1": (
+        "return (c->shape - 1.0) * log(x) - c->rate * x;", "return c->shape * log(x) - c->rate * x;",
+        [als.test_tau_slice_step_matches_posterior]),
+    "sigma slice density with the sigma^2 Jacobian": (
+        "return -c->G * log(x) - c->hS / (x * x);",
+        "return -(c->G - 1.0) * log(x) - c->hS / (x * x);",
+        [als.test_sigma_slice_step_matches_posterior_with_truncation]),
+    "sigma slice ignores the upper bound s_l": (
+        "if (!(x > 0.0 && x < c->s)) return -INFINITY;", "if (!(x > 0.0)) return -INFINITY;",
+        [als.test_sigma_slice_step_matches_posterior_with_truncation]),
     "stepping out never moves right": (
         "if (logu < f(hi, ctx)) hi += w; else break;", "break;",
         [lambda: sm.test_slice_normal_target(0.05)]),

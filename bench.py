@@ -7,7 +7,9 @@ paper's 16 x 5 design), G=40000 genes, L=5, theta=(4,0,0,0,0),
 sigma=(2,.5,.3,.2,.2), tau=0.1, nu=3; priors c=s=10, a=b=1, d=10; run length
 20000 iterations with 10000 burn-in and thin 10.
 
-Forms: "f64" (the plain method in FP64), "f32" (FP32 slice log densities, FP64
+Forms: "f64" (the plain method in FP64: gamma_g, tau, sigma_l^2 drawn exactly),
+"f64_all_slice" (the ablation that slice-samples gamma_g, tau and sigma_l as well,
+as the paper does), "f32" (FP32 slice log densities, FP64
 reductions and hyperparameters, Kahan-compensated FP32 moments) and "learned"
 (the f32 form plus the learned beta_g proposal: 2e6 training pairs drawn by the
 plain sampler during burn-in, trained on the GPU, then an eta-preserving
@@ -58,7 +60,8 @@ def parse():
     ap.add_argument("--steps", type=int, default=10)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=("ours", "reference"), default="ours")
-    ap.add_argument("--form", choices=("f64", "f32", "learned"), default="learned")
+    ap.add_argument("--form", choices=("f64", "f64_all_slice", "f32", "learned"),
+                    default="learned")
     ap.add_argument("--forms", choices=("all", "headline"), default="all",
                     help="run the configured job (ESS) for every form or only the headline one")
     ap.add_argument("--block", type=int, default=0, help="threads per block of the gene kernel")
@@ -282,6 +285,8 @@ def run_batch(args):
 # --------------------------------------------------------------------------- our arm
 FORM_TEXT = {
     "f64": "plain method, FP64",
+    "f64_all_slice": "plain method, FP64, with gamma_g, tau and sigma_l slice-sampled "
+                     "(each with its own tuned width) instead of drawn exactly",
     "f32": "FP32 slice log densities; FP64 reductions and hyperparameters; "
            "Kahan-compensated FP32 moments",
     "learned": "the f32 form plus the learned beta_g proposal (eta-preserving MH move "
@@ -300,9 +305,38 @@ MIN_ACCEPT = 0.01
 
 
 def new_sampler(fbs, data, y, form, seed, chain, block, **kw):
-    prec = fbs.FBS_F64 if form == "f64" else fbs.FBS_F32
+    prec = fbs.FBS_F64 if form.startswith("f64") else fbs.FBS_F32
     return fbs.Sampler(y, data["X"], data["h"], data["priors"], seed=seed, chain=chain,
-                       precision=prec, block=block, **kw)
+                       precision=prec, block=block, all_slice=int(form == "f64_all_slice"),
+                       **kw)
+
+
+def geyer_ess(tr):
+    """Effective sample size of every column of a [rows][S] host trace (Geyer's
+    initial monotone sequence; the device kernel behind fbs_beta_ess does the same
+    for beta).  Used for the few hyperparameter columns."""
+    tr = np.asarray(tr, np.float64)
+    n = tr.shape[0]
+    out = []
+    for x in tr.T:
+        x = x - x.mean()
+        c0 = float(x @ x) / n
+        if not c0 > 0:
+            out.append(float(n))
+            continue
+        ac = np.correlate(x, x, "full")[n - 1:] / n / c0
+        s, prev = 0.0, np.inf
+        for j in range(0, n // 2):
+            if 2 * j + 1 >= n:
+                break
+            pair = ac[2 * j] + ac[2 * j + 1]
+            if not pair > 0:
+                break
+            pair = min(pair, prev)
+            s += pair
+            prev = pair
+        out.append(n / max(-1.0 + 2.0 * s, 1.0 / n))
+    return np.array(out)
 
 
 def ess_job(fbs, torch, data, y_host, form, seed, chain, block, S, train_epochs):
@@ -351,6 +385,7 @@ def ess_job(fbs, torch, data, y_host, form, seed, chain, block, S, train_epochs)
     wall = time.perf_counter() - t0
     dev_s = ev0.elapsed_time(ev1) / 1e3
     e = smp.beta_ess()
+    ess_phi = geyer_ess(smp.trace()["phi"])
     if form == "learned":
         st = smp.proposal_stats()
         extra["accept_rate"] = st["accepted"] / max(1, st["tried"])
@@ -366,6 +401,8 @@ def ess_job(fbs, torch, data, y_host, form, seed, chain, block, S, train_epochs)
            "median_ess": float(np.median(e)), "ess_rows": rows,
            "min_ess_per_s": float(e.min()) / wall, "p05_ess_per_s": float(np.percentile(e, 5)) / wall,
            "median_ess_per_s": float(np.median(e)) / wall,
+           "phi_ess": [round(float(v), 1) for v in ess_phi],
+           "min_phi_ess_per_s": float(ess_phi.min()) / wall,
            "h2d_bytes_per_step": h2d / phi_reads, "d2h_bytes_per_step": d2h / phi_reads}
     out.update(extra)
     return out
@@ -416,7 +453,8 @@ def main():
     burnin, thin = spec["burnin"], spec["thin"]
     forms = {}
     if not args.no_ess:
-        order = ["f64", "f32", "learned"] if args.forms == "all" else [form]
+        order = (["f64", "f64_all_slice", "f32", "learned"] if args.forms == "all"
+                 else [form])
         for f in order:
             barrier()
             forms[f] = ess_job(fbs, torch, data, y_host, f, seed, rank, args.block, S,
@@ -467,15 +505,16 @@ def main():
     ms_k1, ms_k2, ms_hyper, ms_prop = smp.profile(S, burnin=tb, thin=thin)
     ms_gene = ms_k1 + ms_k2
     peak, peak_kind = measured_peaks()
-    prec_name = "f64" if form == "f64" else "f32"
+    prec_name = "f64" if form.startswith("f64") else "f32"
     bpg = bytes_per_gene(N, L, prec_name)
     achieved = bpg * G / (ms_gene / 1e3) / 1e9
     evals = {k: (c1[k] - c0[k]) / (args.steps * S) for k in ("evals_eps", "evals_beta",
-                                                               "evals_nu")}
-    ev_launch = evals["evals_eps"] + evals["evals_beta"]
+                                                               "evals_nu", "evals_gam",
+                                                               "evals_hyp")}
+    ev_launch = evals["evals_eps"] + evals["evals_beta"] + evals["evals_gam"]
     hbm = {"achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
            "bytes_per_gene": bpg, "genes_per_launch": G, "peak_source": peak_kind}
-    if form == "f64":
+    if prec_name == "f64":
         tflops = ev_launch * FP64_FLOP_PER_EVAL / (ms_gene / 1e3) / 1e12
         roofline = {"bound": "alu", "achieved": tflops, "peak": FP64_PEAK_TFLOPS,
                     "unit": "TFLOP/s (FP64)", "frac": tflops / FP64_PEAK_TFLOPS,
@@ -553,6 +592,11 @@ def main():
             line["vs_plain_f64"] = {
                 k: h[k] / b[k] for k in ("iters_per_s_e2e", "min_ess_per_s", "p05_ess_per_s",
                                          "median_ess_per_s")}
+            if "f64_all_slice" in forms:
+                a = forms["f64_all_slice"]
+                line["all_slice_vs_exact_draws"] = {
+                    k: a[k] / b[k] for k in ("iters_per_s_e2e", "min_ess_per_s",
+                                             "median_ess_per_s", "min_phi_ess_per_s")}
     if not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline(data, args.cpu_seconds, G)
     print(json.dumps(line), flush=True)

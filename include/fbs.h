@@ -66,7 +66,9 @@ extern "C" {
 #define FBS_CNT_TRUNC_CAPS 5  /* truncated sigma^2 draws that kept their value */
 #define FBS_CNT_NONFINITE 6   /* slice updates started at a non-finite log density */
 #define FBS_CNT_SWEEPS 7      /* completed iterations */
-#define FBS_NUM_COUNTERS 8
+#define FBS_CNT_EVALS_GAMMA 8 /* log-density evaluations, gamma_g slice updates (all_slice) */
+#define FBS_CNT_EVALS_HYPER 9 /* log-density evaluations, tau and sigma_l slice updates (all_slice) */
+#define FBS_NUM_COUNTERS 10
 
 typedef struct fbs_handle fbs_handle;
 
@@ -90,6 +92,10 @@ typedef struct {
   int trace_beta;        /* 1: the trace also stores all G*L beta per row */
   int block;             /* threads per block of the per-gene kernel (0: library choice) */
   int graph_segment;     /* iterations per captured CUDA graph (0: library choice, 100) */
+  int all_slice;         /* 1: slice-sample gamma_g, tau and sigma_l too, each with its own
+                            width (Section 4.2 slice-samples every non-normal full
+                            conditional); 0 (default): draw them exactly from their
+                            Inverse-Gamma, Gamma and truncated laws.  FBS_F64 only. */
 } fbs_options;
 
 /* Fill *o with the defaults: FP64, w0 = 1, K = 100, shrink_max = 100, chain 0,
@@ -156,6 +162,16 @@ int fbs_set_state(fbs_handle* h, const double* eps, const double* beta, const do
                   const double* phi, const double* w_eps, const double* waux_eps,
                   const double* w_beta, const double* waux_beta, const double* w_nu,
                   const double* waux_nu, int64_t it);
+
+/* Slice widths and tuning sums of the variables that only all_slice samples
+ * by slice updates: w_gam, waux_gam [G] (gamma_g); w_hyp, waux_hyp [1+L]
+ * (tau, then sigma_1..sigma_L; the slice variable is sigma_l, not sigma_l^2).
+ * fbs_init sets every width to w0 and every sum to 0 in either mode.  NULL
+ * pointers are skipped; FBS_E_ARG for an FBS_F32 handle.  Synchronous. */
+int fbs_get_slice_widths(fbs_handle* h, double* w_gam, double* waux_gam, double* w_hyp,
+                         double* waux_hyp);
+int fbs_set_slice_widths(fbs_handle* h, const double* w_gam, const double* waux_gam,
+                         const double* w_hyp, const double* waux_hyp);
 
 /* Thinned trace: up to max_rows rows copied to host: phi rows [rows][2L+2] and,
  * when the handle keeps it and beta != NULL, beta rows [rows][G][L].

@@ -25,7 +25,7 @@ FBS_MAX_CONTRASTS, FBS_MAX_CONTRAST_TERMS = 8, 4
 FBS_MAX_RHAT_CHAINS = 64
 MAX_N, MAX_L, MAX_CLASSES = 64, 8, 8
 COUNTER_NAMES = ("evals_eps", "evals_beta", "evals_nu", "slice_caps", "gamma_caps",
-                 "trunc_caps", "nonfinite", "sweeps")
+                 "trunc_caps", "nonfinite", "sweeps", "evals_gam", "evals_hyp")
 NUM_COUNTERS = len(COUNTER_NAMES)
 
 # symbols declared in include/fbs.h
@@ -38,7 +38,8 @@ EXPORTED = ("fbs_default_options", "fbs_workspace_bytes", "fbs_init", "fbs_run",
             "fbs_proposal_train", "fbs_proposal_calibrate", "fbs_proposal_mode",
             "fbs_proposal_params", "fbs_proposal_stats", "fbs_proposal_loss_grad",
             "fbs_proposal_outputs", "fbs_proposal_step", "fbs_set_contrasts",
-            "fbs_contrast_probs", "fbs_rhat", "fbs_proposal_kinds")
+            "fbs_contrast_probs", "fbs_rhat", "fbs_proposal_kinds", "fbs_get_slice_widths",
+            "fbs_set_slice_widths")
 NOALLOC_MAX_GENES = 2048 * 128
 
 
@@ -57,7 +58,7 @@ class Options(C.Structure):
     _fields_ = [("precision", C.c_int), ("w0", C.c_double), ("step_out_max", C.c_int),
                 ("shrink_max", C.c_int), ("chain", C.c_uint32), ("moments_eps", C.c_int),
                 ("trace_cap", C.c_int64), ("trace_beta", C.c_int), ("block", C.c_int),
-                ("graph_segment", C.c_int)]
+                ("graph_segment", C.c_int), ("all_slice", C.c_int)]
 
 
 _PD = C.POINTER(C.c_double)
@@ -103,6 +104,8 @@ def load_library(path: str = LIB_PATH):
     lib.fbs_moments.argtypes = [vp] + [_PD] * 8 + [_PI64]
     lib.fbs_get_state.argtypes = [vp] + [_PD] * 10 + [_PI64]
     lib.fbs_set_state.argtypes = [vp] + [_PD] * 10 + [i64]
+    lib.fbs_get_slice_widths.argtypes = [vp] + [_PD] * 4
+    lib.fbs_set_slice_widths.argtypes = [vp] + [_PD] * 4
     lib.fbs_trace.argtypes = [vp, i64, _PD, _PD, _PI64]
     lib.fbs_beta_ess.argtypes = [vp, _PD]
     lib.fbs_count_sums.argtypes = [vp, _PI64]
@@ -332,6 +335,11 @@ class Sampler:
             "eps", "beta", "gam", "phi", "w_eps", "waux_eps", "w_beta", "waux_beta", "w_nu",
             "waux_nu")], C.byref(it)))
         out["it"] = it.value
+        if self.options.precision == FBS_F64:
+            wid = {"w_gam": np.empty(G), "waux_gam": np.empty(G), "w_hyp": np.empty(L + 1),
+                   "waux_hyp": np.empty(L + 1)}
+            _check(self.lib.fbs_get_slice_widths(self.h, *[_pd(v) for v in wid.values()]))
+            out.update(wid)
         return out
 
     def phi(self):
@@ -342,14 +350,23 @@ class Sampler:
         return out
 
     def set_state(self, it=0, **arrays):
+        """State arrays by name (as get_state returns them); the gamma, tau and
+        sigma widths w_gam, waux_gam [G], w_hyp, waux_hyp [1+L] exist in FP64 only."""
         names = ("eps", "beta", "gam", "phi", "w_eps", "waux_eps", "w_beta", "waux_beta", "w_nu",
                  "waux_nu")
-        unknown = set(arrays) - set(names)
+        widths = ("w_gam", "waux_gam", "w_hyp", "waux_hyp")
+        unknown = set(arrays) - set(names) - set(widths)
         if unknown:
             raise TypeError(f"unknown state arrays {unknown}")
         conv = {k: np.ascontiguousarray(np.atleast_1d(v), np.float64) for k, v in arrays.items()
                 if v is not None}
+        for k, n in (("w_gam", self.G), ("waux_gam", self.G), ("w_hyp", self.L + 1),
+                     ("waux_hyp", self.L + 1)):
+            if k in conv and conv[k].size != n:
+                raise ValueError(f"{k} needs {n} values")
         _check(self.lib.fbs_set_state(self.h, *[_pd(conv.get(k)) for k in names], int(it)))
+        if any(k in conv for k in widths):
+            _check(self.lib.fbs_set_slice_widths(self.h, *[_pd(conv.get(k)) for k in widths]))
 
     def moments(self):
         G, N, L, P = self.G, self.N, self.L, self.P

@@ -41,7 +41,8 @@ size_t align256(size_t x) { return (x + 255) & ~(size_t)255; }
 // Byte offsets of every device buffer inside one workspace.
 struct Layout {
   size_t y, T, eps, w_eps, waux_eps, m_eps, q_eps, mu, beta, w_beta, waux_beta, m_beta, q_beta;
-  size_t gam, m_gam, q_gam, partial, hyp, trace_phi, trace_beta, counters, pinv, total;
+  size_t gam, w_gam, waux_gam, m_gam, q_gam, partial, hyp, trace_phi, trace_beta, counters, pinv;
+  size_t total;
 };
 
 Layout make_layout(int N, int G, int L, int nblk, long long trace_cap, int trace_beta) {
@@ -67,6 +68,8 @@ Layout make_layout(int N, int G, int L, int nblk, long long trace_cap, int trace
   o.m_beta = take(LG * 8);
   o.q_beta = take(LG * 8);
   o.gam = take((size_t)G * 8);
+  o.w_gam = take((size_t)G * 8);
+  o.waux_gam = take((size_t)G * 8);
   o.m_gam = take((size_t)G * 8);
   o.q_gam = take((size_t)G * 8);
   o.partial = take((size_t)nblk * kNumPart * 8);
@@ -203,6 +206,9 @@ int check_opts(const fbs_options* o) {
   if (o->block < 0 || o->block > 128 || (o->block % 32) != 0)
     return fail(FBS_E_ARG, "block must be 0 or a multiple of 32 up to 128");
   if (o->graph_segment < 0) return fail(FBS_E_ARG, "graph_segment must be >= 0");
+  if (o->all_slice != 0 && o->all_slice != 1) return fail(FBS_E_ARG, "all_slice must be 0 or 1");
+  if (o->all_slice && o->precision != FBS_F64)
+    return fail(FBS_E_ARG, "all_slice runs in the FBS_F64 form");
   return FBS_OK;
 }
 
@@ -268,6 +274,8 @@ DevPtrs carve(char* base, const Layout& o, int trace_beta) {
   p.m_beta = (double*)(base + o.m_beta);
   p.q_beta = (double*)(base + o.q_beta);
   p.gam = (double*)(base + o.gam);
+  p.w_gam = (double*)(base + o.w_gam);
+  p.waux_gam = (double*)(base + o.waux_gam);
   p.m_gam = (double*)(base + o.m_gam);
   p.q_gam = (double*)(base + o.q_gam);
   p.partial = (double*)(base + o.partial);
@@ -466,12 +474,14 @@ int build_model(const int32_t* y, int N, int G, const double* X, int L, const do
   mc.seed_lo = (uint32_t)(seed & 0xffffffffu);
   mc.seed_hi = (uint32_t)(seed >> 32);
   mc.chain = chain;
+  mc.all_slice = o->all_slice;
   mc.a = pri->a;
   mc.b = pri->b;
   mc.d = pri->d;
   for (int l = 0; l < L; ++l) {
     mc.c2[l] = pri->c[l] * pri->c[l];
     mc.s2[l] = pri->s[l] * pri->s[l];
+    mc.s[l] = pri->s[l];
   }
   bool integral = true;
   for (int n = 0; n < N; ++n) {
@@ -797,6 +807,42 @@ int fbs_set_state(fbs_handle* h, const double* eps, const double* beta, const do
   if (w_nu) hy.w_nu = *w_nu;
   if (waux_nu) hy.waux_nu = *waux_nu;
   hy.it = it;
+  FBS_CUDA(cudaMemcpyAsync(h->p.hyp, &hy, sizeof(Hyper), cudaMemcpyHostToDevice, h->s));
+  FBS_CUDA(cudaStreamSynchronize(h->s));
+  return leave(h);
+}
+
+int fbs_get_slice_widths(fbs_handle* h, double* w_gam, double* waux_gam, double* w_hyp,
+                         double* waux_hyp) {
+  if (!h) return fail(FBS_E_ARG, "handle is NULL");
+  if (h->prec != FBS_F64) return fail(FBS_E_ARG, "the FBS_F32 form keeps no gamma, tau or sigma widths");
+  int rc = enter(h);
+  if (rc) return rc;
+  const size_t G = (size_t)h->mc.G, L = (size_t)h->mc.L;
+  if (w_gam) FBS_CUDA(cudaMemcpyAsync(w_gam, h->p.w_gam, G * 8, cudaMemcpyDeviceToHost, h->s));
+  if (waux_gam)
+    FBS_CUDA(cudaMemcpyAsync(waux_gam, h->p.waux_gam, G * 8, cudaMemcpyDeviceToHost, h->s));
+  Hyper hy;
+  if ((rc = read_hyper(h, &hy))) return rc;
+  if (w_hyp) memcpy(w_hyp, hy.w_hyp, (L + 1) * 8);
+  if (waux_hyp) memcpy(waux_hyp, hy.waux_hyp, (L + 1) * 8);
+  return leave(h);
+}
+
+int fbs_set_slice_widths(fbs_handle* h, const double* w_gam, const double* waux_gam,
+                         const double* w_hyp, const double* waux_hyp) {
+  if (!h) return fail(FBS_E_ARG, "handle is NULL");
+  if (h->prec != FBS_F64) return fail(FBS_E_ARG, "the FBS_F32 form keeps no gamma, tau or sigma widths");
+  int rc = enter(h);
+  if (rc) return rc;
+  const size_t G = (size_t)h->mc.G, L = (size_t)h->mc.L;
+  if (w_gam) FBS_CUDA(cudaMemcpyAsync(h->p.w_gam, w_gam, G * 8, cudaMemcpyHostToDevice, h->s));
+  if (waux_gam)
+    FBS_CUDA(cudaMemcpyAsync(h->p.waux_gam, waux_gam, G * 8, cudaMemcpyHostToDevice, h->s));
+  Hyper hy;
+  if ((rc = read_hyper(h, &hy))) return rc;
+  if (w_hyp) memcpy(hy.w_hyp, w_hyp, (L + 1) * 8);
+  if (waux_hyp) memcpy(hy.waux_hyp, waux_hyp, (L + 1) * 8);
   FBS_CUDA(cudaMemcpyAsync(h->p.hyp, &hy, sizeof(Hyper), cudaMemcpyHostToDevice, h->s));
   FBS_CUDA(cudaStreamSynchronize(h->s));
   return leave(h);

@@ -49,10 +49,12 @@ struct ModelConst {
   int N, G, L, P;
   int K, shrink_max;
   int moments_eps, trace_beta;
-  uint32_t seed_lo, seed_hi, chain, pad0;
+  uint32_t seed_lo, seed_hi, chain;
+  int all_slice;                  // 1: gamma_g, tau, sigma_l by slice updates too
   double a, b, d;
   double c2[kMaxL];               // c_l^2
   double s2[kMaxL];               // s_l^2
+  double s[kMaxL];                // s_l
   double h[kMaxN];
   double X[kMaxN * kMaxL];        // [N][L]
   // Column classes for the beta_gl conditional: the non-zero values of column
@@ -93,6 +95,8 @@ struct Hyper {
   // (kernels that may run concurrently with the hyperparameter kernel derive
   // their iteration from these instead of reading `it`)
   long long seg_it, seg_nmom;
+  // slice widths and tuning sums of tau and sigma_1..sigma_L (all_slice only)
+  double w_hyp[kMaxL + 1], waux_hyp[kMaxL + 1];
 };
 
 // Device pointers of one chain.
@@ -106,6 +110,8 @@ struct DevPtrs {
   double* w_beta;     // [L][G]
   double* waux_beta;  // [L][G]
   double* gam;        // [G]
+  double* w_gam;      // [G] slice widths of gamma_g (all_slice only)
+  double* waux_gam;   // [G]
   double* m_eps;      // [N][G] running mean
   double* q_eps;      // [N][G] running mean square
   double* m_beta;     // [L][G]

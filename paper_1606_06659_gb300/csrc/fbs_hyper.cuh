@@ -1,6 +1,8 @@
 // fbs_hyper.cuh -- the hyperparameter steps of one Gibbs sweep (Algorithm 1
 // steps 3, 4, 6, 7 of Landau & Niemi, arXiv 1606.06659) as a block-level device
 // function, shared by the single-chain and the batched hyperparameter kernels.
+// tau and sigma_l^2 are drawn exactly, or (ModelConst::all_slice) by slice
+// updates of their conditionals: tau spread over warp 0, sigma_l on lane 32+l.
 #pragma once
 
 #include <math.h>
@@ -24,6 +26,30 @@ struct NuDensity {
     if (!(nu > 0.0 && nu < d)) return -INFINITY;
     return -G * lgamma(0.5 * nu) + 0.5 * G * nu * log(0.5 * nu * tau) -
            0.5 * nu * (S1 + tau * S2);
+  }
+};
+
+// log f(tau | ...) = (shape - 1) log tau - rate tau on tau > 0, shape = a + G nu/2,
+// rate = b + (nu/2) S2: the Gamma full conditional of step 4, slice-sampled in the
+// all-slice variant (Section 4.2).
+struct TauDensity {
+  double shape, rate;
+  __device__ __forceinline__ double operator()(double x, double* aux) const {
+    *aux = 0.0;
+    if (!(x > 0.0)) return -INFINITY;
+    return (shape - 1.0) * log(x) - rate * x;
+  }
+};
+
+// log f(sigma_l | ...) = -G log sigma_l - hS / sigma_l^2 on 0 < sigma_l < s_l, hS =
+// sum_g (beta_gl - theta_l)^2 / 2: G Normal(theta_l, sigma_l^2) terms times the flat
+// Uniform(0, s_l) prior, the step 7 conditional of sigma_l itself (all-slice variant).
+struct SigDensity {
+  double G, hS, s;
+  __device__ __forceinline__ double operator()(double x, double* aux) const {
+    *aux = 0.0;
+    if (!(x > 0.0 && x < s)) return -INFINITY;
+    return -G * log(x) - hS / (x * x);
   }
 };
 
@@ -82,8 +108,15 @@ __device__ __forceinline__ void hyper_body(const ModelConst& mc, const double* p
     Rng r(mc.seed_lo, mc.seed_hi, mc.chain, kStreamNu, 0u, it32);
     const double x0 = sh.phi[0];
     SliceResult s = slice_update_warp(x0, sh.w_nu, f, r, mc.K, mc.shrink_max);
+    const double nu = s.x;
+    Rng rt(mc.seed_lo, mc.seed_hi, mc.chain, kStreamTau, 0u, it32);
+    const double shape = mc.a + 0.5 * G * nu;
+    const double rate = mc.b + 0.5 * nu * S2;
+    SliceResult st;
+    if (mc.all_slice)  // step 4 by a slice update of the Gamma conditional, on warp 0
+      st = slice_update_warp(sh.phi[1], sh.w_hyp[0], TauDensity{shape, rate}, rt, mc.K,
+                             mc.shrink_max);
     if (tid == 0) {
-      const double nu = s.x;
       if (it <= sh.burnin) {
         double w = sh.w_nu, waux = sh.waux_nu;
         tune_width(w, waux, it, nu, x0, sh.burnin, sh.tune_start);
@@ -97,12 +130,26 @@ __device__ __forceinline__ void hyper_body(const ModelConst& mc, const double* p
         atomicOr(&hy->flags, kFlagNonfinite);
       }
       // step 4: tau ~ Gamma(a + G nu/2, rate b + nu S2 / 2)
-      Rng rt(mc.seed_lo, mc.seed_hi, mc.chain, kStreamTau, 0u, it32);
-      bool gcap = false;
-      const double shape = mc.a + 0.5 * G * nu;
-      const double rate = mc.b + 0.5 * nu * S2;
-      const double tau = gamma_mt(shape, rt, 0, &gcap) / rate;
-      if (gcap) atomicAdd(&counters[FBS_CNT_GAMMA_CAPS], 1ull);
+      double tau;
+      if (mc.all_slice) {
+        tau = st.x;
+        if (it <= sh.burnin) {
+          double w = sh.w_hyp[0], waux = sh.waux_hyp[0];
+          tune_width(w, waux, it, tau, sh.phi[1], sh.burnin, sh.tune_start);
+          hy->w_hyp[0] = w;
+          hy->waux_hyp[0] = waux;
+        }
+        atomicAdd(&counters[FBS_CNT_EVALS_HYPER], (unsigned long long)st.evals);
+        if (st.capped) atomicAdd(&counters[FBS_CNT_SLICE_CAPS], 1ull);
+        if (st.nonfinite) {
+          atomicAdd(&counters[FBS_CNT_NONFINITE], 1ull);
+          atomicOr(&hy->flags, kFlagNonfinite);
+        }
+      } else {
+        bool gcap = false;
+        tau = gamma_mt(shape, rt, 0, &gcap) / rate;
+        if (gcap) atomicAdd(&counters[FBS_CNT_GAMMA_CAPS], 1ull);
+      }
       phi_new[0] = nu;
       phi_new[1] = tau;
     }
@@ -122,10 +169,31 @@ __device__ __forceinline__ void hyper_body(const ModelConst& mc, const double* p
     const double dl = th - th_old;
     const double S = B2s - 2.0 * dl * B1s + G * dl * dl;
     Rng rs(mc.seed_lo, mc.seed_hi, mc.chain, kStreamSigma, (uint32_t)l, it32);
-    bool gcap = false, tcap = false;
-    const double s2n = trunc_invgamma(0.5 * (G - 1.0), 0.5 * S, mc.s2[l], sig2, rs, &gcap, &tcap);
-    if (gcap) atomicAdd(&counters[FBS_CNT_GAMMA_CAPS], 1ull);
-    if (tcap) atomicAdd(&counters[FBS_CNT_TRUNC_CAPS], 1ull);
+    double s2n;
+    if (mc.all_slice) {
+      // a slice update of sigma_l itself on (0, s_l); the state keeps sigma_l^2
+      const double x0 = sqrt(sig2);
+      SliceResult ss = slice_update(x0, sh.w_hyp[1 + l], SigDensity{G, 0.5 * S, mc.s[l]}, rs,
+                                    mc.K, mc.shrink_max);
+      s2n = ss.x * ss.x;
+      if (it <= sh.burnin) {
+        double w = sh.w_hyp[1 + l], waux = sh.waux_hyp[1 + l];
+        tune_width(w, waux, it, ss.x, x0, sh.burnin, sh.tune_start);
+        hy->w_hyp[1 + l] = w;
+        hy->waux_hyp[1 + l] = waux;
+      }
+      atomicAdd(&counters[FBS_CNT_EVALS_HYPER], (unsigned long long)ss.evals);
+      if (ss.capped) atomicAdd(&counters[FBS_CNT_SLICE_CAPS], 1ull);
+      if (ss.nonfinite) {
+        atomicAdd(&counters[FBS_CNT_NONFINITE], 1ull);
+        atomicOr(&hy->flags, kFlagNonfinite);
+      }
+    } else {
+      bool gcap = false, tcap = false;
+      s2n = trunc_invgamma(0.5 * (G - 1.0), 0.5 * S, mc.s2[l], sig2, rs, &gcap, &tcap);
+      if (gcap) atomicAdd(&counters[FBS_CNT_GAMMA_CAPS], 1ull);
+      if (tcap) atomicAdd(&counters[FBS_CNT_TRUNC_CAPS], 1ull);
+    }
     phi_new[2 + l] = th;
     phi_new[2 + L + l] = s2n;
   }

@@ -14,6 +14,10 @@
 // Drawing beta before nu and tau is exact: the beta_gl conditional involves
 // neither, and theirs involve no beta (Figure 3); the counter-based generator
 // gives every variable the same uniforms in either order.
+// With ModelConst::all_slice the gamma_g draw (gene kernel), tau (warp 0 of the
+// hyper kernel, after nu) and sigma_l (lane 32+l) are slice updates of the same
+// full conditionals instead, each variable with its own tuned width, as
+// Section 4.2 slice-samples every non-normal conditional.
 #include <cuda_runtime.h>
 #include <math.h>
 #include <stdint.h>
@@ -94,6 +98,18 @@ struct BetaDensityT {
     *aux = z;
     const double dv = b - theta;
     return b * T - s - dv * dv * hs;
+  }
+};
+
+// log f(gamma_g = x | ...) = -shape1 log x - B / x on x > 0, with shape1 = (N + nu)/2 + 1
+// and B = (sum_n eps_gn^2 + nu tau)/2: the Inverse-Gamma full conditional of step 2,
+// slice-sampled in the all-slice variant (Section 4.2).
+struct GamDensity {
+  double shape1, B;
+  __device__ __forceinline__ double operator()(double x, double* aux) const {
+    *aux = 0.0;
+    if (!(x > 0.0)) return -INFINITY;
+    return -shape1 * log(x) - B / x;
   }
 };
 
@@ -310,10 +326,11 @@ __global__ void __launch_bounds__(128) k_gene_f64(ModelConst mc, DevPtrs p) {
 
 __device__ __forceinline__ void add_counters_u(unsigned long long* base, unsigned evals_e,
                                                unsigned evals_b, unsigned caps, unsigned gcaps,
-                                               unsigned nonfin, unsigned* flags) {
-  unsigned v[5] = {evals_e, evals_b, caps, gcaps, nonfin};
+                                               unsigned nonfin, unsigned* flags,
+                                               unsigned evals_g = 0) {
+  unsigned v[6] = {evals_e, evals_b, caps, gcaps, nonfin, evals_g};
 #pragma unroll
-  for (int i = 0; i < 5; ++i) {
+  for (int i = 0; i < 6; ++i) {
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) v[i] += __shfl_down_sync(0xffffffffu, v[i], o);
   }
@@ -326,6 +343,7 @@ __device__ __forceinline__ void add_counters_u(unsigned long long* base, unsigne
       atomicAdd(&base[FBS_CNT_NONFINITE], (unsigned long long)v[4]);
       atomicOr(flags, kFlagNonfinite);
     }
+    if (v[5]) atomicAdd(&base[FBS_CNT_EVALS_GAMMA], (unsigned long long)v[5]);
   }
 }
 
@@ -486,7 +504,7 @@ __global__ void __launch_bounds__(128) k_gb_f64(ModelConst mc, DevPtrs p, int se
 
 #pragma unroll
   for (int i = 0; i < kNumPart; ++i) ps[i * B + tid] = 0.0;
-  unsigned evals_b = 0, caps = 0, gcaps = 0, nonfin = 0;
+  unsigned evals_b = 0, evals_g = 0, caps = 0, gcaps = 0, nonfin = 0;
 
   if (active) {
     for (int l = 0; l < L; ++l) bs[l * B + tid] = p.beta[(size_t)l * G + g];
@@ -499,14 +517,31 @@ __global__ void __launch_bounds__(128) k_gb_f64(ModelConst mc, DevPtrs p, int se
       mu[n * blockDim.x + tid] = p.mu[e];
     }
 
-    // ---- step 2: gamma_g ~ IG((N + nu)/2, (sum eps^2 + nu tau)/2)
+    // ---- step 2: gamma_g ~ IG((N + nu)/2, (sum eps^2 + nu tau)/2), exactly or
+    // (all_slice) by a slice update of that density with the gene's own width
     {
       Rng r(mc.seed_lo, mc.seed_hi, mc.chain, kStreamGamma, (uint32_t)g, it32);
-      bool gcap = false;
       const double shape = 0.5 * ((double)N + nu);
       const double scale = 0.5 * (ss + nu * tau);
-      const double gam = scale / gamma_mt(shape, r, 0, &gcap);
-      gcaps += gcap;
+      double gam;
+      if (mc.all_slice) {
+        const double x0 = p.gam[g];
+        double w = p.w_gam[g], waux = p.waux_gam[g];
+        SliceResult s = slice_update(x0, w, GamDensity{shape + 1.0, scale}, r, mc.K, mc.shrink_max);
+        evals_g += s.evals;
+        caps += s.capped;
+        nonfin += s.nonfinite;
+        gam = s.x;
+        if (it <= burnin) {
+          tune_width(w, waux, it, s.x, x0, burnin, tune_start);
+          p.w_gam[g] = w;
+          p.waux_gam[g] = waux;
+        }
+      } else {
+        bool gcap = false;
+        gam = scale / gamma_mt(shape, r, 0, &gcap);
+        gcaps += gcap;
+      }
       p.gam[g] = gam;
       if (mom) {
         const double m = p.m_gam[g], q = p.q_gam[g];
@@ -558,7 +593,7 @@ __global__ void __launch_bounds__(128) k_gb_f64(ModelConst mc, DevPtrs p, int se
   for (int i = 0; i < kNumPart; ++i) part[i] = ps[i * B + tid];
   double* red = ps + (size_t)kNumPart * B;
   block_sum_to<kNumPart>(part, p.partial + (size_t)blockIdx.x * kNumPart, red);
-  add_counters_u(p.counters, 0, evals_b, caps, gcaps, nonfin, &p.hyp->flags);
+  add_counters_u(p.counters, 0, evals_b, caps, gcaps, nonfin, &p.hyp->flags, evals_g);
 }
 
 __global__ void __launch_bounds__(kHyperThreads) k_hyper(ModelConst mc, DevPtrs p, int nblk) {
@@ -660,6 +695,10 @@ __global__ void k_init_genes(ModelConst mc, DevPtrs p, const int32_t* y_in, int 
         p.waux_eps[(size_t)n * G + g] = 0.0;
       }
       p.gam[g] = 1.0;
+      if (p.w_gam) {
+        p.w_gam[g] = w0;
+        p.waux_gam[g] = 0.0;
+      }
     }
   }
 }
@@ -737,6 +776,10 @@ __global__ void k_init_hyper(ModelConst mc, Hyper* hy, const double* beta_d,
       hy->phi[1] = 1.0;
       hy->w_nu = w0;
       hy->waux_nu = 0.0;
+      for (int i = 0; i <= kMaxL; ++i) {
+        hy->w_hyp[i] = w0;
+        hy->waux_hyp[i] = 0.0;
+      }
       hy->it = 0;
     }
     for (int i = 0; i < kMaxP; ++i) {

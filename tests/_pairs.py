@@ -13,12 +13,14 @@ from paper_1606_06659_gb300 import synthetic
 RTOL, ATOL = 1e-10, 1e-12
 STATE_KEYS = ("eps", "beta", "gam", "phi", "w_eps", "waux_eps", "w_beta", "waux_beta", "w_nu",
               "waux_nu")
+# with the widths of gamma_g, tau and sigma_l (FP64 handles; all-slice variant)
+ALL_SLICE_KEYS = STATE_KEYS + ("w_gam", "waux_gam", "w_hyp", "waux_hyp")
 
 
 def make_pair(data, seed=12345, chain=0, **opt):
     g = fbs.Sampler(data["y"], data["X"], data["h"], data["priors"], seed=seed, chain=chain, **opt)
     kw = {}
-    for k in ("step_out_max", "shrink_max", "w0"):
+    for k in ("step_out_max", "shrink_max", "w0", "all_slice"):
         if k in opt:
             kw[k] = opt[k]
     o = oracle.Chain(data["y"], data["X"], data["h"], data["priors"], seed=seed, chain=chain, **kw)

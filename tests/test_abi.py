@@ -34,6 +34,7 @@ def test_library_exports_every_declared_symbol():
 def test_default_options():
     o = fbs.default_options()
     assert (o.precision, o.w0, o.step_out_max, o.shrink_max, o.moments_eps) == (0, 1.0, 100, 100, 1)
+    assert o.all_slice == 0
 
 
 def _args(**over):
@@ -46,7 +47,8 @@ def _args(**over):
 
 
 @pytest.mark.parametrize("case", ["N0", "G1", "L9", "singular", "negative_y", "nan_h",
-                                  "bad_prior", "too_many_classes", "bad_precision"])
+                                  "bad_prior", "too_many_classes", "bad_precision",
+                                  "all_slice_f32", "all_slice_2"])
 def test_invalid_arguments_rejected_before_any_cuda_call(case):
     kw = {}
     a = _args()
@@ -71,6 +73,10 @@ def test_invalid_arguments_rejected_before_any_cuda_call(case):
         a["h"] = np.zeros(N)
     elif case == "bad_precision":
         kw["precision"] = 7
+    elif case == "all_slice_f32":
+        kw["precision"], kw["all_slice"] = fbs.FBS_F32, 1
+    elif case == "all_slice_2":
+        kw["all_slice"] = 2
     with pytest.raises(fbs.FbsError) as e:
         fbs.Sampler(a["y"], a["X"], a["h"], a["priors"], workspace="library", **kw)
     assert e.value.code == fbs.FBS_E_ARG

@@ -8,8 +8,8 @@ import pytest
 import oracle
 import paper_1606_06659_gb300 as fbs
 from paper_1606_06659_gb300 import synthetic
-from tests._pairs import (RTOL, ATOL, STATE_KEYS, assert_state_close, close, make_pair,
-                          small_data, sync_gpu_to_oracle)
+from tests._pairs import (ALL_SLICE_KEYS, RTOL, ATOL, STATE_KEYS, assert_state_close, close,
+                          make_pair, small_data, sync_gpu_to_oracle)
 
 pytestmark = pytest.mark.gpu
 
@@ -42,6 +42,10 @@ def test_default_start_matches_oracle(cfg):
 
 
 # ------------------------------------------------------------------ lockstep sweeps
+COUNTS = ("evals_eps", "evals_beta", "evals_nu", "slice_caps", "gamma_caps", "trunc_caps",
+          "evals_gam", "evals_hyp")
+
+
 def _lockstep(d, n_sweeps, burnin, seed=12345, **opt):
     """Both sides start every sweep from the oracle's state (copied into the GPU),
     run one sweep, and must agree element by element; the evaluation counts,
@@ -56,10 +60,9 @@ def _lockstep(d, n_sweeps, burnin, seed=12345, **opt):
         g.run(1, burnin=burnin, thin=1)
         g.sync()
         o.sweep()
-        assert_state_close(g.get_state(), o.get_state(), where=f"sweep {it}")
+        assert_state_close(g.get_state(), o.get_state(), keys=ALL_SLICE_KEYS, where=f"sweep {it}")
         c1, o1 = g.counters(), o.counters_dict()
-        for k in ("evals_eps", "evals_beta", "evals_nu", "slice_caps", "gamma_caps",
-                  "trunc_caps"):
+        for k in COUNTS:
             assert c1[k] - c0[k] == o1[k] - o0[k], (it, k)
     return g, o
 
@@ -96,6 +99,66 @@ def test_lockstep_zero_and_huge_counts():
     _lockstep(d, n_sweeps=3, burnin=0)
 
 
+# ------------------------------------------------------------------ all-slice variant
+@pytest.mark.parametrize("cfg,G", [(0, 1000), (1, 1537)])
+def test_all_slice_lockstep_sweeps(cfg, G):
+    """gamma_g, tau and sigma_l by slice updates (Section 4.2), through burn-in
+    (widths tuned after M_C) and past it."""
+    d = small_data(cfg, G=G)
+    g, o = _lockstep(d, n_sweeps=8, burnin=4, all_slice=1)
+    c = g.counters()
+    assert c["evals_gam"] > 0 and c["evals_hyp"] > 0 and c["gamma_caps"] == 0
+
+
+def test_all_slice_free_running_chain_matches_oracle():
+    d = small_data(0, G=2000)
+    g, o = make_pair(d, all_slice=1)
+    o.init_default()
+    burnin = 20
+    o.set_opts(burnin=burnin, tune_start=burnin // 2)
+    for it in range(1, 41):
+        g.run(1, burnin=burnin, thin=1)
+        o.sweep()
+        assert_state_close(g.get_state(), o.get_state(), keys=ALL_SLICE_KEYS,
+                           where=f"iteration {it}")
+    gm, om = g.moments(), o.moments_dict()
+    for k in ("mean_gam", "msq_gam", "mean_phi", "msq_phi"):
+        assert close(gm[k], om[k], 1e-9, 1e-12).all(), k
+    gc, oc = g.counters(), o.counters_dict()
+    for k in COUNTS:
+        assert gc[k] == oc[k], k
+
+
+def test_all_slice_paper_scale_lockstep_sweep():
+    """The paper-scale workload (N=16, G=40000, L=5) in the launch configuration
+    the benchmark times, one lockstep sweep during burn-in and one after."""
+    d = synthetic.make_config(1)
+    _lockstep(d, n_sweeps=2, burnin=1, all_slice=1)
+
+
+def test_slice_widths_round_trip_and_f32_refuses():
+    d = small_data(0, G=300)
+    g = fbs.Sampler(d["y"], d["X"], d["h"], d["priors"], all_slice=1)
+    st = g.get_state()
+    assert np.all(st["w_gam"] == 1.0) and np.all(st["w_hyp"] == 1.0)
+    assert np.all(st["waux_gam"] == 0.0) and np.all(st["waux_hyp"] == 0.0)
+    rng = np.random.default_rng(0)
+    want = {"w_gam": rng.uniform(0.1, 2, 300), "waux_gam": rng.uniform(0, 5, 300),
+            "w_hyp": rng.uniform(0.1, 2, 3), "waux_hyp": rng.uniform(0, 5, 3)}
+    g.set_state(it=7, **want)
+    st = g.get_state()
+    for k, v in want.items():
+        assert np.array_equal(st[k], v), k
+    assert st["it"] == 7
+    with pytest.raises(ValueError):
+        g.set_state(w_hyp=np.ones(5))
+    f = fbs.Sampler(d["y"], d["X"], d["h"], d["priors"], precision=fbs.FBS_F32)
+    assert "w_gam" not in f.get_state()
+    with pytest.raises(fbs.FbsError) as e:
+        f.set_state(w_gam=np.ones(300))
+    assert e.value.code == fbs.FBS_E_ARG
+
+
 # ------------------------------------------------------------------ free running
 def test_free_running_chain_matches_oracle():
     """Both chains run on their own from the same start; compare after every
@@ -116,14 +179,16 @@ def test_free_running_chain_matches_oracle():
         assert close(gm[k], om[k], 1e-9, 1e-12).all(), k
 
 
-def test_graph_segments_equal_direct_launches():
+@pytest.mark.parametrize("all_slice", [0, 1])
+def test_graph_segments_equal_direct_launches(all_slice):
     d = small_data(0, G=1500)
-    a = fbs.Sampler(d["y"], d["X"], d["h"], d["priors"], seed=5, graph_segment=7)
-    b = fbs.Sampler(d["y"], d["X"], d["h"], d["priors"], seed=5, graph_segment=1000)
+    kw = dict(seed=5, all_slice=all_slice)
+    a = fbs.Sampler(d["y"], d["X"], d["h"], d["priors"], graph_segment=7, **kw)
+    b = fbs.Sampler(d["y"], d["X"], d["h"], d["priors"], graph_segment=1000, **kw)
     a.run(23, burnin=10, thin=2)   # 3 graph segments + 2 direct sweeps
     b.run(23, burnin=10, thin=2)   # 23 direct sweeps
     sa, sb = a.get_state(), b.get_state()
-    for k in STATE_KEYS:
+    for k in ALL_SLICE_KEYS:
         assert np.array_equal(sa[k], sb[k]), k
     assert a.counters() == b.counters()
 

@@ -214,3 +214,30 @@ def test_learned_agrees_with_fp64_from_its_end_states():
     for b in betas:
         ess += np.array([oracle.ess(b[:, i, j]) for i in range(G) for j in range(L)]).reshape(G, L)
     _compare(learned, ref, ess, "learned FP32 vs FP64 from the learned end states")
+
+
+def test_all_slice_long_runs_agree_with_oracle(pool):
+    """The all-slice FP64 variant (gamma_g, tau, sigma_l by slice updates) targets
+    the same posterior as the exact draws: its GPU chains against the oracle's
+    chains of the exact-draw sampler, at configuration 0."""
+    cfg, G, orc_iters, gpu_iters = 0, 1000, 2400, 12000
+    orc, ess = _oracle_runs(pool, cfg, G, orc_iters)
+    d = synthetic.make_config(cfg, G=G)
+    gpu_burn, thin = gpu_iters // 6, 10
+    rows = (gpu_iters - gpu_burn) // thin
+    phis, betas = [], []
+    for c in range(N_GPU_CHAINS):
+        g = fbs.Sampler(d["y"], d["X"], d["h"], d["priors"], seed=303, chain=c, all_slice=1,
+                        trace_cap=rows, trace_beta=1)
+        g.set_state(it=0, **_truth_state(d))
+        g.run(gpu_iters, burnin=gpu_burn, thin=thin)
+        g.sync()
+        tr = g.trace(beta=True)
+        cnt = g.counters()
+        assert cnt["slice_caps"] == 0 and cnt["nonfinite"] == 0 and cnt["gamma_caps"] == 0
+        assert cnt["evals_gam"] > 0 and cnt["evals_hyp"] > 0
+        phis.append(tr["phi"])
+        betas.append(tr["beta"])
+        g.close()
+    _compare({"phi": _stats(phis), "beta": _stats(betas)}, orc, ess,
+             "cfg 0 all-slice FP64 vs oracle")

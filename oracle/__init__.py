@@ -52,6 +52,7 @@ class Model(C.Structure):
         ("y", C.POINTER(C.c_int32)), ("X", C.POINTER(C.c_double)), ("h", C.POINTER(C.c_double)),
         ("a", C.c_double), ("b", C.c_double), ("d", C.c_double),
         ("c", C.POINTER(C.c_double)), ("s", C.POINTER(C.c_double)),
+        ("theta_mean", C.POINTER(C.c_double)),
     ]
 
 
@@ -121,6 +122,8 @@ def _declare(lib):
     lib.orc_count_sums.argtypes = [pM, C.POINTER(i64)]
     lib.orc_ess.argtypes = [_PD, i64]
     lib.orc_ess.restype = d
+    lib.orc_step_psi.argtypes = [C.c_int, C.c_int, _PD, _PD, _PD, _PD, d, d, u64, i64, _PD,
+                                 C.POINTER(i64)]
     return lib
 
 
@@ -257,9 +260,10 @@ class Chain:
         L = self.L
         self.c = np.ascontiguousarray(np.broadcast_to(priors["c"], (L,)), np.float64)
         self.s = np.ascontiguousarray(np.broadcast_to(priors["s"], (L,)), np.float64)
+        self.theta_mean = None
         self.model = Model(self.N, self.G, L, self.y.ctypes.data_as(C.POINTER(C.c_int32)),
                            _pd(self.X), _pd(self.h), float(priors["a"]), float(priors["b"]),
-                           float(priors["d"]), _pd(self.c), _pd(self.s))
+                           float(priors["d"]), _pd(self.c), _pd(self.s), None)
         G, N = self.G, self.N
         self.eps = np.zeros((G, N))
         self.beta = np.zeros((G, L))
@@ -316,6 +320,15 @@ class Chain:
         for k, v in kw.items():
             setattr(self.opts, k, v)
 
+    def set_top_level(self, b, theta_mean):
+        """Priors that the three-level model's top level sets: tau ~ Gamma(a, rate
+        b) and theta_l ~ N(theta_mean_l, c_l^2)."""
+        if self.theta_mean is None:
+            self.theta_mean = np.zeros(self.L)
+            self.model.theta_mean = _pd(self.theta_mean)
+        self.theta_mean[...] = np.asarray(theta_mean, np.float64).reshape(self.L)
+        self.model.b = float(b)
+
     # steps -----------------------------------------------------------------
     def _step(self, name, it, *extra):
         getattr(self.lib, name)(C.byref(self.model), C.byref(self.state), C.byref(self.opts),
@@ -371,3 +384,71 @@ class Chain:
 
     def counters_dict(self):
         return {n: getattr(self.counters, n) for n, _ in Counters._fields_}
+
+
+# --------------------------------------------------------------------------- three levels
+class ThreeLevel:
+    """The three-level model (Section 2.3) over K datasets of the RNA-seq model:
+    dataset k keeps its own phi_k = (nu_k, tau_k, theta_k, sigma^2_k) and the
+    phi_k share psi = (b, m_1..m_L) through tau_k ~ Gamma(a_k, rate b) and
+    theta_kl ~ N(m_l, c_kl^2), with b ~ Gamma(a_b, rate b_b), m_l ~ N(0, e_l^2).
+
+    One sweep runs Algorithm 1 on every dataset given psi (a Chain each, with its
+    own seed and chain number), then draws psi given the phi_k (orc_step_psi).
+    datasets: dicts with y, X, h, priors, seed, chain; every X has the same L.
+    """
+
+    def __init__(self, datasets, e, a_b, b_b, psi_seed, psi0=None, burnin=0, lib=None):
+        self.lib = lib or load()
+        self.chains = [Chain(d["y"], d["X"], d["h"], d["priors"], seed=d["seed"],
+                             chain=d.get("chain", 0), burnin=burnin, lib=self.lib)
+                       for d in datasets]
+        Ls = {ch.L for ch in self.chains}
+        if len(Ls) != 1:
+            raise ValueError("every dataset of a three-level model needs the same L")
+        self.K, self.L = len(self.chains), Ls.pop()
+        self.e = np.ascontiguousarray(np.broadcast_to(e, (self.L,)), np.float64)
+        self.a_b, self.b_b, self.seed = float(a_b), float(b_b), int(psi_seed)
+        self.a = np.array([float(d["priors"]["a"]) for d in datasets])
+        self.c = np.ascontiguousarray(np.stack([ch.c for ch in self.chains]), np.float64)
+        self.psi = (np.asarray(psi0, np.float64).copy() if psi0 is not None
+                    else np.array([self.a_b / self.b_b] + [0.0] * self.L))
+        self.burnin = int(burnin)
+        self.it = 0
+        self.gamma_caps = C.c_int64(0)
+        for ch in self.chains:
+            ch.set_top_level(self.psi[0], self.psi[1:])
+
+    def init_default(self):
+        for ch in self.chains:
+            ch.init_default()
+        return self
+
+    def phis(self):
+        return np.stack([ch.phi for ch in self.chains])
+
+    def step_psi(self, it):
+        phi = np.ascontiguousarray(self.phis())
+        self.lib.orc_step_psi(self.K, self.L, _pd(phi), _pd(self.a), _pd(self.c), _pd(self.e),
+                              self.a_b, self.b_b, self.seed, int(it), _pd(self.psi),
+                              C.byref(self.gamma_caps))
+
+    def sweep(self):
+        self.it += 1
+        for ch in self.chains:
+            ch.set_top_level(self.psi[0], self.psi[1:])
+            ch.sweep()
+        self.step_psi(self.it)
+
+    def run(self, n_iter, thin=1):
+        """n_iter sweeps; returns the post-burn-in rows of every thin-th
+        iteration: psi [rows][1+L] and phi [rows][K][2L+2]."""
+        tp, tf = [], []
+        for _ in range(int(n_iter)):
+            self.sweep()
+            if self.it > self.burnin and (self.it - self.burnin) % thin == 0:
+                tp.append(self.psi.copy())
+                tf.append(self.phis())
+        P = 2 * self.L + 2
+        return {"psi": np.array(tp).reshape(-1, 1 + self.L),
+                "phi": np.array(tf).reshape(-1, self.K, P)}

@@ -512,7 +512,8 @@ void orc_step_theta(const orc_model* m, orc_state* st, const orc_opts* o, int64_
     for (int g = 0; g < m->G; ++g) B1 += st->beta[(size_t)g * L + l];
     double sig2 = st->phi[2 + L + l];
     double v = 1.0 / ((double)m->G / sig2 + 1.0 / (m->c[l] * m->c[l]));
-    double mean = v * B1 / sig2;
+    double mean = m->theta_mean ? v * (B1 / sig2 + m->theta_mean[l] / (m->c[l] * m->c[l]))
+                                : v * B1 / sig2;
     double z = orc_normal(o->seed, o->chain, ORC_STREAM_THETA, (uint32_t)l, (uint32_t)it, 0);
     st->phi[2 + l] = mean + sqrt(v) * z;
   }
@@ -549,6 +550,35 @@ void orc_step_sigma(const orc_model* m, orc_state* st, const orc_opts* o, int64_
         orc_trunc_invgamma(shape, 0.5 * S, upper, st->phi[2 + L + l], o->seed, o->chain,
                            ORC_STREAM_SIGMA, (uint32_t)l, (uint32_t)it, &cnt->gamma_caps,
                            &cnt->trunc_caps);
+  }
+}
+
+/* The top-level step of the three-level model: psi given the K datasets'
+ * hyperparameters.  The theta_kl are Normal(m_l, c_kl^2) terms of m_l and the
+ * tau_k Gamma(a_k, rate b) terms of b, so both updates are conjugate: a
+ * reduction over k to sum_k tau_k and sum_k a_k (b), and to sum_k theta_kl /
+ * c_kl^2 and sum_k 1/c_kl^2 (m_l). */
+void orc_step_psi(int K, int L, const double* phi, const double* a, const double* c,
+                  const double* e, double a_b, double b_b, uint64_t seed, int64_t it,
+                  double* psi, int64_t* gamma_caps) {
+  const int P = 2 * L + 2;
+  double sa = 0.0, st = 0.0;
+  for (int k = 0; k < K; ++k) {
+    sa += a[k];
+    st += phi[(size_t)k * P + 1];
+  }
+  double gv = orc_gamma(a_b + sa, seed, 0u, ORC_STREAM_PSI, 0u, (uint32_t)it, 0, gamma_caps);
+  psi[0] = gv / (b_b + st);
+  for (int l = 0; l < L; ++l) {
+    double prec = 0.0, s = 0.0;
+    for (int k = 0; k < K; ++k) {
+      double c2 = c[(size_t)k * L + l] * c[(size_t)k * L + l];
+      prec += 1.0 / c2;
+      s += phi[(size_t)k * P + 2 + l] / c2;
+    }
+    double w = 1.0 / (prec + 1.0 / (e[l] * e[l]));
+    double z = orc_normal(seed, 0u, ORC_STREAM_PSI, 1u + (uint32_t)l, (uint32_t)it, 0);
+    psi[1 + l] = w * s + sqrt(w) * z;
   }
 }
 

@@ -35,6 +35,7 @@ enum {
   ORC_STREAM_BETA = 5,
   ORC_STREAM_THETA = 6,
   ORC_STREAM_SIGMA = 7,
+  ORC_STREAM_PSI = 10,
   ORC_STREAM_TEST = 200
 };
 
@@ -47,6 +48,8 @@ typedef struct {
   double d;         /* nu ~ Uniform(0, d) */
   const double* c;  /* [L] theta_l ~ Normal(0, c_l^2) */
   const double* s;  /* [L] sigma_l ~ Uniform(0, s_l) */
+  const double* theta_mean; /* [L] prior mean of theta_l (NULL: 0); the three-level
+                               model sets it to the top-level m_l */
 } orc_model;
 
 typedef struct {
@@ -144,6 +147,19 @@ void orc_step_theta(const orc_model* m, orc_state* st, const orc_opts* o, int64_
                     orc_counters* cnt);
 void orc_step_sigma(const orc_model* m, orc_state* st, const orc_opts* o, int64_t it,
                     orc_counters* cnt);
+
+/* Top level of the three-level model (Section 2.3, Figure 2) for K datasets of
+ * this model whose hyperparameters share psi = (b, m_1..m_L):
+ *   tau_k ~ Gamma(a_k, rate b), theta_kl ~ N(m_l, c_kl^2),
+ *   b ~ Gamma(a_b, rate b_b), m_l ~ N(0, e_l^2).
+ * Given phi_1..phi_K (phi [K][2L+2]), draws
+ *   b ~ Gamma(a_b + sum_k a_k, rate b_b + sum_k tau_k),
+ *   m_l ~ N(w sum_k theta_kl / c_kl^2, w), w = 1 / (sum_k 1/c_kl^2 + 1/e_l^2)
+ * into psi [1+L] = (b, m_1..m_L).  a [K], c [K][L], e [L].  Random numbers:
+ * stream ORC_STREAM_PSI, chain 0, index 0 for b and 1+l for m_l. */
+void orc_step_psi(int K, int L, const double* phi, const double* a, const double* c,
+                  const double* e, double a_b, double b_b, uint64_t seed, int64_t it,
+                  double* psi, int64_t* gamma_caps);
 
 /* one full sweep (Algorithm 1 steps 1-7), then Welford moments when it > burnin */
 void orc_sweep(const orc_model* m, orc_state* st, const orc_opts* o, int64_t it,

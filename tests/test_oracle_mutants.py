@@ -11,6 +11,7 @@ from tests import test_oracle_all_slice as als
 from tests import test_oracle_conditionals as cond
 from tests import test_oracle_geweke as gew
 from tests import test_oracle_slice_moments as sm
+from tests import test_oracle_three_level as tl
 
 MUTANTS = {
     "eps prior term dropped": (
@@ -55,6 +56,18 @@ MUTANTS = {
     "sigma slice ignores the upper bound s_l": (
         "if (!(x > 0.0 && x < c->s)) return -INFINITY;", "if (!(x > 0.0)) return -INFINITY;",
         [als.test_sigma_slice_step_matches_posterior_with_truncation]),
+    "psi: rate of b misses b_b": (
+        "psi[0] = gv / (b_b + st);", "psi[0] = gv / st;",
+        [tl.test_psi_step_matches_posterior]),
+    "psi: shape of b counts datasets instead of summing a_k": (
+        "sa += a[k];", "sa += 1.0;",
+        [tl.test_psi_step_matches_posterior]),
+    "psi: prior precision 1/e^2 of m_l dropped": (
+        "double w = 1.0 / (prec + 1.0 / (e[l] * e[l]));", "double w = 1.0 / prec;",
+        [tl.test_psi_step_matches_posterior]),
+    "theta ignores the top-level prior mean": (
+        "v * (B1 / sig2 + m->theta_mean[l] / (m->c[l] * m->c[l]))", "v * (B1 / sig2)",
+        [tl.test_theta_and_tau_steps_use_the_top_level, tl.test_geweke_top_level_composition]),
     "stepping out never moves right": (
         "if (logu < f(hi, ctx)) hi += w; else break;", "break;",
         [lambda: sm.test_slice_normal_target(0.05)]),

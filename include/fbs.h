@@ -390,6 +390,41 @@ int fbs_batch_set_schedule(fbs_batch* b, int eps_block, int gb_block);
 int fbs_batch_autotune(fbs_batch* b, int sweeps, int64_t burnin, int* eps_block, int* gb_block,
                        double* ms_per_sweep);
 
+/* ---- Three-level model over a batch (Section 2.3, Figure 2) ---------------
+ *
+ * The batch's K = C datasets become the groups of a three-level model: dataset
+ * k keeps its own hyperparameters phi_k = (nu_k, tau_k, theta_k, sigma^2_k), and
+ * the phi_k share a top level psi = (b, m_1..m_L) through
+ *   tau_k ~ Gamma(a_k, rate b),  theta_kl ~ N(m_l, c_kl^2),
+ *   b ~ Gamma(a_b, rate b_b),    m_l ~ N(0, e_l^2)
+ * (a_k, c_kl, and the other priors are dataset k's fbs_priors; its b is then
+ * unused).  Every sweep runs the datasets' steps given psi, then draws psi
+ * given the phi_k: b ~ Gamma(a_b + sum_k a_k, rate b_b + sum_k tau_k) and
+ * m_l ~ N(w sum_k theta_kl / c_kl^2, w), w = 1/(sum_k 1/c_kl^2 + 1/e_l^2),
+ * reductions over k in dataset order on one warp; Philox stream 10 with
+ * key `seed`, chain word 0, index 0 for b and 1+l for m_l. */
+typedef struct {
+  double a_b, b_b;   /* b ~ Gamma(a_b, rate b_b); both finite and > 0 */
+  const double* e;   /* [L] host, m_l ~ N(0, e_l^2); finite and > 0 */
+  uint64_t seed;     /* Philox key of the psi draws */
+} fbs_top_prior;
+
+/* Switch the batch to the three-level model (pri != NULL) or back to K
+ * independent datasets (pri == NULL).  psi0: host [1+L] = (b, m_1..m_L)
+ * starting values, or NULL for (a_b / b_b, 0, .., 0).  Resets the psi moments
+ * and trace; the psi trace keeps up to opt.trace_cap rows (same thinning as
+ * the datasets' traces).  FBS_E_ARG if the datasets' L differ or a value is
+ * out of range.  Synchronous. */
+int fbs_batch_three_level(fbs_batch* b, const fbs_top_prior* pri, const double* psi0);
+
+/* Top-level state to host: any pointer may be NULL.  psi, mean, msq [1+L]
+ * (running mean and mean square over the post-burn-in iterations, count of
+ * them in *count); trace [max_rows][1+L] (*rows copied); *gamma_caps = b draws
+ * that ran out of attempts.  FBS_E_ARG if the batch is not three-level.
+ * Synchronous. */
+int fbs_batch_top_level(fbs_batch* b, double* psi, double* mean, double* msq, int64_t* count,
+                        int64_t max_rows, double* trace, int64_t* rows, int64_t* gamma_caps);
+
 void fbs_batch_free(fbs_batch* b);
 
 /* ---- One sweep without any allocation ------------------------------------

@@ -39,7 +39,7 @@ EXPORTED = ("fbs_default_options", "fbs_workspace_bytes", "fbs_init", "fbs_run",
             "fbs_proposal_params", "fbs_proposal_stats", "fbs_proposal_loss_grad",
             "fbs_proposal_outputs", "fbs_proposal_step", "fbs_set_contrasts",
             "fbs_contrast_probs", "fbs_rhat", "fbs_proposal_kinds", "fbs_get_slice_widths",
-            "fbs_set_slice_widths")
+            "fbs_set_slice_widths", "fbs_batch_three_level", "fbs_batch_top_level")
 NOALLOC_MAX_GENES = 2048 * 128
 
 
@@ -63,6 +63,10 @@ class Options(C.Structure):
 
 _PD = C.POINTER(C.c_double)
 _PI64 = C.POINTER(C.c_int64)
+
+
+class TopPrior(C.Structure):
+    _fields_ = [("a_b", C.c_double), ("b_b", C.c_double), ("e", _PD), ("seed", C.c_uint64)]
 _lib = None
 
 
@@ -123,6 +127,8 @@ def load_library(path: str = LIB_PATH):
     lib.fbs_batch_autotune.argtypes = [vp, C.c_int, i64, C.POINTER(C.c_int), C.POINTER(C.c_int),
                                        C.POINTER(C.c_double)]
     lib.fbs_batch_free.argtypes = [vp]
+    lib.fbs_batch_three_level.argtypes = [vp, C.POINTER(TopPrior), _PD]
+    lib.fbs_batch_top_level.argtypes = [vp, _PD, _PD, _PD, _PI64, i64, _PD, _PI64, _PI64]
     lib.fbs_batch_free.restype = None
     _PF = C.POINTER(C.c_float)
     lib.fbs_proposal_param_count.argtypes = [C.c_int]
@@ -559,6 +565,34 @@ class BatchSampler:
 
     def set_schedule(self, eps_block, gb_block):
         _check(self.lib.fbs_batch_set_schedule(self.b, int(eps_block), int(gb_block)))
+
+    def three_level(self, e, a_b, b_b, seed, psi0=None):
+        """Make the datasets the groups of the three-level model: their phi_k share
+        psi = (b, m_1..m_L) with tau_k ~ Gamma(a_k, rate b), theta_kl ~ N(m_l,
+        c_kl^2), b ~ Gamma(a_b, rate b_b), m_l ~ N(0, e_l^2).  e=None switches it off."""
+        if e is None:
+            _check(self.lib.fbs_batch_three_level(self.b, None, None))
+            self.L_top = None
+            return
+        L = self.shapes[0][2]
+        self._top_e = np.ascontiguousarray(np.broadcast_to(e, (L,)), np.float64)
+        pri = TopPrior(float(a_b), float(b_b), _pd(self._top_e), int(seed))
+        p0 = None if psi0 is None else np.ascontiguousarray(psi0, np.float64).reshape(L + 1)
+        _check(self.lib.fbs_batch_three_level(self.b, C.byref(pri), _pd(p0)))
+        self.L_top = L
+
+    def top_level(self, max_rows=None):
+        """psi = (b, m_1..m_L), its running mean / mean square and count, its
+        thinned trace and the count of b draws that ran out of attempts."""
+        n = self.L_top + 1
+        cap = int(self.options.trace_cap) if max_rows is None else int(max_rows)
+        psi, mean, msq = np.empty(n), np.empty(n), np.empty(n)
+        tr = np.empty((max(cap, 0), n))
+        cnt, rows, caps = C.c_int64(), C.c_int64(), C.c_int64()
+        _check(self.lib.fbs_batch_top_level(self.b, _pd(psi), _pd(mean), _pd(msq), C.byref(cnt),
+                                            cap, _pd(tr), C.byref(rows), C.byref(caps)))
+        return {"psi": psi, "mean": mean, "msq": msq, "count": cnt.value,
+                "trace": tr[:rows.value], "gamma_caps": caps.value}
 
     def autotune(self, sweeps=5, burnin=0):
         e, g, ms = C.c_int(), C.c_int(), C.c_double()

@@ -1623,6 +1623,9 @@ struct fbs_batch {
   cudaStream_t user = nullptr, s = nullptr, s2 = nullptr;
   cudaEvent_t ev_in = nullptr, ev_out = nullptr, ev_g = nullptr, ev_h = nullptr;
   cudaGraphExec_t exec = nullptr;
+  TopLevel* d_top = nullptr;       // three-level model: the top level, or null
+  double* d_top_trace = nullptr;   // [trace_cap][1+L]
+  bool three_level = false;
 };
 
 namespace {
@@ -1642,6 +1645,8 @@ void batch_release(fbs_batch* b) {
   cudaFree(b->d_nblk);
   cudaFree(b->d_eps_tab);
   cudaFree(b->d_gb_tab);
+  cudaFree(b->d_top);
+  cudaFree(b->d_top_trace);
   if (b->ev_in) cudaEventDestroy(b->ev_in);
   if (b->ev_out) cudaEventDestroy(b->ev_out);
   if (b->ev_g) cudaEventDestroy(b->ev_g);
@@ -1696,6 +1701,8 @@ cudaError_t batch_sweeps_direct(fbs_batch* b, int64_t n_iter) {
       e = launch_gb_f32_batch(b->d_mc, b->d_pf, b->d_gb_tab, b->n_gb, b->gb_block, b->max_N,
                               (int)i, b->s);
     if (e == cudaSuccess) e = launch_hyper_batch(b->d_mc, b->d_pf, b->d_nblk, b->C, b->s);
+    if (e == cudaSuccess && b->three_level)
+      e = launch_top_level(b->d_mc, b->d_pf, b->C, b->d_top, b->d_top_trace, b->s);
   }
   return e;
 }
@@ -1713,6 +1720,12 @@ cudaError_t batch_capture(fbs_batch* b) {
     if ((e = cudaEventRecord(b->ev_g, b->s)) != cudaSuccess) return e;
     if ((e = cudaStreamWaitEvent(b->s2, b->ev_g, 0)) != cudaSuccess) return e;
     if ((e = launch_hyper_batch(b->d_mc, b->d_pf, b->d_nblk, b->C, b->s2)) != cudaSuccess)
+      return e;
+    // the top level of sweep i follows the datasets' hyperparameters on the same
+    // stream; the next hyper launch reads it
+    if (b->three_level &&
+        (e = launch_top_level(b->d_mc, b->d_pf, b->C, b->d_top, b->d_top_trace, b->s2)) !=
+            cudaSuccess)
       return e;
     if ((e = cudaEventRecord(b->ev_h, b->s2)) != cudaSuccess) return e;
   }
@@ -1953,6 +1966,82 @@ int fbs_batch_autotune(fbs_batch* b, int sweeps, int64_t burnin, int* eps_block,
   if (eps_block) *eps_block = be;
   if (gb_block) *gb_block = bg;
   if (ms_per_sweep) *ms_per_sweep = best;
+  return FBS_OK;
+}
+
+int fbs_batch_three_level(fbs_batch* b, const fbs_top_prior* pri, const double* psi0) {
+  if (!b) return fail(FBS_E_ARG, "batch is NULL");
+  const int L = b->mcs[0].L;
+  auto pos = [](double v) { return isfinite(v) && v > 0.0; };
+  if (pri) {
+    for (int c = 1; c < b->C; ++c)
+      if (b->mcs[c].L != L) return fail(FBS_E_ARG, "a three-level model needs the same L in every dataset");
+    if (!pos(pri->a_b) || !pos(pri->b_b)) return fail(FBS_E_ARG, "a_b and b_b must be finite and > 0");
+    if (!pri->e) return fail(FBS_E_ARG, "e is NULL");
+    for (int l = 0; l < L; ++l)
+      if (!pos(pri->e[l])) return fail(FBS_E_ARG, "e_l must be finite and > 0");
+    if (psi0) {
+      if (!pos(psi0[0])) return fail(FBS_E_ARG, "psi0[0] (b) must be finite and > 0");
+      for (int l = 0; l < L; ++l)
+        if (!isfinite(psi0[1 + l])) return fail(FBS_E_ARG, "psi0 has a non-finite m_l");
+    }
+  }
+  FBS_CUDA(cudaStreamSynchronize(b->s));
+  if (pri) {
+    const long long cap = b->opt.trace_cap;
+    if (!b->d_top) FBS_CUDA(cudaMalloc((void**)&b->d_top, sizeof(TopLevel)));
+    if (cap > 0 && !b->d_top_trace)
+      FBS_CUDA(cudaMalloc((void**)&b->d_top_trace, (size_t)cap * (L + 1) * sizeof(double)));
+    TopLevel t;
+    memset(&t, 0, sizeof(t));
+    t.psi[0] = psi0 ? psi0[0] : pri->a_b / pri->b_b;
+    for (int l = 0; l < L; ++l) {
+      t.psi[1 + l] = psi0 ? psi0[1 + l] : 0.0;
+      t.e2[l] = pri->e[l] * pri->e[l];
+    }
+    t.trace_cap = cap > 0 ? cap : 0;
+    t.a_b = pri->a_b;
+    t.b_b = pri->b_b;
+    t.seed_lo = (uint32_t)(pri->seed & 0xffffffffu);
+    t.seed_hi = (uint32_t)(pri->seed >> 32);
+    t.L = L;
+    t.K = b->C;
+    FBS_CUDA(cudaMemcpyAsync(b->d_top, &t, sizeof(t), cudaMemcpyHostToDevice, b->s));
+  }
+  b->three_level = pri != nullptr;
+  double* d_psi = pri ? reinterpret_cast<double*>(reinterpret_cast<char*>(b->d_top) +
+                                                   offsetof(TopLevel, psi))
+                     : nullptr;
+  for (int c = 0; c < b->C; ++c) b->pfs[c].psi = d_psi;
+  FBS_CUDA(cudaMemcpyAsync(b->d_pf, b->pfs.data(), sizeof(DevPtrsF32) * b->C,
+                           cudaMemcpyHostToDevice, b->s));
+  FBS_CUDA(cudaStreamSynchronize(b->s));
+  if (b->exec) {  // the captured segment changes
+    cudaGraphExecDestroy(b->exec);
+    b->exec = nullptr;
+  }
+  return FBS_OK;
+}
+
+int fbs_batch_top_level(fbs_batch* b, double* psi, double* mean, double* msq, int64_t* count,
+                        int64_t max_rows, double* trace, int64_t* rows, int64_t* gamma_caps) {
+  if (!b) return fail(FBS_E_ARG, "batch is NULL");
+  if (!b->three_level) return fail(FBS_E_ARG, "the batch is not a three-level model");
+  if (max_rows < 0) return fail(FBS_E_ARG, "max_rows must be >= 0");
+  FBS_CUDA(cudaStreamSynchronize(b->s));
+  TopLevel t;
+  FBS_CUDA(cudaMemcpy(&t, b->d_top, sizeof(t), cudaMemcpyDeviceToHost));
+  const int n = t.L + 1;
+  if (psi) memcpy(psi, t.psi, n * sizeof(double));
+  if (mean) memcpy(mean, t.m_psi, n * sizeof(double));
+  if (msq) memcpy(msq, t.q_psi, n * sizeof(double));
+  if (count) *count = t.n_mom;
+  if (gamma_caps) *gamma_caps = (int64_t)t.gamma_caps;
+  const long long r = t.trace_rows < max_rows ? t.trace_rows : max_rows;
+  if (trace && r > 0)
+    FBS_CUDA(cudaMemcpy(trace, b->d_top_trace, (size_t)r * n * sizeof(double),
+                        cudaMemcpyDeviceToHost));
+  if (rows) *rows = trace ? r : 0;
   return FBS_OK;
 }
 

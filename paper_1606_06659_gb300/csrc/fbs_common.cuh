@@ -30,6 +30,7 @@ enum : uint32_t {
   kStreamSigma = 7,
   kStreamMH = 8,      // learned-proposal move of beta_g
   kStreamTrain = 9,   // minibatch sampling when training the proposal
+  kStreamPsi = 10,    // top level of the three-level model
 };
 
 // Proposals of the eta-preserving move: the network's, or centred on the prior.
@@ -99,6 +100,20 @@ struct Hyper {
   double w_hyp[kMaxL + 1], waux_hyp[kMaxL + 1];
 };
 
+// Top level of the three-level model (Section 2.3) over a batch of K datasets,
+// in device memory: psi = (b, m_1..m_L) with tau_k ~ Gamma(a_k, rate b) and
+// theta_kl ~ N(m_l, c_kl^2); b ~ Gamma(a_b, rate b_b), m_l ~ N(0, e_l^2).
+struct TopLevel {
+  double psi[kMaxL + 1];
+  double m_psi[kMaxL + 1], q_psi[kMaxL + 1];  // running mean / mean square
+  long long n_mom, trace_rows, trace_cap;
+  unsigned long long gamma_caps;             // b draws that ran out of attempts
+  double a_b, b_b;
+  double e2[kMaxL];                          // e_l^2
+  uint32_t seed_lo, seed_hi;
+  int L, K;
+};
+
 // Device pointers of one chain.
 struct DevPtrs {
   const int32_t* y;   // [N][G]
@@ -160,6 +175,7 @@ struct DevPtrsF32 {
   unsigned long long* counters;
   const Contrasts* con;  // null: no contrast probabilities
   unsigned* con_count;   // [n][G]
+  const double* psi;     // null, or the batch's TopLevel::psi (three-level model)
 };
 
 // Flag bits in Hyper::flags.

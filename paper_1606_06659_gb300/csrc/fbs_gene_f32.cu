@@ -710,7 +710,64 @@ __global__ void __launch_bounds__(kHyperThreads) k_hyper_batch(const ModelConst*
                                                                const int* __restrict__ nblk) {
   const int c = blockIdx.x;
   const DevPtrsF32& p = ps[c];
-  hyper_body(mcs[c], p.partial, p.hyp, p.trace_phi, p.counters, nblk[c]);
+  hyper_body(mcs[c], p.partial, p.hyp, p.trace_phi, p.counters, nblk[c], p.psi);
+}
+
+// Top level of the three-level model, one warp, after the datasets' hyper
+// steps of the same sweep: lane 0 draws b ~ Gamma(a_b + sum_k a_k, rate b_b +
+// sum_k tau_k), lane 1+l draws m_l ~ N(w sum_k theta_kl / c_kl^2, w) with
+// w = 1 / (sum_k 1/c_kl^2 + 1/e_l^2); the sums over k run in dataset order.
+// Moments and trace follow dataset 0's iteration, burn-in and thinning.
+__global__ void __launch_bounds__(32) k_top_level(const ModelConst* __restrict__ mcs,
+                                                  const DevPtrsF32* __restrict__ ps, int C,
+                                                  TopLevel* __restrict__ top,
+                                                  double* __restrict__ trace) {
+  const int lane = threadIdx.x;
+  const int L = top->L;
+  const Hyper* h0 = ps[0].hyp;
+  const long long it = h0->it;
+  const uint32_t it32 = (uint32_t)it;
+  double x = 0.0;
+  if (lane == 0) {
+    double sa = 0.0, st = 0.0;
+    for (int k = 0; k < C; ++k) {
+      sa += mcs[k].a;
+      st += ps[k].hyp->phi[1];
+    }
+    Rng r(top->seed_lo, top->seed_hi, 0u, kStreamPsi, 0u, it32);
+    bool cap = false;
+    x = gamma_mt(top->a_b + sa, r, 0, &cap) / (top->b_b + st);
+    if (cap) atomicAdd(&top->gamma_caps, 1ull);
+  } else if (lane <= L) {
+    const int l = lane - 1;
+    double prec = 0.0, s = 0.0;
+    for (int k = 0; k < C; ++k) {
+      const double c2 = mcs[k].c2[l];
+      prec += 1.0 / c2;
+      s += ps[k].hyp->phi[2 + l] / c2;
+    }
+    const double w = 1.0 / (prec + 1.0 / top->e2[l]);
+    Rng r(top->seed_lo, top->seed_hi, 0u, kStreamPsi, (uint32_t)lane, it32);
+    x = __dadd_rn(__dmul_rn(w, s), __dmul_rn(sqrt(w), normal_bm(r, 0)));
+  }
+  const bool mom = it > h0->burnin;
+  const bool tr = mom && ((it - h0->burnin) % h0->thin == 0) && top->trace_rows < top->trace_cap &&
+                  trace != nullptr;
+  if (lane <= L) {
+    top->psi[lane] = x;
+    if (mom) {
+      const double inv_k = 1.0 / (double)(top->n_mom + 1);
+      const double m = top->m_psi[lane], q = top->q_psi[lane];
+      top->m_psi[lane] = m + (x - m) * inv_k;
+      top->q_psi[lane] = q + (x * x - q) * inv_k;
+    }
+    if (tr) trace[(size_t)top->trace_rows * (L + 1) + lane] = x;
+  }
+  __syncwarp();
+  if (lane == 0) {
+    if (mom) top->n_mom += 1;
+    if (tr) top->trace_rows += 1;
+  }
 }
 
 __global__ void k_seg_begin_batch(const DevPtrsF32* __restrict__ ps, int C) {
@@ -756,6 +813,12 @@ cudaError_t launch_gb_f32_batch(const ModelConst* mcs, const DevPtrsF32* ps, con
 cudaError_t launch_hyper_batch(const ModelConst* mcs, const DevPtrsF32* ps, const int* nblk,
                                int C, cudaStream_t s) {
   k_hyper_batch<<<C, kHyperThreads, 0, s>>>(mcs, ps, nblk);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_top_level(const ModelConst* mcs, const DevPtrsF32* ps, int C, TopLevel* top,
+                             double* trace, cudaStream_t s) {
+  k_top_level<<<1, 32, 0, s>>>(mcs, ps, C, top, trace);
   return cudaGetLastError();
 }
 

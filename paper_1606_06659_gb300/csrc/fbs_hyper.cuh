@@ -56,10 +56,12 @@ struct SigDensity {
 constexpr int kHyperThreads = 64;
 
 // Steps 3, 4, 6, 7 for one chain, executed by one block of kHyperThreads threads:
-// the chain's `nblk` per-block partial sums are folded in a fixed order.
+// the chain's `nblk` per-block partial sums are folded in a fixed order.  psi:
+// null, or the top level (b, m_1..m_L) of the three-level model, which replaces
+// the rate b of the tau prior and the zero mean of the theta_l priors.
 __device__ __forceinline__ void hyper_body(const ModelConst& mc, const double* partial, Hyper* hy,
                                            double* trace_phi, unsigned long long* counters,
-                                           int nblk) {
+                                           int nblk, const double* psi = nullptr) {
   __shared__ double red[kHyperThreads / 32][kNumPart];
   __shared__ double tot[kNumPart];
   __shared__ double phi_new[kMaxP];
@@ -111,7 +113,7 @@ __device__ __forceinline__ void hyper_body(const ModelConst& mc, const double* p
     const double nu = s.x;
     Rng rt(mc.seed_lo, mc.seed_hi, mc.chain, kStreamTau, 0u, it32);
     const double shape = mc.a + 0.5 * G * nu;
-    const double rate = mc.b + 0.5 * nu * S2;
+    const double rate = (psi ? psi[0] : mc.b) + 0.5 * nu * S2;
     SliceResult st;
     if (mc.all_slice)  // step 4 by a slice update of the Gamma conditional, on warp 0
       st = slice_update_warp(sh.phi[1], sh.w_hyp[0], TauDensity{shape, rate}, rt, mc.K,
@@ -162,7 +164,7 @@ __device__ __forceinline__ void hyper_body(const ModelConst& mc, const double* p
     const double B1s = tot[2 + l], B2s = tot[2 + kMaxL + l];
     const double B1 = B1s + G * th_old;
     const double v = 1.0 / (G / sig2 + 1.0 / mc.c2[l]);
-    const double mean = v * B1 / sig2;
+    const double mean = psi ? v * (B1 / sig2 + psi[1 + l] / mc.c2[l]) : v * B1 / sig2;
     Rng r(mc.seed_lo, mc.seed_hi, mc.chain, kStreamTheta, (uint32_t)l, it32);
     const double th = mean + sqrt(v) * normal_bm(r, 0);
     // step 7: sigma_l^2 ~ IG((G-1)/2, S/2) on (0, s_l^2), S = sum (beta - theta_new)^2

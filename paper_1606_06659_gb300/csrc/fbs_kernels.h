@@ -97,6 +97,8 @@ cudaError_t launch_gb_f32_batch(const ModelConst* mcs, const DevPtrsF32* ps, con
 cudaError_t launch_hyper_batch(const ModelConst* mcs, const DevPtrsF32* ps, const int* nblk,
                                int C, cudaStream_t s);
 cudaError_t launch_seg_begin_batch(const DevPtrsF32* ps, int C, cudaStream_t s);
+cudaError_t launch_top_level(const ModelConst* mcs, const DevPtrsF32* ps, int C, TopLevel* top,
+                             double* trace, cudaStream_t s);
 cudaError_t launch_set_run_batch(const DevPtrsF32* ps, int C, long long burnin,
                                  long long tune_start, long long thin, cudaStream_t s);
 constexpr int kEpsCounterCopiesHost = kCounterCopies;

@@ -572,19 +572,17 @@ class BatchSampler:
         c_kl^2), b ~ Gamma(a_b, rate b_b), m_l ~ N(0, e_l^2).  e=None switches it off."""
         if e is None:
             _check(self.lib.fbs_batch_three_level(self.b, None, None))
-            self.L_top = None
             return
         L = self.shapes[0][2]
         self._top_e = np.ascontiguousarray(np.broadcast_to(e, (L,)), np.float64)
         pri = TopPrior(float(a_b), float(b_b), _pd(self._top_e), int(seed))
         p0 = None if psi0 is None else np.ascontiguousarray(psi0, np.float64).reshape(L + 1)
         _check(self.lib.fbs_batch_three_level(self.b, C.byref(pri), _pd(p0)))
-        self.L_top = L
 
     def top_level(self, max_rows=None):
         """psi = (b, m_1..m_L), its running mean / mean square and count, its
         thinned trace and the count of b draws that ran out of attempts."""
-        n = self.L_top + 1
+        n = self.shapes[0][2] + 1   # the library refuses a batch that is not three-level
         cap = int(self.options.trace_cap) if max_rows is None else int(max_rows)
         psi, mean, msq = np.empty(n), np.empty(n), np.empty(n)
         tr = np.empty((max(cap, 0), n))

@@ -72,7 +72,7 @@ def parse():
     ap.add_argument("--no-ess", action="store_true", help="skip the 20000-iteration ESS jobs")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-seconds", type=float, default=12.0)
-    ap.add_argument("--train-epochs", type=int, default=15,
+    ap.add_argument("--train-epochs", type=int, default=20,
                     help="training epochs of the learned proposal (2e6 pairs per epoch)")
     ap.add_argument("--tune-sweeps", type=int, default=2000,
                     help="burn-in sweeps that tune the slice widths before the timed steps")
@@ -293,7 +293,7 @@ FORM_TEXT = {
                "before the slice updates of beta_g)",
 }
 PAIR_SWEEPS = 50          # x thin 2 x G = 2e6 training pairs at G = 40000
-TRAIN = {"epochs": 15, "batch": 8192, "lr": 3e-3}
+TRAIN = {"epochs": 20, "batch": 8192, "lr": 3e-3}
 CALIBRATE_SWEEPS = 100
 # Calibration threshold of the learned move.  The headline form adds the move to
 # the slice updates of beta_g (mode 1), so the slice sampler always runs and the

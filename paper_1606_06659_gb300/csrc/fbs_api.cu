@@ -1101,67 +1101,27 @@ void learned_apply(fbs_handle* h, int mode, int mh_all) {
 
 // Scratch of one training step for batch size B.
 struct TrainBufs {
-  float *fb, *yb, *z1, *h1, *z2, *h2, *o, *dO, *dh, *dz2, *dz1, *grad, *loss;
+  float *fb, *yb, *part, *grad, *loss;
 };
 
+// Gradient and summed loss of the minibatch in t.fb / t.yb at params.
 int mlp_step(const float* params, int L, int B, TrainBufs& t, cudaStream_t s) {
-  const int H = kMlpHidden, F = 4 * L + 1, K = L + L * (L + 1) / 2;
-  const float* W1 = params;
-  const float* b1 = W1 + H * F;
-  const float* W2 = b1 + H;
-  const float* b2 = W2 + H * H;
-  const float* W3 = b2 + H;
-  const float* b3 = W3 + K * H;
-  float* gW1 = t.grad;
-  float* gb1 = gW1 + H * F;
-  float* gW2 = gb1 + H;
-  float* gb2 = gW2 + H * H;
-  float* gW3 = gb2 + H;
-  float* gb3 = gW3 + K * H;
-  const int split = B >= 2048 ? 32 : 1;
-  // forward
-  FBS_CUDA(launch_gemm(B, H, F, t.fb, F, 1, W1, 1, F, t.z1, H, 1, 0, s));
-  FBS_CUDA(launch_bias_gelu(t.z1, t.h1, b1, B, H, 1, s));
-  FBS_CUDA(launch_gemm(B, H, H, t.h1, H, 1, W2, 1, H, t.z2, H, 1, 0, s));
-  FBS_CUDA(launch_bias_gelu(t.z2, t.h2, b2, B, H, 1, s));
-  FBS_CUDA(launch_gemm(B, K, H, t.h2, H, 1, W3, 1, H, t.o, K, 1, 0, s));
-  FBS_CUDA(launch_bias_gelu(t.o, nullptr, b3, B, K, 0, s));
-  FBS_CUDA(cudaMemsetAsync(t.loss, 0, sizeof(float), s));
-  FBS_CUDA(launch_nll_head(t.o, t.yb, B, L, t.dO, t.loss, s));
-  // backward
-  FBS_CUDA(cudaMemsetAsync(t.grad, 0, sizeof(float) * mlp_param_count(L), s));
-  FBS_CUDA(launch_gemm(K, H, B, t.dO, 1, K, t.h2, H, 1, gW3, H, split, 0, s));
-  FBS_CUDA(launch_colsum(t.dO, B, K, gb3, s));
-  FBS_CUDA(launch_gemm(B, H, K, t.dO, K, 1, W3, H, 1, t.dh, H, 1, 0, s));
-  FBS_CUDA(launch_gelu_back(t.z2, t.dh, t.dz2, (long long)B * H, s));
-  FBS_CUDA(launch_gemm(H, H, B, t.dz2, 1, H, t.h1, H, 1, gW2, H, split, 0, s));
-  FBS_CUDA(launch_colsum(t.dz2, B, H, gb2, s));
-  FBS_CUDA(launch_gemm(B, H, H, t.dz2, H, 1, W2, H, 1, t.dh, H, 1, 0, s));
-  FBS_CUDA(launch_gelu_back(t.z1, t.dh, t.dz1, (long long)B * H, s));
-  FBS_CUDA(launch_gemm(H, F, B, t.dz1, 1, H, t.fb, F, 1, gW1, F, split, 0, s));
-  FBS_CUDA(launch_colsum(t.dz1, B, H, gb1, s));
+  FBS_CUDA(launch_mlp_grad(params, L, B, t.fb, t.yb, t.part, t.grad, t.loss, s));
   return FBS_OK;
 }
 
 int train_bufs_alloc(TrainBufs& t, int L, int B) {
-  const int H = kMlpHidden, F = 4 * L + 1, K = L + L * (L + 1) / 2;
+  const int F = 4 * L + 1, np = mlp_param_count(L);
   memset(&t, 0, sizeof(t));
-  const size_t n = (size_t)B * (F + L + 4 * H + 2 * K + 3 * H) + mlp_param_count(L) + 1;
+  const size_t n = (size_t)B * (F + L) + (size_t)train_blocks(B) * (np + 1) + np + 1;
+  FBS_CUDA(prepare_train_kernel(L));
   float* base = nullptr;
   FBS_CUDA(cudaMalloc((void**)&base, n * sizeof(float)));
   float* q = base;
   t.fb = q; q += (size_t)B * F;
   t.yb = q; q += (size_t)B * L;
-  t.z1 = q; q += (size_t)B * H;
-  t.h1 = q; q += (size_t)B * H;
-  t.z2 = q; q += (size_t)B * H;
-  t.h2 = q; q += (size_t)B * H;
-  t.o = q; q += (size_t)B * K;
-  t.dO = q; q += (size_t)B * K;
-  t.dh = q; q += (size_t)B * H;
-  t.dz2 = q; q += (size_t)B * H;
-  t.dz1 = q; q += (size_t)B * H;
-  t.grad = q; q += mlp_param_count(L);
+  t.part = q; q += (size_t)train_blocks(B) * (np + 1);
+  t.grad = q; q += np;
   t.loss = q;
   return FBS_OK;
 }
@@ -1245,17 +1205,13 @@ int fbs_proposal_train(fbs_handle* h, int epochs, int batch, double lr, uint64_t
   if (e == cudaSuccess) e = cudaMalloc((void**)&d_ctl, sizeof(TrainCtl));
   if (e == cudaSuccess)
     e = cudaMemcpyAsync(d_ctl, &ctl, sizeof(ctl), cudaMemcpyHostToDevice, h->s);
-  if (e == cudaSuccess) e = launch_train_begin(d_ctl, h->s);
   if (e == cudaSuccess) {
     cudaGraph_t graph = nullptr;
     e = cudaStreamBeginCapture(h->s, cudaStreamCaptureModeThreadLocal);
     if (e == cudaSuccess) {
-      cudaError_t ce = launch_gather_rows_ctl(ls->pair_feat, ls->pair_beta, ls->pairs, F, L, batch,
-                                              seed, d_ctl, ls->stats, t.fb, t.yb, h->s);
-      if (ce == cudaSuccess) rc = mlp_step(ls->params, L, batch, t, h->s);
-      if (ce == cudaSuccess && rc == FBS_OK)
-        ce = launch_adam_ctl(ls->params, t.grad, ls->adam_m, ls->adam_v, ls->np, d_ctl, h->s);
-      if (ce == cudaSuccess && rc == FBS_OK) ce = launch_train_tick(d_ctl, t.loss, batch, h->s);
+      cudaError_t ce = launch_train_step(ls->params, L, batch, ls->pair_feat, ls->pair_beta,
+                                         ls->pairs, seed, d_ctl, ls->stats, t.part, t.grad,
+                                         t.loss, ls->adam_m, ls->adam_v, h->s);
       e = cudaStreamEndCapture(h->s, &graph);
       if (e == cudaSuccess) e = ce;
     }

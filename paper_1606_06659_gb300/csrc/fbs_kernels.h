@@ -58,15 +58,15 @@ struct TrainCtl {
   unsigned long long t;      // Adam steps done before the current step
   long long k, steps, epoch_steps;  // step within the call, steps of the call, of an epoch
   double lr, loss_sum;       // base step size; loss summed over the last epoch's steps
-  float b1, b2, c1, c2, lr_t;
+  float b1, b2;
+  unsigned int done;         // blocks of the current step's reduction that finished
 };
-cudaError_t launch_train_begin(TrainCtl* c, cudaStream_t s);
-cudaError_t launch_train_tick(TrainCtl* c, const float* loss, int B, cudaStream_t s);
-cudaError_t launch_adam_ctl(float* w, const float* g, float* m, float* v, int n,
-                            const TrainCtl* c, cudaStream_t s);
-cudaError_t launch_gather_rows_ctl(const float* feat, const float* beta, long long M, int F,
-                                   int L, int Bsz, uint64_t seed, const TrainCtl* c,
-                                   const float* st, float* fb, float* yb, cudaStream_t s);
+// One training step on the device: minibatch drawn for step t + 1, forward and
+// backward, gradient reduction, Adam, control-block update (two launches).
+cudaError_t launch_train_step(float* params, int L, int Bsz, const float* feat, const float* beta,
+                              long long M, uint64_t seed, TrainCtl* ctl, const float* st,
+                              float* part, float* grad, float* loss, float* adam_m, float* adam_v,
+                              cudaStream_t s);
 int mlp_param_count(int L);
 cudaError_t launch_proposal_f32(const ModelConst& mc, const DevPtrsF32& p, const void* w_bf16,
                                 float* out, cudaStream_t s);
@@ -75,16 +75,13 @@ cudaError_t launch_collect_f32(const ModelConst& mc, const DevPtrsF32& p, float*
 cudaError_t launch_col_stats(const float* feat, const float* beta, long long M, int F, int L,
                              float* st, cudaStream_t s);
 cudaError_t launch_fold(float* params, const float* st, int L, int to_raw, cudaStream_t s);
-cudaError_t launch_gemm(int M, int Nn, int Kk, const float* A, long long sai, long long sak,
-                        const float* B, long long sbk, long long sbj, float* C, long long ldc,
-                        int split_k, int accumulate, cudaStream_t s);
-cudaError_t launch_bias_gelu(float* Z, float* H, const float* b, int rows, int cols, int act,
-                             cudaStream_t s);
-cudaError_t launch_gelu_back(const float* Z, const float* dH, float* dZ, long long n,
-                             cudaStream_t s);
-cudaError_t launch_nll_head(const float* O, const float* Y, int Bsz, int L, float* dO,
-                            float* loss_sum, cudaStream_t s);
-cudaError_t launch_colsum(const float* D, int rows, int cols, float* g, cudaStream_t s);
+// one training step's gradient: fused forward/backward per block of rows, then
+// the blocks' partial sums in block order (part: [train_blocks(Bsz)][np + 1])
+size_t train_smem_bytes(int L);
+int train_blocks(int Bsz);
+cudaError_t prepare_train_kernel(int L);
+cudaError_t launch_mlp_grad(const float* params, int L, int Bsz, const float* fb, const float* yb,
+                            float* part, float* grad, float* loss, cudaStream_t s);
 size_t tc_image_bytes(int L);
 cudaError_t launch_pack_image(const float* params, void* img, int L, cudaStream_t s);
 

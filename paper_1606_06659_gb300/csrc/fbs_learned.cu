@@ -630,172 +630,319 @@ __global__ void k_fold(float* __restrict__ w, const float* __restrict__ st, int 
   }
 }
 
-// C[i][j] (+)= sum_k A(i,k) B(k,j) with A(i,k) = A[i*sai + k*sak] and
-// B(k,j) = B[k*sbk + j*sbj]; 16x16 output tiles, the k range split over
-// gridDim.z (partial sums added atomically when split).
-constexpr int kTile = 16;
-
-__global__ void k_gemm(int M, int Nn, int Kk, const float* __restrict__ A, long long sai,
-                       long long sak, const float* __restrict__ Bm, long long sbk, long long sbj,
-                       float* __restrict__ Cm, long long ldc, int accumulate) {
-  __shared__ float As[kTile][kTile + 1];
-  __shared__ float Bs[kTile][kTile + 1];
-  const int ti = threadIdx.y, tj = threadIdx.x;
-  const int i = blockIdx.y * kTile + ti, j = blockIdx.x * kTile + tj;
-  const int kchunk = (Kk + gridDim.z - 1) / gridDim.z;
-  const int k0 = blockIdx.z * kchunk, k1 = min(Kk, k0 + kchunk);
-  float acc = 0.0f;
-  for (int kb = k0; kb < k1; kb += kTile) {
-    const int ka = kb + tj, kbb = kb + ti;
-    As[ti][tj] = (i < M && ka < k1) ? A[(long long)i * sai + (long long)ka * sak] : 0.0f;
-    const int jj = blockIdx.x * kTile + tj;
-    Bs[ti][tj] = (jj < Nn && kbb < k1) ? Bm[(long long)kbb * sbk + (long long)jj * sbj] : 0.0f;
-    __syncthreads();
-#pragma unroll
-    for (int t = 0; t < kTile; ++t) acc += As[ti][t] * Bs[t][tj];
-    __syncthreads();
-  }
-  if (i < M && j < Nn) {
-    float* c = Cm + (long long)i * ldc + j;
-    if (gridDim.z > 1) atomicAdd(c, acc);
-    else *c = accumulate ? *c + acc : acc;
-  }
-}
-
-// Z += b (broadcast over rows), H = gelu(Z).
-__global__ void k_bias_gelu(float* Z, float* Hh, const float* b, int rows, int cols, int act) {
-  const long long n = (long long)rows * cols;
-  for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < n;
-       t += (long long)gridDim.x * blockDim.x) {
-    const float z = Z[t] + b[t % cols];
-    Z[t] = z;
-    if (act) Hh[t] = gelu_f(z);
-  }
-}
-
-// dZ = dH * gelu'(Z)
-__global__ void k_gelu_back(const float* Z, const float* dH, float* dZ, long long n) {
-  for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < n;
-       t += (long long)gridDim.x * blockDim.x)
-    dZ[t] = dH[t] * gelu_grad_f(Z[t]);
-}
-
-// Gaussian head: per row, loss = |u|^2 / 2 + sum log C_ll with C u = beta - mu, and
-// dL/dout (scaled by 1/B): d mu = -v, d logC_ii = 1 - v_i u_i C_ii,
+// One training step's forward and backward pass of the network for
+// kTrainRows rows per block, entirely in shared memory (weights, the rows'
+// features and beta, both layers' pre-activations and activations, the
+// outputs and the back-propagated gradients), then this block's sum over its
+// rows of every parameter gradient and of the loss, written in parameter order
+// to part[block][np + 1] (the loss last).  Rows past Bsz take no part.
+//
+// Gaussian head, per row: loss = |u|^2 / 2 + sum log C_ll with C u = beta - mu;
+// dL/dout (scaled by 1/Bsz): d mu = -v, d logC_ii = 1 - v_i u_i C_ii,
 // d C_ij = -v_i u_j (i > j), where C^T v = u.
-__global__ void k_nll_head(const float* __restrict__ O, const float* __restrict__ Y, int Bsz,
-                           int L, float* __restrict__ dO, float* __restrict__ loss_sum) {
-  const int r = blockIdx.x * blockDim.x + threadIdx.x;
-  const int K = L + L * (L + 1) / 2;
-  float loss = 0.0f;
-  if (r < Bsz) {
-    const float* o = O + (size_t)r * K;
-    float C[kMaxL][kMaxL], u[kMaxL], v[kMaxL];
-    for (int i = 0; i < L; ++i)
-      for (int j = 0; j < L; ++j) C[i][j] = 0.0f;
-    int k = 2 * L;
-    for (int i = 0; i < L; ++i) {
-      C[i][i] = expf(o[L + i]);
-      for (int j = 0; j < i; ++j) C[i][j] = o[k++];
-    }
-    for (int i = 0; i < L; ++i) {
-      float s = Y[(size_t)r * L + i] - o[i];
-      for (int j = 0; j < i; ++j) s -= C[i][j] * u[j];
-      u[i] = s / C[i][i];
-      loss += 0.5f * u[i] * u[i] + o[L + i];
-    }
-    for (int i = L - 1; i >= 0; --i) {
-      float s = u[i];
-      for (int j = i + 1; j < L; ++j) s -= C[j][i] * v[j];
-      v[i] = s / C[i][i];
-    }
-    const float sc = 1.0f / (float)Bsz;
-    float* d = dO + (size_t)r * K;
-    for (int i = 0; i < L; ++i) {
-      d[i] = -v[i] * sc;
-      d[L + i] = (1.0f - v[i] * u[i] * C[i][i]) * sc;
-    }
-    k = 2 * L;
-    for (int i = 0; i < L; ++i)
-      for (int j = 0; j < i; ++j) d[k++] = -v[i] * u[j] * sc;
-  }
-  for (int o = 16; o > 0; o >>= 1) loss += __shfl_down_sync(0xffffffffu, loss, o);
-  if ((threadIdx.x & 31) == 0) atomicAdd(loss_sum, loss);
+constexpr int kTrainRows = 32;
+constexpr int kTrainThreads = 256;
+constexpr int kRowGroups = kTrainThreads / kMlpHidden;       // 4
+constexpr int kRowsPerThread = kTrainRows / kRowGroups;      // 8
+
+__host__ __device__ inline int train_smem_floats(int L) {
+  const int H = kMlpHidden, HP = H + 1, F = 4 * L + 1, K = L + L * (L + 1) / 2, R = kTrainRows;
+  return H * F + H * HP + K * HP + 2 * H + K + R * F + R * L + 6 * R * H + R * K + 32;
 }
 
-// Column sums: g[j] = sum_i D[i][j].
-__global__ void k_colsum(const float* D, int rows, int cols, float* g) {
-  const int j = blockIdx.x;
+__device__ __forceinline__ void nll_row(float* o, const float* y, int L, float sc, float* loss) {
+  float C[kMaxL][kMaxL], u[kMaxL], v[kMaxL];
+  for (int i = 0; i < L; ++i)
+    for (int j = 0; j < L; ++j) C[i][j] = 0.0f;
+  int k = 2 * L;
+  for (int i = 0; i < L; ++i) {
+    C[i][i] = expf(o[L + i]);
+    for (int j = 0; j < i; ++j) C[i][j] = o[k++];
+  }
+  float ls = 0.0f;
+  for (int i = 0; i < L; ++i) {
+    float s = y[i] - o[i];
+    for (int j = 0; j < i; ++j) s -= C[i][j] * u[j];
+    u[i] = s / C[i][i];
+    ls += 0.5f * u[i] * u[i] + o[L + i];
+  }
+  for (int i = L - 1; i >= 0; --i) {
+    float s = u[i];
+    for (int j = i + 1; j < L; ++j) s -= C[j][i] * v[j];
+    v[i] = s / C[i][i];
+  }
+  // o becomes dL/do
+  k = 2 * L;
+  for (int i = 0; i < L; ++i)
+    for (int j = 0; j < i; ++j) o[k++] = -v[i] * u[j] * sc;
+  for (int i = 0; i < L; ++i) {
+    o[L + i] = (1.0f - v[i] * u[i] * C[i][i]) * sc;
+    o[i] = -v[i] * sc;
+  }
+  *loss = ls;
+}
+
+// Rows: fb / yb [Bsz][F], [Bsz][L] as given, or (feat != null) a minibatch drawn
+// with replacement from the M pairs feat [M][F], beta [M][L] for the step the
+// control block describes (Philox stream kStreamTrain, index = row, iteration
+// t + 1), standardised with st = (feature means, feature scales, beta means,
+// beta scales).
+__global__ void __launch_bounds__(kTrainThreads) k_mlp_fwd_bwd(
+    const float* __restrict__ params, int L, int Bsz, const float* __restrict__ fb,
+    const float* __restrict__ yb, const float* __restrict__ feat,
+    const float* __restrict__ beta, long long M, uint32_t seed_lo, uint32_t seed_hi,
+    const TrainCtl* __restrict__ ctl, const float* __restrict__ st, float* __restrict__ part) {
+  extern __shared__ __align__(1024) uint8_t sm_raw[];
+  float* sm = reinterpret_cast<float*>(sm_raw);
+  constexpr int H = kMlpHidden, HP = kMlpHidden + 1, R = kTrainRows, T = kTrainThreads;
+  const int F = 4 * L + 1, K = L + L * (L + 1) / 2;
+  const int np = mlp_n_params(F, K);
+  // weights: W1 [H][F]; W2 and W3 padded to H+1 columns (conflict-free reads by
+  // output row and by input column)
+  float* sW1 = sm;
+  float* sW2 = sW1 + H * F;
+  float* sW3 = sW2 + H * HP;
+  float* sb1 = sW3 + K * HP;
+  float* sb2 = sb1 + H;
+  float* sb3 = sb2 + H;
+  float* sX = sb3 + K;        // [R][F]
+  float* sY = sX + R * F;     // [R][L]
+  float* sZ1 = sY + R * L;    // [R][H] pre-activations and activations
+  float* sA1 = sZ1 + R * H;
+  float* sZ2 = sA1 + R * H;
+  float* sA2 = sZ2 + R * H;
+  float* sG2 = sA2 + R * H;   // dL/dz2
+  float* sG1 = sG2 + R * H;   // dL/dz1
+  float* sD = sG1 + R * H;    // [R][K] outputs, then dL/dout
+  float* sred = sD + R * K;   // [32]
+  const float* W1 = params;
+  const float* b1 = W1 + H * F;
+  const float* W2 = b1 + H;
+  const float* b2 = W2 + H * H;
+  const float* W3 = b2 + H;
+  const float* b3 = W3 + K * H;
+  const int tid = threadIdx.x;
+  const int r0 = blockIdx.x * R;
+  const int nr = min(R, Bsz - r0);
+  __shared__ long long srow[R];
+  if (feat != nullptr && tid < nr) {
+    Rng rg(seed_lo, seed_hi, 0u, kStreamTrain, (uint32_t)(r0 + tid), (uint32_t)(ctl->t + 1));
+    long long m = (long long)(rg.u(0) * (double)M);
+    srow[tid] = m >= M ? M - 1 : m;
+  }
+#pragma unroll 4
+  for (int i = tid; i < H * F; i += T) sW1[i] = W1[i];
+#pragma unroll 4
+  for (int i = tid; i < H * H; i += T) sW2[(i / H) * HP + i % H] = W2[i];
+#pragma unroll 4
+  for (int i = tid; i < K * H; i += T) sW3[(i / H) * HP + i % H] = W3[i];
+  for (int i = tid; i < H; i += T) {
+    sb1[i] = b1[i];
+    sb2[i] = b2[i];
+  }
+  for (int i = tid; i < K; i += T) sb3[i] = b3[i];
+  if (feat != nullptr) {
+    __syncthreads();  // srow
+    const float* mf = st;
+    const float* sf = st + F;
+    const float* mb = st + 2 * F;
+    const float* sb = st + 2 * F + L;
+    for (int i = tid; i < R * F; i += T) {
+      const int r = i / F, f = i % F;
+      sX[i] = r < nr ? (feat[(size_t)srow[r] * F + f] - mf[f]) / sf[f] : 0.0f;
+    }
+    for (int i = tid; i < R * L; i += T) {
+      const int r = i / L, l = i % L;
+      sY[i] = r < nr ? (beta[(size_t)srow[r] * L + l] - mb[l]) / sb[l] : 0.0f;
+    }
+  } else {
+    for (int i = tid; i < R * F; i += T)
+      sX[i] = i / F < nr ? fb[(size_t)r0 * F + i] : 0.0f;
+    for (int i = tid; i < R * L; i += T)
+      sY[i] = i / L < nr ? yb[(size_t)r0 * L + i] : 0.0f;
+  }
+  __syncthreads();
+
+  // thread: unit h of a layer for rows rq, rq + 4, ..
+  const int h = tid % H, rq = tid / H;
+  float acc[kRowsPerThread];
+  // layer 1
+#pragma unroll
+  for (int i = 0; i < kRowsPerThread; ++i) acc[i] = sb1[h];
+  for (int f = 0; f < F; ++f) {
+    const float w = sW1[h * F + f];
+#pragma unroll
+    for (int i = 0; i < kRowsPerThread; ++i) acc[i] += w * sX[(rq + kRowGroups * i) * F + f];
+  }
+#pragma unroll
+  for (int i = 0; i < kRowsPerThread; ++i) {
+    const int r = rq + kRowGroups * i;
+    sZ1[r * H + h] = acc[i];
+    sA1[r * H + h] = gelu_f(acc[i]);
+  }
+  __syncthreads();
+  // layer 2
+#pragma unroll
+  for (int i = 0; i < kRowsPerThread; ++i) acc[i] = sb2[h];
+  for (int k = 0; k < H; ++k) {
+    const float w = sW2[h * HP + k];
+#pragma unroll
+    for (int i = 0; i < kRowsPerThread; ++i) acc[i] += w * sA1[(rq + kRowGroups * i) * H + k];
+  }
+#pragma unroll
+  for (int i = 0; i < kRowsPerThread; ++i) {
+    const int r = rq + kRowGroups * i;
+    sZ2[r * H + h] = acc[i];
+    sA2[r * H + h] = gelu_f(acc[i]);
+  }
+  __syncthreads();
+  // output layer
+  for (int e = tid; e < R * K; e += T) {
+    const int r = e / K, j = e % K;
+    float a = sb3[j];
+    for (int k = 0; k < H; ++k) a += sW3[j * HP + k] * sA2[r * H + k];
+    sD[e] = a;
+  }
+  __syncthreads();
+  // head: one thread per row
+  float loss = 0.0f;
+  if (tid < R) {
+    if (tid < nr) {
+      nll_row(sD + tid * K, sY + tid * L, L, 1.0f / (float)Bsz, &loss);
+    } else {
+      for (int j = 0; j < K; ++j) sD[tid * K + j] = 0.0f;
+    }
+  }
+  if (tid < 32) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) loss += __shfl_down_sync(0xffffffffu, loss, o);
+    if (tid == 0) sred[0] = loss;
+  }
+  __syncthreads();
+  // dL/dz2 = (dL/dout W3) * gelu'(z2)
+#pragma unroll
+  for (int i = 0; i < kRowsPerThread; ++i) acc[i] = 0.0f;
+  for (int j = 0; j < K; ++j) {
+    const float w = sW3[j * HP + h];
+#pragma unroll
+    for (int i = 0; i < kRowsPerThread; ++i) acc[i] += sD[(rq + kRowGroups * i) * K + j] * w;
+  }
+#pragma unroll
+  for (int i = 0; i < kRowsPerThread; ++i) {
+    const int r = rq + kRowGroups * i;
+    sG2[r * H + h] = acc[i] * gelu_grad_f(sZ2[r * H + h]);
+  }
+  __syncthreads();
+  // dL/dz1 = (dL/dz2 W2) * gelu'(z1)
+#pragma unroll
+  for (int i = 0; i < kRowsPerThread; ++i) acc[i] = 0.0f;
+  for (int k = 0; k < H; ++k) {
+    const float w = sW2[k * HP + h];
+#pragma unroll
+    for (int i = 0; i < kRowsPerThread; ++i) acc[i] += sG2[(rq + kRowGroups * i) * H + k] * w;
+  }
+#pragma unroll
+  for (int i = 0; i < kRowsPerThread; ++i) {
+    const int r = rq + kRowGroups * i;
+    sG1[r * H + h] = acc[i] * gelu_grad_f(sZ1[r * H + h]);
+  }
+  __syncthreads();
+  // this block's gradient sums over its rows, in parameter order
+  float* out = part + (size_t)blockIdx.x * (np + 1);
+  // offsets: W1 at 0, then b1, W2, b2, W3, b3
+  const int ob1 = H * F, oW2 = ob1 + H, ob2 = oW2 + H * H, oW3 = ob2 + H, ob3 = oW3 + K * H;
+  for (int p = tid; p < np; p += T) {
+    float g = 0.0f;
+    if (p < ob1) {
+      const int u = p / F, f = p % F;
+      for (int r = 0; r < R; ++r) g += sG1[r * H + u] * sX[r * F + f];
+    } else if (p < oW2) {
+      const int u = p - ob1;
+      for (int r = 0; r < R; ++r) g += sG1[r * H + u];
+    } else if (p < ob2) {
+      const int q = p - oW2, u = q / H, k = q % H;
+      for (int r = 0; r < R; ++r) g += sG2[r * H + u] * sA1[r * H + k];
+    } else if (p < oW3) {
+      const int u = p - ob2;
+      for (int r = 0; r < R; ++r) g += sG2[r * H + u];
+    } else if (p < ob3) {
+      const int q = p - oW3, j = q / H, k = q % H;
+      for (int r = 0; r < R; ++r) g += sD[r * K + j] * sA2[r * H + k];
+    } else {
+      const int j = p - ob3;
+      for (int r = 0; r < R; ++r) g += sD[r * K + j];
+    }
+    out[p] = g;
+  }
+  if (tid == 0) out[np] = sred[0];
+}
+
+// Adam (Kingma & Ba 2015) step sizes of the step the control block describes:
+// t is the Adam step count before the step, k the step within the training
+// call; the base step size decays along a cosine over the call to 5%.
+__device__ __forceinline__ void adam_scalars(const TrainCtl* c, float* c1, float* c2,
+                                             float* lr_t) {
+  const float t1 = (float)(c->t + 1);
+  *c1 = 1.0f - powf(c->b1, t1);
+  *c2 = 1.0f - powf(c->b2, t1);
+  *lr_t = (float)c->lr *
+          (0.05f + 0.475f * (1.0f + cosf(3.14159265f * (float)c->k / (float)c->steps)));
+}
+
+// Gradient and summed loss of the whole minibatch from the blocks' partials
+// (part [nblk][np + 1]), added in block order so that a step is deterministic:
+// block b takes parameters 32b..32b+31, warp w the partial rows w, w + 8, ..,
+// and warp 0 adds the eight warp sums in order.  With a control block it also
+// applies Adam to w, m, v and, in the last block to finish (ticket counter, no
+// waiting), adds the loss to the last epoch's sum and advances t and k.
+__global__ void __launch_bounds__(256) k_reduce_adam(const float* __restrict__ part, int nblk,
+                                                     int np, float* __restrict__ grad,
+                                                     float* __restrict__ loss, float* w, float* m,
+                                                     float* v, TrainCtl* ctl, int B, float eps) {
+  __shared__ float red[8][33];
+  const int lane = threadIdx.x & 31, wp = threadIdx.x >> 5;
+  const int p = blockIdx.x * 32 + lane;
   float s = 0.0f;
-  for (int i = threadIdx.x; i < rows; i += blockDim.x) s += D[(size_t)i * cols + j];
-  for (int o = 16; o > 0; o >>= 1) s += __shfl_down_sync(0xffffffffu, s, o);
-  __shared__ float red[32];
-  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = s;
+  if (p <= np) {
+#pragma unroll 4
+    for (int c = wp; c < nblk; c += 8) s += part[(size_t)c * (np + 1) + p];
+  }
+  red[wp][lane] = s;
+  __syncthreads();
+  if (wp == 0 && p <= np) {
+    float g = 0.0f;
+#pragma unroll
+    for (int i = 0; i < 8; ++i) g += red[i][lane];
+    if (p == np) {
+      *loss = g;
+    } else {
+      grad[p] = g;
+      if (ctl != nullptr) {
+        float c1, c2, lr_t;
+        adam_scalars(ctl, &c1, &c2, &lr_t);
+        const float b1 = ctl->b1, b2 = ctl->b2;
+        const float mt = b1 * m[p] + (1.0f - b1) * g;
+        const float vt = b2 * v[p] + (1.0f - b2) * g * g;
+        m[p] = mt;
+        v[p] = vt;
+        w[p] -= lr_t * (mt / c1) / (sqrtf(vt / c2) + eps);
+      }
+    }
+  }
+  if (ctl == nullptr) return;
   __syncthreads();
   if (threadIdx.x == 0) {
-    float t = 0.0f;
-    for (int w = 0; w < (int)(blockDim.x >> 5); ++w) t += red[w];
-    g[j] = t;
+    __threadfence();
+    const unsigned prev = atomicAdd(&ctl->done, 1u);
+    if (prev == gridDim.x - 1) {
+      __threadfence();
+      const float lv = *(volatile const float*)loss;
+      if (ctl->k >= ctl->steps - ctl->epoch_steps) ctl->loss_sum += (double)lv / (double)B;
+      ctl->t += 1;
+      ctl->k += 1;
+      ctl->done = 0;
+    }
   }
-}
-
-// Adam scalars of the current training step, kept on the device so that a
-// captured training step replays unchanged: t is the Adam step count before the
-// step, k the step within the training call.
-__device__ __forceinline__ void train_scalars(TrainCtl* c) {
-  const double t1 = (double)(c->t + 1);
-  c->c1 = (float)(1.0 - pow((double)c->b1, t1));
-  c->c2 = (float)(1.0 - pow((double)c->b2, t1));
-  // cosine decay of the step size over the call, to 5% of lr
-  c->lr_t = (float)(c->lr * (0.05 + 0.475 * (1.0 + cos(3.141592653589793 * (double)c->k /
-                                                         (double)c->steps))));
-}
-
-__global__ void k_train_begin(TrainCtl* c) {
-  if (threadIdx.x == 0 && blockIdx.x == 0) train_scalars(c);
-}
-
-// After a step: add the step's loss to the last epoch's sum, advance t and k and
-// prepare the next step's scalars.
-__global__ void k_train_tick(TrainCtl* c, const float* loss, int B) {
-  if (threadIdx.x != 0 || blockIdx.x != 0) return;
-  if (c->k >= c->steps - c->epoch_steps) c->loss_sum += (double)*loss / (double)B;
-  c->t += 1;
-  c->k += 1;
-  train_scalars(c);
-}
-
-// Adam (Kingma & Ba 2015) with bias correction, the scalars from the control block.
-__global__ void k_adam_ctl(float* w, const float* g, float* m, float* v, int n,
-                           const TrainCtl* __restrict__ c, float eps) {
-  const int t = blockIdx.x * blockDim.x + threadIdx.x;
-  if (t >= n) return;
-  const float b1 = c->b1, b2 = c->b2;
-  const float gt = g[t];
-  const float mt = b1 * m[t] + (1.0f - b1) * gt;
-  const float vt = b2 * v[t] + (1.0f - b2) * gt * gt;
-  m[t] = mt;
-  v[t] = vt;
-  w[t] -= c->lr_t * (mt / c->c1) / (sqrtf(vt / c->c2) + eps);
-}
-
-// Minibatch rows for the step the control block describes (Philox step t + 1).
-__global__ void k_gather_rows_ctl(const float* __restrict__ feat, const float* __restrict__ beta,
-                                  long long M, int F, int L, int Bsz, uint32_t seed_lo,
-                                  uint32_t seed_hi, const TrainCtl* __restrict__ c,
-                                  const float* __restrict__ st, float* __restrict__ fb,
-                                  float* __restrict__ yb) {
-  const int i = blockIdx.x * blockDim.x + threadIdx.x;
-  if (i >= Bsz) return;
-  Rng r(seed_lo, seed_hi, 0u, kStreamTrain, (uint32_t)i, (uint32_t)(c->t + 1));
-  long long m = (long long)(r.u(0) * (double)M);
-  if (m >= M) m = M - 1;
-  const float* mf = st;
-  const float* sf = st + F;
-  const float* mb = st + 2 * F;
-  const float* sb = st + 2 * F + L;
-  for (int k = 0; k < F; ++k) fb[(size_t)i * F + k] = (feat[(size_t)m * F + k] - mf[k]) / sf[k];
-  for (int l = 0; l < L; ++l) yb[(size_t)i * L + l] = (beta[(size_t)m * L + l] - mb[l]) / sb[l];
 }
 
 // ---------------------------------------------------------------- launchers
@@ -845,58 +992,37 @@ cudaError_t launch_fold(float* params, const float* st, int L, int to_raw, cudaS
   return cudaGetLastError();
 }
 
-cudaError_t launch_gemm(int M, int Nn, int Kk, const float* A, long long sai, long long sak,
-                        const float* B, long long sbk, long long sbj, float* C, long long ldc,
-                        int split_k, int accumulate, cudaStream_t s) {
-  dim3 grid((Nn + kTile - 1) / kTile, (M + kTile - 1) / kTile, split_k), block(kTile, kTile);
-  k_gemm<<<grid, block, 0, s>>>(M, Nn, Kk, A, sai, sak, B, sbk, sbj, C, ldc, accumulate);
+size_t train_smem_bytes(int L) { return (size_t)train_smem_floats(L) * sizeof(float); }
+
+int train_blocks(int Bsz) { return (Bsz + kTrainRows - 1) / kTrainRows; }
+
+cudaError_t prepare_train_kernel(int L) {
+  return cudaFuncSetAttribute(k_mlp_fwd_bwd, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                              (int)train_smem_bytes(L));
+}
+
+cudaError_t launch_mlp_grad(const float* params, int L, int Bsz, const float* fb, const float* yb,
+                            float* part, float* grad, float* loss, cudaStream_t s) {
+  const int nblk = train_blocks(Bsz);
+  const int np = mlp_param_count(L);
+  k_mlp_fwd_bwd<<<nblk, kTrainThreads, train_smem_bytes(L), s>>>(
+      params, L, Bsz, fb, yb, nullptr, nullptr, 0, 0u, 0u, nullptr, nullptr, part);
+  k_reduce_adam<<<(np + 1 + 31) / 32, 256, 0, s>>>(part, nblk, np, grad, loss, nullptr, nullptr,
+                                                   nullptr, nullptr, Bsz, 0.0f);
   return cudaGetLastError();
 }
 
-cudaError_t launch_bias_gelu(float* Z, float* H, const float* b, int rows, int cols, int act,
-                             cudaStream_t s) {
-  k_bias_gelu<<<256, 256, 0, s>>>(Z, H, b, rows, cols, act);
-  return cudaGetLastError();
-}
-
-cudaError_t launch_gelu_back(const float* Z, const float* dH, float* dZ, long long n,
-                             cudaStream_t s) {
-  k_gelu_back<<<256, 256, 0, s>>>(Z, dH, dZ, n);
-  return cudaGetLastError();
-}
-
-cudaError_t launch_nll_head(const float* O, const float* Y, int Bsz, int L, float* dO,
-                            float* loss_sum, cudaStream_t s) {
-  k_nll_head<<<(Bsz + 127) / 128, 128, 0, s>>>(O, Y, Bsz, L, dO, loss_sum);
-  return cudaGetLastError();
-}
-
-cudaError_t launch_colsum(const float* D, int rows, int cols, float* g, cudaStream_t s) {
-  k_colsum<<<cols, 256, 0, s>>>(D, rows, cols, g);
-  return cudaGetLastError();
-}
-
-cudaError_t launch_train_begin(TrainCtl* c, cudaStream_t s) {
-  k_train_begin<<<1, 32, 0, s>>>(c);
-  return cudaGetLastError();
-}
-
-cudaError_t launch_train_tick(TrainCtl* c, const float* loss, int B, cudaStream_t s) {
-  k_train_tick<<<1, 32, 0, s>>>(c, loss, B);
-  return cudaGetLastError();
-}
-
-cudaError_t launch_adam_ctl(float* w, const float* g, float* m, float* v, int n,
-                            const TrainCtl* c, cudaStream_t s) {
-  k_adam_ctl<<<(n + 255) / 256, 256, 0, s>>>(w, g, m, v, n, c, 1e-8f);
-  return cudaGetLastError();
-}
-
-cudaError_t launch_gather_rows_ctl(const float* feat, const float* beta, long long M, int F,
-                                   int L, int Bsz, uint64_t seed, const TrainCtl* c,
-                                   const float* st, float* fb, float* yb, cudaStream_t s) {
-  k_gather_rows_ctl<<<(Bsz + 127) / 128, 128, 0, s>>>(feat, beta, M, F, L, Bsz, (uint32_t)seed,
-                                                      (uint32_t)(seed >> 32), c, st, fb, yb);
+cudaError_t launch_train_step(float* params, int L, int Bsz, const float* feat, const float* beta,
+                              long long M, uint64_t seed, TrainCtl* ctl, const float* st,
+                              float* part, float* grad, float* loss, float* adam_m, float* adam_v,
+                              cudaStream_t s) {
+  const int nblk = train_blocks(Bsz);
+  const int np = mlp_param_count(L);
+  k_mlp_fwd_bwd<<<nblk, kTrainThreads, train_smem_bytes(L), s>>>(
+      params, L, Bsz, nullptr, nullptr, feat, beta, M, (uint32_t)seed, (uint32_t)(seed >> 32),
+      ctl, st, part);
+  k_reduce_adam<<<(np + 1 + 31) / 32, 256, 0, s>>>(part, nblk, np, grad, loss, params, adam_m,
+                                                   adam_v, ctl, Bsz, 1e-8f);
   return cudaGetLastError();
 }
 

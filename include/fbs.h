@@ -194,9 +194,11 @@ int fbs_counters(fbs_handle* h, int64_t* out);
 /* Runs n_iter iterations launching the sweep kernels one at a time (no
  * graph, no overlap) with CUDA events around each launch on the launching
  * stream, and writes the mean durations in milliseconds to ms[0..3]: the eps
- * kernel, the gamma/beta kernel, the hyperparameter kernel and the learned
- * proposal's network (0 when the handle does not use it).  The chain advances
- * as with fbs_run.  Synchronous. */
+ * kernel, the gamma/beta kernel (with the learned proposal and 128-thread
+ * blocks it includes the network pass for its genes), the hyperparameter
+ * kernel, and the learned proposal's network pass launched alone before it
+ * (timed for reference; 0 when the handle does not use the proposal).  The
+ * chain advances as with fbs_run.  Synchronous. */
 int fbs_profile(fbs_handle* h, int64_t n_iter, int64_t burnin, int64_t thin, double* ms);
 
 /* Philox uniforms exactly as the sampler draws them: out[i*n_k + k] is uniform
@@ -305,6 +307,12 @@ int fbs_proposal_calibrate(fbs_handle* h, int64_t n_sweeps, int64_t burnin, doub
  * and the slice updates of beta_g keep eps, so mode 1 alternates between the two
  * parameterisations of the gene's log-rates. */
 int fbs_proposal_mode(fbs_handle* h, int mode);
+
+/* 1 (default): with 128-thread gamma/beta blocks (the FP32 default) that kernel
+ * evaluates the network for its own 128 genes on the tensor cores before their
+ * move; 0: a separate network kernel runs before it.  Both evaluate the same
+ * tile code, so the chains are identical. */
+int fbs_proposal_fused(fbs_handle* h, int on);
 
 /* Copy the FP32 parameters out (get != NULL) and/or in (set != NULL); n must equal
  * fbs_proposal_param_count(L). */

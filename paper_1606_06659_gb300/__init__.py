@@ -39,7 +39,8 @@ EXPORTED = ("fbs_default_options", "fbs_workspace_bytes", "fbs_init", "fbs_run",
             "fbs_proposal_params", "fbs_proposal_stats", "fbs_proposal_loss_grad",
             "fbs_proposal_outputs", "fbs_proposal_step", "fbs_set_contrasts",
             "fbs_contrast_probs", "fbs_rhat", "fbs_proposal_kinds", "fbs_get_slice_widths",
-            "fbs_set_slice_widths", "fbs_batch_three_level", "fbs_batch_top_level")
+            "fbs_set_slice_widths", "fbs_batch_three_level", "fbs_batch_top_level",
+            "fbs_proposal_fused")
 NOALLOC_MAX_GENES = 2048 * 128
 
 
@@ -136,6 +137,7 @@ def load_library(path: str = LIB_PATH):
     lib.fbs_proposal_train.argtypes = [vp, C.c_int, C.c_int, C.c_double, u64, _PD]
     lib.fbs_proposal_calibrate.argtypes = [vp, i64, i64, C.c_double]
     lib.fbs_proposal_mode.argtypes = [vp, C.c_int]
+    lib.fbs_proposal_fused.argtypes = [vp, C.c_int]
     lib.fbs_proposal_params.argtypes = [vp, _PF, _PF, C.c_int]
     lib.fbs_proposal_stats.argtypes = [vp, _PI64, _PI64, C.POINTER(C.c_int), C.POINTER(C.c_int)]
     lib.fbs_proposal_loss_grad.argtypes = [_PF, C.c_int, C.c_int, _PF, _PF, _PD, _PF]
@@ -454,6 +456,9 @@ class Sampler:
 
     def proposal_mode(self, mode):
         _check(self.lib.fbs_proposal_mode(self.h, int(mode)))
+
+    def proposal_fused(self, on):
+        _check(self.lib.fbs_proposal_fused(self.h, int(bool(on))))
 
     def proposal_params(self, set_to=None):
         n = proposal_param_count(self.L)

@@ -150,6 +150,7 @@ struct LearnedState {
   long long pair_cap = 0, pairs = 0;
   int mode = 0;                // 1: genes with use_mh take the learned move
   bool trained = false;
+  bool fused = true;           // the gamma/beta kernel runs the network pass itself
 };
 
 struct fbs_handle {
@@ -368,15 +369,24 @@ int read_hyper(fbs_handle* h, Hyper* out) {
   return FBS_OK;
 }
 
+// The FP32 gamma/beta step of sweep i.  With the learned proposal and 128-thread
+// blocks the kernel evaluates the network itself (tensor cores, its own 128
+// genes); with other block sizes the stand-alone network pass runs first.
+cudaError_t gb_f32_step(fbs_handle* h, int i, cudaStream_t s) {
+  if (h->pf.prop == nullptr) return launch_gb_f32(h->mc, h->pf, h->block, i, s);
+  if (h->block == 128 && h->learned->fused)
+    return launch_gb_f32(h->mc, h->pf, 128, i, s, h->learned->w_image);
+  cudaError_t e = launch_proposal_f32(h->mc, h->pf, h->learned->w_image, h->learned->prop, s);
+  return e != cudaSuccess ? e : launch_gb_f32(h->mc, h->pf, h->block, i, s);
+}
+
 // n_iter sweeps launched one kernel at a time on the handle's stream.
 int sweeps_direct(fbs_handle* h, int64_t n_iter) {
   if (h->prec == FBS_F32) {
     FBS_CUDA(launch_seg_begin(h->p.hyp, h->s));
     for (int64_t i = 0; i < n_iter; ++i) {
       FBS_CUDA(launch_eps_f32(h->mc, h->pf, (int)i, h->s));
-      if (h->pf.prop)
-        FBS_CUDA(launch_proposal_f32(h->mc, h->pf, h->learned->w_image, h->learned->prop, h->s));
-      FBS_CUDA(launch_gb_f32(h->mc, h->pf, h->block, (int)i, h->s));
+      FBS_CUDA(gb_f32_step(h, (int)i, h->s));
       FBS_CUDA(launch_hyper(h->mc, h->p, h->nblk, h->s));
     }
     return FBS_OK;
@@ -402,12 +412,7 @@ cudaError_t capture_segment(fbs_handle* h) {
     e = f32 ? launch_eps_f32(h->mc, h->pf, i, h->s) : launch_eps_f64(h->mc, h->p, i, h->s);
     if (e != cudaSuccess) return e;
     if (i > 0 && (e = cudaStreamWaitEvent(h->s, h->ev_h, 0)) != cudaSuccess) return e;
-    if (f32 && h->pf.prop &&
-        (e = launch_proposal_f32(h->mc, h->pf, h->learned->w_image, h->learned->prop,
-                                 h->s)) != cudaSuccess)
-      return e;
-    e = f32 ? launch_gb_f32(h->mc, h->pf, h->block, i, h->s)
-            : launch_gb_f64(h->mc, h->p, h->block, i, h->s);
+    e = f32 ? gb_f32_step(h, i, h->s) : launch_gb_f64(h->mc, h->p, h->block, i, h->s);
     if (e != cudaSuccess) return e;
     if ((e = cudaEventRecord(h->ev_g, h->s)) != cudaSuccess) return e;
     if ((e = cudaStreamWaitEvent(h->s2, h->ev_g, 0)) != cudaSuccess) return e;
@@ -950,12 +955,13 @@ int fbs_profile(fbs_handle* h, int64_t n_iter, int64_t burnin, int64_t thin, dou
     cudaEventRecord(v[0], h->s);
     e = f32 ? launch_eps_f32(h->mc, h->pf, (int)i, h->s) : launch_eps_f64(h->mc, h->p, (int)i, h->s);
     cudaEventRecord(v[1], h->s);
+    // the network pass alone (the sweep runs it inside the gamma/beta kernel when
+    // blocks have 128 threads): timed for reference, its outputs recomputed there
     if (e == cudaSuccess && learned)
       e = launch_proposal_f32(h->mc, h->pf, h->learned->w_image, h->learned->prop, h->s);
     cudaEventRecord(v[2], h->s);
     if (e == cudaSuccess)
-      e = f32 ? launch_gb_f32(h->mc, h->pf, h->block, (int)i, h->s)
-              : launch_gb_f64(h->mc, h->p, h->block, (int)i, h->s);
+      e = f32 ? gb_f32_step(h, (int)i, h->s) : launch_gb_f64(h->mc, h->p, h->block, (int)i, h->s);
     cudaEventRecord(v[3], h->s);
     if (e == cudaSuccess) e = launch_hyper(h->mc, h->p, h->nblk, h->s);
     cudaEventRecord(v[4], h->s);
@@ -1290,6 +1296,19 @@ int fbs_proposal_mode(fbs_handle* h, int mode) {
   if (mode < 0 || mode > 2) return fail(FBS_E_ARG, "mode must be 0, 1 or 2");
   FBS_CUDA(cudaStreamSynchronize(h->s));
   learned_apply(h, mode, 0);
+  return FBS_OK;
+}
+
+int fbs_proposal_fused(fbs_handle* h, int on) {
+  int rc = learned_setup(h);
+  if (rc) return rc;
+  if (on != 0 && on != 1) return fail(FBS_E_ARG, "on must be 0 or 1");
+  FBS_CUDA(cudaStreamSynchronize(h->s));
+  h->learned->fused = on != 0;
+  if (h->seg_exec) {  // the captured segment changes
+    cudaGraphExecDestroy(h->seg_exec);
+    h->seg_exec = nullptr;
+  }
   return FBS_OK;
 }
 

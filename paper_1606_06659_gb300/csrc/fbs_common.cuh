@@ -161,7 +161,7 @@ struct DevPtrsF32 {
   float* mom_gam;     // [4][G]
   float* mu;          // [N][G] Poisson means at the new eps, from the eps kernel
   // learned proposal (null prop: plain slice updates only)
-  const float* prop;  // [n_out][G] proposal mean and Cholesky parameters per gene
+  float* prop;        // [n_out][G] proposal mean and Cholesky parameters per gene
   const uint8_t* use_mh;  // [G] the gene's proposal kind (0: slice updates only)
   unsigned* mh_acc;   // [2][G] accepted moves per kind (kind - 1)
   unsigned* mh_try;   // [2][G] attempted moves per kind

@@ -24,6 +24,7 @@
 #include "fbs_kernels.h"
 #include "fbs_rng.cuh"
 #include "fbs_hyper.cuh"
+#include "fbs_tc.cuh"
 
 namespace fbs {
 
@@ -231,10 +232,7 @@ __device__ __forceinline__ void add_counters(unsigned long long* base, unsigned 
                                              unsigned nonfin, unsigned* flags) {
   unsigned v[5] = {evals_e, evals_b, caps, gcaps, nonfin};
 #pragma unroll
-  for (int i = 0; i < 5; ++i) {
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) v[i] += __shfl_down_sync(0xffffffffu, v[i], o);
-  }
+  for (int i = 0; i < 5; ++i) v[i] = __reduce_add_sync(0xffffffffu, v[i]);  // warp sum
   if ((threadIdx.x & 31) == 0) {
     if (v[0]) atomicAdd(&base[FBS_CNT_EVALS_EPS], (unsigned long long)v[0]);
     if (v[1]) atomicAdd(&base[FBS_CNT_EVALS_BETA], (unsigned long long)v[1]);
@@ -505,8 +503,10 @@ __device__ __forceinline__ void beta_column_f32(const ModelConst& mc, const DevP
 // Genes marked for the learned proposal first make its move (which keeps every
 // log-rate, so the rates mu stay valid); the slice updates of beta_g follow the
 // gamma draw, for every gene unless the move replaces them (p.mh_replace).
+// net_ok: false when this block's network pass gave up (its genes then skip the
+// network's move).
 __device__ __forceinline__ void gb_f32_body(const ModelConst& mc, const DevPtrsF32& p, int seg_i,
-                                            int blk) {
+                                            int blk, bool net_ok = true) {
   // shared: mu[N][B], y[N][B], beta[L][B], partials[kNumPart][B] (per-thread values
   // indexed by a runtime l live here rather than in local memory); then FP64 warp sums
   extern __shared__ float smem_f[];
@@ -546,7 +546,8 @@ __device__ __forceinline__ void gb_f32_body(const ModelConst& mc, const DevPtrsF
     }
 
     // ---- learned-proposal move (keeps every log-rate, so mu stays valid)
-    const int kind = p.prop != nullptr ? move_kind(p, g, it) : 0;
+    int kind = p.prop != nullptr ? move_kind(p, g, it) : 0;
+    if (kind == kMoveNet && !net_ok) kind = 0;
     const bool mh_gene = kind != 0;
     if (mh_gene) {
       const bool acc = mh_move_f32(mc, p, g, it32, bs, B, tid, hy, 0.5f / p.gam[g], kind);
@@ -653,6 +654,39 @@ __device__ __forceinline__ void gb_f32_body(const ModelConst& mc, const DevPtrsF
 
 __global__ void __launch_bounds__(128) k_gb_f32(ModelConst mc, DevPtrsF32 p, int seg_i) {
   gb_f32_body(mc, p, seg_i, blockIdx.x);
+}
+
+// With the learned proposal (128 threads): the block first evaluates the network
+// for its 128 genes on the tensor cores (outputs to p.prop, read back by the same
+// threads in the move), then frees the tensor memory and reuses the shared
+// memory for the gamma/beta updates.  A kernel of its own, so that the plain
+// gamma/beta kernel keeps its own register allocation.
+__global__ void __launch_bounds__(128) k_gb_net_f32(ModelConst mc, DevPtrsF32 p, int seg_i,
+                                                    const uint8_t* __restrict__ img) {
+  bool net_ok;
+  {
+    extern __shared__ __align__(1024) uint8_t sm_tc[];
+    __shared__ __align__(8) uint64_t bars[2];
+    __shared__ uint32_t tmem_slot;
+    __shared__ int s_abort;
+    const TcShape t = tc_shape(mc.L);
+    size_t off_a;
+    tc_smem_layout(mc.L, &off_a);
+    if (threadIdx.x == 0) s_abort = 0;
+    TcBlock c;
+    tc_begin(c, bars, &tmem_slot, img, sm_tc, t.bytes);
+    if (!c.w_ok) s_abort = 1;
+    __syncthreads();
+    const int g = blockIdx.x * 128 + (int)threadIdx.x;
+    if (!s_abort) tc_tile(c, mc, p, t, sm_tc, sm_tc + off_a, g, net_gene(p, g, mc.G), p.prop,
+                          &s_abort);
+    __syncthreads();
+    net_ok = s_abort == 0;
+    tc_end(c, !net_ok, &p.hyp->flags);
+    fence_async_smem();
+    __syncthreads();  // the shared memory is the gamma/beta updates' from here on
+  }
+  gb_f32_body(mc, p, seg_i, blockIdx.x, net_ok);
 }
 
 // The learned move alone, at the current state, for the genes that use it (every
@@ -906,9 +940,22 @@ cudaError_t launch_eps_f32(const ModelConst& mc, const DevPtrsF32& p, int seg_i,
 }
 
 cudaError_t launch_gb_f32(const ModelConst& mc, const DevPtrsF32& p, int block, int seg_i,
-                          cudaStream_t s) {
+                          cudaStream_t s, const void* img) {
   const int nblk = (mc.G + block - 1) / block;
-  k_gb_f32<<<nblk, block, gene_smem_bytes_f32(mc.N, block), s>>>(mc, p, seg_i);
+  size_t smem = gene_smem_bytes_f32(mc.N, block);
+  if (img != nullptr) {
+    if (block != 128) return cudaErrorInvalidValue;  // one thread per gene of a 128-gene tile
+    const size_t tc = tc_smem_layout(mc.L, nullptr);
+    if (tc > smem) smem = tc;
+    const size_t most = tc_smem_layout(FBS_MAX_L, nullptr) > gene_smem_bytes_f32(FBS_MAX_N, 128)
+                            ? tc_smem_layout(FBS_MAX_L, nullptr)
+                            : gene_smem_bytes_f32(FBS_MAX_N, 128);
+    cudaError_t e = cudaFuncSetAttribute(k_gb_net_f32,
+                                         cudaFuncAttributeMaxDynamicSharedMemorySize, (int)most);
+    if (e != cudaSuccess) return e;
+  }
+  if (img != nullptr) k_gb_net_f32<<<nblk, block, smem, s>>>(mc, p, seg_i, (const uint8_t*)img);
+  else k_gb_f32<<<nblk, block, smem, s>>>(mc, p, seg_i);
   return cudaGetLastError();
 }
 

@@ -330,10 +330,7 @@ __device__ __forceinline__ void add_counters_u(unsigned long long* base, unsigne
                                                unsigned evals_g = 0) {
   unsigned v[6] = {evals_e, evals_b, caps, gcaps, nonfin, evals_g};
 #pragma unroll
-  for (int i = 0; i < 6; ++i) {
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) v[i] += __shfl_down_sync(0xffffffffu, v[i], o);
-  }
+  for (int i = 0; i < 6; ++i) v[i] = __reduce_add_sync(0xffffffffu, v[i]);  // warp sum
   if ((threadIdx.x & 31) == 0) {
     if (v[0]) atomicAdd(&base[FBS_CNT_EVALS_EPS], (unsigned long long)v[0]);
     if (v[1]) atomicAdd(&base[FBS_CNT_EVALS_BETA], (unsigned long long)v[1]);

@@ -34,8 +34,10 @@ cudaError_t launch_init_run(Hyper* hy, long long trace_cap, cudaStream_t s);
 size_t gene_smem_bytes_f32(int N, int block);
 cudaError_t prepare_gene_kernel_f32(int N, int block);
 cudaError_t launch_eps_f32(const ModelConst& mc, const DevPtrsF32& p, int seg_i, cudaStream_t s);
+// img: null, or the learned proposal's weight image, whose network the kernel
+// then evaluates for its own genes first (block must be 128)
 cudaError_t launch_gb_f32(const ModelConst& mc, const DevPtrsF32& p, int block, int seg_i,
-                          cudaStream_t s);
+                          cudaStream_t s, const void* img = nullptr);
 cudaError_t launch_seg_begin(Hyper* hy, cudaStream_t s);
 
 cudaError_t launch_mh_step_f32(const ModelConst& mc, const DevPtrsF32& p, long long it,

@@ -1,8 +1,11 @@
-// fbs_learned.cu -- the learned proposal for the beta_g block: per-gene
-// features, the multilayer perceptron that maps them to a Gaussian, the
+// fbs_learned.cu -- the learned proposal for the beta_g block: the weight
+// image and the stand-alone pass of the multilayer perceptron that maps the
+// per-gene features to a Gaussian (the tensor-core code is in fbs_tc.cuh), the
 // collection of training pairs from the plain sampler, and the training
-// kernels (minibatch gather, GEMMs, GELU, Gaussian negative log-likelihood
-// head, Adam).  The move that uses the proposal is in fbs_gene_f32.cu.
+// kernels (a fused per-block minibatch forward/backward pass with the Gaussian
+// negative log-likelihood head, then the gradient reduction with Adam).  The
+// move that uses the proposal, and the in-sweep network pass fused into the
+// gamma/beta kernel, are in fbs_gene_f32.cu.
 //
 // Network: features (4L+1) -> 64 -> GELU -> 64 -> GELU -> L + L(L+1)/2 outputs:
 // mean mu (L), log of the Cholesky diagonal (L), sub-diagonal entries in row
@@ -17,10 +20,9 @@
 #include "fbs_common.cuh"
 #include "fbs_kernels.h"
 #include "fbs_rng.cuh"
+#include "fbs_tc.cuh"
 
 namespace fbs {
-
-constexpr float kSqrt2OverPi = 0.7978845608028654f;
 
 __device__ __forceinline__ float gelu_f(float x) {
   return 0.5f * x * (1.0f + tanhf(kSqrt2OverPi * (x + 0.044715f * x * x * x)));
@@ -36,122 +38,6 @@ __host__ __device__ inline int mlp_n_params(int F, int K) {
   return kMlpHidden * F + kMlpHidden + kMlpHidden * kMlpHidden + kMlpHidden + K * kMlpHidden + K;
 }
 
-// Part of X^T (eta_g - h) over the samples n0 <= n < n1 (eta - h = eps + X beta).
-__device__ __forceinline__ void feature_sums(const ModelConst& mc, const DevPtrsF32& p, int g,
-                                             int n0, int n1, float* a) {
-  const int G = mc.G, L = mc.L;
-  float b[kMaxL];
-#pragma unroll
-  for (int l = 0; l < kMaxL; ++l) {
-    a[l] = 0.0f;
-    b[l] = l < L ? p.beta[(size_t)l * G + g] : 0.0f;
-  }
-#pragma unroll 4
-  for (int n = n0; n < n1; ++n) {
-    float lin = p.eps[(size_t)n * G + g];
-#pragma unroll
-    for (int l = 0; l < kMaxL; ++l)
-      if (l < L) lin += mc.Xf[n * kMaxL + l] * b[l];
-#pragma unroll
-    for (int l = 0; l < kMaxL; ++l)
-      if (l < L) a[l] += mc.Xf[n * kMaxL + l] * lin;
-  }
-}
-
-// The features of gene g from the sums a = X^T (eta_g - h): a / N, asinh(X^T y_g),
-// log gamma_g, theta, log sigma; all unchanged by the move, which keeps eta.
-__device__ __forceinline__ void finish_features(const ModelConst& mc, const DevPtrsF32& p, int g,
-                                                const Hyper* hy, const float* a, float* f) {
-  const int G = mc.G, L = mc.L;
-  const float invN = 1.0f / (float)mc.N;
-  for (int l = 0; l < L; ++l) {
-    f[l] = a[l] * invN;
-    f[L + l] = asinhf((float)p.T[(size_t)l * G + g]);
-    f[2 * L + 1 + l] = (float)hy->phi[2 + l];
-    f[3 * L + 1 + l] = 0.5f * logf((float)hy->phi[2 + L + l]);
-  }
-  f[2 * L] = logf(p.gam[g]);
-}
-
-__device__ __forceinline__ void gene_features(const ModelConst& mc, const DevPtrsF32& p, int g,
-                                              const Hyper* hy, float* f) {
-  float a[kMaxL];
-  feature_sums(mc, p, g, 0, mc.N, a);
-  finish_features(mc, p, g, hy, a, f);
-}
-
-// ---------------------------------------------------------------- tensor-core inference
-//
-// The network runs on the tensor cores (tcgen05): per tile of 128 genes (one
-// thread per gene, four warps) three GEMMs D = A W^T with BF16 operands read
-// from shared memory and FP32 accumulators in tensor memory, M = 128 and
-// N = 64, 64, n3.  Every FP32 operand x (weights, features, activations) enters
-// as a BF16 pair x = hi + lo, hi = bf16(x), lo = bf16(x - hi); each layer
-// accumulates hi*hi + lo*hi + hi*lo, which keeps about 16 significant bits per
-// operand (the lo*lo term is below that).  GELU, the biases and the split of
-// the next layer's input run in the epilogue, one thread per TMEM lane (= gene).
-//
-// Operands use the canonical K-major layout without swizzle: 8 x 16-byte core
-// matrices of 128 contiguous bytes, the core matrices of one 8-row group
-// consecutive along K (leading byte offset 128), the groups `sbo` bytes apart.
-// An operand with kw columns holds [hi (kw/2) | lo (kw/2)].
-
-struct TcShape {
-  int F, K;      // features, outputs
-  int k1;        // input columns of the first layer per half (F rounded up to 16)
-  int n3;        // rows of the last layer (K rounded up to 16)
-  int off_w2, off_w3, off_b, bytes;  // weight image: W1, W2, W3, biases (FP32)
-};
-
-__host__ __device__ inline TcShape tc_shape(int L) {
-  TcShape t;
-  t.F = 4 * L + 1;
-  t.K = L + L * (L + 1) / 2;
-  t.k1 = (t.F + 15) & ~15;
-  t.n3 = (t.K + 15) & ~15;
-  t.off_w2 = kMlpHidden * 2 * t.k1 * 2;
-  t.off_w3 = t.off_w2 + kMlpHidden * 2 * kMlpHidden * 2;
-  t.off_b = t.off_w3 + t.n3 * 2 * kMlpHidden * 2;
-  t.bytes = t.off_b + (2 * kMlpHidden + t.n3) * 4;
-  return t;
-}
-
-constexpr int kMaxK1 = (kMaxFeat + 15) & ~15;
-
-// Shared memory: the weight image, then one A operand buffer of 128 rows that
-// holds in turn the split features (2 k1 columns) and the split activations of
-// the two hidden layers (128 columns); each is dead once its GEMM completed.
-__host__ __device__ inline size_t tc_smem_layout(int L, size_t* off_a, size_t* off_stage = nullptr) {
-  const TcShape t = tc_shape(L);
-  const size_t a = ((size_t)t.bytes + 1023) & ~(size_t)1023;
-  const size_t cols = 2 * t.k1 > 2 * kMlpHidden ? 2 * t.k1 : 2 * kMlpHidden;
-  const size_t stage = a + (size_t)128 * cols * 2;  // [128][kMaxL] floats
-  if (off_a) *off_a = a;
-  if (off_stage) *off_stage = stage;
-  return stage + (size_t)128 * kMaxL * 4;
-}
-
-// Byte offset of element (r, c) of a canonical operand with kw columns.
-__host__ __device__ inline uint32_t canon_off(int r, int c, int kw) {
-  return (uint32_t)(((r >> 3) * (kw >> 3) + (c >> 3)) * 128 + (r & 7) * 16 + (c & 7) * 2);
-}
-
-// Row r, columns c0..c0+7 of an operand with kw = 2 kin columns: hi parts at
-// c0.., lo parts at kin + c0.. (16-byte stores; pairs converted together).
-__device__ __forceinline__ void store_split8(uint8_t* base, int kin, int r, int c0,
-                                             const float* v) {
-  uint32_t h[4], l[4];
-#pragma unroll
-  for (int i = 0; i < 4; ++i) {
-    const __nv_bfloat162 hb = __floats2bfloat162_rn(v[2 * i], v[2 * i + 1]);
-    const float2 hf = __bfloat1622float2(hb);
-    const __nv_bfloat162 lb = __floats2bfloat162_rn(v[2 * i] - hf.x, v[2 * i + 1] - hf.y);
-    h[i] = *reinterpret_cast<const uint32_t*>(&hb);
-    l[i] = *reinterpret_cast<const uint32_t*>(&lb);
-  }
-  *(uint4*)(base + canon_off(r, c0, 2 * kin)) = make_uint4(h[0], h[1], h[2], h[3]);
-  *(uint4*)(base + canon_off(r, kin + c0, 2 * kin)) = make_uint4(l[0], l[1], l[2], l[3]);
-}
 
 // The weight image the kernel copies into shared memory: W1 [64][2 k1],
 // W2 [64][128], W3 [n3][128] as split canonical operands (zero padding), then
@@ -195,153 +81,12 @@ __global__ void k_pack_image(const float* __restrict__ w, int L, uint8_t* __rest
   }
 }
 
-constexpr unsigned kTcWaitLimit = 1u << 24;  // try_wait polls before a wait gives up
+constexpr int kTcThreads = 128;  // one thread per gene of a tile (= TMEM lane)
 
-__device__ __forceinline__ uint32_t smem_u32(const void* ptr) {
-  return (uint32_t)__cvta_generic_to_shared(ptr);
-}
-
-__device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity) {
-  for (unsigned i = 0; i < kTcWaitLimit; ++i) {
-    uint32_t ok;
-    asm volatile(
-        "{\n\t.reg .pred P;\n\t"
-        "mbarrier.try_wait.parity.shared::cta.b64 P, [%1], %2;\n\t"
-        "selp.u32 %0, 1, 0, P;\n\t}\n"
-        : "=r"(ok)
-        : "r"(bar), "r"(parity)
-        : "memory");
-    if (ok) return true;
-  }
-  return false;
-}
-
-// Shared-memory matrix descriptor: start address, leading byte offset 128,
-// stride byte offset `sbo` (all >> 4), descriptor version 1 (bit 46), no swizzle.
-__device__ __forceinline__ uint64_t umma_desc(uint32_t saddr, uint32_t sbo) {
-  return (uint64_t)((saddr >> 4) & 0x3FFFu) | ((uint64_t)(128u >> 4) << 16) |
-         ((uint64_t)((sbo >> 4) & 0x3FFFu) << 32) | (1ull << 46);
-}
-
-// Instruction descriptor of kind::f16: FP32 accumulator (bits 4-5 = 1), A and
-// B BF16 (bits 7-9 and 10-12 = 1), both K-major, N >> 3 at bit 17, M >> 4 at bit 24.
-__host__ __device__ constexpr uint32_t umma_idesc_bf16(int M, int N) {
-  return (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(N >> 3) << 17) |
-         ((uint32_t)(M >> 4) << 24);
-}
-
-__device__ __forceinline__ void umma_bf16(uint32_t d, uint64_t a, uint64_t b, uint32_t idesc,
-                                          uint32_t acc) {
-  asm volatile(
-      "{\n\t.reg .pred p;\n\t"
-      "setp.ne.b32 p, %4, 0;\n\t"
-      "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}\n"
-      :
-      : "r"(d), "l"(a), "l"(b), "r"(idesc), "r"(acc)
-      : "memory");
-}
-
-// D (+)= A B^T over kin columns for the three hi/lo products; a and b are the
-// operands' shared addresses, both with 2 kin columns.
-__device__ __forceinline__ void issue_layer(uint32_t d, uint32_t a, uint32_t b, int kin,
-                                            uint32_t idesc) {
-  const uint32_t sbo = (uint32_t)(2 * kin / 8) * 128;
-  const uint32_t lo = (uint32_t)(kin / 8) * 128;
-  const uint32_t pa[3] = {0u, lo, 0u}, pb[3] = {0u, 0u, lo};
-  uint32_t acc = 0u;
-#pragma unroll
-  for (int q = 0; q < 3; ++q)
-    for (int k = 0; k < kin; k += 16) {
-      const uint32_t ko = (uint32_t)(k / 8) * 128;
-      umma_bf16(d, umma_desc(a + pa[q] + ko, sbo), umma_desc(b + pb[q] + ko, sbo), idesc, acc);
-      acc = 1u;
-    }
-}
-
-__device__ __forceinline__ void umma_commit(uint32_t bar) {
-  asm volatile(
-      "tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(bar)
-      : "memory");
-}
-
-__device__ __forceinline__ void tc_fence_before() {
-  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
-}
-__device__ __forceinline__ void tc_fence_after() {
-  asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-}
-__device__ __forceinline__ void fence_async_smem() {
-  asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-}
-
-// 16 consecutive FP32 columns of this thread's TMEM lane.
-__device__ __forceinline__ void tmem_ld16(uint32_t taddr, float* v) {
-  uint32_t r[16];
-  asm volatile(
-      "tcgen05.ld.sync.aligned.32x32b.x16.b32 "
-      "{%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, %15}, [%16];"
-      : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]),
-        "=r"(r[7]), "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]),
-        "=r"(r[14]), "=r"(r[15])
-      : "r"(taddr));
-  asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
-#pragma unroll
-  for (int i = 0; i < 16; ++i) v[i] = __uint_as_float(r[i]);
-}
-
-// GELU (tanh form) for inference: x (1 + tanh u) / 2 = x / (1 + e^{-2u}), from the
-// fast exponential and division: about 1e-6 relative error, far below what the
-// proposal needs.
-__device__ __forceinline__ float gelu_fast(float x) {
-  const float u = kSqrt2OverPi * (x + 0.044715f * x * x * x);
-  return __fdividef(x, 1.0f + __expf(-2.0f * u));
-}
-
-// 32 consecutive FP32 columns of this thread's TMEM lane (one load, one wait).
-__device__ __forceinline__ void tmem_ld32(uint32_t taddr, float* v) {
-  uint32_t r[32];
-  asm volatile(
-      "tcgen05.ld.sync.aligned.32x32b.x32.b32 "
-      "{%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, %15, "
-      "%16, %17, %18, %19, %20, %21, %22, %23, %24, %25, %26, %27, %28, %29, %30, %31}, [%32];"
-      : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]),
-        "=r"(r[7]), "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]),
-        "=r"(r[14]), "=r"(r[15]), "=r"(r[16]), "=r"(r[17]), "=r"(r[18]), "=r"(r[19]),
-        "=r"(r[20]), "=r"(r[21]), "=r"(r[22]), "=r"(r[23]), "=r"(r[24]), "=r"(r[25]),
-        "=r"(r[26]), "=r"(r[27]), "=r"(r[28]), "=r"(r[29]), "=r"(r[30]), "=r"(r[31])
-      : "r"(taddr));
-  asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
-#pragma unroll
-  for (int i = 0; i < 32; ++i) v[i] = __uint_as_float(r[i]);
-}
-
-// Bias, GELU and the split store of this thread's 32 columns c0.. of a hidden layer.
-__device__ __forceinline__ void hidden_epilogue(uint32_t taddr, const float* bias, uint8_t* abuf,
-                                                int row, int c0) {
-  float v[32];
-  tmem_ld32(taddr, v);
-#pragma unroll
-  for (int i = 0; i < 32; i += 4) {
-    const float4 bb = *reinterpret_cast<const float4*>(bias + c0 + i);
-    v[i] = gelu_fast(v[i] + bb.x);
-    v[i + 1] = gelu_fast(v[i + 1] + bb.y);
-    v[i + 2] = gelu_fast(v[i + 2] + bb.z);
-    v[i + 3] = gelu_fast(v[i + 3] + bb.w);
-  }
-#pragma unroll
-  for (int i = 0; i < 32; i += 8) store_split8(abuf, kMlpHidden, row, c0 + i, v + i);
-}
-
-constexpr uint32_t kTmemCols = 128;  // D1 at columns 0..63, D2 at 64..127, D3 at 0..n3-1
-constexpr int kTcThreads = 256;      // two warps per TMEM lane quadrant
-
-
-// Persistent over tiles of 128 genes; writes the proposal parameters [K][G] of
-// the genes that may use the network's proposal.  Threads t and
-// t + 128 sum the features of gene row t over the two halves of the samples and
-// thread t writes its split row of the first operand (row = TMEM lane); in the
-// epilogues warp w reads lane quadrant w % 4 and column half w / 4.  A wait that gives up sets
-// kFlagTimeout, and the CTA frees its tensor memory and returns.
+// Stand-alone network pass (fbs_proposal_outputs, fbs_proposal_step): persistent
+// over tiles of 128 genes, writes the outputs [K][G] of the genes that may use
+// the network's proposal.  A wait that gives up sets kFlagTimeout, and the
+// block frees its tensor memory and returns.
 __global__ void __launch_bounds__(kTcThreads) k_proposal_tc(ModelConst mc, DevPtrsF32 p,
                                                            const uint8_t* __restrict__ img_g,
                                                            float* __restrict__ out, int ntiles) {
@@ -350,162 +95,18 @@ __global__ void __launch_bounds__(kTcThreads) k_proposal_tc(ModelConst mc, DevPt
   __shared__ uint32_t tmem_slot;
   __shared__ int s_abort;
   const TcShape t = tc_shape(mc.L);
-  size_t off_a, off_stage;
-  tc_smem_layout(mc.L, &off_a, &off_stage);
-  uint8_t* abuf = sm + off_a;
-  float* stage = (float*)(sm + off_stage);
-  const float* bias = (const float*)(sm + t.off_b);
-  const int tid = threadIdx.x, warp = tid >> 5, lane_id = tid & 31;
-  const int quad = warp & 3, half = warp >> 2;
-  const int row = quad * 32 + lane_id;  // the gene (TMEM lane) this thread reads back
-  const uint32_t bar_w = smem_u32(&bars[0]), bar_m = smem_u32(&bars[1]);
-  if (tid == 0) {
-    s_abort = 0;
-    asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(bar_w) : "memory");
-    asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(bar_m) : "memory");
-    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
-  }
-  if (warp == 0) {
-    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(
-                     smem_u32(&tmem_slot)),
-                 "r"(kTmemCols)
-                 : "memory");
-    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
-  }
-  tc_fence_before();
+  size_t off_a;
+  tc_smem_layout(mc.L, &off_a);
+  if (threadIdx.x == 0) s_abort = 0;
+  TcBlock c;
+  tc_begin(c, bars, &tmem_slot, img_g, sm, t.bytes);
+  if (!c.w_ok) s_abort = 1;
   __syncthreads();
-  tc_fence_after();
-  const uint32_t tmem = tmem_slot;
-  if (tid == 0) {
-    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar_w),
-                 "r"((uint32_t)t.bytes)
-                 : "memory");
-    asm volatile(
-        "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::
-            "r"(smem_u32(sm)),
-        "l"(img_g), "r"((uint32_t)t.bytes), "r"(bar_w)
-        : "memory");
-  }
-  bool w_ok = mbar_wait(bar_w, 0);
-  if (!w_ok) s_abort = 1;
-  __syncthreads();
-
-  const uint32_t id64 = umma_idesc_bf16(128, 64), id3 = umma_idesc_bf16(128, t.n3);
-  const uint32_t lane_addr = (uint32_t)(quad * 32) << 16;
-  const uint32_t sa = smem_u32(abuf), sw = smem_u32(sm);
-  uint32_t ph = 0;
-  bool pending = false;  // an MMA batch whose completion was not seen
-  const int G = mc.G;
-
   for (int tile = blockIdx.x; tile < ntiles && !s_abort; tile += gridDim.x) {
-    const int g = tile * 128 + row;
-    // genes that may use the network's proposal in this sweep
-    const bool act = g < G && (p.mh_all == kMoveNet || p.mh_all == 3 ||
-                               (p.mh_all == 0 && p.use_mh[g] == kMoveNet));
-    // features: threads 0..127 sum X^T (eta - h) over the first half of the
-    // samples, threads 128..255 over the second half (same gene: row = tid % 128)
-    {
-      float a[kMaxL];
-      const int nh = mc.N / 2;
-      if (act) {
-        if (half == 0) feature_sums(mc, p, g, 0, nh, a);
-        else feature_sums(mc, p, g, nh, mc.N, a);
-      }
-      if (half == 1 && act) {
-#pragma unroll
-        for (int l = 0; l < kMaxL; ++l) stage[row * kMaxL + l] = a[l];
-      }
-      __syncthreads();
-      if (half == 0) {
-        float f[kMaxK1];
-#pragma unroll
-        for (int i = 0; i < kMaxK1; ++i) f[i] = 0.0f;
-        if (act) {
-#pragma unroll
-          for (int l = 0; l < kMaxL; ++l) a[l] += stage[row * kMaxL + l];
-          finish_features(mc, p, g, p.hyp, a, f);
-        }
-#pragma unroll
-        for (int c0 = 0; c0 < kMaxK1; c0 += 8)
-          if (c0 < t.k1) store_split8(abuf, t.k1, row, c0, f + c0);
-      }
-    }
-
-    // ---- layer 1: D1 = A1 W1^T
-    fence_async_smem();
-    tc_fence_before();
-    __syncthreads();
-    if (tid == 0) {
-      tc_fence_after();
-      issue_layer(tmem, sa, sw, t.k1, id64);
-      umma_commit(bar_m);
-    }
-    pending = true;
-    if (!mbar_wait(bar_m, ph)) s_abort = 1;
-    else pending = false;
-    ph ^= 1u;
-    tc_fence_after();
-    hidden_epilogue(tmem + lane_addr + (uint32_t)(half * 32), bias, abuf, row, half * 32);
-
-    // ---- layer 2: D2 = A2 W2^T (A2 overwrote A1 after GEMM 1 completed)
-    fence_async_smem();
-    tc_fence_before();
-    __syncthreads();
-    if (s_abort) break;
-    if (tid == 0) {
-      tc_fence_after();
-      issue_layer(tmem + kMlpHidden, sa, sw + (uint32_t)t.off_w2, kMlpHidden, id64);
-      umma_commit(bar_m);
-    }
-    pending = true;
-    if (!mbar_wait(bar_m, ph)) s_abort = 1;
-    else pending = false;
-    ph ^= 1u;
-    tc_fence_after();
-    hidden_epilogue(tmem + lane_addr + (uint32_t)(kMlpHidden + half * 32), bias + kMlpHidden, abuf,
-                    row, half * 32);
-
-    // ---- layer 3: D3 = A3 W3^T (D3 reuses D1's columns)
-    fence_async_smem();
-    tc_fence_before();
-    __syncthreads();
-    if (s_abort) break;
-    if (tid == 0) {
-      tc_fence_after();
-      issue_layer(tmem, sa, sw + (uint32_t)t.off_w3, kMlpHidden, id3);
-      umma_commit(bar_m);
-    }
-    pending = true;
-    if (!mbar_wait(bar_m, ph)) s_abort = 1;
-    else pending = false;
-    ph ^= 1u;
-    tc_fence_after();
-    for (int c0 = half * 16; c0 < t.n3; c0 += 32) {
-      float v[16];
-      tmem_ld16(tmem + lane_addr + (uint32_t)c0, v);
-#pragma unroll
-      for (int i = 0; i < 16; ++i) {
-        const int k = c0 + i;
-        if (act && k < t.K) out[(size_t)k * G + g] = v[i] + bias[2 * kMlpHidden + k];
-      }
-    }
-    tc_fence_before();
-    __syncthreads();
+    const int g = tile * 128 + (int)threadIdx.x;
+    if (!tc_tile(c, mc, p, t, sm, sm + off_a, g, net_gene(p, g, mc.G), out, &s_abort)) break;
   }
-
-  if (s_abort) {
-    if (tid == 0) atomicOr(&p.hyp->flags, kFlagTimeout);
-    if (!w_ok) mbar_wait(bar_w, 0);
-    if (pending) mbar_wait(bar_m, ph ^ 1u);
-  }
-  tc_fence_before();
-  __syncthreads();
-  if (warp == 0) {
-    tc_fence_after();
-    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem),
-                 "r"(kTmemCols)
-                 : "memory");
-  }
+  tc_end(c, s_abort != 0, &p.hyp->flags);
 }
 
 // Training pairs from the current state of every gene: features [M][F] and
@@ -966,7 +567,7 @@ cudaError_t launch_proposal_f32(const ModelConst& mc, const DevPtrsF32& p, const
   e = cudaFuncSetAttribute(k_proposal_tc, cudaFuncAttributeMaxDynamicSharedMemorySize,
                            (int)tc_smem_layout(FBS_MAX_L, nullptr));
   if (e != cudaSuccess) return e;
-  // Up to three CTAs per SM (shared memory), 128 TMEM columns each.
+  // Up to three blocks per SM (shared memory), 128 TMEM columns each.
   const int ntiles = (mc.G + 127) / 128;
   const int grid = ntiles < 3 * nsm ? ntiles : 3 * nsm;
   k_proposal_tc<<<grid, kTcThreads, smem, s>>>(mc, p, (const uint8_t*)img, out, ntiles);

@@ -204,6 +204,34 @@ def test_calibration_selects_genes_and_counts_moves():
     s.close()
 
 
+def test_fused_network_pass_equals_separate_kernel():
+    """The gamma/beta kernel that evaluates the network for its own 128 genes
+    (the default) and the separate network kernel followed by the plain
+    gamma/beta kernel give bit-identical chains (same tile code, same outputs,
+    same moves), through graph segments and direct launches."""
+    d = synthetic.make_config(1, G=1000)
+    s0, _ = _trained_sampler(d, seed=71, sweeps=40, epochs=20)
+    params = s0.proposal_params()
+    s0.close()
+    runs = []
+    for fused in (True, False):
+        s = fbs.Sampler(d["y"], d["X"], d["h"], d["priors"], seed=72, precision=fbs.FBS_F32,
+                        graph_segment=10, trace_cap=5)
+        s.set_state(it=0, **_truth(d))
+        s.proposal_params(set_to=params)
+        s.proposal_fused(fused)
+        s.proposal_calibrate(20, burnin=100, min_accept=0.1)
+        s.run(25, burnin=100, thin=5)
+        s.sync()
+        runs.append((s.get_state(), s.proposal_stats(), s.trace()["phi"], s.counters()))
+        s.close()
+    (sa, pa, ta, ca), (sb, pb, tb, cb) = runs
+    for k in ("eps", "beta", "gam", "phi", "w_eps", "w_beta"):
+        assert np.array_equal(sa[k], sb[k]), k
+    assert pa == pb and np.array_equal(ta, tb) and ca == cb
+    assert pa["tried"] > 0 and pa["accepted"] > 0
+
+
 def _start_after(s):
     st = s.get_state()
     return {k: st[k] for k in ("eps", "beta", "gam", "phi", "w_eps", "waux_eps", "w_beta",

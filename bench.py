@@ -90,10 +90,12 @@ def parse():
 # Re-measure when the kernels change.
 FP64_FLOP_PER_EVAL = 56.5
 FP64_TRAFFIC_BYTES = 44.0e6   # dram read+write of both kernels per sweep, same captures
-# FP32 forms: warp instructions issued per sweep by k_eps_f32 + k_gb_f32 and
-# their dram read+write (writes stay in L2), one ncu capture each at config 1
-FP32_WARP_INST = {"f32": 21.76e6 + 10.68e6, "learned": 21.78e6 + 14.19e6}
-FP32_TRAFFIC_BYTES = {"f32": 18.9e6 + 13.2e6, "learned": 18.9e6 + 16.9e6}
+# FP32 forms: warp instructions issued per sweep (smsp__inst_executed.sum) by the
+# eps kernel and the gamma/beta kernel (k_gb_f32; with the learned proposal
+# k_gb_net_f32, which includes the network pass) and their dram read+write
+# (writes stay in L2), from ncu captures at config 1
+FP32_WARP_INST = {"f32": 21.36e6 + 10.68e6, "learned": 21.36e6 + 20.12e6}
+FP32_TRAFFIC_BYTES = {"f32": 11.2e6 + 13.2e6, "learned": 11.2e6 + 15.4e6}
 # issue peak: 152 SMs x 4 schedulers x 1 warp instruction per clock x 2.07 GHz
 ISSUE_PEAK_WARP_INST_S = 152 * 4 * 2.07e9
 # the proposal network's own flops per gene (2 x (F*64 + 64*64 + 64*K), F = 21,
@@ -528,7 +530,8 @@ def main():
         rate = inst / (ms_gene / 1e3)
         roofline = {"bound": "alu", "achieved": rate, "peak": ISSUE_PEAK_WARP_INST_S,
                     "unit": "warp-instructions/s", "frac": rate / ISSUE_PEAK_WARP_INST_S,
-                    "traffic": FP32_TRAFFIC_BYTES[form], "kernel": "k_eps_f32 + k_gb_f32",
+                    "traffic": FP32_TRAFFIC_BYTES[form],
+                    "kernel": "k_eps_f32 + " + ("k_gb_net_f32" if form == "learned" else "k_gb_f32"),
                     "kernel_ms": ms_gene, "eps_kernel_ms": ms_k1, "gb_kernel_ms": ms_k2,
                     "hyper_kernel_ms": ms_hyper, "warp_instructions_per_sweep": inst,
                     "evals_per_launch": ev_launch,
@@ -554,7 +557,9 @@ def main():
         if world > 1:
             dist.destroy_process_group()
         return
-    launches_per_sweep = 4 if form == "learned" else 3
+    # eps, gamma/beta (with the learned proposal it runs the network too) and
+    # hyperparameter kernels per sweep, plus the segment snapshot per step
+    launches_per_sweep = 3
     line = {
         "metric": METRIC, "value": value, "unit": "iters/s", "n_gpus": world,
         "steps": args.steps, "warmup": args.warmup,

@@ -86,3 +86,32 @@ def test_workspace_bytes_grows_with_trace():
     base = fbs.workspace_bytes(16, 40000, 5)
     o = fbs.default_options(trace_cap=10, trace_beta=1)
     assert fbs.workspace_bytes(16, 40000, 5, o) >= base + 10 * 40000 * 5 * 8
+
+
+def test_null_handles_are_refused_without_cuda():
+    """Entry points given a NULL handle return FBS_E_ARG before any CUDA call."""
+    lib = fbs.load_library()
+    checks = [
+        lib.fbs_run(None, 1, 0, 1),
+        lib.fbs_get_slice_widths(None, None, None, None, None),
+        lib.fbs_set_slice_widths(None, None, None, None, None),
+        lib.fbs_batch_three_level(None, None, None),
+        lib.fbs_batch_top_level(None, None, None, None, None, 0, None, None, None),
+        lib.fbs_proposal_fused(None, 1),
+        lib.fbs_proposal_mode(None, 1),
+    ]
+    assert all(rc == fbs.FBS_E_ARG for rc in checks), checks
+
+
+def test_bench_ess_matches_oracle_ess():
+    """The benchmark's host ESS of the hyperparameter trace is Geyer's initial
+    monotone sequence estimator, as the oracle's is (AR(1) series)."""
+    import bench
+    import oracle
+    rng = np.random.default_rng(4)
+    x = np.zeros((1500, 3))
+    for t in range(1, 1500):
+        x[t] = np.array([0.5, 0.9, -0.3]) * x[t - 1] + rng.normal(size=3)
+    got = bench.geyer_ess(x)
+    want = [oracle.ess(x[:, i]) for i in range(3)]
+    np.testing.assert_allclose(got, want, rtol=1e-10)

@@ -203,6 +203,19 @@ def cpu_baseline(data, seconds, G_full):
 
 
 # --------------------------------------------------------------------------- reference arm
+def job_rate(units_per_rank, seconds, world, device):
+    """Whole-job throughput of `world` replicas: every rank processed
+    units_per_rank units in `seconds`; the job takes as long as its slowest rank
+    (MAX all-reduce of the times), so value = all ranks' units / that time."""
+    if world > 1:
+        import torch
+        import torch.distributed as dist
+        t = torch.tensor([seconds], device=device, dtype=torch.float64)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        seconds = float(t.item())
+    return units_per_rank * world / seconds, seconds
+
+
 def run_reference(args, rank):
     if rank != 0:
         return
@@ -494,13 +507,8 @@ def main():
     clk = clocks.stop()
     step_ms = [a.elapsed_time(b) for a, b in evs]
     total_s = sum(step_ms) / 1e3
-    if world > 1:
-        t = torch.tensor([total_s], device="cuda", dtype=torch.float64)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        total_s = float(t.item())
-        barrier()
-    sweeps_all = args.steps * S * world
-    value = sweeps_all / total_s
+    value, total_s = job_rate(args.steps * S, total_s, world, "cuda")
+    barrier()
 
     # ---- roofline of the per-gene kernels: direct launches with CUDA events on
     #      their launching stream

@@ -129,3 +129,29 @@ def test_all_slice_widths_tune_and_conjugate_streams_idle():
     pc = plain.counters_dict()
     assert pc["evals_gam"] == 0 and pc["evals_hyp"] == 0
     assert np.all(plain.get_state()["w_gam"] == 1.0)
+
+
+def _chain_phi(args):
+    all_slice, seed, n_iter, burnin = args
+    import oracle as orc
+    from paper_1606_06659_gb300 import synthetic as syn
+    d = syn.make_config(0, G=300)
+    ch = orc.Chain(d["y"], d["X"], d["h"], d["priors"], seed=seed, burnin=burnin,
+                   tune_start=burnin // 2, all_slice=all_slice).init_default()
+    return ch.run(n_iter, thin=1, trace_cap=n_iter)["phi"]
+
+
+def test_all_slice_sweeps_target_the_exact_draw_posterior():
+    """Whole sweeps: 8 chains of the all-slice sampler and 8 of the exact-draw
+    sampler (N = 4, G = 300) give the same posterior means of every
+    hyperparameter, within 4.5 standard errors of the difference of the chain
+    means."""
+    import multiprocessing as mp
+    jobs = [(a, 100 + 10 * c + a, 3000, 600) for a in (False, True) for c in range(8)]
+    with mp.get_context("spawn").Pool(8) as pool:
+        res = pool.map(_chain_phi, jobs)
+    means = np.array([r.mean(0) for r in res])
+    exact, sliced = means[:8], means[8:]
+    se = np.sqrt(exact.var(0, ddof=1) / 8 + sliced.var(0, ddof=1) / 8)
+    z = (sliced.mean(0) - exact.mean(0)) / se
+    assert np.all(np.abs(z) < 4.5), z

@@ -21,6 +21,12 @@ the Gaussian tails of the move's target, so the ratio target / proposal is
 bounded and the independence sampler is uniformly ergodic (Mengersen & Tweedie
 1996), even where the network's scale is too small.
 Pinned by scipy's multivariate normal and t densities and by finite differences.
+
+block_conditional / block_step: the exact Gaussian full conditional of beta_g
+given its log-rates (the distribution the network learns to approximate) and an
+exact Gibbs update from it; the tests use a chain of the oracle's sweeps with
+this update added as an independent reference posterior.  Pinned by the joint
+density of the model at fixed log-rates (scipy Poisson and Normal terms).
 """
 from __future__ import annotations
 
@@ -171,3 +177,32 @@ def mh_move(eps, beta, gam, theta, sigma2, X, out, xi, log_u, chi2):
     acc = log_u < la
     eps_new = np.where(acc[:, None], eps - (beta_new - beta) @ X.T, eps)
     return eps_new, np.where(acc[:, None], beta_new, beta), acc, la
+
+
+def block_conditional(eps, beta, gam, theta, sigma2, X):
+    """The full conditional of beta_g given the log-rates eta_g = h + eps_g + X
+    beta_g (and gamma_g, theta, sigma^2), per row: the Poisson likelihood depends
+    on (eps_g, beta_g) only through eta_g, so given eta_g the model leaves the
+    Normal(0, gamma_g) prior of eps_g = eta_g - h - X beta_g and the
+    Normal(theta, sigma^2) prior of beta_g, a Gaussian in beta_g with precision
+    X^T X / gamma_g + diag(1 / sigma^2) and mean that precision's inverse times
+    X^T (eta_g - h) / gamma_g + theta / sigma^2.  Returns the means [G][L] and
+    the covariances [G][L][L]."""
+    eps, beta, X = map(np.asarray, (eps, beta, X))
+    gam = np.asarray(gam, np.float64)
+    lin = eps + beta @ X.T                                 # eta - h
+    prec = (X.T @ X)[None] / gam[:, None, None] + np.diag(1.0 / np.asarray(sigma2))[None]
+    cov = np.linalg.inv(prec)
+    rhs = lin @ X / gam[:, None] + (np.asarray(theta) / np.asarray(sigma2))[None]
+    return np.einsum("gij,gj->gi", cov, rhs), cov
+
+
+def block_step(eps, beta, gam, theta, sigma2, X, z):
+    """An exact Gibbs update of every beta_g given its log-rates (Section 4.1's
+    model in the coordinates (eta_g, beta_g), whose map from (eps_g, beta_g) has
+    unit Jacobian): beta* = mean + chol(cov) z from block_conditional with
+    standard normals z [G][L], and eps* = eps - X (beta* - beta), which keeps
+    every log-rate.  Returns (eps*, beta*)."""
+    mean, cov = block_conditional(eps, beta, gam, theta, sigma2, X)
+    beta_new = mean + np.einsum("gij,gj->gi", np.linalg.cholesky(cov), np.asarray(z))
+    return np.asarray(eps) - (beta_new - np.asarray(beta)) @ np.asarray(X).T, beta_new

@@ -158,3 +158,87 @@ def test_move_with_a_proposal_at_the_current_point_accepts_by_the_uniform():
     assert list(acc) == [True, True, False, False]
     np.testing.assert_allclose(e2, eps, atol=1e-12)
     np.testing.assert_allclose(b2, beta, atol=1e-12)
+
+
+def test_block_conditional_is_the_joint_density_at_fixed_log_rates():
+    """Along any change of beta_g that keeps eta_g (eps moving by -X d), the
+    joint log density (scipy Poisson and Normal terms of the model) changes
+    exactly as the log density of the Gaussian block conditional: the closed
+    form's precision and mean are those of the model."""
+    rng = np.random.default_rng(21)
+    X = paper_design(4)
+    N, L = X.shape
+    G = 6
+    h = rng.normal(0, 0.1, N)
+    y = rng.poisson(30, (G, N))
+    eps = rng.normal(0, 0.4, (G, N))
+    beta = rng.normal(0, 0.6, (G, L))
+    gam = rng.uniform(0.05, 0.8, G)
+    theta, sigma2 = rng.normal(0, 1, L), rng.uniform(0.05, 2, L)
+    mean, cov = P.block_conditional(eps, beta, gam, theta, sigma2, X)
+    for g in range(G):
+        def joint(e, b):
+            lam = np.exp(h + e + X @ b)
+            return (stats.poisson.logpmf(y[g], lam).sum()
+                    + stats.norm.logpdf(e, 0, np.sqrt(gam[g])).sum()
+                    + stats.norm.logpdf(b, theta, np.sqrt(sigma2)).sum())
+        q = stats.multivariate_normal(mean[g], cov[g])
+        for _ in range(3):
+            b2 = beta[g] + rng.normal(0, 0.3, L)
+            e2 = eps[g] - X @ (b2 - beta[g])
+            want = joint(e2, b2) - joint(eps[g], beta[g])
+            assert q.logpdf(b2) - q.logpdf(beta[g]) == pytest.approx(want, rel=1e-9, abs=1e-9)
+
+
+def test_block_step_draws_the_conditional_and_keeps_log_rates():
+    """block_step's draws have the block conditional's mean and covariance (5
+    standard errors, 2e5 rows of one gene) and keep h + eps + X beta."""
+    rng = np.random.default_rng(22)
+    X = paper_design(4)
+    N, L = X.shape
+    G = 200000
+    eps0 = np.tile(rng.normal(0, 0.3, N), (G, 1))
+    beta0 = np.tile(rng.normal(0, 0.5, L), (G, 1))
+    gam = np.full(G, 0.15)
+    theta, sigma2 = rng.normal(0, 1, L), rng.uniform(0.1, 1, L)
+    e2, b2 = P.block_step(eps0, beta0, gam, theta, sigma2, X, rng.normal(size=(G, L)))
+    np.testing.assert_allclose(e2 + b2 @ X.T, eps0 + beta0 @ X.T, atol=1e-10)
+    mean, cov = P.block_conditional(eps0[:1], beta0[:1], gam[:1], theta, sigma2, X)
+    mean, cov = mean[0], cov[0]
+    se = np.sqrt(np.diag(cov) / G)
+    assert np.all(np.abs(b2.mean(0) - mean) < 5 * se)
+    sec = np.sqrt((np.outer(np.diag(cov), np.diag(cov)) + cov ** 2) / G)
+    assert np.all(np.abs(np.cov(b2.T) - cov) < 5 * sec)
+
+
+@pytest.mark.parametrize("mutant", ["no_prior_precision", "gamma_squared", "theta_sign"])
+def test_block_conditional_pin_catches_planted_mistakes(mutant):
+    """Planted mistakes in the block conditional (the prior's precision dropped,
+    gamma squared, the prior mean's sign flipped) break the joint-density pin."""
+    rng = np.random.default_rng(23)
+    X = paper_design(4)
+    N, L = X.shape
+    h = rng.normal(0, 0.1, N)
+    y = rng.poisson(30, N)
+    eps, beta = rng.normal(0, 0.4, N), rng.normal(0, 0.6, L)
+    gam, theta, sigma2 = 0.3, rng.normal(0, 1, L), rng.uniform(0.05, 2, L)
+    lin = eps + X @ beta
+    prec = X.T @ X / (gam ** 2 if mutant == "gamma_squared" else gam)
+    if mutant != "no_prior_precision":
+        prec = prec + np.diag(1.0 / sigma2)
+    sgn = -1.0 if mutant == "theta_sign" else 1.0
+    cov = np.linalg.inv(prec)
+    mean = cov @ (X.T @ lin / gam + sgn * theta / sigma2)
+    q = stats.multivariate_normal(mean, cov)
+
+    def joint(e, b):
+        return (stats.poisson.logpmf(y, np.exp(h + e + X @ b)).sum()
+                + stats.norm.logpdf(e, 0, np.sqrt(gam)).sum()
+                + stats.norm.logpdf(b, theta, np.sqrt(sigma2)).sum())
+    bad = 0
+    for _ in range(5):
+        b2 = beta + rng.normal(0, 0.3, L)
+        e2 = eps - X @ (b2 - beta)
+        want = joint(e2, b2) - joint(eps, beta)
+        bad += abs(q.logpdf(b2) - q.logpdf(beta) - want) > 1e-6
+    assert bad >= 4

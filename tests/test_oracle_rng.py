@@ -105,3 +105,38 @@ def test_gamma_ks(shape):
     g = oracle.gamma_draws(shape, 9, 0, 200, 0, 60000, 2)
     assert np.all(g > 0)
     assert stats.kstest(g, stats.gamma(shape).cdf).pvalue > 1e-4
+
+
+def test_f32_uniforms_agree_with_the_pinned_f64_map():
+    """The FP32 form's uniform 4b+1 (4b+3) and the FP64 form's uniform 2b (2b+1)
+    both come from word 1 (3) of Philox block b: the FP64 uniform keeps that word
+    as its 32 leading bits, the FP32 uniform keeps the word's 23 leading bits, so
+    the two agree within 2^-24, the half-spacing of the FP32 grid.  The FP64 map
+    is pinned exactly above and Philox by the published vectors, so a wrong shift,
+    word or block index in the FP32 map fails here without retyping the map."""
+    seed, chain, stream, it = 0x0123456789ABCDEF, 5, 8, 4242
+    for index in (0, 7, 999_999):
+        u32 = oracle.uniforms_f32(seed, chain, stream, index, it, 16)
+        u64 = oracle.uniforms(seed, chain, stream, index, 1, it, 0, 8)[0]
+        for b in range(4):
+            assert abs(u32[4 * b + 1] - u64[2 * b]) <= 2.0 ** -24
+            assert abs(u32[4 * b + 3] - u64[2 * b + 1]) <= 2.0 ** -24
+
+
+def test_f32_uniforms_are_grid_midpoints():
+    """Every FP32 uniform is exactly an FP32 number, strictly inside (0, 1), on the
+    grid of midpoints (k + 1/2) 2^-23; complementing the Philox word reflects the
+    uniform about 1/2 (u(w) + u(~w) = 1 exactly), and the values are uniform (KS)."""
+    u = np.concatenate([oracle.uniforms_f32(77, 0, 9, i, 3, 12) for i in range(4000)])
+    assert np.all(u.astype(np.float32).astype(np.float64) == u)
+    assert np.all((u > 0) & (u < 1))
+    k = u * 2.0 ** 23 - 0.5
+    assert np.all(k == np.round(k)) and k.min() >= 0 and k.max() <= 2 ** 23 - 1
+    assert stats.kstest(u, "uniform").pvalue > 1e-4
+    # reflection: the word of uniform j and its complement give 1 - u
+    key = (77, 0)
+    w = oracle.philox((5, (9 << 24) | 0, 3, 0), key)
+    u0 = oracle.uniforms_f32(77, 0, 9, 5, 3, 4)
+    for j in range(4):
+        mirrored = (((~w[j] & 0xFFFFFFFF) >> 9) + 0.5) * 2.0 ** -23
+        assert u0[j] + mirrored == 1.0

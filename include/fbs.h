@@ -48,6 +48,7 @@ extern "C" {
 #define FBS_E_ARG (-1)       /* invalid argument (sizes, non-finite inputs, singular X ...) */
 #define FBS_E_CUDA (-2)      /* a CUDA runtime call failed */
 #define FBS_E_OOM (-3)       /* device memory could not be obtained */
+#define FBS_E_SLICE_CAP (-4) /* a slice update ran out of shrinkage proposals (kept its value) */
 #define FBS_E_NONFINITE (-5) /* a slice update started from a non-finite log density */
 
 #define FBS_MAX_N 64 /* samples */
@@ -137,9 +138,15 @@ int fbs_init(fbs_handle** out, const int32_t* y, int N, int G, int gene_major, c
  * Errors: FBS_E_ARG for n_iter < 0, burnin < 0 or thin < 1; FBS_E_CUDA. */
 int fbs_run(fbs_handle* h, int64_t n_iter, int64_t burnin, int64_t thin);
 
-/* Wait for the handle's work.  Returns FBS_E_NONFINITE if any slice update
- * so far started from a non-finite log density, FBS_E_CUDA on a CUDA error,
- * else FBS_OK. */
+/* Wait for the handle's work.  Returns FBS_E_CUDA on a CUDA error (or when a
+ * bounded tensor-core wait of the proposal network gave up), else
+ * FBS_E_NONFINITE if any slice update so far started from a non-finite log
+ * density, else FBS_E_SLICE_CAP if any slice update so far used up its
+ * shrink_max shrinkage proposals without accepting one, else FBS_OK.
+ * Algorithm 2 (Appendix A) puts no bound on its shrinkage loop; here an
+ * update that reaches the bound keeps its current value, so the chain goes on,
+ * and FBS_CNT_SLICE_CAPS counts such updates.  Both conditions are
+ * sticky: they are reported by every later fbs_sync of the handle. */
 int fbs_sync(fbs_handle* h);
 
 /* Running moments (Section 3.1) copied to caller-allocated host arrays, in
@@ -149,6 +156,39 @@ int fbs_sync(fbs_handle* h);
 int fbs_moments(fbs_handle* h, double* mean_eps, double* msq_eps, double* mean_beta,
                 double* msq_beta, double* mean_gam, double* msq_gam, double* mean_phi,
                 double* msq_phi, int64_t* count);
+
+/* ---- Posterior summaries (Section 3.1) ------------------------------------
+ *
+ * From the running means and mean squares of C >= 1 chains of the same model,
+ * pooled as Section 3.1 pools them (mean = (1/C) sum_c mean_c, msq = (1/C)
+ * sum_c msq_c): the posterior mean, the posterior standard deviation
+ * sd = sqrt(msq - mean^2) (0 where rounding makes msq - mean^2 negative), and
+ * the normal-approximation equal-tail interval mean -/+ z * sd, whose level is
+ * 1 - 2 (1 - Phi(z)) (z = 1.959963984540054 gives 95%).  The arithmetic runs on
+ * the device of chains[0]; the results are copied to the caller's host arrays.
+ * Every output pointer may be NULL to skip it.  Layouts are gene-major, as in
+ * fbs_moments: eps [G][N], beta [G][L], gamma [G], phi [2L+2]. */
+typedef struct {
+  double z;                                       /* interval half-width in sds, > 0 */
+  double *mean_eps, *sd_eps, *lo_eps, *hi_eps;    /* [G][N]; need eps moments */
+  double *mean_beta, *sd_beta, *lo_beta, *hi_beta;  /* [G][L] */
+  double *mean_gam, *sd_gam, *lo_gam, *hi_gam;    /* [G] */
+  double *mean_phi, *sd_phi, *lo_phi, *hi_phi;    /* [2L+2] */
+  double* trace_phi;     /* [trace_rows_max][2L+2] thinned phi draws of chains[0], or NULL */
+  int64_t trace_rows_max;
+  int64_t trace_rows;    /* out: rows copied to trace_phi */
+  int64_t count;         /* out: draws per chain folded into the moments (M) */
+  int64_t counters[FBS_NUM_COUNTERS];  /* out: FBS_CNT_* summed over the chains */
+  int64_t mh_accepted, mh_tried;       /* out: learned-proposal moves, summed (0 without) */
+} fbs_estimates_out;
+
+/* Summaries of one chain (fbs_estimates) or of C chains pooled
+ * (fbs_estimates_pooled, 1 <= C <= FBS_MAX_RHAT_CHAINS; batch views allowed;
+ * equal N, G, L, precision and draw counts M >= 1).  FBS_E_ARG for a
+ * mismatch, z <= 0, M = 0, or eps outputs requested from a chain without eps
+ * moments.  Synchronous (waits for every chain). */
+int fbs_estimates(fbs_handle* h, fbs_estimates_out* out);
+int fbs_estimates_pooled(int C, fbs_handle* const* chains, fbs_estimates_out* out);
 
 /* Current state to / from host arrays (gene-major, as in fbs_moments), with
  * slice widths w and tuning sums w_aux: eps, w_eps, waux_eps [G][N]; beta,
@@ -314,6 +354,14 @@ int fbs_proposal_mode(fbs_handle* h, int mode);
  * tile code, so the chains are identical. */
 int fbs_proposal_fused(fbs_handle* h, int on);
 
+/* Bound of every wait of the tensor-core network pass (mbarrier polls; default
+ * 2^24).  A wait that reaches it gives up: the block sets a flag, waits up to
+ * 2^24 polls for its copies and matrix products still in flight, frees its tensor
+ * memory, and its genes skip the network's move in that sweep; fbs_sync then
+ * returns FBS_E_CUDA.  0 makes every pass give up at its first wait (which
+ * exercises that path).  FBS_E_ARG for FP64 handles and batch views. */
+int fbs_proposal_wait_limit(fbs_handle* h, uint32_t polls);
+
 /* Copy the FP32 parameters out (get != NULL) and/or in (set != NULL); n must equal
  * fbs_proposal_param_count(L). */
 int fbs_proposal_params(fbs_handle* h, float* get, const float* set, int n);
@@ -452,7 +500,13 @@ void fbs_batch_free(fbs_batch* b);
  *   hyp [2L+4] = (nu, tau, theta_1..L, sigma^2_1..L, w_nu, waux_nu)  (in/out);
  *   running moments m_* / q_* (mean / mean square): eps [N][G] (both may be
  *   NULL to skip), beta [L][G], gamma [G], phi [2L+2] -- updated, with n_mom
- *   draws already folded in, when it > burnin and otherwise untouched.
+ *   draws already folded in, when it > burnin and otherwise untouched;
+ *   n_mom may not exceed it - 1 - burnin (the post-burn-in iterations before
+ *   this one), else FBS_E_ARG;
+ *   status: NULL, or a device array of 1 + FBS_NUM_COUNTERS uint64 that
+ *   receives this call's flags word (bit 0: a slice update started from a
+ *   non-finite log density, which this call does not check for in the caller's
+ *   state) and its FBS_CNT_* counters (FBS_CNT_SWEEPS = 1).
  * X, h and the priors are host arrays read during the call.  Slice widths are
  * tuned while it <= burnin (M_C = burnin/2).  No trace is written.
  *
@@ -462,7 +516,8 @@ void fbs_batch_free(fbs_batch* b);
  * holds until the process exits.  G above FBS_NOALLOC_MAX_GENES returns
  * FBS_E_ARG.  The first call on a device looks up the array's device address
  * (cudaGetSymbolAddress) with that device current; make that first call before
- * any stream capture.  All calls share the array and every call rewrites what
+ * any stream capture.  The address is kept for the life of the process, so
+ * the entry point must not be used on a device after cudaDeviceReset.  All calls share the array and every call rewrites what
  * it reads from it, so calls whose work overlaps on the GPU (different streams
  * at the same time) race; calls on one stream are ordered.  The call is
  * asynchronous on `stream` (NULL = legacy default stream): the outputs are
@@ -491,6 +546,7 @@ typedef struct {
   double* hyp;
   double *m_eps, *q_eps, *m_beta, *q_beta, *m_gam, *q_gam, *m_phi, *q_phi;
   void* stream;
+  uint64_t* status;     /* device [1 + FBS_NUM_COUNTERS] or NULL: see above */
 } fbs_sweep_args;
 
 int fbs_sweep_noalloc(const fbs_sweep_args* a);

@@ -19,7 +19,7 @@ import numpy as np
 _HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(_HERE, "_build", "libfbs.so")
 
-FBS_OK, FBS_E_ARG, FBS_E_CUDA, FBS_E_OOM, FBS_E_NONFINITE = 0, -1, -2, -3, -5
+FBS_OK, FBS_E_ARG, FBS_E_CUDA, FBS_E_OOM, FBS_E_SLICE_CAP, FBS_E_NONFINITE = 0, -1, -2, -3, -4, -5
 FBS_F64, FBS_F32 = 0, 1
 FBS_MAX_CONTRASTS, FBS_MAX_CONTRAST_TERMS = 8, 4
 FBS_MAX_RHAT_CHAINS = 64
@@ -40,7 +40,8 @@ EXPORTED = ("fbs_default_options", "fbs_workspace_bytes", "fbs_init", "fbs_run",
             "fbs_proposal_outputs", "fbs_proposal_step", "fbs_set_contrasts",
             "fbs_contrast_probs", "fbs_rhat", "fbs_proposal_kinds", "fbs_get_slice_widths",
             "fbs_set_slice_widths", "fbs_batch_three_level", "fbs_batch_top_level",
-            "fbs_proposal_fused")
+            "fbs_proposal_fused", "fbs_estimates", "fbs_estimates_pooled",
+            "fbs_proposal_wait_limit")
 NOALLOC_MAX_GENES = 2048 * 128
 
 
@@ -87,7 +88,17 @@ class SweepArgs(C.Structure):
                 ("T", C.c_void_p)] + [(n, C.c_void_p) for n in (
                     "eps", "w_eps", "waux_eps", "beta", "w_beta", "waux_beta", "gam", "hyp",
                     "m_eps", "q_eps", "m_beta", "q_beta", "m_gam", "q_gam", "m_phi", "q_phi",
-                    "stream")]
+                    "stream", "status")]
+
+
+class EstimatesOut(C.Structure):
+    """fbs_estimates_out: pooled posterior means, sds and intervals (§3.1)."""
+    _fields_ = ([("z", C.c_double)] +
+                [(f"{q}_{v}", _PD) for v in ("eps", "beta", "gam", "phi")
+                 for q in ("mean", "sd", "lo", "hi")] +
+                [("trace_phi", _PD), ("trace_rows_max", C.c_int64), ("trace_rows", C.c_int64),
+                 ("count", C.c_int64), ("counters", C.c_int64 * 10),
+                 ("mh_accepted", C.c_int64), ("mh_tried", C.c_int64)])
 
 
 def load_library(path: str = LIB_PATH):
@@ -138,6 +149,7 @@ def load_library(path: str = LIB_PATH):
     lib.fbs_proposal_calibrate.argtypes = [vp, i64, i64, C.c_double]
     lib.fbs_proposal_mode.argtypes = [vp, C.c_int]
     lib.fbs_proposal_fused.argtypes = [vp, C.c_int]
+    lib.fbs_proposal_wait_limit.argtypes = [vp, u32]
     lib.fbs_proposal_params.argtypes = [vp, _PF, _PF, C.c_int]
     lib.fbs_proposal_stats.argtypes = [vp, _PI64, _PI64, C.POINTER(C.c_int), C.POINTER(C.c_int)]
     lib.fbs_proposal_loss_grad.argtypes = [_PF, C.c_int, C.c_int, _PF, _PF, _PD, _PF]
@@ -146,6 +158,8 @@ def load_library(path: str = LIB_PATH):
     lib.fbs_set_contrasts.argtypes = [vp, C.c_int, C.POINTER(C.c_int), _PD, _PD]
     lib.fbs_contrast_probs.argtypes = [vp, _PD, _PI64]
     lib.fbs_rhat.argtypes = [C.c_int, C.POINTER(vp), _PD, _PD, _PD, _PD]
+    lib.fbs_estimates.argtypes = [vp, C.POINTER(EstimatesOut)]
+    lib.fbs_estimates_pooled.argtypes = [C.c_int, C.POINTER(vp), C.POINTER(EstimatesOut)]
     lib.fbs_proposal_kinds.argtypes = [vp, C.POINTER(C.c_uint8)]
     lib.fbs_free.argtypes = [vp]
     lib.fbs_free.restype = None
@@ -197,9 +211,10 @@ def sweep_noalloc(X, h, priors, *, seed, it, burnin, n_mom=0, chain=0, step_out_
                   shrink_max=100, stream=None, **dev):
     """One sweep on caller-owned device arrays with no allocation (fbs_sweep_noalloc).
 
-    ``dev`` maps y, T, eps, w_eps, waux_eps, beta, w_beta, waux_beta, gam, hyp and the
+    ``dev`` maps y, T, eps, w_eps, waux_eps, beta, w_beta, waux_beta, gam, hyp, the
     optional moment arrays (m_eps, q_eps, m_beta, q_beta, m_gam, q_gam, m_phi, q_phi)
-    to device addresses (ints) in the device layout described in include/fbs.h.
+    and the optional status array (1 + NUM_COUNTERS uint64: flags, counters) to
+    device addresses (ints) in the device layout described in include/fbs.h.
     """
     X = np.ascontiguousarray(X, np.float64)
     N, L = X.shape
@@ -239,6 +254,43 @@ def rhat(chains, eps=False):
     _check(c0.lib.fbs_rhat(len(chains), hs, _pd(out["phi"]), _pd(out["beta"]), _pd(out["gam"]),
                            _pd(out.get("eps"))))
     return out
+
+
+Z95 = 1.959963984540054
+
+
+def estimates(chains, z=Z95, eps=False, trace_rows=0):
+    """Posterior means, sds (sqrt(msq - mean^2)) and normal-approximation
+    intervals mean -/+ z sd (§3.1) from the running moments of one or several
+    chains of the same model, pooled over the chains, computed on the device:
+    dict of {mean, sd, lo, hi}_{beta [G][L], gam [G], phi [2L+2]} (and eps [G][N]),
+    count, counters, mh_accepted, mh_tried and up to trace_rows phi trace rows of
+    the first chain."""
+    if isinstance(chains, Sampler):
+        chains = [chains]
+    c0 = chains[0]
+    shapes = {"beta": (c0.G, c0.L), "gam": (c0.G,), "phi": (c0.P,), "eps": (c0.G, c0.N)}
+    o = EstimatesOut()
+    o.z = float(z)
+    res = {}
+    for v, shp in shapes.items():
+        if v == "eps" and not eps:
+            continue
+        for q in ("mean", "sd", "lo", "hi"):
+            a = np.empty(shp)
+            res[f"{q}_{v}"] = a
+            setattr(o, f"{q}_{v}", _pd(a))
+    tr = np.empty((max(int(trace_rows), 0), c0.P))
+    if trace_rows:
+        o.trace_phi, o.trace_rows_max = _pd(tr), int(trace_rows)
+    hs = (C.c_void_p * len(chains))(*[c.h for c in chains])
+    _check(c0.lib.fbs_estimates_pooled(len(chains), hs, C.byref(o)))
+    res["count"] = o.count
+    res["counters"] = dict(zip(COUNTER_NAMES, (int(v) for v in o.counters)))
+    res["mh_accepted"], res["mh_tried"] = o.mh_accepted, o.mh_tried
+    if trace_rows:
+        res["trace_phi"] = tr[:o.trace_rows]
+    return res
 
 
 def proposal_param_count(L):
@@ -403,6 +455,10 @@ class Sampler:
         _check(self.lib.fbs_beta_ess(self.h, _pd(ess)))
         return ess
 
+    def estimates(self, z=Z95, eps=False, trace_rows=0):
+        """fbs_estimates of this chain (see the module function estimates)."""
+        return estimates([self], z=z, eps=eps, trace_rows=trace_rows)
+
     def count_sums(self):
         T = np.empty((self.G, self.L), np.int64)
         _check(self.lib.fbs_count_sums(self.h, T.ctypes.data_as(_PI64)))
@@ -456,6 +512,10 @@ class Sampler:
 
     def proposal_mode(self, mode):
         _check(self.lib.fbs_proposal_mode(self.h, int(mode)))
+
+    def proposal_wait_limit(self, polls):
+        """Bound of each tensor-core wait of the network pass (0: give up at once)."""
+        _check(self.lib.fbs_proposal_wait_limit(self.h, int(polls)))
 
     def proposal_fused(self, on):
         _check(self.lib.fbs_proposal_fused(self.h, int(bool(on))))

@@ -290,6 +290,7 @@ DevPtrs carve(char* base, const Layout& o, int trace_beta) {
 DevPtrsF32 carve_f32_ptrs(char* base, const LayoutF32& o32, int trace_beta) {
   DevPtrsF32 f;
   memset(&f, 0, sizeof(f));  // no learned proposal until one is set up
+  f.tc_polls = kTcWaitPolls;
   f.y = (const int32_t*)(base + o32.y);
   f.T = (const double*)(base + o32.T);
   f.eps = (float*)(base + o32.eps);
@@ -670,6 +671,38 @@ int fbs_init(fbs_handle** out, const int32_t* y, int N, int G, int gene_major, c
   return FBS_OK;
 }
 
+namespace {
+
+// The handle's counters summed over their copies (synchronous).
+int sum_counters(fbs_handle* h, int64_t* out) {
+  const int copies = kCounterCopies;
+  std::vector<unsigned long long> c((size_t)copies * FBS_NUM_COUNTERS);
+  FBS_CUDA(cudaMemcpyAsync(c.data(), h->p.counters, c.size() * sizeof(unsigned long long),
+                           cudaMemcpyDeviceToHost, h->s));
+  FBS_CUDA(cudaStreamSynchronize(h->s));
+  for (int i = 0; i < FBS_NUM_COUNTERS; ++i) {
+    unsigned long long t = 0;
+    for (int k = 0; k < copies; ++k) t += c[(size_t)k * FBS_NUM_COUNTERS + i];
+    out[i] = (int64_t)t;
+  }
+  return FBS_OK;
+}
+
+// FBS_E_SLICE_CAP once any slice update of the handle has used up its shrinkage
+// proposals (Algorithm 2 has no bound; the update kept its value).
+int slice_cap_status(fbs_handle* h) {
+  int64_t c[FBS_NUM_COUNTERS];
+  int rc = sum_counters(h, c);
+  if (rc) return rc;
+  if (c[FBS_CNT_SLICE_CAPS] > 0)
+    return fail(FBS_E_SLICE_CAP, std::to_string(c[FBS_CNT_SLICE_CAPS]) +
+                                     " slice update(s) ran out of shrinkage proposals and kept "
+                                     "their value");
+  return FBS_OK;
+}
+
+}  // namespace
+
 int fbs_run(fbs_handle* h, int64_t n_iter, int64_t burnin, int64_t thin) {
   if (!h) return fail(FBS_E_ARG, "handle is NULL");
   if (h->is_view) return fail(FBS_E_ARG, "a batch dataset runs with fbs_batch_run");
@@ -706,7 +739,7 @@ int fbs_sync(fbs_handle* h) {
     return fail(FBS_E_CUDA, "a tensor-core wait of the proposal network gave up");
   if (hy.flags & kFlagNonfinite)
     return fail(FBS_E_NONFINITE, "a slice update started from a non-finite log density");
-  return FBS_OK;
+  return slice_cap_status(h);
 }
 
 int fbs_moments(fbs_handle* h, double* mean_eps, double* msq_eps, double* mean_beta,
@@ -923,16 +956,7 @@ int fbs_counters(fbs_handle* h, int64_t* out) {
   if (!h || !out) return fail(FBS_E_ARG, "handle or out is NULL");
   int rc = enter(h);
   if (rc) return rc;
-  const int copies = kCounterCopies;
-  std::vector<unsigned long long> c((size_t)copies * FBS_NUM_COUNTERS);
-  FBS_CUDA(cudaMemcpyAsync(c.data(), h->p.counters, c.size() * sizeof(unsigned long long),
-                           cudaMemcpyDeviceToHost, h->s));
-  FBS_CUDA(cudaStreamSynchronize(h->s));
-  for (int i = 0; i < FBS_NUM_COUNTERS; ++i) {
-    unsigned long long t = 0;
-    for (int k = 0; k < copies; ++k) t += c[(size_t)k * FBS_NUM_COUNTERS + i];
-    out[i] = (int64_t)t;
-  }
+  if ((rc = sum_counters(h, out))) return rc;
   return leave(h);
 }
 
@@ -1312,6 +1336,18 @@ int fbs_proposal_fused(fbs_handle* h, int on) {
   return FBS_OK;
 }
 
+int fbs_proposal_wait_limit(fbs_handle* h, uint32_t polls) {
+  if (!h) return fail(FBS_E_ARG, "handle is NULL");
+  if (h->prec != FBS_F32 || h->is_view)
+    return fail(FBS_E_ARG, "the learned proposal needs a single-chain FBS_F32 handle");
+  h->pf.tc_polls = polls;
+  if (h->seg_exec) {  // captured kernels hold the old value
+    cudaGraphExecDestroy(h->seg_exec);
+    h->seg_exec = nullptr;
+  }
+  return FBS_OK;
+}
+
 int fbs_proposal_params(fbs_handle* h, float* get, const float* set, int n) {
   int rc = learned_setup(h);
   if (rc) return rc;
@@ -1425,6 +1461,106 @@ int fbs_rhat(int C, fbs_handle* const* chains, double* rhat_phi, double* rhat_be
   if (!rc && rhat_phi) rc = run(3, (long long)P, rhat_phi, 1);
   cudaFree(d_out);
   return rc;
+}
+
+int fbs_estimates_pooled(int C, fbs_handle* const* chains, fbs_estimates_out* out) {
+  if (C < 1 || C > FBS_MAX_RHAT_CHAINS || !chains || !out)
+    return fail(FBS_E_ARG, "need 1 <= C <= FBS_MAX_RHAT_CHAINS chains and an output struct");
+  if (!(out->z > 0.0) || !isfinite(out->z)) return fail(FBS_E_ARG, "z must be finite and > 0");
+  if (out->trace_phi && out->trace_rows_max < 0)
+    return fail(FBS_E_ARG, "trace_rows_max must be >= 0");
+  for (int c = 0; c < C; ++c)
+    if (!chains[c]) return fail(FBS_E_ARG, "a chain handle is NULL");
+  fbs_handle* h0 = chains[0];
+  const int N = h0->mc.N, G = h0->mc.G, L = h0->mc.L, P = h0->mc.P;
+  const bool want_eps = out->mean_eps || out->sd_eps || out->lo_eps || out->hi_eps;
+  long long M = -1;
+  for (int k = 0; k < FBS_NUM_COUNTERS; ++k) out->counters[k] = 0;
+  out->mh_accepted = out->mh_tried = 0;
+  for (int c = 0; c < C; ++c) {
+    fbs_handle* h = chains[c];
+    if (h->mc.N != N || h->mc.G != G || h->mc.L != L || h->prec != h0->prec)
+      return fail(FBS_E_ARG, "chains differ in N, G, L or precision");
+    if (want_eps && !h->mc.moments_eps) return fail(FBS_E_ARG, "a chain has no eps moments");
+    FBS_CUDA(cudaStreamSynchronize(h->s));
+    Hyper hy;
+    int rc = read_hyper(h, &hy);
+    if (rc) return rc;
+    if (M < 0) M = hy.n_mom;
+    if (hy.n_mom != M) return fail(FBS_E_ARG, "chains hold different numbers of draws");
+    int64_t cnt[FBS_NUM_COUNTERS];
+    if ((rc = sum_counters(h, cnt))) return rc;
+    for (int k = 0; k < FBS_NUM_COUNTERS; ++k) out->counters[k] += cnt[k];
+    if (h->learned) {
+      int64_t a = 0, t = 0;
+      if ((rc = fbs_proposal_stats(h, &a, &t, nullptr, nullptr))) return rc;
+      out->mh_accepted += a;
+      out->mh_tried += t;
+    }
+  }
+  if (M < 1) return fail(FBS_E_ARG, "the chains hold no post-burn-in draws");
+  out->count = M;
+  const bool f32 = h0->prec == FBS_F32;
+  const size_t NG = (size_t)N * G, LG = (size_t)L * G;
+  const size_t nmax = std::max(NG, std::max(LG, (size_t)P));
+  double* d_out = nullptr;
+  FBS_CUDA(cudaMalloc((void**)&d_out, sizeof(double) * 4 * nmax));
+  cudaStream_t s = h0->s;
+  // which: 0 beta, 1 gamma, 2 eps, 3 phi; dst = mean, sd, lo, hi (each may be NULL)
+  auto run = [&](int which, long long n, int R, double* const* dst) -> int {
+    if (!dst[0] && !dst[1] && !dst[2] && !dst[3]) return FBS_OK;
+    RhatInput in;
+    memset(&in, 0, sizeof(in));
+    in.C = C;
+    in.M = M;
+    in.n = n;
+    in.f32 = f32 && which != 3;
+    for (int c = 0; c < C; ++c) {
+      const fbs_handle* h = chains[c];
+      if (which == 3) {  // phi: FP64 moments in the Hyper block of either form
+        in.m[c] = (const double*)((const char*)h->p.hyp + offsetof(Hyper, m_phi));
+        in.q[c] = (const double*)((const char*)h->p.hyp + offsetof(Hyper, q_phi));
+      } else if (f32) {
+        in.mf[c] = which == 0 ? h->pf.mom_beta : (which == 1 ? h->pf.mom_gam : h->pf.mom_eps);
+      } else {
+        in.m[c] = which == 0 ? h->p.m_beta : (which == 1 ? h->p.m_gam : h->p.m_eps);
+        in.q[c] = which == 0 ? h->p.q_beta : (which == 1 ? h->p.q_gam : h->p.q_eps);
+      }
+    }
+    cudaError_t e = launch_estimates(in, out->z, d_out, s);
+    std::vector<double> tmp(4 * (size_t)n);
+    if (e == cudaSuccess)
+      e = cudaMemcpyAsync(tmp.data(), d_out, sizeof(double) * 4 * n, cudaMemcpyDeviceToHost, s);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    if (e != cudaSuccess) return fail(FBS_E_CUDA, std::string("estimates: ") + cudaGetErrorString(e));
+    for (int k = 0; k < 4; ++k) {
+      double* host = dst[k];
+      if (!host) continue;
+      const double* src = tmp.data() + (size_t)k * n;
+      for (int r = 0; r < R; ++r)
+        for (long long g = 0; g < n / R; ++g) host[(size_t)g * R + r] = src[(size_t)r * (n / R) + g];
+    }
+    return FBS_OK;
+  };
+  double* const beta_d[4] = {out->mean_beta, out->sd_beta, out->lo_beta, out->hi_beta};
+  double* const gam_d[4] = {out->mean_gam, out->sd_gam, out->lo_gam, out->hi_gam};
+  double* const eps_d[4] = {out->mean_eps, out->sd_eps, out->lo_eps, out->hi_eps};
+  double* const phi_d[4] = {out->mean_phi, out->sd_phi, out->lo_phi, out->hi_phi};
+  int rc = run(0, (long long)LG, L, beta_d);
+  if (!rc) rc = run(1, (long long)G, 1, gam_d);
+  if (!rc) rc = run(2, (long long)NG, N, eps_d);
+  if (!rc) rc = run(3, (long long)P, 1, phi_d);
+  cudaFree(d_out);
+  if (rc) return rc;
+  out->trace_rows = 0;
+  if (out->trace_phi && out->trace_rows_max > 0)
+    return fbs_trace(h0, out->trace_rows_max, out->trace_phi, nullptr, &out->trace_rows);
+  return FBS_OK;
+}
+
+int fbs_estimates(fbs_handle* h, fbs_estimates_out* out) {
+  fbs_handle* one[1] = {h};
+  return fbs_estimates_pooled(1, one, out);
 }
 
 int fbs_set_contrasts(fbs_handle* h, int n, const int* n_terms, const double* v, const double* b) {
@@ -1883,6 +2019,10 @@ int fbs_batch_sync(fbs_batch* b) {
     if (rc) return rc;
     if (hy.flags & kFlagNonfinite)
       return fail(FBS_E_NONFINITE, "a slice update started from a non-finite log density");
+  }
+  for (fbs_handle* v : b->views) {
+    int rc = slice_cap_status(v);
+    if (rc) return rc;
   }
   return FBS_OK;
 }

@@ -33,6 +33,10 @@ enum : uint32_t {
   kStreamPsi = 10,    // top level of the three-level model
 };
 
+// Default bound of every tensor-core wait (mbarrier try_wait polls) of the
+// proposal network; a wait that reaches it gives up and sets kFlagTimeout.
+constexpr unsigned kTcWaitPolls = 1u << 24;
+
 // Proposals of the eta-preserving move: the network's, or centred on the prior.
 enum : int { kMoveNet = 1, kMovePrior = 2 };
 
@@ -168,6 +172,7 @@ struct DevPtrsF32 {
   int mh_all;         // 0: per-gene kind (use_mh); 1, 2: that kind for every gene;
                       // 3: every gene, network / prior on alternate iterations
   int mh_replace;     // 1: the move replaces the slice updates of beta_g; 0: both run
+  unsigned tc_polls;  // bound of each tensor-core wait of the network pass
   double* partial;    // [n_blocks][kNumPart]
   Hyper* hyp;
   double* trace_phi;  // [trace_cap][P]

@@ -674,7 +674,7 @@ __global__ void __launch_bounds__(128) k_gb_net_f32(ModelConst mc, DevPtrsF32 p,
     tc_smem_layout(mc.L, &off_a);
     if (threadIdx.x == 0) s_abort = 0;
     TcBlock c;
-    tc_begin(c, bars, &tmem_slot, img, sm_tc, t.bytes);
+    tc_begin(c, bars, &tmem_slot, img, sm_tc, t.bytes, p.tc_polls);
     if (!c.w_ok) s_abort = 1;
     __syncthreads();
     const int g = blockIdx.x * 128 + (int)threadIdx.x;

@@ -631,6 +631,41 @@ __global__ void k_rhat(RhatInput in, double* __restrict__ out) {
   out[i] = W > 0.0 ? sqrt(1.0 + (B / W - 1.0) / M) : NAN;
 }
 
+// Posterior summaries of parameter i (§3.1) from C chains' running means and
+// mean squares, pooled over the chains: mean = (1/C) sum_c mean_c, msq = (1/C)
+// sum_c msq_c, sd = sqrt(msq - mean^2) (0 where rounding makes it negative), and
+// the normal-approximation interval mean -/+ z sd.  out: [4][n] = mean, sd, lo, hi.
+__global__ void k_estimates(RhatInput in, double z, double* __restrict__ out) {
+  const long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  if (i >= in.n) return;
+  double mean = 0.0, msq = 0.0;
+  for (int c = 0; c < in.C; ++c) {
+    if (in.f32) {
+      const float* b = in.mf[c];
+      mean += (double)b[i] - (double)b[in.n + i];
+      msq += (double)b[2 * in.n + i] - (double)b[3 * in.n + i];
+    } else {
+      mean += in.m[c][i];
+      msq += in.q[c][i];
+    }
+  }
+  mean /= in.C;
+  msq /= in.C;
+  const double var = msq - mean * mean;
+  const double sd = var > 0.0 ? sqrt(var) : 0.0;
+  out[i] = mean;
+  out[in.n + i] = sd;
+  out[2 * in.n + i] = mean - z * sd;
+  out[3 * in.n + i] = mean + z * sd;
+}
+
+cudaError_t launch_estimates(const RhatInput& in, double z, double* out, cudaStream_t s) {
+  if (in.n <= 0) return cudaSuccess;
+  const int blk = 128;
+  k_estimates<<<(unsigned)((in.n + blk - 1) / blk), blk, 0, s>>>(in, z, out);
+  return cudaGetLastError();
+}
+
 cudaError_t launch_rhat(const RhatInput& in, double* out, cudaStream_t s) {
   if (in.n <= 0) return cudaSuccess;
   const int blk = 128;

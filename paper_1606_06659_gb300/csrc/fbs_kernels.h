@@ -53,6 +53,9 @@ struct RhatInput {
   const float* mf[FBS_MAX_RHAT_CHAINS];
 };
 cudaError_t launch_rhat(const RhatInput& in, double* out, cudaStream_t s);
+// Pooled posterior mean, sd and the interval mean -/+ z sd of n parameters from
+// the same inputs as launch_rhat (C >= 1): out [4][n] = mean, sd, lo, hi.
+cudaError_t launch_estimates(const RhatInput& in, double z, double* out, cudaStream_t s);
 
 // learned proposal (fbs_learned.cu)
 // Training control block in device memory (one Adam step per captured replay).

@@ -99,7 +99,7 @@ __global__ void __launch_bounds__(kTcThreads) k_proposal_tc(ModelConst mc, DevPt
   tc_smem_layout(mc.L, &off_a);
   if (threadIdx.x == 0) s_abort = 0;
   TcBlock c;
-  tc_begin(c, bars, &tmem_slot, img_g, sm, t.bytes);
+  tc_begin(c, bars, &tmem_slot, img_g, sm, t.bytes, p.tc_polls);
   if (!c.w_ok) s_abort = 1;
   __syncthreads();
   for (int tile = blockIdx.x; tile < ntiles && !s_abort; tile += gridDim.x) {

@@ -65,6 +65,57 @@ int scratch_address(double** out) {
   return FBS_OK;
 }
 
+// Writes the call's whole hyperparameter block into the scratch (the array keeps
+// the previous call's contents): zero, then phi, w_nu, waux_nu and the running
+// phi moments from the caller's arrays and the run fields from the arguments,
+// which a launch passes by value; clears the counters.  One block.
+__global__ void k_noalloc_begin(Hyper* hy, unsigned long long* cnt, const double* __restrict__ hyp,
+                                const double* __restrict__ m_phi, const double* __restrict__ q_phi,
+                                int P, long long it, long long n_mom, long long burnin) {
+  const int tid = threadIdx.x;
+  unsigned long long* w = reinterpret_cast<unsigned long long*>(hy);
+  for (int i = tid; i < (int)(sizeof(Hyper) / 8); i += blockDim.x) w[i] = 0ull;
+  if (tid < FBS_NUM_COUNTERS) cnt[tid] = 0ull;
+  __syncthreads();
+  if (tid < P) {
+    hy->phi[tid] = hyp[tid];
+    if (m_phi) {
+      hy->m_phi[tid] = m_phi[tid];
+      hy->q_phi[tid] = q_phi[tid];
+    }
+  }
+  if (tid == 0) {
+    hy->w_nu = hyp[P];
+    hy->waux_nu = hyp[P + 1];
+    hy->it = it - 1;
+    hy->n_mom = n_mom;
+    hy->burnin = burnin;
+    hy->tune_start = burnin / 2;
+    hy->thin = 1;
+    hy->trace_cap = 0;
+  }
+}
+
+// Copies the new phi, w_nu, waux_nu (and the phi moments) back to the caller's
+// arrays and, when status is not null, the flags word and this call's counters.
+__global__ void k_noalloc_end(const Hyper* hy, const unsigned long long* cnt, double* hyp,
+                              double* m_phi, double* q_phi, int P, unsigned long long* status) {
+  const int tid = threadIdx.x;
+  if (tid < P) {
+    hyp[tid] = hy->phi[tid];
+    if (m_phi) {
+      m_phi[tid] = hy->m_phi[tid];
+      q_phi[tid] = hy->q_phi[tid];
+    }
+  }
+  if (tid == 0) {
+    hyp[P] = hy->w_nu;
+    hyp[P + 1] = hy->waux_nu;
+    if (status) status[0] = hy->flags;
+  }
+  if (status && tid < FBS_NUM_COUNTERS) status[1 + tid] = cnt[tid];
+}
+
 }  // namespace
 
 extern "C" {
@@ -79,6 +130,10 @@ int fbs_sweep_noalloc(const fbs_sweep_args* a) {
     return fail_na(FBS_E_ARG, "G exceeds FBS_NOALLOC_MAX_GENES, the size of the static scratch");
   if (a->it < 1 || a->burnin < 0 || a->n_mom < 0)
     return fail_na(FBS_E_ARG, "need it >= 1, burnin >= 0, n_mom >= 0");
+  // n_mom counts post-burn-in draws folded in before iteration it: at most
+  // it - 1 - burnin of them exist
+  if (a->n_mom > (a->it - 1 > a->burnin ? a->it - 1 - a->burnin : 0))
+    return fail_na(FBS_E_ARG, "n_mom exceeds the post-burn-in iterations before it");
   if (a->step_out_max < 0 || a->shrink_max < 0)
     return fail_na(FBS_E_ARG, "step_out_max and shrink_max must be >= 0");
   if (!a->X || !a->h || !a->priors.c || !a->priors.s)
@@ -177,35 +232,17 @@ int fbs_sweep_noalloc(const fbs_sweep_args* a) {
 
   cudaStream_t s = (cudaStream_t)a->stream;
   const int P = mc.P;
-  // The array keeps the previous call's contents: rewrite the hyperparameter
-  // block and clear the counters before the kernels read them.
-  Hyper hy;
-  memset(&hy, 0, sizeof(hy));
-  hy.it = a->it - 1;
-  hy.n_mom = a->n_mom;
-  hy.burnin = a->burnin;
-  hy.tune_start = a->burnin / 2;
-  hy.thin = 1;
-  hy.trace_cap = 0;
-  NA_CUDA(cudaMemcpyAsync(d_hyp, &hy, sizeof(Hyper), cudaMemcpyHostToDevice, s));
-  NA_CUDA(cudaMemcpyAsync(d_hyp->phi, a->hyp, (size_t)P * 8, cudaMemcpyDeviceToDevice, s));
-  NA_CUDA(cudaMemcpyAsync(&d_hyp->w_nu, a->hyp + P, 2 * 8, cudaMemcpyDeviceToDevice, s));
-  if (mom) {
-    NA_CUDA(cudaMemcpyAsync(d_hyp->m_phi, a->m_phi, (size_t)P * 8, cudaMemcpyDeviceToDevice, s));
-    NA_CUDA(cudaMemcpyAsync(d_hyp->q_phi, a->q_phi, (size_t)P * 8, cudaMemcpyDeviceToDevice, s));
-  }
-  NA_CUDA(cudaMemsetAsync(d_cnt, 0, FBS_NUM_COUNTERS * sizeof(unsigned long long), s));
-
+  double* m_phi = mom ? a->m_phi : nullptr;
+  double* q_phi = mom ? a->q_phi : nullptr;
+  k_noalloc_begin<<<1, 64, 0, s>>>(d_hyp, d_cnt, a->hyp, m_phi, q_phi, P, a->it, a->n_mom,
+                                   a->burnin);
+  NA_CUDA(cudaGetLastError());
   NA_CUDA(prepare_gene_kernel(N, kNoAllocBlock));
   NA_CUDA(launch_gene(mc, p, kNoAllocBlock, s));
   NA_CUDA(launch_hyper(mc, p, (G + kNoAllocBlock - 1) / kNoAllocBlock, s));
-
-  NA_CUDA(cudaMemcpyAsync(a->hyp, d_hyp->phi, (size_t)P * 8, cudaMemcpyDeviceToDevice, s));
-  NA_CUDA(cudaMemcpyAsync(a->hyp + P, &d_hyp->w_nu, 2 * 8, cudaMemcpyDeviceToDevice, s));
-  if (mom) {
-    NA_CUDA(cudaMemcpyAsync(a->m_phi, d_hyp->m_phi, (size_t)P * 8, cudaMemcpyDeviceToDevice, s));
-    NA_CUDA(cudaMemcpyAsync(a->q_phi, d_hyp->q_phi, (size_t)P * 8, cudaMemcpyDeviceToDevice, s));
-  }
+  k_noalloc_end<<<1, 64, 0, s>>>(d_hyp, d_cnt, a->hyp, m_phi, q_phi, P,
+                                 reinterpret_cast<unsigned long long*>(a->status));
+  NA_CUDA(cudaGetLastError());
   return FBS_OK;
 }
 

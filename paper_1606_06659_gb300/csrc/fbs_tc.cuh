@@ -133,14 +133,15 @@ __device__ __forceinline__ void store_split8(uint8_t* base, int kin, int r, int 
   *(uint4*)(base + canon_off(r, kin + c0, 2 * kin)) = make_uint4(l[0], l[1], l[2], l[3]);
 }
 
-constexpr unsigned kTcWaitLimit = 1u << 24;  // try_wait polls before a wait gives up
+constexpr unsigned kTcWaitLimit = kTcWaitPolls;  // polls of a drain wait before it gives up
 
 __device__ __forceinline__ uint32_t smem_u32(const void* ptr) {
   return (uint32_t)__cvta_generic_to_shared(ptr);
 }
 
-__device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity) {
-  for (unsigned i = 0; i < kTcWaitLimit; ++i) {
+__device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity,
+                                          unsigned limit = kTcWaitLimit) {
+  for (unsigned i = 0; i < limit; ++i) {
     uint32_t ok;
     asm volatile(
         "{\n\t.reg .pred P;\n\t"
@@ -276,16 +277,20 @@ constexpr uint32_t kTmemCols = 128;  // D1 at columns 0..63, D2 at 64..127, D3 a
 // image, MMA completion), the completion phase and the wait outcomes.
 struct TcBlock {
   uint32_t tmem, bar_w, bar_m, ph;
+  unsigned polls;  // polls of each wait of the pass before it gives up
   bool w_ok, pending;
 };
 
 // Barriers, 128 tensor-memory columns and the weight image (one bulk copy of
 // img_bytes into sm), by a block of 128 threads.  bars, tmem_slot: the block's
-// static shared words.  Every thread returns with c.w_ok = its wait for the
-// image succeeded.
+// static shared words; polls: the bound of every wait of the pass (the drain
+// waits of tc_end always allow kTcWaitLimit polls).  Every thread returns with
+// c.w_ok = its wait for the image succeeded.
 __device__ __forceinline__ void tc_begin(TcBlock& c, uint64_t* bars, uint32_t* tmem_slot,
-                                         const uint8_t* img_g, uint8_t* sm, int img_bytes) {
+                                         const uint8_t* img_g, uint8_t* sm, int img_bytes,
+                                         unsigned polls) {
   const int tid = threadIdx.x;
+  c.polls = polls;
   c.bar_w = smem_u32(&bars[0]);
   c.bar_m = smem_u32(&bars[1]);
   c.ph = 0;
@@ -316,12 +321,12 @@ __device__ __forceinline__ void tc_begin(TcBlock& c, uint64_t* bars, uint32_t* t
         "l"(img_g), "r"((uint32_t)img_bytes), "r"(c.bar_w)
         : "memory");
   }
-  c.w_ok = mbar_wait(c.bar_w, 0);
+  c.w_ok = mbar_wait(c.bar_w, 0, c.polls);
 }
 
 // Frees the tensor memory.  After a wait that gave up (aborted) it first sets
-// kFlagTimeout in *flags and waits again, with the same bound, for the copy and
-// the MMAs still in flight.
+// kFlagTimeout in *flags and waits again, up to kTcWaitLimit polls, for the copy
+// and the MMAs still in flight, so that none of them outlives the block.
 __device__ __forceinline__ void tc_end(TcBlock& c, bool aborted, unsigned* flags) {
   if (aborted) {
     if (threadIdx.x == 0) atomicOr(flags, kFlagTimeout);
@@ -383,7 +388,7 @@ __device__ __forceinline__ bool tc_tile(TcBlock& c, const ModelConst& mc, const 
       umma_commit(c.bar_m);
     }
     c.pending = true;
-    if (!mbar_wait(c.bar_m, c.ph)) *s_abort = 1;
+    if (!mbar_wait(c.bar_m, c.ph, c.polls)) *s_abort = 1;
     else c.pending = false;
     c.ph ^= 1u;
     tc_fence_after();

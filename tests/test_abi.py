@@ -98,7 +98,10 @@ def test_null_handles_are_refused_without_cuda():
         lib.fbs_batch_three_level(None, None, None),
         lib.fbs_batch_top_level(None, None, None, None, None, 0, None, None, None),
         lib.fbs_proposal_fused(None, 1),
+        lib.fbs_proposal_wait_limit(None, 0),
         lib.fbs_proposal_mode(None, 1),
+        lib.fbs_estimates(None, None),
+        lib.fbs_estimates_pooled(0, None, None),
     ]
     assert all(rc == fbs.FBS_E_ARG for rc in checks), checks
 
@@ -115,3 +118,32 @@ def test_bench_ess_matches_oracle_ess():
     got = bench.geyer_ess(x)
     want = [oracle.ess(x[:, i]) for i in range(3)]
     np.testing.assert_allclose(got, want, rtol=1e-10)
+
+
+def test_estimates_argument_checks_without_cuda():
+    """fbs_estimates_pooled refuses a bad chain count, a missing output struct,
+    NULL handles and a non-positive z before touching the device."""
+    import ctypes as C
+    lib = fbs.load_library()
+    o = fbs.EstimatesOut()
+    o.z = 1.96
+    hs = (C.c_void_p * 2)(None, None)
+    assert lib.fbs_estimates_pooled(2, hs, C.byref(o)) == fbs.FBS_E_ARG
+    assert lib.fbs_estimates_pooled(fbs.FBS_MAX_RHAT_CHAINS + 1, hs, C.byref(o)) == fbs.FBS_E_ARG
+    o.z = 0.0
+    assert lib.fbs_estimates_pooled(1, hs, C.byref(o)) == fbs.FBS_E_ARG
+    o.z = float("nan")
+    assert lib.fbs_estimates_pooled(1, hs, C.byref(o)) == fbs.FBS_E_ARG
+    assert fbs.FBS_E_SLICE_CAP == -4
+
+
+def test_noalloc_rejects_inconsistent_moment_count_without_cuda():
+    """fbs_sweep_noalloc refuses n_mom above the post-burn-in iterations before
+    `it` (it - 1 - burnin) before touching the device."""
+    from paper_1606_06659_gb300 import synthetic
+    dev = dict(y=1, T=1, eps=1, w_eps=1, waux_eps=1, beta=1, w_beta=1, waux_beta=1, gam=1, hyp=1)
+    for it, burnin, n_mom in [(3, 1, 2), (2, 5, 1), (1, 0, 1)]:
+        with pytest.raises(fbs.FbsError) as e:
+            fbs.sweep_noalloc(np.ones((2, 1)), np.zeros(2), synthetic.default_priors(1), seed=1,
+                              it=it, burnin=burnin, n_mom=n_mom, G=10, **dev)
+        assert e.value.code == fbs.FBS_E_ARG and "n_mom" in str(e.value)

@@ -241,6 +241,16 @@ int fbs_counters(fbs_handle* h, int64_t* out);
  * chain advances as with fbs_run.  Synchronous. */
 int fbs_profile(fbs_handle* h, int64_t n_iter, int64_t burnin, int64_t thin, double* ms);
 
+/* Throughput of the arithmetic pipes the sweep kernels use, measured on the
+ * current device by this library's own kernels (every SM full, 8 independent
+ * dependency chains per thread, best of 3 launches timed with CUDA events):
+ * out[0] FP32 fused multiply-adds/s, out[1] ex2.approx/s and out[2] lg2.approx/s
+ * (the MUFU base-2 exponential and logarithm), out[3] 32-bit integer
+ * multiply-high/s (the Philox rounds), out[4] FP64 fused multiply-adds/s, each
+ * counted per lane.  Takes a few milliseconds; changes no clock or other device
+ * setting.  These are the denominators of the sweep's arithmetic roofline. */
+int fbs_measure_peaks(double* out);
+
 /* Philox uniforms exactly as the sampler draws them: out[i*n_k + k] is uniform
  * k0+k of variable index0+i of `stream` at iteration `iter` of chain `chain`,
  * generated on the device.  out is a host array of n_index*n_k doubles. */

@@ -30,7 +30,7 @@ _lib = None
 STREAM_EPS, STREAM_GAMMA, STREAM_NU, STREAM_TAU = 1, 2, 3, 4
 STREAM_BETA, STREAM_THETA, STREAM_SIGMA, STREAM_TEST = 5, 6, 7, 200
 
-CFLAGS = ["-O2", "-std=c11", "-ffp-contract=off", "-fno-fast-math", "-fPIC", "-shared"]
+CFLAGS = ["-O2", "-std=c11", "-ffp-contract=off", "-fno-fast-math", "-fPIC", "-shared", "-fopenmp"]
 
 
 def build(src: str = _SRC, out: str = _LIB_PATH, defines=()) -> str:
@@ -92,6 +92,10 @@ def _declare(lib):
     pM, pS, pO = C.POINTER(Model), C.POINTER(State), C.POINTER(Opts)
     pMo, pCn = C.POINTER(Moments), C.POINTER(Counters)
     lib.orc_philox4x32_10.argtypes = [C.POINTER(u32), C.POINTER(u32), C.POINTER(u32)]
+    lib.orc_set_threads.argtypes = [C.c_int]
+    lib.orc_set_threads.restype = None
+    lib.orc_get_threads.argtypes = []
+    lib.orc_get_threads.restype = C.c_int
     lib.orc_uniform.argtypes = [u64, u32, u32, u32, u32, u32]
     lib.orc_uniform.restype = d
     lib.orc_normal.argtypes = [u64, u32, u32, u32, u32, u32]
@@ -141,6 +145,15 @@ def load(path: str | None = None):
 def _pd(a: np.ndarray):
     assert a.dtype == np.float64 and a.flags.c_contiguous
     return a.ctypes.data_as(_PD)
+
+
+def set_threads(n: int, lib=None) -> int:
+    """Host threads (OpenMP) of the oracle's per-gene loops in this process;
+    returns the previous number.  The states do not depend on it."""
+    lib = lib or load()
+    old = lib.orc_get_threads()
+    lib.orc_set_threads(int(n))
+    return old
 
 
 # --------------------------------------------------------------------------- RNG helpers

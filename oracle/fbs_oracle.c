@@ -386,21 +386,46 @@ static double orc_f_nu(double nu, const void* vctx) {
   return orc_logf_nu_ctx(nu, (const orc_nu_ctx*)vctx);
 }
 
+/* Host threads of the per-gene loops of steps 1, 2 and 5 (OpenMP, when the
+ * oracle is compiled with it; 1 by default).  Every gene's update reads only
+ * its own state and its own Philox counters, so the states do not depend on
+ * the thread count; each thread counts into its own counters, which are added
+ * up at the end of the loop. */
+static int orc_threads = 1;
+
+void orc_set_threads(int n) { orc_threads = n > 0 ? n : 1; }
+
+int orc_get_threads(void) { return orc_threads; }
+
+static void orc_add_counters(orc_counters* to, const orc_counters* from) {
+  int64_t* a = (int64_t*)to;
+  const int64_t* b = (const int64_t*)from;
+  for (size_t i = 0; i < sizeof(orc_counters) / sizeof(int64_t); ++i) a[i] += b[i];
+}
+
 /* Step 1: in parallel over (g, n), a slice update of every eps_gn. */
 void orc_step_eps(const orc_model* m, orc_state* st, const orc_opts* o, int64_t it,
                   orc_counters* cnt) {
   const int N = m->N;
-  for (int g = 0; g < m->G; ++g) {
-    for (int n = 0; n < N; ++n) {
-      size_t e = (size_t)g * N + n;
-      orc_gene_ctx c = {m, st, g, n};
-      orc_rng r = {o->seed, o->chain, ORC_STREAM_EPS, (uint32_t)e, (uint32_t)it};
-      double x_old = st->eps[e];
-      double x_new = orc_slice(x_old, orc_f_eps, &c, st->w_eps[e], o->step_out_max,
-                               o->shrink_max, &r, &cnt->evals_eps, cnt);
-      st->eps[e] = x_new;
-      orc_tune(&st->w_eps[e], &st->waux_eps[e], it, x_new, x_old, o);
+#pragma omp parallel num_threads(orc_threads) if (orc_threads > 1)
+  {
+    orc_counters loc;
+    memset(&loc, 0, sizeof(loc));
+#pragma omp for schedule(static)
+    for (int g = 0; g < m->G; ++g) {
+      for (int n = 0; n < N; ++n) {
+        size_t e = (size_t)g * N + n;
+        orc_gene_ctx c = {m, st, g, n};
+        orc_rng r = {o->seed, o->chain, ORC_STREAM_EPS, (uint32_t)e, (uint32_t)it};
+        double x_old = st->eps[e];
+        double x_new = orc_slice(x_old, orc_f_eps, &c, st->w_eps[e], o->step_out_max,
+                                 o->shrink_max, &r, &loc.evals_eps, &loc);
+        st->eps[e] = x_new;
+        orc_tune(&st->w_eps[e], &st->waux_eps[e], it, x_new, x_old, o);
+      }
     }
+#pragma omp critical
+    orc_add_counters(cnt, &loc);
   }
 }
 
@@ -412,27 +437,35 @@ void orc_step_gamma(const orc_model* m, orc_state* st, const orc_opts* o, int64_
                     orc_counters* cnt) {
   const int N = m->N;
   const double nu = st->phi[0], tau = st->phi[1];
-  for (int g = 0; g < m->G; ++g) {
-    double ss = 0.0;
-    for (int n = 0; n < N; ++n) {
-      double e = st->eps[(size_t)g * N + n];
-      ss += e * e;
+#pragma omp parallel num_threads(orc_threads) if (orc_threads > 1)
+  {
+    orc_counters loc;
+    memset(&loc, 0, sizeof(loc));
+#pragma omp for schedule(static)
+    for (int g = 0; g < m->G; ++g) {
+      double ss = 0.0;
+      for (int n = 0; n < N; ++n) {
+        double e = st->eps[(size_t)g * N + n];
+        ss += e * e;
+      }
+      double shape = 0.5 * ((double)N + nu);
+      double scale = 0.5 * (ss + nu * tau);
+      if (o->all_slice) {
+        orc_gam_ctx c = {shape + 1.0, scale};
+        orc_rng r = {o->seed, o->chain, ORC_STREAM_GAMMA, (uint32_t)g, (uint32_t)it};
+        double x_old = st->gam[g];
+        double x_new = orc_slice(x_old, orc_f_gam, &c, st->w_gam[g], o->step_out_max,
+                                 o->shrink_max, &r, &loc.evals_gam, &loc);
+        st->gam[g] = x_new;
+        orc_tune(&st->w_gam[g], &st->waux_gam[g], it, x_new, x_old, o);
+        continue;
+      }
+      double gv = orc_gamma(shape, o->seed, o->chain, ORC_STREAM_GAMMA, (uint32_t)g,
+                            (uint32_t)it, 0, &loc.gamma_caps);
+      st->gam[g] = scale / gv;
     }
-    double shape = 0.5 * ((double)N + nu);
-    double scale = 0.5 * (ss + nu * tau);
-    if (o->all_slice) {
-      orc_gam_ctx c = {shape + 1.0, scale};
-      orc_rng r = {o->seed, o->chain, ORC_STREAM_GAMMA, (uint32_t)g, (uint32_t)it};
-      double x_old = st->gam[g];
-      double x_new = orc_slice(x_old, orc_f_gam, &c, st->w_gam[g], o->step_out_max,
-                               o->shrink_max, &r, &cnt->evals_gam, cnt);
-      st->gam[g] = x_new;
-      orc_tune(&st->w_gam[g], &st->waux_gam[g], it, x_new, x_old, o);
-      continue;
-    }
-    double gv = orc_gamma(shape, o->seed, o->chain, ORC_STREAM_GAMMA, (uint32_t)g,
-                          (uint32_t)it, 0, &cnt->gamma_caps);
-    st->gam[g] = scale / gv;
+#pragma omp critical
+    orc_add_counters(cnt, &loc);
   }
 }
 
@@ -482,15 +515,23 @@ void orc_step_tau(const orc_model* m, orc_state* st, const orc_opts* o, int64_t 
 void orc_step_beta_l(const orc_model* m, orc_state* st, const orc_opts* o, int64_t it, int l,
                      orc_counters* cnt) {
   const int L = m->L;
-  for (int g = 0; g < m->G; ++g) {
-    size_t e = (size_t)g * L + l;
-    orc_gene_ctx c = {m, st, g, l};
-    orc_rng r = {o->seed, o->chain, ORC_STREAM_BETA, (uint32_t)e, (uint32_t)it};
-    double x_old = st->beta[e];
-    double x_new = orc_slice(x_old, orc_f_beta, &c, st->w_beta[e], o->step_out_max,
-                             o->shrink_max, &r, &cnt->evals_beta, cnt);
-    st->beta[e] = x_new;
-    orc_tune(&st->w_beta[e], &st->waux_beta[e], it, x_new, x_old, o);
+#pragma omp parallel num_threads(orc_threads) if (orc_threads > 1)
+  {
+    orc_counters loc;
+    memset(&loc, 0, sizeof(loc));
+#pragma omp for schedule(static)
+    for (int g = 0; g < m->G; ++g) {
+      size_t e = (size_t)g * L + l;
+      orc_gene_ctx c = {m, st, g, l};
+      orc_rng r = {o->seed, o->chain, ORC_STREAM_BETA, (uint32_t)e, (uint32_t)it};
+      double x_old = st->beta[e];
+      double x_new = orc_slice(x_old, orc_f_beta, &c, st->w_beta[e], o->step_out_max,
+                               o->shrink_max, &r, &loc.evals_beta, &loc);
+      st->beta[e] = x_new;
+      orc_tune(&st->w_beta[e], &st->waux_beta[e], it, x_new, x_old, o);
+    }
+#pragma omp critical
+    orc_add_counters(cnt, &loc);
   }
 }
 

@@ -104,6 +104,10 @@ typedef struct {
   int64_t evals_gam, evals_hyp;            /* all-slice variant: gamma_g; tau and sigma_l */
 } orc_counters;
 
+/* ---- host threads of the per-gene loops (OpenMP; default 1) ---- */
+void orc_set_threads(int n);
+int orc_get_threads(void);
+
 /* ---- random numbers ---- */
 void orc_philox4x32_10(const uint32_t ctr[4], const uint32_t key[2], uint32_t out[4]);
 double orc_uniform(uint64_t seed, uint32_t chain, uint32_t stream, uint32_t index,

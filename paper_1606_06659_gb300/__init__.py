@@ -41,7 +41,7 @@ EXPORTED = ("fbs_default_options", "fbs_workspace_bytes", "fbs_init", "fbs_run",
             "fbs_contrast_probs", "fbs_rhat", "fbs_proposal_kinds", "fbs_get_slice_widths",
             "fbs_set_slice_widths", "fbs_batch_three_level", "fbs_batch_top_level",
             "fbs_proposal_fused", "fbs_estimates", "fbs_estimates_pooled",
-            "fbs_proposal_wait_limit")
+            "fbs_proposal_wait_limit", "fbs_measure_peaks")
 NOALLOC_MAX_GENES = 2048 * 128
 
 
@@ -128,6 +128,7 @@ def load_library(path: str = LIB_PATH):
     lib.fbs_counters.argtypes = [vp, _PI64]
     lib.fbs_profile.argtypes = [vp, i64, i64, i64, _PD]
     lib.fbs_uniforms.argtypes = [u64, u32, u32, u32, i32, u32, u32, i32, _PD]
+    lib.fbs_measure_peaks.argtypes = [_PD]
     lib.fbs_sweep_noalloc.argtypes = [C.POINTER(SweepArgs)]
     lib.fbs_batch_init.argtypes = [C.POINTER(vp), C.c_int, C.POINTER(Dataset), C.POINTER(Options),
                                    vp]
@@ -205,6 +206,18 @@ def uniforms(seed, chain, stream, index0, n_index, it, k0, n_k) -> np.ndarray:
     _check(load_library().fbs_uniforms(seed, chain, stream, index0, n_index, it, k0, n_k,
                                        _pd(out)))
     return out
+
+
+PEAK_NAMES = ("ffma", "ex2", "lg2", "imulhi", "dfma")
+
+
+def measure_peaks() -> dict:
+    """Measured throughput of the arithmetic pipes on the current device
+    (instructions per second summed over lanes): FP32 FMA, MUFU ex2 and lg2,
+    32-bit multiply-high, FP64 FMA (fbs_measure_peaks)."""
+    out = np.zeros(len(PEAK_NAMES))
+    _check(load_library().fbs_measure_peaks(_pd(out)))
+    return dict(zip(PEAK_NAMES, (float(v) for v in out)))
 
 
 def sweep_noalloc(X, h, priors, *, seed, it, burnin, n_mom=0, chain=0, step_out_max=100,

@@ -14,7 +14,8 @@ underestimate it, while each oracle chain spans more than 10 of them.  Every hyp
 For beta only parameters whose oracle effective sample size is at least 100
 are compared (below that the MCSE estimate itself is unreliable); among them at
 most 1% may exceed 4 MCSE (chance alone gives about 0.1%), and none of the well
-mixed ones (oracle ESS at least 1000) may exceed 6 MCSE.  A systematic error
+mixed ones (oracle ESS at least 1000) may exceed the t(15) quantile of a
+familywise level of 1e-3 (the MCSE of each side comes from 16 chain means).  A systematic error
 shows up in the fraction; a lone large z of a slowly mixing, skewed parameter
 in short oracle chains does not indicate one."""
 import multiprocessing as mp
@@ -74,7 +75,16 @@ def pool():
 
 
 def _compare(a, b, ess, label):
+    """z = difference / hypot of the two sides' standard errors of the chain
+    means.  With 16 chains per side each standard error has 15 degrees of
+    freedom, so z has heavier tails than a normal variate: a gross error of a
+    single well-mixed beta_gl is flagged beyond the t(15) quantile of a
+    familywise level of 1e-3 over the compared parameters (about 9.5 for 10^4);
+    a systematic error shows in the fraction beyond 4 (t(15): 0.1% by chance)."""
+    from scipy import stats
     ok, well = ess >= 100, ess >= 1000
+    n_well = max(2 * int(well.sum()), 1)
+    z_max = float(stats.t.isf(0.5e-3 / n_well, df=N_GPU_CHAINS - 1))
     for m in ("m1", "m2"):
         z = np.abs(a["phi"][m] - b["phi"][m]) / np.hypot(a["phi"][m + "_se"], b["phi"][m + "_se"])
         assert np.all(z < 4.0), (label, "phi", m, z)
@@ -84,7 +94,7 @@ def _compare(a, b, ess, label):
         info = (label, "beta", m, "worst (gene, l)", tuple(int(v) for v in worst),
                 float(z[worst]), "ess", float(ess[worst]))
         assert np.mean(z[ok] > 4.0) <= 0.01, info + (float(np.mean(z[ok] > 4.0)),)
-        assert np.all(z[well] < 6.0), info
+        assert np.all(z[well] < z_max), info + (z_max,)
 
 
 _ORACLE_RUNS = {}

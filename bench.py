@@ -60,7 +60,8 @@ def parse():
     ap.add_argument("--steps", type=int, default=10)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=("ours", "reference"), default="ours")
-    ap.add_argument("--form", choices=("f64", "f64_all_slice", "f32", "learned"),
+    ap.add_argument("--form", choices=("f64", "f64_all_slice", "f32", "learned", "learned_a02",
+                                       "learned_cfg4"),
                     default="learned")
     ap.add_argument("--forms", choices=("all", "headline"), default="all",
                     help="run the configured job (ESS) for every form or only the headline one")
@@ -104,6 +105,58 @@ NET_FLOP_PER_GENE = 2 * (21 * 64 + 64 * 64 + 64 * 20)
 MMA_FLOP_PER_GENE = 2 * 3 * (32 * 64 + 64 * 64 + 64 * 32)
 # FP64 peak from unit counts and clock: 152 SMs x 2 DFMA/clk x 2 flop x 2.07 GHz
 FP64_PEAK_TFLOPS = 152 * 2 * 2 * 2.07e9 / 1e12
+
+
+# Algorithmic arithmetic per log-density evaluation of the FP32 slice updates,
+# counted from EpsDensityF and BetaDensityFT (csrc/fbs_gene_f32.cu): an eps
+# evaluation is 19 FP32 operations (the difference to x0, the e^z - 1 - z series
+# of 8 FMA and 2 multiplies, the rate carried to the point, the quadratic prior
+# term, the comparison with the level); a beta evaluation is 6 plus 13 per value
+# class of its column (z = v d, the series, the class's two terms).  Every slice
+# update adds one lg2 (the level log U) and the Philox blocks of its uniforms:
+# 20 multiply-high per block (2 per round, 10 rounds), one block per 4 uniforms,
+# 3 uniforms plus one per shrinkage proposal (bounded here by one per evaluation).
+F32_OPS_EPS_EVAL = 19
+F32_OPS_BETA_EVAL_BASE, F32_OPS_BETA_EVAL_PER_CLASS = 6, 13
+
+
+def class_counts(X):
+    """Distinct non-zero values of every column of X (the beta update's classes)."""
+    X = np.asarray(X)
+    return [len(set(v for v in X[:, l] if v != 0.0)) for l in range(X.shape[1])]
+
+
+def alu_roofline(evals, N, G, L, X, ms_gene, peaks, precision):
+    """Arithmetic roofline of the per-gene kernels of one sweep: the device-counted
+    evaluations of the sweep times the algorithmic operations per evaluation,
+    over the kernels' time inside the replayed graph, against each pipe's
+    throughput measured by fbs_measure_peaks.  The bound is the pipe with the
+    largest fraction."""
+    t = ms_gene / 1e3
+    if precision == "f64":
+        flop = (evals["evals_eps"] + evals["evals_beta"] + evals["evals_gam"]) * FP64_FLOP_PER_EVAL
+        peak = 2.0 * peaks["dfma"]
+        return {"bound": "alu", "pipe": "fp64", "achieved": flop / t / 1e12,
+                "peak": peak / 1e12, "unit": "TFLOP/s (FP64)", "frac": flop / t / peak,
+                "flop_per_eval": FP64_FLOP_PER_EVAL,
+                "peak_source": "measured (fbs_measure_peaks, FP64 FMA x 2)"}
+    cls = class_counts(X)
+    beta_ops = F32_OPS_BETA_EVAL_BASE + F32_OPS_BETA_EVAL_PER_CLASS * float(np.mean(cls))
+    updates = (N + L) * G
+    ev = evals["evals_eps"] + evals["evals_beta"]
+    pipes = {
+        "fp32": (F32_OPS_EPS_EVAL * evals["evals_eps"] + beta_ops * evals["evals_beta"],
+                 peaks["ffma"]),
+        "mufu": (float(updates), peaks["lg2"]),
+        "imul_hi": (5.0 * (3.0 * updates + ev), peaks["imulhi"]),
+    }
+    out = {k: {"ops_per_sweep": ops, "achieved_per_s": ops / t, "peak_per_s": pk,
+               "frac": ops / t / pk} for k, (ops, pk) in pipes.items()}
+    top = max(out, key=lambda k: out[k]["frac"])
+    return {"bound": "alu", "pipe": top, "achieved": out[top]["achieved_per_s"] / 1e12,
+            "peak": out[top]["peak_per_s"] / 1e12, "unit": "Tops/s", "frac": out[top]["frac"],
+            "pipes": out, "peak_source": "measured (fbs_measure_peaks)",
+            "ops_per_eval": {"eps": F32_OPS_EPS_EVAL, "beta": beta_ops}}
 
 
 def bytes_per_gene(N, L, precision="f64"):
@@ -180,26 +233,70 @@ def measured_peaks():
         return 6800.0, "fallback"
 
 
-def cpu_baseline(data, seconds, G_full):
-    """The CPU oracle as it stands, single-threaded, on a gene sample of the same
-    workload; iterations/s scaled to the full G (one sweep costs O(G))."""
+def host_cpu():
+    """Core count (the threads this process may use) and CPU model of this host."""
+    cores = len(os.sched_getaffinity(0)) if hasattr(os, "sched_getaffinity") else os.cpu_count()
+    model = ""
+    try:
+        out = subprocess.run(["lscpu"], capture_output=True, text=True, timeout=10).stdout
+        for ln in out.splitlines():
+            if ln.split(":")[0].strip() in ("Model name", "Model"):
+                model = ln.split(":", 1)[1].strip()
+                if ln.startswith("Model name"):
+                    break
+    except (OSError, subprocess.SubprocessError):
+        pass
+    if not model:
+        try:
+            with open("/proc/cpuinfo") as f:
+                for ln in f:
+                    if ln.lower().startswith(("model name", "cpu part")):
+                        model = ln.split(":", 1)[1].strip()
+                        break
+        except OSError:
+            pass
+    import platform
+    return cores, f"{model or 'unknown'} ({platform.machine()})"
+
+
+def oracle_sweep_rate(data, seconds, threads, G_s=None, min_sweeps=2):
+    """Sweeps per second of the CPU oracle as it stands on `threads` host threads
+    (its per-gene loops under OpenMP), over the full workload or its first G_s
+    genes, burn-in sweeps for about `seconds` (at least min_sweeps)."""
     import oracle
+    y = data["y"] if G_s is None else data["y"][:G_s]
+    old = oracle.set_threads(threads)
+    try:
+        ch = oracle.Chain(y, data["X"], data["h"], data["priors"], seed=7, burnin=10000,
+                          tune_start=5000).init_default()
+        ch.sweep()   # first touch of the state
+        n, t0 = 0, time.perf_counter()
+        while True:
+            ch.sweep()
+            n += 1
+            el = time.perf_counter() - t0
+            if el >= seconds and n >= min_sweeps:
+                break
+    finally:
+        oracle.set_threads(old)
+    return n / el, n, el
+
+
+def cpu_baseline(data, seconds, G_full):
+    """The CPU oracle as it stands on this host's cores: single-threaded on a
+    gene sample (one sweep costs O(G), so the rate is scaled to the full G) and
+    on every core over the full workload (OpenMP over genes), iterations/s each.
+    `value` is the all-core rate."""
+    cores, model = host_cpu()
     G_s = 2000
-    sub = {k: data[k] for k in ("X", "h", "priors")}
-    sub["y"] = data["y"][:G_s]
-    ch = oracle.Chain(sub["y"], sub["X"], sub["h"], sub["priors"], seed=7, burnin=10000,
-                      tune_start=5000).init_default()
-    n, t0 = 0, time.perf_counter()
-    while True:
-        ch.sweep()
-        n += 1
-        el = time.perf_counter() - t0
-        if el >= seconds:
-            break
-    per_sweep_full = el / n * (G_full / G_s)
-    return {"value": 1.0 / per_sweep_full, "unit": "iters/s", "cores": 1, "kind": "oracle",
-            "sample": f"{n} oracle sweeps over the first {G_s} of {G_full} genes (burn-in, "
-                      f"{el:.1f} s), time scaled by G/{G_s}"}
+    r1, n1, t1 = oracle_sweep_rate(data, seconds / 2, 1, G_s=G_s)
+    r1 *= G_s / G_full
+    rn, nn, tn = oracle_sweep_rate(data, seconds / 2, cores)
+    return {"value": rn, "unit": "iters/s", "cores": cores, "kind": "oracle", "cpu": model,
+            "single_thread": r1, "all_cores": rn,
+            "sample": f"all cores: {nn} full oracle sweeps of G={G_full} ({tn:.1f} s of burn-in "
+                      f"sweeps); one core: {n1} sweeps over the first {G_s} genes ({t1:.1f} s), "
+                      f"scaled by G/{G_s}"}
 
 
 # --------------------------------------------------------------------------- reference arm
@@ -217,33 +314,40 @@ def job_rate(units_per_rank, seconds, world, device):
 
 
 def run_reference(args, rank):
+    """The oracle as it stands, on every host core, timed over real full-size
+    sweeps of the paper-scale workload: each step is one sweep of all G genes."""
     if rank != 0:
         return
     from paper_1606_06659_gb300 import synthetic
+    import oracle
     data = synthetic.make_config(CFG)
     G = data["spec"]["G"]
-    import oracle
-    G_s = 1000
-    ch = oracle.Chain(data["y"][:G_s], data["X"], data["h"], data["priors"], seed=7,
-                      burnin=10000, tune_start=5000).init_default()
-    for _ in range(args.warmup):
-        ch.sweep()
-    times = []
-    for _ in range(args.steps):
-        t0 = time.perf_counter()
-        ch.sweep()
-        times.append(time.perf_counter() - t0)
-    per_sweep_full = statistics.mean(times) * G / G_s
-    value = 1.0 / per_sweep_full
+    cores, model = host_cpu()
+    old = oracle.set_threads(cores)
+    try:
+        ch = oracle.Chain(data["y"], data["X"], data["h"], data["priors"], seed=7,
+                          burnin=10000, tune_start=5000).init_default()
+        for _ in range(args.warmup):
+            ch.sweep()
+        times = []
+        for _ in range(args.steps):
+            t0 = time.perf_counter()
+            ch.sweep()
+            times.append(time.perf_counter() - t0)
+    finally:
+        oracle.set_threads(old)
+    per_sweep = statistics.mean(times)
+    value = 1.0 / per_sweep
+    sample = (f"{args.steps} timed full sweeps (G={G}) after {args.warmup} warm-up sweeps, "
+              f"{cores} threads")
     line = {"impl": "reference", "metric": METRIC, "value": value, "unit": "iters/s",
             "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
-            "ms_per_step": per_sweep_full * 1e3, "higher_is_better": True, "scaling": "weak",
+            "ms_per_step": per_sweep * 1e3, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "f64", "data": "synthetic",
             "config": {"workload": "RNA-seq Gibbs sweep N=16 G=40000 L=5 (paper design)",
-                       "N": 16, "G": G, "L": 5, "step": "one oracle sweep over a gene sample"},
-            "cpu_baseline": {"value": value, "unit": "iters/s", "cores": 1, "kind": "oracle",
-                             "sample": f"each step one sweep over the first {G_s} of {G} "
-                                       f"genes, time scaled by G/{G_s}"},
+                       "N": 16, "G": G, "L": 5, "step": "one full oracle sweep"},
+            "cpu_baseline": {"value": value, "unit": "iters/s", "cores": cores, "kind": "oracle",
+                             "cpu": model, "sample": sample},
             "e2e": {"value": value, "unit": "iters/s", "h2d_bytes_per_step": 0,
                     "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
@@ -306,6 +410,9 @@ FORM_TEXT = {
            "Kahan-compensated FP32 moments",
     "learned": "the f32 form plus the learned beta_g proposal (eta-preserving MH move "
                "before the slice updates of beta_g)",
+    "learned_a02": "as learned, with the calibration threshold 0.2 of configuration 4",
+    "learned_cfg4": "configuration 4 as written: the learned move replaces the slice updates "
+                    "of beta_g; genes below 0.2 acceptance keep the slice sampler",
 }
 PAIR_SWEEPS = 50          # x thin 2 x G = 2e6 training pairs at G = 40000
 TRAIN = {"epochs": 20, "batch": 8192, "lr": 3e-3}
@@ -317,6 +424,12 @@ CALIBRATE_SWEEPS = 100
 # nearly independent draw of beta_g given the log-rates).  The 0.2 of the
 # configured fallback applies where the move replaces the slice updates (mode 2).
 MIN_ACCEPT = 0.01
+# The learned forms of the job: (calibration threshold, mode).  "learned" is the
+# headline; "learned_a02" takes configuration 4's threshold 0.2 with the move
+# added to the slice updates; "learned_cfg4" is configuration 4 as written: the
+# move replaces the slice updates of beta_g, and genes whose acceptance stays
+# below 0.2 fall back to the slice sampler.
+LEARNED_FORMS = {"learned": (MIN_ACCEPT, 1), "learned_a02": (0.2, 1), "learned_cfg4": (0.2, 2)}
 
 
 def new_sampler(fbs, data, y, form, seed, chain, block, **kw):
@@ -380,19 +493,21 @@ def ess_job(fbs, torch, data, y_host, form, seed, chain, block, S, train_epochs)
             phi_reads += 1
             done += n
 
-    if form == "learned":
+    if form in LEARNED_FORMS:
+        min_accept, mode = LEARNED_FORMS[form]
         advance(burnin // 2)
         tt = time.perf_counter()
         smp.proposal_collect(PAIR_SWEEPS, burnin=burnin, thin=2)
         done += 2 * PAIR_SWEEPS
         loss = smp.proposal_train(seed=seed, **dict(TRAIN, epochs=train_epochs))
-        smp.proposal_calibrate(CALIBRATE_SWEEPS, burnin=burnin, min_accept=MIN_ACCEPT)
+        smp.proposal_calibrate(CALIBRATE_SWEEPS, burnin=burnin, min_accept=min_accept)
+        smp.proposal_mode(mode)
         done += CALIBRATE_SWEEPS
         st0 = smp.proposal_stats()
         extra = {"train_pairs": PAIR_SWEEPS * data["y"].shape[0], "train_loss": loss,
                  "collect_train_calibrate_s": time.perf_counter() - tt,
                  "mh_genes": st0["mh_genes"], "prior_genes": st0["prior_genes"],
-                 "min_accept": MIN_ACCEPT}
+                 "min_accept": min_accept, "mode": mode}
     advance(iters)
     ev1.record(stream)
     mom = smp.moments()
@@ -401,7 +516,7 @@ def ess_job(fbs, torch, data, y_host, form, seed, chain, block, S, train_epochs)
     dev_s = ev0.elapsed_time(ev1) / 1e3
     e = smp.beta_ess()
     ess_phi = geyer_ess(smp.trace()["phi"])
-    if form == "learned":
+    if form in LEARNED_FORMS:
         st = smp.proposal_stats()
         extra["accept_rate"] = st["accepted"] / max(1, st["tried"])
         extra["params"] = smp.proposal_params()
@@ -468,25 +583,30 @@ def main():
     burnin, thin = spec["burnin"], spec["thin"]
     forms = {}
     if not args.no_ess:
-        order = (["f64", "f64_all_slice", "f32", "learned"] if args.forms == "all"
-                 else [form])
+        order = (["f64", "f64_all_slice", "f32", "learned", "learned_a02", "learned_cfg4"]
+                 if args.forms == "all" else [form])
         for f in order:
             barrier()
             forms[f] = ess_job(fbs, torch, data, y_host, f, seed, rank, args.block, S,
                                args.train_epochs)
     params = forms.get("learned", {}).pop("params", None)
+    for f in ("learned_a02", "learned_cfg4"):
+        forms.get(f, {}).pop("params", None)
 
     # ---- device-timed throughput: W warm-up + K timed steps of S sweeps
     smp = new_sampler(fbs, data, data["y"], form, seed + 1, rank, args.block)
     tb = args.tune_sweeps // 2
     smp.run(args.tune_sweeps, burnin=tb, thin=thin)   # tune the slice widths (burn-in)
-    if form == "learned":
+    learned = form in LEARNED_FORMS
+    if learned:
         if params is None:
             smp.proposal_collect(PAIR_SWEEPS, burnin=tb, thin=2)
             smp.proposal_train(seed=seed, **dict(TRAIN, epochs=args.train_epochs))
         else:
             smp.proposal_params(set_to=params)
-        smp.proposal_calibrate(CALIBRATE_SWEEPS, burnin=tb, min_accept=MIN_ACCEPT)
+        min_accept, mode = LEARNED_FORMS[form]
+        smp.proposal_calibrate(CALIBRATE_SWEEPS, burnin=tb, min_accept=min_accept)
+        smp.proposal_mode(mode)
     flush = torch.empty(L2_FLUSH_BYTES, dtype=torch.uint8, device="cuda")
     for i in range(args.warmup):
         flush.fill_(i & 0xFF)
@@ -510,8 +630,9 @@ def main():
     value, total_s = job_rate(args.steps * S, total_s, world, "cuda")
     barrier()
 
-    # ---- roofline of the per-gene kernels: direct launches with CUDA events on
-    #      their launching stream
+    # ---- rooflines of the per-gene kernels, timed inside a replayed graph laid
+    #      out like the sweep's (fbs_profile: event-record nodes around each
+    #      kernel, on the kernel's own stream)
     ms_k1, ms_k2, ms_hyper, ms_prop = smp.profile(S, burnin=tb, thin=thin)
     ms_gene = ms_k1 + ms_k2
     peak, peak_kind = measured_peaks()
@@ -522,43 +643,48 @@ def main():
                                                                "evals_nu", "evals_gam",
                                                                "evals_hyp")}
     ev_launch = evals["evals_eps"] + evals["evals_beta"] + evals["evals_gam"]
-    hbm = {"achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
-           "bytes_per_gene": bpg, "genes_per_launch": G, "peak_source": peak_kind}
+    pipe_peaks = fbs.measure_peaks()
     if prec_name == "f64":
-        tflops = ev_launch * FP64_FLOP_PER_EVAL / (ms_gene / 1e3) / 1e12
-        roofline = {"bound": "alu", "achieved": tflops, "peak": FP64_PEAK_TFLOPS,
-                    "unit": "TFLOP/s (FP64)", "frac": tflops / FP64_PEAK_TFLOPS,
-                    "traffic": FP64_TRAFFIC_BYTES,
-                    "kernel": "k_eps_f64 + k_gb_f64", "kernel_ms": ms_gene,
-                    "eps_kernel_ms": ms_k1, "gb_kernel_ms": ms_k2, "hyper_kernel_ms": ms_hyper,
-                    "flop_per_eval": FP64_FLOP_PER_EVAL, "evals_per_launch": ev_launch,
-                    "peak_source": "152 SMs x 2 DFMA/clk x 2 flop x 2.07 GHz", "hbm": hbm}
+        kern = "k_eps_f64 + k_gb_f64"
+        traffic = FP64_TRAFFIC_BYTES
     else:
-        inst = FP32_WARP_INST[form]
+        kern = "k_eps_f32 + " + ("k_gb_net_f32" if learned else "k_gb_f32")
+        traffic = FP32_TRAFFIC_BYTES["learned" if learned else "f32"]
+    # primary: the algorithmic bytes of one sweep's per-gene work (bytes_per_gene
+    # x G) over the two per-gene kernels' time, against the measured HBM copy rate
+    roofline = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
+                "frac": achieved / peak, "traffic": traffic, "kernel": kern,
+                "kernel_ms": ms_gene, "eps_kernel_ms": ms_k1, "gb_kernel_ms": ms_k2,
+                "hyper_kernel_ms": ms_hyper, "critical_path_ms": ms_k2 + max(ms_k1, ms_hyper),
+                "sweep_ms": statistics.mean(step_ms) / S, "bytes_per_gene": bpg,
+                "genes_per_launch": G, "peak_source": peak_kind + " (MEASURED_PEAKS.json hbm_gbs)",
+                "timing": "CUDA event-record nodes around each kernel inside a replayed graph "
+                          "of the sweep (fbs_profile), mean over one segment",
+                "evals_per_launch": ev_launch}
+    roofline["alu"] = alu_roofline(evals, N, G, L, data["X"], ms_gene, pipe_peaks, prec_name)
+    roofline["pipe_peaks_per_s"] = pipe_peaks
+    if prec_name == "f32":
+        inst = FP32_WARP_INST["learned" if learned else "f32"]
         rate = inst / (ms_gene / 1e3)
-        roofline = {"bound": "alu", "achieved": rate, "peak": ISSUE_PEAK_WARP_INST_S,
-                    "unit": "warp-instructions/s", "frac": rate / ISSUE_PEAK_WARP_INST_S,
-                    "traffic": FP32_TRAFFIC_BYTES[form],
-                    "kernel": "k_eps_f32 + " + ("k_gb_net_f32" if form == "learned" else "k_gb_f32"),
-                    "kernel_ms": ms_gene, "eps_kernel_ms": ms_k1, "gb_kernel_ms": ms_k2,
-                    "hyper_kernel_ms": ms_hyper, "warp_instructions_per_sweep": inst,
-                    "evals_per_launch": ev_launch,
-                    "peak_source": "152 SMs x 4 schedulers x 1 warp instruction/clk x 2.07 GHz",
-                    "hbm": hbm}
-        if form == "learned":
-            try:
-                with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
-                    bf16, src = float(json.load(f)["bf16_tflops_sustained"]), "measured"
-            except (OSError, KeyError, ValueError):
-                bf16, src = 1700.0, "fallback"
-            tf = NET_FLOP_PER_GENE * G / (ms_prop / 1e3) / 1e12
-            roofline["proposal"] = {
-                "kernel": "k_proposal_tc", "bound": "tensor", "kernel_ms": ms_prop,
-                "achieved": tf, "peak": bf16, "unit": "TFLOP/s", "frac": tf / bf16,
-                "flop_per_launch": NET_FLOP_PER_GENE * G,
-                "mma_flop_per_launch": MMA_FLOP_PER_GENE * G,
-                "peak_source": src + " bf16 sustained"}
-    st = smp.proposal_stats() if form == "learned" else None
+        roofline["issue"] = {"achieved": rate, "peak": ISSUE_PEAK_WARP_INST_S,
+                             "unit": "warp-instructions/s", "frac": rate / ISSUE_PEAK_WARP_INST_S,
+                             "warp_instructions_per_sweep": inst,
+                             "peak_source": "152 SMs x 4 schedulers x 1 warp instruction/clk "
+                                            "x 2.07 GHz (ncu-counted issued instructions)"}
+    if learned:
+        try:
+            with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+                bf16, src = float(json.load(f)["bf16_tflops_sustained"]), "measured"
+        except (OSError, KeyError, ValueError):
+            bf16, src = 1700.0, "fallback"
+        tf = NET_FLOP_PER_GENE * G / (ms_prop / 1e3) / 1e12
+        roofline["proposal"] = {
+            "kernel": "k_proposal_tc", "bound": "tensor", "kernel_ms": ms_prop,
+            "achieved": tf, "peak": bf16, "unit": "TFLOP/s", "frac": tf / bf16,
+            "flop_per_launch": NET_FLOP_PER_GENE * G,
+            "mma_flop_per_launch": MMA_FLOP_PER_GENE * G,
+            "peak_source": src + " bf16 sustained"}
+    st = smp.proposal_stats() if learned else None
     smp.close()
 
     if rank != 0:
@@ -610,6 +736,10 @@ def main():
                 line["all_slice_vs_exact_draws"] = {
                     k: a[k] / b[k] for k in ("iters_per_s_e2e", "min_ess_per_s",
                                              "median_ess_per_s", "min_phi_ess_per_s")}
+            line["learned_vs_plain_f64"] = {
+                f: {k: forms[f][k] / b[k] for k in ("min_ess_per_s", "p05_ess_per_s",
+                                                    "median_ess_per_s", "min_phi_ess_per_s")}
+                for f in LEARNED_FORMS if f in forms}
     if not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline(data, args.cpu_seconds, G)
     print(json.dumps(line), flush=True)

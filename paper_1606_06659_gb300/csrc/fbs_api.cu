@@ -963,47 +963,85 @@ int fbs_counters(fbs_handle* h, int64_t* out) {
 int fbs_profile(fbs_handle* h, int64_t n_iter, int64_t burnin, int64_t thin, double* ms) {
   if (!h || !ms) return fail(FBS_E_ARG, "handle or ms is NULL");
   if (h->is_view) return fail(FBS_E_ARG, "a batch dataset runs with fbs_batch_run");
-  if (n_iter < 1 || burnin < 0 || thin < 1)
-    return fail(FBS_E_ARG, "need n_iter >= 1, burnin >= 0, thin >= 1");
+  if (n_iter < 1 || n_iter > 4096 || burnin < 0 || thin < 1)
+    return fail(FBS_E_ARG, "need 1 <= n_iter <= 4096, burnin >= 0, thin >= 1");
   int rc = enter(h);
   if (rc) return rc;
   FBS_CUDA(launch_set_run(h->p.hyp, burnin, burnin / 2, thin, h->s));
   const bool f32 = h->prec == FBS_F32;
-  FBS_CUDA(launch_seg_begin(h->p.hyp, h->s));
   const bool learned = f32 && h->pf.prop != nullptr;
-  std::vector<cudaEvent_t> ev((size_t)5 * n_iter);
-  for (auto& x : ev) FBS_CUDA(cudaEventCreate(&x));
+  // n_iter sweeps captured as one graph, laid out as the production segment
+  // (hyperparameter kernel on the second stream, overlapping the next eps
+  // kernel), with an event-record node right before and after every kernel
+  const size_t nev = (size_t)6 * n_iter;
+  std::vector<cudaEvent_t> ev(nev, nullptr);
   cudaError_t e = cudaSuccess;
-  for (int64_t i = 0; i < n_iter && e == cudaSuccess; ++i) {
-    cudaEvent_t* v = &ev[5 * i];
-    cudaEventRecord(v[0], h->s);
-    e = f32 ? launch_eps_f32(h->mc, h->pf, (int)i, h->s) : launch_eps_f64(h->mc, h->p, (int)i, h->s);
-    cudaEventRecord(v[1], h->s);
-    // the network pass alone (the sweep runs it inside the gamma/beta kernel when
-    // blocks have 128 threads): timed for reference, its outputs recomputed there
-    if (e == cudaSuccess && learned)
-      e = launch_proposal_f32(h->mc, h->pf, h->learned->w_image, h->learned->prop, h->s);
-    cudaEventRecord(v[2], h->s);
-    if (e == cudaSuccess)
-      e = f32 ? gb_f32_step(h, (int)i, h->s) : launch_gb_f64(h->mc, h->p, h->block, (int)i, h->s);
-    cudaEventRecord(v[3], h->s);
-    if (e == cudaSuccess) e = launch_hyper(h->mc, h->p, h->nblk, h->s);
-    cudaEventRecord(v[4], h->s);
+  for (auto& x : ev)
+    if (e == cudaSuccess) e = cudaEventCreate(&x);
+  cudaGraph_t graph = nullptr;
+  cudaGraphExec_t exec = nullptr;
+  auto rec = [&](cudaEvent_t x, cudaStream_t st) {
+    if (e == cudaSuccess) e = cudaEventRecordWithFlags(x, st, cudaEventRecordExternal);
+  };
+  if (e == cudaSuccess) e = cudaStreamBeginCapture(h->s, cudaStreamCaptureModeThreadLocal);
+  if (e == cudaSuccess) {
+    e = launch_seg_begin(h->p.hyp, h->s);
+    for (int64_t i = 0; i < n_iter && e == cudaSuccess; ++i) {
+      cudaEvent_t* v = &ev[6 * i];
+      rec(v[0], h->s);
+      if (e == cudaSuccess)
+        e = f32 ? launch_eps_f32(h->mc, h->pf, (int)i, h->s) : launch_eps_f64(h->mc, h->p, (int)i, h->s);
+      rec(v[1], h->s);
+      if (e == cudaSuccess && i > 0) e = cudaStreamWaitEvent(h->s, h->ev_h, 0);
+      rec(v[2], h->s);
+      if (e == cudaSuccess)
+        e = f32 ? gb_f32_step(h, (int)i, h->s) : launch_gb_f64(h->mc, h->p, h->block, (int)i, h->s);
+      rec(v[3], h->s);
+      if (e == cudaSuccess) e = cudaEventRecord(h->ev_g, h->s);
+      if (e == cudaSuccess) e = cudaStreamWaitEvent(h->s2, h->ev_g, 0);
+      rec(v[4], h->s2);
+      if (e == cudaSuccess) e = launch_hyper(h->mc, h->p, h->nblk, h->s2);
+      rec(v[5], h->s2);
+      if (e == cudaSuccess) e = cudaEventRecord(h->ev_h, h->s2);
+    }
+    if (e == cudaSuccess) e = cudaStreamWaitEvent(h->s, h->ev_h, 0);
+    cudaError_t e2 = cudaStreamEndCapture(h->s, &graph);
+    if (e == cudaSuccess) e = e2;
   }
+  if (e == cudaSuccess) e = cudaGraphInstantiate(&exec, graph, 0);
+  if (e == cudaSuccess) e = cudaGraphLaunch(exec, h->s);
   if (e == cudaSuccess) e = cudaStreamSynchronize(h->s);
-  double t[4] = {0.0, 0.0, 0.0, 0.0};  // eps, proposal, gamma/beta, hyperparameters
+  double t[3] = {0.0, 0.0, 0.0};  // eps, gamma/beta, hyperparameters
   for (int64_t i = 0; i < n_iter && e == cudaSuccess; ++i)
-    for (int k = 0; k < 4; ++k) {
+    for (int k = 0; k < 3 && e == cudaSuccess; ++k) {
       float a = 0.f;
-      cudaEventElapsedTime(&a, ev[5 * i + k], ev[5 * i + k + 1]);
+      e = cudaEventElapsedTime(&a, ev[6 * i + 2 * k], ev[6 * i + 2 * k + 1]);
       t[k] += a;
     }
-  for (auto& x : ev) cudaEventDestroy(x);
+  if (exec) cudaGraphExecDestroy(exec);
+  if (graph) cudaGraphDestroy(graph);
+  // the network pass alone (the sweep runs it inside the gamma/beta kernel
+  // when blocks have 128 threads): direct launches, timed for reference; its
+  // outputs are recomputed by the next sweep
+  double t_net = 0.0;
+  if (e == cudaSuccess && learned) {
+    for (int64_t i = 0; i < n_iter && e == cudaSuccess; ++i) {
+      cudaEventRecord(ev[0], h->s);
+      e = launch_proposal_f32(h->mc, h->pf, h->learned->w_image, h->learned->prop, h->s);
+      cudaEventRecord(ev[1], h->s);
+      if (e == cudaSuccess) e = cudaEventSynchronize(ev[1]);
+      float a = 0.f;
+      if (e == cudaSuccess) e = cudaEventElapsedTime(&a, ev[0], ev[1]);
+      t_net += a;
+    }
+  }
+  for (auto& x : ev)
+    if (x) cudaEventDestroy(x);
   FBS_CUDA(e);
   ms[0] = t[0] / (double)n_iter;
-  ms[1] = t[2] / (double)n_iter;
-  ms[2] = t[3] / (double)n_iter;
-  ms[3] = t[1] / (double)n_iter;
+  ms[1] = t[1] / (double)n_iter;
+  ms[2] = t[2] / (double)n_iter;
+  ms[3] = t_net / (double)n_iter;
   return leave(h);
 }
 

@@ -1,0 +1,49 @@
+"""fbs_profile and fbs_measure_peaks: the kernel times that the benchmark's
+roofline divides by are taken inside a replayed graph laid out like the
+sweep's own, so their sum along the critical path fits inside the time of a
+sweep; the profiled sweeps advance the chain exactly as fbs_run does; the pipe
+throughputs are positive and ordered as the hardware's unit counts order them."""
+import numpy as np
+import pytest
+
+import paper_1606_06659_gb300 as fbs
+from paper_1606_06659_gb300 import synthetic
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.mark.parametrize("precision", [fbs.FBS_F64, fbs.FBS_F32])
+def test_profile_times_fit_in_a_sweep_and_advance_the_chain(precision):
+    import torch
+    d = synthetic.make_config(1, G=20000)
+    a = fbs.Sampler(d["y"], d["X"], d["h"], d["priors"], seed=9, precision=precision)
+    b = fbs.Sampler(d["y"], d["X"], d["h"], d["priors"], seed=9, precision=precision)
+    a.run(100, burnin=50)
+    b.run(100, burnin=50)
+    ms = a.profile(100, burnin=50)
+    b.run(100, burnin=50)
+    sa, sb = a.get_state(), b.get_state()
+    for k in ("eps", "beta", "gam", "phi", "w_eps", "w_beta"):
+        assert np.array_equal(sa[k], sb[k]), k
+    assert all(v > 0 for v in ms[:3]) and ms[3] == 0.0
+    # one graph segment of 100 sweeps, timed with events on torch's stream
+    st = torch.cuda.current_stream()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(st)
+    b.run(100, burnin=50)
+    e1.record(st)
+    torch.cuda.synchronize()
+    per_sweep = e0.elapsed_time(e1) / 100
+    # critical path: gamma/beta after max(eps, hyperparameters of the sweep before)
+    assert ms[1] + max(ms[0], ms[2]) <= 1.05 * per_sweep, (ms, per_sweep)
+    a.close()
+    b.close()
+
+
+def test_measured_peaks_are_plausible():
+    p = fbs.measure_peaks()
+    assert set(p) == set(fbs.PEAK_NAMES) and all(v > 0 for v in p.values())
+    # per SM and clock: 128 FP32 lanes, 16 MUFU lanes, 2 FP64 lanes (GB300); the
+    # measured rates must keep that order with wide margins
+    assert p["ffma"] > 4 * p["ex2"] and p["ffma"] > 10 * p["dfma"]
+    assert p["ex2"] > p["dfma"]

@@ -231,16 +231,20 @@ int fbs_count_sums(fbs_handle* h, int64_t* T);
 /* Counters (FBS_CNT_* slots, FBS_NUM_COUNTERS values) to a host array. */
 int fbs_counters(fbs_handle* h, int64_t* out);
 
-/* Runs n_iter (1..4096) iterations as one captured CUDA graph laid out like the
- * graph segments fbs_run replays (the hyperparameter kernel on a second stream,
- * overlapping the next iteration's eps kernel), with an event-record node right
- * before and after every kernel, and writes the mean kernel durations inside
- * that replay in milliseconds to ms[0..3]: the eps kernel, the gamma/beta kernel
- * (with the learned proposal and 128-thread blocks it includes the network pass
- * for its genes), the hyperparameter kernel, and the learned proposal's network
- * pass launched alone afterwards (timed for reference with CUDA events around
- * direct launches; 0 when the handle does not use the proposal).  The chain
- * advances by n_iter iterations as with fbs_run.  Synchronous. */
+/* Runs n_iter (1..4096) iterations as one captured CUDA graph, the same launches
+ * on the same two streams as the graph segments fbs_run replays (the
+ * hyperparameter kernel overlapping the next iteration's eps kernel), with the
+ * sweep kernels' timing probe on: the first thread of every block records the
+ * device's global timer at the block's start and end, so each kernel's time is
+ * the span from its first block's start to its last block's end inside the
+ * replay.  Writes the means in milliseconds to ms[0..4]: the eps kernel, the
+ * gamma/beta kernel (with the learned proposal and 128-thread blocks it
+ * includes the network pass for its genes), the hyperparameter kernel, the
+ * learned proposal's network pass launched alone afterwards (CUDA events around
+ * direct launches; 0 when the handle does not use the proposal), and the
+ * replay's time per iteration (first kernel start to last kernel end over
+ * n_iter).  The chain advances by n_iter iterations exactly as with fbs_run.
+ * Synchronous. */
 int fbs_profile(fbs_handle* h, int64_t n_iter, int64_t burnin, int64_t thin, double* ms);
 
 /* Throughput of the arithmetic pipes the sweep kernels use, measured on the

@@ -390,9 +390,10 @@ class Sampler:
         _check(self.lib.fbs_sync(self.h))
 
     def profile(self, n_iter, burnin=0, thin=1):
-        """Mean per-launch milliseconds: (eps kernel, gamma/beta kernel, hyperparameter
-        kernel, learned-proposal network or 0)."""
-        ms = np.zeros(4)
+        """Mean milliseconds per iteration inside a replayed graph of n_iter sweeps:
+        (eps kernel, gamma/beta kernel, hyperparameter kernel, learned-proposal
+        network launched alone or 0, the replay's time per iteration)."""
+        ms = np.zeros(5)
         _check(self.lib.fbs_profile(self.h, int(n_iter), int(burnin), int(thin), _pd(ms)))
         return tuple(float(v) for v in ms)
 

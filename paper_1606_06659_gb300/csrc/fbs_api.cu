@@ -405,11 +405,11 @@ int sweeps_direct(fbs_handle* h, int64_t n_iter) {
 // the hyperparameter kernel of sweep i runs on a second stream, concurrently
 // with the eps kernel of sweep i+1 (whose conditionals involve no
 // hyperparameter); the gamma/beta kernel of sweep i+1 waits for both.
-cudaError_t capture_segment(fbs_handle* h) {
+cudaError_t capture_sweeps(fbs_handle* h, int n) {
   cudaError_t e = cudaSuccess;
   const bool f32 = h->prec == FBS_F32;
   if ((e = launch_seg_begin(h->p.hyp, h->s)) != cudaSuccess) return e;
-  for (int i = 0; i < h->seg; ++i) {
+  for (int i = 0; i < n; ++i) {
     e = f32 ? launch_eps_f32(h->mc, h->pf, i, h->s) : launch_eps_f64(h->mc, h->p, i, h->s);
     if (e != cudaSuccess) return e;
     if (i > 0 && (e = cudaStreamWaitEvent(h->s, h->ev_h, 0)) != cudaSuccess) return e;
@@ -422,6 +422,8 @@ cudaError_t capture_segment(fbs_handle* h) {
   }
   return cudaStreamWaitEvent(h->s, h->ev_h, 0);
 }
+
+cudaError_t capture_segment(fbs_handle* h) { return capture_sweeps(h, h->seg); }
 
 int ensure_graph(fbs_handle* h) {
   if (h->seg_exec) return FBS_OK;
@@ -968,80 +970,74 @@ int fbs_profile(fbs_handle* h, int64_t n_iter, int64_t burnin, int64_t thin, dou
   int rc = enter(h);
   if (rc) return rc;
   FBS_CUDA(launch_set_run(h->p.hyp, burnin, burnin / 2, thin, h->s));
-  const bool f32 = h->prec == FBS_F32;
-  const bool learned = f32 && h->pf.prop != nullptr;
-  // n_iter sweeps captured as one graph, laid out as the production segment
-  // (hyperparameter kernel on the second stream, overlapping the next eps
-  // kernel), with an event-record node right before and after every kernel
-  const size_t nev = (size_t)6 * n_iter;
-  std::vector<cudaEvent_t> ev(nev, nullptr);
-  cudaError_t e = cudaSuccess;
-  for (auto& x : ev)
-    if (e == cudaSuccess) e = cudaEventCreate(&x);
+  const bool learned = h->prec == FBS_F32 && h->pf.prop != nullptr;
+  // probe slots: 3 kernels per sweep; starts [0, n), ends [n, 2n)
+  const int n = (int)(3 * n_iter);
+  unsigned long long* kt = nullptr;
+  FBS_CUDA(cudaMalloc((void**)&kt, sizeof(unsigned long long) * 2 * (size_t)n));
+  cudaError_t e = cudaMemsetAsync(kt, 0xFF, sizeof(unsigned long long) * n, h->s);
+  if (e == cudaSuccess) e = cudaMemsetAsync(kt + n, 0, sizeof(unsigned long long) * n, h->s);
+  // the sweeps captured exactly as fbs_run's segments, with the probe on
   cudaGraph_t graph = nullptr;
   cudaGraphExec_t exec = nullptr;
-  auto rec = [&](cudaEvent_t x, cudaStream_t st) {
-    if (e == cudaSuccess) e = cudaEventRecordWithFlags(x, st, cudaEventRecordExternal);
-  };
   if (e == cudaSuccess) e = cudaStreamBeginCapture(h->s, cudaStreamCaptureModeThreadLocal);
   if (e == cudaSuccess) {
-    e = launch_seg_begin(h->p.hyp, h->s);
-    for (int64_t i = 0; i < n_iter && e == cudaSuccess; ++i) {
-      cudaEvent_t* v = &ev[6 * i];
-      rec(v[0], h->s);
-      if (e == cudaSuccess)
-        e = f32 ? launch_eps_f32(h->mc, h->pf, (int)i, h->s) : launch_eps_f64(h->mc, h->p, (int)i, h->s);
-      rec(v[1], h->s);
-      if (e == cudaSuccess && i > 0) e = cudaStreamWaitEvent(h->s, h->ev_h, 0);
-      rec(v[2], h->s);
-      if (e == cudaSuccess)
-        e = f32 ? gb_f32_step(h, (int)i, h->s) : launch_gb_f64(h->mc, h->p, h->block, (int)i, h->s);
-      rec(v[3], h->s);
-      if (e == cudaSuccess) e = cudaEventRecord(h->ev_g, h->s);
-      if (e == cudaSuccess) e = cudaStreamWaitEvent(h->s2, h->ev_g, 0);
-      rec(v[4], h->s2);
-      if (e == cudaSuccess) e = launch_hyper(h->mc, h->p, h->nblk, h->s2);
-      rec(v[5], h->s2);
-      if (e == cudaSuccess) e = cudaEventRecord(h->ev_h, h->s2);
-    }
-    if (e == cudaSuccess) e = cudaStreamWaitEvent(h->s, h->ev_h, 0);
+    h->p.ktime = h->pf.ktime = kt;
+    h->p.ktime_n = h->pf.ktime_n = n;
+    e = capture_sweeps(h, (int)n_iter);
+    h->p.ktime = h->pf.ktime = nullptr;
+    h->p.ktime_n = h->pf.ktime_n = 0;
     cudaError_t e2 = cudaStreamEndCapture(h->s, &graph);
     if (e == cudaSuccess) e = e2;
   }
   if (e == cudaSuccess) e = cudaGraphInstantiate(&exec, graph, 0);
   if (e == cudaSuccess) e = cudaGraphLaunch(exec, h->s);
+  std::vector<unsigned long long> t((size_t)2 * n);
+  if (e == cudaSuccess)
+    e = cudaMemcpyAsync(t.data(), kt, sizeof(unsigned long long) * 2 * n, cudaMemcpyDeviceToHost,
+                        h->s);
   if (e == cudaSuccess) e = cudaStreamSynchronize(h->s);
-  double t[3] = {0.0, 0.0, 0.0};  // eps, gamma/beta, hyperparameters
-  for (int64_t i = 0; i < n_iter && e == cudaSuccess; ++i)
-    for (int k = 0; k < 3 && e == cudaSuccess; ++k) {
-      float a = 0.f;
-      e = cudaEventElapsedTime(&a, ev[6 * i + 2 * k], ev[6 * i + 2 * k + 1]);
-      t[k] += a;
-    }
   if (exec) cudaGraphExecDestroy(exec);
   if (graph) cudaGraphDestroy(graph);
+  cudaFree(kt);
+  double span[3] = {0.0, 0.0, 0.0};  // eps, gamma/beta, hyperparameters (ns)
+  unsigned long long first = ~0ull, last = 0ull;
+  for (int i = 0; i < n && e == cudaSuccess; ++i) {
+    if (t[i] == ~0ull || t[n + i] < t[i]) {
+      e = cudaErrorUnknown;  // a probed kernel did not run
+      break;
+    }
+    span[i % 3] += (double)(t[n + i] - t[i]);
+    first = std::min(first, t[i]);
+    last = std::max(last, t[n + i]);
+  }
   // the network pass alone (the sweep runs it inside the gamma/beta kernel
-  // when blocks have 128 threads): direct launches, timed for reference; its
-  // outputs are recomputed by the next sweep
+  // when blocks have 128 threads): direct launches with CUDA events, timed for
+  // reference; its outputs are recomputed by the next sweep
   double t_net = 0.0;
   if (e == cudaSuccess && learned) {
+    cudaEvent_t a = nullptr, b = nullptr;
+    e = cudaEventCreate(&a);
+    if (e == cudaSuccess) e = cudaEventCreate(&b);
     for (int64_t i = 0; i < n_iter && e == cudaSuccess; ++i) {
-      cudaEventRecord(ev[0], h->s);
+      cudaEventRecord(a, h->s);
       e = launch_proposal_f32(h->mc, h->pf, h->learned->w_image, h->learned->prop, h->s);
-      cudaEventRecord(ev[1], h->s);
-      if (e == cudaSuccess) e = cudaEventSynchronize(ev[1]);
-      float a = 0.f;
-      if (e == cudaSuccess) e = cudaEventElapsedTime(&a, ev[0], ev[1]);
-      t_net += a;
+      cudaEventRecord(b, h->s);
+      if (e == cudaSuccess) e = cudaEventSynchronize(b);
+      float ms1 = 0.f;
+      if (e == cudaSuccess) e = cudaEventElapsedTime(&ms1, a, b);
+      t_net += ms1;
     }
+    if (a) cudaEventDestroy(a);
+    if (b) cudaEventDestroy(b);
   }
-  for (auto& x : ev)
-    if (x) cudaEventDestroy(x);
+  if (e == cudaErrorUnknown) return fail(FBS_E_CUDA, "fbs_profile: a probed kernel left no time");
   FBS_CUDA(e);
-  ms[0] = t[0] / (double)n_iter;
-  ms[1] = t[1] / (double)n_iter;
-  ms[2] = t[2] / (double)n_iter;
+  ms[0] = span[0] * 1e-6 / (double)n_iter;
+  ms[1] = span[1] * 1e-6 / (double)n_iter;
+  ms[2] = span[2] * 1e-6 / (double)n_iter;
   ms[3] = t_net / (double)n_iter;
+  ms[4] = (double)(last - first) * 1e-6 / (double)n_iter;
   return leave(h);
 }
 

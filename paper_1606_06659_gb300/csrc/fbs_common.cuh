@@ -145,6 +145,8 @@ struct DevPtrs {
   double* mu;         // [N][G] Poisson means at the new eps (split sweep kernels)
   const Contrasts* con;  // null: no contrast probabilities
   unsigned* con_count;   // [n][G]
+  unsigned long long* ktime;  // kernel-time probe (fbs_profile only; see ktime_begin)
+  int ktime_n;
 };
 
 // Device pointers of one chain in the FP32 form: per-gene state in FP32, each
@@ -181,9 +183,37 @@ struct DevPtrsF32 {
   const Contrasts* con;  // null: no contrast probabilities
   unsigned* con_count;   // [n][G]
   const double* psi;     // null, or the batch's TopLevel::psi (three-level model)
+  unsigned long long* ktime;  // kernel-time probe (fbs_profile only; see ktime_begin)
+  int ktime_n;
 };
 
 // Flag bits in Hyper::flags.
 enum : unsigned int { kFlagNonfinite = 1u, kFlagTimeout = 2u };
+
+#ifdef __CUDACC__
+// Kernel-time probe of fbs_profile: with kt non-null (only in the graph that
+// fbs_profile replays), the first thread of every block folds the global timer
+// (ns) at the block's start into kt[slot] (minimum) and at its end into
+// kt[n + slot] (maximum), so that kt[n + slot] - kt[slot] is the kernel's span
+// from its first block's start to its last block's end.  Sweep kernels call
+// ktime_begin first and ktime_end last, with every thread of the block.
+__device__ __forceinline__ unsigned long long global_timer_ns() {
+  unsigned long long t;
+  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+  return t;
+}
+
+__device__ __forceinline__ void ktime_begin(unsigned long long* kt, int n, int slot) {
+  if (kt != nullptr && threadIdx.x == 0 && slot >= 0 && slot < n)
+    atomicMin(kt + slot, global_timer_ns());
+}
+
+__device__ __forceinline__ void ktime_end(unsigned long long* kt, int n, int slot) {
+  if (kt != nullptr) {
+    __syncthreads();
+    if (threadIdx.x == 0 && slot >= 0 && slot < n) atomicMax(kt + n + slot, global_timer_ns());
+  }
+}
+#endif
 
 }  // namespace fbs

@@ -294,8 +294,10 @@ __device__ __forceinline__ void eps_f32_body(const ModelConst& mc, const DevPtrs
 }
 
 __global__ void __launch_bounds__(256) k_eps_f32(ModelConst mc, DevPtrsF32 p, int seg_i) {
+  ktime_begin(p.ktime, p.ktime_n, 3 * seg_i);
   eps_f32_body(mc, p, seg_i, blockIdx.y, blockIdx.x * blockDim.x + threadIdx.x,
                (blockIdx.x + blockIdx.y) % kCounterCopies);
+  ktime_end(p.ktime, p.ktime_n, 3 * seg_i);
 }
 
 // Which proposal gene g uses at iteration it: 0 none, kMoveNet the network's,
@@ -653,7 +655,9 @@ __device__ __forceinline__ void gb_f32_body(const ModelConst& mc, const DevPtrsF
 }
 
 __global__ void __launch_bounds__(128) k_gb_f32(ModelConst mc, DevPtrsF32 p, int seg_i) {
+  ktime_begin(p.ktime, p.ktime_n, 3 * seg_i + 1);
   gb_f32_body(mc, p, seg_i, blockIdx.x);
+  ktime_end(p.ktime, p.ktime_n, 3 * seg_i + 1);
 }
 
 // With the learned proposal (128 threads): the block first evaluates the network
@@ -663,6 +667,7 @@ __global__ void __launch_bounds__(128) k_gb_f32(ModelConst mc, DevPtrsF32 p, int
 // gamma/beta kernel keeps its own register allocation.
 __global__ void __launch_bounds__(128) k_gb_net_f32(ModelConst mc, DevPtrsF32 p, int seg_i,
                                                     const uint8_t* __restrict__ img) {
+  ktime_begin(p.ktime, p.ktime_n, 3 * seg_i + 1);
   bool net_ok;
   {
     extern __shared__ __align__(1024) uint8_t sm_tc[];
@@ -687,6 +692,7 @@ __global__ void __launch_bounds__(128) k_gb_net_f32(ModelConst mc, DevPtrsF32 p,
     __syncthreads();  // the shared memory is the gamma/beta updates' from here on
   }
   gb_f32_body(mc, p, seg_i, blockIdx.x, net_ok);
+  ktime_end(p.ktime, p.ktime_n, 3 * seg_i + 1);
 }
 
 // The learned move alone, at the current state, for the genes that use it (every

@@ -346,6 +346,7 @@ __device__ __forceinline__ void add_counters_u(unsigned long long* base, unsigne
 
 // Step 1: one thread per eps_gn (element e = n*G + g of the [N][G] planes).
 __global__ void __launch_bounds__(256) k_eps_f64(ModelConst mc, DevPtrs p, int seg_i) {
+  ktime_begin(p.ktime, p.ktime_n, 3 * seg_i);
   const int G = mc.G, N = mc.N, L = mc.L;
   const Hyper* hy = p.hyp;
   const long long it = hy->seg_it + seg_i + 1;
@@ -388,6 +389,7 @@ __global__ void __launch_bounds__(256) k_eps_f64(ModelConst mc, DevPtrs p, int s
   }
   add_counters_u(p.counters + ((blockIdx.x + blockIdx.y) % kCounterCopies) * FBS_NUM_COUNTERS, evals, 0, caps,
                  0, nonfin, &p.hyp->flags);
+  ktime_end(p.ktime, p.ktime_n, 3 * seg_i);
 }
 
 // Steps 2 and 5: one thread per gene, after the eps kernel of this sweep and the
@@ -479,6 +481,7 @@ __global__ void __launch_bounds__(128) k_gb_f64(ModelConst mc, DevPtrs p, int se
   // shared: mu[N][B], beta[L][B], partials[kNumPart][B] (values indexed by a runtime
   // l live here rather than in local memory), then the reduction scratch
   extern __shared__ double smem_dyn[];
+  ktime_begin(p.ktime, p.ktime_n, 3 * seg_i + 1);
   const int G = mc.G, N = mc.N, L = mc.L;
   const Hyper* hy = p.hyp;
   const long long it = hy->seg_it + seg_i + 1;
@@ -591,10 +594,15 @@ __global__ void __launch_bounds__(128) k_gb_f64(ModelConst mc, DevPtrs p, int se
   double* red = ps + (size_t)kNumPart * B;
   block_sum_to<kNumPart>(part, p.partial + (size_t)blockIdx.x * kNumPart, red);
   add_counters_u(p.counters, 0, evals_b, caps, gcaps, nonfin, &p.hyp->flags, evals_g);
+  ktime_end(p.ktime, p.ktime_n, 3 * seg_i + 1);
 }
 
 __global__ void __launch_bounds__(kHyperThreads) k_hyper(ModelConst mc, DevPtrs p, int nblk) {
+  // the sweep of the segment this launch completes (probe slot only)
+  const int slot = p.ktime ? 3 * (int)(p.hyp->it - p.hyp->seg_it) + 2 : 0;
+  ktime_begin(p.ktime, p.ktime_n, slot);
   hyper_body(mc, p.partial, p.hyp, p.trace_phi, p.counters, nblk);
+  ktime_end(p.ktime, p.ktime_n, slot);
 }
 
 // ---------------------------------------------------------------- convergence

@@ -25,7 +25,7 @@ def test_profile_times_fit_in_a_sweep_and_advance_the_chain(precision):
     sa, sb = a.get_state(), b.get_state()
     for k in ("eps", "beta", "gam", "phi", "w_eps", "w_beta"):
         assert np.array_equal(sa[k], sb[k]), k
-    assert all(v > 0 for v in ms[:3]) and ms[3] == 0.0
+    assert all(v > 0 for v in ms[:3]) and ms[3] == 0.0 and ms[4] > 0
     # one graph segment of 100 sweeps, timed with events on torch's stream
     st = torch.cuda.current_stream()
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
@@ -34,8 +34,11 @@ def test_profile_times_fit_in_a_sweep_and_advance_the_chain(precision):
     e1.record(st)
     torch.cuda.synchronize()
     per_sweep = e0.elapsed_time(e1) / 100
-    # critical path: gamma/beta after max(eps, hyperparameters of the sweep before)
-    assert ms[1] + max(ms[0], ms[2]) <= 1.05 * per_sweep, (ms, per_sweep)
+    # the probed replay runs as fast as the plain one, and along the critical
+    # path (gamma/beta after both eps and the hyperparameters of the sweep
+    # before) the kernel spans fit inside a sweep
+    assert abs(ms[4] - per_sweep) <= 0.1 * per_sweep, (ms, per_sweep)
+    assert ms[1] + max(ms[0], ms[2]) <= 1.02 * ms[4], (ms, per_sweep)
     a.close()
     b.close()
 
@@ -43,7 +46,7 @@ def test_profile_times_fit_in_a_sweep_and_advance_the_chain(precision):
 def test_measured_peaks_are_plausible():
     p = fbs.measure_peaks()
     assert set(p) == set(fbs.PEAK_NAMES) and all(v > 0 for v in p.values())
-    # per SM and clock: 128 FP32 lanes, 16 MUFU lanes, 2 FP64 lanes (GB300); the
-    # measured rates must keep that order with wide margins
-    assert p["ffma"] > 4 * p["ex2"] and p["ffma"] > 10 * p["dfma"]
-    assert p["ex2"] > p["dfma"]
+    # FP32 FMA lanes outnumber the MUFU and integer multiply-high lanes, which
+    # outnumber the FP64 FMA lanes (GB300: 2 per SM and clock)
+    assert p["ffma"] > 2 * max(p["ex2"], p["lg2"], p["imulhi"])
+    assert min(p["ex2"], p["lg2"], p["imulhi"]) > 4 * p["dfma"]

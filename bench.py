@@ -70,6 +70,8 @@ def parse():
                     help="paper: N=16 G=40000 L=5 (the metric's workload); batch: 64 datasets "
                          "of uneven N, G, L in one set of launches")
     ap.add_argument("--sweeps-per-step", type=int, default=100)
+    ap.add_argument("--chains", type=int, default=4,
+                    help="chains of the concurrent multi-chain job (the paper runs 4); 1: skip")
     ap.add_argument("--no-ess", action="store_true", help="skip the 20000-iteration ESS jobs")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-seconds", type=float, default=12.0)
@@ -538,6 +540,98 @@ def ess_job(fbs, torch, data, y_host, form, seed, chain, block, S, train_epochs)
     return out
 
 
+def chains_job(fbs, torch, data, y_host, form, seed, C, block, S, train_epochs):
+    """The paper's job shape (§5 runs 4 chains): C independent chains of the
+    configured job (20000 iterations, burn-in 10000, thin 10), each a handle on
+    its own CUDA stream so that the chains run concurrently on the one GPU, end to
+    end through the public API with pinned host counts.  For a learned form chain
+    0 collects the training pairs and trains the network inside the job; every
+    chain then calibrates.  Pooled ESS of a beta_gl = the sum of its chains'
+    Geyer ESS; convergence from the chains' running moments (fbs_rhat, §3.1)."""
+    spec = data["spec"]
+    iters, burnin, thin = spec["iters"], spec["burnin"], spec["thin"]
+    rows = (iters - burnin) // thin
+    main = torch.cuda.current_stream()
+    streams = [torch.cuda.Stream() for _ in range(C)]
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    smps = []
+    for c in range(C):
+        with torch.cuda.stream(streams[c]):
+            smps.append(new_sampler(fbs, data, y_host, form, seed, c, block, trace_cap=rows,
+                                    trace_beta=1))
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    ev0.record(main)
+    for st in streams:
+        st.wait_event(ev0)
+    done, phi_reads = 0, 0
+
+    def advance(upto):
+        nonlocal done, phi_reads
+        while done < upto:
+            n = min(S, upto - done)
+            for c in range(C):
+                with torch.cuda.stream(streams[c]):
+                    smps[c].run(n, burnin=burnin, thin=thin)
+            for c in range(C):
+                smps[c].phi()
+                phi_reads += 1
+            done += n
+
+    extra = {}
+    if form in LEARNED_FORMS:
+        min_accept, mode = LEARNED_FORMS[form]
+        advance(burnin // 2)
+        tt = time.perf_counter()
+        with torch.cuda.stream(streams[0]):
+            smps[0].proposal_collect(PAIR_SWEEPS, burnin=burnin, thin=2)
+            smps[0].proposal_train(seed=seed, **dict(TRAIN, epochs=train_epochs))
+        params = smps[0].proposal_params()
+        for c in range(C):
+            with torch.cuda.stream(streams[c]):
+                if c > 0:  # the same sweeps as chain 0's collection, without collecting
+                    smps[c].run(2 * PAIR_SWEEPS, burnin=burnin, thin=thin)
+                    smps[c].proposal_params(set_to=params)
+                smps[c].proposal_calibrate(CALIBRATE_SWEEPS, burnin=burnin, min_accept=min_accept)
+                smps[c].proposal_mode(mode)
+        done += 2 * PAIR_SWEEPS + CALIBRATE_SWEEPS
+        extra = {"collect_train_calibrate_s": time.perf_counter() - tt, "min_accept": min_accept,
+                 "mode": mode, "trained_on": "chain 0's pairs"}
+    advance(iters)
+    for st in streams:
+        main.wait_stream(st)
+    ev1.record(main)
+    moms = [s.moments() for s in smps]
+    torch.cuda.synchronize()
+    wall = time.perf_counter() - t0
+    dev_s = ev0.elapsed_time(ev1) / 1e3
+    ess = sum(s.beta_ess() for s in smps)
+    phi_ess = sum(geyer_ess(s.trace()["phi"]) for s in smps)
+    rh = fbs.rhat(smps)
+    if form in LEARNED_FORMS:
+        sts = [s.proposal_stats() for s in smps]
+        extra["accept_rate"] = sum(x["accepted"] for x in sts) / max(1, sum(x["tried"] for x in sts))
+    h2d = C * (y_host.nbytes + data["X"].nbytes + data["h"].nbytes)
+    d2h = phi_reads * 8 * (2 * spec["L"] + 2) + sum(
+        np.asarray(v).nbytes for m in moms for k, v in m.items() if k != "count")
+    for s in smps:
+        s.close()
+    torch.cuda.empty_cache()
+    out = {"chains": C, "iters_per_s_e2e": C * iters / wall, "iters_per_s_job_device": C * iters / dev_s,
+           "job_wall_s": wall, "pooled_min_ess": float(ess.min()),
+           "pooled_p05_ess": float(np.percentile(ess, 5)), "pooled_median_ess": float(np.median(ess)),
+           "min_ess_per_s": float(ess.min()) / wall,
+           "p05_ess_per_s": float(np.percentile(ess, 5)) / wall,
+           "median_ess_per_s": float(np.median(ess)) / wall,
+           "min_phi_ess_per_s": float(phi_ess.min()) / wall,
+           "rhat_phi_max": float(np.nanmax(rh["phi"])),
+           "rhat_beta_frac_above_1_1": float(np.mean(rh["beta"] > 1.1)),
+           "h2d_bytes_per_step": h2d / max(1, phi_reads // C),
+           "d2h_bytes_per_step": d2h / max(1, phi_reads // C)}
+    out.update(extra)
+    return out
+
+
 def main():
     args = parse()
     world = int(os.environ.get("WORLD_SIZE", "1"))
@@ -589,6 +683,12 @@ def main():
             barrier()
             forms[f] = ess_job(fbs, torch, data, y_host, f, seed, rank, args.block, S,
                                args.train_epochs)
+    jobs_c = {}
+    if not args.no_ess and args.chains > 1:
+        for f in ("f64", "learned") if args.forms == "all" else (form,):
+            barrier()
+            jobs_c[f] = chains_job(fbs, torch, data, y_host, f, seed + 100, args.chains,
+                                   args.block, S, args.train_epochs)
     params = forms.get("learned", {}).pop("params", None)
     for f in ("learned_a02", "learned_cfg4"):
         forms.get(f, {}).pop("params", None)
@@ -742,6 +842,17 @@ def main():
                 f: {k: forms[f][k] / b[k] for k in ("min_ess_per_s", "p05_ess_per_s",
                                                     "median_ess_per_s", "min_phi_ess_per_s")}
                 for f in LEARNED_FORMS if f in forms}
+    if jobs_c:
+        line["chains_job"] = jobs_c
+        if "f64" in jobs_c and "learned" in jobs_c:
+            a, b = jobs_c["learned"], jobs_c["f64"]
+            line["chains_job_learned_vs_plain_f64"] = {
+                k: a[k] / b[k] for k in ("iters_per_s_e2e", "min_ess_per_s", "p05_ess_per_s",
+                                         "median_ess_per_s", "min_phi_ess_per_s")}
+        if "learned" in jobs_c and "learned" in forms:
+            line["chains_job_vs_one_chain"] = {
+                k: jobs_c["learned"][k] / forms["learned"][k]
+                for k in ("iters_per_s_e2e", "min_ess_per_s", "p05_ess_per_s", "median_ess_per_s")}
     if not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline(data, args.cpu_seconds, G)
     print(json.dumps(line), flush=True)

@@ -126,9 +126,16 @@ __global__ void k_collect_f32(ModelConst mc, DevPtrsF32 p, float* __restrict__ f
 // ---------------------------------------------------------------- training
 
 // Column means and scales of the training pairs, in FP64: block c < F takes
-// feature column c, block F + l takes beta column l.  The scale is the standard
-// deviation, or 1 for a column that is constant to within 1e-6 of its size.
-// st = [mean_f (F), scale_f (F), mean_beta (L), scale_beta (L)].
+// feature column c, block F + l takes beta column l.  A beta column's scale is
+// its standard deviation, or 1 when it is constant to within 1e-6 of its size.
+// A feature column's scale is its standard deviation but at least
+// kFeatScaleFloor: theta and log sigma, the same for every gene of a sweep, vary
+// across the collected sweeps only by their posterior spread (~1e-3), and
+// dividing by that would let the network fit noise with weights that, in raw
+// coordinates, react strongly to the small moves of theta and sigma during
+// sampling.  st = [mean_f (F), scale_f (F), mean_beta (L), scale_beta (L)].
+constexpr double kFeatScaleFloor = 0.1;
+
 __global__ void k_col_stats(const float* __restrict__ feat, const float* __restrict__ beta,
                             long long M, int F, int L, float* __restrict__ st) {
   const int c = blockIdx.x;
@@ -159,7 +166,7 @@ __global__ void k_col_stats(const float* __restrict__ feat, const float* __restr
     const double mean = t1 / (double)M;
     const double var = fmax(t2 / (double)M - mean * mean, 0.0);
     const double tol = 1e-6 * (1.0 + fabs(mean));
-    const double sc = var > tol * tol ? sqrt(var) : 1.0;
+    const double sc = c < F ? fmax(sqrt(var), kFeatScaleFloor) : (var > tol * tol ? sqrt(var) : 1.0);
     if (c < F) {
       st[c] = (float)mean;
       st[F + c] = (float)sc;

@@ -259,16 +259,19 @@ __device__ __forceinline__ SliceResult slice_update_warp(double x0, double w, co
 
   // shrinkage: lane j proposes the (base + j)-th point of the rejection chain;
   // the first round takes 8 proposals (most updates accept within a few), later
-  // rounds 32
+  // rounds 32.  Lane j draws only the uniform of proposal base + j (one Philox
+  // block per lane, in parallel); every lane then walks the chain with the
+  // uniforms broadcast from their lanes, keeping its own point, and ends with
+  // the bracket left after rejecting all m points.
   for (int base = 0, width = 8; base < shrink_max; base += width, width = 32) {
     const int m = min(width, shrink_max - base);
+    const double u_mine = lane < m ? r.u(3u + (uint32_t)(base + lane)) : 0.0;
     double l2 = lo, h2 = hi, xs = 0.0;
-    const int mine = lane < m ? lane : m - 1;
-    for (int i = 0; i <= mine; ++i) {
-      xs = __dadd_rn(l2, __dmul_rn(__dsub_rn(h2, l2), r.u(3u + (uint32_t)(base + i))));
-      if (i < mine) {
-        if (xs > x0) h2 = xs; else l2 = xs;
-      }
+    for (int i = 0; i < m; ++i) {
+      const double ui = __shfl_sync(0xffffffffu, u_mine, i);
+      const double xi = __dadd_rn(l2, __dmul_rn(__dsub_rn(h2, l2), ui));
+      if (i == lane) xs = xi;
+      if (xi > x0) h2 = xi; else l2 = xi;
     }
     const bool act = lane < m;
     fv = act ? f(xs, &aux) : -INFINITY;
@@ -282,10 +285,8 @@ __device__ __forceinline__ SliceResult slice_update_warp(double x0, double w, co
       return res;
     }
     res.evals += (unsigned)m;
-    // the bracket after the m rejections: lane m-1 holds the chain's last proposal
-    if (xs > x0) h2 = xs; else l2 = xs;
-    lo = __shfl_sync(0xffffffffu, l2, m - 1);
-    hi = __shfl_sync(0xffffffffu, h2, m - 1);
+    lo = l2;  // the bracket after the m rejections (the same in every lane)
+    hi = h2;
   }
   res.x = x0;
   res.aux = aux0;

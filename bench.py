@@ -789,6 +789,22 @@ def main():
     st = smp.proposal_stats() if learned else None
     smp.close()
 
+    # ---- the plain FP32 sweep as a graph of separate launches against the
+    #      persistent form (one cooperative launch per segment), device-timed
+    persist = {}
+    for pers in (0, 1):
+        p2 = new_sampler(fbs, data, data["y"], "f32", seed + 2, rank, args.block, persistent=pers)
+        p2.run(args.tune_sweeps, burnin=tb, thin=thin)
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        flush.fill_(pers)
+        e0.record(stream)
+        p2.run(args.steps * S, burnin=tb, thin=thin)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        persist["persistent" if pers else "graph"] = e0.elapsed_time(e1) / (args.steps * S)
+        p2.close()
+
     if rank != 0:
         if world > 1:
             dist.destroy_process_group()
@@ -813,6 +829,10 @@ def main():
         "clocks": clk,
         "roofline": roofline,
         "evals_per_sweep": evals,
+        "persistent_vs_graph_ms_per_sweep": dict(
+            persist, form="f32", what="device-timed sweeps of the plain FP32 form: the graph "
+                                       "of three launches per sweep against one cooperative "
+                                       "launch per segment (the chains are identical)"),
     }
     if st is not None:
         line["learned_timed"] = {"mh_genes": st["mh_genes"],

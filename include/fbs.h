@@ -97,6 +97,12 @@ typedef struct {
                             width (Section 4.2 slice-samples every non-normal full
                             conditional); 0 (default): draw them exactly from their
                             Inverse-Gamma, Gamma and truncated laws.  FBS_F64 only. */
+  int persistent;        /* 1: fbs_run sweeps each segment of graph_segment iterations in
+                            one cooperative launch of resident blocks with grid barriers
+                            (every step of Algorithm 1 inside; the same chain as the graph
+                            of separate launches); 0 (default): a CUDA graph of three
+                            launches per iteration.  FBS_F32 only; while the learned
+                            proposal is in use the graph path runs. */
 } fbs_options;
 
 /* Fill *o with the defaults: FP64, w0 = 1, K = 100, shrink_max = 100, chain 0,

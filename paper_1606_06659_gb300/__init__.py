@@ -60,7 +60,7 @@ class Options(C.Structure):
     _fields_ = [("precision", C.c_int), ("w0", C.c_double), ("step_out_max", C.c_int),
                 ("shrink_max", C.c_int), ("chain", C.c_uint32), ("moments_eps", C.c_int),
                 ("trace_cap", C.c_int64), ("trace_beta", C.c_int), ("block", C.c_int),
-                ("graph_segment", C.c_int), ("all_slice", C.c_int)]
+                ("graph_segment", C.c_int), ("all_slice", C.c_int), ("persistent", C.c_int)]
 
 
 _PD = C.POINTER(C.c_double)

@@ -85,7 +85,7 @@ Layout make_layout(int N, int G, int L, int nblk, long long trace_cap, int trace
 // FP32 form: per-gene state in FP32, four FP32 moment planes per parameter.
 struct LayoutF32 {
   size_t y, T, eps, w_eps, waux_eps, mom_eps, mu, beta, w_beta, waux_beta, mom_beta, gam, mom_gam;
-  size_t partial, hyp, trace_phi, trace_beta, counters, pinv, total;
+  size_t partial, hyp, trace_phi, trace_beta, counters, pinv, gsync, total;
 };
 
 LayoutF32 make_layout_f32(int N, int G, int L, int nblk, long long trace_cap, int trace_beta) {
@@ -116,6 +116,7 @@ LayoutF32 make_layout_f32(int N, int G, int L, int nblk, long long trace_cap, in
   o.trace_beta = trace_beta && trace_cap > 0 ? take((size_t)trace_cap * LG * 8) : 0;
   o.counters = take(kEpsCounterCopiesHost * FBS_NUM_COUNTERS * sizeof(unsigned long long));
   o.pinv = take((size_t)kMaxL * kMaxN * 8);
+  o.gsync = take(kPersistentSyncBytes);
   o.total = at + 256;
   return o;
 }
@@ -210,6 +211,9 @@ int check_opts(const fbs_options* o) {
   if (o->all_slice != 0 && o->all_slice != 1) return fail(FBS_E_ARG, "all_slice must be 0 or 1");
   if (o->all_slice && o->precision != FBS_F64)
     return fail(FBS_E_ARG, "all_slice runs in the FBS_F64 form");
+  if (o->persistent != 0 && o->persistent != 1) return fail(FBS_E_ARG, "persistent must be 0 or 1");
+  if (o->persistent && o->precision != FBS_F32)
+    return fail(FBS_E_ARG, "the persistent sweep runs in the FBS_F32 form");
   return FBS_OK;
 }
 
@@ -715,6 +719,17 @@ int fbs_run(fbs_handle* h, int64_t n_iter, int64_t burnin, int64_t thin) {
   if (rc) return rc;
   FBS_CUDA(launch_set_run(h->p.hyp, burnin, burnin / 2, thin, h->s));
   int64_t left = n_iter;
+  if (h->opt.persistent && h->pf.prop == nullptr) {
+    // one cooperative launch per segment (the learned move takes the graph path)
+    void* gsync = (char*)(((uintptr_t)h->ws + 255) & ~(uintptr_t)255) + h->lay32.gsync;
+    while (left > 0) {
+      const int n = (int)(left < h->seg ? left : h->seg);
+      FBS_CUDA(launch_seg_begin(h->p.hyp, h->s));
+      FBS_CUDA(launch_sweeps_f32(h->mc, h->pf, h->p, n, gsync, h->s, nullptr));
+      left -= n;
+    }
+    return leave(h);
+  }
   if (left >= h->seg) {
     rc = ensure_graph(h);
     if (rc) return rc;
@@ -738,7 +753,8 @@ int fbs_sync(fbs_handle* h) {
   int rc = read_hyper(h, &hy);
   if (rc) return rc;
   if (hy.flags & kFlagTimeout)
-    return fail(FBS_E_CUDA, "a tensor-core wait of the proposal network gave up");
+    return fail(FBS_E_CUDA, "a bounded wait gave up (a tensor-core wait of the proposal network "
+                            "or a grid barrier of the persistent sweep)");
   if (hy.flags & kFlagNonfinite)
     return fail(FBS_E_NONFINITE, "a slice update started from a non-finite log density");
   return slice_cap_status(h);

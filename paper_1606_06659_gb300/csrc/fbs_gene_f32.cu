@@ -722,6 +722,121 @@ __global__ void k_seg_begin(Hyper* hy) {
   }
 }
 
+// ---------------------------------------------------------------- persistent sweeps (FP32)
+//
+// A whole segment of sweeps of one chain (Algorithm 1, every step) in one
+// cooperative launch whose blocks are all resident: per sweep, every block takes
+// tiles of 128 eps_gn updates (step 1), a grid barrier, every block takes
+// 128-gene blocks of gamma/beta updates (steps 2, 5), a grid barrier, then block 0
+// runs the hyperparameter steps (3, 4, 6, 7) while the other blocks go on to the
+// next sweep's eps updates, which involve no hyperparameter; the next barrier
+// also waits for block 0.  The per-element, per-gene and hyperparameter device
+// functions are those of k_eps_f32, k_gb_f32 and k_hyper, with the same Philox
+// counters and the same per-gene-block partial sums, so the chain is
+// bit-identical to the graph of separate launches.
+
+// Sense-reversing grid barrier in device memory (zeroed before each launch).
+struct GridSync {
+  unsigned int count, gen;
+};
+
+// Polls of a barrier wait (each followed by a 64 ns sleep, about 4 s in all)
+// before the wait gives up, sets kFlagTimeout and ends the launch.
+constexpr unsigned kGridWaitLimit = 1u << 26;
+
+__device__ __forceinline__ unsigned ld_acquire_gpu(const unsigned* p) {
+  unsigned v;
+  asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+  return v;
+}
+
+__device__ __forceinline__ void st_release_gpu(unsigned* p, unsigned v) {
+  asm volatile("st.release.gpu.global.u32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
+}
+
+// Every block of the grid arrives; the last one to arrive resets the count and
+// opens the next generation.  Writes of every block before the barrier are
+// visible to every block after it.  Returns false in every thread of a block
+// whose wait gave up.
+__device__ __forceinline__ bool grid_sync(GridSync* gs, unsigned* flags, volatile int* s_ok) {
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    const unsigned gen = ld_acquire_gpu(&gs->gen);
+    __threadfence();
+    const unsigned arrived = atomicAdd(&gs->count, 1u) + 1u;
+    int ok = 1;
+    if (arrived == gridDim.x) {
+      atomicExch(&gs->count, 0u);
+      __threadfence();
+      st_release_gpu(&gs->gen, gen + 1u);
+    } else {
+      unsigned polls = 0;
+      while (ld_acquire_gpu(&gs->gen) == gen) {
+        if (++polls >= kGridWaitLimit) {
+          ok = 0;
+          atomicOr(flags, kFlagTimeout);
+          break;
+        }
+        __nanosleep(64);
+      }
+    }
+    __threadfence();
+    *s_ok = ok;
+  }
+  __syncthreads();
+  return *s_ok != 0;
+}
+
+__global__ void __launch_bounds__(128, 4) k_sweeps_f32(ModelConst mc, DevPtrsF32 p, DevPtrs hp,
+                                                   int n_sweeps, int nblk, GridSync* gs) {
+  __shared__ int s_ok;
+  const int tiles_g = (mc.G + 127) / 128;
+  const int n_tiles = tiles_g * mc.N;
+  for (int i = 0; i < n_sweeps; ++i) {
+    for (int t = blockIdx.x; t < n_tiles; t += gridDim.x) {
+      const int n = t / tiles_g;
+      eps_f32_body(mc, p, i, n, (t - n * tiles_g) * 128 + (int)threadIdx.x, t % kCounterCopies);
+    }
+    if (!grid_sync(gs, &p.hyp->flags, &s_ok)) return;
+    for (int b = blockIdx.x; b < nblk; b += gridDim.x) {
+      gb_f32_body(mc, p, i, b);
+      __syncthreads();  // the next gene block reuses the shared memory
+    }
+    if (!grid_sync(gs, &p.hyp->flags, &s_ok)) return;
+    if (blockIdx.x == 0) hyper_body(mc, hp.partial, hp.hyp, hp.trace_phi, hp.counters, nblk);
+  }
+}
+
+cudaError_t launch_sweeps_f32(const ModelConst& mc, const DevPtrsF32& p, const DevPtrs& hp,
+                              int n_sweeps, void* gsync, cudaStream_t s, int* grid_out) {
+  const int block = 128;
+  const int nblk = (mc.G + block - 1) / block;
+  const size_t smem = gene_smem_bytes_f32(mc.N, block);
+  cudaError_t e = cudaFuncSetAttribute(k_sweeps_f32, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                       (int)gene_smem_bytes_f32(FBS_MAX_N, block));
+  if (e != cudaSuccess) return e;
+  int dev = 0, sms = 0, per_sm = 0;
+  if ((e = cudaGetDevice(&dev)) != cudaSuccess) return e;
+  if ((e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev)) != cudaSuccess)
+    return e;
+  e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_sweeps_f32, block, smem);
+  if (e != cudaSuccess) return e;
+  if (per_sm < 1) return cudaErrorInvalidConfiguration;
+  int grid = per_sm * sms;
+  const int most = nblk > ((mc.G + 127) / 128) * mc.N ? nblk : ((mc.G + 127) / 128) * mc.N;
+  if (grid > most) grid = most;
+  if ((e = cudaMemsetAsync(gsync, 0, sizeof(GridSync), s)) != cudaSuccess) return e;
+  ModelConst mc_ = mc;
+  DevPtrsF32 p_ = p;
+  DevPtrs hp_ = hp;
+  int n_ = n_sweeps, nb_ = nblk;
+  GridSync* gs_ = (GridSync*)gsync;
+  void* args[] = {&mc_, &p_, &hp_, &n_, &nb_, &gs_};
+  if (grid_out) *grid_out = grid;
+  return cudaLaunchCooperativeKernel((const void*)k_sweeps_f32, dim3(grid), dim3(block), args, smem,
+                                     s);
+}
+
 // ---------------------------------------------------------------- batched kernels (FP32)
 //
 // Many independent datasets / chains in one launch.  Each dataset keeps its own

@@ -39,6 +39,12 @@ cudaError_t launch_eps_f32(const ModelConst& mc, const DevPtrsF32& p, int seg_i,
 cudaError_t launch_gb_f32(const ModelConst& mc, const DevPtrsF32& p, int block, int seg_i,
                           cudaStream_t s, const void* img = nullptr);
 cudaError_t launch_seg_begin(Hyper* hy, cudaStream_t s);
+// A segment of n_sweeps sweeps of the plain FP32 form in one cooperative launch
+// (persistent blocks, grid barriers; bit-identical to the separate launches).
+// gsync: kPersistentSyncBytes of device memory, reset by the launch.
+constexpr size_t kPersistentSyncBytes = 256;
+cudaError_t launch_sweeps_f32(const ModelConst& mc, const DevPtrsF32& p, const DevPtrs& hp,
+                              int n_sweeps, void* gsync, cudaStream_t s, int* grid_out);
 
 cudaError_t launch_mh_step_f32(const ModelConst& mc, const DevPtrsF32& p, long long it,
                               cudaStream_t s);

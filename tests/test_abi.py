@@ -48,7 +48,8 @@ def _args(**over):
 
 @pytest.mark.parametrize("case", ["N0", "G1", "L9", "singular", "negative_y", "nan_h",
                                   "bad_prior", "too_many_classes", "bad_precision",
-                                  "all_slice_f32", "all_slice_2"])
+                                  "all_slice_f32", "all_slice_2", "persistent_f64",
+                                  "persistent_2"])
 def test_invalid_arguments_rejected_before_any_cuda_call(case):
     kw = {}
     a = _args()
@@ -77,6 +78,10 @@ def test_invalid_arguments_rejected_before_any_cuda_call(case):
         kw["precision"], kw["all_slice"] = fbs.FBS_F32, 1
     elif case == "all_slice_2":
         kw["all_slice"] = 2
+    elif case == "persistent_f64":
+        kw["persistent"] = 1
+    elif case == "persistent_2":
+        kw["precision"], kw["persistent"] = fbs.FBS_F32, 2
     with pytest.raises(fbs.FbsError) as e:
         fbs.Sampler(a["y"], a["X"], a["h"], a["priors"], workspace="library", **kw)
     assert e.value.code == fbs.FBS_E_ARG

@@ -80,23 +80,6 @@ __device__ __forceinline__ float gamma_mt_f(float shape, Rng4& r, uint32_t k0, b
   return shape;
 }
 
-// e^z - 1 - z without cancellation: Taylor series to z^9 for |z| < 1/2 (relative
-// truncation error below 3e-9), expf otherwise.
-__device__ __forceinline__ float em1mx(float z) {
-  if (fabsf(z) < 0.5f) {
-    float p = 1.0f / 362880.0f;
-    p = fmaf(p, z, 1.0f / 40320.0f);
-    p = fmaf(p, z, 1.0f / 5040.0f);
-    p = fmaf(p, z, 1.0f / 720.0f);
-    p = fmaf(p, z, 1.0f / 120.0f);
-    p = fmaf(p, z, 1.0f / 24.0f);
-    p = fmaf(p, z, 1.0f / 6.0f);
-    p = fmaf(p, z, 0.5f);
-    return z * z * p;
-  }
-  return expf(z) - 1.0f - z;
-}
-
 // ---------------------------------------------------------------- densities
 
 struct EpsDensityF {

@@ -101,6 +101,73 @@ struct BetaDensityT {
   }
 };
 
+// FP32 filters of the FP64 slice updates (slice_update_filtered).  Each returns
+// Delta(p) = log f(p) - log f(x0) in the relative form of the FP32 sweep, which
+// needs no evaluation at x0, and a bound on |Delta32 - Delta| + |the FP64
+// evaluation's error|.  FP32 part: 2^-20 (16 times the unit roundoff) times the
+// sum of the terms' magnitudes and of the sensitivities of Delta to the FP32
+// roundings of its inputs (x - x0, y or T, the rate mu0 from expf of the rounded
+// log-rate, Q_j, 1/(2 gamma) or 1/(2 sigma^2)) and to the series or expf of
+// e^z - 1 - z; FP64 part: 2^-46 (64 times the FP64 unit roundoff) times the
+// magnitudes of the terms of log f(p), log f(x0) and the level.
+
+// eps: Delta(x) = d (y - mu0) - mu0 (e^d - 1 - d) - d (d + 2 x0) hg, d = x - x0.
+struct EpsFilter {
+  double x0;
+  float y, mu0, x0f, hg, amag, c64;  // amag = |log-rate at x0| + 8; c64: log f(x0) magnitude
+  __device__ __forceinline__ float operator()(double pt, float* eb) const {
+    const float d = (float)(pt - x0);
+    const float ad = fabsf(d);
+    const float e = em1mx(d);
+    const float ed1 = d + e;             // e^d - 1
+    const float mued = mu0 + mu0 * ed1;  // mu0 e^d, the rate at pt
+    const float t1 = d * (y - mu0);
+    const float t2 = mu0 * e;
+    const float t3 = d * (d + 2.0f * x0f) * hg;
+    const float b32 = fabsf(t1) + fabsf(t2) + fabsf(t3) +
+                      ad * (y + mu0 + mued + (2.0f * fabsf(x0f) + 2.0f * ad) * hg) +
+                      amag * mu0 * fabsf(ed1) + mu0 * (2.0f + fabsf(ed1) + ad);
+    const float px = fabsf(x0f) + ad;
+    const float b64 = c64 + y * px + mued * (amag + ad) + px * px * hg;
+    *eb = 0x1p-20f * b32 + 0x1p-46f * b64;
+    return t1 - t2 - t3;
+  }
+};
+
+// beta_gl: Delta(b) = d T - sum_j Q_j (e^{v_j d} - 1) - d (d + 2 (b0 - theta)) hs.
+template <int NC>
+struct BetaFilterT {
+  double b0;
+  float T, bt, hs, b0f, c64;  // bt = b0 - theta; c64: log f(b0) magnitude
+  int ncls;
+  float Q[NC], v[NC];
+  __device__ __forceinline__ float operator()(double b, float* eb) const {
+    const float d = (float)(b - b0);
+    const float ad = fabsf(d);
+    float s = 0.0f, sa = 0.0f, sq = 0.0f, se = 0.0f;
+#pragma unroll
+    for (int j = 0; j < NC; ++j) {
+      if (NC < kMaxCls || j < ncls) {
+        const float z = v[j] * d;
+        const float ej1 = z + em1mx(z);  // e^z - 1
+        const float q = Q[j] * ej1;
+        s += q;
+        sa += fabsf(q);
+        sq += Q[j] * ((fabsf(v[j]) * ad + 1.0f) * (2.0f + fabsf(ej1)) + fabsf(z));
+        se += Q[j] * (2.0f + fabsf(ej1));
+      }
+    }
+    const float t1 = d * T;
+    const float t3 = d * (d + 2.0f * bt) * hs;
+    const float b32 = fabsf(t1) + sa + fabsf(t3) +
+                      ad * (fabsf(T) + (2.0f * fabsf(bt) + 2.0f * ad) * hs) + sq;
+    const float pb = fabsf(b0f) + ad, pt = fabsf(bt) + ad;
+    const float b64 = c64 + pb * fabsf(T) + se + pt * pt * hs;
+    *eb = 0x1p-20f * b32 + 0x1p-46f * b64;
+    return t1 - s - t3;
+  }
+};
+
 // log f(gamma_g = x | ...) = -shape1 log x - B / x on x > 0, with shape1 = (N + nu)/2 + 1
 // and B = (sum_n eps_gn^2 + nu tau)/2: the Inverse-Gamma full conditional of step 2,
 // slice-sampled in the all-slice variant (Section 4.2).
@@ -369,7 +436,20 @@ __global__ void __launch_bounds__(256) k_eps_f64(ModelConst mc, DevPtrs p, int s
           (uint32_t)it);
     const double x0 = p.eps[e];
     double w = p.w_eps[e];
-    SliceResult s = slice_update(x0, w, f, r, mc.K, mc.shrink_max);
+    // comparisons decided in FP32 where an error bound allows (the same result);
+    // a start whose rate does not fit FP32 takes the FP64 comparisons throughout
+    const float af = (float)(A + x0), hgf = (float)f.hg, yf = (float)f.y, x0f = (float)x0;
+    const float mu0f = expf(af);
+    SliceResult s;
+    if (isfinite(mu0f) && isfinite(hgf) && isfinite(x0f) && af < 80.0f) {
+      const float amag = fabsf(af) + 8.0f;
+      EpsFilter ff{x0, yf, mu0f, x0f, hgf, amag,
+                   yf * fabsf(x0f) + mu0f * amag + x0f * x0f * hgf + 64.0f};
+      s = slice_update_filtered(x0, w, f, ff, r, mc.K, mc.shrink_max);
+      s.aux = exp(A + s.x);  // the rate at the result, as the density computes it
+    } else {
+      s = slice_update(x0, w, f, r, mc.K, mc.shrink_max);
+    }
     evals = s.evals;
     caps = s.capped;
     nonfin = s.nonfinite;
@@ -432,7 +512,26 @@ __device__ __forceinline__ void beta_column_f64(const ModelConst& mc, const DevP
   Rng r(mc.seed_lo, mc.seed_hi, mc.chain, kStreamBeta, (uint32_t)((size_t)g * L + l), it32);
   const double x0 = b_cur;
   double w = p.w_beta[e];
-  SliceResult s = slice_update(x0, w, f, r, mc.K, mc.shrink_max);
+  // comparisons decided in FP32 where an error bound allows (the same result)
+  BetaFilterT<NC> ff;
+  ff.b0 = x0;
+  ff.b0f = (float)x0;
+  ff.T = (float)f.T;
+  ff.bt = (float)(x0 - theta);
+  ff.hs = (float)f.hs;
+  ff.ncls = f.ncls;
+  bool filt = isfinite(ff.T) && isfinite(ff.bt) && isfinite(ff.hs) && isfinite(ff.b0f);
+  float qs = 0.0f;
+#pragma unroll
+  for (int j = 0; j < NC; ++j) {
+    ff.Q[j] = (float)f.Q[j];
+    ff.v[j] = (float)f.v[j];
+    if (NC < kMaxCls || j < f.ncls) qs += ff.Q[j];
+  }
+  filt = filt && isfinite(qs);
+  ff.c64 = fabsf(ff.b0f) * fabsf(ff.T) + qs + ff.bt * ff.bt * ff.hs + 64.0f;
+  SliceResult s = filt && isfinite(ff.c64) ? slice_update_filtered(x0, w, f, ff, r, mc.K, mc.shrink_max)
+                                           : slice_update(x0, w, f, r, mc.K, mc.shrink_max);
   evals_b += s.evals;
   caps += s.capped;
   nonfin += s.nonfinite;

@@ -18,6 +18,23 @@ constexpr int kGammaAttempts = 64;
 constexpr int kTruncAttempts = 16;
 constexpr uint32_t kTruncStride = 256;  // uniforms reserved per truncated-draw attempt
 
+// e^z - 1 - z without cancellation: Taylor series to z^9 for |z| < 1/2 (relative
+// truncation error below 3e-9), expf otherwise.
+__device__ __forceinline__ float em1mx(float z) {
+  if (fabsf(z) < 0.5f) {
+    float p = 1.0f / 362880.0f;
+    p = fmaf(p, z, 1.0f / 40320.0f);
+    p = fmaf(p, z, 1.0f / 5040.0f);
+    p = fmaf(p, z, 1.0f / 720.0f);
+    p = fmaf(p, z, 1.0f / 120.0f);
+    p = fmaf(p, z, 1.0f / 24.0f);
+    p = fmaf(p, z, 1.0f / 6.0f);
+    p = fmaf(p, z, 0.5f);
+    return z * z * p;
+  }
+  return expf(z) - 1.0f - z;
+}
+
 // Ten Philox rounds: two 32x32->64 multiplies per round, key bumped by the
 // Weyl constants between rounds.
 __device__ __forceinline__ uint4 philox4x32_10(uint4 c, uint32_t k0, uint32_t k1) {
@@ -53,8 +70,14 @@ struct Rng {
     const unsigned long long x = (k & 1u)
                                      ? ((unsigned long long)w.w << 32 | w.z)
                                      : ((unsigned long long)w.y << 32 | w.x);
-    // (floor(x / 2^12) + 1/2) / 2^52: every step is exact in double
-    return __dmul_rn(__dadd_rn(__ull2double_rn(x >> 12), 0.5), 0x1p-52);
+    // (floor(x / 2^12) + 1/2) / 2^52 = v / 2^53 with v = 2 floor(x / 2^12) + 1, an odd
+    // integer below 2^53, so the double is assembled from integer operations: the
+    // leading bit of v moved to bit 52 gives the mantissa, its position the exponent
+    const unsigned long long v = ((x >> 12) << 1) | 1ull;
+    const int sh = __clzll((long long)v) - 11;
+    const unsigned long long bits =
+        ((unsigned long long)(1022 - sh) << 52) | ((v << sh) & 0xFFFFFFFFFFFFFull);
+    return __longlong_as_double((long long)bits);
   }
 };
 
@@ -158,6 +181,74 @@ __device__ __forceinline__ SliceResult slice_update(double x0, double w, const F
   }
   res.x = x0;
   res.aux = aux0;
+  res.capped = true;
+  return res;
+}
+
+// slice_update (Algorithm 2, steps 1-6) with every comparison "log u < log f(p)"
+// first decided in FP32.  ff(p, &bound) returns Delta(p) = log f(p) - log f(x0)
+// in FP32 and a bound on the sum of its error and of the error with which the
+// FP64 evaluation (f) of the same comparison is made; with the FP32 level
+// log U_0, a gap beyond the two bounds decides the comparison exactly as the
+// FP64 arithmetic would, and only a gap inside them evaluates f in FP64 (the
+// level log f(x0) + log U_0 is then computed once).  The uniforms, the interval
+// arithmetic (FP64, rounded step by step), the evaluation count, the result and
+// its flags are those of slice_update; the caller computes the auxiliary value
+// at the result.  ff must be usable only where f(x0) is finite (the caller
+// checks this and otherwise calls slice_update), so nonfinite is false.
+template <class F, class FF>
+__device__ __forceinline__ SliceResult slice_update_filtered(double x0, double w, const F& f,
+                                                             const FF& ff, Rng& r, int K,
+                                                             int shrink_max) {
+  SliceResult res;
+  res.evals = 1;
+  res.nonfinite = false;
+  res.aux = 0.0;
+  const double u0 = r.u(0);
+  const float lu = logf((float)u0);
+  // error of lu: the rounding of u0 to FP32 and logf's (ulp) error, with margin
+  const float lu_err = 0x1p-20f * (fabsf(lu) + 1.0f);
+  double logu = 0.0;
+  bool have_level = false;
+  auto above = [&](double pt) -> bool {  // the FP64 comparison logu < f(pt)
+    float eb;
+    const float gap = ff(pt, &eb) - lu;
+    const float tol = eb + lu_err;
+    if (gap > tol) return true;
+    if (gap < -tol) return false;
+    if (!have_level) {
+      double a0;
+      logu = __dadd_rn(f(x0, &a0), log(u0));
+      have_level = true;
+    }
+    double a;
+    return logu < f(pt, &a);
+  };
+  const double v = __dmul_rn(w, r.u(1));
+  double lo = __dsub_rn(x0, v);
+  double hi = __dadd_rn(lo, w);
+  int KL = (int)__dmul_rn((double)(K + 1), r.u(2));
+  if (KL > K) KL = K;
+  const int KR = K - KL;
+  for (int k = 0; k < KL; ++k) {
+    ++res.evals;
+    if (above(lo)) lo = __dsub_rn(lo, w); else break;
+  }
+  for (int k = 0; k < KR; ++k) {
+    ++res.evals;
+    if (above(hi)) hi = __dadd_rn(hi, w); else break;
+  }
+  for (int j = 0; j < shrink_max; ++j) {
+    const double xs = __dadd_rn(lo, __dmul_rn(__dsub_rn(hi, lo), r.u(3u + (uint32_t)j)));
+    ++res.evals;
+    if (above(xs)) {
+      res.x = xs;
+      res.capped = false;
+      return res;
+    }
+    if (xs > x0) hi = xs; else lo = xs;
+  }
+  res.x = x0;
   res.capped = true;
   return res;
 }

@@ -70,6 +70,10 @@ def parse():
                     help="paper: N=16 G=40000 L=5 (the metric's workload); batch: 64 datasets "
                          "of uneven N, G, L in one set of launches")
     ap.add_argument("--sweeps-per-step", type=int, default=100)
+    ap.add_argument("--profile-run", type=int, default=0,
+                    help="set up the timed sampler (tuning, and for a learned form training and "
+                         "calibration), run this many sweeps as direct launches inside the NVTX "
+                         "range 'profile_sweeps' and exit (for ncu captures)")
     ap.add_argument("--chains", type=int, default=4,
                     help="chains of the concurrent multi-chain job (the paper runs 4); 1: skip")
     ap.add_argument("--no-ess", action="store_true", help="skip the 20000-iteration ESS jobs")
@@ -707,6 +711,21 @@ def main():
         min_accept, mode = LEARNED_FORMS[form]
         smp.proposal_calibrate(CALIBRATE_SWEEPS, burnin=tb, min_accept=min_accept)
         smp.proposal_mode(mode)
+    if args.profile_run > 0:
+        torch.cuda.synchronize()
+        k0 = smp.counters()
+        torch.cuda.nvtx.range_push("profile_sweeps")
+        for _ in range(args.profile_run):
+            smp.run(1, burnin=tb, thin=thin)   # one sweep: its kernels as direct launches
+        torch.cuda.synchronize()
+        torch.cuda.nvtx.range_pop()
+        k1 = smp.counters()
+        smp.close()
+        print(json.dumps({"profile_run": args.profile_run, "form": form,
+                          "evals_per_sweep": {k: (k1[k] - k0[k]) / args.profile_run
+                                              for k in ("evals_eps", "evals_beta", "evals_nu",
+                                                        "evals_gam")}}), flush=True)
+        return
     flush = torch.empty(L2_FLUSH_BYTES, dtype=torch.uint8, device="cuda")
     for i in range(args.warmup):
         flush.fill_(i & 0xFF)
@@ -717,12 +736,14 @@ def main():
     evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
            for _ in range(args.steps)]
     c0 = smp.counters()
+    torch.cuda.nvtx.range_push("timed_steps")
     for i, (a, b) in enumerate(evs):
         flush.fill_((i + 7) & 0xFF)
         a.record(stream)
         smp.run(S, burnin=tb, thin=thin)
         b.record(stream)
     torch.cuda.synchronize()
+    torch.cuda.nvtx.range_pop()
     c1 = smp.counters()
     clk = clocks.stop()
     step_ms = [a.elapsed_time(b) for a, b in evs]

@@ -89,20 +89,22 @@ def parse():
 # --------------------------------------------------------------------------- helpers
 # FP64 floating-point operations per slice log-density evaluation of the FP64
 # sweep kernels k_eps_f64 + k_gb_f64 (DFMA counted as 2, DADD and DMUL as 1),
-# from one ncu capture of each at config 1: 2.328e8 (eps) + 1.152e8 (gb) flop
-# per sweep (per-cycle DFMA/DADD/DMUL thread counts x elapsed cycles) over the
-# 6.157e6 log-density evaluations the device counted per sweep in the captured
-# run = 56.5.  It covers everything the kernels do per evaluation on average
-# (density, Philox-to-double, interval arithmetic, the per-draw log, moments).
-# Re-measure when the kernels change.
-FP64_FLOP_PER_EVAL = 56.5
-FP64_TRAFFIC_BYTES = 44.0e6   # dram read+write of both kernels per sweep, same captures
+# from one ncu capture of each in a sampling sweep at config 1 (bench.py --form
+# f64 --profile-run 2): 1.339e8 (eps) + 1.000e8 (gb) flop per sweep over the
+# 6.141e6 log-density evaluations the device counted per sweep = 38.1.  The slice
+# comparisons are decided in FP32 (0.35% fall back to FP64), so this covers the
+# FP64 work that remains per evaluation on average (rates at accepted points,
+# log-rates, class sums and rate updates, gamma draws, interval arithmetic,
+# moments).  Re-measure when the kernels change.
+FP64_FLOP_PER_EVAL = 38.1
+FP64_TRAFFIC_BYTES = 44.1e6   # dram read+write of both kernels per sweep, same captures
 # FP32 forms: warp instructions issued per sweep (smsp__inst_executed.sum) by the
 # eps kernel and the gamma/beta kernel (k_gb_f32; with the learned proposal
-# k_gb_net_f32, which includes the network pass) and their dram read+write
-# (writes stay in L2), from ncu captures at config 1
-FP32_WARP_INST = {"f32": 21.36e6 + 10.68e6, "learned": 21.36e6 + 20.12e6}
-FP32_TRAFFIC_BYTES = {"f32": 11.2e6 + 13.2e6, "learned": 11.2e6 + 15.4e6}
+# k_gb_net_f32, which includes the network pass, in a sampling sweep after
+# calibration) and their dram read+write (writes stay in L2), from ncu captures
+# at config 1 (bench.py --profile-run; k_gb_f32 from an earlier capture)
+FP32_WARP_INST = {"f32": 22.04e6 + 10.68e6, "learned": 22.04e6 + 21.05e6}
+FP32_TRAFFIC_BYTES = {"f32": 18.9e6 + 13.2e6, "learned": 18.9e6 + 15.6e6}
 # issue peak: 152 SMs x 4 schedulers x 1 warp instruction per clock x 2.07 GHz
 ISSUE_PEAK_WARP_INST_S = 152 * 4 * 2.07e9
 # the proposal network's own flops per gene (2 x (F*64 + 64*64 + 64*K), F = 21,

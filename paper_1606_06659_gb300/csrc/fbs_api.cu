@@ -1179,21 +1179,26 @@ void learned_apply(fbs_handle* h, int mode, int mh_all) {
   }
 }
 
-// Scratch of one training step for batch size B.
+constexpr int kTrainGraphSteps = 8;  // training steps per replayed graph
+
+// Scratch of one training step for batch size B; flags: the tensor-core wait
+// flag word of the step's kernels (zeroed here).
 struct TrainBufs {
   float *fb, *yb, *part, *grad, *loss;
+  unsigned* flags;
 };
 
 // Gradient and summed loss of the minibatch in t.fb / t.yb at params.
 int mlp_step(const float* params, int L, int B, TrainBufs& t, cudaStream_t s) {
-  FBS_CUDA(launch_mlp_grad(params, L, B, t.fb, t.yb, t.part, t.grad, t.loss, s));
+  FBS_CUDA(launch_mlp_grad(params, L, B, t.fb, t.yb, t.part, t.grad, t.loss, t.flags,
+                           kTcWaitPolls, s));
   return FBS_OK;
 }
 
 int train_bufs_alloc(TrainBufs& t, int L, int B) {
   const int F = 4 * L + 1, np = mlp_param_count(L);
   memset(&t, 0, sizeof(t));
-  const size_t n = (size_t)B * (F + L) + (size_t)train_blocks(B) * (np + 1) + np + 1;
+  const size_t n = (size_t)B * (F + L) + (size_t)train_blocks(B) * (np + 1) + np + 2;
   FBS_CUDA(prepare_train_kernel(L));
   float* base = nullptr;
   FBS_CUDA(cudaMalloc((void**)&base, n * sizeof(float)));
@@ -1202,7 +1207,20 @@ int train_bufs_alloc(TrainBufs& t, int L, int B) {
   t.yb = q; q += (size_t)B * L;
   t.part = q; q += (size_t)train_blocks(B) * (np + 1);
   t.grad = q; q += np;
-  t.loss = q;
+  t.loss = q; q += 1;
+  t.flags = reinterpret_cast<unsigned*>(q);
+  FBS_CUDA(cudaMemset(t.flags, 0, sizeof(unsigned)));
+  return FBS_OK;
+}
+
+// Whether a tensor-core wait of the training kernels gave up (*flags, read
+// after the stream's work finished).
+int train_flags_ok(const TrainBufs& t, cudaStream_t s) {
+  unsigned f = 0;
+  FBS_CUDA(cudaMemcpyAsync(&f, t.flags, sizeof(f), cudaMemcpyDeviceToHost, s));
+  FBS_CUDA(cudaStreamSynchronize(s));
+  if (f & kFlagTimeout)
+    return fail(FBS_E_CUDA, "a tensor-core wait of the training step gave up");
   return FBS_OK;
 }
 
@@ -1269,9 +1287,10 @@ int fbs_proposal_train(fbs_handle* h, int epochs, int batch, double lr, uint64_t
   if (e == cudaSuccess) e = cudaStreamSynchronize(h->s);
   double log_scale = 0.0;  // NLL of raw beta = NLL of standardised beta + sum log s_beta
   for (int l = 0; l < L; ++l) log_scale += log((double)st_h[2 * F + L + l]);
-  // One training step (minibatch gather, forward, backward, Adam, bookkeeping)
-  // is captured once and replayed `steps` times; the step counter, the Adam
-  // scalars and the loss sum live in a device control block.
+  // Training steps (minibatch gather, forward, backward, Adam, bookkeeping) are
+  // captured once, kTrainGraphSteps of them in one graph and one alone, and
+  // replayed to make `steps`; the step counter, the Adam scalars and the loss
+  // sum live in a device control block.
   TrainCtl ctl;
   memset(&ctl, 0, sizeof(ctl));
   ctl.t = (unsigned long long)ls->adam_t;
@@ -1281,30 +1300,39 @@ int fbs_proposal_train(fbs_handle* h, int epochs, int batch, double lr, uint64_t
   ctl.b1 = 0.9f;
   ctl.b2 = 0.999f;
   TrainCtl* d_ctl = nullptr;
-  cudaGraphExec_t exec = nullptr;
+  cudaGraphExec_t exec[2] = {nullptr, nullptr};  // kTrainGraphSteps steps, one step
   if (e == cudaSuccess) e = cudaMalloc((void**)&d_ctl, sizeof(TrainCtl));
   if (e == cudaSuccess)
     e = cudaMemcpyAsync(d_ctl, &ctl, sizeof(ctl), cudaMemcpyHostToDevice, h->s);
-  if (e == cudaSuccess) {
+  for (int gi = 0; gi < 2 && e == cudaSuccess; ++gi) {
     cudaGraph_t graph = nullptr;
     e = cudaStreamBeginCapture(h->s, cudaStreamCaptureModeThreadLocal);
     if (e == cudaSuccess) {
-      cudaError_t ce = launch_train_step(ls->params, L, batch, ls->pair_feat, ls->pair_beta,
-                                         ls->pairs, seed, d_ctl, ls->stats, t.part, t.grad,
-                                         t.loss, ls->adam_m, ls->adam_v, h->s);
+      cudaError_t ce = cudaSuccess;
+      for (int k = 0; k < (gi == 0 ? kTrainGraphSteps : 1) && ce == cudaSuccess; ++k)
+        ce = launch_train_step(ls->params, L, batch, ls->pair_feat, ls->pair_beta, ls->pairs,
+                               seed, d_ctl, ls->stats, t.part, t.grad, t.loss, ls->adam_m,
+                               ls->adam_v, t.flags, h->pf.tc_polls, h->s);
       e = cudaStreamEndCapture(h->s, &graph);
       if (e == cudaSuccess) e = ce;
     }
-    if (e == cudaSuccess && rc == FBS_OK) e = cudaGraphInstantiate(&exec, graph, 0);
+    if (e == cudaSuccess && rc == FBS_OK) e = cudaGraphInstantiate(&exec[gi], graph, 0);
     if (graph) cudaGraphDestroy(graph);
   }
-  for (long long st = 0; st < steps && rc == FBS_OK && e == cudaSuccess; ++st)
-    e = cudaGraphLaunch(exec, h->s);
+  for (long long st = 0; st < steps / kTrainGraphSteps && rc == FBS_OK && e == cudaSuccess; ++st)
+    e = cudaGraphLaunch(exec[0], h->s);
+  for (long long st = 0; st < steps % kTrainGraphSteps && rc == FBS_OK && e == cudaSuccess; ++st)
+    e = cudaGraphLaunch(exec[1], h->s);
   if (e == cudaSuccess && rc == FBS_OK)
     e = cudaMemcpyAsync(&ctl, d_ctl, sizeof(ctl), cudaMemcpyDeviceToHost, h->s);
   if (e == cudaSuccess) e = cudaStreamSynchronize(h->s);
-  if (exec) cudaGraphExecDestroy(exec);
+  for (cudaGraphExec_t x : exec)
+    if (x) cudaGraphExecDestroy(x);
   cudaFree(d_ctl);
+  // a step whose tensor-core wait gave up left the parameters as they were; the
+  // parameters still go back to raw coordinates before the error is returned
+  int rc_wait = FBS_OK;
+  if (e == cudaSuccess && rc == FBS_OK) rc_wait = train_flags_ok(t, h->s);
   if (e == cudaSuccess && rc == FBS_OK) ls->adam_t = (long long)ctl.t;
   const double loss_epoch = ctl.loss_sum;
   if (e == cudaSuccess && rc == FBS_OK) e = launch_fold(ls->params, ls->stats, L, 1, h->s);
@@ -1313,6 +1341,7 @@ int fbs_proposal_train(fbs_handle* h, int epochs, int batch, double lr, uint64_t
   cudaFree(t.fb);
   if (rc) return rc;
   FBS_CUDA(e);
+  if (rc_wait) return rc_wait;
   ls->trained = true;
   if (final_loss) *final_loss = loss_epoch / (double)steps_per_epoch + log_scale;
   if (h->seg_exec) {
@@ -1750,6 +1779,7 @@ int fbs_proposal_loss_grad(const float* params, int L, int B, const float* feat,
   if (e == cudaSuccess) e = cudaMemcpy(t.fb, feat, sizeof(float) * (size_t)B * F, cudaMemcpyHostToDevice);
   if (e == cudaSuccess) e = cudaMemcpy(t.yb, beta, sizeof(float) * (size_t)B * L, cudaMemcpyHostToDevice);
   if (e == cudaSuccess) rc = mlp_step(dp, L, B, t, 0);
+  if (e == cudaSuccess && rc == FBS_OK) rc = train_flags_ok(t, 0);
   float l = 0.f;
   if (e == cudaSuccess && rc == FBS_OK) e = cudaMemcpy(&l, t.loss, sizeof(float), cudaMemcpyDeviceToHost);
   if (e == cudaSuccess && rc == FBS_OK && grad)

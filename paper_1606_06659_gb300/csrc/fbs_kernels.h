@@ -73,11 +73,13 @@ struct TrainCtl {
   unsigned int done;         // blocks of the current step's reduction that finished
 };
 // One training step on the device: minibatch drawn for step t + 1, forward and
-// backward, gradient reduction, Adam, control-block update (two launches).
+// backward on the tensor cores, gradient reduction, Adam, control-block update
+// (two launches).  A tensor-core wait that gives up after `polls` polls sets
+// kFlagTimeout in *flags, and the step then leaves the parameters unchanged.
 cudaError_t launch_train_step(float* params, int L, int Bsz, const float* feat, const float* beta,
                               long long M, uint64_t seed, TrainCtl* ctl, const float* st,
                               float* part, float* grad, float* loss, float* adam_m, float* adam_v,
-                              cudaStream_t s);
+                              unsigned* flags, unsigned polls, cudaStream_t s);
 int mlp_param_count(int L);
 cudaError_t launch_proposal_f32(const ModelConst& mc, const DevPtrsF32& p, const void* w_bf16,
                                 float* out, cudaStream_t s);
@@ -86,13 +88,15 @@ cudaError_t launch_collect_f32(const ModelConst& mc, const DevPtrsF32& p, float*
 cudaError_t launch_col_stats(const float* feat, const float* beta, long long M, int F, int L,
                              float* st, cudaStream_t s);
 cudaError_t launch_fold(float* params, const float* st, int L, int to_raw, cudaStream_t s);
-// one training step's gradient: fused forward/backward per block of rows, then
-// the blocks' partial sums in block order (part: [train_blocks(Bsz)][np + 1])
+// one training step's gradient: fused forward/backward per block of 128 rows on
+// the tensor cores, then the blocks' partial sums in block order (part:
+// [train_blocks(Bsz)][np + 1]); flags and polls as for launch_train_step
 size_t train_smem_bytes(int L);
 int train_blocks(int Bsz);
 cudaError_t prepare_train_kernel(int L);
 cudaError_t launch_mlp_grad(const float* params, int L, int Bsz, const float* fb, const float* yb,
-                            float* part, float* grad, float* loss, cudaStream_t s);
+                            float* part, float* grad, float* loss, unsigned* flags,
+                            unsigned polls, cudaStream_t s);
 size_t tc_image_bytes(int L);
 cudaError_t launch_pack_image(const float* params, void* img, int L, cudaStream_t s);
 

@@ -104,7 +104,9 @@ __global__ void __launch_bounds__(kTcThreads) k_proposal_tc(ModelConst mc, DevPt
   __syncthreads();
   for (int tile = blockIdx.x; tile < ntiles && !s_abort; tile += gridDim.x) {
     const int g = tile * 128 + (int)threadIdx.x;
-    if (!tc_tile(c, mc, p, t, sm, sm + off_a, g, net_gene(p, g, mc.G), out, &s_abort)) break;
+    if (!tc_tile(c, mc, p, t, sm, sm + off_a, g, net_gene(p, g, mc.G), out, (size_t)mc.G, g,
+                 &s_abort))
+      break;
   }
   tc_end(c, s_abort != 0, &p.hyp->flags);
 }
@@ -238,26 +240,10 @@ __global__ void k_fold(float* __restrict__ w, const float* __restrict__ st, int 
   }
 }
 
-// One training step's forward and backward pass of the network for
-// kTrainRows rows per block, entirely in shared memory (weights, the rows'
-// features and beta, both layers' pre-activations and activations, the
-// outputs and the back-propagated gradients), then this block's sum over its
-// rows of every parameter gradient and of the loss, written in parameter order
-// to part[block][np + 1] (the loss last).  Rows past Bsz take no part.
-//
 // Gaussian head, per row: loss = |u|^2 / 2 + sum log C_ll with C u = beta - mu;
-// dL/dout (scaled by 1/Bsz): d mu = -v, d logC_ii = 1 - v_i u_i C_ii,
-// d C_ij = -v_i u_j (i > j), where C^T v = u.
-constexpr int kTrainRows = 32;
-constexpr int kTrainThreads = 256;
-constexpr int kRowGroups = kTrainThreads / kMlpHidden;       // 4
-constexpr int kRowsPerThread = kTrainRows / kRowGroups;      // 8
-
-__host__ __device__ inline int train_smem_floats(int L) {
-  const int H = kMlpHidden, HP = H + 1, F = 4 * L + 1, K = L + L * (L + 1) / 2, R = kTrainRows;
-  return H * F + H * HP + K * HP + 2 * H + K + R * F + R * L + 6 * R * H + R * K + 32;
-}
-
+// dL/dout (scaled by sc = 1/Bsz): d mu = -v, d logC_ii = 1 - v_i u_i C_ii,
+// d C_ij = -v_i u_j (i > j), where C^T v = u.  o holds the outputs on entry and
+// dL/dout on return.
 __device__ __forceinline__ void nll_row(float* o, const float* y, int L, float sc, float* loss) {
   float C[kMaxL][kMaxL], u[kMaxL], v[kMaxL];
   for (int i = 0; i < L; ++i)
@@ -290,199 +276,394 @@ __device__ __forceinline__ void nll_row(float* o, const float* y, int L, float s
   *loss = ls;
 }
 
-// Rows: fb / yb [Bsz][F], [Bsz][L] as given, or (feat != null) a minibatch drawn
-// with replacement from the M pairs feat [M][F], beta [M][L] for the step the
-// control block describes (Philox stream kStreamTrain, index = row, iteration
-// t + 1), standardised with st = (feature means, feature scales, beta means,
-// beta scales).
-__global__ void __launch_bounds__(kTrainThreads) k_mlp_fwd_bwd(
+// ---------------------------------------------------------------- training step (tensor cores)
+//
+// One training step's forward and backward pass for 128 minibatch rows per
+// block (thread t = row t = tensor-memory lane t), every matrix product on the
+// tensor cores (tcgen05, BF16 operands split as x = hi + lo, hi*hi + lo*hi +
+// hi*lo accumulated in FP32, about 16 significant bits per operand):
+//   forward   Z1 = X W1^T, A1 = gelu(Z1 + b1); Z2 = A1 W2^T, A2 = gelu(Z2 + b2);
+//             O = A2 W3^T + b3; the Gaussian head gives the loss and dO = dL/dO
+//   backward  G2 = (dO W3) . gelu'(Z2 + b2); G1 = (G2 W2) . gelu'(Z1 + b1)
+//   weights   one product of [G2 | A2]^T (128 rows) with [A1 | X, 1 | dO] over
+//             the block's rows gives dW2, db2 (the column of ones appended to
+//             X) and dW3^T; a second, of [X, 1 | ..]^T with G1, gives dW1^T and
+//             db1; db3 is a warp sum of dO.
+// The forward and backward products read K-major operands (one row per
+// thread); the weight-gradient products read the same bytes as MN-major
+// operands (K = the block's rows), and the backward products read the weight
+// images as MN-major operands, so nothing is transposed.  The block's sums
+// over its rows of every parameter gradient and of the loss go to
+// part[block][np + 1] in parameter order (the loss last); rows past Bsz take
+// no part.  Every wait on the tensor cores is bounded by `polls`; a wait that
+// gives up sets kFlagTimeout in *flags and the block returns after draining.
+//
+// Shared memory, in 16-byte chunks of 8 BF16 values, each operand row a hi
+// half then a lo half:
+//   W1 [64][k1], W2 [64][64], W3 [n3][64]    weight images (K-major)
+//   b1 [64], b2 [64], b3 [n3]                FP32
+//   bufF rows  [A1 (64) | X, 1 (k1) | dO (n3)]
+//   bufG rows  [G2 (64) | A2 (64)]
+//   bufG1 rows [G1 (64)]
+// Tensor memory (512 columns): Z1 at 0, Z2 64, O 128, dO W3 192, G2 W2 256,
+// the first weight-gradient product 320 (64 + k1 + n3 columns), the second 128.
+struct TrainTc {
+  int F, K, k1, n3, cx, co, half;  // half: chunks in a half row of bufF
+  uint32_t sbo_w1, sbo_f;          // 8-row group strides of W1 and bufF
+  uint32_t off_w2, off_w3, off_b, off_f, off_g, off_g1, bytes;
+};
+
+__host__ __device__ inline TrainTc train_tc_shape(int L) {
+  TrainTc t;
+  t.F = 4 * L + 1;
+  t.K = L + L * (L + 1) / 2;
+  t.k1 = (t.F + 1 + 15) & ~15;  // the features and the column of ones
+  t.n3 = (t.K + 15) & ~15;
+  t.cx = t.k1 / 8;
+  t.co = t.n3 / 8;
+  t.half = 8 + t.cx + t.co;
+  t.sbo_w1 = (uint32_t)(2 * t.cx * 128);
+  t.sbo_f = (uint32_t)(2 * t.half * 128);
+  t.off_w2 = 8 * t.sbo_w1;
+  t.off_w3 = t.off_w2 + 8 * 2048;
+  t.off_b = t.off_w3 + (uint32_t)(t.n3 / 8) * 2048;
+  t.off_f = (t.off_b + (uint32_t)(128 + t.n3) * 4 + 1023) & ~1023u;
+  t.off_g = t.off_f + 16 * t.sbo_f;  // the second weight-gradient product reads up to
+  t.off_g1 = t.off_g + 16 * 4096;    // 24 - half chunks past bufF, inside bufG
+  t.bytes = t.off_g1 + 16 * 2048;
+  return t;
+}
+
+constexpr uint32_t kTrainTmemCols = 512;
+constexpr int kTrainOutPad = (kMaxOut + 15) & ~15;
+
+// D (+)= A B^T over 16 ksteps rows of K for the three split products hi*hi,
+// lo*hi, hi*lo.  Each operand: start addresses of its hi and lo halves, the
+// address step per 16 rows of K, and its descriptor's leading and stride byte
+// offsets.
+__device__ __forceinline__ void issue_split(uint32_t d, uint32_t idesc, int ksteps, uint32_t a_hi,
+                                            uint32_t a_lo, uint32_t a_step, uint32_t a_lbo,
+                                            uint32_t a_sbo, uint32_t b_hi, uint32_t b_lo,
+                                            uint32_t b_step, uint32_t b_lbo, uint32_t b_sbo) {
+  const uint32_t pa[3] = {a_hi, a_lo, a_hi}, pb[3] = {b_hi, b_hi, b_lo};
+  uint32_t acc = 0u;
+#pragma unroll
+  for (int q = 0; q < 3; ++q)
+    for (int k = 0; k < ksteps; ++k) {
+      umma_bf16(d, umma_desc_ls(pa[q] + k * a_step, a_lbo, a_sbo),
+                umma_desc_ls(pb[q] + k * b_step, b_lbo, b_sbo), idesc, acc);
+      acc = 1u;
+    }
+}
+
+// Block barrier, then (thread 0) the products `issue` describes and a commit;
+// every thread waits for their completion, and a second block barrier makes
+// the outcome the same for every thread: false once any wait gave up.
+template <class Issue>
+__device__ __forceinline__ bool tc_run(TcBlock& c, volatile int* s_abort, Issue issue) {
+  fence_async_smem();
+  tc_fence_before();
+  __syncthreads();
+  if (*s_abort) return false;
+  if (threadIdx.x == 0) {
+    tc_fence_after();
+    issue();
+    umma_commit(c.bar_m);
+  }
+  c.pending = true;
+  if (!mbar_wait(c.bar_m, c.ph, c.polls)) *s_abort = 1;
+  else c.pending = false;
+  c.ph ^= 1u;
+  tc_fence_after();
+  __syncthreads();
+  return *s_abort == 0;
+}
+
+__global__ void __launch_bounds__(128) k_mlp_tc(
     const float* __restrict__ params, int L, int Bsz, const float* __restrict__ fb,
     const float* __restrict__ yb, const float* __restrict__ feat,
     const float* __restrict__ beta, long long M, uint32_t seed_lo, uint32_t seed_hi,
-    const TrainCtl* __restrict__ ctl, const float* __restrict__ st, float* __restrict__ part) {
-  extern __shared__ __align__(1024) uint8_t sm_raw[];
-  float* sm = reinterpret_cast<float*>(sm_raw);
-  constexpr int H = kMlpHidden, HP = kMlpHidden + 1, R = kTrainRows, T = kTrainThreads;
-  const int F = 4 * L + 1, K = L + L * (L + 1) / 2;
+    const TrainCtl* __restrict__ ctl, const float* __restrict__ st, float* __restrict__ part,
+    unsigned* __restrict__ flags, unsigned polls) {
+  extern __shared__ __align__(1024) uint8_t sm[];
+  __shared__ __align__(8) uint64_t bars[2];
+  __shared__ uint32_t tmem_slot;
+  __shared__ int s_abort;
+  __shared__ float s_db3[4][kTrainOutPad];
+  __shared__ float s_loss[4];
+  constexpr int H = kMlpHidden;
+  const TrainTc t = train_tc_shape(L);
+  const int F = t.F, K = t.K, half = t.half;
   const int np = mlp_n_params(F, K);
-  // weights: W1 [H][F]; W2 and W3 padded to H+1 columns (conflict-free reads by
-  // output row and by input column)
-  float* sW1 = sm;
-  float* sW2 = sW1 + H * F;
-  float* sW3 = sW2 + H * HP;
-  float* sb1 = sW3 + K * HP;
-  float* sb2 = sb1 + H;
-  float* sb3 = sb2 + H;
-  float* sX = sb3 + K;        // [R][F]
-  float* sY = sX + R * F;     // [R][L]
-  float* sZ1 = sY + R * L;    // [R][H] pre-activations and activations
-  float* sA1 = sZ1 + R * H;
-  float* sZ2 = sA1 + R * H;
-  float* sA2 = sZ2 + R * H;
-  float* sG2 = sA2 + R * H;   // dL/dz2
-  float* sG1 = sG2 + R * H;   // dL/dz1
-  float* sD = sG1 + R * H;    // [R][K] outputs, then dL/dout
-  float* sred = sD + R * K;   // [32]
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  const int r0 = blockIdx.x * 128;
+  const bool row_ok = tid < Bsz - r0;
+  uint8_t* w1s = sm;
+  uint8_t* w2s = sm + t.off_w2;
+  uint8_t* w3s = sm + t.off_w3;
+  float* bsm = reinterpret_cast<float*>(sm + t.off_b);
+  uint8_t* bF = sm + t.off_f;
+  uint8_t* bG = sm + t.off_g;
+  uint8_t* bG1 = sm + t.off_g1;
   const float* W1 = params;
   const float* b1 = W1 + H * F;
   const float* W2 = b1 + H;
   const float* b2 = W2 + H * H;
   const float* W3 = b2 + H;
   const float* b3 = W3 + K * H;
-  const int tid = threadIdx.x;
-  const int r0 = blockIdx.x * R;
-  const int nr = min(R, Bsz - r0);
-  __shared__ long long srow[R];
-  if (feat != nullptr && tid < nr) {
-    Rng rg(seed_lo, seed_hi, 0u, kStreamTrain, (uint32_t)(r0 + tid), (uint32_t)(ctl->t + 1));
-    long long m = (long long)(rg.u(0) * (double)M);
-    srow[tid] = m >= M ? M - 1 : m;
-  }
-#pragma unroll 4
-  for (int i = tid; i < H * F; i += T) sW1[i] = W1[i];
-#pragma unroll 4
-  for (int i = tid; i < H * H; i += T) sW2[(i / H) * HP + i % H] = W2[i];
-#pragma unroll 4
-  for (int i = tid; i < K * H; i += T) sW3[(i / H) * HP + i % H] = W3[i];
-  for (int i = tid; i < H; i += T) {
-    sb1[i] = b1[i];
-    sb2[i] = b2[i];
-  }
-  for (int i = tid; i < K; i += T) sb3[i] = b3[i];
-  if (feat != nullptr) {
-    __syncthreads();  // srow
-    const float* mf = st;
-    const float* sf = st + F;
-    const float* mb = st + 2 * F;
-    const float* sb = st + 2 * F + L;
-    for (int i = tid; i < R * F; i += T) {
-      const int r = i / F, f = i % F;
-      sX[i] = r < nr ? (feat[(size_t)srow[r] * F + f] - mf[f]) / sf[f] : 0.0f;
-    }
-    for (int i = tid; i < R * L; i += T) {
-      const int r = i / L, l = i % L;
-      sY[i] = r < nr ? (beta[(size_t)srow[r] * L + l] - mb[l]) / sb[l] : 0.0f;
-    }
-  } else {
-    for (int i = tid; i < R * F; i += T)
-      sX[i] = i / F < nr ? fb[(size_t)r0 * F + i] : 0.0f;
-    for (int i = tid; i < R * L; i += T)
-      sY[i] = i / L < nr ? yb[(size_t)r0 * L + i] : 0.0f;
-  }
-  __syncthreads();
 
-  // thread: unit h of a layer for rows rq, rq + 4, ..
-  const int h = tid % H, rq = tid / H;
-  float acc[kRowsPerThread];
-  // layer 1
-#pragma unroll
-  for (int i = 0; i < kRowsPerThread; ++i) acc[i] = sb1[h];
-  for (int f = 0; f < F; ++f) {
-    const float w = sW1[h * F + f];
-#pragma unroll
-    for (int i = 0; i < kRowsPerThread; ++i) acc[i] += w * sX[(rq + kRowGroups * i) * F + f];
+  TcBlock c;
+  c.polls = polls;
+  c.cols = kTrainTmemCols;  // what the dealloc of tc_end frees
+  c.bar_w = smem_u32(&bars[0]);
+  c.bar_m = smem_u32(&bars[1]);
+  c.ph = 0;
+  c.pending = false;
+  c.w_ok = true;  // no bulk copy: the block writes the weight images itself
+  if (tid == 0) {
+    s_abort = 0;
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(c.bar_m) : "memory");
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
   }
-#pragma unroll
-  for (int i = 0; i < kRowsPerThread; ++i) {
-    const int r = rq + kRowGroups * i;
-    sZ1[r * H + h] = acc[i];
-    sA1[r * H + h] = gelu_f(acc[i]);
+  if (warp == 0) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(
+                     smem_u32(&tmem_slot)),
+                 "r"(kTrainTmemCols)
+                 : "memory");
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
   }
-  __syncthreads();
-  // layer 2
+
+  // the weight images (zero padding beyond F columns of W1 and K rows of W3)
+  const int n_w1 = 64 * t.cx, n_w2 = 64 * 8, n_w3 = t.n3 * 8;
+  for (int i = tid; i < n_w1 + n_w2 + n_w3; i += 128) {
+    float v[8];
+    if (i < n_w1) {
+      const int h = i / t.cx, q = i % t.cx;
 #pragma unroll
-  for (int i = 0; i < kRowsPerThread; ++i) acc[i] = sb2[h];
-  for (int k = 0; k < H; ++k) {
-    const float w = sW2[h * HP + k];
+      for (int j = 0; j < 8; ++j) v[j] = 8 * q + j < F ? W1[h * F + 8 * q + j] : 0.0f;
+      store_split8_ch(w1s, t.sbo_w1, h, q, q + t.cx, v);
+    } else if (i < n_w1 + n_w2) {
+      const int h = (i - n_w1) / 8, q = (i - n_w1) % 8;
 #pragma unroll
-    for (int i = 0; i < kRowsPerThread; ++i) acc[i] += w * sA1[(rq + kRowGroups * i) * H + k];
-  }
-#pragma unroll
-  for (int i = 0; i < kRowsPerThread; ++i) {
-    const int r = rq + kRowGroups * i;
-    sZ2[r * H + h] = acc[i];
-    sA2[r * H + h] = gelu_f(acc[i]);
-  }
-  __syncthreads();
-  // output layer
-  for (int e = tid; e < R * K; e += T) {
-    const int r = e / K, j = e % K;
-    float a = sb3[j];
-    for (int k = 0; k < H; ++k) a += sW3[j * HP + k] * sA2[r * H + k];
-    sD[e] = a;
-  }
-  __syncthreads();
-  // head: one thread per row
-  float loss = 0.0f;
-  if (tid < R) {
-    if (tid < nr) {
-      nll_row(sD + tid * K, sY + tid * L, L, 1.0f / (float)Bsz, &loss);
+      for (int j = 0; j < 8; ++j) v[j] = W2[h * H + 8 * q + j];
+      store_split8_ch(w2s, 2048, h, q, q + 8, v);
     } else {
-      for (int j = 0; j < K; ++j) sD[tid * K + j] = 0.0f;
+      const int k = (i - n_w1 - n_w2) / 8, q = (i - n_w1 - n_w2) % 8;
+#pragma unroll
+      for (int j = 0; j < 8; ++j) v[j] = k < K ? W3[k * H + 8 * q + j] : 0.0f;
+      store_split8_ch(w3s, 2048, k, q, q + 8, v);
     }
   }
-  if (tid < 32) {
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) loss += __shfl_down_sync(0xffffffffu, loss, o);
-    if (tid == 0) sred[0] = loss;
+  for (int i = tid; i < 2 * H + t.n3; i += 128)
+    bsm[i] = i < H ? b1[i] : (i < 2 * H ? b2[i - H] : (i - 2 * H < K ? b3[i - 2 * H] : 0.0f));
+
+  // this thread's row: features and the column of ones (split into bufF), beta
+  long long srow = 0;
+  if (feat != nullptr && row_ok) {
+    Rng rg(seed_lo, seed_hi, 0u, kStreamTrain, (uint32_t)(r0 + tid), (uint32_t)(ctl->t + 1));
+    const long long m = (long long)(rg.u(0) * (double)M);
+    srow = m >= M ? M - 1 : m;
   }
-  __syncthreads();
-  // dL/dz2 = (dL/dout W3) * gelu'(z2)
+  for (int q = 0; q < t.cx; ++q) {
+    float v[8];
 #pragma unroll
-  for (int i = 0; i < kRowsPerThread; ++i) acc[i] = 0.0f;
-  for (int j = 0; j < K; ++j) {
-    const float w = sW3[j * HP + h];
-#pragma unroll
-    for (int i = 0; i < kRowsPerThread; ++i) acc[i] += sD[(rq + kRowGroups * i) * K + j] * w;
-  }
-#pragma unroll
-  for (int i = 0; i < kRowsPerThread; ++i) {
-    const int r = rq + kRowGroups * i;
-    sG2[r * H + h] = acc[i] * gelu_grad_f(sZ2[r * H + h]);
-  }
-  __syncthreads();
-  // dL/dz1 = (dL/dz2 W2) * gelu'(z1)
-#pragma unroll
-  for (int i = 0; i < kRowsPerThread; ++i) acc[i] = 0.0f;
-  for (int k = 0; k < H; ++k) {
-    const float w = sW2[k * HP + h];
-#pragma unroll
-    for (int i = 0; i < kRowsPerThread; ++i) acc[i] += sG2[(rq + kRowGroups * i) * H + k] * w;
-  }
-#pragma unroll
-  for (int i = 0; i < kRowsPerThread; ++i) {
-    const int r = rq + kRowGroups * i;
-    sG1[r * H + h] = acc[i] * gelu_grad_f(sZ1[r * H + h]);
-  }
-  __syncthreads();
-  // this block's gradient sums over its rows, in parameter order
-  float* out = part + (size_t)blockIdx.x * (np + 1);
-  // offsets: W1 at 0, then b1, W2, b2, W3, b3
-  const int ob1 = H * F, oW2 = ob1 + H, ob2 = oW2 + H * H, oW3 = ob2 + H, ob3 = oW3 + K * H;
-  for (int p = tid; p < np; p += T) {
-    float g = 0.0f;
-    if (p < ob1) {
-      const int u = p / F, f = p % F;
-      for (int r = 0; r < R; ++r) g += sG1[r * H + u] * sX[r * F + f];
-    } else if (p < oW2) {
-      const int u = p - ob1;
-      for (int r = 0; r < R; ++r) g += sG1[r * H + u];
-    } else if (p < ob2) {
-      const int q = p - oW2, u = q / H, k = q % H;
-      for (int r = 0; r < R; ++r) g += sG2[r * H + u] * sA1[r * H + k];
-    } else if (p < oW3) {
-      const int u = p - ob2;
-      for (int r = 0; r < R; ++r) g += sG2[r * H + u];
-    } else if (p < ob3) {
-      const int q = p - oW3, j = q / H, k = q % H;
-      for (int r = 0; r < R; ++r) g += sD[r * K + j] * sA2[r * H + k];
-    } else {
-      const int j = p - ob3;
-      for (int r = 0; r < R; ++r) g += sD[r * K + j];
+    for (int j = 0; j < 8; ++j) {
+      const int f = 8 * q + j;
+      float x = 0.0f;
+      if (row_ok) {
+        if (f < F)
+          x = feat != nullptr ? (feat[(size_t)srow * F + f] - st[f]) / st[F + f]
+                              : fb[(size_t)(r0 + tid) * F + f];
+        else if (f == F)
+          x = 1.0f;
+      }
+      v[j] = x;
     }
-    out[p] = g;
+    store_split8_ch(bF, t.sbo_f, tid, 8 + q, 8 + q + half, v);
   }
-  if (tid == 0) out[np] = sred[0];
+  float y[kMaxL];
+#pragma unroll
+  for (int l = 0; l < kMaxL; ++l) {
+    y[l] = 0.0f;
+    if (l < L && row_ok)
+      y[l] = feat != nullptr ? (beta[(size_t)srow * L + l] - st[2 * F + l]) / st[2 * F + L + l]
+                             : yb[(size_t)(r0 + tid) * L + l];
+  }
+
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  c.tmem = tmem_slot;
+  const uint32_t tm = c.tmem, la = (uint32_t)(warp * 32) << 16;
+  const uint32_t sF = smem_u32(bF), sG = smem_u32(bG), sG1 = smem_u32(bG1);
+  const uint32_t sW1 = smem_u32(w1s), sW2 = smem_u32(w2s), sW3 = smem_u32(w3s);
+  const uint32_t sbo_f = t.sbo_f, hb = (uint32_t)half * 128;
+  const int cx = t.cx, k1 = t.k1, n3 = t.n3;
+  bool ok = true;
+
+  // ---- forward
+  ok = tc_run(c, &s_abort, [&] {  // Z1 = X W1^T
+    issue_split(tm, umma_idesc_bf16(128, H), k1 / 16, sF + 8 * 128, sF + 8 * 128 + hb, 256, 128,
+                sbo_f, sW1, sW1 + cx * 128, 256, 128, t.sbo_w1);
+  });
+  if (ok) {
+#pragma unroll
+    for (int h = 0; h < 2; ++h) {
+      float v[32];
+      tmem_ld32(tm + la + 32 * h, v);
+#pragma unroll
+      for (int i = 0; i < 32; ++i) v[i] = gelu_f(v[i] + bsm[32 * h + i]);
+#pragma unroll
+      for (int q = 0; q < 4; ++q) store_split8_ch(bF, sbo_f, tid, 4 * h + q, 4 * h + q + half, v + 8 * q);
+    }
+    ok = tc_run(c, &s_abort, [&] {  // Z2 = A1 W2^T
+      issue_split(tm + 64, umma_idesc_bf16(128, H), 4, sF, sF + hb, 256, 128, sbo_f, sW2,
+                  sW2 + 8 * 128, 256, 128, 2048);
+    });
+  }
+  if (ok) {
+#pragma unroll
+    for (int h = 0; h < 2; ++h) {
+      float v[32];
+      tmem_ld32(tm + la + 64 + 32 * h, v);
+#pragma unroll
+      for (int i = 0; i < 32; ++i) v[i] = gelu_f(v[i] + bsm[H + 32 * h + i]);
+#pragma unroll
+      for (int q = 0; q < 4; ++q) store_split8_ch(bG, 4096, tid, 8 + 4 * h + q, 24 + 4 * h + q, v + 8 * q);
+    }
+    ok = tc_run(c, &s_abort, [&] {  // O = A2 W3^T
+      issue_split(tm + 128, umma_idesc_bf16(128, n3), 4, sG + 8 * 128, sG + 24 * 128, 256, 128,
+                  4096, sW3, sW3 + 8 * 128, 256, 128, 2048);
+    });
+  }
+  // ---- head: loss and dO (rows past Bsz: zero), dO into bufF, warp sums of dO
+  if (ok) {
+    float o[kTrainOutPad];
+#pragma unroll
+    for (int c0 = 0; c0 < kTrainOutPad; c0 += 16)
+      if (c0 < n3) {
+        float v[16];
+        tmem_ld16(tm + la + 128 + (uint32_t)c0, v);
+#pragma unroll
+        for (int i = 0; i < 16; ++i) o[c0 + i] = v[i] + bsm[2 * H + c0 + i];
+      }
+    float loss = 0.0f;
+    if (row_ok) nll_row(o, y, L, 1.0f / (float)Bsz, &loss);
+#pragma unroll
+    for (int k = 0; k < kTrainOutPad; ++k)
+      if (!row_ok || k >= K) o[k] = 0.0f;
+#pragma unroll
+    for (int q = 0; q < kTrainOutPad / 8; ++q)
+      if (q < t.co) store_split8_ch(bF, sbo_f, tid, 8 + cx + q, 8 + cx + q + half, o + 8 * q);
+#pragma unroll
+    for (int k = 0; k < kTrainOutPad; ++k) {
+      if (k < K) {
+        float v = o[k];
+#pragma unroll
+        for (int sh = 16; sh > 0; sh >>= 1) v += __shfl_xor_sync(0xffffffffu, v, sh);
+        if (lane == 0) s_db3[warp][k] = v;
+      }
+    }
+#pragma unroll
+    for (int sh = 16; sh > 0; sh >>= 1) loss += __shfl_xor_sync(0xffffffffu, loss, sh);
+    if (lane == 0) s_loss[warp] = loss;
+    ok = tc_run(c, &s_abort, [&] {  // dO W3 (W3 read as an MN-major B)
+      issue_split(tm + 192, umma_idesc_bf16_mn(128, H, 0, 1), n3 / 16, sF + (8 + cx) * 128,
+                  sF + (8 + cx) * 128 + hb, 256, 128, sbo_f, sW3, sW3 + 8 * 128, 4096, 2048, 128);
+    });
+  }
+  // ---- backward
+  if (ok) {
+#pragma unroll
+    for (int h = 0; h < 2; ++h) {
+      float d[32], z[32];
+      tmem_ld32(tm + la + 192 + 32 * h, d);
+      tmem_ld32(tm + la + 64 + 32 * h, z);
+#pragma unroll
+      for (int i = 0; i < 32; ++i) d[i] *= gelu_grad_f(z[i] + bsm[H + 32 * h + i]);
+#pragma unroll
+      for (int q = 0; q < 4; ++q) store_split8_ch(bG, 4096, tid, 4 * h + q, 16 + 4 * h + q, d + 8 * q);
+    }
+    ok = tc_run(c, &s_abort, [&] {  // G2 W2 (W2 read as an MN-major B)
+      issue_split(tm + 256, umma_idesc_bf16_mn(128, H, 0, 1), 4, sG, sG + 16 * 128, 256, 128,
+                  4096, sW2, sW2 + 8 * 128, 4096, 2048, 128);
+    });
+  }
+  if (ok) {
+#pragma unroll
+    for (int h = 0; h < 2; ++h) {
+      float d[32], z[32];
+      tmem_ld32(tm + la + 256 + 32 * h, d);
+      tmem_ld32(tm + la + 32 * h, z);
+#pragma unroll
+      for (int i = 0; i < 32; ++i) d[i] *= gelu_grad_f(z[i] + bsm[32 * h + i]);
+#pragma unroll
+      for (int q = 0; q < 4; ++q) store_split8_ch(bG1, 2048, tid, 4 * h + q, 8 + 4 * h + q, d + 8 * q);
+    }
+    // the weight gradients: K = the block's 128 rows, both operands MN-major
+    ok = tc_run(c, &s_abort, [&] {
+      issue_split(tm + 320, umma_idesc_bf16_mn(128, H + k1 + n3, 1, 1), 8, sG, sG + 16 * 128,
+                  2 * 4096, 4096, 128, sF, sF + hb, 2 * sbo_f, sbo_f, 128);
+      issue_split(tm + 128, umma_idesc_bf16_mn(128, H, 1, 1), 8, sF + 8 * 128,
+                  sF + 8 * 128 + hb, 2 * sbo_f, sbo_f, 128, sG1, sG1 + 8 * 128, 2 * 2048, 2048,
+                  128);
+    });
+  }
+  // ---- this block's sums, in parameter order: W1 [64][F], b1, W2 [64][64], b2,
+  // W3 [K][64], b3, loss
+  if (ok) {
+    float* out = part + (size_t)blockIdx.x * (np + 1);
+    const int oW1 = 0, ob1 = H * F, oW2 = ob1 + H, ob2 = oW2 + H * H, oW3 = ob2 + H,
+              ob3 = oW3 + K * H;
+    if (warp < 2) {
+      // first product, rows 0..63 (unit of G2): dW2 in columns 0..63, db2 in column 64 + F
+#pragma unroll
+      for (int h = 0; h < 2; ++h) {
+        float v[32];
+        tmem_ld32(tm + la + 320 + 32 * h, v);
+#pragma unroll
+        for (int i = 0; i < 32; ++i) out[oW2 + tid * H + 32 * h + i] = v[i];
+      }
+      {
+        float v[16];
+        const int cb = H + (F / 16) * 16;
+        tmem_ld16(tm + la + 320 + (uint32_t)cb, v);
+#pragma unroll
+        for (int i = 0; i < 16; ++i)
+          if (cb + i == H + F) out[ob2 + tid] = v[i];
+      }
+      // second product, rows 0..63 (feature m of X, then the ones at m = F):
+      // dW1^T and db1 in columns 0..63
+#pragma unroll
+      for (int h = 0; h < 2; ++h) {
+        float v[32];
+        tmem_ld32(tm + la + 128 + 32 * h, v);
+        if (tid < F) {
+#pragma unroll
+          for (int i = 0; i < 32; ++i) out[oW1 + (32 * h + i) * F + tid] = v[i];
+        } else if (tid == F) {
+#pragma unroll
+          for (int i = 0; i < 32; ++i) out[ob1 + 32 * h + i] = v[i];
+        }
+      }
+    } else {
+      // first product, rows 64..127 (unit of A2): dW3^T in columns 64 + k1 + k
+      const int u = tid - H;
+#pragma unroll
+      for (int c0 = 0; c0 < kTrainOutPad; c0 += 16)
+        if (c0 < n3) {
+          float v[16];
+          tmem_ld16(tm + la + 320 + (uint32_t)(H + k1 + c0), v);
+#pragma unroll
+          for (int i = 0; i < 16; ++i)
+            if (c0 + i < K) out[oW3 + (c0 + i) * H + u] = v[i];
+        }
+    }
+    __syncthreads();  // s_db3, s_loss (written before the last products)
+    if (tid < K) out[ob3 + tid] = s_db3[0][tid] + s_db3[1][tid] + s_db3[2][tid] + s_db3[3][tid];
+    if (tid == 0) out[np] = s_loss[0] + s_loss[1] + s_loss[2] + s_loss[3];
+  }
+  tc_end(c, s_abort != 0, flags);
 }
 
 // Adam (Kingma & Ba 2015) step sizes of the step the control block describes:
@@ -502,11 +683,15 @@ __device__ __forceinline__ void adam_scalars(const TrainCtl* c, float* c1, float
 // block b takes parameters 32b..32b+31, warp w the partial rows w, w + 8, ..,
 // and warp 0 adds the eight warp sums in order.  With a control block it also
 // applies Adam to w, m, v and, in the last block to finish (ticket counter, no
-// waiting), adds the loss to the last epoch's sum and advances t and k.
+// waiting), adds the loss to the last epoch's sum and advances t and k.  Does
+// nothing once *flags is set (a tensor-core wait of the forward and backward
+// pass gave up, so the partials are incomplete).
 __global__ void __launch_bounds__(256) k_reduce_adam(const float* __restrict__ part, int nblk,
                                                      int np, float* __restrict__ grad,
                                                      float* __restrict__ loss, float* w, float* m,
-                                                     float* v, TrainCtl* ctl, int B, float eps) {
+                                                     float* v, TrainCtl* ctl, int B, float eps,
+                                                     const unsigned* __restrict__ flags) {
+  if (*(volatile const unsigned*)flags != 0u) return;
   __shared__ float red[8][33];
   const int lane = threadIdx.x & 31, wp = threadIdx.x >> 5;
   const int p = blockIdx.x * 32 + lane;
@@ -600,37 +785,38 @@ cudaError_t launch_fold(float* params, const float* st, int L, int to_raw, cudaS
   return cudaGetLastError();
 }
 
-size_t train_smem_bytes(int L) { return (size_t)train_smem_floats(L) * sizeof(float); }
+size_t train_smem_bytes(int L) { return (size_t)train_tc_shape(L).bytes; }
 
-int train_blocks(int Bsz) { return (Bsz + kTrainRows - 1) / kTrainRows; }
+int train_blocks(int Bsz) { return (Bsz + 127) / 128; }
 
 cudaError_t prepare_train_kernel(int L) {
-  return cudaFuncSetAttribute(k_mlp_fwd_bwd, cudaFuncAttributeMaxDynamicSharedMemorySize,
+  return cudaFuncSetAttribute(k_mlp_tc, cudaFuncAttributeMaxDynamicSharedMemorySize,
                               (int)train_smem_bytes(L));
 }
 
 cudaError_t launch_mlp_grad(const float* params, int L, int Bsz, const float* fb, const float* yb,
-                            float* part, float* grad, float* loss, cudaStream_t s) {
+                            float* part, float* grad, float* loss, unsigned* flags,
+                            unsigned polls, cudaStream_t s) {
   const int nblk = train_blocks(Bsz);
   const int np = mlp_param_count(L);
-  k_mlp_fwd_bwd<<<nblk, kTrainThreads, train_smem_bytes(L), s>>>(
-      params, L, Bsz, fb, yb, nullptr, nullptr, 0, 0u, 0u, nullptr, nullptr, part);
+  k_mlp_tc<<<nblk, 128, train_smem_bytes(L), s>>>(params, L, Bsz, fb, yb, nullptr, nullptr, 0,
+                                                  0u, 0u, nullptr, nullptr, part, flags, polls);
   k_reduce_adam<<<(np + 1 + 31) / 32, 256, 0, s>>>(part, nblk, np, grad, loss, nullptr, nullptr,
-                                                   nullptr, nullptr, Bsz, 0.0f);
+                                                   nullptr, nullptr, Bsz, 0.0f, flags);
   return cudaGetLastError();
 }
 
 cudaError_t launch_train_step(float* params, int L, int Bsz, const float* feat, const float* beta,
                               long long M, uint64_t seed, TrainCtl* ctl, const float* st,
                               float* part, float* grad, float* loss, float* adam_m, float* adam_v,
-                              cudaStream_t s) {
+                              unsigned* flags, unsigned polls, cudaStream_t s) {
   const int nblk = train_blocks(Bsz);
   const int np = mlp_param_count(L);
-  k_mlp_fwd_bwd<<<nblk, kTrainThreads, train_smem_bytes(L), s>>>(
-      params, L, Bsz, nullptr, nullptr, feat, beta, M, (uint32_t)seed, (uint32_t)(seed >> 32),
-      ctl, st, part);
+  k_mlp_tc<<<nblk, 128, train_smem_bytes(L), s>>>(params, L, Bsz, nullptr, nullptr, feat, beta, M,
+                                                  (uint32_t)seed, (uint32_t)(seed >> 32), ctl, st,
+                                                  part, flags, polls);
   k_reduce_adam<<<(np + 1 + 31) / 32, 256, 0, s>>>(part, nblk, np, grad, loss, params, adam_m,
-                                                   adam_v, ctl, Bsz, 1e-8f);
+                                                   adam_v, ctl, Bsz, 1e-8f, flags);
   return cudaGetLastError();
 }
 

@@ -133,6 +133,81 @@ __device__ __forceinline__ void store_split8(uint8_t* base, int kin, int r, int 
   *(uint4*)(base + canon_off(r, kin + c0, 2 * kin)) = make_uint4(l[0], l[1], l[2], l[3]);
 }
 
+// The features of gene g for L = LL columns, split into row `row` of the first
+// operand (2 k1 columns): the same operations in the same order as
+// gene_features, with every global load issued before the arithmetic so that
+// their latencies overlap, and every feature slot a compile-time index, so that
+// the features stay in registers.  act = false stores zeros.
+template <int LL>
+__device__ __forceinline__ void features_split(const ModelConst& mc, const DevPtrsF32& p, int g,
+                                               const Hyper* hy, bool act, int k1, uint8_t* abuf,
+                                               int row) {
+  constexpr int F = 4 * LL + 1;
+  constexpr int K1 = (F + 15) & ~15;
+  float f[K1];
+#pragma unroll
+  for (int i = 0; i < K1; ++i) f[i] = 0.0f;
+  if (act) {
+    const int G = mc.G, N = mc.N;
+    float b[LL], tl[LL], th[LL], s2[LL], a[LL];
+#pragma unroll
+    for (int l = 0; l < LL; ++l) {
+      b[l] = p.beta[(size_t)l * G + g];
+      tl[l] = (float)p.T[(size_t)l * G + g];
+      th[l] = (float)hy->phi[2 + l];
+      s2[l] = (float)hy->phi[2 + LL + l];
+      a[l] = 0.0f;
+    }
+    const float gm = p.gam[g];
+    for (int n0 = 0; n0 < N; n0 += 16) {
+      float ev[16];
+#pragma unroll
+      for (int i = 0; i < 16; ++i) ev[i] = n0 + i < N ? p.eps[(size_t)(n0 + i) * G + g] : 0.0f;
+#pragma unroll
+      for (int i = 0; i < 16; ++i) {
+        if (n0 + i < N) {
+          const float* xn = mc.Xf + (n0 + i) * kMaxL;
+          float lin = ev[i];
+#pragma unroll
+          for (int l = 0; l < LL; ++l) lin += xn[l] * b[l];
+#pragma unroll
+          for (int l = 0; l < LL; ++l) a[l] += xn[l] * lin;
+        }
+      }
+    }
+    const float invN = 1.0f / (float)N;
+#pragma unroll
+    for (int l = 0; l < LL; ++l) {
+      f[l] = a[l] * invN;
+      f[LL + l] = asinhf(tl[l]);
+      f[2 * LL + 1 + l] = th[l];
+      f[3 * LL + 1 + l] = 0.5f * logf(s2[l]);
+    }
+    f[2 * LL] = logf(gm);
+  }
+#pragma unroll
+  for (int c0 = 0; c0 < K1; c0 += 8) store_split8(abuf, k1, row, c0, f + c0);
+}
+
+// Row r, 8 consecutive values v of an operand whose 8-row groups are sbo bytes
+// apart: the BF16 hi parts into 16-byte chunk ch_hi of the row, the lo parts
+// into chunk ch_lo (K-major: the chunk is 8 consecutive K columns).
+__device__ __forceinline__ void store_split8_ch(uint8_t* base, uint32_t sbo, int r, int ch_hi,
+                                                int ch_lo, const float* v) {
+  uint32_t h[4], l[4];
+#pragma unroll
+  for (int i = 0; i < 4; ++i) {
+    const __nv_bfloat162 hb = __floats2bfloat162_rn(v[2 * i], v[2 * i + 1]);
+    const float2 hf = __bfloat1622float2(hb);
+    const __nv_bfloat162 lb = __floats2bfloat162_rn(v[2 * i] - hf.x, v[2 * i + 1] - hf.y);
+    h[i] = *reinterpret_cast<const uint32_t*>(&hb);
+    l[i] = *reinterpret_cast<const uint32_t*>(&lb);
+  }
+  uint8_t* row = base + (size_t)(r >> 3) * sbo + (r & 7) * 16;
+  *(uint4*)(row + ch_hi * 128) = make_uint4(h[0], h[1], h[2], h[3]);
+  *(uint4*)(row + ch_lo * 128) = make_uint4(l[0], l[1], l[2], l[3]);
+}
+
 constexpr unsigned kTcWaitLimit = kTcWaitPolls;  // polls of a drain wait before it gives up
 
 __device__ __forceinline__ uint32_t smem_u32(const void* ptr) {
@@ -167,6 +242,21 @@ __device__ __forceinline__ uint64_t umma_desc(uint32_t saddr, uint32_t sbo) {
 __host__ __device__ constexpr uint32_t umma_idesc_bf16(int M, int N) {
   return (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(N >> 3) << 17) |
          ((uint32_t)(M >> 4) << 24);
+}
+
+// The same with A (bit 15) and/or B (bit 16) MN-major: for such an operand the
+// descriptor's leading byte offset is the stride between groups of 8 rows
+// along K and the stride byte offset the stride between 16-byte chunks (8
+// elements) along M or N; a core matrix holds 8 K rows of 16 bytes.
+__host__ __device__ constexpr uint32_t umma_idesc_bf16_mn(int M, int N, int a_mn, int b_mn) {
+  return umma_idesc_bf16(M, N) | ((uint32_t)a_mn << 15) | ((uint32_t)b_mn << 16);
+}
+
+// Shared-memory matrix descriptor with explicit leading and stride byte offsets
+// (no swizzle, descriptor version 1).
+__device__ __forceinline__ uint64_t umma_desc_ls(uint32_t saddr, uint32_t lbo, uint32_t sbo) {
+  return (uint64_t)((saddr >> 4) & 0x3FFFu) | ((uint64_t)((lbo >> 4) & 0x3FFFu) << 16) |
+         ((uint64_t)((sbo >> 4) & 0x3FFFu) << 32) | (1ull << 46);
 }
 
 __device__ __forceinline__ void umma_bf16(uint32_t d, uint64_t a, uint64_t b, uint32_t idesc,
@@ -276,7 +366,7 @@ constexpr uint32_t kTmemCols = 128;  // D1 at columns 0..63, D2 at 64..127, D3 a
 // Per-block state of the network: tensor-memory base, the two mbarriers (weight
 // image, MMA completion), the completion phase and the wait outcomes.
 struct TcBlock {
-  uint32_t tmem, bar_w, bar_m, ph;
+  uint32_t tmem, cols, bar_w, bar_m, ph;  // cols: tensor-memory columns allocated
   unsigned polls;  // polls of each wait of the pass before it gives up
   bool w_ok, pending;
 };
@@ -291,6 +381,7 @@ __device__ __forceinline__ void tc_begin(TcBlock& c, uint64_t* bars, uint32_t* t
                                          unsigned polls) {
   const int tid = threadIdx.x;
   c.polls = polls;
+  c.cols = kTmemCols;
   c.bar_w = smem_u32(&bars[0]);
   c.bar_m = smem_u32(&bars[1]);
   c.ph = 0;
@@ -324,7 +415,7 @@ __device__ __forceinline__ void tc_begin(TcBlock& c, uint64_t* bars, uint32_t* t
   c.w_ok = mbar_wait(c.bar_w, 0, c.polls);
 }
 
-// Frees the tensor memory.  After a wait that gave up (aborted) it first sets
+// Frees the block's c.cols tensor-memory columns.  After a wait that gave up (aborted) it first sets
 // kFlagTimeout in *flags and waits again, up to kTcWaitLimit polls, for the copy
 // and the MMAs still in flight, so that none of them outlives the block.
 __device__ __forceinline__ void tc_end(TcBlock& c, bool aborted, unsigned* flags) {
@@ -338,7 +429,7 @@ __device__ __forceinline__ void tc_end(TcBlock& c, bool aborted, unsigned* flags
   if (threadIdx.x < 32) {
     tc_fence_after();
     asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(c.tmem),
-                 "r"(kTmemCols)
+                 "r"(c.cols)
                  : "memory");
   }
 }
@@ -346,30 +437,32 @@ __device__ __forceinline__ void tc_end(TcBlock& c, bool aborted, unsigned* flags
 // The network for one tile of 128 genes by the block's 128 threads: thread t
 // holds gene g (its TMEM lane, row t of the operands), warp w reads lane
 // quadrant w.  The weight image is at sm, the A operand buffer at abuf.  Genes
-// with act write their K outputs to out[k G + g].  Every wait is bounded; one
+// with act write their K outputs to out[k ostride + oidx] (global [K][G] with
+// ostride = G, oidx = g, or a block's shared [K][128] with ostride = 128,
+// oidx = t, which may lie in the operand buffer: it is written after the last
+// GEMM completed).  Every wait is bounded; one
 // that gives up sets *s_abort (block-shared), and the function returns false
 // once every thread has seen it.  Ends with a block barrier.
 __device__ __forceinline__ bool tc_tile(TcBlock& c, const ModelConst& mc, const DevPtrsF32& p,
                                         const TcShape& t, uint8_t* sm, uint8_t* abuf, int g,
-                                        bool act, float* out, volatile int* s_abort) {
+                                        bool act, float* out, size_t ostride, int oidx,
+                                        volatile int* s_abort) {
   const int tid = threadIdx.x, warp = tid >> 5;
   const uint32_t lane_addr = (uint32_t)(warp * 32) << 16;
   const uint32_t id64 = umma_idesc_bf16(128, 64), id3 = umma_idesc_bf16(128, t.n3);
   const uint32_t sa = smem_u32(abuf), sw = smem_u32(sm);
   const float* bias = (const float*)(sm + t.off_b);
   // features of this thread's gene, split into the first operand
-  {
-    float f[kMaxK1];
-#pragma unroll
-    for (int i = 0; i < kMaxK1; ++i) f[i] = 0.0f;
-    if (act) {
-      float a[kMaxL];
-      feature_sums(mc, p, g, 0, mc.N, a);
-      finish_features(mc, p, g, p.hyp, a, f);
-    }
-#pragma unroll
-    for (int c0 = 0; c0 < kMaxK1; c0 += 8)
-      if (c0 < t.k1) store_split8(abuf, t.k1, tid, c0, f + c0);
+  static_assert(kMaxL == 8, "one case per number of columns");
+  switch (mc.L) {
+    case 1: features_split<1>(mc, p, g, p.hyp, act, t.k1, abuf, tid); break;
+    case 2: features_split<2>(mc, p, g, p.hyp, act, t.k1, abuf, tid); break;
+    case 3: features_split<3>(mc, p, g, p.hyp, act, t.k1, abuf, tid); break;
+    case 4: features_split<4>(mc, p, g, p.hyp, act, t.k1, abuf, tid); break;
+    case 5: features_split<5>(mc, p, g, p.hyp, act, t.k1, abuf, tid); break;
+    case 6: features_split<6>(mc, p, g, p.hyp, act, t.k1, abuf, tid); break;
+    case 7: features_split<7>(mc, p, g, p.hyp, act, t.k1, abuf, tid); break;
+    default: features_split<kMaxL>(mc, p, g, p.hyp, act, t.k1, abuf, tid); break;
   }
   // three layers: D1 = A1 W1^T (columns 0..63), D2 = A2 W2^T (64..127), D3 = A3 W3^T
   // (columns 0..n3-1); A2, A3 overwrite the operand buffer once the GEMM before
@@ -404,7 +497,7 @@ __device__ __forceinline__ bool tc_tile(TcBlock& c, const ModelConst& mc, const 
 #pragma unroll
         for (int i = 0; i < 16; ++i) {
           const int k = c0 + i;
-          if (act && k < t.K) out[(size_t)k * mc.G + g] = v[i] + bias[2 * kMlpHidden + k];
+          if (act && k < t.K) out[(size_t)k * ostride + oidx] = v[i] + bias[2 * kMlpHidden + k];
         }
       }
     }

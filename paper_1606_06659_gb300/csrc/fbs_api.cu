@@ -1186,11 +1186,19 @@ constexpr int kTrainGraphSteps = 8;  // training steps per replayed graph
 struct TrainBufs {
   float *fb, *yb, *part, *grad, *loss;
   unsigned* flags;
+  void* img;  // the training kernel's weight image (zeroed)
 };
+
+void train_bufs_free(TrainBufs& t) {
+  cudaFree(t.fb);
+  cudaFree(t.img);
+  t.fb = nullptr;
+  t.img = nullptr;
+}
 
 // Gradient and summed loss of the minibatch in t.fb / t.yb at params.
 int mlp_step(const float* params, int L, int B, TrainBufs& t, cudaStream_t s) {
-  FBS_CUDA(launch_mlp_grad(params, L, B, t.fb, t.yb, t.part, t.grad, t.loss, t.flags,
+  FBS_CUDA(launch_mlp_grad(params, L, B, t.fb, t.yb, t.part, t.grad, t.loss, t.img, t.flags,
                            kTcWaitPolls, s));
   return FBS_OK;
 }
@@ -1209,7 +1217,12 @@ int train_bufs_alloc(TrainBufs& t, int L, int B) {
   t.grad = q; q += np;
   t.loss = q; q += 1;
   t.flags = reinterpret_cast<unsigned*>(q);
-  FBS_CUDA(cudaMemset(t.flags, 0, sizeof(unsigned)));
+  t.img = nullptr;
+  cudaError_t e = cudaMemset(t.flags, 0, sizeof(unsigned));
+  if (e == cudaSuccess) e = cudaMalloc(&t.img, train_image_bytes(L));
+  if (e == cudaSuccess) e = cudaMemset(t.img, 0, train_image_bytes(L));
+  if (e != cudaSuccess) train_bufs_free(t);
+  FBS_CUDA(e);
   return FBS_OK;
 }
 
@@ -1304,6 +1317,7 @@ int fbs_proposal_train(fbs_handle* h, int epochs, int batch, double lr, uint64_t
   if (e == cudaSuccess) e = cudaMalloc((void**)&d_ctl, sizeof(TrainCtl));
   if (e == cudaSuccess)
     e = cudaMemcpyAsync(d_ctl, &ctl, sizeof(ctl), cudaMemcpyHostToDevice, h->s);
+  if (e == cudaSuccess) e = launch_pack_train_image(ls->params, L, t.img, h->s);
   for (int gi = 0; gi < 2 && e == cudaSuccess; ++gi) {
     cudaGraph_t graph = nullptr;
     e = cudaStreamBeginCapture(h->s, cudaStreamCaptureModeThreadLocal);
@@ -1312,7 +1326,7 @@ int fbs_proposal_train(fbs_handle* h, int epochs, int batch, double lr, uint64_t
       for (int k = 0; k < (gi == 0 ? kTrainGraphSteps : 1) && ce == cudaSuccess; ++k)
         ce = launch_train_step(ls->params, L, batch, ls->pair_feat, ls->pair_beta, ls->pairs,
                                seed, d_ctl, ls->stats, t.part, t.grad, t.loss, ls->adam_m,
-                               ls->adam_v, t.flags, h->pf.tc_polls, h->s);
+                               ls->adam_v, t.img, t.flags, h->pf.tc_polls, h->s);
       e = cudaStreamEndCapture(h->s, &graph);
       if (e == cudaSuccess) e = ce;
     }
@@ -1338,7 +1352,7 @@ int fbs_proposal_train(fbs_handle* h, int epochs, int batch, double lr, uint64_t
   if (e == cudaSuccess && rc == FBS_OK) e = launch_fold(ls->params, ls->stats, L, 1, h->s);
   if (e == cudaSuccess && rc == FBS_OK) e = launch_pack_image(ls->params, ls->w_image, ls->L, h->s);
   if (e == cudaSuccess && rc == FBS_OK) e = cudaStreamSynchronize(h->s);
-  cudaFree(t.fb);
+  train_bufs_free(t);
   if (rc) return rc;
   FBS_CUDA(e);
   if (rc_wait) return rc_wait;
@@ -1785,7 +1799,7 @@ int fbs_proposal_loss_grad(const float* params, int L, int B, const float* feat,
   if (e == cudaSuccess && rc == FBS_OK && grad)
     e = cudaMemcpy(grad, t.grad, sizeof(float) * np, cudaMemcpyDeviceToHost);
   cudaFree(dp);
-  cudaFree(t.fb);
+  train_bufs_free(t);
   if (rc) return rc;
   FBS_CUDA(e);
   if (loss) *loss = (double)l / B;

@@ -164,83 +164,6 @@ __device__ __forceinline__ SliceResultF slice_update_f(float x0, float aux0, flo
   return res;
 }
 
-// The same update with two log-density evaluations per round, so that their
-// latencies overlap in one thread: stepping out evaluates the next left and
-// right points together (the two expansions are independent), and shrinkage
-// evaluates proposal j together with proposal j + 1, the one that follows if j
-// is rejected (which end j replaces is known once j is drawn).  Every proposal
-// is the same floating-point expression of the same uniform as in
-// slice_update_f, so the result is bit-identical, and evals counts the
-// evaluations of the one-at-a-time order; the speculative ones are not counted.
-template <class F>
-__device__ __forceinline__ SliceResultF slice_update_f2(float x0, float aux0, float w, const F& f,
-                                                        Rng4& r, int K, int shrink_max) {
-  SliceResultF res;
-  res.evals = 0;
-  res.nonfinite = !(isfinite(x0) && isfinite(aux0));
-  const float logu = __logf(r.u(0));
-  const float v = __fmul_rn(w, r.u(1));
-  float lo = __fsub_rn(x0, v);
-  float hi = __fadd_rn(lo, w);
-  int KL = (int)__fmul_rn((float)(K + 1), r.u(2));
-  if (KL > K) KL = K;
-  const int KR = K - KL;
-  int kl = 0, kr = 0;
-  bool go_l = KL > 0, go_r = KR > 0;
-  while (go_l || go_r) {
-    float al, ar;
-    const float fl = f(lo, &al), fr = f(hi, &ar);
-    if (go_l) {
-      ++res.evals;
-      if (logu < fl) {
-        lo = __fsub_rn(lo, w);
-        go_l = ++kl < KL;
-      } else {
-        go_l = false;
-      }
-    }
-    if (go_r) {
-      ++res.evals;
-      if (logu < fr) {
-        hi = __fadd_rn(hi, w);
-        go_r = ++kr < KR;
-      } else {
-        go_r = false;
-      }
-    }
-  }
-  for (int j = 0; j < shrink_max; j += 2) {
-    const float xa = __fadd_rn(lo, __fmul_rn(__fsub_rn(hi, lo), r.u(3u + (uint32_t)j)));
-    float lo2 = lo, hi2 = hi;
-    if (xa > x0) hi2 = xa; else lo2 = xa;
-    const float xb = __fadd_rn(lo2, __fmul_rn(__fsub_rn(hi2, lo2), r.u(4u + (uint32_t)j)));
-    float aa, ab;
-    const float fa = f(xa, &aa), fb = f(xb, &ab);
-    ++res.evals;
-    if (logu < fa) {
-      res.x = xa;
-      res.aux = aa;
-      res.capped = false;
-      return res;
-    }
-    if (j + 1 >= shrink_max) break;
-    ++res.evals;
-    if (logu < fb) {
-      res.x = xb;
-      res.aux = ab;
-      res.capped = false;
-      return res;
-    }
-    if (xb > x0) hi2 = xb; else lo2 = xb;
-    lo = lo2;
-    hi = hi2;
-  }
-  res.x = x0;
-  res.aux = aux0;
-  res.capped = true;
-  return res;
-}
-
 __device__ __forceinline__ void tune_width_f(float& w, float& waux, long long it, float x_new,
                                              float x_old, long long burnin, long long tune_start) {
   if (it > burnin) return;
@@ -387,17 +310,14 @@ __device__ __forceinline__ int move_kind(const DevPtrsF32& p, int g, long long i
 // genes whose conditional is close to the prior (very large gamma_g), where the
 // network, trained mostly on typical genes, extrapolates poorly.  Either way
 // the proposal depends only on quantities the move keeps.
-// The network's outputs are read from prop[k pstride + pidx]; es = the block's
-// shared copy of eps_g (es[n B + tid], kept up to date with p.eps) or nullptr
-// (p.eps alone); phf = theta_l, sigma2_l in FP32 (phf[l], phf[kMaxL + l]).
-// Returns true when accepted.
+// The network's outputs are read from prop[k pstride + pidx].  Returns true
+// when accepted.
 constexpr int kTDof = 8;
 
 __device__ __forceinline__ bool mh_move_f32(const ModelConst& mc, const DevPtrsF32& p, int g,
                                             uint32_t it32, float* bs, int B, int tid,
                                             const Hyper* hy, float hg, int kind,
-                                            const float* prop, size_t pstride, int pidx,
-                                            float* es, const float* phf) {
+                                            const float* prop, size_t pstride, int pidx) {
   const int G = mc.G, N = mc.N, L = mc.L;
   float mu[kMaxL], C[kMaxL][kMaxL], xi[kMaxL], bn[kMaxL], d[kMaxL];
 #pragma unroll
@@ -417,8 +337,8 @@ __device__ __forceinline__ bool mh_move_f32(const ModelConst& mc, const DevPtrsF
         for (int j = 0; j < kMaxL; ++j)
           if (j < i) C[i][j] = prop[(size_t)(k++) * pstride + pidx];
       } else {  // the prior's centre and scales
-        mu[i] = phf[i];
-        C[i][i] = sqrtf(phf[kMaxL + i]);
+        mu[i] = (float)hy->phi[2 + i];
+        C[i][i] = sqrtf((float)hy->phi[2 + L + i]);
       }
     }
   }
@@ -458,8 +378,8 @@ __device__ __forceinline__ bool mh_move_f32(const ModelConst& mc, const DevPtrsF
         if (j < i) v -= C[i][j] * u[j];
       u[i] = v / C[i][i];
       uu += u[i] * u[i];
-      const float bt = bs[i * B + tid] - phf[i];
-      lp -= d[i] * (d[i] + 2.0f * bt) * (0.5f / phf[kMaxL + i]);
+      const float bt = bs[i * B + tid] - (float)hy->phi[2 + i];
+      lp -= d[i] * (d[i] + 2.0f * bt) * (0.5f / (float)hy->phi[2 + L + i]);
     }
   }
   // log q(beta) - log q(beta*), with C^-1 (beta* - mu) = st xi
@@ -473,8 +393,7 @@ __device__ __forceinline__ bool mh_move_f32(const ModelConst& mc, const DevPtrsF
 #pragma unroll
     for (int l = 0; l < kMaxL; ++l)
       if (l < L) xd += mc.Xf[n * kMaxL + l] * d[l];
-    const float en = es ? es[n * B + tid] : p.eps[(size_t)n * G + g];
-    se += xd * (2.0f * en - xd);
+    se += xd * (2.0f * p.eps[(size_t)n * G + g] - xd);
   }
   const float la = se * hg + lp + lq;
   const bool acc = log_u < la;
@@ -484,13 +403,7 @@ __device__ __forceinline__ bool mh_move_f32(const ModelConst& mc, const DevPtrsF
 #pragma unroll
       for (int l = 0; l < kMaxL; ++l)
         if (l < L) xd += mc.Xf[n * kMaxL + l] * d[l];
-      if (es) {
-        const float en = es[n * B + tid] - xd;
-        es[n * B + tid] = en;
-        p.eps[(size_t)n * G + g] = en;
-      } else {
-        p.eps[(size_t)n * G + g] -= xd;
-      }
+      p.eps[(size_t)n * G + g] -= xd;
     }
 #pragma unroll
     for (int i = 0; i < kMaxL; ++i)
@@ -507,13 +420,12 @@ __device__ __forceinline__ void beta_column_f32(const ModelConst& mc, const DevP
                                                 int g, float* mu, const float* ys, float* bs,
                                                 int B, int tid, const Hyper* hy, long long it,
                                                 uint32_t it32, long long burnin,
-                                                long long tune_start, float w,
-                                                const float* phf, unsigned& evals_b,
+                                                long long tune_start, unsigned& evals_b,
                                                 unsigned& caps, unsigned& nonfin) {
   const int G = mc.G, N = mc.N, L = mc.L;
   const size_t e = (size_t)l * G + g;
-  const float theta = phf[l];
-  const float sig2 = phf[kMaxL + l];
+  const float theta = (float)hy->phi[2 + l];
+  const float sig2 = (float)hy->phi[2 + L + l];
   BetaDensityFT<NC> f;
   const float b_cur = bs[l * B + tid];
   f.b0 = b_cur;
@@ -527,7 +439,6 @@ __device__ __forceinline__ void beta_column_f32(const ModelConst& mc, const DevP
     Y[j] = 0.0f;
     f.v[j] = mc.cvalf[l][j];
   }
-#pragma unroll 8
   for (int n = 0; n < N; ++n) {
     const int c = mc.cls[l][n];
     const float m = mu[n * B + tid];
@@ -543,7 +454,8 @@ __device__ __forceinline__ void beta_column_f32(const ModelConst& mc, const DevP
   for (int j = 0; j < NC; ++j) f.D[j] = Y[j] - f.Q[j];
   Rng4 r(mc.seed_lo, mc.seed_hi, mc.chain, kStreamBeta, (uint32_t)((size_t)g * L + l), it32);
   const float x0 = b_cur;
-  SliceResultF s = slice_update_f2(x0, 0.0f, w, f, r, mc.K, mc.shrink_max);
+  float w = p.w_beta[e];
+  SliceResultF s = slice_update_f(x0, 0.0f, w, f, r, mc.K, mc.shrink_max);
   evals_b += s.evals;
   caps += s.capped;
   nonfin += s.nonfinite;
@@ -555,7 +467,6 @@ __device__ __forceinline__ void beta_column_f32(const ModelConst& mc, const DevP
       const float z = f.v[j] * d;
       fac[j] = 1.0f + (z + em1mx(z));
     }
-#pragma unroll 8
     for (int n = 0; n < N; ++n) {
       const int c = mc.cls[l][n];
       float fc = 1.0f;
@@ -574,14 +485,11 @@ __device__ __forceinline__ void beta_column_f32(const ModelConst& mc, const DevP
   }
 }
 
-// Float offset of the FP64 warp sums in the gamma/beta kernels' shared memory
-// (after mu, y, eps [N][B], beta, widths [kMaxL][B], partials [kNumPart][B]).
-__host__ __device__ inline size_t gb_red_offset_f32(int N, int B) {
-  return ((3 * (size_t)N + 2 * kMaxL + kNumPart) * B + 1) & ~(size_t)1;
-}
-
+// Shared memory of the gamma/beta updates for blocks of B threads: mu, y [N][B],
+// beta [kMaxL][B], partials [kNumPart][B] (floats), then FP64 warp sums.
 __host__ __device__ inline size_t gb_smem_bytes_f32(int N, int B) {
-  return gb_red_offset_f32(N, B) * sizeof(float) + (size_t)(B / 32) * kNumPart * sizeof(double);
+  return ((2 * (size_t)N + kMaxL + kNumPart) * B + 2) * sizeof(float) +
+         (size_t)(B / 32) * kNumPart * sizeof(double);
 }
 
 // Steps 2 and 5 of Algorithm 1 in the FP32 form: one thread per gene.  The
@@ -591,13 +499,12 @@ __host__ __device__ inline size_t gb_smem_bytes_f32(int N, int B) {
 // gamma draw, for every gene unless the move replaces them (p.mh_replace).
 // net_ok: false when this block's network pass gave up (its genes then skip the
 // network's move); prop_s: the network's outputs of the block's genes in shared
-// memory ([K][B]), or nullptr (the move reads p.prop).
+// memory ([K][B]), or nullptr (the move reads p.prop, [K][G]).
 __device__ __forceinline__ void gb_f32_body(const ModelConst& mc, const DevPtrsF32& p, int seg_i,
                                             int blk, bool net_ok = true,
                                             const float* prop_s = nullptr) {
-  // shared: mu[N][B], y[N][B], eps[N][B], beta[L][B], widths[L][B],
-  // partials[kNumPart][B] (per-thread values indexed by a runtime n or l live
-  // here rather than in local memory); then FP64 warp sums
+  // shared: mu[N][B], y[N][B], beta[L][B], partials[kNumPart][B] (per-thread values
+  // indexed by a runtime l live here rather than in local memory); then FP64 warp sums
   extern __shared__ float smem_f[];
   const int G = mc.G, N = mc.N, L = mc.L;
   const Hyper* hy = p.hyp;
@@ -607,13 +514,6 @@ __device__ __forceinline__ void gb_f32_body(const ModelConst& mc, const DevPtrsF
   const bool mom = it > burnin;
   const float inv_k = mom ? 1.0f / (float)(hy->n_mom + 1) : 0.0f;
   const float nu = (float)hy->phi[0], tau = (float)hy->phi[1];
-  // theta_l, sigma2_l in FP32, read once by the block
-  __shared__ float phf[2 * kMaxL];
-  if (threadIdx.x < 2 * kMaxL) {
-    const int l = threadIdx.x % kMaxL;
-    phf[threadIdx.x] = l < L ? (float)hy->phi[2 + (threadIdx.x < kMaxL ? 0 : L) + l] : 1.0f;
-  }
-  __syncthreads();
   const bool trace_now = mom && mc.trace_beta && p.trace_beta != nullptr &&
                          ((it - burnin) % hy->thin == 0) && hy->trace_rows < hy->trace_cap;
   const long long trace_row = hy->trace_rows;
@@ -622,10 +522,8 @@ __device__ __forceinline__ void gb_f32_body(const ModelConst& mc, const DevPtrsF
   const int B = blockDim.x;
   float* mu = smem_f;
   float* ys = mu + (size_t)N * B;
-  float* es = ys + (size_t)N * B;
-  float* bs = es + (size_t)N * B;
-  float* ws = bs + (size_t)kMaxL * B;
-  float* ps = ws + (size_t)kMaxL * B;
+  float* bs = ys + (size_t)N * B;
+  float* ps = bs + (size_t)kMaxL * B;
   const int tid = threadIdx.x;
   const int g = blk * B + tid;
   const bool active = g < G;
@@ -635,63 +533,34 @@ __device__ __forceinline__ void gb_f32_body(const ModelConst& mc, const DevPtrsF
   unsigned evals_b = 0, caps = 0, gcaps = 0, nonfin = 0;
 
   if (active) {
-    // every per-gene input in batches of loads into registers, then shared
-    // memory, so that their latencies overlap
-    {
-      float bv[kMaxL], wv[kMaxL];
-#pragma unroll
-      for (int l = 0; l < kMaxL; ++l)
-        if (l < L) {
-          bv[l] = p.beta[(size_t)l * G + g];
-          wv[l] = p.w_beta[(size_t)l * G + g];
-        }
-#pragma unroll
-      for (int l = 0; l < kMaxL; ++l)
-        if (l < L) {
-          bs[l * B + tid] = bv[l];
-          ws[l * B + tid] = wv[l];
-        }
+    for (int l = 0; l < L; ++l) bs[l * B + tid] = p.beta[(size_t)l * G + g];
+#pragma unroll 4
+    for (int n = 0; n < N; ++n) {
+      const size_t e = (size_t)n * G + g;
+      mu[n * B + tid] = p.mu[e];
+      ys[n * B + tid] = (float)p.y[e];
     }
-    for (int n0 = 0; n0 < N; n0 += 16) {
-      float mv[16], yv[16], ev[16];
-#pragma unroll
-      for (int i = 0; i < 16; ++i)
-        if (n0 + i < N) {
-          const size_t e = (size_t)(n0 + i) * G + g;
-          mv[i] = p.mu[e];
-          yv[i] = (float)p.y[e];
-          ev[i] = p.eps[e];
-        }
-#pragma unroll
-      for (int i = 0; i < 16; ++i)
-        if (n0 + i < N) {
-          mu[(n0 + i) * B + tid] = mv[i];
-          ys[(n0 + i) * B + tid] = yv[i];
-          es[(n0 + i) * B + tid] = ev[i];
-        }
-    }
-    const float gam_prev = p.gam[g];
 
     // ---- learned-proposal move (keeps every log-rate, so mu stays valid)
     int kind = p.prop != nullptr ? move_kind(p, g, it) : 0;
     if (kind == kMoveNet && !net_ok) kind = 0;
     const bool mh_gene = kind != 0;
     if (mh_gene) {
+      const bool acc =
+          prop_s != nullptr
+              ? mh_move_f32(mc, p, g, it32, bs, B, tid, hy, 0.5f / p.gam[g], kind, prop_s,
+                            (size_t)B, tid)
+              : mh_move_f32(mc, p, g, it32, bs, B, tid, hy, 0.5f / p.gam[g], kind, p.prop,
+                            (size_t)G, g);
       const size_t ci = (size_t)(kind - 1) * G + g;
-      const unsigned n_try = p.mh_try[ci], n_acc = p.mh_acc[ci];  // read ahead of the move
-      const bool acc = prop_s != nullptr
-                           ? mh_move_f32(mc, p, g, it32, bs, B, tid, hy, 0.5f / gam_prev, kind,
-                                         prop_s, (size_t)B, tid, es, phf)
-                           : mh_move_f32(mc, p, g, it32, bs, B, tid, hy, 0.5f / gam_prev, kind,
-                                         p.prop, (size_t)G, g, es, phf);
-      p.mh_try[ci] = n_try + 1u;
-      p.mh_acc[ci] = n_acc + (acc ? 1u : 0u);
+      p.mh_try[ci] += 1u;
+      p.mh_acc[ci] += acc ? 1u : 0u;
     }
 
     float ss = 0.0f;
 #pragma unroll 4
     for (int n = 0; n < N; ++n) {
-      const float x = es[n * B + tid];
+      const float x = p.eps[(size_t)n * G + g];
       ss += x * x;
     }
 
@@ -715,19 +584,19 @@ __device__ __forceinline__ void gb_f32_body(const ModelConst& mc, const DevPtrsF
       switch (mc.ncls[l]) {
         case 1:
           beta_column_f32<1>(mc, p, l, g, mu, ys, bs, B, tid, hy, it, it32, burnin, tune_start,
-                             ws[l * B + tid], phf, evals_b, caps, nonfin);
+                             evals_b, caps, nonfin);
           break;
         case 2:
           beta_column_f32<2>(mc, p, l, g, mu, ys, bs, B, tid, hy, it, it32, burnin, tune_start,
-                             ws[l * B + tid], phf, evals_b, caps, nonfin);
+                             evals_b, caps, nonfin);
           break;
         case 3:
           beta_column_f32<3>(mc, p, l, g, mu, ys, bs, B, tid, hy, it, it32, burnin, tune_start,
-                             ws[l * B + tid], phf, evals_b, caps, nonfin);
+                             evals_b, caps, nonfin);
           break;
         default:
           beta_column_f32<kMaxCls>(mc, p, l, g, mu, ys, bs, B, tid, hy, it, it32, burnin,
-                                   tune_start, ws[l * B + tid], phf, evals_b, caps, nonfin);
+                                   tune_start, evals_b, caps, nonfin);
       }
     }
 
@@ -738,7 +607,7 @@ __device__ __forceinline__ void gb_f32_body(const ModelConst& mc, const DevPtrsF
       p.beta[e] = b;
       if (mom) welford_kahan(p.mom_beta, LG, e, b, inv_k);
       if (trace_now) p.trace_beta[(size_t)trace_row * LG + e] = (double)b;
-      const float dv = b - phf[l];
+      const float dv = b - (float)hy->phi[2 + l];
       ps[(2 + l) * B + tid] = dv;
       ps[(2 + kMaxL + l) * B + tid] = dv * dv;
     }
@@ -761,7 +630,8 @@ __device__ __forceinline__ void gb_f32_body(const ModelConst& mc, const DevPtrsF
   // Lane i < kNumPart sums row i of the warp's 32 values (read in an order
   // rotated by i, so that the lanes hit distinct shared-memory banks).
   const int lane = tid & 31, warp = tid >> 5, nwarp = B >> 5;
-  double* red = reinterpret_cast<double*>(smem_f + gb_red_offset_f32(N, B));
+  double* red = reinterpret_cast<double*>(
+      smem_f + (((2 * (size_t)N + kMaxL + kNumPart) * B + 1) & ~(size_t)1));
   __syncwarp();
   if (lane < kNumPart) {
     const float* row = ps + (size_t)lane * B + warp * 32;
@@ -808,9 +678,10 @@ size_t gb_net_smem_bytes(int N, int L) {
 
 // With the learned proposal (128 threads): the block first evaluates the network
 // for its 128 genes on the tensor cores (outputs to shared memory, read by the
-// same threads in the move), then frees the tensor memory and reuses the shared
-// memory for the gamma/beta updates.  A kernel of its own, so that the plain
-// gamma/beta kernel keeps its own register allocation.
+// same threads in the move: a round trip through global memory less), then frees
+// the tensor memory and reuses the shared memory below the outputs for the
+// gamma/beta updates.  A kernel of its own, so that the plain gamma/beta kernel
+// keeps its own register allocation.
 __global__ void __launch_bounds__(128) k_gb_net_f32(ModelConst mc, DevPtrsF32 p, int seg_i,
                                                     const uint8_t* __restrict__ img) {
   ktime_begin(p.ktime, p.ktime_n, 3 * seg_i + 1);
@@ -838,7 +709,7 @@ __global__ void __launch_bounds__(128) k_gb_net_f32(ModelConst mc, DevPtrsF32 p,
     net_ok = s_abort == 0;
     tc_end(c, !net_ok, &p.hyp->flags);
     fence_async_smem();
-    __syncthreads();  // the shared memory below the outputs is the gamma/beta updates' from here on
+    __syncthreads();  // below the outputs, the shared memory is the gamma/beta updates' from here on
   }
   gb_f32_body(mc, p, seg_i, blockIdx.x, net_ok, prop_s);
   ktime_end(p.ktime, p.ktime_n, 3 * seg_i + 1);
@@ -855,14 +726,8 @@ __global__ void __launch_bounds__(128) k_mh_step_f32(ModelConst mc, DevPtrsF32 p
   if (kind == 0) return;
   const int G = mc.G, L = mc.L;
   for (int l = 0; l < L; ++l) bs[l * B + tid] = p.beta[(size_t)l * G + g];
-  float phf[2 * kMaxL];
-#pragma unroll
-  for (int l = 0; l < kMaxL; ++l) {
-    phf[l] = l < L ? (float)p.hyp->phi[2 + l] : 0.0f;
-    phf[kMaxL + l] = l < L ? (float)p.hyp->phi[2 + L + l] : 1.0f;
-  }
   const bool acc = mh_move_f32(mc, p, g, (uint32_t)it, bs, B, tid, p.hyp, 0.5f / p.gam[g], kind,
-                               p.prop, (size_t)G, g, nullptr, phf);
+                               p.prop, (size_t)G, g);
   const size_t ci = (size_t)(kind - 1) * G + g;
   p.mh_try[ci] += 1u;
   if (acc) {

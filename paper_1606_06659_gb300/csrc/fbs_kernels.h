@@ -76,10 +76,15 @@ struct TrainCtl {
 // backward on the tensor cores, gradient reduction, Adam, control-block update
 // (two launches).  A tensor-core wait that gives up after `polls` polls sets
 // kFlagTimeout in *flags, and the step then leaves the parameters unchanged.
+// img: the step's weight image (train_image_bytes(L), zeroed when allocated,
+// packed from params by launch_pack_train_image before the first step); the
+// Adam update rewrites it for the next step.
 cudaError_t launch_train_step(float* params, int L, int Bsz, const float* feat, const float* beta,
                               long long M, uint64_t seed, TrainCtl* ctl, const float* st,
                               float* part, float* grad, float* loss, float* adam_m, float* adam_v,
-                              unsigned* flags, unsigned polls, cudaStream_t s);
+                              void* img, unsigned* flags, unsigned polls, cudaStream_t s);
+size_t train_image_bytes(int L);
+cudaError_t launch_pack_train_image(const float* params, int L, void* img, cudaStream_t s);
 int mlp_param_count(int L);
 cudaError_t launch_proposal_f32(const ModelConst& mc, const DevPtrsF32& p, const void* w_bf16,
                                 float* out, cudaStream_t s);
@@ -95,7 +100,7 @@ size_t train_smem_bytes(int L);
 int train_blocks(int Bsz);
 cudaError_t prepare_train_kernel(int L);
 cudaError_t launch_mlp_grad(const float* params, int L, int Bsz, const float* fb, const float* yb,
-                            float* part, float* grad, float* loss, unsigned* flags,
+                            float* part, float* grad, float* loss, void* img, unsigned* flags,
                             unsigned polls, cudaStream_t s);
 size_t tc_image_bytes(int L);
 cudaError_t launch_pack_image(const float* params, void* img, int L, cudaStream_t s);

@@ -24,14 +24,17 @@
 
 namespace fbs {
 
-__device__ __forceinline__ float gelu_f(float x) {
-  return 0.5f * x * (1.0f + tanhf(kSqrt2OverPi * (x + 0.044715f * x * x * x)));
-}
-
-__device__ __forceinline__ float gelu_grad_f(float x) {
-  const float t = tanhf(kSqrt2OverPi * (x + 0.044715f * x * x * x));
+// GELU (tanh form) and its derivative at x from one tanh:
+// a = x (1 + t) / 2, gd = (1 + t) / 2 + x (1 - t^2) u'(x) / 2, t = tanh(u(x)),
+// u(x) = sqrt(2/pi) (x + 0.044715 x^3).  t = 1 - 2 / (1 + e^{2u}) from the fast
+// exponential and division, as inference evaluates GELU (absolute error of t
+// about 1e-7; |u| is clamped at 15, where tanh is 1 in FP32).
+__device__ __forceinline__ void gelu_and_grad_f(float x, float* a, float* gd) {
+  const float u = fminf(fmaxf(kSqrt2OverPi * (x + 0.044715f * x * x * x), -15.0f), 15.0f);
+  const float t = 1.0f - __fdividef(2.0f, 1.0f + __expf(2.0f * u));
   const float du = kSqrt2OverPi * (1.0f + 3.0f * 0.044715f * x * x);
-  return 0.5f * (1.0f + t) + 0.5f * x * (1.0f - t * t) * du;
+  *a = 0.5f * x * (1.0f + t);
+  *gd = 0.5f * (1.0f + t) + 0.5f * x * (1.0f - t * t) * du;
 }
 
 __host__ __device__ inline int mlp_n_params(int F, int K) {
@@ -240,42 +243,6 @@ __global__ void k_fold(float* __restrict__ w, const float* __restrict__ st, int 
   }
 }
 
-// Gaussian head, per row: loss = |u|^2 / 2 + sum log C_ll with C u = beta - mu;
-// dL/dout (scaled by sc = 1/Bsz): d mu = -v, d logC_ii = 1 - v_i u_i C_ii,
-// d C_ij = -v_i u_j (i > j), where C^T v = u.  o holds the outputs on entry and
-// dL/dout on return.
-__device__ __forceinline__ void nll_row(float* o, const float* y, int L, float sc, float* loss) {
-  float C[kMaxL][kMaxL], u[kMaxL], v[kMaxL];
-  for (int i = 0; i < L; ++i)
-    for (int j = 0; j < L; ++j) C[i][j] = 0.0f;
-  int k = 2 * L;
-  for (int i = 0; i < L; ++i) {
-    C[i][i] = expf(o[L + i]);
-    for (int j = 0; j < i; ++j) C[i][j] = o[k++];
-  }
-  float ls = 0.0f;
-  for (int i = 0; i < L; ++i) {
-    float s = y[i] - o[i];
-    for (int j = 0; j < i; ++j) s -= C[i][j] * u[j];
-    u[i] = s / C[i][i];
-    ls += 0.5f * u[i] * u[i] + o[L + i];
-  }
-  for (int i = L - 1; i >= 0; --i) {
-    float s = u[i];
-    for (int j = i + 1; j < L; ++j) s -= C[j][i] * v[j];
-    v[i] = s / C[i][i];
-  }
-  // o becomes dL/do
-  k = 2 * L;
-  for (int i = 0; i < L; ++i)
-    for (int j = 0; j < i; ++j) o[k++] = -v[i] * u[j] * sc;
-  for (int i = 0; i < L; ++i) {
-    o[L + i] = (1.0f - v[i] * u[i] * C[i][i]) * sc;
-    o[i] = -v[i] * sc;
-  }
-  *loss = ls;
-}
-
 // ---------------------------------------------------------------- training step (tensor cores)
 //
 // One training step's forward and backward pass for 128 minibatch rows per
@@ -302,15 +269,19 @@ __device__ __forceinline__ void nll_row(float* o, const float* y, int L, float s
 // half then a lo half:
 //   W1 [64][k1], W2 [64][64], W3 [n3][64]    weight images (K-major)
 //   b1 [64], b2 [64], b3 [n3]                FP32
+//     (the image: one bulk copy of img, which the previous step's Adam update
+//     or k_pack_train_image wrote)
 //   bufF rows  [A1 (64) | X, 1 (k1) | dO (n3)]
 //   bufG rows  [G2 (64) | A2 (64)]
 //   bufG1 rows [G1 (64)]
-// Tensor memory (512 columns): Z1 at 0, Z2 64, O 128, dO W3 192, G2 W2 256,
-// the first weight-gradient product 320 (64 + k1 + n3 columns), the second 128.
+// Tensor memory (512 columns): Z1 at 0 and Z2 at 64 (each replaced by GELU's
+// derivative at Z + b in its forward epilogue, for the backward pass), O 128,
+// dO W3 192, G2 W2 256, the first weight-gradient product 320 (64 + k1 + n3
+// columns), the second 128.
 struct TrainTc {
   int F, K, k1, n3, cx, co, half;  // half: chunks in a half row of bufF
   uint32_t sbo_w1, sbo_f;          // 8-row group strides of W1 and bufF
-  uint32_t off_w2, off_w3, off_b, off_f, off_g, off_g1, bytes;
+  uint32_t off_w2, off_w3, off_b, img_bytes, off_f, off_g, off_g1, bytes;
 };
 
 __host__ __device__ inline TrainTc train_tc_shape(int L) {
@@ -327,15 +298,160 @@ __host__ __device__ inline TrainTc train_tc_shape(int L) {
   t.off_w2 = 8 * t.sbo_w1;
   t.off_w3 = t.off_w2 + 8 * 2048;
   t.off_b = t.off_w3 + (uint32_t)(t.n3 / 8) * 2048;
-  t.off_f = (t.off_b + (uint32_t)(128 + t.n3) * 4 + 1023) & ~1023u;
+  t.img_bytes = t.off_b + (uint32_t)(128 + t.n3) * 4;  // a multiple of 16
+  t.off_f = (t.img_bytes + 1023) & ~1023u;
   t.off_g = t.off_f + 16 * t.sbo_f;  // the second weight-gradient product reads up to
   t.off_g1 = t.off_g + 16 * 4096;    // 24 - half chunks past bufF, inside bufG
   t.bytes = t.off_g1 + 16 * 2048;
   return t;
 }
 
+// Parameter p (value w) into the training kernel's weight image (the bytes
+// [0, img_bytes) of its shared memory): weights as split BF16 at their
+// canonical positions, biases in FP32.  The padding (W1 columns from F, W3 rows
+// and b3 entries from K) is zero from the image's allocation.
+__device__ __forceinline__ void train_img_put(uint8_t* img, const TrainTc& t, int p, float w) {
+  constexpr int H = kMlpHidden;
+  const int F = t.F, K = t.K;
+  const int ob1 = H * F, oW2 = ob1 + H, ob2 = oW2 + H * H, oW3 = ob2 + H, ob3 = oW3 + K * H;
+  float* bias = reinterpret_cast<float*>(img + t.off_b);
+  int r, c, lo;  // row, column, chunk offset of the lo half
+  uint32_t base, sbo;
+  if (p < ob1) {
+    r = p / F, c = p % F, base = 0, sbo = t.sbo_w1, lo = t.cx;
+  } else if (p < oW2) {
+    bias[p - ob1] = w;
+    return;
+  } else if (p < ob2) {
+    r = (p - oW2) / H, c = (p - oW2) % H, base = t.off_w2, sbo = 2048, lo = 8;
+  } else if (p < oW3) {
+    bias[H + p - ob2] = w;
+    return;
+  } else if (p < ob3) {
+    r = (p - oW3) / H, c = (p - oW3) % H, base = t.off_w3, sbo = 2048, lo = 8;
+  } else {
+    bias[2 * H + p - ob3] = w;
+    return;
+  }
+  const __nv_bfloat16 hi = __float2bfloat16_rn(w);
+  const __nv_bfloat16 lw = __float2bfloat16_rn(w - __bfloat162float(hi));
+  uint8_t* row = img + base + (size_t)(r >> 3) * sbo + (r & 7) * 16 + (c & 7) * 2;
+  *(__nv_bfloat16*)(row + (c >> 3) * 128) = hi;
+  *(__nv_bfloat16*)(row + ((c >> 3) + lo) * 128) = lw;
+}
+
+__global__ void k_pack_train_image(const float* __restrict__ w, int L, uint8_t* __restrict__ img) {
+  const TrainTc t = train_tc_shape(L);
+  const int np = mlp_n_params(t.F, t.K);
+  for (int p = blockIdx.x * blockDim.x + threadIdx.x; p < np; p += gridDim.x * blockDim.x)
+    train_img_put(img, t, p, w[p]);
+}
+
 constexpr uint32_t kTrainTmemCols = 512;
 constexpr int kTrainOutPad = (kMaxOut + 15) & ~15;
+
+// Writes 32 FP32 columns of this thread's tensor-memory lane and waits for the
+// store.
+__device__ __forceinline__ void tmem_st32(uint32_t taddr, const float* v) {
+  asm volatile(
+      "tcgen05.st.sync.aligned.32x32b.x32.b32 [%0], "
+      "{%1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, %15, %16, "
+      "%17, %18, %19, %20, %21, %22, %23, %24, %25, %26, %27, %28, %29, %30, %31, %32};" ::"r"(taddr),
+      "f"(v[0]), "f"(v[1]), "f"(v[2]), "f"(v[3]), "f"(v[4]), "f"(v[5]), "f"(v[6]), "f"(v[7]),
+      "f"(v[8]), "f"(v[9]), "f"(v[10]), "f"(v[11]), "f"(v[12]), "f"(v[13]), "f"(v[14]),
+      "f"(v[15]), "f"(v[16]), "f"(v[17]), "f"(v[18]), "f"(v[19]), "f"(v[20]), "f"(v[21]),
+      "f"(v[22]), "f"(v[23]), "f"(v[24]), "f"(v[25]), "f"(v[26]), "f"(v[27]), "f"(v[28]),
+      "f"(v[29]), "f"(v[30]), "f"(v[31])
+      : "memory");
+  asm volatile("tcgen05.wait::st.sync.aligned;" ::: "memory");
+}
+
+// Gaussian head, per row: loss = |u|^2 / 2 + sum log C_ll with C u = beta - mu;
+// dL/dout (scaled by sc = 1/Bsz): d mu = -v, d logC_ii = 1 - v_i u_i C_ii,
+// d C_ij = -v_i u_j (i > j), where C^T v = u.  o holds the outputs on entry and
+// dL/dout on return.
+// LL columns, every index a compile-time constant (registers only).
+template <int LL>
+__device__ __forceinline__ void nll_row_t(float* o, const float* y, float sc, float* loss) {
+  float C[LL][LL], u[LL], v[LL];
+#pragma unroll
+  for (int i = 0; i < LL; ++i) {
+#pragma unroll
+    for (int j = 0; j < LL; ++j) C[i][j] = 0.0f;
+  }
+  int k = 2 * LL;
+#pragma unroll
+  for (int i = 0; i < LL; ++i) {
+    C[i][i] = expf(o[LL + i]);
+#pragma unroll
+    for (int j = 0; j < i; ++j) C[i][j] = o[k++];
+  }
+  float ls = 0.0f;
+#pragma unroll
+  for (int i = 0; i < LL; ++i) {
+    float s = y[i] - o[i];
+#pragma unroll
+    for (int j = 0; j < i; ++j) s -= C[i][j] * u[j];
+    u[i] = s / C[i][i];
+    ls += 0.5f * u[i] * u[i] + o[LL + i];
+  }
+#pragma unroll
+  for (int i = LL - 1; i >= 0; --i) {
+    float s = u[i];
+#pragma unroll
+    for (int j = i + 1; j < LL; ++j) s -= C[j][i] * v[j];
+    v[i] = s / C[i][i];
+  }
+  k = 2 * LL;
+#pragma unroll
+  for (int i = 0; i < LL; ++i) {
+#pragma unroll
+    for (int j = 0; j < i; ++j) o[k++] = -v[i] * u[j] * sc;
+  }
+#pragma unroll
+  for (int i = 0; i < LL; ++i) {
+    o[LL + i] = (1.0f - v[i] * u[i] * C[i][i]) * sc;
+    o[i] = -v[i] * sc;
+  }
+  *loss = ls;
+}
+
+// The head of the training step for LL columns: the outputs O + b3 from tensor
+// memory, the loss and dO (zero for rows past the batch and columns past K),
+// dO split into bufF, and the warp sums of dO (s_db3[warp]) and of the loss.
+template <int LL>
+__device__ __forceinline__ void train_head(uint32_t taddr, const float* b3, const float* y,
+                                           bool row_ok, float sc, uint8_t* bF, uint32_t sbo_f,
+                                           int ch_hi, int ch_lo, float* db3w, float* lossw) {
+  constexpr int K = LL + LL * (LL + 1) / 2;
+  constexpr int n3 = (K + 15) & ~15;
+  const int tid = threadIdx.x, lane = tid & 31;
+  float o[n3];
+#pragma unroll
+  for (int c0 = 0; c0 < n3; c0 += 16) {
+    float v[16];
+    tmem_ld16(taddr + (uint32_t)c0, v);
+#pragma unroll
+    for (int i = 0; i < 16; ++i) o[c0 + i] = v[i] + b3[c0 + i];
+  }
+  float loss = 0.0f;
+  if (row_ok) nll_row_t<LL>(o, y, sc, &loss);
+#pragma unroll
+  for (int k = 0; k < n3; ++k)
+    if (!row_ok || k >= K) o[k] = 0.0f;
+#pragma unroll
+  for (int q = 0; q < n3 / 8; ++q) store_split8_ch(bF, sbo_f, tid, ch_hi + q, ch_lo + q, o + 8 * q);
+#pragma unroll
+  for (int k = 0; k < K; ++k) {
+    float v = o[k];
+#pragma unroll
+    for (int sh = 16; sh > 0; sh >>= 1) v += __shfl_xor_sync(0xffffffffu, v, sh);
+    if (lane == 0) db3w[k] = v;
+  }
+#pragma unroll
+  for (int sh = 16; sh > 0; sh >>= 1) loss += __shfl_xor_sync(0xffffffffu, loss, sh);
+  if (lane == 0) *lossw = loss;
+}
 
 // D (+)= A B^T over 16 ksteps rows of K for the three split products hi*hi,
 // lo*hi, hi*lo.  Each operand: start addresses of its hi and lo halves, the
@@ -380,11 +496,11 @@ __device__ __forceinline__ bool tc_run(TcBlock& c, volatile int* s_abort, Issue 
 }
 
 __global__ void __launch_bounds__(128) k_mlp_tc(
-    const float* __restrict__ params, int L, int Bsz, const float* __restrict__ fb,
+    int L, int Bsz, const float* __restrict__ fb,
     const float* __restrict__ yb, const float* __restrict__ feat,
     const float* __restrict__ beta, long long M, uint32_t seed_lo, uint32_t seed_hi,
     const TrainCtl* __restrict__ ctl, const float* __restrict__ st, float* __restrict__ part,
-    unsigned* __restrict__ flags, unsigned polls) {
+    const uint8_t* __restrict__ img, unsigned* __restrict__ flags, unsigned polls) {
   extern __shared__ __align__(1024) uint8_t sm[];
   __shared__ __align__(8) uint64_t bars[2];
   __shared__ uint32_t tmem_slot;
@@ -395,7 +511,7 @@ __global__ void __launch_bounds__(128) k_mlp_tc(
   const TrainTc t = train_tc_shape(L);
   const int F = t.F, K = t.K, half = t.half;
   const int np = mlp_n_params(F, K);
-  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  const int tid = threadIdx.x, warp = tid >> 5;
   const int r0 = blockIdx.x * 128;
   const bool row_ok = tid < Bsz - r0;
   uint8_t* w1s = sm;
@@ -405,13 +521,6 @@ __global__ void __launch_bounds__(128) k_mlp_tc(
   uint8_t* bF = sm + t.off_f;
   uint8_t* bG = sm + t.off_g;
   uint8_t* bG1 = sm + t.off_g1;
-  const float* W1 = params;
-  const float* b1 = W1 + H * F;
-  const float* W2 = b1 + H;
-  const float* b2 = W2 + H * H;
-  const float* W3 = b2 + H;
-  const float* b3 = W3 + K * H;
-
   TcBlock c;
   c.polls = polls;
   c.cols = kTrainTmemCols;  // what the dealloc of tc_end frees
@@ -419,11 +528,22 @@ __global__ void __launch_bounds__(128) k_mlp_tc(
   c.bar_m = smem_u32(&bars[1]);
   c.ph = 0;
   c.pending = false;
-  c.w_ok = true;  // no bulk copy: the block writes the weight images itself
+  c.w_ok = false;
   if (tid == 0) {
     s_abort = 0;
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(c.bar_w) : "memory");
     asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(c.bar_m) : "memory");
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    // the weight image (written by the previous step's Adam update, or packed
+    // before the first step): one bulk copy, waited for before the first product
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(c.bar_w),
+                 "r"(t.img_bytes)
+                 : "memory");
+    asm volatile(
+        "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::
+            "r"(smem_u32(sm)),
+        "l"(img), "r"(t.img_bytes), "r"(c.bar_w)
+        : "memory");
   }
   if (warp == 0) {
     asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(
@@ -433,30 +553,6 @@ __global__ void __launch_bounds__(128) k_mlp_tc(
     asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
   }
 
-  // the weight images (zero padding beyond F columns of W1 and K rows of W3)
-  const int n_w1 = 64 * t.cx, n_w2 = 64 * 8, n_w3 = t.n3 * 8;
-  for (int i = tid; i < n_w1 + n_w2 + n_w3; i += 128) {
-    float v[8];
-    if (i < n_w1) {
-      const int h = i / t.cx, q = i % t.cx;
-#pragma unroll
-      for (int j = 0; j < 8; ++j) v[j] = 8 * q + j < F ? W1[h * F + 8 * q + j] : 0.0f;
-      store_split8_ch(w1s, t.sbo_w1, h, q, q + t.cx, v);
-    } else if (i < n_w1 + n_w2) {
-      const int h = (i - n_w1) / 8, q = (i - n_w1) % 8;
-#pragma unroll
-      for (int j = 0; j < 8; ++j) v[j] = W2[h * H + 8 * q + j];
-      store_split8_ch(w2s, 2048, h, q, q + 8, v);
-    } else {
-      const int k = (i - n_w1 - n_w2) / 8, q = (i - n_w1 - n_w2) % 8;
-#pragma unroll
-      for (int j = 0; j < 8; ++j) v[j] = k < K ? W3[k * H + 8 * q + j] : 0.0f;
-      store_split8_ch(w3s, 2048, k, q, q + 8, v);
-    }
-  }
-  for (int i = tid; i < 2 * H + t.n3; i += 128)
-    bsm[i] = i < H ? b1[i] : (i < 2 * H ? b2[i - H] : (i - 2 * H < K ? b3[i - 2 * H] : 0.0f));
-
   // this thread's row: features and the column of ones (split into bufF), beta
   long long srow = 0;
   if (feat != nullptr && row_ok) {
@@ -464,32 +560,34 @@ __global__ void __launch_bounds__(128) k_mlp_tc(
     const long long m = (long long)(rg.u(0) * (double)M);
     srow = m >= M ? M - 1 : m;
   }
-  for (int q = 0; q < t.cx; ++q) {
-    float v[8];
+  // every load of the row first (one round of latency), then the arithmetic
+  constexpr int kX = (kMaxFeat + 1 + 15) & ~15;
+  float x[kX], y[kMaxL];
+  {
+    const float* xr = feat != nullptr ? feat + (size_t)srow * F : fb + (size_t)(r0 + tid) * F;
+    const float* yr = feat != nullptr ? beta + (size_t)srow * L : yb + (size_t)(r0 + tid) * L;
 #pragma unroll
-    for (int j = 0; j < 8; ++j) {
-      const int f = 8 * q + j;
-      float x = 0.0f;
-      if (row_ok) {
-        if (f < F)
-          x = feat != nullptr ? (feat[(size_t)srow * F + f] - st[f]) / st[F + f]
-                              : fb[(size_t)(r0 + tid) * F + f];
-        else if (f == F)
-          x = 1.0f;
-      }
-      v[j] = x;
+    for (int f = 0; f < kX; ++f) x[f] = row_ok && f < F ? xr[f] : 0.0f;
+#pragma unroll
+    for (int l = 0; l < kMaxL; ++l) y[l] = row_ok && l < L ? yr[l] : 0.0f;
+    if (feat != nullptr) {
+#pragma unroll
+      for (int f = 0; f < kX; ++f)
+        if (f < F) x[f] = (x[f] - st[f]) / st[F + f];
+#pragma unroll
+      for (int l = 0; l < kMaxL; ++l)
+        if (l < L) y[l] = (y[l] - st[2 * F + l]) / st[2 * F + L + l];
     }
-    store_split8_ch(bF, t.sbo_f, tid, 8 + q, 8 + q + half, v);
-  }
-  float y[kMaxL];
 #pragma unroll
-  for (int l = 0; l < kMaxL; ++l) {
-    y[l] = 0.0f;
-    if (l < L && row_ok)
-      y[l] = feat != nullptr ? (beta[(size_t)srow * L + l] - st[2 * F + l]) / st[2 * F + L + l]
-                             : yb[(size_t)(r0 + tid) * L + l];
+    for (int f = 0; f < kX; ++f)
+      if (f == F && row_ok) x[f] = 1.0f;
+#pragma unroll
+    for (int q = 0; q < kX / 8; ++q)
+      if (q < t.cx) store_split8_ch(bF, t.sbo_f, tid, 8 + q, 8 + q + half, x + 8 * q);
   }
 
+  c.w_ok = mbar_wait(c.bar_w, 0, c.polls);
+  if (!c.w_ok) s_abort = 1;
   tc_fence_before();
   __syncthreads();
   tc_fence_after();
@@ -510,9 +608,11 @@ __global__ void __launch_bounds__(128) k_mlp_tc(
 #pragma unroll
     for (int h = 0; h < 2; ++h) {
       float v[32];
+      float gd[32];
       tmem_ld32(tm + la + 32 * h, v);
 #pragma unroll
-      for (int i = 0; i < 32; ++i) v[i] = gelu_f(v[i] + bsm[32 * h + i]);
+      for (int i = 0; i < 32; ++i) gelu_and_grad_f(v[i] + bsm[32 * h + i], &v[i], &gd[i]);
+      tmem_st32(tm + la + 32 * h, gd);  // Z1 becomes gelu'(Z1 + b1)
 #pragma unroll
       for (int q = 0; q < 4; ++q) store_split8_ch(bF, sbo_f, tid, 4 * h + q, 4 * h + q + half, v + 8 * q);
     }
@@ -525,9 +625,11 @@ __global__ void __launch_bounds__(128) k_mlp_tc(
 #pragma unroll
     for (int h = 0; h < 2; ++h) {
       float v[32];
+      float gd[32];
       tmem_ld32(tm + la + 64 + 32 * h, v);
 #pragma unroll
-      for (int i = 0; i < 32; ++i) v[i] = gelu_f(v[i] + bsm[H + 32 * h + i]);
+      for (int i = 0; i < 32; ++i) gelu_and_grad_f(v[i] + bsm[H + 32 * h + i], &v[i], &gd[i]);
+      tmem_st32(tm + la + 64 + 32 * h, gd);  // Z2 becomes gelu'(Z2 + b2)
 #pragma unroll
       for (int q = 0; q < 4; ++q) store_split8_ch(bG, 4096, tid, 8 + 4 * h + q, 24 + 4 * h + q, v + 8 * q);
     }
@@ -538,35 +640,22 @@ __global__ void __launch_bounds__(128) k_mlp_tc(
   }
   // ---- head: loss and dO (rows past Bsz: zero), dO into bufF, warp sums of dO
   if (ok) {
-    float o[kTrainOutPad];
-#pragma unroll
-    for (int c0 = 0; c0 < kTrainOutPad; c0 += 16)
-      if (c0 < n3) {
-        float v[16];
-        tmem_ld16(tm + la + 128 + (uint32_t)c0, v);
-#pragma unroll
-        for (int i = 0; i < 16; ++i) o[c0 + i] = v[i] + bsm[2 * H + c0 + i];
-      }
-    float loss = 0.0f;
-    if (row_ok) nll_row(o, y, L, 1.0f / (float)Bsz, &loss);
-#pragma unroll
-    for (int k = 0; k < kTrainOutPad; ++k)
-      if (!row_ok || k >= K) o[k] = 0.0f;
-#pragma unroll
-    for (int q = 0; q < kTrainOutPad / 8; ++q)
-      if (q < t.co) store_split8_ch(bF, sbo_f, tid, 8 + cx + q, 8 + cx + q + half, o + 8 * q);
-#pragma unroll
-    for (int k = 0; k < kTrainOutPad; ++k) {
-      if (k < K) {
-        float v = o[k];
-#pragma unroll
-        for (int sh = 16; sh > 0; sh >>= 1) v += __shfl_xor_sync(0xffffffffu, v, sh);
-        if (lane == 0) s_db3[warp][k] = v;
-      }
+    static_assert(kMaxL == 8, "one case per number of columns");
+    const float sc = 1.0f / (float)Bsz;
+    const uint32_t ta = tm + la + 128;
+    float* db3w = s_db3[warp];
+    float* lw = &s_loss[warp];
+    const int chh = 8 + cx, chl = 8 + cx + half;
+    switch (L) {
+      case 1: train_head<1>(ta, bsm + 2 * H, y, row_ok, sc, bF, sbo_f, chh, chl, db3w, lw); break;
+      case 2: train_head<2>(ta, bsm + 2 * H, y, row_ok, sc, bF, sbo_f, chh, chl, db3w, lw); break;
+      case 3: train_head<3>(ta, bsm + 2 * H, y, row_ok, sc, bF, sbo_f, chh, chl, db3w, lw); break;
+      case 4: train_head<4>(ta, bsm + 2 * H, y, row_ok, sc, bF, sbo_f, chh, chl, db3w, lw); break;
+      case 5: train_head<5>(ta, bsm + 2 * H, y, row_ok, sc, bF, sbo_f, chh, chl, db3w, lw); break;
+      case 6: train_head<6>(ta, bsm + 2 * H, y, row_ok, sc, bF, sbo_f, chh, chl, db3w, lw); break;
+      case 7: train_head<7>(ta, bsm + 2 * H, y, row_ok, sc, bF, sbo_f, chh, chl, db3w, lw); break;
+      default: train_head<8>(ta, bsm + 2 * H, y, row_ok, sc, bF, sbo_f, chh, chl, db3w, lw); break;
     }
-#pragma unroll
-    for (int sh = 16; sh > 0; sh >>= 1) loss += __shfl_xor_sync(0xffffffffu, loss, sh);
-    if (lane == 0) s_loss[warp] = loss;
     ok = tc_run(c, &s_abort, [&] {  // dO W3 (W3 read as an MN-major B)
       issue_split(tm + 192, umma_idesc_bf16_mn(128, H, 0, 1), n3 / 16, sF + (8 + cx) * 128,
                   sF + (8 + cx) * 128 + hb, 256, 128, sbo_f, sW3, sW3 + 8 * 128, 4096, 2048, 128);
@@ -578,9 +667,9 @@ __global__ void __launch_bounds__(128) k_mlp_tc(
     for (int h = 0; h < 2; ++h) {
       float d[32], z[32];
       tmem_ld32(tm + la + 192 + 32 * h, d);
-      tmem_ld32(tm + la + 64 + 32 * h, z);
+      tmem_ld32(tm + la + 64 + 32 * h, z);  // gelu'(Z2 + b2)
 #pragma unroll
-      for (int i = 0; i < 32; ++i) d[i] *= gelu_grad_f(z[i] + bsm[H + 32 * h + i]);
+      for (int i = 0; i < 32; ++i) d[i] *= z[i];
 #pragma unroll
       for (int q = 0; q < 4; ++q) store_split8_ch(bG, 4096, tid, 4 * h + q, 16 + 4 * h + q, d + 8 * q);
     }
@@ -594,9 +683,9 @@ __global__ void __launch_bounds__(128) k_mlp_tc(
     for (int h = 0; h < 2; ++h) {
       float d[32], z[32];
       tmem_ld32(tm + la + 256 + 32 * h, d);
-      tmem_ld32(tm + la + 32 * h, z);
+      tmem_ld32(tm + la + 32 * h, z);  // gelu'(Z1 + b1)
 #pragma unroll
-      for (int i = 0; i < 32; ++i) d[i] *= gelu_grad_f(z[i] + bsm[32 * h + i]);
+      for (int i = 0; i < 32; ++i) d[i] *= z[i];
 #pragma unroll
       for (int q = 0; q < 4; ++q) store_split8_ch(bG1, 2048, tid, 4 * h + q, 8 + 4 * h + q, d + 8 * q);
     }
@@ -682,15 +771,17 @@ __device__ __forceinline__ void adam_scalars(const TrainCtl* c, float* c1, float
 // (part [nblk][np + 1]), added in block order so that a step is deterministic:
 // block b takes parameters 32b..32b+31, warp w the partial rows w, w + 8, ..,
 // and warp 0 adds the eight warp sums in order.  With a control block it also
-// applies Adam to w, m, v and, in the last block to finish (ticket counter, no
-// waiting), adds the loss to the last epoch's sum and advances t and k.  Does
+// applies Adam to w, m, v, writes the new w into the training kernel's weight
+// image img and, in the last block to finish (ticket counter, no waiting), adds
+// the loss to the last epoch's sum and advances t and k.  Does
 // nothing once *flags is set (a tensor-core wait of the forward and backward
 // pass gave up, so the partials are incomplete).
 __global__ void __launch_bounds__(256) k_reduce_adam(const float* __restrict__ part, int nblk,
                                                      int np, float* __restrict__ grad,
                                                      float* __restrict__ loss, float* w, float* m,
                                                      float* v, TrainCtl* ctl, int B, float eps,
-                                                     const unsigned* __restrict__ flags) {
+                                                     const unsigned* __restrict__ flags,
+                                                     uint8_t* __restrict__ img, int L) {
   if (*(volatile const unsigned*)flags != 0u) return;
   __shared__ float red[8][33];
   const int lane = threadIdx.x & 31, wp = threadIdx.x >> 5;
@@ -718,7 +809,9 @@ __global__ void __launch_bounds__(256) k_reduce_adam(const float* __restrict__ p
         const float vt = b2 * v[p] + (1.0f - b2) * g * g;
         m[p] = mt;
         v[p] = vt;
-        w[p] -= lr_t * (mt / c1) / (sqrtf(vt / c2) + eps);
+        const float wn = w[p] - lr_t * (mt / c1) / (sqrtf(vt / c2) + eps);
+        w[p] = wn;
+        train_img_put(img, train_tc_shape(L), p, wn);
       }
     }
   }
@@ -794,29 +887,39 @@ cudaError_t prepare_train_kernel(int L) {
                               (int)train_smem_bytes(L));
 }
 
+size_t train_image_bytes(int L) { return (size_t)train_tc_shape(L).img_bytes; }
+
+cudaError_t launch_pack_train_image(const float* params, int L, void* img, cudaStream_t s) {
+  k_pack_train_image<<<32, 256, 0, s>>>(params, L, (uint8_t*)img);
+  return cudaGetLastError();
+}
+
 cudaError_t launch_mlp_grad(const float* params, int L, int Bsz, const float* fb, const float* yb,
-                            float* part, float* grad, float* loss, unsigned* flags,
+                            float* part, float* grad, float* loss, void* img, unsigned* flags,
                             unsigned polls, cudaStream_t s) {
   const int nblk = train_blocks(Bsz);
   const int np = mlp_param_count(L);
-  k_mlp_tc<<<nblk, 128, train_smem_bytes(L), s>>>(params, L, Bsz, fb, yb, nullptr, nullptr, 0,
-                                                  0u, 0u, nullptr, nullptr, part, flags, polls);
+  k_pack_train_image<<<32, 256, 0, s>>>(params, L, (uint8_t*)img);
+  k_mlp_tc<<<nblk, 128, train_smem_bytes(L), s>>>(L, Bsz, fb, yb, nullptr, nullptr, 0,
+                                                  0u, 0u, nullptr, nullptr, part,
+                                                  (const uint8_t*)img, flags, polls);
   k_reduce_adam<<<(np + 1 + 31) / 32, 256, 0, s>>>(part, nblk, np, grad, loss, nullptr, nullptr,
-                                                   nullptr, nullptr, Bsz, 0.0f, flags);
+                                                   nullptr, nullptr, Bsz, 0.0f, flags, nullptr, L);
   return cudaGetLastError();
 }
 
 cudaError_t launch_train_step(float* params, int L, int Bsz, const float* feat, const float* beta,
                               long long M, uint64_t seed, TrainCtl* ctl, const float* st,
                               float* part, float* grad, float* loss, float* adam_m, float* adam_v,
-                              unsigned* flags, unsigned polls, cudaStream_t s) {
+                              void* img, unsigned* flags, unsigned polls, cudaStream_t s) {
   const int nblk = train_blocks(Bsz);
   const int np = mlp_param_count(L);
-  k_mlp_tc<<<nblk, 128, train_smem_bytes(L), s>>>(params, L, Bsz, nullptr, nullptr, feat, beta, M,
+  k_mlp_tc<<<nblk, 128, train_smem_bytes(L), s>>>(L, Bsz, nullptr, nullptr, feat, beta, M,
                                                   (uint32_t)seed, (uint32_t)(seed >> 32), ctl, st,
-                                                  part, flags, polls);
+                                                  part, (const uint8_t*)img, flags, polls);
   k_reduce_adam<<<(np + 1 + 31) / 32, 256, 0, s>>>(part, nblk, np, grad, loss, params, adam_m,
-                                                   adam_v, ctl, Bsz, 1e-8f, flags);
+                                                   adam_v, ctl, Bsz, 1e-8f, flags,
+                                                   (uint8_t*)img, L);
   return cudaGetLastError();
 }
 

@@ -133,65 +133,10 @@ __device__ __forceinline__ void store_split8(uint8_t* base, int kin, int r, int 
   *(uint4*)(base + canon_off(r, kin + c0, 2 * kin)) = make_uint4(l[0], l[1], l[2], l[3]);
 }
 
-// The features of gene g for L = LL columns, split into row `row` of the first
-// operand (2 k1 columns): the same operations in the same order as
-// gene_features, with every global load issued before the arithmetic so that
-// their latencies overlap, and every feature slot a compile-time index, so that
-// the features stay in registers.  act = false stores zeros.
-template <int LL>
-__device__ __forceinline__ void features_split(const ModelConst& mc, const DevPtrsF32& p, int g,
-                                               const Hyper* hy, bool act, int k1, uint8_t* abuf,
-                                               int row) {
-  constexpr int F = 4 * LL + 1;
-  constexpr int K1 = (F + 15) & ~15;
-  float f[K1];
-#pragma unroll
-  for (int i = 0; i < K1; ++i) f[i] = 0.0f;
-  if (act) {
-    const int G = mc.G, N = mc.N;
-    float b[LL], tl[LL], th[LL], s2[LL], a[LL];
-#pragma unroll
-    for (int l = 0; l < LL; ++l) {
-      b[l] = p.beta[(size_t)l * G + g];
-      tl[l] = (float)p.T[(size_t)l * G + g];
-      th[l] = (float)hy->phi[2 + l];
-      s2[l] = (float)hy->phi[2 + LL + l];
-      a[l] = 0.0f;
-    }
-    const float gm = p.gam[g];
-    for (int n0 = 0; n0 < N; n0 += 16) {
-      float ev[16];
-#pragma unroll
-      for (int i = 0; i < 16; ++i) ev[i] = n0 + i < N ? p.eps[(size_t)(n0 + i) * G + g] : 0.0f;
-#pragma unroll
-      for (int i = 0; i < 16; ++i) {
-        if (n0 + i < N) {
-          const float* xn = mc.Xf + (n0 + i) * kMaxL;
-          float lin = ev[i];
-#pragma unroll
-          for (int l = 0; l < LL; ++l) lin += xn[l] * b[l];
-#pragma unroll
-          for (int l = 0; l < LL; ++l) a[l] += xn[l] * lin;
-        }
-      }
-    }
-    const float invN = 1.0f / (float)N;
-#pragma unroll
-    for (int l = 0; l < LL; ++l) {
-      f[l] = a[l] * invN;
-      f[LL + l] = asinhf(tl[l]);
-      f[2 * LL + 1 + l] = th[l];
-      f[3 * LL + 1 + l] = 0.5f * logf(s2[l]);
-    }
-    f[2 * LL] = logf(gm);
-  }
-#pragma unroll
-  for (int c0 = 0; c0 < K1; c0 += 8) store_split8(abuf, k1, row, c0, f + c0);
-}
-
 // Row r, 8 consecutive values v of an operand whose 8-row groups are sbo bytes
 // apart: the BF16 hi parts into 16-byte chunk ch_hi of the row, the lo parts
-// into chunk ch_lo (K-major: the chunk is 8 consecutive K columns).
+// into chunk ch_lo (K-major: the chunk is 8 consecutive K columns; read as an
+// MN-major operand, 8 consecutive M or N elements of K row r).
 __device__ __forceinline__ void store_split8_ch(uint8_t* base, uint32_t sbo, int r, int ch_hi,
                                                 int ch_lo, const float* v) {
   uint32_t h[4], l[4];
@@ -453,16 +398,18 @@ __device__ __forceinline__ bool tc_tile(TcBlock& c, const ModelConst& mc, const 
   const uint32_t sa = smem_u32(abuf), sw = smem_u32(sm);
   const float* bias = (const float*)(sm + t.off_b);
   // features of this thread's gene, split into the first operand
-  static_assert(kMaxL == 8, "one case per number of columns");
-  switch (mc.L) {
-    case 1: features_split<1>(mc, p, g, p.hyp, act, t.k1, abuf, tid); break;
-    case 2: features_split<2>(mc, p, g, p.hyp, act, t.k1, abuf, tid); break;
-    case 3: features_split<3>(mc, p, g, p.hyp, act, t.k1, abuf, tid); break;
-    case 4: features_split<4>(mc, p, g, p.hyp, act, t.k1, abuf, tid); break;
-    case 5: features_split<5>(mc, p, g, p.hyp, act, t.k1, abuf, tid); break;
-    case 6: features_split<6>(mc, p, g, p.hyp, act, t.k1, abuf, tid); break;
-    case 7: features_split<7>(mc, p, g, p.hyp, act, t.k1, abuf, tid); break;
-    default: features_split<kMaxL>(mc, p, g, p.hyp, act, t.k1, abuf, tid); break;
+  {
+    float f[kMaxK1];
+#pragma unroll
+    for (int i = 0; i < kMaxK1; ++i) f[i] = 0.0f;
+    if (act) {
+      float a[kMaxL];
+      feature_sums(mc, p, g, 0, mc.N, a);
+      finish_features(mc, p, g, p.hyp, a, f);
+    }
+#pragma unroll
+    for (int c0 = 0; c0 < kMaxK1; c0 += 8)
+      if (c0 < t.k1) store_split8(abuf, t.k1, tid, c0, f + c0);
   }
   // three layers: D1 = A1 W1^T (columns 0..63), D2 = A2 W2^T (64..127), D3 = A3 W3^T
   // (columns 0..n3-1); A2, A3 overwrite the operand buffer once the GEMM before

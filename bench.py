@@ -111,6 +111,16 @@ ISSUE_PEAK_WARP_INST_S = 152 * 4 * 2.07e9
 # K = 20) and the tensor-core flops its split-BF16 GEMMs issue per gene
 NET_FLOP_PER_GENE = 2 * (21 * 64 + 64 * 64 + 64 * 20)
 MMA_FLOP_PER_GENE = 2 * 3 * (32 * 64 + 64 * 64 + 64 * 32)
+# One training row (L = 5: F = 21 features, K = 20 outputs, hidden 64): the
+# forward products, the two backward products that carry the gradient to the
+# hidden layers, and the three weight-gradient products; and what the tensor
+# cores execute for it (three split-BF16 products each, padded shapes: 22 -> 32
+# input columns with the column of ones, 20 -> 32 outputs, the weight-gradient
+# products as one of 128 x (64 + 32 + 32) and one of 128 x 64 over the rows)
+TRAIN_FLOP_PER_ROW = 2 * (21 * 64 + 64 * 64 + 64 * 20) + 2 * (20 * 64 + 64 * 64) + \
+    2 * (64 * 21 + 64 * 64 + 20 * 64)
+TRAIN_MMA_FLOP_PER_ROW = 2 * 3 * ((32 * 64 + 64 * 64 + 64 * 32) + (32 * 64 + 64 * 64) +
+                                  128 * 128 + 128 * 64)
 # FP64 peak from unit counts and clock: 152 SMs x 2 DFMA/clk x 2 flop x 2.07 GHz
 FP64_PEAK_TFLOPS = 152 * 2 * 2 * 2.07e9 / 1e12
 
@@ -700,6 +710,7 @@ def main():
         forms.get(f, {}).pop("params", None)
 
     # ---- device-timed throughput: W warm-up + K timed steps of S sweeps
+    train_timed = None
     smp = new_sampler(fbs, data, data["y"], form, seed + 1, rank, args.block)
     tb = args.tune_sweeps // 2
     smp.run(args.tune_sweeps, burnin=tb, thin=thin)   # tune the slice widths (burn-in)
@@ -707,7 +718,13 @@ def main():
     if learned:
         if params is None:
             smp.proposal_collect(PAIR_SWEEPS, burnin=tb, thin=2)
+            torch.cuda.synchronize()
+            t_tr = time.perf_counter()
             smp.proposal_train(seed=seed, **dict(TRAIN, epochs=args.train_epochs))
+            t_tr = time.perf_counter() - t_tr
+            n_pairs = PAIR_SWEEPS * data["y"].shape[0]
+            train_timed = {"s": t_tr, "steps": args.train_epochs *
+                           ((n_pairs + TRAIN["batch"] - 1) // TRAIN["batch"])}
         else:
             smp.proposal_params(set_to=params)
         min_accept, mode = LEARNED_FORMS[form]
@@ -809,6 +826,21 @@ def main():
             "flop_per_launch": NET_FLOP_PER_GENE * G,
             "mma_flop_per_launch": MMA_FLOP_PER_GENE * G,
             "peak_source": src + " bf16 sustained"}
+        if train_timed is not None:
+            step_s = train_timed["s"] / train_timed["steps"]
+            rows = TRAIN["batch"]
+            tft = TRAIN_FLOP_PER_ROW * rows / step_s / 1e12
+            roofline["training"] = {
+                "kernels": "k_mlp_tc + k_reduce_adam per step (one graph replay per 8 steps)",
+                "bound": "tensor", "step_us": step_s * 1e6, "rows_per_step": rows,
+                "achieved": tft, "peak": bf16, "unit": "TFLOP/s", "frac": tft / bf16,
+                "flop_per_step": TRAIN_FLOP_PER_ROW * rows,
+                "mma_flop_per_step": TRAIN_MMA_FLOP_PER_ROW * rows,
+                "mma_tflops": TRAIN_MMA_FLOP_PER_ROW * rows / step_s / 1e12,
+                "timing": "host-timed fbs_proposal_train call (device synchronised on both "
+                          "sides; column statistics, folding and graph instantiation "
+                          "included) / its steps",
+                "peak_source": src + " bf16 sustained"}
     st = smp.proposal_stats() if learned else None
     smp.close()
 

@@ -344,7 +344,11 @@ int fbs_proposal_collect(fbs_handle* h, int64_t n_sweeps, int64_t burnin, int64_
 
 /* Train the network on the collected pairs with Adam (Kingma & Ba) on minibatches
  * of `batch` pairs drawn with replacement, for `epochs` passes; every forward and
- * backward pass runs in this library's kernels.  Training works in standardised
+ * backward pass runs in this library's kernels (tcgen05 tensor cores, split-BF16
+ * operands, 128 pairs per block).  The tensor-core waits of a step are bounded
+ * by fbs_proposal_wait_limit's poll count: a step whose wait gives up leaves the
+ * parameters unchanged, and the call returns FBS_E_CUDA with the parameters of
+ * the last completed step.  Training works in standardised
  * coordinates (each feature and each beta column shifted by its mean over the
  * pairs and divided by its standard deviation); the parameters are mapped back
  * to raw coordinates afterwards, so inference and fbs_proposal_params see the
@@ -380,8 +384,10 @@ int fbs_proposal_fused(fbs_handle* h, int on);
  * 2^24).  A wait that reaches it gives up: the block sets a flag, waits up to
  * 2^24 polls for its copies and matrix products still in flight, frees its tensor
  * memory, and its genes skip the network's move in that sweep; fbs_sync then
- * returns FBS_E_CUDA.  0 makes every pass give up at its first wait (which
- * exercises that path).  FBS_E_ARG for FP64 handles and batch views. */
+ * returns FBS_E_CUDA.  The training steps of fbs_proposal_train use the same
+ * bound (a step that gives up is skipped and the call returns FBS_E_CUDA).  0
+ * makes every pass give up at its first wait (which exercises that path).
+ * FBS_E_ARG for FP64 handles and batch views. */
 int fbs_proposal_wait_limit(fbs_handle* h, uint32_t polls);
 
 /* Copy the FP32 parameters out (get != NULL) and/or in (set != NULL); n must equal

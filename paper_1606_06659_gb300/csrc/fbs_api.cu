@@ -1355,8 +1355,8 @@ int fbs_proposal_train(fbs_handle* h, int epochs, int batch, double lr, uint64_t
   train_bufs_free(t);
   if (rc) return rc;
   FBS_CUDA(e);
+  ls->trained = true;  // raw coordinates from here on, even after a failed wait
   if (rc_wait) return rc_wait;
-  ls->trained = true;
   if (final_loss) *final_loss = loss_epoch / (double)steps_per_epoch + log_scale;
   if (h->seg_exec) {
     cudaGraphExecDestroy(h->seg_exec);

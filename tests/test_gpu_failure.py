@@ -191,3 +191,29 @@ def test_tensor_core_wait_that_gives_up_is_reported():
     assert all(np.isfinite(st[k]).all() for k in ("eps", "beta", "gam", "phi"))
     assert s.counters()["sweeps"] == 30 + 20 + 10 + 5
     s.close()
+
+
+def test_training_wait_that_gives_up_is_reported():
+    """With a poll bound of 0 the training kernel gives up at its first wait (for
+    the weight image): every block drains the copy and frees its tensor memory,
+    the Adam update skips the step, and fbs_proposal_train returns FBS_E_CUDA
+    naming the wait with the parameters as they were (back in raw coordinates).
+    With the default bound restored the same call trains."""
+    d = synthetic.make_config(1, G=1000)
+    s = fbs.Sampler(d["y"], d["X"], d["h"], d["priors"], seed=13, precision=fbs.FBS_F32)
+    t = d["truth"]
+    s.set_state(it=0, eps=t["eps"], beta=t["beta"], gam=t["gam"], phi=t["phi"])
+    s.proposal_collect(20, burnin=20, thin=1)
+    s.proposal_train(epochs=1, batch=2048, lr=2e-3, seed=13)
+    before = s.proposal_params()
+    s.proposal_wait_limit(0)
+    with pytest.raises(fbs.FbsError) as e:
+        s.proposal_train(epochs=2, batch=2048, lr=2e-3, seed=13)
+    assert e.value.code == fbs.FBS_E_CUDA and "tensor-core wait" in str(e.value)
+    assert np.allclose(s.proposal_params(), before, rtol=1e-5, atol=1e-6)
+    s.proposal_wait_limit(1 << 24)
+    loss = s.proposal_train(epochs=2, batch=2048, lr=2e-3, seed=13)
+    assert np.isfinite(loss)
+    after = s.proposal_params()
+    assert np.all(np.isfinite(after)) and not np.allclose(after, before)
+    s.close()

@@ -517,12 +517,16 @@ def ess_job(fbs, torch, data, y_host, form, seed, chain, block, S, train_epochs)
         tt = time.perf_counter()
         smp.proposal_collect(PAIR_SWEEPS, burnin=burnin, thin=2)
         done += 2 * PAIR_SWEEPS
+        t_tr = time.perf_counter()   # proposal_collect returns with the stream synchronised
         loss = smp.proposal_train(seed=seed, **dict(TRAIN, epochs=train_epochs))
+        t_tr = time.perf_counter() - t_tr   # and proposal_train too
         smp.proposal_calibrate(CALIBRATE_SWEEPS, burnin=burnin, min_accept=min_accept)
         smp.proposal_mode(mode)
         done += CALIBRATE_SWEEPS
         st0 = smp.proposal_stats()
-        extra = {"train_pairs": PAIR_SWEEPS * data["y"].shape[0], "train_loss": loss,
+        n_pairs = PAIR_SWEEPS * data["y"].shape[0]
+        extra = {"train_pairs": n_pairs, "train_loss": loss, "train_s": t_tr,
+                 "train_steps": train_epochs * ((n_pairs + TRAIN["batch"] - 1) // TRAIN["batch"]),
                  "collect_train_calibrate_s": time.perf_counter() - tt,
                  "mh_genes": st0["mh_genes"], "prior_genes": st0["prior_genes"],
                  "min_accept": min_accept, "mode": mode}
@@ -711,6 +715,8 @@ def main():
 
     # ---- device-timed throughput: W warm-up + K timed steps of S sweeps
     train_timed = None
+    if form in forms and "train_s" in forms[form]:
+        train_timed = {"s": forms[form]["train_s"], "steps": forms[form]["train_steps"]}
     smp = new_sampler(fbs, data, data["y"], form, seed + 1, rank, args.block)
     tb = args.tune_sweeps // 2
     smp.run(args.tune_sweeps, burnin=tb, thin=thin)   # tune the slice widths (burn-in)
@@ -837,9 +843,9 @@ def main():
                 "flop_per_step": TRAIN_FLOP_PER_ROW * rows,
                 "mma_flop_per_step": TRAIN_MMA_FLOP_PER_ROW * rows,
                 "mma_tflops": TRAIN_MMA_FLOP_PER_ROW * rows / step_s / 1e12,
-                "timing": "host-timed fbs_proposal_train call (device synchronised on both "
-                          "sides; column statistics, folding and graph instantiation "
-                          "included) / its steps",
+                "timing": "host-timed fbs_proposal_train call of the job (20 epochs of the "
+                          "2e6 pairs; device synchronised on both sides; column statistics, "
+                          "folding and graph instantiation included) / its steps",
                 "peak_source": src + " bf16 sustained"}
     st = smp.proposal_stats() if learned else None
     smp.close()

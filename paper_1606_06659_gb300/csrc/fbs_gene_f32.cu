@@ -662,8 +662,9 @@ __global__ void __launch_bounds__(128) k_gb_f32(ModelConst mc, DevPtrsF32 p, int
   ktime_end(p.ktime, p.ktime_n, 3 * seg_i + 1);
 }
 
-// Shared memory of the fused kernel: the network pass (weight image and operand
-// buffer) from offset 0, then the gamma/beta updates' arrays from offset 0, and
+// Shared memory of the fused kernel: the network pass (its weight image; the A
+// operands are in tensor memory) from offset 0, then the gamma/beta updates'
+// arrays from offset 0, and
 // the network's outputs of the block's genes ([K][128] floats) at
 // gb_net_stash_offset, past both the weight image and those arrays.
 __host__ __device__ inline size_t gb_net_stash_offset(int N, int L) {
@@ -696,8 +697,6 @@ __global__ void __launch_bounds__(128) k_gb_net_f32(ModelConst mc, DevPtrsF32 p,
     __shared__ uint32_t tmem_slot;
     __shared__ int s_abort;
     const TcShape t = tc_shape(mc.L);
-    size_t off_a;
-    tc_smem_layout(mc.L, &off_a);
     if (threadIdx.x == 0) s_abort = 0;
     TcBlock c;
     tc_begin(c, bars, &tmem_slot, img, sm_tc, t.bytes, p.tc_polls);
@@ -706,8 +705,8 @@ __global__ void __launch_bounds__(128) k_gb_net_f32(ModelConst mc, DevPtrsF32 p,
     const int g = blockIdx.x * 128 + (int)threadIdx.x;
     prop_s = reinterpret_cast<float*>(sm_tc + gb_net_stash_offset(mc.N, mc.L));
     if (!s_abort)
-      tc_tile(c, mc, p, t, sm_tc, sm_tc + off_a, g, net_gene(p, g, mc.G), prop_s, 128,
-              (int)threadIdx.x, &s_abort);
+      tc_tile(c, mc, p, t, sm_tc, g, net_gene(p, g, mc.G), prop_s, 128, (int)threadIdx.x,
+              &s_abort);
     __syncthreads();
     net_ok = s_abort == 0;
     tc_end(c, !net_ok, &p.hyp->flags);

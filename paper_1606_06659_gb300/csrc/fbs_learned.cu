@@ -98,8 +98,6 @@ __global__ void __launch_bounds__(kTcThreads) k_proposal_tc(ModelConst mc, DevPt
   __shared__ uint32_t tmem_slot;
   __shared__ int s_abort;
   const TcShape t = tc_shape(mc.L);
-  size_t off_a;
-  tc_smem_layout(mc.L, &off_a);
   if (threadIdx.x == 0) s_abort = 0;
   TcBlock c;
   tc_begin(c, bars, &tmem_slot, img_g, sm, t.bytes, p.tc_polls);
@@ -107,8 +105,7 @@ __global__ void __launch_bounds__(kTcThreads) k_proposal_tc(ModelConst mc, DevPt
   __syncthreads();
   for (int tile = blockIdx.x; tile < ntiles && !s_abort; tile += gridDim.x) {
     const int g = tile * 128 + (int)threadIdx.x;
-    if (!tc_tile(c, mc, p, t, sm, sm + off_a, g, net_gene(p, g, mc.G), out, (size_t)mc.G, g,
-                 &s_abort))
+    if (!tc_tile(c, mc, p, t, sm, g, net_gene(p, g, mc.G), out, (size_t)mc.G, g, &s_abort))
       break;
   }
   tc_end(c, s_abort != 0, &p.hyp->flags);
@@ -852,9 +849,9 @@ cudaError_t launch_proposal_f32(const ModelConst& mc, const DevPtrsF32& p, const
   e = cudaFuncSetAttribute(k_proposal_tc, cudaFuncAttributeMaxDynamicSharedMemorySize,
                            (int)tc_smem_layout(FBS_MAX_L, nullptr));
   if (e != cudaSuccess) return e;
-  // Up to three blocks per SM (shared memory), 128 TMEM columns each.
+  // Up to four blocks per SM: 128 of the SM's 512 TMEM columns each.
   const int ntiles = (mc.G + 127) / 128;
-  const int grid = ntiles < 3 * nsm ? ntiles : 3 * nsm;
+  const int grid = ntiles < 4 * nsm ? ntiles : 4 * nsm;
   k_proposal_tc<<<grid, kTcThreads, smem, s>>>(mc, p, (const uint8_t*)img, out, ntiles);
   return cudaGetLastError();
 }

@@ -65,18 +65,23 @@ __device__ __forceinline__ void gene_features(const ModelConst& mc, const DevPtr
 // ---------------------------------------------------------------- tensor-core inference
 //
 // The network runs on the tensor cores (tcgen05): per tile of 128 genes (one
-// thread per gene, four warps) three GEMMs D = A W^T with BF16 operands read
-// from shared memory and FP32 accumulators in tensor memory, M = 128 and
-// N = 64, 64, n3.  Every FP32 operand x (weights, features, activations) enters
-// as a BF16 pair x = hi + lo, hi = bf16(x), lo = bf16(x - hi); each layer
-// accumulates hi*hi + lo*hi + hi*lo, which keeps about 16 significant bits per
-// operand (the lo*lo term is below that).  GELU, the biases and the split of
-// the next layer's input run in the epilogue, one thread per TMEM lane (= gene).
+// thread per gene, four warps) three GEMMs D = A W^T with FP32 accumulators in
+// tensor memory, M = 128 and N = 64, 64, n3.  Every FP32 operand x (weights,
+// features, activations) enters as a BF16 pair x = hi + lo, hi = bf16(x),
+// lo = bf16(x - hi); each layer accumulates hi*hi + lo*hi + hi*lo, which keeps
+// about 16 significant bits per operand (the lo*lo term is below that).  GELU,
+// the biases and the split of the next layer's input run in the epilogue, one
+// thread per TMEM lane (= gene).
 //
-// Operands use the canonical K-major layout without swizzle: 8 x 16-byte core
-// matrices of 128 contiguous bytes, the core matrices of one 8-row group
-// consecutive along K (leading byte offset 128), the groups `sbo` bytes apart.
-// An operand with kw columns holds [hi (kw/2) | lo (kw/2)].
+// The weights (B operands) sit in shared memory in the canonical K-major
+// layout without swizzle: 8 x 16-byte core matrices of 128 contiguous bytes,
+// the core matrices of one 8-row group consecutive along K (leading byte
+// offset 128), the groups `sbo` bytes apart; an operand with kw columns holds
+// [hi (kw/2) | lo (kw/2)].  The features and activations (A operands) sit in
+// tensor memory next to the accumulators: row m in lane m, BF16 values packed
+// two per 32-bit column (element 2c in the low half of column c), hi columns
+// then lo columns, so the epilogue writes the next layer's input with
+// tcgen05.st and no shared memory is involved.
 
 struct TcShape {
   int F, K;      // features, outputs
@@ -100,37 +105,19 @@ __host__ __device__ inline TcShape tc_shape(int L) {
 
 constexpr int kMaxK1 = (kMaxFeat + 15) & ~15;
 
-// Shared memory: the weight image, then one A operand buffer of 128 rows that
-// holds in turn the split features (2 k1 columns) and the split activations of
-// the two hidden layers (128 columns); each is dead once its GEMM completed.
+// Shared memory of the network pass: the weight image alone (the A operands are
+// in tensor memory); *off_a = its size rounded to 1 KB, where a caller's own
+// shared data may start.
 __host__ __device__ inline size_t tc_smem_layout(int L, size_t* off_a) {
   const TcShape t = tc_shape(L);
   const size_t a = ((size_t)t.bytes + 1023) & ~(size_t)1023;
-  const size_t cols = 2 * t.k1 > 2 * kMlpHidden ? 2 * t.k1 : 2 * kMlpHidden;
   if (off_a) *off_a = a;
-  return a + (size_t)128 * cols * 2;
+  return a;
 }
 
-// Byte offset of element (r, c) of a canonical operand with kw columns.
+// Byte offset of element (r, c) of a canonical K-major operand with kw columns.
 __host__ __device__ inline uint32_t canon_off(int r, int c, int kw) {
   return (uint32_t)(((r >> 3) * (kw >> 3) + (c >> 3)) * 128 + (r & 7) * 16 + (c & 7) * 2);
-}
-
-// Row r, columns c0..c0+7 of an operand with kw = 2 kin columns: hi parts at
-// c0.., lo parts at kin + c0.. (16-byte stores; pairs converted together).
-__device__ __forceinline__ void store_split8(uint8_t* base, int kin, int r, int c0,
-                                             const float* v) {
-  uint32_t h[4], l[4];
-#pragma unroll
-  for (int i = 0; i < 4; ++i) {
-    const __nv_bfloat162 hb = __floats2bfloat162_rn(v[2 * i], v[2 * i + 1]);
-    const float2 hf = __bfloat1622float2(hb);
-    const __nv_bfloat162 lb = __floats2bfloat162_rn(v[2 * i] - hf.x, v[2 * i + 1] - hf.y);
-    h[i] = *reinterpret_cast<const uint32_t*>(&hb);
-    l[i] = *reinterpret_cast<const uint32_t*>(&lb);
-  }
-  *(uint4*)(base + canon_off(r, c0, 2 * kin)) = make_uint4(h[0], h[1], h[2], h[3]);
-  *(uint4*)(base + canon_off(r, kin + c0, 2 * kin)) = make_uint4(l[0], l[1], l[2], l[3]);
 }
 
 // Row r, 8 consecutive values v of an operand whose 8-row groups are sbo bytes
@@ -215,22 +202,6 @@ __device__ __forceinline__ void umma_bf16(uint32_t d, uint64_t a, uint64_t b, ui
       : "memory");
 }
 
-// D (+)= A B^T over kin columns for the three hi/lo products; a and b are the
-// operands' shared addresses, both with 2 kin columns.
-__device__ __forceinline__ void issue_layer(uint32_t d, uint32_t a, uint32_t b, int kin,
-                                            uint32_t idesc) {
-  const uint32_t sbo = (uint32_t)(2 * kin / 8) * 128;
-  const uint32_t lo = (uint32_t)(kin / 8) * 128;
-  const uint32_t pa[3] = {0u, lo, 0u}, pb[3] = {0u, 0u, lo};
-  uint32_t acc = 0u;
-#pragma unroll
-  for (int q = 0; q < 3; ++q)
-    for (int k = 0; k < kin; k += 16) {
-      const uint32_t ko = (uint32_t)(k / 8) * 128;
-      umma_bf16(d, umma_desc(a + pa[q] + ko, sbo), umma_desc(b + pb[q] + ko, sbo), idesc, acc);
-      acc = 1u;
-    }
-}
 
 __device__ __forceinline__ void umma_commit(uint32_t bar) {
   asm volatile(
@@ -289,11 +260,65 @@ __device__ __forceinline__ void tmem_ld32(uint32_t taddr, float* v) {
   for (int i = 0; i < 32; ++i) v[i] = __uint_as_float(r[i]);
 }
 
-// Bias, GELU and the split store of this thread's 32 columns c0.. of a hidden layer.
-__device__ __forceinline__ void hidden_epilogue(uint32_t taddr, const float* bias, uint8_t* abuf,
-                                                int row, int c0) {
+
+
+// Tensor-memory A operands: 16-bit elements packed two per 32-bit column (element
+// 2c in the low half of column c), row m in lane m.
+__device__ __forceinline__ void tmem_st8(uint32_t taddr, const uint32_t* r) {
+  asm volatile("tcgen05.st.sync.aligned.32x32b.x8.b32 [%0], {%1, %2, %3, %4, %5, %6, %7, %8};" ::"r"(taddr),
+               "r"(r[0]), "r"(r[1]), "r"(r[2]), "r"(r[3]), "r"(r[4]), "r"(r[5]), "r"(r[6]), "r"(r[7])
+               : "memory");
+}
+__device__ __forceinline__ void tmem_st16(uint32_t taddr, const uint32_t* r) {
+  asm volatile("tcgen05.st.sync.aligned.32x32b.x16.b32 [%0], {%1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, %15, %16};" ::"r"(taddr),
+               "r"(r[0]), "r"(r[1]), "r"(r[2]), "r"(r[3]), "r"(r[4]), "r"(r[5]), "r"(r[6]), "r"(r[7]),
+               "r"(r[8]), "r"(r[9]), "r"(r[10]), "r"(r[11]), "r"(r[12]), "r"(r[13]), "r"(r[14]), "r"(r[15])
+               : "memory");
+}
+// 2n values split into BF16 hi / lo parts packed in pairs: hi[i], lo[i] hold elements 2i, 2i+1.
+template <int NW>
+__device__ __forceinline__ void pack_split(const float* v, uint32_t* hi, uint32_t* lo) {
+#pragma unroll
+  for (int i = 0; i < NW; ++i) {
+    const __nv_bfloat162 hb = __floats2bfloat162_rn(v[2 * i], v[2 * i + 1]);
+    const float2 hf = __bfloat1622float2(hb);
+    const __nv_bfloat162 lb = __floats2bfloat162_rn(v[2 * i] - hf.x, v[2 * i + 1] - hf.y);
+    hi[i] = *reinterpret_cast<const uint32_t*>(&hb);
+    lo[i] = *reinterpret_cast<const uint32_t*>(&lb);
+  }
+}
+__device__ __forceinline__ void umma_bf16_ta(uint32_t d, uint32_t a_tmem, uint64_t b, uint32_t idesc,
+                                             uint32_t acc) {
+  asm volatile(
+      "{\n\t.reg .pred p;\n\t"
+      "setp.ne.b32 p, %4, 0;\n\t"
+      "tcgen05.mma.cta_group::1.kind::f16 [%0], [%1], %2, %3, p;\n\t}\n"
+      :
+      : "r"(d), "r"(a_tmem), "l"(b), "r"(idesc), "r"(acc)
+      : "memory");
+}
+// D (+)= A B^T over kin columns for the three hi/lo products, A in tensor memory
+// (hi at column a, lo at a + kin / 2), B in shared memory with 2 kin columns.
+__device__ __forceinline__ void issue_layer_ta(uint32_t d, uint32_t a, uint32_t b, int kin,
+                                               uint32_t idesc) {
+  const uint32_t sbo = (uint32_t)(2 * kin / 8) * 128;
+  const uint32_t lo = (uint32_t)(kin / 8) * 128;
+  const uint32_t pa[3] = {0u, (uint32_t)(kin / 2), 0u}, pb[3] = {0u, 0u, lo};
+  uint32_t acc = 0u;
+#pragma unroll
+  for (int q = 0; q < 3; ++q)
+    for (int k = 0; k < kin; k += 16) {
+      umma_bf16_ta(d, a + pa[q] + (uint32_t)(k / 2), umma_desc(b + pb[q] + (uint32_t)(k / 8) * 128, sbo),
+                   idesc, acc);
+      acc = 1u;
+    }
+}
+// Bias, GELU and the split tensor-memory store of this thread's 32 columns c0.. of a
+// hidden layer (D at taddr_d, the next layer's A at a_hi / a_hi + 32).
+__device__ __forceinline__ void hidden_epilogue_ta(uint32_t taddr_d, const float* bias,
+                                                   uint32_t a_hi, int c0) {
   float v[32];
-  tmem_ld32(taddr, v);
+  tmem_ld32(taddr_d, v);
 #pragma unroll
   for (int i = 0; i < 32; i += 4) {
     const float4 bb = *reinterpret_cast<const float4*>(bias + c0 + i);
@@ -302,11 +327,13 @@ __device__ __forceinline__ void hidden_epilogue(uint32_t taddr, const float* bia
     v[i + 2] = gelu_fast(v[i + 2] + bb.z);
     v[i + 3] = gelu_fast(v[i + 3] + bb.w);
   }
-#pragma unroll
-  for (int i = 0; i < 32; i += 8) store_split8(abuf, kMlpHidden, row, c0 + i, v + i);
+  uint32_t hi[16], lo[16];
+  pack_split<16>(v, hi, lo);
+  tmem_st16(a_hi + (uint32_t)(c0 / 2), hi);
+  tmem_st16(a_hi + 32u + (uint32_t)(c0 / 2), lo);
 }
 
-constexpr uint32_t kTmemCols = 128;  // D1 at columns 0..63, D2 at 64..127, D3 at 0..n3-1
+constexpr uint32_t kTmemCols = 128;  // accumulators at columns 0..63, A operands at 64..127
 
 // Per-block state of the network: tensor-memory base, the two mbarriers (weight
 // image, MMA completion), the completion phase and the wait outcomes.
@@ -380,23 +407,25 @@ __device__ __forceinline__ void tc_end(TcBlock& c, bool aborted, unsigned* flags
 }
 
 // The network for one tile of 128 genes by the block's 128 threads: thread t
-// holds gene g (its TMEM lane, row t of the operands), warp w reads lane
-// quadrant w.  The weight image is at sm, the A operand buffer at abuf.  Genes
-// with act write their K outputs to out[k ostride + oidx] (global [K][G] with
+// holds gene g (its TMEM lane, row t of the A operands and accumulators), warp
+// w reads and writes lane quadrant w.  The weight image is at sm.  Genes with
+// act write their K outputs to out[k ostride + oidx] (global [K][G] with
 // ostride = G, oidx = g, or a block's shared [K][128] with ostride = 128,
-// oidx = t, which may lie in the operand buffer: it is written after the last
-// GEMM completed).  Every wait is bounded; one
-// that gives up sets *s_abort (block-shared), and the function returns false
-// once every thread has seen it.  Ends with a block barrier.
+// oidx = t, outside the weight image).  Every wait is bounded; one that gives
+// up sets *s_abort (block-shared), and the function returns false once every
+// thread has seen it.  Ends with a block barrier.
 __device__ __forceinline__ bool tc_tile(TcBlock& c, const ModelConst& mc, const DevPtrsF32& p,
-                                        const TcShape& t, uint8_t* sm, uint8_t* abuf, int g,
-                                        bool act, float* out, size_t ostride, int oidx,
+                                        const TcShape& t, uint8_t* sm, int g, bool act,
+                                        float* out, size_t ostride, int oidx,
                                         volatile int* s_abort) {
   const int tid = threadIdx.x, warp = tid >> 5;
   const uint32_t lane_addr = (uint32_t)(warp * 32) << 16;
   const uint32_t id64 = umma_idesc_bf16(128, 64), id3 = umma_idesc_bf16(128, t.n3);
-  const uint32_t sa = smem_u32(abuf), sw = smem_u32(sm);
+  const uint32_t sw = smem_u32(sm);
   const float* bias = (const float*)(sm + t.off_b);
+  // tensor memory: D at columns 0..63 (0..n3-1 for the last layer), the A
+  // operand of the next product at 64..127 (hi, then lo)
+  const uint32_t a_col = c.tmem + lane_addr + 64u;
   // features of this thread's gene, split into the first operand
   {
     float f[kMaxK1];
@@ -408,23 +437,28 @@ __device__ __forceinline__ bool tc_tile(TcBlock& c, const ModelConst& mc, const 
       finish_features(mc, p, g, p.hyp, a, f);
     }
 #pragma unroll
-    for (int c0 = 0; c0 < kMaxK1; c0 += 8)
-      if (c0 < t.k1) store_split8(abuf, t.k1, tid, c0, f + c0);
+    for (int c0 = 0; c0 < kMaxK1; c0 += 16)
+      if (c0 < t.k1) {
+        uint32_t hi[8], lo[8];
+        pack_split<8>(f + c0, hi, lo);
+        tmem_st8(a_col + (uint32_t)(c0 / 2), hi);
+        tmem_st8(a_col + (uint32_t)(t.k1 / 2 + c0 / 2), lo);
+      }
+    asm volatile("tcgen05.wait::st.sync.aligned;" ::: "memory");
   }
-  // three layers: D1 = A1 W1^T (columns 0..63), D2 = A2 W2^T (64..127), D3 = A3 W3^T
-  // (columns 0..n3-1); A2, A3 overwrite the operand buffer once the GEMM before
-  // them has completed
+  // three layers: D1 = A1 W1^T, D2 = A2 W2^T, D3 = A3 W3^T, each D at columns 0..;
+  // A2, A3 overwrite the A columns once the product before them has completed
+  const uint32_t ta = c.tmem + 64u;
   for (int layer = 0; layer < 3; ++layer) {
-    fence_async_smem();
     tc_fence_before();
     __syncthreads();
     if (*s_abort) return false;
-    const uint32_t d = layer == 1 ? c.tmem + kMlpHidden : c.tmem;
+    const uint32_t d = c.tmem;
     if (tid == 0) {
       tc_fence_after();
-      if (layer == 0) issue_layer(d, sa, sw, t.k1, id64);
-      else if (layer == 1) issue_layer(d, sa, sw + (uint32_t)t.off_w2, kMlpHidden, id64);
-      else issue_layer(d, sa, sw + (uint32_t)t.off_w3, kMlpHidden, id3);
+      if (layer == 0) issue_layer_ta(d, ta, sw, t.k1, id64);
+      else if (layer == 1) issue_layer_ta(d, ta, sw + (uint32_t)t.off_w2, kMlpHidden, id64);
+      else issue_layer_ta(d, ta, sw + (uint32_t)t.off_w3, kMlpHidden, id3);
       umma_commit(c.bar_m);
     }
     c.pending = true;
@@ -434,9 +468,9 @@ __device__ __forceinline__ bool tc_tile(TcBlock& c, const ModelConst& mc, const 
     tc_fence_after();
     if (layer < 2) {
       const float* bl = bias + layer * kMlpHidden;
-      const uint32_t col = layer == 1 ? kMlpHidden : 0u;
-      hidden_epilogue(c.tmem + lane_addr + col, bl, abuf, tid, 0);
-      hidden_epilogue(c.tmem + lane_addr + col + 32u, bl, abuf, tid, 32);
+      hidden_epilogue_ta(c.tmem + lane_addr, bl, a_col, 0);
+      hidden_epilogue_ta(c.tmem + lane_addr + 32u, bl, a_col, 32);
+      asm volatile("tcgen05.wait::st.sync.aligned;" ::: "memory");
     } else {
       for (int c0 = 0; c0 < t.n3; c0 += 16) {
         float v[16];

@@ -543,9 +543,9 @@ void fbs_batch_free(fbs_batch* b);
  * (FBS_NOALLOC_MAX_GENES / 128 blocks), which every GPU that loads the library
  * holds until the process exits.  G above FBS_NOALLOC_MAX_GENES returns
  * FBS_E_ARG.  The first call on a device looks up the array's device address
- * (cudaGetSymbolAddress) with that device current; make that first call before
- * any stream capture.  The address is kept for the life of the process, so
- * the entry point must not be used on a device after cudaDeviceReset.  All calls share the array and every call rewrites what
+ * (cudaGetSymbolAddress) with that device current.  The address is kept for
+ * the life of the process, so the entry point must not be used on a device
+ * after cudaDeviceReset.  All calls share the array and every call rewrites what
  * it reads from it, so calls whose work overlaps on the GPU (different streams
  * at the same time) race; calls on one stream are ordered.  The call is
  * asynchronous on `stream` (NULL = legacy default stream): the outputs are

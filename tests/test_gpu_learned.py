@@ -59,10 +59,12 @@ def _oracle_outputs(st, d, params_flat):
     return P.forward(w, f)[0]
 
 
-@pytest.mark.parametrize("L,B", [(5, 1000), (2, 37)])
+@pytest.mark.parametrize("L,B", [(5, 1000), (2, 37), (8, 300)])
 def test_loss_and_gradient_match_oracle(L, B):
-    """One forward and backward pass of the training kernels (FP32, split-K
-    atomics) against the oracle's explicit backpropagation in FP64."""
+    """One forward and backward pass of the training kernels (tensor cores,
+    split-BF16 operands, 128 rows per block: a ragged last block in every case)
+    against the oracle's explicit backpropagation in FP64; L = 8 is the largest
+    shape (33 features with the column of ones in 48, 44 outputs in 48)."""
     F = P.n_features(L)
     p = _random_params(L, seed=L)
     flat = _flat(p)
@@ -92,6 +94,40 @@ def test_outputs_match_oracle_network():
     s.run(20, burnin=20)
     L = d["X"].shape[1]
     flat = _flat(_random_params(L, seed=9))
+    s.proposal_params(set_to=flat)
+    got = s.proposal_outputs()
+    want = _oracle_outputs(s.get_state(), d, flat)
+    assert got.shape == want.shape == (1000, P.n_outputs(L))
+    assert np.abs(want).max() > 0.5
+    np.testing.assert_allclose(got, want, rtol=1e-4, atol=1e-4)
+    s.close()
+
+
+def _design(L, N=16):
+    """The paper's N = 16 design for L <= 5; for L > 5 three more columns of
+    -1/0/1 entries (a fixed draw of full rank)."""
+    base = synthetic.paper_design(4)
+    if L <= 5:
+        return base[:, :L]
+    extra = np.random.default_rng(48).choice([-1.0, 0.0, 1.0], size=(N, 3))
+    return np.hstack([base, extra])[:, :L]
+
+
+@pytest.mark.parametrize("L", [2, 8])
+def test_outputs_match_oracle_network_other_widths(L):
+    """The inference kernel at the smallest and largest widths (L = 2: 9
+    features in 16 columns, 5 outputs in 16; L = 8: 33 in 48, 44 in 48, the
+    tensor-memory A operand at its widest) against the oracle's forward pass."""
+    X = _design(L)
+    assert np.linalg.matrix_rank(X) == L
+    theta = [4.0] + [0.0] * (L - 1)
+    sigma = [2.0] + [0.3] * (L - 1)
+    d = synthetic.simulate(X, theta, sigma, 0.1, 3.0, 1000, seed=900 + L)
+    d["priors"] = synthetic.default_priors(L)
+    s = fbs.Sampler(d["y"], d["X"], d["h"], d["priors"], seed=5, precision=fbs.FBS_F32)
+    s.set_state(it=0, **_truth(d))
+    s.run(20, burnin=20)
+    flat = _flat(_random_params(L, seed=9 + L))
     s.proposal_params(set_to=flat)
     got = s.proposal_outputs()
     want = _oracle_outputs(s.get_state(), d, flat)

@@ -530,6 +530,26 @@ int build_model(const int32_t* y, int N, int G, const double* X, int L, const do
     }
     mc.ncls[l] = nc;
   }
+  // distinct rows of X, for the FP32 beta columns' per-pattern rate sums
+  {
+    int rep[kMaxPat];
+    mc.npat = 0;
+    for (int n = 0; n < N && mc.npat <= kMaxPat; ++n) {
+      int r = 0;
+      while (r < mc.npat && memcmp(&X[n * L], &X[rep[r] * L], sizeof(double) * L) != 0) ++r;
+      if (r == mc.npat) {
+        if (mc.npat == kMaxPat) {
+          mc.npat = kMaxPat + 1;
+          break;
+        }
+        rep[mc.npat++] = n;
+      }
+      mc.pat[n] = (int8_t)r;
+    }
+    for (int l = 0; l < kMaxL; ++l)
+      for (int r = 0; r < kMaxPat; ++r)
+        mc.pcls[l][r] = (l < L && r < mc.npat && mc.npat <= kMaxPat) ? mc.cls[l][rep[r]] : -1;
+  }
   if (!pseudo_inverse(X, N, L, pinv)) return fail(FBS_E_ARG, "X^T X is singular");
   return FBS_OK;
 

@@ -16,6 +16,7 @@ constexpr int kMaxN = FBS_MAX_N;
 constexpr int kMaxL = FBS_MAX_L;
 constexpr int kMaxP = 2 * FBS_MAX_L + 2;     // nu, tau, theta[L], sigma2[L]
 constexpr int kMaxCls = FBS_MAX_CLASSES;
+constexpr int kMaxPat = 8;  // distinct rows of X the FP32 beta columns sum over
 constexpr int kNumPart = 2 + 2 * FBS_MAX_L;  // S1, S2, B1'[L], B2'[L]
 constexpr int kCounterCopies = 32;  // the eps kernels spread their counter atomics
 
@@ -72,6 +73,12 @@ struct ModelConst {
   float hf[kMaxN];
   float Xf[kMaxN * kMaxL];
   float cvalf[kMaxL][kMaxCls];
+  // Distinct rows of X (patterns): pat[n] = pattern of sample n, pcls[l][r] =
+  // class of pattern r in column l (-1 for a zero); npat = kMaxPat + 1 when X
+  // has more distinct rows (the FP32 beta columns then sum over samples).
+  int npat;
+  int8_t pat[kMaxN];
+  int8_t pcls[kMaxL][kMaxPat];
 };
 
 // Propositions of the contrast probabilities, in device memory: proposition q

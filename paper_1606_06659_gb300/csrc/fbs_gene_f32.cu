@@ -424,7 +424,8 @@ __device__ __forceinline__ void beta_column_f32(const ModelConst& mc, const DevP
                                                 int B, int tid, const Hyper* hy, long long it,
                                                 uint32_t it32, long long burnin,
                                                 long long tune_start, unsigned& evals_b,
-                                                unsigned& caps, unsigned& nonfin) {
+                                                unsigned& caps, unsigned& nonfin, bool use_pat,
+                                                float* E, const float* Yp) {
   const int G = mc.G, N = mc.N, L = mc.L;
   const size_t e = (size_t)l * G + g;
   const float theta = (float)hy->phi[2 + l];
@@ -442,16 +443,30 @@ __device__ __forceinline__ void beta_column_f32(const ModelConst& mc, const DevP
     Y[j] = 0.0f;
     f.v[j] = mc.cvalf[l][j];
   }
-  for (int n = 0; n < N; ++n) {
-    const int c = mc.cls[l][n];
-    const float m = mu[n * B + tid];
-    const float yv = ys[n * B + tid];
+  if (use_pat) {
 #pragma unroll
-    for (int j = 0; j < NC; ++j)
-      if (j == c) {
-        f.Q[j] += m;
-        Y[j] += yv;
+    for (int r = 0; r < kMaxPat; ++r)
+      if (r < mc.npat) {
+        const int c = mc.pcls[l][r];
+#pragma unroll
+        for (int j = 0; j < NC; ++j)
+          if (j == c) {
+            f.Q[j] += E[r];
+            Y[j] += Yp[r];
+          }
       }
+  } else {
+    for (int n = 0; n < N; ++n) {
+      const int c = mc.cls[l][n];
+      const float m = mu[n * B + tid];
+      const float yv = ys[n * B + tid];
+#pragma unroll
+      for (int j = 0; j < NC; ++j)
+        if (j == c) {
+          f.Q[j] += m;
+          Y[j] += yv;
+        }
+    }
   }
 #pragma unroll
   for (int j = 0; j < NC; ++j) f.D[j] = Y[j] - f.Q[j];
@@ -470,13 +485,26 @@ __device__ __forceinline__ void beta_column_f32(const ModelConst& mc, const DevP
       const float z = f.v[j] * d;
       fac[j] = 1.0f + (z + em1mx(z));
     }
-    for (int n = 0; n < N; ++n) {
-      const int c = mc.cls[l][n];
-      float fc = 1.0f;
+    if (use_pat) {
 #pragma unroll
-      for (int j = 0; j < NC; ++j)
-        if (j == c) fc = fac[j];
-      mu[n * B + tid] *= fc;
+      for (int r = 0; r < kMaxPat; ++r)
+        if (r < mc.npat) {
+          const int c = mc.pcls[l][r];
+          float fc = 1.0f;
+#pragma unroll
+          for (int j = 0; j < NC; ++j)
+            if (j == c) fc = fac[j];
+          E[r] *= fc;
+        }
+    } else {
+      for (int n = 0; n < N; ++n) {
+        const int c = mc.cls[l][n];
+        float fc = 1.0f;
+#pragma unroll
+        for (int j = 0; j < NC; ++j)
+          if (j == c) fc = fac[j];
+        mu[n * B + tid] *= fc;
+      }
     }
   }
   bs[l * B + tid] = s.x;
@@ -544,6 +572,28 @@ __device__ __forceinline__ void gb_f32_body(const ModelConst& mc, const DevPtrsF
       ys[n * B + tid] = (float)p.y[e];
     }
 
+    // per-pattern sums of the rates and counts, in registers, when X has at most
+    // kMaxPat distinct rows (the move below keeps every rate)
+    const bool use_pat = mc.npat <= kMaxPat;
+    float E[kMaxPat], Yp[kMaxPat];
+#pragma unroll
+    for (int r = 0; r < kMaxPat; ++r) {
+      E[r] = 0.0f;
+      Yp[r] = 0.0f;
+    }
+    if (use_pat) {
+      for (int n = 0; n < N; ++n) {
+        const int pr = mc.pat[n];
+        const float m = mu[n * B + tid], yv = ys[n * B + tid];
+#pragma unroll
+        for (int r = 0; r < kMaxPat; ++r)
+          if (r == pr) {
+            E[r] += m;
+            Yp[r] += yv;
+          }
+      }
+    }
+
     // ---- learned-proposal move (keeps every log-rate, so mu stays valid)
     int kind = p.prop != nullptr ? move_kind(p, g, it) : 0;
     if (kind == kMoveNet && !net_ok) kind = 0;
@@ -587,19 +637,19 @@ __device__ __forceinline__ void gb_f32_body(const ModelConst& mc, const DevPtrsF
       switch (mc.ncls[l]) {
         case 1:
           beta_column_f32<1>(mc, p, l, g, mu, ys, bs, B, tid, hy, it, it32, burnin, tune_start,
-                             evals_b, caps, nonfin);
+                             evals_b, caps, nonfin, use_pat, E, Yp);
           break;
         case 2:
           beta_column_f32<2>(mc, p, l, g, mu, ys, bs, B, tid, hy, it, it32, burnin, tune_start,
-                             evals_b, caps, nonfin);
+                             evals_b, caps, nonfin, use_pat, E, Yp);
           break;
         case 3:
           beta_column_f32<3>(mc, p, l, g, mu, ys, bs, B, tid, hy, it, it32, burnin, tune_start,
-                             evals_b, caps, nonfin);
+                             evals_b, caps, nonfin, use_pat, E, Yp);
           break;
         default:
           beta_column_f32<kMaxCls>(mc, p, l, g, mu, ys, bs, B, tid, hy, it, it32, burnin,
-                                   tune_start, evals_b, caps, nonfin);
+                                   tune_start, evals_b, caps, nonfin, use_pat, E, Yp);
       }
     }
 

@@ -95,6 +95,52 @@ def test_f32_beta_transition_keeps_its_conditional(l):
     assert ks_pvalue(st["beta"][:, l], dist) > P_MIN
 
 
+def test_f32_beta_transition_many_rows():
+    """A design with 12 distinct rows, more than the 8 row patterns whose rate
+    sums the FP32 beta columns keep in registers, so the update sums the rates
+    sample by sample: column 1 (three value classes) keeps its conditional;
+    eps and columns 0 and 2 are held."""
+    N, L, l = 12, 3, 1
+    a_vals, b_vals = np.array([-1.0, 1.0, 2.0]), np.array([-1.0, 0.0, 1.0, 2.0])
+    X = np.stack([np.ones(N), a_vals[np.arange(N) % 3], b_vals[np.arange(N) // 3]], 1)
+    assert len({tuple(r) for r in X}) == 12
+    h = np.linspace(-0.1, 0.1, N)
+    y_row = np.array([3, 9, 0, 22, 5, 1, 14, 7, 2, 30, 6, 11], np.int32)
+    y = np.tile(y_row, (G, 1))
+    pri = {"a": 1.0, "b": 1.0, "d": 10.0, "c": np.full(L, 10.0), "s": np.full(L, 10.0)}
+    s = fbs.Sampler(y, X, h, pri, seed=81, precision=fbs.FBS_F32)
+    eps_row = np.linspace(-0.3, 0.3, N)
+    beta_row = np.array([1.2, -0.3, 0.2])
+    phi = [3.0, 1.0, 0.8, 0.1, 0.0, 0.5, 0.3, 0.4]
+
+    @vectorized
+    def logpost(b):
+        b = np.asarray(b, float)[..., None]
+        bb = np.where(np.arange(L) == l, b, beta_row)
+        lam = np.exp(h + eps_row + bb @ X.T)
+        out = stats.poisson.logpmf(y_row, lam).sum(-1)
+        return out + stats.norm.logpdf(b[..., 0], phi[2 + l], np.sqrt(phi[2 + L + l]))
+
+    lo, hi = bracket(logpost, beta_row[l], 0.05)
+    dist = GridDist(logpost, lo, hi)
+    rng = np.random.default_rng(91)
+    start = np.tile(beta_row, (G, 1))
+    start[:, l] = dist.sample(G, rng)
+    w_beta = np.full((G, L), FROZEN)
+    w_beta[:, l] = 1.0
+    s.set_state(it=0, eps=np.tile(eps_row, (G, 1)), beta=start, gam=np.full(G, 0.3), phi=phi,
+                w_eps=np.full((G, N), FROZEN), w_beta=w_beta)
+    s.run(1, burnin=0)
+    s.sync()
+    st = s.get_state()
+    assert np.max(np.abs(st["eps"] - eps_row.astype(np.float32))) < 1e-6
+    for k in (0, 2):
+        assert np.max(np.abs(st["beta"][:, k] - beta_row[k])) < 1e-6
+    assert np.mean(st["beta"][:, l] != start[:, l].astype(np.float32)) > 0.99
+    assert ks_pvalue(st["beta"][:, l], dist) > P_MIN
+    s.close()
+
+
 def test_f32_gamma_draw_is_its_inverse_gamma():
     """With eps held, gamma_g after one sweep is a draw from Inverse-Gamma((N +
     nu)/2, (sum_n eps_gn^2 + nu tau)/2) (step 2); tested against scipy's CDF."""

@@ -102,9 +102,9 @@ FP64_TRAFFIC_BYTES = 44.1e6   # dram read+write of both kernels per sweep, same 
 # eps kernel and the gamma/beta kernel (k_gb_f32; with the learned proposal
 # k_gb_net_f32, which includes the network pass, in a sampling sweep after
 # calibration) and their dram read+write (writes stay in L2), from ncu captures
-# at config 1 (bench.py --profile-run; k_gb_f32 from an earlier capture)
-FP32_WARP_INST = {"f32": 22.40e6 + 10.68e6, "learned": 22.40e6 + 20.56e6}
-FP32_TRAFFIC_BYTES = {"f32": 18.9e6 + 13.2e6, "learned": 18.9e6 + 15.47e6}
+# at config 1 (bench.py --profile-run)
+FP32_WARP_INST = {"f32": 22.39e6 + 9.49e6, "learned": 22.39e6 + 19.42e6}
+FP32_TRAFFIC_BYTES = {"f32": 18.9e6 + 13.23e6, "learned": 18.9e6 + 15.47e6}
 # issue peak: 152 SMs x 4 schedulers x 1 warp instruction per clock x 2.07 GHz
 ISSUE_PEAK_WARP_INST_S = 152 * 4 * 2.07e9
 # the proposal network's own flops per gene (2 x (F*64 + 64*64 + 64*K), F = 21,

@@ -50,7 +50,21 @@ struct Rng4 {
     }
     const uint32_t j = k & 3u;
     const uint32_t x = j == 0 ? w.x : (j == 1 ? w.y : (j == 2 ? w.z : w.w));
+    return word(x);
+  }
+
+  // The uniform of Philox word x.
+  static __device__ __forceinline__ float word(uint32_t x) {
     return __fmul_rn(__fadd_rn(__uint2float_rn(x >> 9), 0.5f), 0x1p-23f);
+  }
+
+  // Philox block blk (uniforms 4 blk .. 4 blk + 3), cached.
+  __device__ __forceinline__ uint4 block(uint32_t blk) {
+    if (blk != cached) {
+      w = philox4x32_10(make_uint4(index, sblk | blk, iter, chain), key0, key1);
+      cached = blk;
+    }
+    return w;
   }
 };
 
@@ -147,16 +161,31 @@ __device__ __forceinline__ SliceResultF slice_update_f(float x0, float aux0, flo
     ++res.evals;
     if (logu < f(hi, &aux)) hi = __fadd_rn(hi, w); else break;
   }
-  for (int j = 0; j < shrink_max; ++j) {
-    const float xs = __fadd_rn(lo, __fmul_rn(__fsub_rn(hi, lo), r.u(3u + (uint32_t)j)));
+  // shrinkage: proposal j takes uniform 3 + j (word 3 of block 0, then the four
+  // words of block 1, 2, ..), so that the word is a compile-time choice
+  auto propose = [&](float u) -> bool {
+    const float xs = __fadd_rn(lo, __fmul_rn(__fsub_rn(hi, lo), u));
     ++res.evals;
     if (logu < f(xs, &aux)) {
       res.x = xs;
       res.aux = aux;
       res.capped = false;
-      return res;
+      return true;
     }
     if (xs > x0) hi = xs; else lo = xs;
+    return false;
+  };
+  if (shrink_max > 0 && propose(Rng4::word(r.block(0u).w))) return res;
+  for (int j = 1, b = 1; j < shrink_max; ++b) {
+    const uint4 q = r.block((uint32_t)b);
+    if (propose(Rng4::word(q.x))) return res;
+    if (++j >= shrink_max) break;
+    if (propose(Rng4::word(q.y))) return res;
+    if (++j >= shrink_max) break;
+    if (propose(Rng4::word(q.z))) return res;
+    if (++j >= shrink_max) break;
+    if (propose(Rng4::word(q.w))) return res;
+    ++j;
   }
   res.x = x0;
   res.aux = aux0;

@@ -103,8 +103,8 @@ FP64_TRAFFIC_BYTES = 44.1e6   # dram read+write of both kernels per sweep, same 
 # k_gb_net_f32, which includes the network pass, in a sampling sweep after
 # calibration) and their dram read+write (writes stay in L2), from ncu captures
 # at config 1 (bench.py --profile-run)
-FP32_WARP_INST = {"f32": 22.39e6 + 9.49e6, "learned": 22.39e6 + 19.42e6}
-FP32_TRAFFIC_BYTES = {"f32": 18.9e6 + 13.23e6, "learned": 18.9e6 + 15.47e6}
+FP32_WARP_INST = {"f32": 21.01e6 + 9.12e6, "learned": 21.01e6 + 19.08e6}
+FP32_TRAFFIC_BYTES = {"f32": 19.7e6 + 13.24e6, "learned": 19.7e6 + 15.49e6}
 # issue peak: 152 SMs x 4 schedulers x 1 warp instruction per clock x 2.07 GHz
 ISSUE_PEAK_WARP_INST_S = 152 * 4 * 2.07e9
 # the proposal network's own flops per gene (2 x (F*64 + 64*64 + 64*K), F = 21,
